@@ -1,0 +1,203 @@
+/*
+ * rf.h - C ABI of the reduced-frequency Lippmann-Schwinger solver for GB300 (sm_103a).
+ *
+ * The library solves the periodic microscopic boundary value problem of Sec. 2 (div sigma = 0,
+ * sigma = sigma(eps, internal variables), eps = ebar + symmetric gradient of a periodic
+ * displacement) with the reduced fixed-point scheme of Sec. 4: per iteration
+ *   a) polarization stress tau = sigma(eps) - C0 : eps on every voxel,
+ *   b) its DFT, evaluated only on the K frequencies of a sampling pattern,
+ *   c) eps^(xi) = -Gamma0(xi) : tau^(xi) for xi != 0, eps^(0) = N ebar (Sec. 3, eq. Gamma),
+ *   d) the inverse DFT from those K frequencies back to the grid,
+ * until the convergence measure of Sec. 3 drops below tol. Every step runs in the library's
+ * own CUDA kernels; nothing falls back to the CPU.
+ *
+ * Conventions
+ *  - Grid: n[0] = Nx, n[1] = Ny, n[2] = Nz; Nz = 1 for dim = 2. Voxel fields are x fastest.
+ *    2D problems are plane strain (eps_33 = eps_13 = eps_23 = 0; sigma_33 is an output).
+ *  - Six-component tensors use the order (11, 22, 33, 23, 13, 12) with TENSOR shear
+ *    components (eps_12, not gamma_12).
+ *  - A frequency is an int32 triple (kx, ky, kz) in the signed range (-N_j/2, N_j/2]; the
+ *    DFT is f^(k) = sum_x f(x) exp(-2 pi i sum_j k_j x_j / N_j), the inverse carries 1/N.
+ *  - A pattern (the reduced set of Sec. 4) holds the zero frequency once, no duplicates, and
+ *    is closed under k -> -k (mod N).
+ *  - Units are the caller's; the synthetic workloads use GPa.
+ *
+ * Errors: every call returns an int status. 0 = RF_OK; RF_NOT_CONVERGED (1) means the
+ * iteration cap was reached, outputs are written. Negative values are hard errors; outputs
+ * are then unspecified. rf_last_error() returns a message for the calling thread (owned by
+ * the library, valid until the thread's next call). No C++ exception crosses this ABI.
+ *
+ * Ownership: the caller owns every pointer it passes; inputs are copied before the call
+ * returns unless stated otherwise. Outputs go to caller-owned buffers of the documented size.
+ * A context owns all device memory it allocates and frees it in rf_destroy.
+ * Threading: a context must not be used from two threads at once.
+ */
+#ifndef RF_H
+#define RF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RF_OK = 0,
+  RF_NOT_CONVERGED = 1,
+  RF_ERR_INVALID = -1,
+  RF_ERR_CUDA = -2,
+  RF_ERR_NONFINITE = -3,
+  RF_ERR_DIVERGED = -4,
+  RF_ERR_OOM = -5,
+  RF_ERR_TIMEOUT = -6,
+  RF_ERR_STATE = -7
+};
+
+enum { RF_GREEN_ROTATED = 0, RF_GREEN_CONTINUOUS = 1 };
+enum { RF_REF_MINMAX = 0, RF_REF_VOLUME = 1 };
+enum { RF_PREC_FP32 = 0, RF_PREC_SPLIT_BF16 = 1 };
+
+typedef struct rf_ctx rf_ctx;
+
+/* Grid: dim in {2, 3}; n = (Nx, Ny, Nz), each >= 1, Nz = 1 when dim = 2; Nx <= 4096,
+ * Ny, Nz <= 4096, Nx*Ny*Nz < 2^31. */
+typedef struct rf_grid {
+  int32_t dim;
+  int32_t n[3];
+} rf_grid;
+
+/* One phase (Sec. 2): isotropic linear elasticity (lambda, mu > 0); when plastic != 0 also the
+ * von Mises yield function with linear isotropic hardening, initial yield stress sigma_y0 > 0
+ * and hardening modulus H >= 0 (associative flow, radial return). */
+typedef struct rf_phase {
+  double lambda;
+  double mu;
+  double sigma_y0;
+  double hardening;
+  int32_t plastic;
+  int32_t reserved;
+} rf_phase;
+
+/* Solver options.
+ *  tol        convergence measure threshold (Sec. 3): RMS over voxels of the Frobenius norm of
+ *             eps^(i+1) - eps^(i), divided by the Frobenius norm of ebar; iterate while >= tol.
+ *  max_iter   cap on fixed-point updates per solve (>= 1).
+ *  green      RF_GREEN_ROTATED: wave vector of first-order finite differences on the rotated
+ *             stencil (Sec. 3); RF_GREEN_CONTINUOUS: q = 2 pi k / N (Nyquist frequencies get a
+ *             zero operator).
+ *  ref_medium RF_REF_MINMAX: lambda0 = (min + max)/2 and mu0 likewise over the phases present
+ *             (the basic scheme of Sec. 3); RF_REF_VOLUME: volume averages.
+ *  precision  RF_PREC_FP32 (SIMT FP32 transforms) or RF_PREC_SPLIT_BF16 (tensor-core
+ *             transforms with hi/lo BF16 operands and FP32 accumulation). The residual and
+ *             the homogenised stress are accumulated in FP64 in both modes.
+ *  check_every  iterations launched between host checks of the device convergence flag
+ *             (0 = library default). Work after convergence is skipped on the device, so
+ *             results do not depend on it. */
+typedef struct rf_options {
+  double tol;
+  int32_t max_iter;
+  int32_t green;
+  int32_t ref_medium;
+  int32_t precision;
+  int32_t check_every;
+  int32_t reserved[3];
+} rf_options;
+
+/* Run statistics of the last solve on a context. */
+typedef struct rf_info {
+  int64_t K;              /* pattern size */
+  int64_t K_half;         /* frequencies held on the device (kx >= 0 half of the pattern) */
+  int32_t Kx, Ky, Kz;     /* distinct kx >= 0, ky, kz values of that half */
+  int32_t last_iters;     /* fixed-point updates of the last solve */
+  double last_residual;   /* convergence measure after the last update */
+  int64_t kernel_launches;/* kernels this context has launched so far */
+  double j2_max_violation;/* FP64 check of the last commit: max |sigma_eq - (sy + H a)| / sy */
+  double lambda0, mu0;    /* reference medium in use */
+} rf_info;
+
+/* Create a solver context for one microstructure.
+ *  phase_map: HOST uint8 [Nz][Ny][Nx], entries < n_phases (1 <= n_phases <= 16); copied.
+ *  stream: a cudaStream_t (or NULL for the legacy default stream) on which all work of this
+ *  context is enqueued. The device is the current CUDA device at creation.
+ *  Errors: RF_ERR_INVALID for bad sizes, phases or ids; RF_ERR_OOM; RF_ERR_CUDA. */
+int rf_create(rf_ctx** ctx, const rf_grid* grid, int32_t n_phases, const rf_phase* phases,
+              const uint8_t* phase_map, const rf_options* opt, void* stream);
+
+/* Replace the phase map (same grid) from HOST memory, or from DEVICE memory (same device,
+ * readable on the context's stream). The reference medium is recomputed; the internal
+ * variables and the load-path state are reset. */
+int rf_set_phase_map(rf_ctx* ctx, const uint8_t* phase_map);
+int rf_set_phase_map_device(rf_ctx* ctx, const uint8_t* d_phase_map);
+
+/* Set the reduced set of frequencies (Sec. 4), HOST int32 [K][3] (kx, ky, kz); copied.
+ * Must satisfy the pattern rules above (checked: RF_ERR_INVALID). Resets the load-path state. */
+int rf_set_pattern(rf_ctx* ctx, const int32_t* freqs, int64_t K);
+
+/* One solve at macroscopic strain macro[6] with the internal variables held fixed (they are
+ * not committed). warm: nullable HOST float [K][6][2] (re, im) start coefficients in the
+ * pattern's order, projected onto compatible strains before use; NULL = uniform start
+ * eps = ebar. Outputs (each nullable): homogenised stress [6] (volume average, FP64
+ * accumulation), iteration count, final convergence measure.
+ * Returns RF_OK, RF_NOT_CONVERGED, or an error (RF_ERR_NONFINITE if the measure is not finite). */
+int rf_solve(rf_ctx* ctx, const double macro[6], const float* warm, double hom_stress[6],
+             int32_t* iters, double* residual);
+
+/* Load path: n_steps macroscopic strains path[n_steps][6] applied as increments from the
+ * context's current state (after rf_create / rf_set_pattern / rf_reset_path: zero strain, zero
+ * internal variables). Each increment starts from eps_(n-1) + (ebar_n - ebar_(n-1)), iterates
+ * with the internal variables frozen, then commits them from the return map at the converged
+ * strain. Outputs (nullable): hom_stress [n_steps][6], iters [n_steps], residuals [n_steps].
+ * Returns RF_OK, or RF_NOT_CONVERGED if any increment hit max_iter (the path continues). */
+int rf_solve_path(rf_ctx* ctx, int32_t n_steps, const double* path, double* hom_stress,
+                  int32_t* iters, double* residuals);
+
+/* Reset the load-path state (strain and internal variables) to zero. */
+int rf_reset_path(rf_ctx* ctx);
+
+/* Fields of the last solve, HOST float buffers (nullable) of [6][N] (strain, stress; order
+ * 11,22,33,23,13,12) and [N] (accumulated plastic strain after the last commit). */
+int rf_get_fields(rf_ctx* ctx, float* strain, float* stress, float* eps_p_acc);
+
+/* Reduced strain coefficients of the last solve: HOST float [K][6][2] in the pattern's order. */
+int rf_get_reduced_strain(rf_ctx* ctx, float* coeffs);
+
+/* Checkpoint of the load-path state (strain coefficients, internal variables, last macro
+ * strain). Call with buf = NULL to get the size in *bytes. rf_set_state restores a buffer
+ * produced by rf_get_state on a context with the same grid, phases and pattern. */
+int rf_get_state(rf_ctx* ctx, void* buf, size_t* bytes);
+int rf_set_state(rf_ctx* ctx, const void* buf, size_t bytes);
+
+int rf_get_info(const rf_ctx* ctx, rf_info* info);
+
+/* Destroy a context and free its device memory. NULL is accepted. */
+int rf_destroy(rf_ctx* ctx);
+
+/* Geometrically adapted sampling pattern (Sec. 4.2, 3D as in Sec. 5.3): the step function
+ * g = [phase == inclusion_phase] is transformed (FP64), amplitudes |g^| are quantised to
+ * round(|g^| / |g^(0)| * 2^30); pairs (k, -k) are ranked by (larger amplitude, smaller |k|^2,
+ * smaller signed linear index) and added whole until >= k_target frequencies are held.
+ *  phase_map: HOST uint8 [Nz][Ny][Nx]. freqs_out: HOST int32 [cap][3], sorted by signed linear
+ *  index (z slowest, x fastest; index = ((kz+hz)Ny + ky+hy)Nx + kx+hx, h_j = (N_j-1)/2).
+ *  *K_out receives the pattern size (k_target or k_target + 1); RF_ERR_INVALID if it exceeds cap.
+ *  stream: cudaStream_t or NULL. Runs on the current device; allocates and frees scratch. */
+int rf_pattern_adapted(const rf_grid* grid, const uint8_t* phase_map, int32_t inclusion_phase,
+                       int64_t k_target, int32_t* freqs_out, int64_t cap, int64_t* K_out,
+                       void* stream);
+
+/* Fixed radial sampling pattern (Sec. 4.1), 2D only. The paper shows it only as a figure;
+ * this library's reading: L equiangular lines through the origin at angles pi l / L, each
+ * rasterised by unit steps along its dominant axis with the other coordinate rounded half away
+ * from zero; the smallest L whose union holds >= k_target frequencies; trimmed by keeping
+ * pairs of smaller |k|^2 first (ties: signed linear index). Output as rf_pattern_adapted. */
+int rf_pattern_radial(const rf_grid* grid, int64_t k_target, int32_t* freqs_out, int64_t cap,
+                      int64_t* K_out, void* stream);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* rf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RF_H */

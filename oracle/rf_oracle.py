@@ -326,11 +326,13 @@ def solve(phase_map, phases, macro_strain, pattern, tol=1e-6, max_iter=1000,
 
 
 def solve_path(phase_map, phases, path, pattern, tol=1e-6, max_iter=1000, scheme="rotated",
-               ref="minmax"):
+               ref="minmax", fixed_iters=None):
     """Load path of macroscopic strains path[n] (n = 0..T-1), one increment at a time.
 
     Internal variables are frozen during the iterations of an increment and committed from the
     return map at its converged strain; increment n starts from eps_{n-1} + (ebar_n - ebar_{n-1}).
+    fixed_iters: optional per-increment update counts (tol is then ignored), to replay a path
+    iterate by iterate.
     Returns (sigma_bar [T,6], iters [T], last SolveResult).
     """
     pm = _as_grid(phase_map)
@@ -344,7 +346,8 @@ def solve_path(phase_map, phases, path, pattern, tol=1e-6, max_iter=1000, scheme
     res = None
     for n, e in enumerate(path):
         eps0 = None if eps is None else eps + vec6_to_tensor(e - prev)
-        res = solve(pm, phases, e, pattern, tol, max_iter, scheme, ref, eps_p=eps_p,
+        t_n, m_n = (tol, max_iter) if fixed_iters is None else (0.0, int(fixed_iters[n]))
+        res = solve(pm, phases, e, pattern, t_n, m_n, scheme, ref, eps_p=eps_p,
                     alpha=alpha, eps0=eps0)
         if res.eps_p is not None:
             eps_p, alpha = res.eps_p, res.alpha

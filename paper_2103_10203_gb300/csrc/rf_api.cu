@@ -1,0 +1,741 @@
+// C ABI of the reduced-frequency solver: contexts, pattern bookkeeping, solve loops.
+//
+// Host code here only validates inputs, builds index tables for the reduced set and drives
+// kernel launches; all arithmetic of the scheme runs in the kernels of rf_kernels.cu and
+// rf_pattern.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "rf_internal.cuh"
+
+namespace rfk {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& m) { g_err = m; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? RF_ERR_OOM : RF_ERR_CUDA;
+}
+
+long long zero_base(const rf_ctx* c) { return c->zero_base_idx; }
+
+}  // namespace rfk
+
+using namespace rfk;
+
+namespace {
+
+struct DeviceGuard {
+  int old = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&old) == cudaSuccess && old != dev) {
+      cudaSetDevice(dev);
+      changed = true;
+    }
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(old);
+  }
+};
+
+int invalid(const char* msg) {
+  set_error(msg);
+  return RF_ERR_INVALID;
+}
+
+int ck(cudaError_t e, const char* what) { return e == cudaSuccess ? RF_OK : cuda_fail(e, what); }
+
+template <class T>
+int dalloc(T** p, size_t n, const char* what) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  return ck(cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)), what);
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+double frob6(const double* e) {
+  return std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2] +
+                   2.0 * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]));
+}
+
+int signed_of(int i, int n) { return i <= n / 2 ? i : i - n; }
+int wrapi(int k, int n) {
+  int r = k % n;
+  return r < 0 ? r + n : r;
+}
+
+// reference medium from the phases present (device histogram of the phase map)
+int update_reference(rf_ctx* c) {
+  unsigned long long* d_hist = nullptr;
+  if (int e = dalloc(&d_hist, 256, "hist")) return e;
+  std::vector<unsigned long long> hist(256, 0);
+  int err = ck(cudaMemsetAsync(d_hist, 0, 256 * sizeof(unsigned long long), c->stream), "memset");
+  if (!err) err = launch_phase_hist(c, d_hist);
+  if (!err)
+    err = ck(cudaMemcpyAsync(hist.data(), d_hist, 256 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream), "copy hist");
+  if (!err) err = ck(cudaStreamSynchronize(c->stream), "sync hist");
+  cudaFree(d_hist);
+  if (err) return err;
+  double lmin = 1e300, lmax = -1e300, mmin = 1e300, mmax = -1e300, lsum = 0, msum = 0;
+  bool plastic = false;
+  for (int p = 0; p < 256; ++p) {
+    if (!hist[p]) continue;
+    if (p >= c->n_phases) return invalid("phase map holds an id >= n_phases");
+    const rf_phase& ph = c->phases[p];
+    lmin = std::min(lmin, ph.lambda);
+    lmax = std::max(lmax, ph.lambda);
+    mmin = std::min(mmin, ph.mu);
+    mmax = std::max(mmax, ph.mu);
+    lsum += ph.lambda * (double)hist[p];
+    msum += ph.mu * (double)hist[p];
+    plastic = plastic || ph.plastic;
+  }
+  if (c->opt.ref_medium == RF_REF_MINMAX) {
+    c->lam0 = 0.5 * (lmin + lmax);
+    c->mu0 = 0.5 * (mmin + mmax);
+  } else {
+    c->lam0 = lsum / (double)c->N;
+    c->mu0 = msum / (double)c->N;
+  }
+  c->law.lam0 = (float)c->lam0;
+  c->law.mu0 = (float)c->mu0;
+  (void)plastic;
+  return RF_OK;
+}
+
+void free_pattern(rf_ctx* c) {
+  dfree(c->d_kx);
+  dfree(c->d_kym);
+  dfree(c->d_kzm);
+  dfree(c->d_fac);
+  dfree(c->d_hidx);
+  dfree(c->d_hn);
+  dfree(c->d_ER);
+  dfree(c->d_T1);
+  dfree(c->d_T1p);
+  dfree(c->d_T2);
+  dfree(c->d_T2f);
+  dfree(c->d_OUT);
+  dfree(c->d_part);
+  dfree(c->d_sbar_part);
+  dfree(c->d_viol_part);
+  dfree(c->d_warm);
+  c->have_pattern = false;
+  c->fields_valid = false;
+}
+
+int reset_path_state(rf_ctx* c) {
+  for (double& v : c->prev_macro) v = 0.0;
+  if (c->d_ER)
+    if (int e = ck(cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream), "memset ER"))
+      return e;
+  if (c->d_state)
+    if (int e = ck(cudaMemsetAsync(c->d_state, 0, sizeof(float) * c->ns * c->N, c->stream),
+                   "memset state"))
+      return e;
+  c->fields_valid = false;
+  return RF_OK;
+}
+
+int init_status(rf_ctx* c, const double* macro) {
+  Status& s = *c->h_status;
+  s.done = 0;
+  s.iters = 0;
+  s.max_iter = c->opt.max_iter;
+  s.nonfinite = 0;
+  s.tol = c->opt.tol;
+  s.enorm = frob6(macro);
+  s.inv_n2 = 1.0 / ((double)c->N * (double)c->N);
+  s.last_r = 0.0;
+  for (int i = 0; i < 6; ++i) s.ebar[i] = macro[i];
+  return ck(cudaMemcpyAsync(c->d_status, c->h_status, sizeof(Status), cudaMemcpyHostToDevice,
+                            c->stream), "upload status");
+}
+
+int run_iterations(rf_ctx* c) {
+  const int maxchunk = c->opt.check_every > 0 ? c->opt.check_every : 32;
+  int chunk = std::min(4, maxchunk);
+  for (;;) {
+    for (int i = 0; i < chunk; ++i)
+      if (int e = launch_iteration(c)) return e;
+    if (int e = ck(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status),
+                                   cudaMemcpyDeviceToHost, c->stream), "read status"))
+      return e;
+    if (int e = ck(cudaStreamSynchronize(c->stream), "iterate")) return e;
+    if (c->h_status->done) break;
+    chunk = std::min(chunk * 2, maxchunk);
+  }
+  c->last_iters = c->h_status->iters;
+  c->last_residual = c->h_status->last_r;
+  if (c->h_status->nonfinite) {
+    set_error("convergence measure is not finite");
+    return RF_ERR_NONFINITE;
+  }
+  return RF_OK;
+}
+
+int finish(rf_ctx* c, int commit, double* sbar) {
+  if (int e = launch_final(c, commit)) return e;
+  if (int e = ck(cudaMemcpyAsync(c->h_sbar, c->d_sbar, 8 * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream), "read sbar"))
+    return e;
+  if (int e = ck(cudaStreamSynchronize(c->stream), "final pass")) return e;
+  c->fields_valid = true;
+  if (commit) c->last_viol = c->h_sbar[6];
+  for (int i = 0; i < 6; ++i) {
+    if (!std::isfinite(c->h_sbar[i])) {
+      set_error("homogenised stress is not finite");
+      return RF_ERR_NONFINITE;
+    }
+    if (sbar) sbar[i] = c->h_sbar[i];
+  }
+  return RF_OK;
+}
+
+int check_macro(const rf_ctx* c, const double* m) {
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(m[i])) return invalid("macroscopic strain is not finite");
+  if (c->dim == 2 && (m[2] != 0.0 || m[3] != 0.0 || m[4] != 0.0))
+    return invalid("2D (plane strain): macro strain components 33, 23, 13 must be zero");
+  return RF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rf_last_error(void) { return rfk::g_err.c_str(); }
+
+int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phase* phases,
+              const uint8_t* phase_map, const rf_options* opt, void* stream) {
+  set_error("");
+  if (!out || !grid || !phases || !phase_map || !opt) return invalid("rf_create: null argument");
+  *out = nullptr;
+  if (grid->dim != 2 && grid->dim != 3) return invalid("grid: dim must be 2 or 3");
+  for (int j = 0; j < 3; ++j)
+    if (grid->n[j] < 1 || grid->n[j] > 4096) return invalid("grid: sizes must be in [1, 4096]");
+  if (grid->dim == 2 && grid->n[2] != 1) return invalid("grid: Nz must be 1 in 2D");
+  const long long N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  if (N >= (1LL << 31)) return invalid("grid: too many voxels");
+  if (n_phases < 1 || n_phases > kMaxPhases) return invalid("n_phases must be in [1, 16]");
+  for (int p = 0; p < n_phases; ++p) {
+    const rf_phase& ph = phases[p];
+    if (!(ph.mu > 0.0) || !(ph.lambda + 2.0 * ph.mu / 3.0 > 0.0) || !std::isfinite(ph.lambda))
+      return invalid("phase moduli must satisfy mu > 0 and lambda + 2 mu / 3 > 0");
+    if (ph.plastic && (!(ph.sigma_y0 > 0.0) || !(ph.hardening >= 0.0) ||
+                       !std::isfinite(ph.sigma_y0) || !std::isfinite(ph.hardening)))
+      return invalid("plastic phase needs sigma_y0 > 0 and H >= 0");
+  }
+  if (!(opt->tol >= 0.0) || opt->max_iter < 1) return invalid("options: tol >= 0, max_iter >= 1");
+  if (opt->green != RF_GREEN_ROTATED && opt->green != RF_GREEN_CONTINUOUS)
+    return invalid("options: unknown green operator");
+  if (opt->ref_medium != RF_REF_MINMAX && opt->ref_medium != RF_REF_VOLUME)
+    return invalid("options: unknown reference medium rule");
+  if (opt->precision != RF_PREC_FP32 && opt->precision != RF_PREC_SPLIT_BF16)
+    return invalid("options: unknown precision");
+
+  rf_ctx* c = new rf_ctx();
+  cudaGetDevice(&c->dev);
+  c->dim = grid->dim;
+  c->nx = grid->n[0];
+  c->ny = grid->n[1];
+  c->nz = grid->n[2];
+  c->N = N;
+  c->rows = c->ny * c->nz;
+  c->nc = c->dim == 2 ? 3 : 6;
+  c->opt = *opt;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->n_phases = n_phases;
+  bool any_plastic = false;
+  for (int p = 0; p < n_phases; ++p) {
+    c->phases[p] = phases[p];
+    DevPhase& d = c->law.ph[p];
+    d.lam = (float)phases[p].lambda;
+    d.mu = (float)phases[p].mu;
+    d.plastic = phases[p].plastic ? 1 : 0;
+    d.sy = d.plastic ? (float)phases[p].sigma_y0 : 0.f;
+    d.H = d.plastic ? (float)phases[p].hardening : 0.f;
+    any_plastic = any_plastic || d.plastic;
+  }
+  c->has_plastic = any_plastic;
+  c->law.has_plastic = any_plastic;
+  c->ns = any_plastic ? (c->dim == 2 ? 4 : 7) : 0;
+  int err = dalloc(&c->d_phase, N, "phase map");
+  if (!err && c->ns) err = dalloc(&c->d_state, (size_t)c->ns * N, "state");
+  if (!err) err = dalloc(&c->d_twx, c->nx, "tables");
+  if (!err) err = dalloc(&c->d_twy, c->ny, "tables");
+  if (!err) err = dalloc(&c->d_twz, c->nz, "tables");
+  if (!err) err = dalloc(&c->d_status, 1, "status");
+  if (!err) err = dalloc(&c->d_sbar, 8, "sbar");
+  if (!err) err = dalloc(&c->d_eps, 6 * (size_t)N, "fields");
+  if (!err) err = dalloc(&c->d_sig, 6 * (size_t)N, "fields");
+  if (!err) err = dalloc(&c->d_alpha, (size_t)N, "fields");
+  if (!err) err = ck(cudaMallocHost(&c->h_status, sizeof(Status)), "pinned");
+  if (!err) err = ck(cudaMallocHost(&c->h_sbar, 8 * sizeof(double)), "pinned");
+  if (!err)
+    err = ck(cudaMemcpyAsync(c->d_phase, phase_map, N, cudaMemcpyHostToDevice, c->stream),
+             "upload phase map");
+  if (!err && c->d_state)
+    err = ck(cudaMemsetAsync(c->d_state, 0, sizeof(float) * c->ns * N, c->stream), "state");
+  if (!err) err = launch_setup_tables(c);
+  if (!err) err = update_reference(c);
+  if (err) {
+    std::string keep = g_err;
+    rf_destroy(c);
+    g_err = keep;
+    return err;
+  }
+  *out = c;
+  return RF_OK;
+}
+
+int rf_set_phase_map(rf_ctx* c, const uint8_t* pm) {
+  if (!c || !pm) return invalid("rf_set_phase_map: null argument");
+  DeviceGuard dg(c->dev);
+  if (int e = ck(cudaMemcpyAsync(c->d_phase, pm, c->N, cudaMemcpyHostToDevice, c->stream),
+                 "upload phase map"))
+    return e;
+  if (int e = update_reference(c)) return e;
+  return reset_path_state(c);
+}
+
+int rf_set_phase_map_device(rf_ctx* c, const uint8_t* d_pm) {
+  if (!c || !d_pm) return invalid("rf_set_phase_map_device: null argument");
+  DeviceGuard dg(c->dev);
+  if (int e = ck(cudaMemcpyAsync(c->d_phase, d_pm, c->N, cudaMemcpyDeviceToDevice, c->stream),
+                 "copy phase map"))
+    return e;
+  if (int e = update_reference(c)) return e;
+  return reset_path_state(c);
+}
+
+int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
+  if (!c || !freqs) return invalid("rf_set_pattern: null argument");
+  if (K < 1 || K > c->N) return invalid("rf_set_pattern: K must be in [1, N]");
+  DeviceGuard dg(c->dev);
+  const int n[3] = {c->nx, c->ny, c->nz};
+  // signed range (-N/2, N/2]: -(N-1)/2 <= k <= N/2 with integer division
+  auto in_range = [](int k, int nn) { return k >= -((nn - 1) / 2) && k <= nn / 2; };
+  std::map<std::tuple<int, int, int>, long long> index;
+  int zeros = 0;
+  for (long long p = 0; p < K; ++p) {
+    const int kx = freqs[3 * p], ky = freqs[3 * p + 1], kz = freqs[3 * p + 2];
+    if (!in_range(kx, n[0]) || !in_range(ky, n[1]) || !in_range(kz, n[2]))
+      return invalid("rf_set_pattern: frequency outside the signed range (-N/2, N/2]");
+    if (!index.emplace(std::make_tuple(kx, ky, kz), p).second)
+      return invalid("rf_set_pattern: duplicate frequency");
+    if (kx == 0 && ky == 0 && kz == 0) ++zeros;
+  }
+  if (zeros != 1) return invalid("rf_set_pattern: the zero frequency must be present");
+  auto conj = [&](int kx, int ky, int kz) {
+    return std::make_tuple(signed_of(wrapi(-kx, n[0]), n[0]), signed_of(wrapi(-ky, n[1]), n[1]),
+                           signed_of(wrapi(-kz, n[2]), n[2]));
+  };
+  for (const auto& kv : index) {
+    auto [kx, ky, kz] = kv.first;
+    if (!index.count(conj(kx, ky, kz)))
+      return invalid("rf_set_pattern: pattern is not closed under k -> -k");
+  }
+  // half set: kx >= 0, sorted by (kx, ky, kz)
+  std::vector<std::tuple<int, int, int>> H;
+  for (const auto& kv : index)
+    if (std::get<0>(kv.first) >= 0) H.push_back(kv.first);
+  std::sort(H.begin(), H.end());
+  std::vector<int> xs, ys, zs;
+  for (auto& t : H) {
+    xs.push_back(std::get<0>(t));
+    ys.push_back(std::get<1>(t));
+    zs.push_back(std::get<2>(t));
+  }
+  auto uniq = [](std::vector<int>& v) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  };
+  uniq(xs);
+  uniq(ys);
+  uniq(zs);
+  free_pattern(c);
+  c->K = K;
+  c->Kh = (long long)H.size();
+  c->Kx = (int)xs.size();
+  c->Ky = (int)ys.size();
+  c->Kz = (int)zs.size();
+  c->pat.assign(freqs, freqs + 3 * K);
+  std::map<std::tuple<int, int, int>, long long> hpos;
+  for (long long h = 0; h < c->Kh; ++h) hpos[H[h]] = h;
+  c->map_h.assign(K, 0);
+  c->map_conj.assign(K, 0);
+  c->h_src.assign(c->Kh, -1);
+  for (long long p = 0; p < K; ++p) {
+    const int kx = freqs[3 * p], ky = freqs[3 * p + 1], kz = freqs[3 * p + 2];
+    if (kx >= 0) {
+      c->map_h[p] = hpos[std::make_tuple(kx, ky, kz)];
+      c->map_conj[p] = 0;
+      c->h_src[c->map_h[p]] = p;
+    } else {
+      c->map_h[p] = hpos[conj(kx, ky, kz)];
+      c->map_conj[p] = 1;
+    }
+  }
+  auto pos = [](const std::vector<int>& v, int x) {
+    return (int)(std::lower_bound(v.begin(), v.end(), x) - v.begin());
+  };
+  const bool even_x = (c->nx % 2 == 0);
+  std::vector<int> hk(4 * c->Kh);
+  c->h_hidx.assign(c->Kh, HIdx{0, 0, 0, 0});
+  for (long long h = 0; h < c->Kh; ++h) {
+    auto [kx, ky, kz] = H[h];
+    const bool self = (kx == 0) || (even_x && kx == c->nx / 2);
+    hk[4 * h] = kx;
+    hk[4 * h + 1] = ky;
+    hk[4 * h + 2] = kz;
+    hk[4 * h + 3] = self ? 1 : 2;
+    c->h_hidx[h] = HIdx{pos(xs, kx), pos(ys, ky), pos(zs, kz), 0};
+  }
+  std::vector<int> kym(c->Ky), kzm(c->Kz);
+  std::vector<float> fac(c->Kx);
+  for (int i = 0; i < c->Ky; ++i) kym[i] = wrapi(ys[i], c->ny);
+  for (int i = 0; i < c->Kz; ++i) kzm[i] = wrapi(zs[i], c->nz);
+  for (int j = 0; j < c->Kx; ++j) {
+    const bool self = (xs[j] == 0) || (even_x && xs[j] == c->nx / 2);
+    fac[j] = (float)((self ? 1.0 : 2.0) / (double)c->N);
+  }
+  const int NCK = c->nc * c->Kx;
+  c->rect = (long long)c->Kz * c->Ky * NCK;
+  c->zero_base_idx = ((long long)(pos(zs, 0) * c->Ky + pos(ys, 0)) * c->nc) * c->Kx + pos(xs, 0);
+  // split-K for the forward transforms so that the grid covers the GPU
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+  if (c->dim == 2) {
+    const long long blocks = (long long)((NCK + 63) / 64) * ((c->Ky + 31) / 32);
+    c->splitB = (int)std::max(1LL, std::min<long long>((2LL * sms + blocks - 1) / blocks,
+                                                        std::max(1, c->ny / 64)));
+    c->splitC = 1;
+  } else {
+    c->splitB = 1;
+    const long long blocks = (long long)((c->Ky * NCK + 63) / 64) * ((c->Kz + 31) / 32);
+    c->splitC = (int)std::max(1LL, std::min<long long>((2LL * sms + blocks - 1) / blocks,
+                                                        std::max(1, c->nz / 64)));
+  }
+  // row kernel geometry
+  c->row_R = std::max(1, std::min(16, 2048 / c->nx));
+  auto smem_for = [&](int R) {
+    return (size_t)c->nx * sizeof(float2) + (size_t)R * NCK * sizeof(float2) +
+           (size_t)c->Kx * (sizeof(int) + sizeof(float)) + (size_t)R * c->nc * c->nx * sizeof(float) +
+           64;
+  };
+  while (c->row_R > 1 && smem_for(c->row_R) > 160 * 1024) --c->row_R;
+  if (smem_for(c->row_R) > 200 * 1024) return invalid("rf_set_pattern: pattern too wide for the row kernel");
+  c->row_smem = smem_for(c->row_R);
+  c->row_blocks = (c->rows + c->row_R - 1) / c->row_R;
+  const int splits = std::max(c->splitB, c->splitC);
+  int err = dalloc(&c->d_kx, c->Kx, "pattern");
+  if (!err) err = dalloc(&c->d_kym, c->Ky, "pattern");
+  if (!err) err = dalloc(&c->d_kzm, c->Kz, "pattern");
+  if (!err) err = dalloc(&c->d_fac, c->Kx, "pattern");
+  if (!err) err = dalloc(&c->d_hidx, c->Kh, "pattern");
+  if (!err) err = dalloc(&c->d_hn, c->Kh, "pattern");
+  if (!err) err = dalloc(&c->d_ER, c->rect, "coefficients");
+  if (!err) err = dalloc(&c->d_T1, (size_t)c->rows * NCK, "line transforms");
+  if (!err) err = dalloc(&c->d_T1p, (size_t)c->rows * NCK, "line transforms");
+  if (!err && c->dim == 3) err = dalloc(&c->d_T2, (size_t)c->nz * c->Ky * NCK, "line transforms");
+  if (!err && c->dim == 3) err = dalloc(&c->d_T2f, (size_t)c->nz * c->Ky * NCK, "line transforms");
+  if (!err) err = dalloc(&c->d_OUT, (size_t)splits * c->rect, "partials");
+  if (!err) err = dalloc(&c->d_part, (size_t)((c->Kh + 255) / 256), "partials");
+  if (!err) err = dalloc(&c->d_sbar_part, (size_t)c->row_blocks * 6, "partials");
+  if (!err) err = dalloc(&c->d_viol_part, (size_t)c->row_blocks, "partials");
+  if (!err) err = dalloc(&c->d_warm, (size_t)c->Kh * 6, "warm");
+  int* d_hk = nullptr;
+  if (!err) err = dalloc(&d_hk, hk.size(), "pattern");
+  if (!err) err = ck(cudaMemcpyAsync(c->d_kx, xs.data(), sizeof(int) * c->Kx, cudaMemcpyHostToDevice, c->stream), "up");
+  if (!err) err = ck(cudaMemcpyAsync(c->d_kym, kym.data(), sizeof(int) * c->Ky, cudaMemcpyHostToDevice, c->stream), "up");
+  if (!err) err = ck(cudaMemcpyAsync(c->d_kzm, kzm.data(), sizeof(int) * c->Kz, cudaMemcpyHostToDevice, c->stream), "up");
+  if (!err) err = ck(cudaMemcpyAsync(c->d_fac, fac.data(), sizeof(float) * c->Kx, cudaMemcpyHostToDevice, c->stream), "up");
+  if (!err) err = ck(cudaMemcpyAsync(c->d_hidx, c->h_hidx.data(), sizeof(HIdx) * c->Kh, cudaMemcpyHostToDevice, c->stream), "up");
+  if (!err) err = ck(cudaMemcpyAsync(d_hk, hk.data(), sizeof(int) * hk.size(), cudaMemcpyHostToDevice, c->stream), "up");
+  if (!err) err = launch_hinfo(c, d_hk, c->Kh);
+  if (!err) err = ck(cudaMemsetAsync(c->d_OUT, 0, sizeof(float2) * splits * c->rect, c->stream), "memset");
+  if (!err) err = ck(cudaStreamSynchronize(c->stream), "pattern setup");
+  if (d_hk) cudaFree(d_hk);
+  if (!err) {
+    // frequency kinds back to the host copy (zero / null flags)
+    err = ck(cudaMemcpy(c->h_hidx.data(), c->d_hidx, sizeof(HIdx) * c->Kh, cudaMemcpyDeviceToHost),
+             "read kinds");
+  }
+  if (err) {
+    free_pattern(c);
+    return err;
+  }
+  c->have_pattern = true;
+  return reset_path_state(c);
+}
+
+int rf_reset_path(rf_ctx* c) {
+  if (!c) return invalid("rf_reset_path: null context");
+  DeviceGuard dg(c->dev);
+  return reset_path_state(c);
+}
+
+int rf_solve(rf_ctx* c, const double macro[6], const float* warm, double hom_stress[6],
+             int32_t* iters, double* residual) {
+  if (!c || !macro) return invalid("rf_solve: null argument");
+  if (!c->have_pattern) {
+    set_error("rf_solve: no pattern set");
+    return RF_ERR_STATE;
+  }
+  if (int e = check_macro(c, macro)) return e;
+  DeviceGuard dg(c->dev);
+  if (int e = init_status(c, macro)) return e;
+  if (warm) {
+    std::vector<float2> w6((size_t)c->Kh * 6);
+    for (long long h = 0; h < c->Kh; ++h) {
+      const long long p = c->h_src[h];
+      for (int i = 0; i < 6; ++i)
+        w6[h * 6 + i] = make_float2(warm[(p * 6 + i) * 2], warm[(p * 6 + i) * 2 + 1]);
+    }
+    if (int e = ck(cudaMemcpyAsync(c->d_warm, w6.data(), sizeof(float2) * w6.size(),
+                                   cudaMemcpyHostToDevice, c->stream), "upload warm"))
+      return e;
+    if (int e = ck(cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream), "memset"))
+      return e;
+    if (int e = launch_warm_project(c, c->d_warm, macro)) return e;
+    // the staging vector must outlive the copy
+    if (int e = ck(cudaStreamSynchronize(c->stream), "warm")) return e;
+  } else {
+    if (int e = launch_reset_er(c, macro, 0.0)) return e;
+  }
+  int st = run_iterations(c);
+  if (st < 0) return st;
+  if (int e = finish(c, 0, hom_stress)) return e;
+  for (int i = 0; i < 6; ++i) c->prev_macro[i] = macro[i];
+  if (iters) *iters = c->last_iters;
+  if (residual) *residual = c->last_residual;
+  return c->last_residual < c->opt.tol ? RF_OK : RF_NOT_CONVERGED;
+}
+
+int rf_solve_path(rf_ctx* c, int32_t n_steps, const double* path, double* hom_stress,
+                  int32_t* iters, double* residuals) {
+  if (!c || !path || n_steps < 1) return invalid("rf_solve_path: invalid arguments");
+  if (!c->have_pattern) {
+    set_error("rf_solve_path: no pattern set");
+    return RF_ERR_STATE;
+  }
+  for (int n = 0; n < n_steps; ++n)
+    if (int e = check_macro(c, path + 6 * n)) return e;
+  DeviceGuard dg(c->dev);
+  int status = RF_OK;
+  for (int n = 0; n < n_steps; ++n) {
+    const double* m = path + 6 * n;
+    double d[6];
+    for (int i = 0; i < 6; ++i) d[i] = m[i] - c->prev_macro[i];
+    if (int e = init_status(c, m)) return e;
+    if (int e = launch_reset_er(c, d, 1.0)) return e;
+    int st = run_iterations(c);
+    if (st < 0) return st;
+    if (int e = finish(c, 1, hom_stress ? hom_stress + 6 * n : nullptr)) return e;
+    for (int i = 0; i < 6; ++i) c->prev_macro[i] = m[i];
+    if (iters) iters[n] = c->last_iters;
+    if (residuals) residuals[n] = c->last_residual;
+    if (!(c->last_residual < c->opt.tol)) status = RF_NOT_CONVERGED;
+  }
+  return status;
+}
+
+int rf_get_fields(rf_ctx* c, float* strain, float* stress, float* eps_p_acc) {
+  if (!c) return invalid("rf_get_fields: null context");
+  if (!c->fields_valid) {
+    set_error("rf_get_fields: no solve has produced fields yet");
+    return RF_ERR_STATE;
+  }
+  DeviceGuard dg(c->dev);
+  if (strain)
+    if (int e = ck(cudaMemcpyAsync(strain, c->d_eps, sizeof(float) * 6 * c->N,
+                                   cudaMemcpyDeviceToHost, c->stream), "copy strain"))
+      return e;
+  if (stress)
+    if (int e = ck(cudaMemcpyAsync(stress, c->d_sig, sizeof(float) * 6 * c->N,
+                                   cudaMemcpyDeviceToHost, c->stream), "copy stress"))
+      return e;
+  if (eps_p_acc)
+    if (int e = ck(cudaMemcpyAsync(eps_p_acc, c->d_alpha, sizeof(float) * c->N,
+                                   cudaMemcpyDeviceToHost, c->stream), "copy alpha"))
+      return e;
+  return ck(cudaStreamSynchronize(c->stream), "get fields");
+}
+
+int rf_get_reduced_strain(rf_ctx* c, float* coeffs) {
+  if (!c || !coeffs) return invalid("rf_get_reduced_strain: null argument");
+  if (!c->have_pattern) {
+    set_error("rf_get_reduced_strain: no pattern set");
+    return RF_ERR_STATE;
+  }
+  DeviceGuard dg(c->dev);
+  std::vector<float2> er(c->rect);
+  if (int e = ck(cudaMemcpyAsync(er.data(), c->d_ER, sizeof(float2) * c->rect,
+                                 cudaMemcpyDeviceToHost, c->stream), "copy coefficients"))
+    return e;
+  if (int e = ck(cudaStreamSynchronize(c->stream), "sync")) return e;
+  for (long long p = 0; p < c->K; ++p) {
+    const HIdx& hi = c->h_hidx[c->map_h[p]];
+    const long long base = ((long long)(hi.iz * c->Ky + hi.iy) * c->nc) * c->Kx + hi.j;
+    const float sg = c->map_conj[p] ? -1.f : 1.f;
+    for (int i = 0; i < 6; ++i) {
+      int comp = -1;
+      if (c->nc == 6) comp = i;
+      else if (i == 0) comp = 0;
+      else if (i == 1) comp = 1;
+      else if (i == 5) comp = 2;
+      float re = 0.f, im = 0.f;
+      if (comp >= 0) {
+        const float2 v = er[base + (long long)comp * c->Kx];
+        re = v.x;
+        im = sg * v.y;
+      }
+      coeffs[(p * 6 + i) * 2] = re;
+      coeffs[(p * 6 + i) * 2 + 1] = im;
+    }
+  }
+  return RF_OK;
+}
+
+struct StateHeader {
+  uint64_t magic;
+  int64_t N, rect;
+  int32_t nc, ns;
+  double prev_macro[6];
+};
+
+int rf_get_state(rf_ctx* c, void* buf, size_t* bytes) {
+  if (!c || !bytes) return invalid("rf_get_state: null argument");
+  if (!c->have_pattern) {
+    set_error("rf_get_state: no pattern set");
+    return RF_ERR_STATE;
+  }
+  const size_t need = sizeof(StateHeader) + sizeof(float2) * c->rect +
+                      sizeof(float) * (size_t)c->ns * c->N;
+  if (!buf) {
+    *bytes = need;
+    return RF_OK;
+  }
+  if (*bytes < need) return invalid("rf_get_state: buffer too small");
+  DeviceGuard dg(c->dev);
+  StateHeader h{0x52465354415445ull, c->N, c->rect, c->nc, c->ns, {0}};
+  for (int i = 0; i < 6; ++i) h.prev_macro[i] = c->prev_macro[i];
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  if (int e = ck(cudaMemcpyAsync(p, c->d_ER, sizeof(float2) * c->rect, cudaMemcpyDeviceToHost,
+                                 c->stream), "copy state"))
+    return e;
+  p += sizeof(float2) * c->rect;
+  if (c->ns)
+    if (int e = ck(cudaMemcpyAsync(p, c->d_state, sizeof(float) * c->ns * c->N,
+                                   cudaMemcpyDeviceToHost, c->stream), "copy state"))
+      return e;
+  *bytes = need;
+  return ck(cudaStreamSynchronize(c->stream), "get state");
+}
+
+int rf_set_state(rf_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return invalid("rf_set_state: null argument");
+  if (!c->have_pattern) {
+    set_error("rf_set_state: no pattern set");
+    return RF_ERR_STATE;
+  }
+  StateHeader h;
+  if (bytes < sizeof h) return invalid("rf_set_state: buffer too small");
+  std::memcpy(&h, buf, sizeof h);
+  const size_t need = sizeof(StateHeader) + sizeof(float2) * c->rect +
+                      sizeof(float) * (size_t)c->ns * c->N;
+  if (h.magic != 0x52465354415445ull || h.N != c->N || h.rect != c->rect || h.nc != c->nc ||
+      h.ns != c->ns || bytes < need)
+    return invalid("rf_set_state: state does not match this context");
+  DeviceGuard dg(c->dev);
+  const char* p = static_cast<const char*>(buf) + sizeof h;
+  if (int e = ck(cudaMemcpyAsync(c->d_ER, p, sizeof(float2) * c->rect, cudaMemcpyHostToDevice,
+                                 c->stream), "restore"))
+    return e;
+  p += sizeof(float2) * c->rect;
+  if (c->ns)
+    if (int e = ck(cudaMemcpyAsync(c->d_state, p, sizeof(float) * c->ns * c->N,
+                                   cudaMemcpyHostToDevice, c->stream), "restore"))
+      return e;
+  for (int i = 0; i < 6; ++i) c->prev_macro[i] = h.prev_macro[i];
+  c->fields_valid = false;
+  return ck(cudaStreamSynchronize(c->stream), "set state");
+}
+
+int rf_get_info(const rf_ctx* c, rf_info* info) {
+  if (!c || !info) return invalid("rf_get_info: null argument");
+  info->K = c->K;
+  info->K_half = c->Kh;
+  info->Kx = c->Kx;
+  info->Ky = c->Ky;
+  info->Kz = c->Kz;
+  info->last_iters = c->last_iters;
+  info->last_residual = c->last_residual;
+  info->kernel_launches = c->launches;
+  info->j2_max_violation = c->last_viol;
+  info->lambda0 = c->lam0;
+  info->mu0 = c->mu0;
+  return RF_OK;
+}
+
+int rf_destroy(rf_ctx* c) {
+  if (!c) return RF_OK;
+  DeviceGuard dg(c->dev);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_pattern(c);
+  dfree(c->d_phase);
+  dfree(c->d_state);
+  dfree(c->d_twx);
+  dfree(c->d_twy);
+  dfree(c->d_twz);
+  dfree(c->d_status);
+  dfree(c->d_sbar);
+  dfree(c->d_eps);
+  dfree(c->d_sig);
+  dfree(c->d_alpha);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_sbar) cudaFreeHost(c->h_sbar);
+  delete c;
+  return RF_OK;
+}
+
+int rf_pattern_adapted(const rf_grid* grid, const uint8_t* phase_map, int32_t inclusion_phase,
+                       int64_t k_target, int32_t* freqs_out, int64_t cap, int64_t* K_out,
+                       void* stream) {
+  set_error("");
+  long long K = 0;
+  int e = rfk::pattern_adapted(grid, phase_map, inclusion_phase, k_target, freqs_out, cap, &K,
+                               static_cast<cudaStream_t>(stream));
+  if (K_out) *K_out = K;
+  return e;
+}
+
+int rf_pattern_radial(const rf_grid* grid, int64_t k_target, int32_t* freqs_out, int64_t cap,
+                      int64_t* K_out, void* stream) {
+  set_error("");
+  long long K = 0;
+  int e = rfk::pattern_radial(grid, k_target, freqs_out, cap, &K,
+                              static_cast<cudaStream_t>(stream));
+  if (K_out) *K_out = K;
+  return e;
+}
+
+}  // extern "C"

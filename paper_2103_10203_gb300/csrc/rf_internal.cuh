@@ -1,0 +1,202 @@
+// Internal declarations of the reduced-frequency solver library (sm_103a).
+//
+// Data layout in device memory (see the C ABI header for conventions):
+//   phase    uint8  [Nz][Ny][Nx]
+//   state    float  [NS][N]     J2 internal variables, NS = 4 in 2D (ep11, ep22, ep12, alpha;
+//                                ep33 = -(ep11 + ep22)), 7 in 3D (ep 11,22,33,23,13,12, alpha)
+//   ER       float2 [Kz][Ky][NC][Kx]  reduced strain coefficients on the kx >= 0 half of the
+//                                pattern, scattered into the dense (kz, ky, kx) rectangle of the
+//                                distinct values; entries outside the pattern stay zero
+//   T1, T1p  float2 [rows][NC][Kx]   per grid row (y, z): line transforms along x
+//   T2       float2 [Nz][Ky][NC][Kx] (3D) line transforms along y
+//   OUT      float2 [S][Kz][Ky][NC][Kx] split-K partial sums of the forward transform
+// NC = 3 (11, 22, 12) in 2D plane strain, 6 (11, 22, 33, 23, 13, 12) in 3D.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rf.h"
+
+namespace rfk {
+
+constexpr int kMaxPhases = 16;
+
+struct DevPhase {
+  float lam, mu, sy, H;
+  int plastic;
+  int pad[3];
+};
+
+struct LawParams {
+  DevPhase ph[kMaxPhases];
+  float lam0, mu0;
+  int has_plastic;
+  int pad;
+};
+
+// per frequency of the half pattern
+struct HIdx {
+  int j, iy, iz;
+  int kind;   // 0: regular, 1: zero frequency, 2: null operator
+};
+
+struct Status {
+  int done;       // set when converged, capped, or non-finite
+  int iters;      // fixed-point updates of this solve
+  int max_iter;
+  int nonfinite;
+  double tol;
+  double enorm;   // Frobenius norm of ebar (0: absolute measure)
+  double inv_n2;  // 1 / N^2 (Parseval)
+  double last_r;
+  double ebar[6];
+};
+
+struct DftAxisArgs {
+  const float2* in;
+  long long in_split_stride;
+  int in_splits;
+  long long in_bstride;
+  float2* out;
+  long long out_split_stride;
+  int out_splits;
+  long long out_bstride;
+  int M, N, K, batch;
+  const int* mvals;   // nullable: m itself; values reduced to [0, L)
+  const int* kvals;   // nullable: k itself
+  const float2* table;  // exp(+2 pi i t / L), t in [0, L)
+  int L;
+  int sign;           // +1 inverse, -1 forward
+  const int* done;    // nullable early-exit flag
+};
+
+struct RowArgs {
+  const float2* T;      // [rows][NC][Kx]
+  float2* Tout;         // [rows][NC][Kx]
+  const uint8_t* phase;
+  float* state;         // [NS][N] or null
+  const int* kx;        // [Kx]
+  const float* fac;     // [Kx] weight / N
+  const float2* table;  // exp(+2 pi i t / Nx)
+  int Nx, Kx, rows, R;
+  long long N;
+  LawParams law;
+  float* eps_out;       // final pass: [6][N] (nullable)
+  float* sig_out;       // final pass: [6][N] (nullable)
+  float* alpha_out;     // final pass: [N] (nullable)
+  double* sbar_part;    // final pass: [gridDim.x][6]
+  double* viol_part;    // final pass: [gridDim.x]
+  int commit;
+  const int* done;
+};
+
+struct GammaArgs {
+  const float2* OUT;
+  int splits;
+  long long split_stride;
+  float2* ER;
+  const HIdx* hidx;
+  const float4* hn;     // unit wave vector (x, y, z) and multiplicity in w
+  long long Kh;
+  int Kx, Ky, NC;
+  float inv2mu0, cgam;
+  const Status* st;
+  double* part;         // [gridDim.x]
+  const int* done;
+};
+
+}  // namespace rfk
+
+struct rf_ctx {
+  int dev = 0;
+  int dim = 2, nx = 1, ny = 1, nz = 1, nc = 3, ns = 0;
+  long long N = 0;
+  int rows = 0;
+  rf_options opt{};
+  cudaStream_t stream = nullptr;
+  int n_phases = 0;
+  rf_phase phases[rfk::kMaxPhases];
+  rfk::LawParams law{};
+  double lam0 = 0, mu0 = 0;
+  bool has_plastic = false;
+
+  uint8_t* d_phase = nullptr;
+  float* d_state = nullptr;
+
+  // pattern
+  bool have_pattern = false;
+  long long K = 0, Kh = 0;
+  int Kx = 0, Ky = 0, Kz = 0;
+  std::vector<int32_t> pat;       // [K][3] as given
+  std::vector<long long> map_h;   // per pattern entry: half index
+  std::vector<char> map_conj;     // per pattern entry: conjugate of the half entry
+  std::vector<long long> h_src;   // per half entry: a pattern entry equal to it
+  int* d_kx = nullptr;   // kx values (>= 0)
+  int* d_kym = nullptr;  // ky values mod Ny
+  int* d_kzm = nullptr;  // kz values mod Nz
+  float* d_fac = nullptr;
+  rfk::HIdx* d_hidx = nullptr;
+  float4* d_hn = nullptr;
+  float2* d_ER = nullptr;
+  float2* d_T1 = nullptr;
+  float2* d_T1p = nullptr;
+  float2* d_T2 = nullptr;
+  float2* d_T2f = nullptr;
+  float2* d_OUT = nullptr;
+  int splitB = 1, splitC = 1;
+  long long rect = 0;             // Kz*Ky*NC*Kx
+  float2* d_twx = nullptr;
+  float2* d_twy = nullptr;
+  float2* d_twz = nullptr;
+  double* d_part = nullptr;       // residual block partials
+  int n_part = 0;
+  double* d_sbar_part = nullptr;  // [row blocks][6]
+  double* d_viol_part = nullptr;
+  double* d_sbar = nullptr;       // [8]: sbar[6], viol, pad
+  rfk::Status* d_status = nullptr;
+  rfk::Status* h_status = nullptr;  // pinned
+  double* h_sbar = nullptr;         // pinned [8]
+  float* d_eps = nullptr;
+  float* d_sig = nullptr;
+  float* d_alpha = nullptr;
+  bool fields_valid = false;
+  int row_R = 1, row_blocks = 0;
+  size_t row_smem = 0;
+
+  long long zero_base_idx = 0;    // ER offset of the zero frequency, component 0
+  std::vector<rfk::HIdx> h_hidx;  // host copy of the half-pattern indices
+  float2* d_warm = nullptr;       // [Kh][6] warm-start staging
+
+  // load-path state
+  double prev_macro[6] = {0, 0, 0, 0, 0, 0};
+
+  // statistics
+  long long launches = 0;
+  int last_iters = 0;
+  double last_residual = 0;
+  double last_viol = 0;
+};
+
+namespace rfk {
+// kernels.cu
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+int launch_iteration(rf_ctx* c);
+int launch_inverse(rf_ctx* c);
+int launch_final(rf_ctx* c, int commit);
+int launch_setup_tables(rf_ctx* c);
+int launch_hinfo(rf_ctx* c, const int* d_hk, long long Kh);
+int launch_reset_er(rf_ctx* c, const double* ebar6, double scale_old);
+int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* ebar6);
+int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist);
+long long zero_base(const rf_ctx* c);
+// pattern.cu
+int pattern_adapted(const rf_grid* g, const uint8_t* pm, int incl, long long k_target,
+                    int32_t* out, long long cap, long long* K_out, cudaStream_t s);
+int pattern_radial(const rf_grid* g, long long k_target, int32_t* out, long long cap,
+                   long long* K_out, cudaStream_t s);
+}  // namespace rfk

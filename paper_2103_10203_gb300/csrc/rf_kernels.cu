@@ -1,0 +1,822 @@
+// Solver kernels of the reduced fixed-point scheme (Sec. 4, steps a-d), FP32 SIMT path.
+//
+// One iteration is a chain of kernels on the context's stream:
+//   [3D] inverse transform along z  (ER -> T2)            step d), part 1
+//   inverse transform along y       (ER or T2 -> T1)       step d), part 2
+//   row kernel: inverse transform along x, constitutive law, polarization stress,
+//               forward transform along x (T1 -> T1p)      steps d) part 3, a), b) part 1
+//   forward transform along y       (T1p -> OUT or T2f)    step b), part 2
+//   [3D] forward transform along z  (T2f -> OUT)           step b), part 3
+//   Green operator update + squared-increment partials     step c)
+//   finalize: convergence measure (FP64), device flag      criterion of Sec. 3
+// Every kernel returns at once when the device flag says the solve is done, so the host can
+// enqueue several iterations between checks without changing the result.
+#include <cmath>
+#include <cstdio>
+
+#include "rf_internal.cuh"
+
+namespace rfk {
+
+// ------------------------------------------------------------------------------------------
+// tables and per-frequency data
+__global__ void k_twiddle(float2* t, int L) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) {
+    double s, c;
+    sincospi(2.0 * (double)i / (double)L, &s, &c);
+    t[i] = make_float2((float)c, (float)s);
+  }
+}
+
+// hk: [Kh][4] = (kx, ky, kz, multiplicity). Writes unit wave vector and the frequency kind.
+__global__ void k_hinfo(const int* hk, long long Kh, int nx, int ny, int nz, int green,
+                        HIdx* hidx, float4* hn) {
+  long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (h >= Kh) return;
+  int k[3] = {hk[4 * h], hk[4 * h + 1], hk[4 * h + 2]};
+  int n[3] = {nx, ny, nz};
+  bool zero = (k[0] == 0 && k[1] == 0 && k[2] == 0);
+  int nyq = 0;
+  for (int j = 0; j < 3; ++j)
+    if (n[j] > 1 && (n[j] % 2) == 0 && k[j] == n[j] / 2) ++nyq;
+  double q[3];
+  bool null;
+  if (green == RF_GREEN_ROTATED) {
+    double s[3], c[3];
+    for (int j = 0; j < 3; ++j) sincospi((double)k[j] / (double)n[j], &s[j], &c[j]);
+    q[0] = 2.0 * s[0] * c[1] * c[2];
+    q[1] = 2.0 * s[1] * c[0] * c[2];
+    q[2] = 2.0 * s[2] * c[0] * c[1];
+    null = !zero && nyq >= 2;   // q = 0 exactly when two components sit at Nyquist
+  } else {
+    for (int j = 0; j < 3; ++j) q[j] = 2.0 * M_PI * (double)k[j] / (double)n[j];
+    null = !zero && nyq >= 1;
+  }
+  double nn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+  float4 out = make_float4(0.f, 0.f, 0.f, (float)hk[4 * h + 3]);
+  if (!zero && !null) {
+    out.x = (float)(q[0] / nn);
+    out.y = (float)(q[1] / nn);
+    out.z = (float)(q[2] / nn);
+  }
+  hn[h] = out;
+  hidx[h].kind = zero ? 1 : (null ? 2 : 0);
+}
+
+// ------------------------------------------------------------------------------------------
+// line transform along one axis as a batched complex product with generated twiddles:
+//   out[s][b][m][n] = sum_{k in split s} w(m, k) * (sum_t in[t][b][k][n]),
+//   w(m, k) = exp(sign * 2 pi i * (mv(m) * kv(k) mod L) / L).
+// Block: 64 n-columns x 32 m-rows, 256 threads, k staged through shared memory in tiles of 32.
+template <int MT>
+__global__ __launch_bounds__(256) void k_dft_axis(DftAxisArgs a) {
+  if (a.done && *a.done) return;
+  __shared__ float2 xs[32][64];
+  __shared__ float2 ws[4 * MT][33];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 64 + tx;
+  const int n0 = blockIdx.x * 64, m0 = blockIdx.y * (4 * MT);
+  const int b = blockIdx.z / a.out_splits, s = blockIdx.z % a.out_splits;
+  int kchunk = (a.K + a.out_splits - 1) / a.out_splits;
+  kchunk = (kchunk + 31) & ~31;
+  const int kbeg = s * kchunk;
+  const int kend = min(a.K, kbeg + kchunk);
+  float accr[MT], acci[MT];
+#pragma unroll
+  for (int i = 0; i < MT; ++i) accr[i] = acci[i] = 0.f;
+  const float2* inb = a.in + (long long)b * a.in_bstride;
+  for (int kb = kbeg; kb < kend; kb += 32) {
+    for (int i = tid; i < 32 * 64; i += 256) {
+      int kk = i >> 6, nn = i & 63;
+      int k = kb + kk, n = n0 + nn;
+      float2 v = make_float2(0.f, 0.f);
+      if (k < kend && n < a.N) {
+        const float2* p = inb + (long long)k * a.N + n;
+        for (int t = 0; t < a.in_splits; ++t) {
+          float2 u = p[t * a.in_split_stride];
+          v.x += u.x;
+          v.y += u.y;
+        }
+      }
+      xs[kk][nn] = v;
+    }
+    for (int i = tid; i < 4 * MT * 32; i += 256) {
+      int mm = i >> 5, kk = i & 31;
+      int m = m0 + mm, k = kb + kk;
+      float2 w = make_float2(0.f, 0.f);
+      if (m < a.M && k < kend) {
+        int mv = a.mvals ? a.mvals[m] : m;
+        int kv = a.kvals ? a.kvals[k] : k;
+        w = a.table[(int)(((long long)mv * kv) % a.L)];
+        if (a.sign < 0) w.y = -w.y;
+      }
+      ws[mm][kk] = w;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      float2 x = xs[kk][tx];
+#pragma unroll
+      for (int i = 0; i < MT; ++i) {
+        float2 w = ws[ty * MT + i][kk];
+        accr[i] = fmaf(w.x, x.x, fmaf(-w.y, x.y, accr[i]));
+        acci[i] = fmaf(w.x, x.y, fmaf(w.y, x.x, acci[i]));
+      }
+    }
+    __syncthreads();
+  }
+  const int n = n0 + tx;
+  if (n >= a.N) return;
+  float2* ob = a.out + (long long)s * a.out_split_stride + (long long)b * a.out_bstride;
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    int m = m0 + ty * MT + i;
+    if (m < a.M) ob[(long long)m * a.N + n] = make_float2(accr[i], acci[i]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// constitutive law (Sec. 2) on six-component tensors (11, 22, 33, 23, 13, 12)
+struct LawOut {
+  float s[6];
+  float ep[6];
+  float alpha;
+  bool yielded;
+};
+
+template <bool PLASTIC>
+__device__ __forceinline__ void stress6(const float* e, const DevPhase& p, const float* ep,
+                                        float alpha, LawOut& o) {
+  bool elastic = true;
+  if constexpr (PLASTIC) elastic = !p.plastic;
+  if (elastic) {
+    float tr = e[0] + e[1] + e[2];
+    float lt = p.lam * tr;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) o.s[i] = lt + 2.f * p.mu * e[i];
+#pragma unroll
+    for (int i = 3; i < 6; ++i) o.s[i] = 2.f * p.mu * e[i];
+    o.yielded = false;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o.ep[i] = ep[i];
+    o.alpha = alpha;
+    return;
+  }
+  // trial state with the internal variables of the last converged increment
+  float ee[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) ee[i] = e[i] - ep[i];
+  float tre = ee[0] + ee[1] + ee[2];
+  float m = tre * (1.f / 3.f);
+  float s[6] = {2.f * p.mu * (ee[0] - m), 2.f * p.mu * (ee[1] - m), 2.f * p.mu * (ee[2] - m),
+                2.f * p.mu * ee[3], 2.f * p.mu * ee[4], 2.f * p.mu * ee[5]};
+  float ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] +
+             2.f * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+  float seq = sqrtf(1.5f * ss);
+  float phi = seq - (p.sy + p.H * alpha);
+  float pm = (p.lam + (2.f / 3.f) * p.mu) * tre;
+  if (phi > 0.f) {
+    // radial return: dgamma = phi / (3 mu + H), flow direction 3/2 s / sigma_eq
+    float dg = phi / (3.f * p.mu + p.H);
+    float fl = 1.5f * dg / seq;
+    float f = 1.f - 3.f * p.mu * dg / seq;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      o.ep[i] = ep[i] + fl * s[i];
+      s[i] *= f;
+    }
+    o.alpha = alpha + dg;
+    o.yielded = true;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o.ep[i] = ep[i];
+    o.alpha = alpha;
+    o.yielded = false;
+  }
+  o.s[0] = s[0] + pm;
+  o.s[1] = s[1] + pm;
+  o.s[2] = s[2] + pm;
+  o.s[3] = s[3];
+  o.s[4] = s[4];
+  o.s[5] = s[5];
+}
+
+template <int NC>
+__device__ __forceinline__ void load_state(const float* st, long long N, long long g, float* ep,
+                                           float& alpha) {
+  if (NC == 3) {
+    ep[0] = st[g];
+    ep[1] = st[N + g];
+    ep[5] = st[2 * N + g];
+    ep[2] = -(ep[0] + ep[1]);
+    ep[3] = ep[4] = 0.f;
+    alpha = st[3 * N + g];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ep[i] = st[i * N + g];
+    alpha = st[6 * N + g];
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void store_state(float* st, long long N, long long g, const float* ep,
+                                            float alpha) {
+  if (NC == 3) {
+    st[g] = ep[0];
+    st[N + g] = ep[1];
+    st[2 * N + g] = ep[5];
+    st[3 * N + g] = alpha;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st[i * N + g] = ep[i];
+    st[6 * N + g] = alpha;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void comp_to6(const float* e, float* e6) {
+  if (NC == 3) {
+    e6[0] = e[0];
+    e6[1] = e[1];
+    e6[2] = 0.f;
+    e6[3] = 0.f;
+    e6[4] = 0.f;
+    e6[5] = e[2];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) e6[i] = e[i];
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ int comp6(int c) {
+  return NC == 3 ? (c == 2 ? 5 : c) : c;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  // deterministic: fixed shuffle tree inside warps, fixed order across warps
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t += red[i];
+  }
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+  }
+  __syncthreads();
+  return t;
+}
+
+// ------------------------------------------------------------------------------------------
+// Row kernel: R grid rows (lines along x) per block.
+//   phase 1 (per voxel): eps = (1/N) sum_j w_j Re(T_j exp(+2 pi i kx_j x / Nx)), law, tau
+//   phase 2 (per row, kx_j): T'_j = sum_x tau(x) exp(-2 pi i kx_j x / Nx)
+// FINAL: phase 1 only, with stress, fields, homogenised-stress partials and the J2 commit.
+template <int NC, bool PLASTIC, bool FINAL>
+__global__ __launch_bounds__(256) void k_row(RowArgs a) {
+  if (!FINAL && a.done && *a.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tab = reinterpret_cast<float2*>(smem);
+  float2* Ts = tab + a.Nx;
+  int* kxs = reinterpret_cast<int*>(Ts + a.R * NC * a.Kx);
+  float* fac = reinterpret_cast<float*>(kxs + a.Kx);
+  float* taus = fac + a.Kx;
+  __shared__ double red[8];
+
+  const int tid = threadIdx.x;
+  const int row0 = blockIdx.x * a.R;
+  const int nr = min(a.R, a.rows - row0);
+  for (int i = tid; i < a.Nx; i += blockDim.x) tab[i] = a.table[i];
+  for (int i = tid; i < a.Kx; i += blockDim.x) {
+    kxs[i] = a.kx[i];
+    fac[i] = a.fac[i];
+  }
+  const float2* Tg = a.T + (long long)row0 * NC * a.Kx;
+  for (int i = tid; i < nr * NC * a.Kx; i += blockDim.x) Ts[i] = Tg[i];
+  __syncthreads();
+
+  const bool pow2 = (a.Nx & (a.Nx - 1)) == 0;
+  const int mask = a.Nx - 1;
+  double sb[6] = {0, 0, 0, 0, 0, 0};
+  double vmax = 0.0;
+  const float lam0 = a.law.lam0, mu0 = a.law.mu0;
+  for (int v = tid; v < nr * a.Nx; v += blockDim.x) {
+    const int r = v / a.Nx;
+    const int x = v - r * a.Nx;
+    const long long g = (long long)(row0 + r) * a.Nx + x;
+    float e[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) e[c] = 0.f;
+    const float2* Tr = Ts + r * NC * a.Kx;
+    for (int j = 0; j < a.Kx; ++j) {
+      int m = kxs[j] * x;
+      m = pow2 ? (m & mask) : (m % a.Nx);
+      const float2 w = tab[m];
+      const float f = fac[j];
+      const float cr = f * w.x, ci = f * w.y;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float2 t = Tr[c * a.Kx + j];
+        e[c] = fmaf(t.x, cr, fmaf(-t.y, ci, e[c]));
+      }
+    }
+    float e6[6];
+    comp_to6<NC>(e, e6);
+    const DevPhase ph = a.law.ph[a.phase[g]];
+    float ep[6] = {0, 0, 0, 0, 0, 0};
+    float alpha = 0.f;
+    if (PLASTIC) load_state<NC>(a.state, a.N, g, ep, alpha);
+    LawOut o;
+    stress6<PLASTIC>(e6, ph, ep, alpha, o);
+    if (!FINAL) {
+      const float tr = e6[0] + e6[1] + e6[2];
+      float tau6[6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (lam0 * tr + 2.f * mu0 * e6[i]);
+#pragma unroll
+      for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * mu0 * e6[i];
+      float* tr_ = taus + r * NC * a.Nx;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) tr_[c * a.Nx + x] = tau6[comp6<NC>(c)];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
+      if (a.eps_out) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) a.eps_out[i * a.N + g] = e6[i];
+      }
+      if (a.sig_out) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) a.sig_out[i * a.N + g] = o.s[i];
+      }
+      if (PLASTIC) {
+        if (a.commit) store_state<NC>(a.state, a.N, g, o.ep, o.alpha);
+        if (a.alpha_out) a.alpha_out[g] = o.alpha;
+        if (o.yielded) {
+          // FP64 consistency check of the FP32 return map: sigma_eq(sigma) = sy + H alpha
+          double s0 = o.s[0], s1 = o.s[1], s2 = o.s[2];
+          double pmd = (s0 + s1 + s2) / 3.0;
+          double d0 = s0 - pmd, d1 = s1 - pmd, d2 = s2 - pmd;
+          double q = d0 * d0 + d1 * d1 + d2 * d2 +
+                     2.0 * ((double)o.s[3] * o.s[3] + (double)o.s[4] * o.s[4] +
+                            (double)o.s[5] * o.s[5]);
+          double seq = sqrt(1.5 * q);
+          double yl = (double)ph.sy + (double)ph.H * (double)o.alpha;
+          vmax = fmax(vmax, fabs(seq - yl) / (double)ph.sy);
+        }
+      } else if (a.alpha_out) {
+        a.alpha_out[g] = 0.f;
+      }
+    }
+  }
+  if (FINAL) {
+    for (int i = 0; i < 6; ++i) {
+      double t = block_sum_d(sb[i], red);
+      if (tid == 0) a.sbar_part[blockIdx.x * 6 + i] = t;
+    }
+    double vm = block_max_d(vmax, red);
+    if (tid == 0) a.viol_part[blockIdx.x] = vm;
+    return;
+  }
+  __syncthreads();
+  for (int u = tid; u < nr * a.Kx; u += blockDim.x) {
+    const int r = u / a.Kx;
+    const int j = u - r * a.Kx;
+    const int kxj = kxs[j];
+    const float* tr_ = taus + r * NC * a.Nx;
+    float ar[NC], ai[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ar[c] = ai[c] = 0.f;
+    int m = 0;
+    for (int x = 0; x < a.Nx; ++x) {
+      const float2 w = tab[m];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float t = tr_[c * a.Nx + x];
+        ar[c] = fmaf(t, w.x, ar[c]);
+        ai[c] = fmaf(-t, w.y, ai[c]);
+      }
+      m += kxj;
+      if (m >= a.Nx) m -= a.Nx;
+    }
+    float2* o = a.Tout + ((long long)(row0 + r) * NC) * a.Kx + j;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) o[c * a.Kx] = make_float2(ar[c], ai[c]);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Green operator of the isotropic reference medium applied to a symmetric tensor (Sec. 3):
+//   (Gamma : t)_ij = (n_i (t n)_j + n_j (t n)_i) / (2 mu0) - c n_i n_j (n . t . n),
+//   c = (lam0 + mu0) / (mu0 (lam0 + 2 mu0)), n = q / |q|.
+__device__ __forceinline__ void gamma6(const float4& n, const float* t, float inv2mu0, float cg,
+                                       float* o) {
+  // t: (11, 22, 33, 23, 13, 12)
+  const float v0 = t[0] * n.x + t[5] * n.y + t[4] * n.z;
+  const float v1 = t[5] * n.x + t[1] * n.y + t[3] * n.z;
+  const float v2 = t[4] * n.x + t[3] * n.y + t[2] * n.z;
+  const float nvn = n.x * v0 + n.y * v1 + n.z * v2;
+  o[0] = 2.f * n.x * v0 * inv2mu0 - cg * n.x * n.x * nvn;
+  o[1] = 2.f * n.y * v1 * inv2mu0 - cg * n.y * n.y * nvn;
+  o[2] = 2.f * n.z * v2 * inv2mu0 - cg * n.z * n.z * nvn;
+  o[3] = (n.y * v2 + n.z * v1) * inv2mu0 - cg * n.y * n.z * nvn;
+  o[4] = (n.x * v2 + n.z * v0) * inv2mu0 - cg * n.x * n.z * nvn;
+  o[5] = (n.x * v1 + n.y * v0) * inv2mu0 - cg * n.x * n.y * nvn;
+}
+
+template <int NC>
+__global__ __launch_bounds__(256) void k_gamma(GammaArgs a, double Nd) {
+  if (a.done && *a.done) return;
+  __shared__ double red[8];
+  const long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double diff = 0.0;
+  if (h < a.Kh) {
+    const HIdx hi = a.hidx[h];
+    const long long base = ((long long)(hi.iz * a.Ky + hi.iy) * NC) * a.Kx + hi.j;
+    float er[NC], ei[NC];
+    if (hi.kind == 1) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        er[c] = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
+        ei[c] = 0.f;
+      }
+    } else if (hi.kind == 2) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) er[c] = ei[c] = 0.f;
+    } else {
+      float tr[NC], ti[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float2 v = make_float2(0.f, 0.f);
+        const float2* p = a.OUT + base + c * a.Kx;
+        for (int s = 0; s < a.splits; ++s) {
+          float2 u = p[s * a.split_stride];
+          v.x += u.x;
+          v.y += u.y;
+        }
+        tr[c] = v.x;
+        ti[c] = v.y;
+      }
+      float t6[6], o6[6];
+      const float4 n = a.hn[h];
+      comp_to6<NC>(tr, t6);
+      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) er[c] = -o6[comp6<NC>(c)];
+      comp_to6<NC>(ti, t6);
+      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
+    }
+    const float mult = a.hn[h].w;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float2* p = a.ER + base + c * a.Kx;
+      const float2 old = *p;
+      const double dr = (double)er[c] - (double)old.x, di = (double)ei[c] - (double)old.y;
+      const double wc = (comp6<NC>(c) >= 3) ? 2.0 : 1.0;   // Frobenius: shear counted twice
+      diff += (double)mult * wc * (dr * dr + di * di);
+      *p = make_float2(er[c], ei[c]);
+    }
+  }
+  const double t = block_sum_d(diff, red);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = t;
+}
+
+// convergence measure r = sqrt(sum / N^2) / |ebar| (Parseval), decision on the device
+__global__ __launch_bounds__(256) void k_finalize(const double* part, int n, Status* st) {
+  if (st->done) return;
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double r = sqrt(sh[0] * st->inv_n2);
+    if (st->enorm > 0.0) r /= st->enorm;
+    st->iters += 1;
+    st->last_r = r;
+    if (!isfinite(r)) {
+      st->nonfinite = 1;
+      st->done = 1;
+    } else if (r < st->tol || st->iters >= st->max_iter) {
+      st->done = 1;
+    }
+  }
+}
+
+__global__ void k_reduce_sbar(const double* part, const double* vpart, int nb, double invN,
+                              double* out) {
+  __shared__ double sh[256];
+  for (int c = 0; c < 7; ++c) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256)
+      s = (c < 6) ? s + part[i * 6 + c] : fmax(s, vpart[i]);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+        sh[threadIdx.x] = (c < 6) ? sh[threadIdx.x] + sh[threadIdx.x + w]
+                                  : fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = (c < 6) ? sh[0] * invN : sh[0];
+    __syncthreads();
+  }
+}
+
+// zero frequency of ER: set (mode 0) or add (mode 1) N * value
+__global__ void k_zero_freq(float2* ER, long long base0, int NC, int Kx, double Nd, double v0,
+                            double v1, double v2, double v3, double v4, double v5, int mode) {
+  const double v6[6] = {v0, v1, v2, v3, v4, v5};
+  for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+    const int c6 = (NC == 3) ? (c == 2 ? 5 : c) : c;
+    float2* p = ER + base0 + (long long)c * Kx;
+    const float val = (float)(Nd * v6[c6]);
+    if (mode == 0) *p = make_float2(val, 0.f);
+    else p->x = (float)((double)p->x + Nd * v6[c6]);
+  }
+}
+
+// warm start: project given coefficients onto compatible strains, P(e) = Gamma0 : (C0 : e)
+template <int NC>
+__global__ void k_warm_project(const float2* w6, float2* ER, const HIdx* hidx, const float4* hn,
+                               long long Kh, int Kx, int Ky, float lam0, float mu0,
+                               float inv2mu0, float cg, double Nd, double e0, double e1,
+                               double e2, double e3, double e4, double e5) {
+  const long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (h >= Kh) return;
+  const HIdx hi = hidx[h];
+  const long long base = ((long long)(hi.iz * Ky + hi.iy) * NC) * Kx + hi.j;
+  const double eb[6] = {e0, e1, e2, e3, e4, e5};
+  float outr[6], outi[6];
+  if (hi.kind == 1) {
+    for (int i = 0; i < 6; ++i) {
+      outr[i] = (float)(Nd * eb[i]);
+      outi[i] = 0.f;
+    }
+  } else if (hi.kind == 2) {
+    for (int i = 0; i < 6; ++i) outr[i] = outi[i] = 0.f;
+  } else {
+    float er[6], ei[6];
+    for (int i = 0; i < 6; ++i) {
+      float2 v = w6[h * 6 + i];
+      er[i] = v.x;
+      ei[i] = v.y;
+    }
+    if (NC == 3) er[2] = er[3] = er[4] = ei[2] = ei[3] = ei[4] = 0.f;
+    float sr[6], si[6];
+    const float trr = er[0] + er[1] + er[2], tri = ei[0] + ei[1] + ei[2];
+    for (int i = 0; i < 6; ++i) {
+      sr[i] = 2.f * mu0 * er[i] + (i < 3 ? lam0 * trr : 0.f);
+      si[i] = 2.f * mu0 * ei[i] + (i < 3 ? lam0 * tri : 0.f);
+    }
+    const float4 n = hn[h];
+    gamma6(n, sr, inv2mu0, cg, outr);
+    gamma6(n, si, inv2mu0, cg, outi);
+  }
+  for (int c = 0; c < NC; ++c) {
+    const int c6 = (NC == 3) ? (c == 2 ? 5 : c) : c;
+    ER[base + (long long)c * Kx] = make_float2(outr[c6], outi[c6]);
+  }
+}
+
+__global__ void k_phase_hist(const uint8_t* pm, long long N, unsigned long long* hist) {
+  __shared__ unsigned int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
+       g += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&h[pm[g]], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers
+static int launch_check(rf_ctx* c, const char* what) {
+  c->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return RF_OK;
+}
+
+static int dft(rf_ctx* c, const float2* in, int in_splits, long long in_split_stride,
+               long long in_bstride, float2* out, int out_splits, long long out_split_stride,
+               long long out_bstride, int M, int N, int K, int batch, const int* mvals,
+               const int* kvals, const float2* tab, int L, int sign, const int* done) {
+  DftAxisArgs a;
+  a.in = in;
+  a.in_splits = in_splits;
+  a.in_split_stride = in_split_stride;
+  a.in_bstride = in_bstride;
+  a.out = out;
+  a.out_splits = out_splits;
+  a.out_split_stride = out_split_stride;
+  a.out_bstride = out_bstride;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.batch = batch;
+  a.mvals = mvals;
+  a.kvals = kvals;
+  a.table = tab;
+  a.L = L;
+  a.sign = sign;
+  a.done = done;
+  dim3 block(64, 4);
+  dim3 grid((N + 63) / 64, (M + 31) / 32, batch * out_splits);
+  k_dft_axis<8><<<grid, block, 0, c->stream>>>(a);
+  return launch_check(c, "dft_axis");
+}
+
+int launch_setup_tables(rf_ctx* c) {
+  k_twiddle<<<(c->nx + 255) / 256, 256, 0, c->stream>>>(c->d_twx, c->nx);
+  if (int e = launch_check(c, "twiddle x")) return e;
+  k_twiddle<<<(c->ny + 255) / 256, 256, 0, c->stream>>>(c->d_twy, c->ny);
+  if (int e = launch_check(c, "twiddle y")) return e;
+  k_twiddle<<<(c->nz + 255) / 256, 256, 0, c->stream>>>(c->d_twz, c->nz);
+  return launch_check(c, "twiddle z");
+}
+
+int launch_hinfo(rf_ctx* c, const int* d_hk, long long Kh) {
+  k_hinfo<<<(unsigned)((Kh + 255) / 256), 256, 0, c->stream>>>(d_hk, Kh, c->nx, c->ny, c->nz,
+                                                                c->opt.green, c->d_hidx, c->d_hn);
+  return launch_check(c, "hinfo");
+}
+
+int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist) {
+  k_phase_hist<<<304, 256, 0, c->stream>>>(c->d_phase, c->N, d_hist);
+  return launch_check(c, "phase_hist");
+}
+
+static RowArgs row_args(rf_ctx* c, const int* done) {
+  RowArgs a{};
+  a.T = c->d_T1;
+  a.Tout = c->d_T1p;
+  a.phase = c->d_phase;
+  a.state = c->d_state;
+  a.kx = c->d_kx;
+  a.fac = c->d_fac;
+  a.table = c->d_twx;
+  a.Nx = c->nx;
+  a.Kx = c->Kx;
+  a.rows = c->rows;
+  a.R = c->row_R;
+  a.N = c->N;
+  a.law = c->law;
+  a.done = done;
+  return a;
+}
+
+template <int NC, bool PL, bool FIN>
+static int row_launch(rf_ctx* c, const RowArgs& a) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_row<NC, PL, FIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr_set = true;
+  }
+  k_row<NC, PL, FIN><<<c->row_blocks, 256, c->row_smem, c->stream>>>(a);
+  return launch_check(c, "row");
+}
+
+static int row_dispatch(rf_ctx* c, const RowArgs& a, bool final_pass) {
+  const bool pl = c->has_plastic;
+  if (c->nc == 3) {
+    if (final_pass) return pl ? row_launch<3, true, true>(c, a) : row_launch<3, false, true>(c, a);
+    return pl ? row_launch<3, true, false>(c, a) : row_launch<3, false, false>(c, a);
+  }
+  if (final_pass) return pl ? row_launch<6, true, true>(c, a) : row_launch<6, false, true>(c, a);
+  return pl ? row_launch<6, true, false>(c, a) : row_launch<6, false, false>(c, a);
+}
+
+static int inverse_stages(rf_ctx* c, const int* done) {
+  const int NCK = c->nc * c->Kx;
+  if (c->dim == 3) {
+    // along z: T2[z][ky][c][kx] = sum_kz exp(+..kz z) ER[kz][ky][c][kx]
+    if (int e = dft(c, c->d_ER, 1, 0, 0, c->d_T2, 1, 0, 0, c->nz, c->Ky * NCK, c->Kz, 1, nullptr,
+                    c->d_kzm, c->d_twz, c->nz, +1, done))
+      return e;
+    // along y, batched over z
+    return dft(c, c->d_T2, 1, 0, (long long)c->Ky * NCK, c->d_T1, 1, 0, (long long)c->ny * NCK,
+               c->ny, NCK, c->Ky, c->nz, nullptr, c->d_kym, c->d_twy, c->ny, +1, done);
+  }
+  return dft(c, c->d_ER, 1, 0, 0, c->d_T1, 1, 0, 0, c->ny, NCK, c->Ky, 1, nullptr, c->d_kym,
+             c->d_twy, c->ny, +1, done);
+}
+
+int launch_iteration(rf_ctx* c) {
+  const int* done = &c->d_status->done;
+  if (int e = inverse_stages(c, done)) return e;
+  RowArgs ra = row_args(c, done);
+  if (int e = row_dispatch(c, ra, false)) return e;
+  const int NCK = c->nc * c->Kx;
+  const long long outstride = c->rect;
+  if (c->dim == 3) {
+    if (int e = dft(c, c->d_T1p, 1, 0, (long long)c->ny * NCK, c->d_T2f, 1, 0,
+                    (long long)c->Ky * NCK, c->Ky, NCK, c->ny, c->nz, c->d_kym, nullptr, c->d_twy,
+                    c->ny, -1, done))
+      return e;
+    if (int e = dft(c, c->d_T2f, 1, 0, 0, c->d_OUT, c->splitC, outstride, 0, c->Kz,
+                    c->Ky * NCK, c->nz, 1, c->d_kzm, nullptr, c->d_twz, c->nz, -1, done))
+      return e;
+  } else {
+    if (int e = dft(c, c->d_T1p, 1, 0, 0, c->d_OUT, c->splitB, outstride, 0, c->Ky, NCK, c->ny,
+                    1, c->d_kym, nullptr, c->d_twy, c->ny, -1, done))
+      return e;
+  }
+  GammaArgs g{};
+  g.OUT = c->d_OUT;
+  g.splits = (c->dim == 3) ? c->splitC : c->splitB;
+  g.split_stride = outstride;
+  g.ER = c->d_ER;
+  g.hidx = c->d_hidx;
+  g.hn = c->d_hn;
+  g.Kh = c->Kh;
+  g.Kx = c->Kx;
+  g.Ky = c->Ky;
+  g.NC = c->nc;
+  g.inv2mu0 = (float)(0.5 / c->mu0);
+  g.cgam = (float)((c->lam0 + c->mu0) / (c->mu0 * (c->lam0 + 2.0 * c->mu0)));
+  g.st = c->d_status;
+  g.part = c->d_part;
+  g.done = done;
+  const unsigned gb = (unsigned)((c->Kh + 255) / 256);
+  if (c->nc == 3) k_gamma<3><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
+  else k_gamma<6><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
+  if (int e = launch_check(c, "gamma")) return e;
+  k_finalize<<<1, 256, 0, c->stream>>>(c->d_part, (int)gb, c->d_status);
+  return launch_check(c, "finalize");
+}
+
+int launch_final(rf_ctx* c, int commit) {
+  if (int e = inverse_stages(c, nullptr)) return e;
+  RowArgs ra = row_args(c, nullptr);
+  ra.eps_out = c->d_eps;
+  ra.sig_out = c->d_sig;
+  ra.alpha_out = c->d_alpha;
+  ra.sbar_part = c->d_sbar_part;
+  ra.viol_part = c->d_viol_part;
+  ra.commit = commit;
+  if (int e = row_dispatch(c, ra, true)) return e;
+  k_reduce_sbar<<<1, 256, 0, c->stream>>>(c->d_sbar_part, c->d_viol_part, c->row_blocks,
+                                          1.0 / (double)c->N, c->d_sbar);
+  return launch_check(c, "reduce_sbar");
+}
+
+int launch_reset_er(rf_ctx* c, const double* ebar6, double mode_add) {
+  // mode_add == 0: ER = 0 except the zero frequency = N ebar; otherwise add N * ebar6 there
+  if (mode_add == 0.0) {
+    cudaError_t e = cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "memset ER");
+  }
+  // zero frequency sits at kx index 0 and the indices of ky = 0, kz = 0 (host-computed base)
+  k_zero_freq<<<1, 32, 0, c->stream>>>(c->d_ER, zero_base(c), c->nc, c->Kx, (double)c->N,
+                                      ebar6[0], ebar6[1], ebar6[2], ebar6[3], ebar6[4], ebar6[5],
+                                      mode_add == 0.0 ? 0 : 1);
+  return launch_check(c, "zero_freq");
+}
+
+int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* eb) {
+  const float inv2mu0 = (float)(0.5 / c->mu0);
+  const float cg = (float)((c->lam0 + c->mu0) / (c->mu0 * (c->lam0 + 2.0 * c->mu0)));
+  const unsigned gb = (unsigned)((c->Kh + 255) / 256);
+  if (c->nc == 3)
+    k_warm_project<3><<<gb, 256, 0, c->stream>>>(d_warm6, c->d_ER, c->d_hidx, c->d_hn, c->Kh,
+                                                 c->Kx, c->Ky, (float)c->lam0, (float)c->mu0,
+                                                 inv2mu0, cg, (double)c->N, eb[0], eb[1], eb[2],
+                                                 eb[3], eb[4], eb[5]);
+  else
+    k_warm_project<6><<<gb, 256, 0, c->stream>>>(d_warm6, c->d_ER, c->d_hidx, c->d_hn, c->Kh,
+                                                 c->Kx, c->Ky, (float)c->lam0, (float)c->mu0,
+                                                 inv2mu0, cg, (double)c->N, eb[0], eb[1], eb[2],
+                                                 eb[3], eb[4], eb[5]);
+  return launch_check(c, "warm_project");
+}
+
+int launch_inverse(rf_ctx* c) { return inverse_stages(c, nullptr); }
+
+}  // namespace rfk

@@ -1,0 +1,477 @@
+// Sampling patterns (reduced sets of frequencies), computed on the GPU.
+//
+// Adapted pattern (Sec. 4.2; 3D as in Sec. 5.3): the phase map becomes the step function g
+// (1 on the inclusion phase), g is transformed in FP64 axis by axis, and the amplitudes |g^|
+// rank the conjugate pairs (k, -k). Ranking key (smaller first): quantised amplitude
+// round(|g^| / |g^(0)| * 2^30) descending, |k|^2 ascending, signed linear index ascending.
+// Pairs are taken whole until at least k_target frequencies are held; the selection threshold
+// is found by binary search over the key with device-side counting.
+// Radial pattern (Sec. 4.1): L equiangular rasterised lines; the same selection machinery
+// ranks pairs by (not on a line, |k|^2, index).
+#include <climits>
+#include <cmath>
+#include <vector>
+
+#include "rf_internal.cuh"
+
+namespace rfk {
+
+namespace {
+
+struct Grid3 {
+  int nx, ny, nz;
+  long long N;
+  int hx, hy, hz;
+};
+
+__device__ __forceinline__ int sgn_index(int i, int n) { return i <= n / 2 ? i : i - n; }
+__device__ __forceinline__ int wrap(int k, int n) {
+  int r = k % n;
+  return r < 0 ? r + n : r;
+}
+__device__ __forceinline__ long long signed_lin(int kx, int ky, int kz, const Grid3& g) {
+  return ((long long)(kz + g.hz) * g.ny + (ky + g.hy)) * g.nx + (kx + g.hx);
+}
+
+__global__ void k_table_f64(double2* t, int L) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L) {
+    double s, c;
+    sincospi(2.0 * (double)i / (double)L, &s, &c);
+    t[i] = make_double2(c, -s);   // exp(-2 pi i t / L)
+  }
+}
+
+// out[row][kx] = sum_x g(row, x) exp(-2 pi i kx x / nx), one block per row
+__global__ void k_g_rows(const uint8_t* pm, int incl, int nx, const double2* tab, double2* out) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double2* t = reinterpret_cast<double2*>(sm);
+  float* gr = reinterpret_cast<float*>(t + nx);
+  const long long row = blockIdx.x;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    t[i] = tab[i];
+    gr[i] = pm[row * nx + i] == incl ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nx; k += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    int m = 0;
+    for (int x = 0; x < nx; ++x) {
+      if (gr[x] != 0.f) {
+        re += t[m].x;
+        im += t[m].y;
+      }
+      m += k;
+      if (m >= nx) m -= nx;
+    }
+    out[row * nx + k] = make_double2(re, im);
+  }
+}
+
+// out[b][m][n] = sum_k exp(-2 pi i m k / L) in[b][k][n]; 4 m per thread, lanes over n
+__global__ void k_axis_f64(const double2* in, double2* out, int L, int N, long long bstride,
+                           const double2* tab) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m0 = blockIdx.y * 4;
+  const long long b = blockIdx.z;
+  if (n >= N) return;
+  double ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+  const double2* ib = in + b * bstride;
+  for (int k = 0; k < L; ++k) {
+    const double2 v = ib[(long long)k * N + n];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int m = m0 + i;
+      if (m < L) {
+        const double2 w = tab[(int)(((long long)m * k) % L)];
+        ar[i] += w.x * v.x - w.y * v.y;
+        ai[i] += w.x * v.y + w.y * v.x;
+      }
+    }
+  }
+  double2* ob = out + b * bstride;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (m0 + i < L) ob[(long long)(m0 + i) * N + n] = make_double2(ar[i], ai[i]);
+}
+
+// keys at canonical pair members (array order [z][y][x]); others get ~0
+__global__ void k_keys(const double2* G, const uint8_t* mark, Grid3 g, unsigned long long* key,
+                       int* lin, int* size) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // |g^(0)| = number of inclusion voxels, exact in FP64 (a sum of ones)
+  const double amax = G ? G[0].x : 0.0;
+  if (i >= g.N) return;
+  const int ix = (int)(i % g.nx);
+  const int iy = (int)((i / g.nx) % g.ny);
+  const int iz = (int)(i / ((long long)g.nx * g.ny));
+  const int kx = sgn_index(ix, g.nx), ky = sgn_index(iy, g.ny), kz = sgn_index(iz, g.nz);
+  const int cx = sgn_index(wrap(-kx, g.nx), g.nx);
+  const int cy = sgn_index(wrap(-ky, g.ny), g.ny);
+  const int cz = sgn_index(wrap(-kz, g.nz), g.nz);
+  const long long l = signed_lin(kx, ky, kz, g);
+  const long long lc = signed_lin(cx, cy, cz, g);
+  lin[i] = (int)l;
+  if (l > lc) {
+    key[i] = ~0ull;
+    size[i] = 0;
+    return;
+  }
+  size[i] = (l == lc) ? 1 : 2;
+  const unsigned long long k2 =
+      (unsigned long long)((long long)kx * kx + (long long)ky * ky + (long long)kz * kz);
+  unsigned long long primary;
+  if (mark) {
+    primary = mark[i] ? 0ull : 1ull;
+  } else {
+    long long aq = 0;
+    if (amax > 0.0) {
+      const double a = hypot(G[i].x, G[i].y);
+      aq = llrint(a / amax * 1073741824.0);
+    }
+    long long p = 1073741824LL - aq;
+    primary = (unsigned long long)(p < 0 ? 0 : p);
+  }
+  key[i] = (primary << 33) | k2;
+}
+
+__global__ void k_count_le(const unsigned long long* key, const int* lin, const int* size,
+                           long long N, unsigned long long vhi, int vlin,
+                           unsigned long long* out) {
+  __shared__ unsigned long long sh[256];
+  unsigned long long s = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long k = key[i];
+    if (k != ~0ull && (k < vhi || (k == vhi && lin[i] <= vlin))) s += (unsigned long long)size[i];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sh[0]) atomicAdd(out, sh[0]);
+}
+
+// flags in signed-linear order
+__global__ void k_flags(const unsigned long long* key, const int* lin, Grid3 g,
+                        unsigned long long thi, int tlin, int* flags) {
+  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s >= g.N) return;
+  const int kx = (int)(s % g.nx) - g.hx;
+  const int ky = (int)((s / g.nx) % g.ny) - g.hy;
+  const int kz = (int)(s / ((long long)g.nx * g.ny)) - g.hz;
+  const long long ia = ((long long)wrap(kz, g.nz) * g.ny + wrap(ky, g.ny)) * g.nx + wrap(kx, g.nx);
+  const long long ic = ((long long)wrap(-kz, g.nz) * g.ny + wrap(-ky, g.ny)) * g.nx +
+                       wrap(-kx, g.nx);
+  const long long canon = (key[ia] != ~0ull) ? ia : ic;
+  const unsigned long long k = key[canon];
+  flags[s] = (k < thi || (k == thi && lin[canon] <= tlin)) ? 1 : 0;
+}
+
+// three-pass exclusive scan (block totals, scan of totals, write)
+__global__ void k_block_totals(const int* flags, long long N, int* tot) {
+  __shared__ int sh[1024];
+  const long long i = blockIdx.x * 1024LL + threadIdx.x;
+  sh[threadIdx.x] = (i < N) ? flags[i] : 0;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tot[blockIdx.x] = sh[0];
+}
+
+__global__ void k_scan_totals(int* tot, int nb) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int run = 0;
+    for (int b = 0; b < nb; ++b) {
+      int t = tot[b];
+      tot[b] = run;
+      run += t;
+    }
+    tot[nb] = run;
+  }
+}
+
+__global__ void k_compact(const int* flags, long long N, const int* tot, Grid3 g, int* out,
+                          long long cap) {
+  __shared__ int sh[1024];
+  const long long i = blockIdx.x * 1024LL + threadIdx.x;
+  const int f = (i < N) ? flags[i] : 0;
+  sh[threadIdx.x] = f;
+  __syncthreads();
+  // Hillis-Steele inclusive scan inside the block
+  for (int o = 1; o < 1024; o <<= 1) {
+    int v = (threadIdx.x >= o) ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  if (f) {
+    const long long pos = (long long)tot[blockIdx.x] + sh[threadIdx.x] - 1;
+    if (pos < cap) {
+      out[3 * pos + 0] = (int)(i % g.nx) - g.hx;
+      out[3 * pos + 1] = (int)((i / g.nx) % g.ny) - g.hy;
+      out[3 * pos + 2] = (int)(i / ((long long)g.nx * g.ny)) - g.hz;
+    }
+  }
+}
+
+__global__ void k_radial_mark(int L, int nx, int ny, uint8_t* mark) {
+  const int l = blockIdx.y;
+  const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+  const double th = M_PI * (double)l / (double)L;
+  const double c = cos(th), s = sin(th);
+  long long x, y;
+  if (fabs(c) >= fabs(s)) {
+    const int t = ti - nx / 2;
+    if (t > nx / 2) return;
+    const double v = (double)t * (s / c);
+    x = t;
+    y = (long long)copysign(floor(fabs(v) + 0.5), v);
+  } else {
+    const int t = ti - ny / 2;
+    if (t > ny / 2) return;
+    const double v = (double)t * (c / s);
+    y = t;
+    x = (long long)copysign(floor(fabs(v) + 0.5), v);
+  }
+  if (llabs(x) <= nx / 2 && llabs(y) <= ny / 2) {
+    const int ix = (int)(((x % nx) + nx) % nx), iy = (int)(((y % ny) + ny) % ny);
+    mark[(long long)iy * nx + ix] = 1;
+  }
+}
+
+__global__ void k_count_u8(const uint8_t* m, long long N, unsigned long long* out) {
+  __shared__ unsigned long long sh[256];
+  unsigned long long s = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    s += m[i] ? 1 : 0;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sh[0]) atomicAdd(out, sh[0]);
+}
+
+// RAII scratch
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(T) + 16) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+};
+
+int check(cudaError_t e, const char* what) { return e == cudaSuccess ? RF_OK : cuda_fail(e, what); }
+
+int validate_grid(const rf_grid* g, Grid3& out) {
+  if (!g || (g->dim != 2 && g->dim != 3)) {
+    set_error("grid: dim must be 2 or 3");
+    return RF_ERR_INVALID;
+  }
+  for (int j = 0; j < 3; ++j)
+    if (g->n[j] < 1 || g->n[j] > 4096) {
+      set_error("grid: sizes must be in [1, 4096]");
+      return RF_ERR_INVALID;
+    }
+  if (g->dim == 2 && g->n[2] != 1) {
+    set_error("grid: Nz must be 1 in 2D");
+    return RF_ERR_INVALID;
+  }
+  out.nx = g->n[0];
+  out.ny = g->n[1];
+  out.nz = g->n[2];
+  out.N = (long long)out.nx * out.ny * out.nz;
+  if (out.N >= (1LL << 31)) {
+    set_error("grid: too many voxels");
+    return RF_ERR_INVALID;
+  }
+  out.hx = (out.nx - 1) / 2;
+  out.hy = (out.ny - 1) / 2;
+  out.hz = (out.nz - 1) / 2;
+  return RF_OK;
+}
+
+// shared selection + compaction on keys already in `key/lin/size`
+int select_and_compact(const Grid3& g, unsigned long long* key, int* lin, int* size,
+                       long long k_target, int32_t* out_host, long long cap, long long* K_out,
+                       cudaStream_t s, Scratch& sc) {
+  unsigned long long* d_cnt = sc.get<unsigned long long>(1);
+  unsigned long long* h_cnt = nullptr;
+  if (!d_cnt) return RF_ERR_OOM;
+  if (int e = check(cudaMallocHost(&h_cnt, sizeof(unsigned long long)), "pinned")) return e;
+  struct PinFree {
+    void* p;
+    ~PinFree() { cudaFreeHost(p); }
+  } pf{h_cnt};
+  auto count = [&](unsigned long long vhi, int vlin, unsigned long long& res) -> int {
+    if (int e = check(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s), "memset")) return e;
+    k_count_le<<<304, 256, 0, s>>>(key, lin, size, g.N, vhi, vlin, d_cnt);
+    if (int e = check(cudaGetLastError(), "count_le")) return e;
+    if (int e = check(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, s), "copy count"))
+      return e;
+    if (int e = check(cudaStreamSynchronize(s), "sync count")) return e;
+    res = *h_cnt;
+    return RF_OK;
+  };
+  unsigned long long total = 0;
+  if (int e = count(~0ull - 1, INT_MAX, total)) return e;
+  if ((long long)total < k_target) {
+    set_error("pattern: k_target exceeds the number of frequencies");
+    return RF_ERR_INVALID;
+  }
+  // smallest key_hi with count >= k_target
+  unsigned long long lo = 0, hi = (1ull << 63);
+  while (lo < hi) {
+    unsigned long long mid = lo + (hi - lo) / 2;
+    unsigned long long c = 0;
+    if (int e = count(mid, INT_MAX, c)) return e;
+    if ((long long)c >= k_target) hi = mid;
+    else lo = mid + 1;
+  }
+  const unsigned long long thi = lo;
+  long long llo = 0, lhi = g.N;
+  while (llo < lhi) {
+    long long mid = llo + (lhi - llo) / 2;
+    unsigned long long c = 0;
+    if (int e = count(thi, (int)mid, c)) return e;
+    if ((long long)c >= k_target) lhi = mid;
+    else llo = mid + 1;
+  }
+  const int tlin = (int)llo;
+  unsigned long long K = 0;
+  if (int e = count(thi, tlin, K)) return e;
+  *K_out = (long long)K;
+  if ((long long)K > cap) {
+    set_error("pattern: output capacity too small");
+    return RF_ERR_INVALID;
+  }
+  int* flags = sc.get<int>(g.N);
+  const long long nb = (g.N + 1023) / 1024;
+  int* tot = sc.get<int>(nb + 1);
+  int* d_out = sc.get<int>(3 * (K > 0 ? K : 1));
+  if (!flags || !tot || !d_out) return RF_ERR_OOM;
+  const unsigned gb = (unsigned)((g.N + 255) / 256);
+  k_flags<<<gb, 256, 0, s>>>(key, lin, g, thi, tlin, flags);
+  k_block_totals<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot);
+  k_scan_totals<<<1, 32, 0, s>>>(tot, (int)nb);
+  k_compact<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot, g, d_out, (long long)K);
+  if (int e = check(cudaGetLastError(), "compact")) return e;
+  if (int e = check(cudaMemcpyAsync(out_host, d_out, sizeof(int) * 3 * K, cudaMemcpyDeviceToHost,
+                                    s), "copy pattern"))
+    return e;
+  return check(cudaStreamSynchronize(s), "sync pattern");
+}
+
+}  // namespace
+
+int pattern_adapted(const rf_grid* grid, const uint8_t* pm_host, int incl, long long k_target,
+                    int32_t* out, long long cap, long long* K_out, cudaStream_t s) {
+  Grid3 g;
+  if (int e = validate_grid(grid, g)) return e;
+  if (!pm_host || !out || !K_out || k_target < 1 || k_target > g.N) {
+    set_error("pattern_adapted: invalid arguments");
+    return RF_ERR_INVALID;
+  }
+  Scratch sc;
+  uint8_t* d_pm = sc.get<uint8_t>(g.N);
+  double2* A = sc.get<double2>(g.N);
+  double2* B = sc.get<double2>(g.N);
+  double2* tx = sc.get<double2>(g.nx);
+  double2* ty = sc.get<double2>(g.ny);
+  double2* tz = sc.get<double2>(g.nz);
+  unsigned long long* key = sc.get<unsigned long long>(g.N);
+  int* lin = sc.get<int>(g.N);
+  int* size = sc.get<int>(g.N);
+  if (!d_pm || !A || !B || !tx || !ty || !tz || !key || !lin || !size) {
+    set_error("pattern_adapted: out of device memory");
+    return RF_ERR_OOM;
+  }
+  if (int e = check(cudaMemcpyAsync(d_pm, pm_host, g.N, cudaMemcpyHostToDevice, s), "upload"))
+    return e;
+  k_table_f64<<<(g.nx + 255) / 256, 256, 0, s>>>(tx, g.nx);
+  k_table_f64<<<(g.ny + 255) / 256, 256, 0, s>>>(ty, g.ny);
+  k_table_f64<<<(g.nz + 255) / 256, 256, 0, s>>>(tz, g.nz);
+  const size_t smem = (size_t)g.nx * (sizeof(double2) + sizeof(float));
+  cudaFuncSetAttribute(k_g_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+  k_g_rows<<<(unsigned)(g.N / g.nx), 256, smem, s>>>(d_pm, incl, g.nx, tx, A);
+  if (int e = check(cudaGetLastError(), "g rows")) return e;
+  // along y: batch z, k = y, n = kx
+  {
+    dim3 grd((g.nx + 127) / 128, (g.ny + 3) / 4, g.nz);
+    k_axis_f64<<<grd, 128, 0, s>>>(A, B, g.ny, g.nx, (long long)g.ny * g.nx, ty);
+  }
+  double2* G = B;
+  if (g.nz > 1) {
+    const int Nn = g.ny * g.nx;
+    dim3 grd((Nn + 127) / 128, (g.nz + 3) / 4, 1);
+    k_axis_f64<<<grd, 128, 0, s>>>(B, A, g.nz, Nn, 0, tz);
+    G = A;
+  }
+  if (int e = check(cudaGetLastError(), "g axes")) return e;
+  k_keys<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(G, nullptr, g, key, lin, size);
+  if (int e = check(cudaGetLastError(), "keys")) return e;
+  return select_and_compact(g, key, lin, size, k_target, out, cap, K_out, s, sc);
+}
+
+int pattern_radial(const rf_grid* grid, long long k_target, int32_t* out, long long cap,
+                   long long* K_out, cudaStream_t s) {
+  Grid3 g;
+  if (int e = validate_grid(grid, g)) return e;
+  if (grid->dim != 2) {
+    set_error("pattern_radial: 2D only");
+    return RF_ERR_INVALID;
+  }
+  if (!out || !K_out || k_target < 1 || k_target > g.N) {
+    set_error("pattern_radial: invalid arguments");
+    return RF_ERR_INVALID;
+  }
+  Scratch sc;
+  uint8_t* mark = sc.get<uint8_t>(g.N);
+  unsigned long long* d_cnt = sc.get<unsigned long long>(1);
+  unsigned long long* key = sc.get<unsigned long long>(g.N);
+  int* lin = sc.get<int>(g.N);
+  int* size = sc.get<int>(g.N);
+  if (!mark || !d_cnt || !key || !lin || !size) {
+    set_error("pattern_radial: out of device memory");
+    return RF_ERR_OOM;
+  }
+  const int maxL = 4 * (g.nx > g.ny ? g.nx : g.ny);
+  const int tcount = (g.nx > g.ny ? g.nx : g.ny) + 1;
+  unsigned long long cnt = 0;
+  int L = 1;
+  for (; L <= maxL; ++L) {
+    if (int e = check(cudaMemsetAsync(mark, 0, g.N, s), "memset mark")) return e;
+    dim3 grd((tcount + 127) / 128, L);
+    k_radial_mark<<<grd, 128, 0, s>>>(L, g.nx, g.ny, mark);
+    if (int e = check(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s), "memset")) return e;
+    k_count_u8<<<304, 256, 0, s>>>(mark, g.N, d_cnt);
+    if (int e = check(cudaGetLastError(), "radial")) return e;
+    if (int e = check(cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, s), "cp"))
+      return e;
+    if (int e = check(cudaStreamSynchronize(s), "sync")) return e;
+    if ((long long)cnt >= k_target) break;
+  }
+  if ((long long)cnt < k_target) {
+    set_error("pattern_radial: k_target not reachable");
+    return RF_ERR_INVALID;
+  }
+  k_keys<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(nullptr, mark, g, key, lin, size);
+  if (int e = check(cudaGetLastError(), "keys")) return e;
+  return select_and_compact(g, key, lin, size, k_target, out, cap, K_out, s, sc);
+}
+
+}  // namespace rfk

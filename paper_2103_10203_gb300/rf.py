@@ -1,0 +1,244 @@
+"""Python binding of the C ABI in include/rf.h (argument marshalling only).
+
+Every computation happens in librf.so's CUDA kernels. Importing this module loads the
+library and raises if it is missing: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librf.so")
+
+RF_OK, RF_NOT_CONVERGED = 0, 1
+ERRORS = {-1: "invalid argument", -2: "CUDA error", -3: "non-finite", -4: "diverged",
+          -5: "out of memory", -6: "device timeout", -7: "state"}
+GREEN = {"rotated": 0, "continuous": 1}
+REF = {"minmax": 0, "volume": 1}
+PRECISION = {"fp32": 0, "split_bf16": 1}
+
+
+class rf_grid(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n", C.c_int32 * 3)]
+
+
+class rf_phase(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("mu", C.c_double), ("sigma_y0", C.c_double),
+                ("hardening", C.c_double), ("plastic", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rf_options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("green", C.c_int32),
+                ("ref_medium", C.c_int32), ("precision", C.c_int32), ("check_every", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
+
+
+class rf_info(C.Structure):
+    _fields_ = [("K", C.c_int64), ("K_half", C.c_int64), ("Kx", C.c_int32), ("Ky", C.c_int32),
+                ("Kz", C.c_int32), ("last_iters", C.c_int32), ("last_residual", C.c_double),
+                ("kernel_launches", C.c_int64), ("j2_max_violation", C.c_double),
+                ("lambda0", C.c_double), ("mu0", C.c_double)]
+
+
+class RFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rf error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    i32, i64, dbl = C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "rf_create": [C.POINTER(P), C.POINTER(rf_grid), i32, C.POINTER(rf_phase), P,
+                      C.POINTER(rf_options), P],
+        "rf_set_phase_map": [P, P],
+        "rf_set_phase_map_device": [P, P],
+        "rf_set_pattern": [P, P, i64],
+        "rf_solve": [P, P, P, P, P, P],
+        "rf_solve_path": [P, i32, P, P, P, P],
+        "rf_reset_path": [P],
+        "rf_get_fields": [P, P, P, P],
+        "rf_get_reduced_strain": [P, P],
+        "rf_get_state": [P, P, C.POINTER(C.c_size_t)],
+        "rf_set_state": [P, P, C.c_size_t],
+        "rf_get_info": [P, C.POINTER(rf_info)],
+        "rf_destroy": [P],
+        "rf_pattern_adapted": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64), P],
+        "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.rf_last_error.argtypes = []
+    lib.rf_last_error.restype = C.c_char_p
+    _ = (dbl,)
+    return lib
+
+
+lib = _load()
+
+# names declared in include/rf.h, for the export check
+EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_pattern",
+            "rf_solve", "rf_solve_path", "rf_reset_path", "rf_get_fields",
+            "rf_get_reduced_strain", "rf_get_state", "rf_set_state", "rf_get_info", "rf_destroy",
+            "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error"]
+
+
+def _check(code, allow_nc=True):
+    if code == RF_OK or (allow_nc and code == RF_NOT_CONVERGED):
+        return code
+    raise RFError(code, lib.rf_last_error().decode())
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def make_grid(shape) -> rf_grid:
+    """shape (Ny, Nx) or (Nz, Ny, Nx) -> rf_grid."""
+    g = rf_grid()
+    if len(shape) == 2:
+        g.dim, g.n[0], g.n[1], g.n[2] = 2, shape[1], shape[0], 1
+    else:
+        g.dim, g.n[0], g.n[1], g.n[2] = 3, shape[2], shape[1], shape[0]
+    return g
+
+
+def make_phases(table) -> C.Array:
+    arr = (rf_phase * len(table))()
+    for i, r in enumerate(table):
+        arr[i].lambda_ = float(r["lam"])
+        arr[i].mu = float(r["mu"])
+        arr[i].sigma_y0 = float(r["sigma_y0"])
+        arr[i].hardening = float(r["hardening"])
+        arr[i].plastic = int(r["plastic"])
+    return arr
+
+
+def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
+                 check_every=0) -> rf_options:
+    o = rf_options()
+    o.tol, o.max_iter = float(tol), int(max_iter)
+    o.green, o.ref_medium = GREEN[green], REF[ref]
+    o.precision, o.check_every = PRECISION[precision], int(check_every)
+    return o
+
+
+def rf_pattern_adapted(phase_map, inclusion_phase, k_target, stream=None):
+    pm = np.ascontiguousarray(phase_map, dtype=np.uint8)
+    g = make_grid(pm.shape)
+    cap = int(k_target) + 1
+    out = np.zeros((cap, 3), np.int32)
+    K = C.c_int64(0)
+    _check(lib.rf_pattern_adapted(C.byref(g), _ptr(pm), int(inclusion_phase), int(k_target),
+                                  _ptr(out), cap, C.byref(K), stream), allow_nc=False)
+    return out[:K.value].copy()
+
+
+def rf_pattern_radial(shape, k_target, stream=None):
+    g = make_grid(shape)
+    cap = int(k_target) + 1
+    out = np.zeros((cap, 3), np.int32)
+    K = C.c_int64(0)
+    _check(lib.rf_pattern_radial(C.byref(g), int(k_target), _ptr(out), cap, C.byref(K), stream),
+           allow_nc=False)
+    return out[:K.value].copy()
+
+
+class Solver:
+    """One solver context (rf_create ... rf_destroy)."""
+
+    def __init__(self, phase_map, phases, pattern=None, stream=None, **opts):
+        self.pm = np.ascontiguousarray(phase_map, dtype=np.uint8)
+        self.shape = self.pm.shape
+        self.N = self.pm.size
+        self._grid = make_grid(self.shape)
+        self._phases = make_phases(phases)
+        self._opts = make_options(**opts)
+        self.ctx = C.c_void_p()
+        _check(lib.rf_create(C.byref(self.ctx), C.byref(self._grid), len(phases), self._phases,
+                             _ptr(self.pm), C.byref(self._opts), stream), allow_nc=False)
+        self.K = 0
+        if pattern is not None:
+            self.rf_set_pattern(pattern)
+
+    def close(self):
+        if self.ctx:
+            lib.rf_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    __del__ = close
+
+    def rf_set_pattern(self, pattern):
+        p = np.ascontiguousarray(pattern, dtype=np.int32).reshape(-1, 3)
+        _check(lib.rf_set_pattern(self.ctx, _ptr(p), len(p)), allow_nc=False)
+        self.K = len(p)
+
+    def rf_set_phase_map(self, phase_map):
+        pm = np.ascontiguousarray(phase_map, dtype=np.uint8)
+        _check(lib.rf_set_phase_map(self.ctx, _ptr(pm)), allow_nc=False)
+
+    def rf_set_phase_map_device(self, dev_ptr: int):
+        _check(lib.rf_set_phase_map_device(self.ctx, C.c_void_p(dev_ptr)), allow_nc=False)
+
+    def rf_solve(self, macro, warm=None):
+        m = np.ascontiguousarray(macro, dtype=np.float64)
+        w = None if warm is None else np.ascontiguousarray(warm, dtype=np.float32)
+        sbar = np.zeros(6)
+        it = C.c_int32(0)
+        res = C.c_double(0)
+        code = _check(lib.rf_solve(self.ctx, _ptr(m), _ptr(w), _ptr(sbar), C.byref(it),
+                                   C.byref(res)))
+        return dict(sigma_bar=sbar, iters=it.value, residual=res.value,
+                    converged=code == RF_OK)
+
+    def rf_solve_path(self, path):
+        p = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 6)
+        n = len(p)
+        sbar = np.zeros((n, 6))
+        its = np.zeros(n, np.int32)
+        res = np.zeros(n)
+        code = _check(lib.rf_solve_path(self.ctx, n, _ptr(p), _ptr(sbar), _ptr(its), _ptr(res)))
+        return dict(sigma_bar=sbar, iters=its, residuals=res, converged=code == RF_OK)
+
+    def rf_reset_path(self):
+        _check(lib.rf_reset_path(self.ctx), allow_nc=False)
+
+    def rf_get_fields(self):
+        eps = np.zeros((6, self.N), np.float32)
+        sig = np.zeros((6, self.N), np.float32)
+        alpha = np.zeros(self.N, np.float32)
+        _check(lib.rf_get_fields(self.ctx, _ptr(eps), _ptr(sig), _ptr(alpha)), allow_nc=False)
+        sh = self.shape
+        return (eps.reshape((6,) + sh), sig.reshape((6,) + sh), alpha.reshape(sh))
+
+    def rf_get_reduced_strain(self):
+        out = np.zeros((self.K, 6, 2), np.float32)
+        _check(lib.rf_get_reduced_strain(self.ctx, _ptr(out)), allow_nc=False)
+        return out
+
+    def rf_get_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(lib.rf_get_state(self.ctx, None, C.byref(n)), allow_nc=False)
+        buf = np.zeros(n.value, np.uint8)
+        _check(lib.rf_get_state(self.ctx, _ptr(buf), C.byref(n)), allow_nc=False)
+        return buf.tobytes()
+
+    def rf_set_state(self, state: bytes):
+        buf = np.frombuffer(state, np.uint8).copy()
+        _check(lib.rf_set_state(self.ctx, _ptr(buf), len(buf)), allow_nc=False)
+
+    def rf_get_info(self) -> dict:
+        i = rf_info()
+        _check(lib.rf_get_info(self.ctx, C.byref(i)), allow_nc=False)
+        return {k: getattr(i, k) for k, _ in rf_info._fields_}

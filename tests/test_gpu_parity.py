@@ -1,0 +1,297 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances: relative L2 error of the strain field <= 1e-5 and relative error of the homogenised
+stress <= 1e-6 (FP32 path against FP64). Integer work (sampling patterns) is compared exactly.
+Solves are compared at equal iteration counts (the oracle replays as many updates as the GPU
+made), so that the comparison measures arithmetic, not a one-iteration difference in stopping.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.rf_oracle import VOIGT, _as_grid
+from synth import (centred_disc, laminate, make_config, phase_table, random_discs,
+                   random_macro_strain, random_spheres)
+from synth.configs import elastic_phases, j2_phases, k_target, uniaxial_path
+
+pytestmark = pytest.mark.gpu
+
+EPS_TOL = 1e-5
+SBAR_TOL = 1e-6
+
+
+def vec6_field(t):
+    """oracle [Nz,Ny,Nx,3,3] -> [6, *grid] with the grid shape of the phase map."""
+    g = t[0] if t.shape[0] == 1 else t
+    return np.stack([g[..., i, j] for (i, j) in VOIGT])
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_pattern_equal_or_valid(pm, got, want, incl=1):
+    if np.array_equal(got, want):
+        return
+    # several correct answers only where amplitudes tie within rounding: check validity
+    g = _as_grid(pm)
+    amp = np.abs(np.fft.fftn((g == incl).astype(float)))
+    a = lambda k: amp[k[2] % g.shape[0], k[1] % g.shape[1], k[0] % g.shape[2]]  # noqa: E731
+    sg = {tuple(k) for k in got}
+    sw = {tuple(k) for k in want}
+    diff = sg ^ sw
+    thr = min(a(k) for k in sw)
+    assert len(got) == len(want)
+    assert all(abs(a(k) - thr) <= 1e-9 * amp.max() for k in diff), "pattern differs"
+
+
+# ----------------------------------------------------------------------------- patterns
+@pytest.mark.parametrize("case", ["c1", "discs96", "ragged", "laminate", "3d", "3d_odd"])
+def test_adapted_pattern_matches_oracle(lib, case):
+    if case == "c1":
+        pm, K = centred_disc(64, 0.3), 205
+    elif case == "discs96":
+        pm, K = random_discs(96, (6.0, 14.0), 0.4, seed=5), 461
+    elif case == "ragged":
+        pm, K = (np.random.default_rng(2).random((40, 24)) < 0.35).astype(np.uint8), 97
+    elif case == "laminate":
+        pm, K = laminate((16, 32), (7, 25)), 20
+    elif case == "3d":
+        pm, K = random_spheres(16, (2.0, 4.0), 0.25, seed=3), 82
+    else:
+        pm, K = (np.random.default_rng(4).random((6, 10, 7)) < 0.3).astype(np.uint8), 42
+    want = O.pattern_adapted(pm, 1, K)
+    got = lib.rf_pattern_adapted(pm, 1, K)
+    assert_pattern_equal_or_valid(pm, got, want)
+
+
+@pytest.mark.parametrize("shape,K", [((64, 64), 205), ((48, 80), 300), ((33, 17), 60)])
+def test_radial_pattern_matches_oracle(lib, shape, K):
+    want = O.pattern_radial(shape, K)
+    got = lib.rf_pattern_radial(shape, K)
+    assert np.array_equal(got, want)
+
+
+def test_adapted_pattern_full_size_c2(lib):
+    cfg = make_config("c2")
+    pm = cfg["phase_map"]
+    for ratio in (0.01, 0.05):
+        K = k_target(ratio, pm.size)
+        assert_pattern_equal_or_valid(pm, lib.rf_pattern_adapted(pm, 1, K),
+                                      O.pattern_adapted(pm, 1, K))
+
+
+# ----------------------------------------------------------------------------- solves
+def _case(name):
+    rng = np.random.default_rng(11)
+    if name == "c1":
+        c = make_config("c1")
+        return c["phase_map"], c["phases"], c["macro"], O.pattern_adapted(c["phase_map"], 1, 205)
+    if name == "ragged2d":
+        pm = (rng.random((40, 24)) < 0.35).astype(np.uint8)
+        return pm, elastic_phases(), random_macro_strain(7, 2), O.pattern_adapted(pm, 1, 96)
+    if name == "odd2d":
+        pm = random_discs(21, (2.0, 4.0), 0.3, seed=9)[:, :15].copy()
+        return pm, elastic_phases(), random_macro_strain(8, 2), O.pattern_adapted(pm, 1, 64)
+    if name == "fullset":
+        pm = centred_disc(32, 0.3)
+        return pm, elastic_phases(), np.array([0.01, -0.01, 0, 0, 0, 0.004]), \
+            O.pattern_adapted(pm, 1, pm.size)
+    if name == "3d":
+        pm = random_spheres(16, (2.0, 4.0), 0.25, seed=3)
+        return pm, elastic_phases(), random_macro_strain(30, 3), O.pattern_adapted(pm, 1, 410)
+    if name == "3d_ragged":
+        pm = (rng.random((10, 12, 14)) < 0.3).astype(np.uint8)
+        return pm, elastic_phases(), random_macro_strain(31, 3), O.pattern_adapted(pm, 1, 170)
+    if name == "j2":
+        pm = random_discs(48, (4.0, 9.0), 0.4, seed=2)
+        return pm, j2_phases(), np.array([0.02, 0, 0, 0, 0, 0]), O.pattern_adapted(pm, 1, 116)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["c1", "ragged2d", "odd2d", "fullset", "3d", "3d_ragged", "j2"])
+@pytest.mark.parametrize("scheme,ref", [("rotated", "minmax"), ("continuous", "volume")])
+def test_fixed_iterations_match_oracle(lib, name, scheme, ref):
+    pm, ph, macro, pat = _case(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=6, green=scheme, ref=ref)
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    coeffs = s.rf_get_reduced_strain()
+    s.close()
+    assert out["iters"] == 6 and not out["converged"]
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=6, scheme=scheme, ref=ref)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    want = np.stack([r.eps_hat[:, i, j] for (i, j) in VOIGT], axis=1)
+    got = coeffs[..., 0] + 1j * coeffs[..., 1]
+    assert rel(got, want) <= EPS_TOL
+
+
+@pytest.mark.parametrize("name", ["c1", "3d", "j2"])
+def test_solve_to_tolerance_matches_oracle(lib, name):
+    pm, ph, macro, pat = _case(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=2000)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    assert out["converged"] and out["residual"] < 1e-6
+    ref_tol = O.solve(pm, ph, macro, pat, tol=1e-6, max_iter=2000)
+    assert abs(out["iters"] - ref_tol.iters) <= 1
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=out["iters"])
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    assert abs(out["residual"] - r.residual) <= 1e-3 * r.residual + 1e-8
+
+
+def test_j2_load_path_matches_oracle(lib):
+    pm = random_discs(48, (4.0, 9.0), 0.4, seed=2)
+    ph = j2_phases()
+    pat = O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    path = uniaxial_path(20, 0.02)[::4]            # 5 increments to 2 %
+    s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000)
+    out = s.rf_solve_path(path)
+    eps, sig, alpha = s.rf_get_fields()
+    info = s.rf_get_info()
+    s.close()
+    assert out["converged"]
+    sbar_ref, _, r = O.solve_path(pm, ph, path, pat, fixed_iters=out["iters"])
+    for n in range(len(path)):
+        assert rel(out["sigma_bar"][n], sbar_ref[n]) <= SBAR_TOL, n
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(alpha, r.alpha[0]) <= 1e-4            # accumulated plastic strain field
+    assert alpha.max() > 0 and info["j2_max_violation"] < 1e-4
+
+
+def test_warm_start_from_converged_coefficients(lib):
+    pm, ph, macro, pat = _case("c1")
+    r = O.solve(pm, ph, macro, pat, tol=1e-9, max_iter=3000)
+    warm = np.zeros((len(pat), 6, 2), np.float32)
+    for a, (i, j) in enumerate(VOIGT):
+        warm[:, a, 0] = r.eps_hat[:, i, j].real
+        warm[:, a, 1] = r.eps_hat[:, i, j].imag
+    s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=500)
+    cold = s.rf_solve(macro)
+    hot = s.rf_solve(macro, warm=warm)
+    s.close()
+    assert hot["converged"] and hot["iters"] <= 2 < cold["iters"]
+    assert rel(hot["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
+def test_checkpoint_resume_reproduces_uninterrupted_path(lib):
+    pm = random_discs(40, (4.0, 8.0), 0.4, seed=6)
+    ph = j2_phases()
+    pat = O.pattern_adapted(pm, 1, 80)
+    path = uniaxial_path(6, 0.02)
+    a = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000)
+    full = a.rf_solve_path(path)
+    a.close()
+    b = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000)
+    first = b.rf_solve_path(path[:3])
+    state = b.rf_get_state()
+    b.close()
+    c = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000)
+    c.rf_set_state(state)
+    second = c.rf_solve_path(path[3:])
+    c.close()
+    got = np.vstack([first["sigma_bar"], second["sigma_bar"]])
+    assert np.array_equal(got, full["sigma_bar"])
+    assert list(first["iters"]) + list(second["iters"]) == list(full["iters"])
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_zero_only_pattern_is_voigt(lib):
+    pm = centred_disc(16, 0.3)
+    ph = elastic_phases()
+    macro = np.array([0.01, 0.003, 0, 0, 0, -0.002])
+    s = lib.Solver(pm, ph, pattern=np.zeros((1, 3), np.int32), tol=1e-8)
+    out = s.rf_solve(macro)
+    s.close()
+    r = O.solve(pm, ph, macro, np.zeros((1, 3), np.int64), tol=1e-8)
+    assert out["iters"] == 1 and rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
+def test_homogeneous_medium_one_iteration(lib):
+    pm = np.zeros((12, 20), np.uint8)
+    ph = phase_table([(40.0, 27.0, 0, 0, 0)])
+    s = lib.Solver(pm, ph, pattern=O.pattern_adapted(pm, 1, 30), tol=1e-8)
+    out = s.rf_solve(np.array([0.01, -0.002, 0, 0, 0, 0.003]))
+    s.close()
+    assert out["iters"] == 1 and out["residual"] == 0.0
+
+
+def test_single_voxel_grid_and_widest_rows(lib):
+    pm = np.zeros((1, 1), np.uint8)
+    s = lib.Solver(pm, elastic_phases(), pattern=np.zeros((1, 3), np.int32), tol=1e-8)
+    out = s.rf_solve(np.array([0.01, 0, 0, 0, 0, 0]))
+    s.close()
+    assert out["iters"] == 1
+    pm = (np.random.default_rng(1).random((4, 4096)) < 0.3).astype(np.uint8)
+    pat = O.pattern_adapted(pm, 1, 410)
+    s = lib.Solver(pm, elastic_phases(), pattern=pat, tol=0.0, max_iter=3)
+    out = s.rf_solve(np.array([0.01, 0, 0, 0, 0, 0.002]))
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, elastic_phases(), np.array([0.01, 0, 0, 0, 0, 0.002]), pat, tol=0.0,
+                max_iter=3)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+
+
+def test_iteration_cap_reports_not_converged(lib):
+    pm, ph, macro, pat = _case("c1")
+    s = lib.Solver(pm, ph, pattern=pat, tol=1e-12, max_iter=3)
+    out = s.rf_solve(macro)
+    s.close()
+    assert not out["converged"] and out["iters"] == 3
+
+
+def test_api_errors_on_device(lib):
+    pm, ph, macro, pat = _case("c1")
+    s = lib.Solver(pm, ph)
+    with pytest.raises(lib.RFError) as e:
+        s.rf_solve(macro)
+    assert e.value.code == -7
+    with pytest.raises(lib.RFError):
+        s.rf_set_pattern(pat[1:])                      # not conjugate-closed / no zero
+    with pytest.raises(lib.RFError):
+        s.rf_set_pattern(np.vstack([pat, pat[:1]]))   # duplicate
+    with pytest.raises(lib.RFError):
+        s.rf_set_pattern(np.array([[0, 0, 0], [40, 0, 0], [-40, 0, 0]]))  # out of range
+    s.rf_set_pattern(pat)
+    with pytest.raises(lib.RFError):
+        s.rf_solve(np.array([0.01, 0, 0.001, 0, 0, 0]))  # 2D needs eps_33 = 0
+    bad = pm.copy()
+    bad[0, 0] = 5
+    with pytest.raises(lib.RFError):
+        s.rf_set_phase_map(bad)
+    s.close()
+
+
+# ----------------------------------------------------------------------------- full sizes
+def test_full_size_c2_first_iterations(lib):
+    cfg = make_config("c2")
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    macro = np.array([0.02, 0, 0, 0, 0, 0])
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=3)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
+def test_full_size_c3_first_iterations(lib):
+    cfg = make_config("c3")
+    pm, ph, macro = cfg["phase_map"], cfg["phases"], cfg["macro"]
+    pat = lib.rf_pattern_adapted(pm, 1, cfg["k_target"])
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=2)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=2)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
