@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Throughput of the reduced-frequency solver on the 2D elastoplastic composite workload.
+
+Workload (one step): a 1024 x 1024 periodic composite of random non-overlapping circular
+fibres (radius 8-24 voxels, volume fraction 0.4), J2 elastoplastic matrix (E 70 GPa, nu 0.3,
+yield 0.25 GPa, H 1 GPa) and elastic fibres (E 400 GPa, nu 0.2), loaded by 20 uniaxial-strain
+increments of eps_11 up to 2 %, each solved to a convergence measure below 1e-6 on the
+geometrically adapted reduced set with K = 5 % of the frequencies (52429).
+
+Legs:
+  value  device-resident: phase map, pattern and state live in HBM; a step is the whole load
+         path (rf_reset_path + rf_solve_path). L2 is flushed (256 MB write) before every step,
+         outside the timed events. Timed with CUDA events on the solver's stream.
+  e2e    the same metric through the C ABI with HOST buffers: pattern generation from the host
+         phase map, phase map and pattern upload, load path, homogenised stresses back.
+  cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the same workload.
+Multi-GPU: independent replicas (one RVE per rank, weak scaling); no data-path collective.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RVE voxel-iterations/s to 1e-6 residual (plain start)"
+UNIT = "voxel-iterations/s"
+RATIO = 0.05
+TOL = 1e-6
+MAX_ITER = 20000
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--cpu-iters", type=int, default=4, help="oracle updates in the CPU sample")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload():
+    from synth import make_config
+    from synth.configs import k_target
+    cfg = make_config("c2")
+    pm = cfg["phase_map"]
+    return cfg, pm, k_target(RATIO, pm.size)
+
+
+def config_block(pm, K):
+    return {"workload": "2D 1024x1024 J2 fibre composite (vf 0.4, r 8-24), 20 uniaxial-strain "
+                        "increments to 2%, adapted reduced set K=5%",
+            "grid": list(pm.shape[::-1]), "K": int(K), "increments": 20, "tol": TOL,
+            "l2": "flushed before every timed step (256 MB write)"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ----------------------------------------------------------------------------- roofline
+def stage_work(name, info, shape, nc=3, ns=4):
+    """Algorithmic FLOPs and bytes of one launch of a stage (2D workload)."""
+    ny, nx = shape
+    N = nx * ny
+    Kx, Ky = info["Kx"], info["Ky"]
+    if name == "row":
+        flops = 8.0 * nc * Kx * N                       # x transforms both ways, FMA = 2 FLOP
+        byts = N * (1 + 4 * ns) + 2 * ny * nc * Kx * 8
+    elif name in ("inverse_y", "forward_y"):
+        flops = 8.0 * ny * Ky * nc * Kx                 # complex MAC = 8 FLOP, dense rectangle
+        byts = (ny + Ky) * nc * Kx * 8
+    else:
+        flops, byts = 0.0, 0.0
+    return flops, byts
+
+
+def sources_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2103_10203_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed capture, if it matches the sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        if d.get("sources_sha") != sources_sha():
+            return None
+        return d["kernels"][kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_sample(pm, phases, pattern, iters):
+    """FP64 oracle on the host: `iters` updates of the first solve at eps_11 = 2 % (plastic
+    matrix, zero internal variables) on the full 1024^2 grid."""
+    import oracle
+    macro = np.array([0.02, 0, 0, 0, 0, 0])
+    t0c, t0 = time.process_time(), time.perf_counter()
+    oracle.solve(pm, phases, macro, pattern, tol=0.0, max_iter=iters)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - t0c
+    return {"value": iters * pm.size / wall, "unit": UNIT,
+            "cores": max(1, int(round(cpu / wall))), "kind": "oracle",
+            "sample": f"{iters} fixed-point updates of the 1024^2 J2 solve at eps_11=2% "
+                      f"(oracle, FP64, {wall:.1f} s wall)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    cfg, pm, K = workload()
+    pat = oracle.pattern_adapted(pm, 1, K)
+    its = max(1, args.cpu_iters // 2)
+    for _ in range(args.warmup):
+        cpu_sample(pm, cfg["phases"], pat, its)
+    vals, walls = [], []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        s = cpu_sample(pm, cfg["phases"], pat, its)
+        walls.append(time.perf_counter() - t)
+        vals.append(s)
+    v = float(np.mean([s["value"] for s in vals]))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(walls)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(pm, K), "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"] + " per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    ws, rank, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2103_10203_gb300 import rf
+
+    cfg, pm, K = workload()
+    phases, path = cfg["phases"], cfg["path"]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    pattern = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
+    solver = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER)
+    info = solver.rf_get_info()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        solver.rf_reset_path()
+        out = solver.rf_solve_path(path)
+        return int(np.sum(out["iters"])), out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    solver.rf_set_tracing(True)
+    solver.rf_reset_stage_times()
+    launches0 = solver.rf_get_info()["kernel_launches"]
+    iters, ms_steps, outs = 0, [], []
+    with ClockSampler(gpu_id_for(torch, local)) as clk:
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            n, out = step()
+            e1.record(stream)
+            e1.synchronize()
+            ms_steps.append(e0.elapsed_time(e1))
+            iters += n
+            outs.append(out)
+        torch.cuda.synchronize()
+    launches = solver.rf_get_info()["kernel_launches"] - launches0
+    solver.rf_set_tracing(False)
+    stage = solver.rf_get_stage_times()
+    total_ms = float(np.sum(ms_steps))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        v = torch.tensor([float(iters)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(v)
+        all_iters = float(v.item())
+    else:
+        all_iters = float(iters)
+    value = all_iters * pm.size / (total_ms / 1000.0)
+    solves = ws * args.steps / (total_ms / 1000.0)
+
+    # dominant stage and its roofline
+    real = {k: v for k, v in stage.items() if v[1] > 0}
+    dom = max(real, key=lambda k: real[k][0])
+    dom_ms = real[dom][0] / real[dom][1]
+    flops, byts = stage_work(dom, info, pm.shape)
+    clocks = clk.summary()
+    sm_max = clocks["sm_max_mhz"] or 2070.0
+    props = torch.cuda.get_device_properties(local)
+    if dom == "row" or dom.endswith("_y"):
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        kname = {"row": "k_row", "inverse_y": "k_dft_axis", "forward_y": "k_dft_axis"}[dom]
+        tr = ncu_traffic(kname)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": tr, "kernel": kname, "stage": dom,
+                "launch_ms": dom_ms, "algorithmic_flops_per_launch": flops,
+                "algorithmic_bytes_per_launch": byts,
+                "peak_source": "FP32 FMA: SMs x 128 lanes x 2 FLOP x max SM clock"}
+    else:
+        roof = {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
+                "traffic": None, "stage": dom}
+    stage_share = {k: round(v[0] / max(1e-9, sum(x[0] for x in real.values())), 4)
+                   for k, v in real.items()}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d = pm.nbytes * 2 + len(pattern) * 12 + path.nbytes
+        d2h = len(pattern) * 12 + path.shape[0] * (48 + 4 + 8)
+        e_iters, e_t = 0, 0.0
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pat = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
+            solver.rf_set_phase_map(pm)
+            solver.rf_set_pattern(pat)
+            out = solver.rf_solve_path(path)
+            _ = out["sigma_bar"].sum()
+            e_t += time.perf_counter() - t0
+            e_iters += int(np.sum(out["iters"]))
+        e2e = {"value": e_iters * pm.size / e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_sample(pm, phases, pattern, args.cpu_iters)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_block(pm, K), "solves_per_s": solves,
+                "iterations_per_step": iters / args.steps, "e2e": e2e,
+                "gpu_launches": int(launches), "roofline": roof, "stage_share": stage_share,
+                "cpu_baseline": cpu, "clocks": clocks,
+                "precision": "FP32 transforms and law; FP64 residual and homogenised stress",
+                "sigma_bar_final": [float(x) for x in outs[-1]["sigma_bar"][-1]]}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -170,6 +170,17 @@ int rf_set_state(rf_ctx* ctx, const void* buf, size_t bytes);
 
 int rf_get_info(const rf_ctx* ctx, rf_info* info);
 
+/* Per-stage device-time accounting. With tracing on, every stage launch of every fixed-point
+ * update is bracketed by CUDA events on the context's stream; the elapsed times of updates
+ * that did work (not the ones skipped after convergence) are accumulated per stage.
+ * Stages: 0 inverse transform along z, 1 inverse along y, 2 row kernel (transforms along x,
+ * constitutive law, polarization), 3 forward along y, 4 forward along z, 5 Green-operator
+ * update, 6 convergence check, 7 final pass (fields, homogenised stress, commit).
+ * rf_get_stage_times fills ms_total[8] (milliseconds) and counts[8] (launches timed). */
+int rf_set_tracing(rf_ctx* ctx, int on);
+int rf_get_stage_times(const rf_ctx* ctx, double ms_total[8], int64_t counts[8]);
+int rf_reset_stage_times(rf_ctx* ctx);
+
 /* Destroy a context and free its device memory. NULL is accepted. */
 int rf_destroy(rf_ctx* ctx);
 

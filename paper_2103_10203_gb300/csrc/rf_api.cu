@@ -152,6 +152,7 @@ int reset_path_state(rf_ctx* c) {
 }
 
 int init_status(rf_ctx* c, const double* macro) {
+  c->launched_iters = 0;
   Status& s = *c->h_status;
   s.done = 0;
   s.iters = 0;
@@ -176,6 +177,7 @@ int run_iterations(rf_ctx* c) {
                                    cudaMemcpyDeviceToHost, c->stream), "read status"))
       return e;
     if (int e = ck(cudaStreamSynchronize(c->stream), "iterate")) return e;
+    trace_collect(c, c->h_status->iters);
     if (c->h_status->done) break;
     chunk = std::min(chunk * 2, maxchunk);
   }
@@ -194,6 +196,7 @@ int finish(rf_ctx* c, int commit, double* sbar) {
                                  cudaMemcpyDeviceToHost, c->stream), "read sbar"))
     return e;
   if (int e = ck(cudaStreamSynchronize(c->stream), "final pass")) return e;
+  trace_collect(c, 0);
   c->fields_valid = true;
   if (commit) c->last_viol = c->h_sbar[6];
   for (int i = 0; i < 6; ++i) {
@@ -695,11 +698,38 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   return RF_OK;
 }
 
+int rf_set_tracing(rf_ctx* c, int on) {
+  if (!c) return invalid("rf_set_tracing: null context");
+  c->tracing = on != 0;
+  return RF_OK;
+}
+
+int rf_get_stage_times(const rf_ctx* c, double ms_total[8], int64_t counts[8]) {
+  if (!c || !ms_total || !counts) return invalid("rf_get_stage_times: null argument");
+  for (int i = 0; i < 8; ++i) {
+    ms_total[i] = c->stage_ms[i];
+    counts[i] = c->stage_n[i];
+  }
+  return RF_OK;
+}
+
+int rf_reset_stage_times(rf_ctx* c) {
+  if (!c) return invalid("rf_reset_stage_times: null context");
+  for (int i = 0; i < 8; ++i) {
+    c->stage_ms[i] = 0.0;
+    c->stage_n[i] = 0;
+  }
+  return RF_OK;
+}
+
 int rf_destroy(rf_ctx* c) {
   if (!c) return RF_OK;
   DeviceGuard dg(c->dev);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  trace_collect(c, 0);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
   free_pattern(c);
   dfree(c->d_phase);
   dfree(c->d_state);

@@ -174,6 +174,21 @@ struct rf_ctx {
   // load-path state
   double prev_macro[6] = {0, 0, 0, 0, 0, 0};
 
+  // tracing: one event before each stage of an update and one after the last stage
+  bool tracing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct TraceIter {
+    long long idx;                 // update index within the solve (-1: final pass)
+    int stage[8];
+    cudaEvent_t ev[9];
+    int n;
+  };
+  std::vector<TraceIter> pending;
+  TraceIter* cur = nullptr;
+  long long launched_iters = 0;
+  double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long stage_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
   // statistics
   long long launches = 0;
   int last_iters = 0;
@@ -194,6 +209,10 @@ int launch_reset_er(rf_ctx* c, const double* ebar6, double scale_old);
 int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* ebar6);
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist);
 long long zero_base(const rf_ctx* c);
+void trace_begin(rf_ctx* c, long long idx);
+void trace_stage(rf_ctx* c, int stage);
+void trace_end(rf_ctx* c);
+int trace_collect(rf_ctx* c, long long real_iters);
 // pattern.cu
 int pattern_adapted(const rf_grid* g, const uint8_t* pm, int incl, long long k_target,
                     int32_t* out, long long cap, long long* K_out, cudaStream_t s);

@@ -717,29 +717,36 @@ static int inverse_stages(rf_ctx* c, const int* done) {
   const int NCK = c->nc * c->Kx;
   if (c->dim == 3) {
     // along z: T2[z][ky][c][kx] = sum_kz exp(+..kz z) ER[kz][ky][c][kx]
+    trace_stage(c, 0);
     if (int e = dft(c, c->d_ER, 1, 0, 0, c->d_T2, 1, 0, 0, c->nz, c->Ky * NCK, c->Kz, 1, nullptr,
                     c->d_kzm, c->d_twz, c->nz, +1, done))
       return e;
     // along y, batched over z
+    trace_stage(c, 1);
     return dft(c, c->d_T2, 1, 0, (long long)c->Ky * NCK, c->d_T1, 1, 0, (long long)c->ny * NCK,
                c->ny, NCK, c->Ky, c->nz, nullptr, c->d_kym, c->d_twy, c->ny, +1, done);
   }
+  trace_stage(c, 1);
   return dft(c, c->d_ER, 1, 0, 0, c->d_T1, 1, 0, 0, c->ny, NCK, c->Ky, 1, nullptr, c->d_kym,
              c->d_twy, c->ny, +1, done);
 }
 
 int launch_iteration(rf_ctx* c) {
   const int* done = &c->d_status->done;
+  trace_begin(c, c->launched_iters++);
   if (int e = inverse_stages(c, done)) return e;
   RowArgs ra = row_args(c, done);
+  trace_stage(c, 2);
   if (int e = row_dispatch(c, ra, false)) return e;
   const int NCK = c->nc * c->Kx;
   const long long outstride = c->rect;
+  trace_stage(c, 3);
   if (c->dim == 3) {
     if (int e = dft(c, c->d_T1p, 1, 0, (long long)c->ny * NCK, c->d_T2f, 1, 0,
                     (long long)c->Ky * NCK, c->Ky, NCK, c->ny, c->nz, c->d_kym, nullptr, c->d_twy,
                     c->ny, -1, done))
       return e;
+    trace_stage(c, 4);
     if (int e = dft(c, c->d_T2f, 1, 0, 0, c->d_OUT, c->splitC, outstride, 0, c->Kz,
                     c->Ky * NCK, c->nz, 1, c->d_kzm, nullptr, c->d_twz, c->nz, -1, done))
       return e;
@@ -765,15 +772,25 @@ int launch_iteration(rf_ctx* c) {
   g.part = c->d_part;
   g.done = done;
   const unsigned gb = (unsigned)((c->Kh + 255) / 256);
+  trace_stage(c, 5);
   if (c->nc == 3) k_gamma<3><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
   else k_gamma<6><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
   if (int e = launch_check(c, "gamma")) return e;
+  trace_stage(c, 6);
   k_finalize<<<1, 256, 0, c->stream>>>(c->d_part, (int)gb, c->d_status);
-  return launch_check(c, "finalize");
+  int e = launch_check(c, "finalize");
+  trace_end(c);
+  return e;
 }
 
 int launch_final(rf_ctx* c, int commit) {
-  if (int e = inverse_stages(c, nullptr)) return e;
+  trace_begin(c, -1);
+  trace_stage(c, 7);
+  const bool tr = c->tracing;
+  c->tracing = false;   // the whole final pass is one stage
+  int ie = inverse_stages(c, nullptr);
+  c->tracing = tr;
+  if (ie) return ie;
   RowArgs ra = row_args(c, nullptr);
   ra.eps_out = c->d_eps;
   ra.sig_out = c->d_sig;
@@ -784,7 +801,9 @@ int launch_final(rf_ctx* c, int commit) {
   if (int e = row_dispatch(c, ra, true)) return e;
   k_reduce_sbar<<<1, 256, 0, c->stream>>>(c->d_sbar_part, c->d_viol_part, c->row_blocks,
                                           1.0 / (double)c->N, c->d_sbar);
-  return launch_check(c, "reduce_sbar");
+  int e = launch_check(c, "reduce_sbar");
+  trace_end(c);
+  return e;
 }
 
 int launch_reset_er(rf_ctx* c, const double* ebar6, double mode_add) {
@@ -818,5 +837,64 @@ int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* eb) {
 }
 
 int launch_inverse(rf_ctx* c) { return inverse_stages(c, nullptr); }
+
+// ------------------------------------------------------------------------------------------
+// tracing
+static cudaEvent_t take_event(rf_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void trace_begin(rf_ctx* c, long long idx) {
+  if (!c->tracing) return;
+  c->pending.push_back(rf_ctx::TraceIter{});
+  c->cur = &c->pending.back();
+  c->cur->idx = idx;
+  c->cur->n = 0;
+}
+
+void trace_stage(rf_ctx* c, int stage) {
+  if (!c->tracing || !c->cur || c->cur->n >= 8) return;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->stream);
+  c->cur->stage[c->cur->n] = stage;
+  c->cur->ev[c->cur->n] = e;
+  c->cur->n += 1;
+}
+
+void trace_end(rf_ctx* c) {
+  if (!c->tracing || !c->cur) return;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->stream);
+  c->cur->ev[c->cur->n] = e;
+  c->cur = nullptr;
+}
+
+int trace_collect(rf_ctx* c, long long real_iters) {
+  // call after a stream synchronize: accumulate updates with index < real_iters, and finals
+  for (auto& t : c->pending) {
+    const bool real = (t.idx < 0) || (t.idx < real_iters);
+    for (int i = 0; i < t.n; ++i) {
+      if (real) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.ev[i], t.ev[i + 1]) == cudaSuccess) {
+          c->stage_ms[t.stage[i]] += ms;
+          c->stage_n[t.stage[i]] += 1;
+        }
+      }
+      c->ev_pool.push_back(t.ev[i]);
+    }
+    if (t.n > 0) c->ev_pool.push_back(t.ev[t.n]);
+  }
+  c->pending.clear();
+  c->cur = nullptr;
+  return RF_OK;
+}
 
 }  // namespace rfk

@@ -74,6 +74,9 @@ def _load() -> C.CDLL:
         "rf_destroy": [P],
         "rf_pattern_adapted": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
+        "rf_set_tracing": [P, i32],
+        "rf_get_stage_times": [P, P, P],
+        "rf_reset_stage_times": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -91,7 +94,10 @@ lib = _load()
 EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_pattern",
             "rf_solve", "rf_solve_path", "rf_reset_path", "rf_get_fields",
             "rf_get_reduced_strain", "rf_get_state", "rf_set_state", "rf_get_info", "rf_destroy",
-            "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error"]
+            "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error", "rf_set_tracing",
+            "rf_get_stage_times", "rf_reset_stage_times"]
+
+STAGES = ["inverse_z", "inverse_y", "row", "forward_y", "forward_z", "green", "check", "final"]
 
 
 def _check(code, allow_nc=True):
@@ -237,6 +243,18 @@ class Solver:
     def rf_set_state(self, state: bytes):
         buf = np.frombuffer(state, np.uint8).copy()
         _check(lib.rf_set_state(self.ctx, _ptr(buf), len(buf)), allow_nc=False)
+
+    def rf_set_tracing(self, on=True):
+        _check(lib.rf_set_tracing(self.ctx, int(bool(on))), allow_nc=False)
+
+    def rf_reset_stage_times(self):
+        _check(lib.rf_reset_stage_times(self.ctx), allow_nc=False)
+
+    def rf_get_stage_times(self) -> dict:
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        _check(lib.rf_get_stage_times(self.ctx, _ptr(ms), _ptr(n)), allow_nc=False)
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(STAGES)}
 
     def rf_get_info(self) -> dict:
         i = rf_info()
