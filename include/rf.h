@@ -196,6 +196,25 @@ int rf_pattern_adapted(const rf_grid* grid, const uint8_t* phase_map, int32_t in
                        int64_t k_target, int32_t* freqs_out, int64_t cap, int64_t* K_out,
                        void* stream);
 
+/* Same result as rf_pattern_adapted, for grids of at most 65536 voxels, without allocating.
+ * No counterpart in the paper: this exists for callers that cannot allocate device memory.
+ * rf_pattern_adapted calls cudaMalloc/cudaFree for its scratch, and cudaFree synchronises the
+ * whole device; a caller that shares the GPU with streams it must not stall, or whose device
+ * memory belongs to another framework's pool allocator, cannot make those calls. This entry
+ * point uses a fixed scratch array (about 4.5 MB) that lives in the library's static device
+ * memory on every GPU that loads the library, until the process exits; it calls no
+ * cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.
+ *  - The first call on a device looks up that array's device address (once per device, with
+ *    the device current); make that first call before any stream capture begins.
+ *  - Grids with more than 65536 voxels are rejected with RF_ERR_INVALID and a message.
+ *  - All calls share the one array: calls whose GPU work overlaps (different streams or host
+ *    threads at the same time) race and corrupt each other's results. Serialise them.
+ *  - Arguments, output order and errors are those of rf_pattern_adapted; the call returns
+ *    when the result is in freqs_out. */
+int rf_pattern_adapted_noalloc(const rf_grid* grid, const uint8_t* phase_map,
+                               int32_t inclusion_phase, int64_t k_target, int32_t* freqs_out,
+                               int64_t cap, int64_t* K_out, void* stream);
+
 /* Fixed radial sampling pattern (Sec. 4.1), 2D only. The paper shows it only as a figure;
  * this library's reading: L equiangular lines through the origin at angles pi l / L, each
  * rasterised by unit steps along its dominant axis with the other coordinate rounded half away

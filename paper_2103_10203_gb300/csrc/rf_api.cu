@@ -758,6 +758,17 @@ int rf_pattern_adapted(const rf_grid* grid, const uint8_t* phase_map, int32_t in
   return e;
 }
 
+int rf_pattern_adapted_noalloc(const rf_grid* grid, const uint8_t* phase_map,
+                               int32_t inclusion_phase, int64_t k_target, int32_t* freqs_out,
+                               int64_t cap, int64_t* K_out, void* stream) {
+  set_error("");
+  long long K = 0;
+  int e = rfk::pattern_adapted_noalloc(grid, phase_map, inclusion_phase, k_target, freqs_out, cap,
+                                       &K, static_cast<cudaStream_t>(stream));
+  if (K_out) *K_out = K;
+  return e;
+}
+
 int rf_pattern_radial(const rf_grid* grid, int64_t k_target, int32_t* freqs_out, int64_t cap,
                       int64_t* K_out, void* stream) {
   set_error("");

@@ -218,4 +218,6 @@ int pattern_adapted(const rf_grid* g, const uint8_t* pm, int incl, long long k_t
                     int32_t* out, long long cap, long long* K_out, cudaStream_t s);
 int pattern_radial(const rf_grid* g, long long k_target, int32_t* out, long long cap,
                    long long* K_out, cudaStream_t s);
+int pattern_adapted_noalloc(const rf_grid* g, const uint8_t* pm, int incl, long long k_target,
+                            int32_t* out, long long cap, long long* K_out, cudaStream_t s);
 }  // namespace rfk

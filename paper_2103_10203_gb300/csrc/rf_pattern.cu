@@ -10,6 +10,7 @@
 // ranks pairs by (not on a line, |k|^2, index).
 #include <climits>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "rf_internal.cuh"
@@ -473,5 +474,176 @@ int pattern_radial(const rf_grid* grid, long long k_target, int32_t* out, long l
   if (int e = check(cudaGetLastError(), "keys")) return e;
   return select_and_compact(g, key, lin, size, k_target, out, cap, K_out, s, sc);
 }
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of the adapted pattern.
+//
+// rf_pattern_adapted allocates its device scratch with cudaMalloc and frees it with cudaFree,
+// and cudaFree synchronises the whole device. Callers that share the GPU with other streams
+// they must not stall, or whose device memory is owned by another framework's pool allocator,
+// cannot make those calls. rf_pattern_adapted_noalloc runs the same kernels with all scratch
+// carved from the file-scope array below instead, for grids of at most kNoAllocMaxVoxels.
+// Every GPU that loads this library holds the array until the process exits.
+namespace {
+
+constexpr long long kNoAllocMaxVoxels = 65536;     // e.g. 256 x 256 or 40 x 40 x 40
+constexpr int kNoAllocMaxSide = 4096;
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kNoAllocBytes =
+    align256(kNoAllocMaxVoxels)                                   // phase map
+    + 2 * align256(kNoAllocMaxVoxels * sizeof(double2))           // transform buffers
+    + 3 * align256(kNoAllocMaxSide * sizeof(double2))             // twiddle tables
+    + align256(kNoAllocMaxVoxels * sizeof(unsigned long long))    // keys
+    + 3 * align256(kNoAllocMaxVoxels * sizeof(int))               // lin, size, flags
+    + align256((kNoAllocMaxVoxels / 1024 + 2) * sizeof(int))      // scan totals
+    + align256(sizeof(unsigned long long))                        // counter
+    + align256(3 * kNoAllocMaxVoxels * sizeof(int));              // output frequencies
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device (looked up once per device).
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (int e = check(cudaGetDevice(&dev), "noalloc: cudaGetDevice")) return e;
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("rf_pattern_adapted_noalloc: device index out of range");
+    return RF_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (int e = check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "noalloc: scratch address"))
+      return e;
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return RF_OK;
+}
+
+}  // namespace
+
+int pattern_adapted_noalloc(const rf_grid* grid, const uint8_t* pm_host, int incl,
+                            long long k_target, int32_t* out_host, long long cap,
+                            long long* K_out, cudaStream_t s) {
+  Grid3 g;
+  if (int e = validate_grid(grid, g)) return e;
+  if (!pm_host || !out_host || !K_out || k_target < 1 || k_target > g.N) {
+    set_error("rf_pattern_adapted_noalloc: invalid arguments");
+    return RF_ERR_INVALID;
+  }
+  if (g.N > kNoAllocMaxVoxels) {
+    set_error("rf_pattern_adapted_noalloc: grid has more than 65536 voxels (the limit of its "
+              "static scratch); use rf_pattern_adapted");
+    return RF_ERR_INVALID;
+  }
+  unsigned char* base = nullptr;
+  if (int e = noalloc_scratch(&base)) return e;
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    unsigned char* p = base + off;
+    off += align256(bytes);
+    return p;
+  };
+  uint8_t* d_pm = carve(kNoAllocMaxVoxels);
+  double2* A = reinterpret_cast<double2*>(carve(kNoAllocMaxVoxels * sizeof(double2)));
+  double2* B = reinterpret_cast<double2*>(carve(kNoAllocMaxVoxels * sizeof(double2)));
+  double2* tx = reinterpret_cast<double2*>(carve(kNoAllocMaxSide * sizeof(double2)));
+  double2* ty = reinterpret_cast<double2*>(carve(kNoAllocMaxSide * sizeof(double2)));
+  double2* tz = reinterpret_cast<double2*>(carve(kNoAllocMaxSide * sizeof(double2)));
+  auto* key = reinterpret_cast<unsigned long long*>(
+      carve(kNoAllocMaxVoxels * sizeof(unsigned long long)));
+  int* lin = reinterpret_cast<int*>(carve(kNoAllocMaxVoxels * sizeof(int)));
+  int* size = reinterpret_cast<int*>(carve(kNoAllocMaxVoxels * sizeof(int)));
+  int* flags = reinterpret_cast<int*>(carve(kNoAllocMaxVoxels * sizeof(int)));
+  int* tot = reinterpret_cast<int*>(carve((kNoAllocMaxVoxels / 1024 + 2) * sizeof(int)));
+  auto* d_cnt = reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long)));
+  int* d_out = reinterpret_cast<int*>(carve(3 * kNoAllocMaxVoxels * sizeof(int)));
+
+  // same kernels as rf_pattern_adapted
+  if (int e = check(cudaMemcpyAsync(d_pm, pm_host, g.N, cudaMemcpyHostToDevice, s), "upload"))
+    return e;
+  k_table_f64<<<(g.nx + 255) / 256, 256, 0, s>>>(tx, g.nx);
+  k_table_f64<<<(g.ny + 255) / 256, 256, 0, s>>>(ty, g.ny);
+  k_table_f64<<<(g.nz + 255) / 256, 256, 0, s>>>(tz, g.nz);
+  const size_t smem = (size_t)g.nx * (sizeof(double2) + sizeof(float));
+  if (int e = check(cudaFuncSetAttribute(k_g_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         100 * 1024), "noalloc: smem attribute"))
+    return e;
+  k_g_rows<<<(unsigned)(g.N / g.nx), 256, smem, s>>>(d_pm, incl, g.nx, tx, A);
+  {
+    dim3 grd((g.nx + 127) / 128, (g.ny + 3) / 4, g.nz);
+    k_axis_f64<<<grd, 128, 0, s>>>(A, B, g.ny, g.nx, (long long)g.ny * g.nx, ty);
+  }
+  double2* G = B;
+  if (g.nz > 1) {
+    const int Nn = g.ny * g.nx;
+    dim3 grd((Nn + 127) / 128, (g.nz + 3) / 4, 1);
+    k_axis_f64<<<grd, 128, 0, s>>>(B, A, g.nz, Nn, 0, tz);
+    G = A;
+  }
+  k_keys<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(G, nullptr, g, key, lin, size);
+  if (int e = check(cudaGetLastError(), "noalloc: keys")) return e;
+
+  // selection: the counter is the only scratch that must start at zero; it is cleared
+  // before every count
+  unsigned long long h_cnt = 0;
+  auto count = [&](unsigned long long vhi, int vlin, unsigned long long& res) -> int {
+    if (int e = check(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s), "memset"))
+      return e;
+    k_count_le<<<304, 256, 0, s>>>(key, lin, size, g.N, vhi, vlin, d_cnt);
+    if (int e = check(cudaGetLastError(), "count_le")) return e;
+    if (int e = check(cudaMemcpyAsync(&h_cnt, d_cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s),
+                      "copy count"))
+      return e;
+    if (int e = check(cudaStreamSynchronize(s), "sync count")) return e;
+    res = h_cnt;
+    return RF_OK;
+  };
+  unsigned long long total = 0;
+  if (int e = count(~0ull - 1, INT_MAX, total)) return e;
+  if ((long long)total < k_target) {
+    set_error("pattern: k_target exceeds the number of frequencies");
+    return RF_ERR_INVALID;
+  }
+  unsigned long long lo = 0, hi = (1ull << 63);
+  while (lo < hi) {
+    unsigned long long mid = lo + (hi - lo) / 2, c = 0;
+    if (int e = count(mid, INT_MAX, c)) return e;
+    if ((long long)c >= k_target) hi = mid;
+    else lo = mid + 1;
+  }
+  const unsigned long long thi = lo;
+  long long llo = 0, lhi = g.N;
+  while (llo < lhi) {
+    long long mid = llo + (lhi - llo) / 2;
+    unsigned long long c = 0;
+    if (int e = count(thi, (int)mid, c)) return e;
+    if ((long long)c >= k_target) lhi = mid;
+    else llo = mid + 1;
+  }
+  const int tlin = (int)llo;
+  unsigned long long K = 0;
+  if (int e = count(thi, tlin, K)) return e;
+  *K_out = (long long)K;
+  if ((long long)K > cap) {
+    set_error("pattern: output capacity too small");
+    return RF_ERR_INVALID;
+  }
+  const long long nb = (g.N + 1023) / 1024;
+  k_flags<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(key, lin, g, thi, tlin, flags);
+  k_block_totals<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot);
+  k_scan_totals<<<1, 32, 0, s>>>(tot, (int)nb);
+  k_compact<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot, g, d_out, (long long)K);
+  if (int e = check(cudaGetLastError(), "noalloc: compact")) return e;
+  if (int e = check(cudaMemcpyAsync(out_host, d_out, sizeof(int) * 3 * K,
+                                    cudaMemcpyDeviceToHost, s), "copy pattern"))
+    return e;
+  return check(cudaStreamSynchronize(s), "sync pattern");
+}
+
 
 }  // namespace rfk

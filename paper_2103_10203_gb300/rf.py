@@ -74,6 +74,8 @@ def _load() -> C.CDLL:
         "rf_destroy": [P],
         "rf_pattern_adapted": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
+        "rf_pattern_adapted_noalloc": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64),
+                                       P],
         "rf_set_tracing": [P, i32],
         "rf_get_stage_times": [P, P, P],
         "rf_reset_stage_times": [P],
@@ -95,7 +97,7 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_solve", "rf_solve_path", "rf_reset_path", "rf_get_fields",
             "rf_get_reduced_strain", "rf_get_state", "rf_set_state", "rf_get_info", "rf_destroy",
             "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error", "rf_set_tracing",
-            "rf_get_stage_times", "rf_reset_stage_times"]
+            "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc"]
 
 STAGES = ["inverse_z", "inverse_y", "row", "forward_y", "forward_z", "green", "check", "final"]
 
@@ -148,6 +150,19 @@ def rf_pattern_adapted(phase_map, inclusion_phase, k_target, stream=None):
     K = C.c_int64(0)
     _check(lib.rf_pattern_adapted(C.byref(g), _ptr(pm), int(inclusion_phase), int(k_target),
                                   _ptr(out), cap, C.byref(K), stream), allow_nc=False)
+    return out[:K.value].copy()
+
+
+def rf_pattern_adapted_noalloc(phase_map, inclusion_phase, k_target, stream=None):
+    """Allocation-free variant (grids of at most 65536 voxels); see include/rf.h."""
+    pm = np.ascontiguousarray(phase_map, dtype=np.uint8)
+    g = make_grid(pm.shape)
+    cap = int(k_target) + 1
+    out = np.zeros((cap, 3), np.int32)
+    K = C.c_int64(0)
+    _check(lib.rf_pattern_adapted_noalloc(C.byref(g), _ptr(pm), int(inclusion_phase),
+                                          int(k_target), _ptr(out), cap, C.byref(K), stream),
+           allow_nc=False)
     return out[:K.value].copy()
 
 
