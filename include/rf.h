@@ -56,7 +56,7 @@ enum {
 
 enum { RF_GREEN_ROTATED = 0, RF_GREEN_CONTINUOUS = 1 };
 enum { RF_REF_MINMAX = 0, RF_REF_VOLUME = 1 };
-enum { RF_PREC_FP32 = 0, RF_PREC_SPLIT_BF16 = 1 };
+enum { RF_PREC_FP32 = 0, RF_PREC_SPLIT_BF16 = 1, RF_PREC_SPLIT_TF32 = 2 };
 
 typedef struct rf_ctx rf_ctx;
 
@@ -88,9 +88,11 @@ typedef struct rf_phase {
  *             zero operator).
  *  ref_medium RF_REF_MINMAX: lambda0 = (min + max)/2 and mu0 likewise over the phases present
  *             (the basic scheme of Sec. 3); RF_REF_VOLUME: volume averages.
- *  precision  RF_PREC_FP32 (SIMT FP32 transforms) or RF_PREC_SPLIT_BF16 (tensor-core
- *             transforms with hi/lo BF16 operands and FP32 accumulation). The residual and
- *             the homogenised stress are accumulated in FP64 in both modes.
+ *  precision  RF_PREC_FP32: FP32 SIMT transforms. RF_PREC_SPLIT_BF16 / RF_PREC_SPLIT_TF32:
+ *             the transforms along x run on the tensor cores (tcgen05) with operands split into
+ *             hi + lo parts of BF16 or TF32, three products (hi*hi + hi*lo + lo*hi) and FP32
+ *             accumulation; the law stays FP32. The residual and the homogenised stress are
+ *             accumulated in FP64 in every mode. Split modes need 2 Kx <= 1152.
  *  check_every  iterations launched between host checks of the device convergence flag
  *             (0 = library default). Work after convergence is skipped on the device, so
  *             results do not depend on it. */

@@ -134,6 +134,10 @@ void free_pattern(rf_ctx* c) {
   dfree(c->d_sbar_part);
   dfree(c->d_viol_part);
   dfree(c->d_warm);
+  dfree(c->d_phiI);
+  dfree(c->d_phiF);
+  dfree(c->d_Tout);
+  dfree(c->d_tc_err);
   c->have_pattern = false;
   c->fields_valid = false;
 }
@@ -158,6 +162,8 @@ int init_status(rf_ctx* c, const double* macro) {
   s.iters = 0;
   s.max_iter = c->opt.max_iter;
   s.nonfinite = 0;
+  s.timeout = 0;
+  s.pad = 0;
   s.tol = c->opt.tol;
   s.enorm = frob6(macro);
   s.inv_n2 = 1.0 / ((double)c->N * (double)c->N);
@@ -178,11 +184,15 @@ int run_iterations(rf_ctx* c) {
       return e;
     if (int e = ck(cudaStreamSynchronize(c->stream), "iterate")) return e;
     trace_collect(c, c->h_status->iters);
-    if (c->h_status->done) break;
+    if (c->h_status->done || c->h_status->timeout) break;
     chunk = std::min(chunk * 2, maxchunk);
   }
   c->last_iters = c->h_status->iters;
   c->last_residual = c->h_status->last_r;
+  if (c->h_status->timeout) {
+    set_error("a bounded device-side wait ran out in the tensor-core transform");
+    return RF_ERR_TIMEOUT;
+  }
   if (c->h_status->nonfinite) {
     set_error("convergence measure is not finite");
     return RF_ERR_NONFINITE;
@@ -248,7 +258,8 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
     return invalid("options: unknown green operator");
   if (opt->ref_medium != RF_REF_MINMAX && opt->ref_medium != RF_REF_VOLUME)
     return invalid("options: unknown reference medium rule");
-  if (opt->precision != RF_PREC_FP32 && opt->precision != RF_PREC_SPLIT_BF16)
+  if (opt->precision != RF_PREC_FP32 && opt->precision != RF_PREC_SPLIT_BF16 &&
+      opt->precision != RF_PREC_SPLIT_TF32)
     return invalid("options: unknown precision");
 
   rf_ctx* c = new rf_ctx();
@@ -471,6 +482,7 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err) err = ck(cudaMemcpyAsync(c->d_hidx, c->h_hidx.data(), sizeof(HIdx) * c->Kh, cudaMemcpyHostToDevice, c->stream), "up");
   if (!err) err = ck(cudaMemcpyAsync(d_hk, hk.data(), sizeof(int) * hk.size(), cudaMemcpyHostToDevice, c->stream), "up");
   if (!err) err = launch_hinfo(c, d_hk, c->Kh);
+  if (!err && c->opt.precision != RF_PREC_FP32) err = tc_setup(c);
   if (!err) err = ck(cudaMemsetAsync(c->d_OUT, 0, sizeof(float2) * splits * c->rect, c->stream), "memset");
   if (!err) err = ck(cudaStreamSynchronize(c->stream), "pattern setup");
   if (d_hk) cudaFree(d_hk);

@@ -49,6 +49,8 @@ struct Status {
   int iters;      // fixed-point updates of this solve
   int max_iter;
   int nonfinite;
+  int timeout;    // a bounded device-side wait ran out
+  int pad;
   double tol;
   double enorm;   // Frobenius norm of ebar (0: absolute measure)
   double inv_n2;  // 1 / N^2 (Parseval)
@@ -171,6 +173,15 @@ struct rf_ctx {
   std::vector<rfk::HIdx> h_hidx;  // host copy of the half-pattern indices
   float2* d_warm = nullptr;       // [Kh][6] warm-start staging
 
+  // split-precision (tensor-core) transforms along x
+  unsigned char* d_phiI = nullptr;
+  unsigned char* d_phiF = nullptr;
+  float* d_Tout = nullptr;        // [nXS][rows][NC][2 Kx] partial forward sums per x slice
+  int* d_tc_err = nullptr;
+  int tc_nXS = 0, tc_nJT = 0, tc_nJC = 0, tc_nXC = 0, tc_R = 0, tc_Qp = 0;
+  unsigned tc_cols = 0;
+  size_t tc_smem = 0;
+
   // load-path state
   double prev_macro[6] = {0, 0, 0, 0, 0, 0};
 
@@ -209,6 +220,9 @@ int launch_reset_er(rf_ctx* c, const double* ebar6, double scale_old);
 int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* ebar6);
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist);
 long long zero_base(const rf_ctx* c);
+// rf_tc.cu
+int tc_setup(rf_ctx* c);
+int launch_tc_row(rf_ctx* c, const int* done);
 void trace_begin(rf_ctx* c, long long idx);
 void trace_stage(rf_ctx* c, int stage);
 void trace_end(rf_ctx* c);

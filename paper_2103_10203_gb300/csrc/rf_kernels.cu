@@ -15,6 +15,7 @@
 #include <cstdio>
 
 #include "rf_internal.cuh"
+#include "rf_law.cuh"
 
 namespace rfk {
 
@@ -136,70 +137,7 @@ __global__ __launch_bounds__(256) void k_dft_axis(DftAxisArgs a) {
 }
 
 // ------------------------------------------------------------------------------------------
-// constitutive law (Sec. 2) on six-component tensors (11, 22, 33, 23, 13, 12)
-struct LawOut {
-  float s[6];
-  float ep[6];
-  float alpha;
-  bool yielded;
-};
-
-template <bool PLASTIC>
-__device__ __forceinline__ void stress6(const float* e, const DevPhase& p, const float* ep,
-                                        float alpha, LawOut& o) {
-  bool elastic = true;
-  if constexpr (PLASTIC) elastic = !p.plastic;
-  if (elastic) {
-    float tr = e[0] + e[1] + e[2];
-    float lt = p.lam * tr;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) o.s[i] = lt + 2.f * p.mu * e[i];
-#pragma unroll
-    for (int i = 3; i < 6; ++i) o.s[i] = 2.f * p.mu * e[i];
-    o.yielded = false;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) o.ep[i] = ep[i];
-    o.alpha = alpha;
-    return;
-  }
-  // trial state with the internal variables of the last converged increment
-  float ee[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) ee[i] = e[i] - ep[i];
-  float tre = ee[0] + ee[1] + ee[2];
-  float m = tre * (1.f / 3.f);
-  float s[6] = {2.f * p.mu * (ee[0] - m), 2.f * p.mu * (ee[1] - m), 2.f * p.mu * (ee[2] - m),
-                2.f * p.mu * ee[3], 2.f * p.mu * ee[4], 2.f * p.mu * ee[5]};
-  float ss = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] +
-             2.f * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
-  float seq = sqrtf(1.5f * ss);
-  float phi = seq - (p.sy + p.H * alpha);
-  float pm = (p.lam + (2.f / 3.f) * p.mu) * tre;
-  if (phi > 0.f) {
-    // radial return: dgamma = phi / (3 mu + H), flow direction 3/2 s / sigma_eq
-    float dg = phi / (3.f * p.mu + p.H);
-    float fl = 1.5f * dg / seq;
-    float f = 1.f - 3.f * p.mu * dg / seq;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      o.ep[i] = ep[i] + fl * s[i];
-      s[i] *= f;
-    }
-    o.alpha = alpha + dg;
-    o.yielded = true;
-  } else {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) o.ep[i] = ep[i];
-    o.alpha = alpha;
-    o.yielded = false;
-  }
-  o.s[0] = s[0] + pm;
-  o.s[1] = s[1] + pm;
-  o.s[2] = s[2] + pm;
-  o.s[3] = s[3];
-  o.s[4] = s[4];
-  o.s[5] = s[5];
-}
+// constitutive law: rf_law.cuh
 
 template <int NC>
 __device__ __forceinline__ void load_state(const float* st, long long N, long long g, float* ep,
@@ -735,14 +673,23 @@ int launch_iteration(rf_ctx* c) {
   const int* done = &c->d_status->done;
   trace_begin(c, c->launched_iters++);
   if (int e = inverse_stages(c, done)) return e;
-  RowArgs ra = row_args(c, done);
+  const bool tcm = c->opt.precision != RF_PREC_FP32;
   trace_stage(c, 2);
-  if (int e = row_dispatch(c, ra, false)) return e;
+  if (tcm) {
+    if (int e = launch_tc_row(c, done)) return e;
+  } else {
+    RowArgs ra = row_args(c, done);
+    if (int e = row_dispatch(c, ra, false)) return e;
+  }
   const int NCK = c->nc * c->Kx;
   const long long outstride = c->rect;
+  // the tensor-core row kernel leaves one partial sum per 128-wide x slice
+  const float2* fin = tcm ? reinterpret_cast<const float2*>(c->d_Tout) : c->d_T1p;
+  const int fsplits = tcm ? c->tc_nXS : 1;
+  const long long fstride = (long long)c->rows * NCK;
   trace_stage(c, 3);
   if (c->dim == 3) {
-    if (int e = dft(c, c->d_T1p, 1, 0, (long long)c->ny * NCK, c->d_T2f, 1, 0,
+    if (int e = dft(c, fin, fsplits, fstride, (long long)c->ny * NCK, c->d_T2f, 1, 0,
                     (long long)c->Ky * NCK, c->Ky, NCK, c->ny, c->nz, c->d_kym, nullptr, c->d_twy,
                     c->ny, -1, done))
       return e;
@@ -751,8 +698,8 @@ int launch_iteration(rf_ctx* c) {
                     c->Ky * NCK, c->nz, 1, c->d_kzm, nullptr, c->d_twz, c->nz, -1, done))
       return e;
   } else {
-    if (int e = dft(c, c->d_T1p, 1, 0, 0, c->d_OUT, c->splitB, outstride, 0, c->Ky, NCK, c->ny,
-                    1, c->d_kym, nullptr, c->d_twy, c->ny, -1, done))
+    if (int e = dft(c, fin, fsplits, fstride, 0, c->d_OUT, c->splitB, outstride, 0, c->Ky, NCK,
+                    c->ny, 1, c->d_kym, nullptr, c->d_twy, c->ny, -1, done))
       return e;
   }
   GammaArgs g{};

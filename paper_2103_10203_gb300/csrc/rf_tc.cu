@@ -1,0 +1,539 @@
+// Tensor-core (tcgen05) transforms along x for the split-precision modes.
+//
+// The row kernel of one update (Sec. 4, steps d, a, b along x) as two GEMMs around the law:
+//   inverse   eps[x][q]  = sum_j' Phi[x][j'] * Tq[q][j']          (M = 128 x, N = Qp, K = 2 Kx)
+//   law       tau[q][x]  = sigma(eps) - C0 : eps                    (per voxel, FP32)
+//   forward   T'[j'][q]  = sum_x  Phi[x][j'] * tau[q][x]           (M = 128 j' per tile, K = 128 x)
+// with q = (row, component), j' = 2 j + (0: real, 1: imaginary part) over the pattern's kx >= 0
+// columns, Phi[x][2j] = cos(2 pi kx_j x / Nx), Phi[x][2j+1] = -sin(...), and Tq holding the
+// line coefficients scaled by w_j / N. One CTA owns a 128-wide slice of x for R rows; the
+// forward sums over its slice only, and the transform along y adds the slices' partial sums.
+//
+// Operands are split into hi + lo parts of the tensor-core type (BF16 or TF32) and multiplied
+// as hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory. All operand tiles use the
+// canonical no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix). The
+// twiddle tiles are precomputed per pattern in that exact layout and staged into shared memory
+// with bulk asynchronous copies; every mbarrier wait is bounded and reports a timeout.
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "rf_internal.cuh"
+#include "rf_law.cuh"
+
+namespace rfk {
+namespace tc {
+
+constexpr int kTile = 128;           // x slice width and j' tile height
+constexpr int kChunkBytes = 128;     // K bytes per staged chunk row
+constexpr int kTileBytes = kTile * kChunkBytes;   // 16 KB: one 128-row chunk of one part
+constexpr int kMaxQ = 48;            // Qp: rows * components per CTA (padded to 16)
+constexpr long kWaitLimit = 1L << 26;
+
+struct EBf16 {
+  static constexpr int kBytes = 2;
+  static constexpr uint32_t kFmt = 1;
+};
+struct ETf32 {
+  static constexpr int kBytes = 4;
+  static constexpr uint32_t kFmt = 2;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version; base offset 0; no swizzle
+  return d;
+}
+
+template <class E>
+__host__ __device__ constexpr uint32_t idesc(int m, int n) {
+  return (1u << 4) | (E::kFmt << 7) | (E::kFmt << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+// byte offset of (row, kbyte) in a K-major tile of `rb` bytes per row
+__device__ __forceinline__ uint32_t cm_off(int row, int kbyte, int rb) {
+  return (uint32_t)(((row >> 3) * (rb >> 4) + (kbyte >> 4)) * 128 + (row & 7) * 16 + (kbyte & 15));
+}
+
+template <class E>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if constexpr (E::kFmt == 1) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar)));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok = 0;
+  for (long it = 0; it < kWaitLimit; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity));
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes));
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// hi + lo split into the tensor-core type, written at byte offsets of the hi and lo tiles
+template <class E>
+__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, uint32_t off,
+                                          float x) {
+  if constexpr (E::kBytes == 2) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    *reinterpret_cast<__nv_bfloat16*>(hi + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>(lo + off) = l;
+  } else {
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float r = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+    *reinterpret_cast<uint32_t*>(hi + off) = h;
+    *reinterpret_cast<uint32_t*>(lo + off) = l;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// twiddle tiles: PhiI[xs][jc][part] (rows x, K = j' chunk), PhiF[jt][xs][xc][part] (rows j',
+// K = x chunk); each tile 128 rows x 128 bytes in the core-matrix layout
+template <class E>
+__global__ void k_phi_tiles(const int* kx, int Kx, int Nx, const float2* tab, int nXS, int nJC,
+                            int nJT, int nXC, unsigned char* phiI, unsigned char* phiF) {
+  constexpr int per = kChunkBytes / E::kBytes;   // elements per chunk row
+  const long long total = (long long)nXS * kTile * nJC * per;   // (x, j') elements
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int jp = (int)(i % ((long long)nJC * per));
+    const int x = (int)(i / ((long long)nJC * per));
+    float v = 0.f;
+    if (x < Nx && jp < 2 * Kx) {
+      const int j = jp >> 1;
+      const int m = (int)(((long long)kx[j] * x) % Nx);
+      const float2 w = tab[m];                 // (cos, sin)(2 pi m / Nx)
+      v = (jp & 1) ? -w.y : w.x;
+    }
+    const int xs = x / kTile, xr = x % kTile;
+    // inverse tile
+    {
+      const int jc = jp / per, k = jp % per;
+      unsigned char* base = phiI + ((long long)(xs * nJC + jc) * 2) * kTileBytes;
+      put_split<E>(base, base + kTileBytes, cm_off(xr, k * E::kBytes, kChunkBytes), v);
+    }
+    // forward tile (only j' inside the nJT tiles)
+    if (jp < nJT * kTile) {
+      const int jt = jp / kTile, jr = jp % kTile;
+      const int xc = xr / per, k = xr % per;
+      unsigned char* base =
+          phiF + ((long long)((jt * nXS + xs) * nXC + xc) * 2) * kTileBytes;
+      put_split<E>(base, base + kTileBytes, cm_off(jr, k * E::kBytes, kChunkBytes), v);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+struct TcRowArgs {
+  const float2* T;        // [rows][NC][Kx]
+  float* Tout;            // [nXS][rows][NC][2 Kx]
+  const uint8_t* phase;
+  float* state;
+  const float* fac;
+  const unsigned char* phiI;
+  const unsigned char* phiF;
+  int Nx, Kx, rows, R, Qp, nJC, nJT, nXC, nXS;
+  uint32_t tmem_cols;
+  long long N;
+  LawParams law;
+  const int* done;
+  int* err;
+};
+
+}  // namespace tc
+
+namespace tc {
+
+template <class E, int NC, bool PLASTIC>
+__global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
+  if (a.done && *a.done) return;
+  constexpr int per = kChunkBytes / E::kBytes;         // K elements per chunk
+  constexpr int tau_rb = kTile * E::kBytes;            // tau row bytes (K = 128 x)
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* bufA = smem;                                  // 2 x (hi, lo) 16 KB tiles
+  unsigned char* bufT = smem + 4 * kTileBytes;                 // 2 x (hi, lo) Qp x 128 B
+  const int tq_bytes = a.Qp * kChunkBytes;
+  unsigned char* tau = bufT + 4 * tq_bytes;                    // (hi, lo) Qp x tau_rb
+  const int tau_bytes = a.Qp * tau_rb;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tau + 2 * tau_bytes);   // lbar[2], mbar[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int xs = blockIdx.x;
+  const int x = xs * kTile + tid;
+  const int row0 = blockIdx.y * a.R;
+  const int Q = a.R * NC;
+
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+
+  const int n_stages = a.nJC + a.nJT * a.nXC;
+  const uint32_t id_mma = idesc<E>(kTile, a.Qp);
+  // Failures (a bounded wait that ran out) are combined in s_err at CTA barriers, so that every
+  // thread takes the same path through barriers and warp-collective tensor-memory loads.
+  bool ok = true;
+
+  for (int g = 0; g < n_stages; ++g) {
+    const int b = g & 1;
+    unsigned char* A = bufA + b * 2 * kTileBytes;
+    unsigned char* Tb = bufT + b * 2 * tq_bytes;
+    // buffer b is free once the MMAs of stage g - 2 completed
+    if (g >= 2 && !mbar_wait(&bars[2 + b], ((g - 2) >> 1) & 1)) {
+      ok = false;
+      atomicOr(s_err, 1);
+    }
+    if (tid == 0 && ok) {
+      const unsigned char* src;
+      if (g < a.nJC) {
+        src = a.phiI + ((long long)(xs * a.nJC + g) * 2) * kTileBytes;
+      } else {
+        const int f = g - a.nJC, jt = f / a.nXC, xc = f % a.nXC;
+        src = a.phiF + ((long long)((jt * a.nXS + xs) * a.nXC + xc) * 2) * kTileBytes;
+      }
+      bulk_load(A, src, 2 * kTileBytes, &bars[b]);
+    }
+    if (g < a.nJC && ok) {
+      // Tq chunk: rows q, K = j' in [g * per, (g + 1) * per)
+      for (int i = tid; i < a.Qp * (per / 2); i += blockDim.x) {
+        const int q = i / (per / 2), kp = i % (per / 2);
+        const int jp = g * per + 2 * kp;
+        const int j = jp >> 1;
+        float vr = 0.f, vi = 0.f;
+        if (q < Q && j < a.Kx) {
+          const int r = q / NC, c = q % NC, row = row0 + r;
+          if (row < a.rows) {
+            const float2 t = a.T[((long long)row * NC + c) * a.Kx + j];
+            const float f = a.fac[j];
+            vr = f * t.x;
+            vi = f * t.y;
+          }
+        }
+        put_split<E>(Tb, Tb + tq_bytes, cm_off(q, 2 * kp * E::kBytes, kChunkBytes), vr);
+        put_split<E>(Tb, Tb + tq_bytes, cm_off(q, (2 * kp + 1) * E::kBytes, kChunkBytes), vi);
+      }
+    }
+    if (g == a.nJC) {
+      // law: D1 complete (stage nJC - 1 committed); eps for x = this thread's lane
+      if (!mbar_wait(&bars[2 + ((a.nJC - 1) & 1)], ((a.nJC - 1) >> 1) & 1)) atomicOr(s_err, 1);
+      __syncthreads();
+      ok = (*s_err == 0);
+    }
+    if (g == a.nJC && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      float ev[kMaxQ];
+#pragma unroll
+      for (int c0 = 0; c0 < kMaxQ; c0 += 16)
+        if (c0 < a.Qp) tmem_ld16(tmem + lane_base + c0, ev + c0);
+      unsigned char* th = tau;
+      unsigned char* tl = tau + tau_bytes;
+#pragma unroll
+      for (int r = 0; r < kMaxQ / NC; ++r) {
+        if (r >= a.R) break;
+        const int row = row0 + r;
+        float tv[6] = {0, 0, 0, 0, 0, 0};
+        if (row < a.rows && x < a.Nx) {
+          const long long gi = (long long)row * a.Nx + x;
+          float e6[6];
+          if (NC == 3) {
+            e6[0] = ev[r * NC + 0];
+            e6[1] = ev[r * NC + 1];
+            e6[2] = 0.f;
+            e6[3] = 0.f;
+            e6[4] = 0.f;
+            e6[5] = ev[r * NC + 2];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) e6[i] = ev[r * NC + i];
+          }
+          const DevPhase ph = a.law.ph[a.phase[gi]];
+          float ep[6] = {0, 0, 0, 0, 0, 0};
+          float alpha = 0.f;
+          if (PLASTIC) {
+            if (NC == 3) {
+              ep[0] = a.state[gi];
+              ep[1] = a.state[a.N + gi];
+              ep[5] = a.state[2 * a.N + gi];
+              ep[2] = -(ep[0] + ep[1]);
+              alpha = a.state[3 * a.N + gi];
+            } else {
+#pragma unroll
+              for (int i = 0; i < 6; ++i) ep[i] = a.state[i * a.N + gi];
+              alpha = a.state[6 * a.N + gi];
+            }
+          }
+          LawOut o;
+          stress6<PLASTIC>(e6, ph, ep, alpha, o);
+          const float tr = e6[0] + e6[1] + e6[2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) tv[i] = o.s[i] - (a.law.lam0 * tr + 2.f * a.law.mu0 * e6[i]);
+#pragma unroll
+          for (int i = 3; i < 6; ++i) tv[i] = o.s[i] - 2.f * a.law.mu0 * e6[i];
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int c6 = NC == 3 ? (c == 2 ? 5 : c) : c;
+          put_split<E>(th, tl, cm_off(r * NC + c, tid * E::kBytes, tau_rb), tv[c6]);
+        }
+      }
+      // padding rows of tau are zero
+      for (int q = Q; q < a.Qp; ++q) put_split<E>(th, tl, cm_off(q, tid * E::kBytes, tau_rb), 0.f);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0 && *s_err == 0) {
+      if (!mbar_wait(&bars[b], (g >> 1) & 1)) {
+        atomicOr(s_err, 1);
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a_hi = smem_u32(A), a_lo = a_hi + kTileBytes;
+        if (g < a.nJC) {
+          const uint32_t b_hi = smem_u32(Tb), b_lo = b_hi + tq_bytes;
+          const uint32_t d = tmem;   // D1 at columns [0, Qp)
+          for (int s = 0; s < kChunkBytes / 32; ++s) {
+            const uint32_t o = s * 256;
+            const uint32_t sbo_a = (kChunkBytes / 16) * 128, sbo_b = sbo_a;
+            const uint64_t ah = make_desc(a_hi + o, 128, sbo_a), al = make_desc(a_lo + o, 128, sbo_a);
+            const uint64_t bh = make_desc(b_hi + o, 128, sbo_b), bl = make_desc(b_lo + o, 128, sbo_b);
+            const uint32_t first = (g == 0 && s == 0) ? 0u : 1u;
+            mma<E>(d, ah, bh, id_mma, first);
+            mma<E>(d, ah, bl, id_mma, 1u);
+            mma<E>(d, al, bh, id_mma, 1u);
+          }
+        } else {
+          const int f = g - a.nJC, jt = f / a.nXC, xc = f % a.nXC;
+          const uint32_t d = tmem + (uint32_t)(a.Qp * (1 + jt));
+          const uint32_t t_hi = smem_u32(tau), t_lo = t_hi + tau_bytes;
+          const uint32_t sbo_t = (tau_rb / 16) * 128;
+          for (int s = 0; s < kChunkBytes / 32; ++s) {
+            const uint32_t oa = s * 256;
+            const uint32_t ob = (xc * (kChunkBytes / 16) + 2 * s) * 128;
+            const uint32_t sbo_a = (kChunkBytes / 16) * 128;
+            const uint64_t ah = make_desc(a_hi + oa, 128, sbo_a), al = make_desc(a_lo + oa, 128, sbo_a);
+            const uint64_t bh = make_desc(t_hi + ob, 128, sbo_t), bl = make_desc(t_lo + ob, 128, sbo_t);
+            const uint32_t first = (xc == 0 && s == 0) ? 0u : 1u;
+            mma<E>(d, ah, bh, id_mma, first);
+            mma<E>(d, ah, bl, id_mma, 1u);
+            mma<E>(d, al, bh, id_mma, 1u);
+          }
+        }
+        mma_commit(&bars[2 + b]);
+      }
+    }
+    __syncthreads();
+    ok = (*s_err == 0);
+    if (!ok) break;     // uniform: every thread read s_err after the same barrier
+  }
+  // all MMAs done: wait for the last stage's commit
+  if (ok) {
+    const int gl = n_stages - 1;
+    if (!mbar_wait(&bars[2 + (gl & 1)], (gl >> 1) & 1)) atomicOr(s_err, 1);
+  }
+  __syncthreads();
+  ok = (*s_err == 0);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int jp_base = 0;
+    for (int jt = 0; jt < a.nJT; ++jt) {
+      const int jp = jt * kTile + tid + jp_base;
+      float ov[kMaxQ];
+#pragma unroll
+      for (int c0 = 0; c0 < kMaxQ; c0 += 16)
+        if (c0 < a.Qp) tmem_ld16(tmem + lane_base + (uint32_t)(a.Qp * (1 + jt)) + c0, ov + c0);
+      if (jp < 2 * a.Kx) {
+#pragma unroll
+        for (int q = 0; q < kMaxQ; ++q) {
+          if (q >= Q) break;
+          const int r = q / NC, c = q % NC, row = row0 + r;
+          if (row < a.rows)
+            a.Tout[(((long long)xs * a.rows + row) * NC + c) * (2LL * a.Kx) + jp] = ov[q];
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(a.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------------
+// host side
+int tc_setup(rf_ctx* c) {
+  using namespace tc;
+  const bool bf = c->opt.precision == RF_PREC_SPLIT_BF16;
+  const int bytes = bf ? 2 : 4;
+  const int per = kChunkBytes / bytes;
+  c->tc_nXS = (c->nx + kTile - 1) / kTile;
+  const int jp = 2 * c->Kx;
+  c->tc_nJT = (jp + kTile - 1) / kTile;
+  c->tc_nJC = (c->tc_nJT * kTile) / per;     // inverse K covers the same padded range
+  c->tc_nXC = kTile / per;
+  // rows per CTA: Qp * (1 + nJT) tensor-memory columns must fit in 512
+  int R = (c->nc == 3) ? 16 : 8;
+  auto qp_of = [&](int r) { return ((r * c->nc + 15) / 16) * 16; };
+  while (R > 1 && qp_of(R) * (1 + c->tc_nJT) > 512) --R;
+  const int Qp = qp_of(R);
+  if (Qp * (1 + c->tc_nJT) > 512) {
+    set_error("split precision: pattern too wide for tensor memory (2 Kx > 1152)");
+    return RF_ERR_INVALID;
+  }
+  c->tc_R = R;
+  c->tc_Qp = Qp;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(Qp * (1 + c->tc_nJT))) cols <<= 1;
+  c->tc_cols = cols;
+  const size_t tile_pairs_I = (size_t)c->tc_nXS * c->tc_nJC;
+  const size_t tile_pairs_F = (size_t)c->tc_nJT * c->tc_nXS * c->tc_nXC;
+  cudaError_t e = cudaMalloc(&c->d_phiI, tile_pairs_I * 2 * kTileBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_phiF, tile_pairs_F * 2 * kTileBytes);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&c->d_Tout, sizeof(float) * (size_t)c->tc_nXS * c->rows * c->nc * 2 * c->Kx);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_tc_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "split precision buffers");
+  if (bf)
+    k_phi_tiles<EBf16><<<608, 256, 0, c->stream>>>(c->d_kx, c->Kx, c->nx, c->d_twx, c->tc_nXS,
+                                                    c->tc_nJC, c->tc_nJT, c->tc_nXC, c->d_phiI,
+                                                    c->d_phiF);
+  else
+    k_phi_tiles<ETf32><<<608, 256, 0, c->stream>>>(c->d_kx, c->Kx, c->nx, c->d_twx, c->tc_nXS,
+                                                    c->tc_nJC, c->tc_nJT, c->tc_nXC, c->d_phiI,
+                                                    c->d_phiF);
+  c->launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "phi tiles");
+  const int tau_rb = kTile * bytes;
+  // force one CTA per SM when it needs all 512 tensor-memory columns
+  size_t smem = 4 * kTileBytes + 4 * (size_t)Qp * kChunkBytes + 2 * (size_t)Qp * tau_rb + 64;
+  if (cols > 256 && smem < 120 * 1024) smem = 120 * 1024;
+  c->tc_smem = smem;
+  return RF_OK;
+}
+
+template <class E, int NC, bool PL>
+static int tc_row_launch(rf_ctx* c, const tc::TcRowArgs& a) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::k_tc_row<E, NC, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr = true;
+  }
+  dim3 grid(c->tc_nXS, (c->rows + c->tc_R - 1) / c->tc_R);
+  tc::k_tc_row<E, NC, PL><<<grid, 128, c->tc_smem, c->stream>>>(a);
+  c->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : cuda_fail(e, "tc row");
+}
+
+int launch_tc_row(rf_ctx* c, const int* done) {
+  tc::TcRowArgs a{};
+  a.T = c->d_T1;
+  a.Tout = c->d_Tout;
+  a.phase = c->d_phase;
+  a.state = c->d_state;
+  a.fac = c->d_fac;
+  a.phiI = c->d_phiI;
+  a.phiF = c->d_phiF;
+  a.Nx = c->nx;
+  a.Kx = c->Kx;
+  a.rows = c->rows;
+  a.R = c->tc_R;
+  a.Qp = c->tc_Qp;
+  a.nJC = c->tc_nJC;
+  a.nJT = c->tc_nJT;
+  a.nXC = c->tc_nXC;
+  a.nXS = c->tc_nXS;
+  a.tmem_cols = c->tc_cols;
+  a.N = c->N;
+  a.law = c->law;
+  a.done = done;
+  a.err = &c->d_status->timeout;
+  const bool bf = c->opt.precision == RF_PREC_SPLIT_BF16;
+  const bool pl = c->has_plastic;
+  if (c->nc == 3) {
+    if (bf) return pl ? tc_row_launch<tc::EBf16, 3, true>(c, a) : tc_row_launch<tc::EBf16, 3, false>(c, a);
+    return pl ? tc_row_launch<tc::ETf32, 3, true>(c, a) : tc_row_launch<tc::ETf32, 3, false>(c, a);
+  }
+  if (bf) return pl ? tc_row_launch<tc::EBf16, 6, true>(c, a) : tc_row_launch<tc::EBf16, 6, false>(c, a);
+  return pl ? tc_row_launch<tc::ETf32, 6, true>(c, a) : tc_row_launch<tc::ETf32, 6, false>(c, a);
+}
+
+}  // namespace rfk

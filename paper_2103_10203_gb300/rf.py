@@ -19,7 +19,7 @@ ERRORS = {-1: "invalid argument", -2: "CUDA error", -3: "non-finite", -4: "diver
           -5: "out of memory", -6: "device timeout", -7: "state"}
 GREEN = {"rotated": 0, "continuous": 1}
 REF = {"minmax": 0, "volume": 1}
-PRECISION = {"fp32": 0, "split_bf16": 1}
+PRECISION = {"fp32": 0, "split_bf16": 1, "split_tf32": 2}
 
 
 class rf_grid(C.Structure):
