@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--cpu-iters", type=int, default=4, help="oracle updates in the CPU sample")
+    p.add_argument("--transform", default="fft", choices=["fft", "dft"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_tf32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -70,10 +72,11 @@ def workload():
     return cfg, pm, k_target(RATIO, pm.size)
 
 
-def config_block(pm, K):
+def config_block(pm, K, transform="fft", precision="fp32"):
     return {"workload": "2D 1024x1024 J2 fibre composite (vf 0.4, r 8-24), 20 uniaxial-strain "
                         "increments to 2%, adapted reduced set K=5%",
             "grid": list(pm.shape[::-1]), "K": int(K), "increments": 20, "tol": TOL,
+            "transform": transform, "precision": precision,
             "l2": "flushed before every timed step (256 MB write)"}
 
 
@@ -142,17 +145,30 @@ def gpu_id_for(torch, dev):
 
 
 # ----------------------------------------------------------------------------- roofline
-def stage_work(name, info, shape, nc=3, ns=4):
-    """Algorithmic FLOPs and bytes of one launch of a stage (2D workload)."""
+def stage_work(name, info, shape, transform, nc=3, ns=4):
+    """Algorithmic FLOPs and bytes of one launch of a stage (2D workload).
+
+    Bytes are the compulsory device-memory traffic of the launch: phase map and J2 state read
+    by the row kernel, line coefficients in and out. FLOPs count the transform arithmetic
+    the kernel's algorithm needs (dense DFT: 8 FLOP per complex MAC; FFT: 5 L log2 L per
+    complex transform of length L)."""
+    import math
     ny, nx = shape
     N = nx * ny
     Kx, Ky = info["Kx"], info["Ky"]
+    lines = ny * nc * Kx * 8
     if name == "row":
-        flops = 8.0 * nc * Kx * N                       # x transforms both ways, FMA = 2 FLOP
-        byts = N * (1 + 4 * ns) + 2 * ny * nc * Kx * 8
+        byts = N * (1 + 4 * ns) + 2 * lines
+        if transform == "fft":
+            flops = 2 * (ny * nc / 2) * 5 * nx * math.log2(nx)
+        else:
+            flops = 8.0 * nc * Kx * N
     elif name in ("inverse_y", "forward_y"):
-        flops = 8.0 * ny * Ky * nc * Kx                 # complex MAC = 8 FLOP, dense rectangle
         byts = (ny + Ky) * nc * Kx * 8
+        if transform == "fft":
+            flops = nc * Kx * 5 * ny * math.log2(ny)
+        else:
+            flops = 8.0 * ny * Ky * nc * Kx
     else:
         flops, byts = 0.0, 0.0
     return flops, byts
@@ -242,7 +258,8 @@ def main():
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     pattern = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
-    solver = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER)
+    solver = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER,
+                       transform=args.transform, precision=args.precision)
     info = solver.rf_get_info()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -293,14 +310,30 @@ def main():
     real = {k: v for k, v in stage.items() if v[1] > 0}
     dom = max(real, key=lambda k: real[k][0])
     dom_ms = real[dom][0] / real[dom][1]
-    flops, byts = stage_work(dom, info, pm.shape)
+    flops, byts = stage_work(dom, info, pm.shape, args.transform)
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2070.0
     props = torch.cuda.get_device_properties(local)
-    if dom == "row" or dom.endswith("_y"):
+    kernel_names = {("fft", "row"): "k_fft_row", ("fft", "inverse_y"): "k_fft_cols",
+                    ("fft", "forward_y"): "k_fft_cols", ("dft", "row"): "k_row",
+                    ("dft", "inverse_y"): "k_dft_axis", ("dft", "forward_y"): "k_dft_axis"}
+    if args.precision != "fp32" and dom == "row":
+        kernel_names[("dft", "row")] = "k_tc_row"
+    if args.transform == "fft" and dom in ("row", "inverse_y", "forward_y"):
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+        kname = kernel_names[("fft", dom)]
+        achieved = byts / (dom_ms / 1e3) / 1e9
+        tr = ncu_traffic(kname)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": tr, "kernel": kname, "stage": dom,
+                "launch_ms": dom_ms, "algorithmic_bytes_per_launch": byts,
+                "algorithmic_flops_per_launch": flops,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
+    elif dom == "row" or dom.endswith("_y"):
         peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
         achieved = flops / (dom_ms / 1e3) / 1e12
-        kname = {"row": "k_row", "inverse_y": "k_dft_axis", "forward_y": "k_dft_axis"}[dom]
+        kname = kernel_names[("dft", dom)]
         tr = ncu_traffic(kname)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": tr, "kernel": kname, "stage": dom,
@@ -341,12 +374,17 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_block(pm, K), "solves_per_s": solves,
+                "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "split_bf16": "bf16x3", "split_tf32": "tf32x3"}[args.precision],
+                "data": "synthetic",
+                "config": config_block(pm, K, args.transform, args.precision),
+                "solves_per_s": solves,
                 "iterations_per_step": iters / args.steps, "e2e": e2e,
                 "gpu_launches": int(launches), "roofline": roof, "stage_share": stage_share,
                 "cpu_baseline": cpu, "clocks": clocks,
-                "precision": "FP32 transforms and law; FP64 residual and homogenised stress",
+                "precision": {"fp32": "FP32 transforms and law",
+                              "split_bf16": "BF16 hi+lo tensor-core x transforms, FP32 law",
+                              "split_tf32": "TF32 hi+lo tensor-core x transforms, FP32 law"}
+                [args.precision] + "; FP64 residual and homogenised stress",
                 "sigma_bar_final": [float(x) for x in outs[-1]["sigma_bar"][-1]]}
         print(json.dumps(line), flush=True)
     solver.close()

@@ -57,6 +57,7 @@ enum {
 enum { RF_GREEN_ROTATED = 0, RF_GREEN_CONTINUOUS = 1 };
 enum { RF_REF_MINMAX = 0, RF_REF_VOLUME = 1 };
 enum { RF_PREC_FP32 = 0, RF_PREC_SPLIT_BF16 = 1, RF_PREC_SPLIT_TF32 = 2 };
+enum { RF_TRANSFORM_DFT = 0, RF_TRANSFORM_FFT = 1 };
 
 typedef struct rf_ctx rf_ctx;
 
@@ -95,7 +96,12 @@ typedef struct rf_phase {
  *             accumulated in FP64 in every mode. Split modes need 2 Kx <= 1152.
  *  check_every  iterations launched between host checks of the device convergence flag
  *             (0 = library default). Work after convergence is skipped on the device, so
- *             results do not depend on it. */
+ *             results do not depend on it.
+ *  transform  RF_TRANSFORM_DFT: pruned separable DFT (only the pattern's distinct kx >= 0
+ *             columns along x, its (ky, kx) rectangle along y, (kz, ky, kx) along z).
+ *             RF_TRANSFORM_FFT: full FFTs along each axis restricted to the pattern (the
+ *             transform the paper uses, Sec. 4); needs power-of-two sizes (Nz = 1 in 2D) and
+ *             precision RF_PREC_FP32. Both compute the same restricted transform. */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
@@ -103,7 +109,8 @@ typedef struct rf_options {
   int32_t ref_medium;
   int32_t precision;
   int32_t check_every;
-  int32_t reserved[3];
+  int32_t transform;
+  int32_t reserved[2];
 } rf_options;
 
 /* Run statistics of the last solve on a context. */

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -31,6 +32,18 @@ long long zero_base(const rf_ctx* c) { return c->zero_base_idx; }
 using namespace rfk;
 
 namespace {
+
+std::mutex g_attr_mutex;
+bool g_attr_done[64] = {false};
+
+void init_attributes(int dev) {
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  if (dev < 0 || dev >= 64 || g_attr_done[dev]) return;
+  init_attributes_kernels();
+  init_attributes_tc();
+  init_attributes_fft();
+  g_attr_done[dev] = true;
+}
 
 struct DeviceGuard {
   int old = -1;
@@ -117,7 +130,58 @@ int update_reference(rf_ctx* c) {
   return RF_OK;
 }
 
+void free_graphs(rf_ctx* c) {
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  for (auto& t : c->graph_traces)
+    for (int i = 0; i <= t.n; ++i)
+      if (t.ev[i]) cudaEventDestroy(t.ev[i]);
+  c->graph_traces.clear();
+}
+
+// graph of `chunk` updates (captured once per chunk size and tracing state, then replayed)
+int get_graph(rf_ctx* c, int chunk, rf_ctx::GraphEntry** out) {
+  for (auto& g : c->graphs)
+    if (g.chunk == chunk && g.tracing == c->tracing) {
+      *out = &g;
+      return RF_OK;
+    }
+  rf_ctx::GraphEntry g{chunk, c->tracing, nullptr, {}};
+  const size_t first = c->graph_traces.size();
+  if (c->tracing) {
+    // events are created before the capture begins
+    while (c->ev_pool.size() < (size_t)chunk * 9) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      c->ev_pool.push_back(e);
+    }
+  }
+  const long long launched = c->launched_iters;
+  cudaGraph_t graph = nullptr;
+  if (int e = ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture"))
+    return e;
+  c->capturing = true;
+  int err = RF_OK;
+  for (int i = 0; i < chunk && !err; ++i) err = launch_iteration(c);
+  c->capturing = false;
+  c->launched_iters = launched;
+  cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+  if (!err && ce != cudaSuccess) err = cuda_fail(ce, "end capture");
+  if (!err) {
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (ce != cudaSuccess) err = cuda_fail(ce, "instantiate graph");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (err) return err;
+  for (size_t i = first; i < c->graph_traces.size(); ++i) g.trace_first.push_back((int)i);
+  c->graphs.push_back(g);
+  *out = &c->graphs.back();
+  return RF_OK;
+}
+
 void free_pattern(rf_ctx* c) {
+  free_graphs(c);
   dfree(c->d_kx);
   dfree(c->d_kym);
   dfree(c->d_kzm);
@@ -131,6 +195,7 @@ void free_pattern(rf_ctx* c) {
   dfree(c->d_T2f);
   dfree(c->d_OUT);
   dfree(c->d_part);
+  dfree(c->d_counter);
   dfree(c->d_sbar_part);
   dfree(c->d_viol_part);
   dfree(c->d_warm);
@@ -177,13 +242,16 @@ int run_iterations(rf_ctx* c) {
   const int maxchunk = c->opt.check_every > 0 ? c->opt.check_every : 32;
   int chunk = std::min(4, maxchunk);
   for (;;) {
-    for (int i = 0; i < chunk; ++i)
-      if (int e = launch_iteration(c)) return e;
+    rf_ctx::GraphEntry* g = nullptr;
+    if (int e = get_graph(c, chunk, &g)) return e;
+    const long long base = c->launched_iters;
+    if (int e = ck(cudaGraphLaunch(g->exec, c->stream), "graph launch")) return e;
+    c->launched_iters += chunk;
     if (int e = ck(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status),
                                    cudaMemcpyDeviceToHost, c->stream), "read status"))
       return e;
     if (int e = ck(cudaStreamSynchronize(c->stream), "iterate")) return e;
-    trace_collect(c, c->h_status->iters);
+    if (c->tracing) trace_collect_graph(c, *g, base, c->h_status->iters);
     if (c->h_status->done || c->h_status->timeout) break;
     chunk = std::min(chunk * 2, maxchunk);
   }
@@ -261,6 +329,15 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (opt->precision != RF_PREC_FP32 && opt->precision != RF_PREC_SPLIT_BF16 &&
       opt->precision != RF_PREC_SPLIT_TF32)
     return invalid("options: unknown precision");
+  if (opt->transform != RF_TRANSFORM_DFT && opt->transform != RF_TRANSFORM_FFT)
+    return invalid("options: unknown transform");
+  if (opt->transform == RF_TRANSFORM_FFT) {
+    auto pow2 = [](int v) { return v >= 2 && (v & (v - 1)) == 0; };
+    if (opt->precision != RF_PREC_FP32)
+      return invalid("options: the FFT transform runs in FP32 precision only");
+    if (!pow2(grid->n[0]) || !pow2(grid->n[1]) || (grid->dim == 3 && !pow2(grid->n[2])))
+      return invalid("options: the FFT transform needs power-of-two grid sizes (>= 2)");
+  }
 
   rf_ctx* c = new rf_ctx();
   cudaGetDevice(&c->dev);
@@ -273,6 +350,16 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   c->nc = c->dim == 2 ? 3 : 6;
   c->opt = *opt;
   c->stream = static_cast<cudaStream_t>(stream);
+  init_attributes(c->dev);
+  if (!c->stream) {
+    // updates are replayed as CUDA graphs, which cannot be captured on the legacy stream
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      set_error("rf_create: cannot create a stream");
+      return RF_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
   c->n_phases = n_phases;
   bool any_plastic = false;
   for (int p = 0; p < n_phases; ++p) {
@@ -323,6 +410,7 @@ int rf_set_phase_map(rf_ctx* c, const uint8_t* pm) {
   if (int e = ck(cudaMemcpyAsync(c->d_phase, pm, c->N, cudaMemcpyHostToDevice, c->stream),
                  "upload phase map"))
     return e;
+  free_graphs(c);   // the graphs hold the reference medium by value
   if (int e = update_reference(c)) return e;
   return reset_path_state(c);
 }
@@ -333,6 +421,7 @@ int rf_set_phase_map_device(rf_ctx* c, const uint8_t* d_pm) {
   if (int e = ck(cudaMemcpyAsync(c->d_phase, d_pm, c->N, cudaMemcpyDeviceToDevice, c->stream),
                  "copy phase map"))
     return e;
+  free_graphs(c);
   if (int e = update_reference(c)) return e;
   return reset_path_state(c);
 }
@@ -456,6 +545,11 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (smem_for(c->row_R) > 200 * 1024) return invalid("rf_set_pattern: pattern too wide for the row kernel");
   c->row_smem = smem_for(c->row_R);
   c->row_blocks = (c->rows + c->row_R - 1) / c->row_R;
+  if (c->opt.transform == RF_TRANSFORM_FFT) {
+    if (int e = fft_geometry(c)) return e;
+    c->splitB = c->splitC = 1;
+  }
+  const int part_blocks = std::max(c->row_blocks, c->fft_blocks);
   const int splits = std::max(c->splitB, c->splitC);
   int err = dalloc(&c->d_kx, c->Kx, "pattern");
   if (!err) err = dalloc(&c->d_kym, c->Ky, "pattern");
@@ -470,8 +564,10 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err && c->dim == 3) err = dalloc(&c->d_T2f, (size_t)c->nz * c->Ky * NCK, "line transforms");
   if (!err) err = dalloc(&c->d_OUT, (size_t)splits * c->rect, "partials");
   if (!err) err = dalloc(&c->d_part, (size_t)((c->Kh + 255) / 256), "partials");
-  if (!err) err = dalloc(&c->d_sbar_part, (size_t)c->row_blocks * 6, "partials");
-  if (!err) err = dalloc(&c->d_viol_part, (size_t)c->row_blocks, "partials");
+  if (!err) err = dalloc(&c->d_counter, 1, "counter");
+  if (!err) err = ck(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), c->stream), "memset");
+  if (!err) err = dalloc(&c->d_sbar_part, (size_t)part_blocks * 6, "partials");
+  if (!err) err = dalloc(&c->d_viol_part, (size_t)part_blocks, "partials");
   if (!err) err = dalloc(&c->d_warm, (size_t)c->Kh * 6, "warm");
   int* d_hk = nullptr;
   if (!err) err = dalloc(&d_hk, hk.size(), "pattern");
@@ -740,6 +836,7 @@ int rf_destroy(rf_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   trace_collect(c, 0);
+  free_graphs(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
   free_pattern(c);
@@ -755,6 +852,7 @@ int rf_destroy(rf_ctx* c) {
   dfree(c->d_alpha);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_sbar) cudaFreeHost(c->h_sbar);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return RF_OK;
 }

@@ -1,0 +1,568 @@
+// FFT transform mode: steps b and d of Sec. 4 as full FFTs along each axis restricted to the
+// reduced set (the paper's own choice of transform), for power-of-two grid sizes, FP32.
+//
+// Along x (row kernel, fused with the law): two real lines are packed into one complex
+// sequence z = a + i b; the inverse builds z's spectrum from the lines' kx >= 0 coefficients
+// (Hermitian completion), transforms back, applies the law per voxel, packs tau the same way,
+// transforms forward and separates the two lines' spectra at the pattern's kx columns.
+// Along y and z (column kernel): sparse spectra (the pattern's distinct ky or kz values) are
+// scattered into full-length sequences for the inverse; the forward keeps only those values.
+// The transforms are out-of-place Stockham radix-4 (plus one radix-2 stage when log2 L is odd)
+// in shared memory, with an FP32 twiddle table computed in FP64.
+#include <cmath>
+
+#include "rf_internal.cuh"
+#include "rf_law.cuh"
+
+namespace rfk {
+
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Stage-major twiddles: for the radix-4 stage with sub-transform size Ns the butterfly at
+// position k < Ns needs exp(+2 pi i r k / (4 Ns)), r = 1, 2, 3; they are stored contiguously in k
+// (three arrays per stage) so that neighbouring threads read neighbouring words. A final
+// radix-2 stage (log2 L odd) stores exp(+2 pi i k / (2 Ns)). Total entries < 3 L / 2.
+// Built once per block from the global table tab[t] = exp(+2 pi i t / L).
+__device__ int stage_twiddles(const float2* tab, int L, float2* tw) {
+  int off = 0;
+  int Ns = 1;
+  while (Ns * 4 <= L) {
+    const int step = L / (4 * Ns);
+    for (int k = threadIdx.x; k < Ns; k += blockDim.x) {
+      tw[off + k] = tab[k * step];
+      tw[off + Ns + k] = tab[2 * k * step];
+      tw[off + 2 * Ns + k] = tab[3 * k * step];
+    }
+    off += 3 * Ns;
+    Ns *= 4;
+  }
+  if (Ns < L) {
+    const int step = L / (2 * Ns);
+    for (int k = threadIdx.x; k < Ns; k += blockDim.x) tw[off + k] = tab[k * step];
+    off += Ns;
+  }
+  return off;
+}
+
+__host__ __device__ constexpr int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+// Batched in-shared-memory FFT of P sequences of length L = 2^lg, sign -1 forward, +1 inverse
+// (unnormalised). Sequence p occupies [p * L, (p + 1) * L) of both buffers. Out-of-place
+// Stockham radix-4 with a final radix-2 stage when lg is odd. Returns the buffer holding the
+// result. The whole block calls it.
+__device__ float2* fft_block(float2* in, float2* out, const float2* tw, int lg, int P, int sign) {
+  const int L = 1 << lg;
+  const int lq = lg - 2;          // log2 (L / 4)
+  const int q = L >> 2;
+  int off = 0;
+  int ls = 0;                     // log2 Ns
+  while (ls + 2 <= lg) {
+    const int Ns = 1 << ls;
+    for (int u = threadIdx.x; u < (P << lq); u += blockDim.x) {
+      const int p = u >> lq, j = u & (q - 1);
+      const float2* src = in + (p << lg);
+      float2* dst = out + (p << lg);
+      float2 v0 = src[j], v1 = src[j + q], v2 = src[j + 2 * q], v3 = src[j + 3 * q];
+      const int k = j & (Ns - 1);
+      if (ls > 0) {
+        float2 w1 = tw[off + k], w2 = tw[off + Ns + k], w3 = tw[off + 2 * Ns + k];
+        if (sign < 0) {
+          w1.y = -w1.y;
+          w2.y = -w2.y;
+          w3.y = -w3.y;
+        }
+        v1 = cmul(v1, w1);
+        v2 = cmul(v2, w2);
+        v3 = cmul(v3, w3);
+      }
+      const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y);
+      const float2 d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
+      const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y);
+      const float2 d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
+      // sign * i * d13
+      const float2 id13 = sign < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
+      const int base = ((j >> ls) << (ls + 2)) + k;
+      dst[base] = make_float2(s02.x + s13.x, s02.y + s13.y);
+      dst[base + Ns] = make_float2(d02.x + id13.x, d02.y + id13.y);
+      dst[base + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
+      dst[base + 3 * Ns] = make_float2(d02.x - id13.x, d02.y - id13.y);
+    }
+    __syncthreads();
+    float2* t = in;
+    in = out;
+    out = t;
+    off += 3 * Ns;
+    ls += 2;
+  }
+  if (ls < lg) {   // one radix-2 stage
+    const int Ns = 1 << ls;
+    const int h = L >> 1, lh = lg - 1;
+    for (int u = threadIdx.x; u < (P << lh); u += blockDim.x) {
+      const int p = u >> lh, j = u & (h - 1);
+      const float2* src = in + (p << lg);
+      float2* dst = out + (p << lg);
+      float2 v0 = src[j], v1 = src[j + h];
+      const int k = j & (Ns - 1);
+      float2 w = tw[off + k];
+      if (sign < 0) w.y = -w.y;
+      v1 = cmul(v1, w);
+      const int base = ((j >> ls) << (ls + 1)) + k;
+      dst[base] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      dst[base + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    __syncthreads();
+    in = out;
+  }
+  return in;
+}
+
+}  // namespace
+
+struct FftRowArgs {
+  const float2* T;      // [rows][NC][Kx]
+  float2* Tout;         // [rows][NC][Kx]
+  const uint8_t* phase;
+  float* state;
+  const int* kx;
+  const float2* table;  // exp(+2 pi i t / Nx)
+  int Nx, Kx, rows, R;
+  long long N;
+  float invN;
+  LawParams law;
+  float* eps_out;
+  float* sig_out;
+  float* alpha_out;
+  double* sbar_part;
+  double* viol_part;
+  int commit;
+  const int* done;
+};
+
+template <int NC, bool PLASTIC, bool FINAL>
+__global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
+  if (!FINAL && a.done && *a.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = a.Nx;
+  const int S = a.R * NC;              // real lines in this block
+  const int P = (S + 1) / 2;           // packed complex sequences
+  float2* tw = reinterpret_cast<float2*>(smem);    // stage twiddles, < 3 L / 2 entries
+  float2* b0 = tw + (3 * L) / 2 + 1;
+  float2* b1 = b0 + (size_t)P * L;
+  int* kxs = reinterpret_cast<int*>(b1 + (size_t)P * L);
+  __shared__ double red[8];
+  __shared__ DevPhase phs[kMaxPhases];
+  const int tid = threadIdx.x;
+  const int row0 = blockIdx.x * a.R;
+  const int lg = ilog2(L);
+  stage_twiddles(a.table, L, tw);
+  for (int i = tid; i < a.Kx; i += blockDim.x) kxs[i] = a.kx[i];
+  for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
+  for (int i = tid; i < P * L; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // spectra: line s = r * NC + c is the real (s even) or imaginary (s odd) carrier of p = s / 2
+  // coefficients are loaded in register batches (both carriers), then scattered: the real
+  // carriers write, and after a barrier the imaginary carriers add. The batch loop's trip count
+  // is the same for every thread (it contains barriers).
+  constexpr int kBatch = 8;
+  const int nsc = P * a.Kx;
+  for (int base = 0; base < nsc; base += kBatch * blockDim.x) {
+    float2 tl[2][kBatch];
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+      for (int m = 0; m < kBatch; ++m) {
+        tl[pass][m] = make_float2(0.f, 0.f);
+        const int u = base + tid + m * blockDim.x;
+        if (u < nsc) {
+          const int p = u / a.Kx, j = u - p * a.Kx;
+          const int s = 2 * p + pass;
+          const int r = s / NC, c = s - r * NC, row = row0 + r;
+          if (s < S && row < a.rows) tl[pass][m] = a.T[((long long)row * NC + c) * a.Kx + j];
+        }
+      }
+#pragma unroll
+    for (int m = 0; m < kBatch; ++m) {
+      const int u = base + tid + m * blockDim.x;
+      if (u >= nsc) continue;
+      const int p = u / a.Kx, j = u - p * a.Kx;
+      float2 t = tl[0][m];
+      const int k = kxs[j];
+      const bool self = (k == 0) || (2 * k == L);
+      if (self) t.y = 0.f;
+      float2* z = b0 + (size_t)p * L;
+      z[k] = t;
+      if (!self) z[L - k] = make_float2(t.x, -t.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < kBatch; ++m) {
+      const int u = base + tid + m * blockDim.x;
+      if (u >= nsc) continue;
+      const int p = u / a.Kx, j = u - p * a.Kx;
+      if (2 * p + 1 >= S) continue;
+      float2 t = tl[1][m];
+      const int k = kxs[j];
+      const bool self = (k == 0) || (2 * k == L);
+      if (self) t.y = 0.f;
+      float2* z = b0 + (size_t)p * L;
+      z[k].x -= t.y;        // add i * t at k and i * conj(t) at L - k
+      z[k].y += t.x;
+      if (!self) {
+        z[L - k].x += t.y;
+        z[L - k].y += t.x;
+      }
+    }
+    __syncthreads();
+  }
+  float2* zb = fft_block(b0, b1, tw, lg, P, +1);
+  float2* other = (zb == b0) ? b1 : b0;
+  double sb[6] = {0, 0, 0, 0, 0, 0};
+  double vmax = 0.0;
+  const float lam0 = a.law.lam0, mu0 = a.law.mu0;
+  constexpr int kVox = 4;
+  constexpr int NS = NC == 3 ? 4 : 7;
+  for (int vb = 0; vb < a.R * L; vb += kVox * blockDim.x) {
+    int pid[kVox];
+    float stv[kVox][NS];
+#pragma unroll
+    for (int u = 0; u < kVox; ++u) {
+      const int v = vb + tid + u * blockDim.x;
+      const int r = v / L, x = v - r * L, row = row0 + r;
+      pid[u] = 0;
+      if (v < a.R * L && row < a.rows) {
+        const long long g = (long long)row * L + x;
+        pid[u] = a.phase[g];
+        if (PLASTIC) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i) stv[u][i] = a.state[i * a.N + g];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kVox; ++u) {
+      const int v = vb + tid + u * blockDim.x;
+      if (v >= a.R * L) continue;
+      const int r = v / L, x = v - r * L, row = row0 + r;
+      float e[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int s = r * NC + c;
+        const float2 z = zb[(size_t)(s >> 1) * L + x];
+        e[c] = ((s & 1) ? z.y : z.x) * a.invN;
+      }
+      float tau6[6] = {0, 0, 0, 0, 0, 0};
+      if (row < a.rows) {
+        const long long g = (long long)row * L + x;
+        float e6[6];
+        comp_to6<NC>(e, e6);
+        const DevPhase ph = phs[pid[u]];
+        float ep[6] = {0, 0, 0, 0, 0, 0};
+        float alpha = 0.f;
+        if (PLASTIC) {
+          if (NC == 3) {
+            ep[0] = stv[u][0];
+            ep[1] = stv[u][1];
+            ep[5] = stv[u][2];
+            ep[2] = -(ep[0] + ep[1]);
+            alpha = stv[u][3];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) ep[i] = stv[u][i];
+            alpha = stv[u][NS - 1];
+          }
+        }
+        LawOut o;
+        stress6<PLASTIC>(e6, ph, ep, alpha, o);
+        if (!FINAL) {
+          const float tr = e6[0] + e6[1] + e6[2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (lam0 * tr + 2.f * mu0 * e6[i]);
+#pragma unroll
+          for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * mu0 * e6[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
+          if (a.eps_out) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) a.eps_out[i * a.N + g] = e6[i];
+          }
+          if (a.sig_out) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) a.sig_out[i * a.N + g] = o.s[i];
+          }
+          if (PLASTIC) {
+            if (a.commit) store_state<NC>(a.state, a.N, g, o.ep, o.alpha);
+            if (a.alpha_out) a.alpha_out[g] = o.alpha;
+            if (o.yielded) {
+              double s0 = o.s[0], s1 = o.s[1], s2 = o.s[2];
+              double pmd = (s0 + s1 + s2) / 3.0;
+              double d0 = s0 - pmd, d1 = s1 - pmd, d2 = s2 - pmd;
+              double qq = d0 * d0 + d1 * d1 + d2 * d2 +
+                          2.0 * ((double)o.s[3] * o.s[3] + (double)o.s[4] * o.s[4] +
+                                 (double)o.s[5] * o.s[5]);
+              double yl = (double)ph.sy + (double)ph.H * (double)o.alpha;
+              vmax = fmax(vmax, fabs(sqrt(1.5 * qq) - yl) / (double)ph.sy);
+            }
+          } else if (a.alpha_out) {
+            a.alpha_out[g] = 0.f;
+          }
+        }
+      }
+      if (!FINAL) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int s = r * NC + c;
+          float* dst = reinterpret_cast<float*>(other + (size_t)(s >> 1) * L + x);
+          dst[s & 1] = tau6[comp6<NC>(c)];
+        }
+      }
+    }
+  }
+  if (FINAL) {
+    for (int i = 0; i < 6; ++i) {
+      double t = block_sum_d(sb[i], red);
+      if (tid == 0) a.sbar_part[blockIdx.x * 6 + i] = t;
+    }
+    double vm = block_max_d(vmax, red);
+    if (tid == 0) a.viol_part[blockIdx.x] = vm;
+    return;
+  }
+  // an odd line count leaves the last sequence's imaginary carrier unused: zero it
+  if (S & 1)
+    for (int x = tid; x < L; x += blockDim.x) other[(size_t)(P - 1) * L + x].y = 0.f;
+  __syncthreads();
+  float2* zf = fft_block(other, zb, tw, lg, P, -1);
+  for (int u = tid; u < S * a.Kx; u += blockDim.x) {
+    const int s = u / a.Kx, j = u - s * a.Kx;
+    const int r = s / NC, c = s - r * NC, row = row0 + r;
+    if (row >= a.rows) continue;
+    const int k = kxs[j];
+    const float2* z = zf + (size_t)(s >> 1) * L;
+    const float2 zk = z[k], zm = z[(L - k) & (L - 1)];
+    float2 out;
+    if ((s & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    a.Tout[((long long)row * NC + c) * a.Kx + j] = out;
+  }
+}
+
+struct FftColArgs {
+  const float2* in;
+  long long in_bstride;
+  int in_rows;            // rows of `in` (sparse count if in_list)
+  const int* in_list;     // nullable: row i holds position in_list[i] (reduced mod L)
+  float2* out;
+  long long out_bstride;
+  int out_rows;
+  const int* out_list;    // nullable: output row i = position out_list[i]
+  int ncols, L, C, sign;
+  const float2* table;
+  const int* done;
+};
+
+// columns [col0, col0 + C) of a row-major [rows][ncols] array, batched over blockIdx.y
+__global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
+  if (a.done && *a.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = a.L, C = a.C;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* b0 = tw + (3 * L) / 2 + 1;
+  float2* b1 = b0 + (size_t)C * L;
+  const int col0 = blockIdx.x * C;
+  const long long b = blockIdx.y;
+  const float2* in = a.in + b * a.in_bstride;
+  float2* out = a.out + b * a.out_bstride;
+  stage_twiddles(a.table, L, tw);
+  if (a.in_list)
+    for (int i = threadIdx.x; i < C * L; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // loads are issued in batches of 8 per thread before they are stored, so their latencies overlap
+  const int total = a.in_rows * C;
+  for (int i0 = threadIdx.x; i0 < total; i0 += 8 * blockDim.x) {
+    float2 v[8];
+    int dst[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = make_float2(0.f, 0.f);
+      dst[u] = -1;
+      if (i < total) {
+        const int r = i / C, cc = i - r * C, col = col0 + cc;
+        if (col < a.ncols) v[u] = in[(long long)r * a.ncols + col];
+        dst[u] = cc * L + (a.in_list ? a.in_list[r] : r);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (dst[u] >= 0) b0[dst[u]] = v[u];
+  }
+  __syncthreads();
+  const float2* z = fft_block(b0, b1, tw, ilog2(L), C, a.sign);
+  for (int i = threadIdx.x; i < a.out_rows * C; i += blockDim.x) {
+    const int r = i / C, cc = i - r * C, col = col0 + cc;
+    if (col >= a.ncols) continue;
+    const int pos = a.out_list ? a.out_list[r] : r;
+    out[(long long)r * a.ncols + col] = z[(size_t)cc * L + pos];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+static int fft_check(rf_ctx* c, const char* what) {
+  c->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : cuda_fail(e, what);
+}
+
+static int cols_tile(int L) {
+  int C = 4096 / L;
+  if (C > 32) C = 32;
+  if (C < 1) C = 1;
+  return C;
+}
+
+static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, const int* in_list,
+                    float2* out, long long out_bs, int out_rows, const int* out_list, int ncols,
+                    int L, int batch, int sign, const float2* tab, const int* done) {
+  FftColArgs a;
+  a.in = in;
+  a.in_bstride = in_bs;
+  a.in_rows = in_rows;
+  a.in_list = in_list;
+  a.out = out;
+  a.out_bstride = out_bs;
+  a.out_rows = out_rows;
+  a.out_list = out_list;
+  a.ncols = ncols;
+  a.L = L;
+  a.C = cols_tile(L);
+  a.sign = sign;
+  a.table = tab;
+  a.done = done;
+  const size_t smem = ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)a.C * L) * sizeof(float2);
+  dim3 grid((ncols + a.C - 1) / a.C, batch);
+  k_fft_cols<<<grid, 256, smem, c->stream>>>(a);
+  return fft_check(c, "fft cols");
+}
+
+int fft_geometry(rf_ctx* c) {
+  // rows per row-kernel block: about 6144 complex points per ping-pong buffer, even line count
+  const int L = c->nx;
+  int R = (2 * 6144) / (c->nc * L);
+  if (R < 1) R = 1;
+  if (R > c->rows) R = c->rows;
+  c->fft_R = R;
+  c->fft_blocks = (c->rows + R - 1) / R;
+  const int P = (R * c->nc + 1) / 2;
+  c->fft_smem = ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)P * L) * sizeof(float2) +
+                (size_t)c->Kx * sizeof(int) + 16;
+  if (c->fft_smem > 200 * 1024) {
+    set_error("FFT mode: rows too long for the row kernel's shared memory");
+    return RF_ERR_INVALID;
+  }
+  return RF_OK;
+}
+
+static FftRowArgs fft_row_args(rf_ctx* c, const int* done) {
+  FftRowArgs a{};
+  a.T = c->d_T1;
+  a.Tout = c->d_T1p;
+  a.phase = c->d_phase;
+  a.state = c->d_state;
+  a.kx = c->d_kx;
+  a.table = c->d_twx;
+  a.Nx = c->nx;
+  a.Kx = c->Kx;
+  a.rows = c->rows;
+  a.R = c->fft_R;
+  a.N = c->N;
+  a.invN = (float)(1.0 / (double)c->N);
+  a.law = c->law;
+  a.done = done;
+  return a;
+}
+
+void init_attributes_fft() {
+  const int s = 200 * 1024;
+  cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<3, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<3, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<3, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<6, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<6, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<6, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_row<6, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+}
+
+template <int NC, bool PL, bool FIN>
+static int fft_row_launch(rf_ctx* c, const FftRowArgs& a) {
+  k_fft_row<NC, PL, FIN><<<c->fft_blocks, 256, c->fft_smem, c->stream>>>(a);
+  return fft_check(c, "fft row");
+}
+
+int launch_fft_row(rf_ctx* c, const int* done, bool final_pass, int commit) {
+  FftRowArgs a = fft_row_args(c, done);
+  if (final_pass) {
+    a.eps_out = c->d_eps;
+    a.sig_out = c->d_sig;
+    a.alpha_out = c->d_alpha;
+    a.sbar_part = c->d_sbar_part;
+    a.viol_part = c->d_viol_part;
+    a.commit = commit;
+  }
+  const bool pl = c->has_plastic;
+  if (c->nc == 3) {
+    if (final_pass)
+      return pl ? fft_row_launch<3, true, true>(c, a) : fft_row_launch<3, false, true>(c, a);
+    return pl ? fft_row_launch<3, true, false>(c, a) : fft_row_launch<3, false, false>(c, a);
+  }
+  if (final_pass)
+    return pl ? fft_row_launch<6, true, true>(c, a) : fft_row_launch<6, false, true>(c, a);
+  return pl ? fft_row_launch<6, true, false>(c, a) : fft_row_launch<6, false, false>(c, a);
+}
+
+// inverse transforms along z and y: ER -> T1
+int fft_inverse_stages(rf_ctx* c, const int* done) {
+  const int NCK = c->nc * c->Kx;
+  if (c->dim == 3) {
+    trace_stage(c, 0);
+    if (int e = fft_cols(c, c->d_ER, 0, c->Kz, c->d_kzm, c->d_T2, 0, c->nz, nullptr,
+                         c->Ky * NCK, c->nz, 1, +1, c->d_twz, done))
+      return e;
+    trace_stage(c, 1);
+    return fft_cols(c, c->d_T2, (long long)c->Ky * NCK, c->Ky, c->d_kym, c->d_T1,
+                    (long long)c->ny * NCK, c->ny, nullptr, NCK, c->ny, c->nz, +1, c->d_twy, done);
+  }
+  trace_stage(c, 1);
+  return fft_cols(c, c->d_ER, 0, c->Ky, c->d_kym, c->d_T1, 0, c->ny, nullptr, NCK, c->ny, 1, +1,
+                  c->d_twy, done);
+}
+
+// forward transforms along y and z: T1p -> OUT (one split)
+int fft_forward_stages(rf_ctx* c, const int* done) {
+  const int NCK = c->nc * c->Kx;
+  if (c->dim == 3) {
+    trace_stage(c, 3);
+    if (int e = fft_cols(c, c->d_T1p, (long long)c->ny * NCK, c->ny, nullptr, c->d_T2f,
+                         (long long)c->Ky * NCK, c->Ky, c->d_kym, NCK, c->ny, c->nz, -1,
+                         c->d_twy, done))
+      return e;
+    trace_stage(c, 4);
+    return fft_cols(c, c->d_T2f, 0, c->nz, nullptr, c->d_OUT, 0, c->Kz, c->d_kzm, c->Ky * NCK,
+                    c->nz, 1, -1, c->d_twz, done);
+  }
+  trace_stage(c, 3);
+  return fft_cols(c, c->d_T1p, 0, c->ny, nullptr, c->d_OUT, 0, c->Ky, c->d_kym, NCK, c->ny, 1,
+                  -1, c->d_twy, done);
+}
+
+}  // namespace rfk

@@ -107,6 +107,8 @@ struct GammaArgs {
   int Kx, Ky, NC;
   float inv2mu0, cgam;
   const Status* st;
+  Status* status;       // convergence decision written by the last block
+  unsigned* counter;    // blocks finished (reset to 0 by the last block)
   double* part;         // [gridDim.x]
   const int* done;
 };
@@ -155,6 +157,7 @@ struct rf_ctx {
   float2* d_twy = nullptr;
   float2* d_twz = nullptr;
   double* d_part = nullptr;       // residual block partials
+  unsigned* d_counter = nullptr;  // finished-block counter of the Green kernel
   int n_part = 0;
   double* d_sbar_part = nullptr;  // [row blocks][6]
   double* d_viol_part = nullptr;
@@ -173,6 +176,10 @@ struct rf_ctx {
   std::vector<rfk::HIdx> h_hidx;  // host copy of the half-pattern indices
   float2* d_warm = nullptr;       // [Kh][6] warm-start staging
 
+  // FFT transform mode
+  int fft_R = 0, fft_blocks = 0;
+  size_t fft_smem = 0;
+
   // split-precision (tensor-core) transforms along x
   unsigned char* d_phiI = nullptr;
   unsigned char* d_phiF = nullptr;
@@ -185,6 +192,18 @@ struct rf_ctx {
   // load-path state
   double prev_macro[6] = {0, 0, 0, 0, 0, 0};
 
+  // CUDA graphs of update chunks (replayed instead of per-kernel launches)
+  struct TraceIter;
+  struct GraphEntry {
+    int chunk;
+    bool tracing;
+    cudaGraphExec_t exec;
+    std::vector<int> trace_first;   // index into traces of each captured update
+  };
+  std::vector<GraphEntry> graphs;
+  bool own_stream = false;
+  bool capturing = false;
+
   // tracing: one event before each stage of an update and one after the last stage
   bool tracing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -195,6 +214,7 @@ struct rf_ctx {
     int n;
   };
   std::vector<TraceIter> pending;
+  std::vector<TraceIter> graph_traces;   // events owned by captured graphs
   TraceIter* cur = nullptr;
   long long launched_iters = 0;
   double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -223,10 +243,20 @@ long long zero_base(const rf_ctx* c);
 // rf_tc.cu
 int tc_setup(rf_ctx* c);
 int launch_tc_row(rf_ctx* c, const int* done);
+// rf_fft.cu
+int fft_geometry(rf_ctx* c);
+int launch_fft_row(rf_ctx* c, const int* done, bool final_pass, int commit);
+int fft_inverse_stages(rf_ctx* c, const int* done);
+int fft_forward_stages(rf_ctx* c, const int* done);
 void trace_begin(rf_ctx* c, long long idx);
 void trace_stage(rf_ctx* c, int stage);
 void trace_end(rf_ctx* c);
 int trace_collect(rf_ctx* c, long long real_iters);
+void trace_collect_graph(rf_ctx* c, const rf_ctx::GraphEntry& g, long long base,
+                         long long real_iters);
+void init_attributes_kernels();
+void init_attributes_tc();
+void init_attributes_fft();
 // pattern.cu
 int pattern_adapted(const rf_grid* g, const uint8_t* pm, int incl, long long k_target,
                     int32_t* out, long long cap, long long* K_out, cudaStream_t s);

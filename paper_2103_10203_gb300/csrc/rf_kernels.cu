@@ -139,89 +139,6 @@ __global__ __launch_bounds__(256) void k_dft_axis(DftAxisArgs a) {
 // ------------------------------------------------------------------------------------------
 // constitutive law: rf_law.cuh
 
-template <int NC>
-__device__ __forceinline__ void load_state(const float* st, long long N, long long g, float* ep,
-                                           float& alpha) {
-  if (NC == 3) {
-    ep[0] = st[g];
-    ep[1] = st[N + g];
-    ep[5] = st[2 * N + g];
-    ep[2] = -(ep[0] + ep[1]);
-    ep[3] = ep[4] = 0.f;
-    alpha = st[3 * N + g];
-  } else {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) ep[i] = st[i * N + g];
-    alpha = st[6 * N + g];
-  }
-}
-
-template <int NC>
-__device__ __forceinline__ void store_state(float* st, long long N, long long g, const float* ep,
-                                            float alpha) {
-  if (NC == 3) {
-    st[g] = ep[0];
-    st[N + g] = ep[1];
-    st[2 * N + g] = ep[5];
-    st[3 * N + g] = alpha;
-  } else {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) st[i * N + g] = ep[i];
-    st[6 * N + g] = alpha;
-  }
-}
-
-template <int NC>
-__device__ __forceinline__ void comp_to6(const float* e, float* e6) {
-  if (NC == 3) {
-    e6[0] = e[0];
-    e6[1] = e[1];
-    e6[2] = 0.f;
-    e6[3] = 0.f;
-    e6[4] = 0.f;
-    e6[5] = e[2];
-  } else {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) e6[i] = e[i];
-  }
-}
-
-template <int NC>
-__device__ __forceinline__ int comp6(int c) {
-  return NC == 3 ? (c == 2 ? 5 : c) : c;
-}
-
-__device__ __forceinline__ double block_sum_d(double v, double* red) {
-  // deterministic: fixed shuffle tree inside warps, fixed order across warps
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0) {
-    int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) t += red[i];
-  }
-  __syncthreads();
-  return t;
-}
-
-__device__ __forceinline__ double block_max_d(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0) {
-    int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
-  }
-  __syncthreads();
-  return t;
-}
-
 // ------------------------------------------------------------------------------------------
 // Row kernel: R grid rows (lines along x) per block.
 //   phase 1 (per voxel): eps = (1/N) sum_j w_j Re(T_j exp(+2 pi i kx_j x / Nx)), law, tau
@@ -379,15 +296,64 @@ __device__ __forceinline__ void gamma6(const float4& n, const float* t, float in
   o[5] = (n.x * v1 + n.y * v0) * inv2mu0 - cg * n.x * n.y * nvn;
 }
 
+// convergence decision from the block partials, in a fixed summation order (one block)
+__device__ void decide(const double* part, int n, Status* st, double* sh) {
+  if (threadIdx.x >= 32) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) s += __ldcg(part + i);
+  sh[threadIdx.x] = s;
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < 32; ++i) tot += sh[i];
+    double r = sqrt(tot * st->inv_n2);
+    if (st->enorm > 0.0) r /= st->enorm;
+    st->iters += 1;
+    st->last_r = r;
+    if (!isfinite(r)) {
+      st->nonfinite = 1;
+      st->done = 1;
+    } else if (r < st->tol || st->iters >= st->max_iter) {
+      st->done = 1;
+    }
+  }
+}
+
 template <int NC>
 __global__ __launch_bounds__(256) void k_gamma(GammaArgs a, double Nd) {
-  if (a.done && *a.done) return;
   __shared__ double red[8];
+  __shared__ double sh[256];
+  __shared__ bool last;
   const long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double diff = 0.0;
-  if (h < a.Kh) {
-    const HIdx hi = a.hidx[h];
+  const bool act = h < a.Kh;
+  // independent loads first (flag, indices, wave vector), so that they overlap
+  const int dn = a.done ? __ldcg(a.done) : 0;
+  HIdx hi{0, 0, 0, 2};
+  float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (act) {
+    hi = a.hidx[h];
+    n = a.hn[h];
+  }
+  if (dn) return;
+  float diff = 0.f;
+  if (act) {
     const long long base = ((long long)(hi.iz * a.Ky + hi.iy) * NC) * a.Kx + hi.j;
+    const float2* __restrict__ out = a.OUT + base;
+    float2* __restrict__ er_p = a.ER + base;
+    float2 tv[NC], old[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      tv[c] = out[c * a.Kx];
+      old[c] = er_p[c * a.Kx];
+    }
+    for (int s = 1; s < a.splits; ++s) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float2 u = out[s * a.split_stride + c * a.Kx];
+        tv[c].x += u.x;
+        tv[c].y += u.y;
+      }
+    }
     float er[NC], ei[NC];
     if (hi.kind == 1) {
 #pragma unroll
@@ -402,18 +368,10 @@ __global__ __launch_bounds__(256) void k_gamma(GammaArgs a, double Nd) {
       float tr[NC], ti[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        float2 v = make_float2(0.f, 0.f);
-        const float2* p = a.OUT + base + c * a.Kx;
-        for (int s = 0; s < a.splits; ++s) {
-          float2 u = p[s * a.split_stride];
-          v.x += u.x;
-          v.y += u.y;
-        }
-        tr[c] = v.x;
-        ti[c] = v.y;
+        tr[c] = tv[c].x;
+        ti[c] = tv[c].y;
       }
       float t6[6], o6[6];
-      const float4 n = a.hn[h];
       comp_to6<NC>(tr, t6);
       gamma6(n, t6, a.inv2mu0, a.cgam, o6);
 #pragma unroll
@@ -423,44 +381,36 @@ __global__ __launch_bounds__(256) void k_gamma(GammaArgs a, double Nd) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
     }
-    const float mult = a.hn[h].w;
+    const float mult = n.w;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      float2* p = a.ER + base + c * a.Kx;
-      const float2 old = *p;
-      const double dr = (double)er[c] - (double)old.x, di = (double)ei[c] - (double)old.y;
-      const double wc = (comp6<NC>(c) >= 3) ? 2.0 : 1.0;   // Frobenius: shear counted twice
-      diff += (double)mult * wc * (dr * dr + di * di);
-      *p = make_float2(er[c], ei[c]);
+      const float dr = er[c] - old[c].x, di = ei[c] - old[c].y;
+      const float wc = (comp6<NC>(c) >= 3) ? 2.f : 1.f;   // Frobenius: shear counted twice
+      diff = fmaf(mult * wc, dr * dr + di * di, diff);
+      er_p[c * a.Kx] = make_float2(er[c], ei[c]);
     }
   }
-  const double t = block_sum_d(diff, red);
-  if (threadIdx.x == 0) a.part[blockIdx.x] = t;
-}
-
-// convergence measure r = sqrt(sum / N^2) / |ebar| (Parseval), decision on the device
-__global__ __launch_bounds__(256) void k_finalize(const double* part, int n, Status* st) {
-  if (st->done) return;
-  __shared__ double sh[256];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) s += part[i];
-  sh[threadIdx.x] = s;
+  // one frequency's squared increment in FP32 (a sum of at most six non-negative terms); the
+  // sums over warps and blocks are FP64
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)diff;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  // the last block to finish reduces all partials and takes the convergence decision
   if (threadIdx.x == 0) {
-    double r = sqrt(sh[0] * st->inv_n2);
-    if (st->enorm > 0.0) r /= st->enorm;
-    st->iters += 1;
-    st->last_r = r;
-    if (!isfinite(r)) {
-      st->nonfinite = 1;
-      st->done = 1;
-    } else if (r < st->tol || st->iters >= st->max_iter) {
-      st->done = 1;
-    }
+    a.part[blockIdx.x] = t;
+    __threadfence();
+    const unsigned prev = atomicAdd(a.counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    decide(a.part, gridDim.x, a.status, sh);
+    if (threadIdx.x == 0) *a.counter = 0u;
   }
 }
 
@@ -629,14 +579,20 @@ static RowArgs row_args(rf_ctx* c, const int* done) {
   return a;
 }
 
+void init_attributes_kernels() {
+  const int s = 200 * 1024;
+  cudaFuncSetAttribute(k_row<3, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_row<3, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_row<3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_row<3, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_row<6, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_row<6, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_row<6, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_row<6, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+}
+
 template <int NC, bool PL, bool FIN>
 static int row_launch(rf_ctx* c, const RowArgs& a) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_row<NC, PL, FIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr_set = true;
-  }
   k_row<NC, PL, FIN><<<c->row_blocks, 256, c->row_smem, c->stream>>>(a);
   return launch_check(c, "row");
 }
@@ -650,6 +606,8 @@ static int row_dispatch(rf_ctx* c, const RowArgs& a, bool final_pass) {
   if (final_pass) return pl ? row_launch<6, true, true>(c, a) : row_launch<6, false, true>(c, a);
   return pl ? row_launch<6, true, false>(c, a) : row_launch<6, false, false>(c, a);
 }
+
+int launch_gamma_finalize(rf_ctx* c, int splits, const int* done);
 
 static int inverse_stages(rf_ctx* c, const int* done) {
   const int NCK = c->nc * c->Kx;
@@ -672,6 +630,14 @@ static int inverse_stages(rf_ctx* c, const int* done) {
 int launch_iteration(rf_ctx* c) {
   const int* done = &c->d_status->done;
   trace_begin(c, c->launched_iters++);
+  const bool fftm = c->opt.transform == RF_TRANSFORM_FFT;
+  if (fftm) {
+    if (int e = fft_inverse_stages(c, done)) return e;
+    trace_stage(c, 2);
+    if (int e = launch_fft_row(c, done, false, 0)) return e;
+    if (int e = fft_forward_stages(c, done)) return e;
+    return launch_gamma_finalize(c, 1, done);
+  }
   if (int e = inverse_stages(c, done)) return e;
   const bool tcm = c->opt.precision != RF_PREC_FP32;
   trace_stage(c, 2);
@@ -702,10 +668,14 @@ int launch_iteration(rf_ctx* c) {
                     c->ny, 1, c->d_kym, nullptr, c->d_twy, c->ny, -1, done))
       return e;
   }
+  return launch_gamma_finalize(c, (c->dim == 3) ? c->splitC : c->splitB, done);
+}
+
+int launch_gamma_finalize(rf_ctx* c, int splits, const int* done) {
   GammaArgs g{};
   g.OUT = c->d_OUT;
-  g.splits = (c->dim == 3) ? c->splitC : c->splitB;
-  g.split_stride = outstride;
+  g.splits = splits;
+  g.split_stride = c->rect;
   g.ER = c->d_ER;
   g.hidx = c->d_hidx;
   g.hn = c->d_hn;
@@ -716,16 +686,15 @@ int launch_iteration(rf_ctx* c) {
   g.inv2mu0 = (float)(0.5 / c->mu0);
   g.cgam = (float)((c->lam0 + c->mu0) / (c->mu0 * (c->lam0 + 2.0 * c->mu0)));
   g.st = c->d_status;
+  g.status = c->d_status;
+  g.counter = c->d_counter;
   g.part = c->d_part;
   g.done = done;
   const unsigned gb = (unsigned)((c->Kh + 255) / 256);
   trace_stage(c, 5);
   if (c->nc == 3) k_gamma<3><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
   else k_gamma<6><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
-  if (int e = launch_check(c, "gamma")) return e;
-  trace_stage(c, 6);
-  k_finalize<<<1, 256, 0, c->stream>>>(c->d_part, (int)gb, c->d_status);
-  int e = launch_check(c, "finalize");
+  int e = launch_check(c, "gamma");
   trace_end(c);
   return e;
 }
@@ -735,6 +704,17 @@ int launch_final(rf_ctx* c, int commit) {
   trace_stage(c, 7);
   const bool tr = c->tracing;
   c->tracing = false;   // the whole final pass is one stage
+  if (c->opt.transform == RF_TRANSFORM_FFT) {
+    int ie = fft_inverse_stages(c, nullptr);
+    if (!ie) ie = launch_fft_row(c, nullptr, true, commit);
+    c->tracing = tr;
+    if (ie) return ie;
+    k_reduce_sbar<<<1, 256, 0, c->stream>>>(c->d_sbar_part, c->d_viol_part, c->fft_blocks,
+                                            1.0 / (double)c->N, c->d_sbar);
+    int e = launch_check(c, "reduce_sbar");
+    trace_end(c);
+    return e;
+  }
   int ie = inverse_stages(c, nullptr);
   c->tracing = tr;
   if (ie) return ie;
@@ -798,10 +778,18 @@ static cudaEvent_t take_event(rf_ctx* c) {
   return e;
 }
 
+// While a graph is being captured the events become event-record nodes of the graph (they are
+// recorded on the device timeline at every replay) and belong to the graph.
+static void record_event(rf_ctx* c, cudaEvent_t e) {
+  if (c->capturing) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+  else cudaEventRecord(e, c->stream);
+}
+
 void trace_begin(rf_ctx* c, long long idx) {
   if (!c->tracing) return;
-  c->pending.push_back(rf_ctx::TraceIter{});
-  c->cur = &c->pending.back();
+  auto& list = c->capturing ? c->graph_traces : c->pending;
+  list.push_back(rf_ctx::TraceIter{});
+  c->cur = &list.back();
   c->cur->idx = idx;
   c->cur->n = 0;
 }
@@ -809,7 +797,7 @@ void trace_begin(rf_ctx* c, long long idx) {
 void trace_stage(rf_ctx* c, int stage) {
   if (!c->tracing || !c->cur || c->cur->n >= 8) return;
   cudaEvent_t e = take_event(c);
-  cudaEventRecord(e, c->stream);
+  record_event(c, e);
   c->cur->stage[c->cur->n] = stage;
   c->cur->ev[c->cur->n] = e;
   c->cur->n += 1;
@@ -818,9 +806,25 @@ void trace_stage(rf_ctx* c, int stage) {
 void trace_end(rf_ctx* c) {
   if (!c->tracing || !c->cur) return;
   cudaEvent_t e = take_event(c);
-  cudaEventRecord(e, c->stream);
+  record_event(c, e);
   c->cur->ev[c->cur->n] = e;
   c->cur = nullptr;
+}
+
+// after a replay of graph g (first update index `base`) and a stream synchronize
+void trace_collect_graph(rf_ctx* c, const rf_ctx::GraphEntry& g, long long base,
+                         long long real_iters) {
+  for (size_t i = 0; i < g.trace_first.size(); ++i) {
+    if (base + (long long)i >= real_iters) break;
+    const rf_ctx::TraceIter& t = c->graph_traces[g.trace_first[i]];
+    for (int s = 0; s < t.n; ++s) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.ev[s], t.ev[s + 1]) == cudaSuccess) {
+        c->stage_ms[t.stage[s]] += ms;
+        c->stage_n[t.stage[s]] += 1;
+      }
+    }
+  }
 }
 
 int trace_collect(rf_ctx* c, long long real_iters) {

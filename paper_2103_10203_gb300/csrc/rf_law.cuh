@@ -73,4 +73,88 @@ __device__ __forceinline__ void stress6(const float* e, const DevPhase& p, const
   o.s[5] = s[5];
 }
 
+// J2 state, component maps and deterministic block reductions
+template <int NC>
+__device__ __forceinline__ void load_state(const float* st, long long N, long long g, float* ep,
+                                           float& alpha) {
+  if (NC == 3) {
+    ep[0] = st[g];
+    ep[1] = st[N + g];
+    ep[5] = st[2 * N + g];
+    ep[2] = -(ep[0] + ep[1]);
+    ep[3] = ep[4] = 0.f;
+    alpha = st[3 * N + g];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ep[i] = st[i * N + g];
+    alpha = st[6 * N + g];
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void store_state(float* st, long long N, long long g, const float* ep,
+                                            float alpha) {
+  if (NC == 3) {
+    st[g] = ep[0];
+    st[N + g] = ep[1];
+    st[2 * N + g] = ep[5];
+    st[3 * N + g] = alpha;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) st[i * N + g] = ep[i];
+    st[6 * N + g] = alpha;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void comp_to6(const float* e, float* e6) {
+  if (NC == 3) {
+    e6[0] = e[0];
+    e6[1] = e[1];
+    e6[2] = 0.f;
+    e6[3] = 0.f;
+    e6[4] = 0.f;
+    e6[5] = e[2];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) e6[i] = e[i];
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ int comp6(int c) {
+  return NC == 3 ? (c == 2 ? 5 : c) : c;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  // deterministic: fixed shuffle tree inside warps, fixed order across warps
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t += red[i];
+  }
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t = fmax(t, red[i]);
+  }
+  __syncthreads();
+  return t;
+}
+
 }  // namespace rfk

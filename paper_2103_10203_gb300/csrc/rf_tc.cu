@@ -488,14 +488,21 @@ int tc_setup(rf_ctx* c) {
   return RF_OK;
 }
 
+void init_attributes_tc() {
+  using namespace tc;
+  const int s = 200 * 1024;
+  cudaFuncSetAttribute(k_tc_row<EBf16, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_row<EBf16, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_row<EBf16, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_row<EBf16, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_row<ETf32, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_row<ETf32, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_row<ETf32, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_row<ETf32, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+}
+
 template <class E, int NC, bool PL>
 static int tc_row_launch(rf_ctx* c, const tc::TcRowArgs& a) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tc::k_tc_row<E, NC, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr = true;
-  }
   dim3 grid(c->tc_nXS, (c->rows + c->tc_R - 1) / c->tc_R);
   tc::k_tc_row<E, NC, PL><<<grid, 128, c->tc_smem, c->stream>>>(a);
   c->launches += 1;

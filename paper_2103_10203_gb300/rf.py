@@ -20,6 +20,7 @@ ERRORS = {-1: "invalid argument", -2: "CUDA error", -3: "non-finite", -4: "diver
 GREEN = {"rotated": 0, "continuous": 1}
 REF = {"minmax": 0, "volume": 1}
 PRECISION = {"fp32": 0, "split_bf16": 1, "split_tf32": 2}
+TRANSFORM = {"dft": 0, "fft": 1}
 
 
 class rf_grid(C.Structure):
@@ -34,7 +35,7 @@ class rf_phase(C.Structure):
 class rf_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("green", C.c_int32),
                 ("ref_medium", C.c_int32), ("precision", C.c_int32), ("check_every", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("transform", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class rf_info(C.Structure):
@@ -134,11 +135,12 @@ def make_phases(table) -> C.Array:
 
 
 def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
-                 check_every=0) -> rf_options:
+                 check_every=0, transform="dft") -> rf_options:
     o = rf_options()
     o.tol, o.max_iter = float(tol), int(max_iter)
     o.green, o.ref_medium = GREEN[green], REF[ref]
     o.precision, o.check_every = PRECISION[precision], int(check_every)
+    o.transform = TRANSFORM[transform]
     return o
 
 

@@ -340,3 +340,110 @@ def test_split_precision_converges_and_load_path(lib, prec):
     for n in range(len(path)):
         assert rel(out["sigma_bar"][n], sbar_ref[n]) <= SPLIT_TOL
     assert rel(eps, vec6_field(r.eps)) <= SPLIT_TOL
+
+
+# ----------------------------------------------------------------------------- FFT transform
+def _pow2_case(name):
+    if name == "c1":
+        return _case("c1")
+    if name == "fullset":
+        return _case("fullset")
+    if name == "3d":
+        return _case("3d")
+    if name == "j2_64":
+        pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
+        return pm, j2_phases(), np.array([0.02, 0, 0, 0, 0, 0.003]), \
+            O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    if name == "rect":
+        pm = (np.random.default_rng(5).random((32, 128)) < 0.3).astype(np.uint8)
+        return pm, elastic_phases(), random_macro_strain(9, 2), O.pattern_adapted(pm, 1, 300)
+    if name == "3d_rect":
+        pm = (np.random.default_rng(6).random((8, 16, 32)) < 0.3).astype(np.uint8)
+        return pm, elastic_phases(), random_macro_strain(10, 3), O.pattern_adapted(pm, 1, 200)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["c1", "fullset", "3d", "j2_64", "rect", "3d_rect"])
+@pytest.mark.parametrize("scheme,ref", [("rotated", "minmax"), ("continuous", "volume")])
+def test_fft_transform_matches_oracle(lib, name, scheme, ref):
+    pm, ph, macro, pat = _pow2_case(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=6, green=scheme, ref=ref,
+                   transform="fft")
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    coeffs = s.rf_get_reduced_strain()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=6, scheme=scheme, ref=ref)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    want = np.stack([r.eps_hat[:, i, j] for (i, j) in VOIGT], axis=1)
+    assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
+
+
+def test_fft_transform_load_path_and_tolerance(lib):
+    pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
+    ph = j2_phases()
+    pat = O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    path = uniaxial_path(20, 0.02)[::4]
+    s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform="fft")
+    out = s.rf_solve_path(path)
+    eps, sig, alpha = s.rf_get_fields()
+    s.close()
+    assert out["converged"]
+    sbar_ref, _, r = O.solve_path(pm, ph, path, pat, fixed_iters=out["iters"])
+    for n in range(len(path)):
+        assert rel(out["sigma_bar"][n], sbar_ref[n]) <= SBAR_TOL, n
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(alpha, r.alpha[0]) <= 1e-4
+
+
+def test_fft_and_dft_transforms_agree(lib):
+    cfg = make_config("c2", n=256)
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    res = {}
+    for tr in ("dft", "fft"):
+        s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform=tr)
+        res[tr] = (s.rf_solve_path(uniaxial_path(20, 0.02)[::5]), s.rf_get_fields()[0])
+        s.close()
+    (a, ea), (b, eb) = res["dft"], res["fft"]
+    assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
+    assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
+    assert rel(eb, ea) <= 2e-5
+
+
+def test_fft_full_size_c2_first_iterations(lib):
+    cfg = make_config("c2")
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    macro = np.array([0.02, 0, 0, 0, 0, 0])
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft")
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=3)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
+def test_fft_full_size_c3_first_iterations(lib):
+    cfg = make_config("c3")
+    pm, ph, macro = cfg["phase_map"], cfg["phases"], cfg["macro"]
+    pat = lib.rf_pattern_adapted(pm, 1, cfg["k_target"])
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=2, transform="fft")
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=2)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
+def test_fft_transform_rejects_non_power_of_two(lib):
+    pm = np.zeros((24, 40), np.uint8)
+    with pytest.raises(lib.RFError):
+        lib.Solver(pm, elastic_phases(), transform="fft")
+    with pytest.raises(lib.RFError):
+        lib.Solver(np.zeros((32, 32), np.uint8), elastic_phases(), transform="fft",
+                   precision="split_bf16")
