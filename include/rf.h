@@ -232,6 +232,35 @@ int rf_pattern_adapted_noalloc(const rf_grid* grid, const uint8_t* phase_map,
 int rf_pattern_radial(const rf_grid* grid, int64_t k_target, int32_t* freqs_out, int64_t cap,
                       int64_t* K_out, void* stream);
 
+/* ---- Batched solve: many independent 2D RVEs (e.g. the Gauss points of an FE-FFT macro model,
+ * Sec. 1), each with its own grid (sides 2..1024, any size), phase map, adapted pattern and
+ * macroscopic strain, solved together on one GPU. Every update of all unconverged RVEs is a fixed
+ * sequence of persistent kernels walking (RVE, tile) work lists; RVEs leave the work as they
+ * converge. Elastic phases only, plane strain, FP32 pruned-DFT transforms (options.transform =
+ * RF_TRANSFORM_DFT, precision RF_PREC_FP32), FP64 convergence measure and homogenised stress.
+ * Same convergence measure and rules as rf_solve.
+ *  rf_batch_create: grids[n_rve]; phase_maps[n_rve] HOST uint8 pointers; phases shared by all
+ *  RVEs; patterns[n_rve] HOST int32 [K[r]][3] pointers (rules of rf_set_pattern, kz = 0); all
+ *  inputs are copied. Chooses rows per work item and the persistent grid size by timing a few
+ *  updates (autotuner). stream as in rf_create.
+ *  rf_batch_solve: macro [n_rve][6]; warm nullable, else warm[r] nullable HOST float
+ *  [K[r]][6][2] start coefficients (projected as in rf_solve); outputs (each nullable):
+ *  hom_stress [n_rve][6], iters [n_rve], residuals [n_rve], status [n_rve] (RF_OK,
+ *  RF_NOT_CONVERGED or RF_ERR_NONFINITE per RVE). Returns RF_OK when every RVE converged,
+ *  RF_NOT_CONVERGED otherwise, or a hard error.
+ *  rf_batch_info: kernels launched so far (graph replays included), chosen rows per row item,
+ *  persistent grid size. */
+typedef struct rf_batch rf_batch;
+int rf_batch_create(rf_batch** batch, int32_t n_rve, const rf_grid* grids,
+                    const uint8_t* const* phase_maps, int32_t n_phases, const rf_phase* phases,
+                    const int32_t* const* patterns, const int64_t* K, const rf_options* opt,
+                    void* stream);
+int rf_batch_solve(rf_batch* batch, const double* macro, const float* const* warm,
+                   double* hom_stress, int32_t* iters, double* residuals, int32_t* status);
+int rf_batch_info(const rf_batch* batch, int64_t* kernel_launches, int32_t* rows_per_item,
+                  int32_t* grid);
+int rf_batch_destroy(rf_batch* batch);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* rf_last_error(void);
 

@@ -1,0 +1,1062 @@
+// Batched solver: many independent 2D RVEs of uneven size (FE-FFT Gauss points), each with its
+// own phase map, adapted pattern and macroscopic strain, solved together.
+//
+// One update of every unconverged RVE is five persistent kernels, each walking a work list of
+// (RVE, tile) items in a fixed order (largest RVEs first) with a stride of the grid size:
+//   inverse y transform tiles, row tiles (x transforms + law), forward y transform tiles,
+//   Green-operator chunks (with squared-increment partials), per-RVE convergence decisions.
+// Items of converged RVEs return at once. Chunks of updates are captured as CUDA graphs and
+// replayed until every RVE has converged or hit its cap. Elastic phases, plane strain (NC = 3),
+// pruned DFT transforms in FP32; convergence measure and homogenised stress in FP64.
+// Row tiles and the persistent grid size are chosen per batch by a timing autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "rf_internal.cuh"
+#include "rf_law.cuh"
+
+namespace rfk {
+
+namespace {
+
+constexpr int NC = 3;
+
+struct BDesc {
+  int nx, ny, Kx, Ky;
+  int Kh, rows, R, row_items;
+  int mt_inv, nt, mt_fwd, chunks;
+  long long N;
+  long long off_phase;   // uint8
+  long long off_er;      // float2, Ky * NC * Kx
+  long long off_t1;      // float2, ny * NC * Kx (T1 and T1p use the same offsets)
+  long long off_h;       // hidx / hn
+  long long off_kx;      // int (kx values), float (fac)
+  long long off_ky;      // int (ky mod ny)
+  long long off_part;    // double, chunks
+  long long off_spart;   // double, row_items * 6
+  int tab_x, tab_y;      // offsets into the twiddle buffer
+  long long zero_base;   // ER offset (within the RVE) of the zero frequency
+  float lam0, mu0, inv2mu0, cgam;
+};
+
+struct BStat {
+  int done, iters, nonfinite, max_iter;
+  double tol, enorm, inv_n2, last_r;
+  double ebar[6];
+  double sbar[6];
+};
+
+struct BArgs {
+  const BDesc* d;
+  BStat* st;
+  const int2* items;
+  int n_items;
+  const uint8_t* phase;
+  float2* ER;
+  float2* T1;
+  float2* T1p;
+  float2* OUT;
+  const HIdx* hidx;
+  const float4* hn;
+  const int* kx;
+  const float* fac;
+  const int* kym;
+  const float2* tab;
+  double* part;
+  double* spart;
+  int* n_done;
+  LawParams law;
+  int final_pass;
+};
+
+__device__ __forceinline__ bool rve_done(const BArgs& a, int r) { return a.st[r].done != 0; }
+
+// out[m][n] = sum_k w(m, k) in[k][n] for one 32 x 64 tile (same tile body as the unbatched
+// transform kernel): inverse (sign +1): m = y, k over ky; forward (sign -1): m over ky, k = y
+__device__ void dft_tile(const float2* in, float2* out, int M, int N, int K, const int* mvals,
+                         const int* kvals, const float2* tab, int L, int sign, int m0, int n0,
+                         float2 (*xs)[64], float2 (*ws)[33]) {
+  constexpr int MT = 8;
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6, tid = threadIdx.x;
+  float accr[MT], acci[MT];
+#pragma unroll
+  for (int i = 0; i < MT; ++i) accr[i] = acci[i] = 0.f;
+  for (int kb = 0; kb < K; kb += 32) {
+    for (int i = tid; i < 32 * 64; i += 256) {
+      const int kk = i >> 6, nn = i & 63, k = kb + kk, n = n0 + nn;
+      xs[kk][nn] = (k < K && n < N) ? in[(long long)k * N + n] : make_float2(0.f, 0.f);
+    }
+    for (int i = tid; i < 32 * 32; i += 256) {
+      const int mm = i >> 5, kk = i & 31, m = m0 + mm, k = kb + kk;
+      float2 w = make_float2(0.f, 0.f);
+      if (m < M && k < K) {
+        const int mv = mvals ? mvals[m] : m;
+        const int kv = kvals ? kvals[k] : k;
+        w = tab[(int)(((long long)mv * kv) % L)];
+        if (sign < 0) w.y = -w.y;
+      }
+      ws[mm][kk] = w;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      const float2 x = xs[kk][tx];
+#pragma unroll
+      for (int i = 0; i < MT; ++i) {
+        const float2 w = ws[ty * MT + i][kk];
+        accr[i] = fmaf(w.x, x.x, fmaf(-w.y, x.y, accr[i]));
+        acci[i] = fmaf(w.x, x.y, fmaf(w.y, x.x, acci[i]));
+      }
+    }
+    __syncthreads();
+  }
+  const int n = n0 + tx;
+  if (n < N) {
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+      const int m = m0 + ty * MT + i;
+      if (m < M) out[(long long)m * N + n] = make_float2(accr[i], acci[i]);
+    }
+  }
+}
+
+__global__ __launch_bounds__(256) void kb_inv_y(BArgs a) {
+  __shared__ float2 xs[32][64];
+  __shared__ float2 ws[32][33];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int2 w = a.items[it];
+    if (!a.final_pass && rve_done(a, w.x)) continue;   // the final pass covers every RVE
+    const BDesc d = a.d[w.x];
+    const int mt = w.y / d.nt, nt = w.y % d.nt;
+    dft_tile(a.ER + d.off_er, a.T1 + d.off_t1, d.ny, NC * d.Kx, d.Ky, nullptr, a.kym + d.off_ky,
+             a.tab + d.tab_y, d.ny, +1, mt * 32, nt * 64, xs, ws);
+  }
+}
+
+__global__ __launch_bounds__(256) void kb_fwd_y(BArgs a) {
+  __shared__ float2 xs[32][64];
+  __shared__ float2 ws[32][33];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int2 w = a.items[it];
+    if (rve_done(a, w.x)) continue;
+    const BDesc d = a.d[w.x];
+    const int mt = w.y / d.nt, nt = w.y % d.nt;
+    dft_tile(a.T1p + d.off_t1, a.OUT + d.off_er, d.Ky, NC * d.Kx, d.ny, a.kym + d.off_ky,
+             nullptr, a.tab + d.tab_y, d.ny, -1, mt * 32, nt * 64, xs, ws);
+  }
+}
+
+// row tiles: R rows of one RVE; inverse x transform, law, forward x transform (FINAL: stress
+// partials instead of the forward transform)
+__global__ __launch_bounds__(256) void kb_row(BArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int2 w = a.items[it];
+    if (!a.final_pass && rve_done(a, w.x)) continue;
+    const BDesc d = a.d[w.x];
+    const int Nx = d.nx, Kx = d.Kx, R = d.R;
+    const int row0 = w.y * R;
+    const int nr = min(R, d.rows - row0);
+    float2* tab = reinterpret_cast<float2*>(smem);
+    float2* Ts = tab + Nx;
+    int* kxs = reinterpret_cast<int*>(Ts + R * NC * Kx);
+    float* fac = reinterpret_cast<float*>(kxs + Kx);
+    float* taus = fac + Kx;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < Nx; i += blockDim.x) tab[i] = a.tab[d.tab_x + i];
+    for (int i = tid; i < Kx; i += blockDim.x) {
+      kxs[i] = a.kx[d.off_kx + i];
+      fac[i] = a.fac[d.off_kx + i];
+    }
+    const float2* Tg = a.T1 + d.off_t1 + (long long)row0 * NC * Kx;
+    for (int i = tid; i < nr * NC * Kx; i += blockDim.x) Ts[i] = Tg[i];
+    __syncthreads();
+    double sb[6] = {0, 0, 0, 0, 0, 0};
+    for (int v = tid; v < nr * Nx; v += blockDim.x) {
+      const int r = v / Nx, x = v - r * Nx;
+      float e[NC] = {0.f, 0.f, 0.f};
+      const float2* Tr = Ts + r * NC * Kx;
+      for (int j = 0; j < Kx; ++j) {
+        const int m = (kxs[j] * x) % Nx;
+        const float2 tw = tab[m];
+        const float cr = fac[j] * tw.x, ci = fac[j] * tw.y;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float2 t = Tr[c * Kx + j];
+          e[c] = fmaf(t.x, cr, fmaf(-t.y, ci, e[c]));
+        }
+      }
+      float e6[6];
+      comp_to6<NC>(e, e6);
+      const long long g = (long long)(row0 + r) * Nx + x;
+      const DevPhase ph = a.law.ph[a.phase[d.off_phase + g]];
+      float ep[6] = {0, 0, 0, 0, 0, 0};
+      LawOut o;
+      stress6<false>(e6, ph, ep, 0.f, o);
+      if (a.final_pass) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
+      } else {
+        const float tr = e6[0] + e6[1] + e6[2];
+        float tau6[6];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (d.lam0 * tr + 2.f * d.mu0 * e6[i]);
+#pragma unroll
+        for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * d.mu0 * e6[i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) taus[(r * NC + c) * Nx + x] = tau6[comp6<NC>(c)];
+      }
+    }
+    if (a.final_pass) {
+      for (int i = 0; i < 6; ++i) {
+        const double t = block_sum_d(sb[i], red);
+        if (tid == 0) a.spart[d.off_spart + (long long)w.y * 6 + i] = t;
+      }
+      __syncthreads();
+      continue;
+    }
+    __syncthreads();
+    for (int u = tid; u < nr * Kx; u += blockDim.x) {
+      const int r = u / Kx, j = u - r * Kx;
+      const int kxj = kxs[j];
+      const float* tr_ = taus + r * NC * Nx;
+      float ar[NC] = {0.f, 0.f, 0.f}, ai[NC] = {0.f, 0.f, 0.f};
+      int m = 0;
+      for (int x = 0; x < Nx; ++x) {
+        const float2 tw = tab[m];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float t = tr_[c * Nx + x];
+          ar[c] = fmaf(t, tw.x, ar[c]);
+          ai[c] = fmaf(-t, tw.y, ai[c]);
+        }
+        m += kxj;
+        if (m >= Nx) m -= Nx;
+      }
+      float2* o = a.T1p + d.off_t1 + ((long long)(row0 + r) * NC) * Kx + j;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) o[c * Kx] = make_float2(ar[c], ai[c]);
+    }
+    __syncthreads();
+  }
+}
+
+// Green operator on chunks of 256 half-pattern frequencies, squared-increment partials
+__global__ __launch_bounds__(256) void kb_gamma(BArgs a) {
+  __shared__ double red[8];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int2 w = a.items[it];
+    if (rve_done(a, w.x)) continue;
+    const BDesc d = a.d[w.x];
+    const BStat& st = a.st[w.x];
+    const int h = w.y * 256 + threadIdx.x;
+    float diff = 0.f;
+    if (h < d.Kh) {
+      const HIdx hi = a.hidx[d.off_h + h];
+      const float4 n = a.hn[d.off_h + h];
+      const long long base = ((long long)hi.iy * NC) * d.Kx + hi.j;
+      float2* erp = a.ER + d.off_er + base;
+      const float2* outp = a.OUT + d.off_er + base;
+      float2 tv[NC], old[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        tv[c] = outp[c * d.Kx];
+        old[c] = erp[c * d.Kx];
+      }
+      float er[NC], ei[NC];
+      if (hi.kind == 1) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          er[c] = (float)((double)d.N * st.ebar[comp6<NC>(c)]);
+          ei[c] = 0.f;
+        }
+      } else if (hi.kind == 2) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) er[c] = ei[c] = 0.f;
+      } else {
+        float tr[NC], ti[NC], t6[6], o6[6];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          tr[c] = tv[c].x;
+          ti[c] = tv[c].y;
+        }
+        comp_to6<NC>(tr, t6);
+        gamma6(n, t6, d.inv2mu0, d.cgam, o6);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) er[c] = -o6[comp6<NC>(c)];
+        comp_to6<NC>(ti, t6);
+        gamma6(n, t6, d.inv2mu0, d.cgam, o6);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float dr = er[c] - old[c].x, di = ei[c] - old[c].y;
+        const float wc = (comp6<NC>(c) >= 3) ? 2.f : 1.f;
+        diff = fmaf(n.w * wc, dr * dr + di * di, diff);
+        erp[c * d.Kx] = make_float2(er[c], ei[c]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)diff;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < 8; ++k) t += red[k];
+      a.part[d.off_part + w.y] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// one thread per RVE: convergence measure from its partials (fixed order), decision
+__global__ void kb_decide(BArgs a, int n_rve) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rve; r += gridDim.x * blockDim.x) {
+    BStat& st = a.st[r];
+    if (st.done) continue;
+    const BDesc d = a.d[r];
+    double s = 0.0;
+    for (int k = 0; k < d.chunks; ++k) s += a.part[d.off_part + k];
+    double rr = sqrt(s * st.inv_n2);
+    if (st.enorm > 0.0) rr /= st.enorm;
+    st.iters += 1;
+    st.last_r = rr;
+    if (!isfinite(rr)) {
+      st.nonfinite = 1;
+      st.done = 1;
+    } else if (rr < st.tol || st.iters >= st.max_iter) {
+      st.done = 1;
+    }
+    if (st.done) atomicAdd(a.n_done, 1);
+  }
+}
+
+// homogenised stress per RVE from the final pass partials
+__global__ void kb_sbar(BArgs a, int n_rve) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rve; r += gridDim.x * blockDim.x) {
+    const BDesc d = a.d[r];
+    for (int i = 0; i < 6; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < d.row_items; ++k) s += a.spart[d.off_spart + (long long)k * 6 + i];
+      a.st[r].sbar[i] = s / (double)d.N;
+    }
+  }
+}
+
+// starting coefficients: zero except the zero frequency N ebar, or projected warm starts
+__global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long* warm_off) {
+  const int r = blockIdx.x;
+  if (r >= n_rve) return;
+  const BDesc d = a.d[r];
+  const BStat& st = a.st[r];
+  float2* er = a.ER + d.off_er;
+  const long long rect = (long long)d.Ky * NC * d.Kx;
+  for (long long i = threadIdx.x; i < rect; i += blockDim.x) er[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  if (warm && warm_off[r] >= 0) {
+    const float2* w6 = warm + warm_off[r];
+    const float lam0 = d.lam0, mu0 = d.mu0;
+    for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
+      const HIdx hi = a.hidx[d.off_h + h];
+      const float4 n = a.hn[d.off_h + h];
+      float outr[6] = {0, 0, 0, 0, 0, 0}, outi[6] = {0, 0, 0, 0, 0, 0};
+      if (hi.kind == 0) {
+        float e_r[6], e_i[6];
+        for (int i = 0; i < 6; ++i) {
+          e_r[i] = w6[h * 6 + i].x;
+          e_i[i] = w6[h * 6 + i].y;
+        }
+        e_r[2] = e_r[3] = e_r[4] = e_i[2] = e_i[3] = e_i[4] = 0.f;
+        float sr[6], si[6];
+        const float trr = e_r[0] + e_r[1], tri = e_i[0] + e_i[1];
+        for (int i = 0; i < 6; ++i) {
+          sr[i] = 2.f * mu0 * e_r[i] + (i < 3 ? lam0 * trr : 0.f);
+          si[i] = 2.f * mu0 * e_i[i] + (i < 3 ? lam0 * tri : 0.f);
+        }
+        gamma6(n, sr, d.inv2mu0, d.cgam, outr);
+        gamma6(n, si, d.inv2mu0, d.cgam, outi);
+      }
+      if (hi.kind != 1) {
+        const long long base = ((long long)hi.iy * NC) * d.Kx + hi.j;
+        for (int c = 0; c < NC; ++c)
+          er[base + (long long)c * d.Kx] = make_float2(outr[comp6<NC>(c)], outi[comp6<NC>(c)]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < NC) {
+    const int c = threadIdx.x;
+    er[d.zero_base + (long long)c * d.Kx] =
+        make_float2((float)((double)d.N * st.ebar[comp6<NC>(c)]), 0.f);
+  }
+}
+
+}  // namespace
+
+}  // namespace rfk
+
+// ------------------------------------------------------------------------------------------
+// host side
+struct rf_batch {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int n = 0;
+  rf_options opt{};
+  rfk::LawParams law{};
+  std::vector<rfk::BDesc> desc;
+  std::vector<std::vector<int32_t>> patterns;  // as given
+  std::vector<std::vector<long long>> h_src;   // per RVE: half index -> pattern entry
+  rfk::BDesc* d_desc = nullptr;
+  rfk::BStat* d_stat = nullptr;
+  rfk::BStat* h_stat = nullptr;   // pinned
+  uint8_t* d_phase = nullptr;
+  float2 *d_ER = nullptr, *d_T1 = nullptr, *d_T1p = nullptr, *d_OUT = nullptr;
+  rfk::HIdx* d_hidx = nullptr;
+  float4* d_hn = nullptr;
+  int* d_kx = nullptr;
+  float* d_fac = nullptr;
+  int* d_kym = nullptr;
+  float2* d_tab = nullptr;
+  double *d_part = nullptr, *d_spart = nullptr;
+  int* d_ndone = nullptr;
+  int* h_ndone = nullptr;   // pinned
+  int2* d_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int n_items[5] = {0, 0, 0, 0, 0};
+  float2* d_warm = nullptr;
+  long long* d_warm_off = nullptr;
+  long long warm_total = 0;
+  int grid = 0;
+  size_t row_smem = 0;
+  int R_choice[5] = {0, 0, 0, 0, 0};   // rows per row item, per size class (autotuned)
+  std::vector<std::pair<int, cudaGraphExec_t>> graphs;
+  long long launches = 0;
+  int last_max_iters = 0;
+};
+
+using namespace rfk;
+
+namespace {
+
+int bfail(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+template <class T>
+int balloc(T** p, size_t n, const char* what) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+  return e == cudaSuccess ? RF_OK : bfail(e, what);
+}
+
+BArgs batch_args(rf_batch* b, int stage) {
+  BArgs a{};
+  a.d = b->d_desc;
+  a.st = b->d_stat;
+  a.items = stage >= 0 ? b->d_items[stage] : nullptr;
+  a.n_items = stage >= 0 ? b->n_items[stage] : 0;
+  a.phase = b->d_phase;
+  a.ER = b->d_ER;
+  a.T1 = b->d_T1;
+  a.T1p = b->d_T1p;
+  a.OUT = b->d_OUT;
+  a.hidx = b->d_hidx;
+  a.hn = b->d_hn;
+  a.kx = b->d_kx;
+  a.fac = b->d_fac;
+  a.kym = b->d_kym;
+  a.tab = b->d_tab;
+  a.part = b->d_part;
+  a.spart = b->d_spart;
+  a.n_done = b->d_ndone;
+  a.law = b->law;
+  return a;
+}
+
+int launch_update(rf_batch* b) {
+  const int G = b->grid;
+  kb_inv_y<<<G, 256, 0, b->stream>>>(batch_args(b, 0));
+  kb_row<<<G, 256, b->row_smem, b->stream>>>(batch_args(b, 1));
+  kb_fwd_y<<<G, 256, 0, b->stream>>>(batch_args(b, 2));
+  kb_gamma<<<G, 256, 0, b->stream>>>(batch_args(b, 3));
+  kb_decide<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
+  b->launches += 5;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : bfail(e, "batch update");
+}
+
+int size_class(int side) {
+  static const int sides[5] = {64, 96, 128, 192, 256};
+  for (int i = 0; i < 5; ++i)
+    if (side <= sides[i]) return i;
+  return 4;
+}
+
+// row items for a given rows-per-item choice per size class; sets desc R / row_items
+int build_row_items(rf_batch* b) {
+  std::vector<int2> items;
+  std::vector<int> order(b->n);
+  for (int i = 0; i < b->n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->desc[x].N > b->desc[y].N; });
+  size_t smem = 0;
+  long long spart = 0;
+  for (int r : order) {
+    BDesc& d = b->desc[r];
+    d.R = std::max(1, std::min(b->R_choice[size_class(std::max(d.nx, d.ny))], d.rows));
+    d.row_items = (d.rows + d.R - 1) / d.R;
+    for (int k = 0; k < d.row_items; ++k) items.push_back(make_int2(r, k));
+    const size_t s = (size_t)d.nx * sizeof(float2) + (size_t)d.R * NC * d.Kx * sizeof(float2) +
+                     (size_t)d.Kx * 8 + (size_t)d.R * NC * d.nx * sizeof(float) + 64;
+    smem = std::max(smem, s);
+  }
+  for (int r = 0; r < b->n; ++r) {
+    b->desc[r].off_spart = spart;
+    spart += (long long)b->desc[r].row_items * 6;
+  }
+  if (b->d_items[1]) cudaFree(b->d_items[1]);
+  if (b->d_spart) cudaFree(b->d_spart);
+  if (int e = balloc(&b->d_items[1], items.size(), "batch items")) return e;
+  if (int e = balloc(&b->d_spart, (size_t)spart, "batch partials")) return e;
+  b->n_items[1] = (int)items.size();
+  if (smem > 200 * 1024) {
+    set_error("batch: row tile too large for shared memory");
+    return RF_ERR_INVALID;
+  }
+  b->row_smem = smem;
+  cudaError_t e = cudaMemcpy(b->d_items[1], items.data(), sizeof(int2) * items.size(),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_desc, b->desc.data(), sizeof(BDesc) * b->n, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? RF_OK : bfail(e, "batch upload");
+}
+
+void free_graphs(rf_batch* b) {
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
+  b->graphs.clear();
+}
+
+int graph_for(rf_batch* b, int chunk, cudaGraphExec_t* out) {
+  for (auto& g : b->graphs)
+    if (g.first == chunk) {
+      *out = g.second;
+      return RF_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfail(e, "batch capture");
+  int err = RF_OK;
+  const long long launched = b->launches;   // captured kernels are counted at each replay
+  for (int i = 0; i < chunk && !err; ++i) err = launch_update(b);
+  b->launches = launched;
+  e = cudaStreamEndCapture(b->stream, &graph);
+  if (!err && e != cudaSuccess) err = bfail(e, "batch end capture");
+  cudaGraphExec_t ex = nullptr;
+  if (!err) {
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    if (e != cudaSuccess) err = bfail(e, "batch instantiate");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (err) return err;
+  b->graphs.push_back({chunk, ex});
+  *out = ex;
+  return RF_OK;
+}
+
+int set_status(rf_batch* b, const double* macro) {
+  for (int r = 0; r < b->n; ++r) {
+    BStat& s = b->h_stat[r];
+    std::memset(&s, 0, sizeof(s));
+    s.max_iter = b->opt.max_iter;
+    s.tol = b->opt.tol;
+    const double* m = macro + 6 * r;
+    for (int i = 0; i < 6; ++i) s.ebar[i] = m[i];
+    s.enorm = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] +
+                        2.0 * (m[3] * m[3] + m[4] * m[4] + m[5] * m[5]));
+    const double N = (double)b->desc[r].N;
+    s.inv_n2 = 1.0 / (N * N);
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_stat, b->h_stat, sizeof(BStat) * b->n,
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ndone, 0, sizeof(int), b->stream);
+  return e == cudaSuccess ? RF_OK : bfail(e, "batch status");
+}
+
+// iterate until every RVE is done; returns the number of chunks
+int iterate(rf_batch* b) {
+  const int maxchunk = b->opt.check_every > 0 ? b->opt.check_every : 16;
+  int chunk = std::min(4, maxchunk);
+  for (;;) {
+    cudaGraphExec_t ex;
+    if (int e = graph_for(b, chunk, &ex)) return e;
+    cudaError_t e = cudaGraphLaunch(ex, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->h_ndone, b->d_ndone, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(e, "batch iterate");
+    b->launches += 5LL * chunk;
+    if (*b->h_ndone >= b->n) break;
+    chunk = std::min(chunk * 2, maxchunk);
+  }
+  return RF_OK;
+}
+
+int run_solve(rf_batch* b, const double* macro, bool use_warm) {
+  if (int e = set_status(b, macro)) return e;
+  BArgs a = batch_args(b, -1);
+  kb_init<<<b->n, 256, 0, b->stream>>>(a, b->n, use_warm ? b->d_warm : nullptr, b->d_warm_off);
+  b->launches += 1;
+  if (cudaGetLastError() != cudaSuccess) return bfail(cudaGetLastError(), "batch init");
+  return iterate(b);
+}
+
+// autotuner: rows per row item per size class (and the persistent grid), timed on updates
+int autotune(rf_batch* b, const double* macro) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
+  const int Rc[4] = {1, 2, 4, 8};
+  const int Gc[3] = {2, 4, 8};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bestR = 2, bestG = 4;
+  for (int ri = 0; ri < 4; ++ri) {
+    for (int k = 0; k < 5; ++k) b->R_choice[k] = Rc[ri];
+    if (int e = build_row_items(b)) return e;
+    for (int gi = 0; gi < 3; ++gi) {
+      b->grid = sms * Gc[gi];
+      if (int e = set_status(b, macro)) return e;
+      kb_init<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, nullptr, b->d_warm_off);
+      if (int e = launch_update(b)) return e;   // warm-up
+      cudaEventRecord(e0, b->stream);
+      for (int i = 0; i < 3; ++i)
+        if (int e = launch_update(b)) return e;
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bestR = Rc[ri];
+        bestG = Gc[gi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int k = 0; k < 5; ++k) b->R_choice[k] = bestR;
+  b->grid = sms * bestG;
+  return build_row_items(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
+                    const uint8_t* const* phase_maps, int32_t n_phases, const rf_phase* phases,
+                    const int32_t* const* patterns, const int64_t* K, const rf_options* opt,
+                    void* stream) {
+  set_error("");
+  if (!out || n_rve < 1 || !grids || !phase_maps || !phases || !patterns || !K || !opt) {
+    set_error("rf_batch_create: invalid arguments");
+    return RF_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (n_phases < 1 || n_phases > kMaxPhases) {
+    set_error("rf_batch_create: n_phases must be in [1, 16]");
+    return RF_ERR_INVALID;
+  }
+  for (int p = 0; p < n_phases; ++p)
+    if (phases[p].plastic || !(phases[p].mu > 0.0) ||
+        !(phases[p].lambda + 2.0 * phases[p].mu / 3.0 > 0.0)) {
+      set_error("rf_batch_create: elastic phases with mu > 0, lambda + 2 mu / 3 > 0 only");
+      return RF_ERR_INVALID;
+    }
+  if (opt->transform != RF_TRANSFORM_DFT || opt->precision != RF_PREC_FP32 || opt->max_iter < 1 ||
+      !(opt->tol >= 0.0) || (opt->green != 0 && opt->green != 1)) {
+    set_error("rf_batch_create: options must select FP32 DFT transforms");
+    return RF_ERR_INVALID;
+  }
+  rf_batch* b = new rf_batch();
+  cudaGetDevice(&b->dev);
+  b->n = n_rve;
+  b->opt = *opt;
+  b->stream = static_cast<cudaStream_t>(stream);
+  if (!b->stream) {
+    cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = true;
+  }
+  for (int p = 0; p < n_phases; ++p) {
+    b->law.ph[p].lam = (float)phases[p].lambda;
+    b->law.ph[p].mu = (float)phases[p].mu;
+  }
+  // per-RVE pattern bookkeeping (same rules as rf_set_pattern)
+  std::vector<uint8_t> all_phase;
+  std::vector<int> kx_all, kym_all;
+  std::vector<float> fac_all;
+  std::vector<HIdx> hidx_all;
+  std::vector<int> hk_all;        // kx, ky, kz, mult per half entry
+  std::vector<int> tab_sizes;     // distinct sizes
+  std::map<int, int> tab_off;
+  long long off_er = 0, off_t1 = 0, off_h = 0, off_kx = 0, off_ky = 0, off_part = 0;
+  b->desc.resize(n_rve);
+  b->h_src.resize(n_rve);
+  auto fail = [&](const char* msg) {
+    set_error(msg);
+    rf_batch_destroy(b);
+    return RF_ERR_INVALID;
+  };
+  for (int r = 0; r < n_rve; ++r) {
+    const rf_grid& g = grids[r];
+    if (g.dim != 2 || g.n[2] != 1 || g.n[0] < 2 || g.n[1] < 2 || g.n[0] > 1024 || g.n[1] > 1024)
+      return fail("rf_batch_create: 2D grids with sides in [2, 1024] only");
+    const int nx = g.n[0], ny = g.n[1];
+    const long long N = (long long)nx * ny;
+    BDesc& d = b->desc[r];
+    std::memset(&d, 0, sizeof(d));
+    d.nx = nx;
+    d.ny = ny;
+    d.N = N;
+    d.rows = ny;
+    d.off_phase = (long long)all_phase.size();
+    unsigned long long present = 0;
+    for (long long i = 0; i < N; ++i) {
+      const uint8_t v = phase_maps[r][i];
+      if (v >= n_phases) return fail("rf_batch_create: phase id >= n_phases");
+      present |= 1ull << v;
+      all_phase.push_back(v);
+    }
+    double lmin = 1e300, lmax = -1e300, mmin = 1e300, mmax = -1e300;
+    for (int p = 0; p < n_phases; ++p)
+      if (present & (1ull << p)) {
+        lmin = std::min(lmin, phases[p].lambda);
+        lmax = std::max(lmax, phases[p].lambda);
+        mmin = std::min(mmin, phases[p].mu);
+        mmax = std::max(mmax, phases[p].mu);
+      }
+    double lam0 = 0.5 * (lmin + lmax), mu0 = 0.5 * (mmin + mmax);
+    if (opt->ref_medium == RF_REF_VOLUME) {
+      double ls = 0, ms = 0;
+      for (long long i = 0; i < N; ++i) {
+        ls += phases[phase_maps[r][i]].lambda;
+        ms += phases[phase_maps[r][i]].mu;
+      }
+      lam0 = ls / N;
+      mu0 = ms / N;
+    }
+    d.lam0 = (float)lam0;
+    d.mu0 = (float)mu0;
+    d.inv2mu0 = (float)(0.5 / mu0);
+    d.cgam = (float)((lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0)));
+    // pattern
+    const long long Kr = K[r];
+    if (Kr < 1 || Kr > N) return fail("rf_batch_create: K must be in [1, N]");
+    std::map<std::tuple<int, int>, long long> index;
+    int zeros = 0;
+    for (long long p = 0; p < Kr; ++p) {
+      const int kx = patterns[r][3 * p], ky = patterns[r][3 * p + 1], kz = patterns[r][3 * p + 2];
+      if (kz != 0 || kx < -((nx - 1) / 2) || kx > nx / 2 || ky < -((ny - 1) / 2) || ky > ny / 2)
+        return fail("rf_batch_create: frequency outside the signed range");
+      if (!index.emplace(std::make_tuple(kx, ky), p).second)
+        return fail("rf_batch_create: duplicate frequency");
+      if (kx == 0 && ky == 0) ++zeros;
+    }
+    if (zeros != 1) return fail("rf_batch_create: the zero frequency must be present");
+    auto sgn = [](int i, int n) { return i <= n / 2 ? i : i - n; };
+    auto wrp = [](int k, int n) { return ((k % n) + n) % n; };
+    for (auto& kv : index) {
+      auto [kx, ky] = kv.first;
+      if (!index.count(std::make_tuple(sgn(wrp(-kx, nx), nx), sgn(wrp(-ky, ny), ny))))
+        return fail("rf_batch_create: pattern is not closed under k -> -k");
+    }
+    std::vector<std::tuple<int, int>> H;
+    for (auto& kv : index)
+      if (std::get<0>(kv.first) >= 0) H.push_back(kv.first);
+    std::sort(H.begin(), H.end());
+    std::vector<int> xs, ys;
+    for (auto& t : H) {
+      xs.push_back(std::get<0>(t));
+      ys.push_back(std::get<1>(t));
+    }
+    std::sort(xs.begin(), xs.end());
+    xs.erase(std::unique(xs.begin(), xs.end()), xs.end());
+    std::sort(ys.begin(), ys.end());
+    ys.erase(std::unique(ys.begin(), ys.end()), ys.end());
+    d.Kx = (int)xs.size();
+    d.Ky = (int)ys.size();
+    d.Kh = (int)H.size();
+    auto pos = [](const std::vector<int>& v, int x) {
+      return (int)(std::lower_bound(v.begin(), v.end(), x) - v.begin());
+    };
+    d.off_er = off_er;
+    d.off_t1 = off_t1;
+    d.off_h = off_h;
+    d.off_kx = off_kx;
+    d.off_ky = off_ky;
+    d.off_part = off_part;
+    d.chunks = (d.Kh + 255) / 256;
+    d.nt = (NC * d.Kx + 63) / 64;
+    d.mt_inv = (ny + 31) / 32;
+    d.mt_fwd = (d.Ky + 31) / 32;
+    d.zero_base = ((long long)pos(ys, 0) * NC) * d.Kx + pos(xs, 0);
+    std::map<std::tuple<int, int>, long long> hpos;
+    b->h_src[r].assign(d.Kh, 0);
+    for (int h = 0; h < d.Kh; ++h) {
+      auto [kx, ky] = H[h];
+      hpos[H[h]] = h;
+      const bool self = (kx == 0) || (nx % 2 == 0 && kx == nx / 2);
+      hidx_all.push_back(HIdx{pos(xs, kx), pos(ys, ky), 0, 0});
+      hk_all.insert(hk_all.end(), {kx, ky, 0, self ? 1 : 2});
+    }
+    for (long long p = 0; p < Kr; ++p) {
+      const int kx = patterns[r][3 * p], ky = patterns[r][3 * p + 1];
+      if (kx >= 0) b->h_src[r][hpos[std::make_tuple(kx, ky)]] = p;
+    }
+    for (int j = 0; j < d.Kx; ++j) {
+      kx_all.push_back(xs[j]);
+      const bool self = (xs[j] == 0) || (nx % 2 == 0 && xs[j] == nx / 2);
+      fac_all.push_back((float)((self ? 1.0 : 2.0) / (double)N));
+    }
+    for (int i = 0; i < d.Ky; ++i) kym_all.push_back(wrp(ys[i], ny));
+    for (int L : {nx, ny})
+      if (!tab_off.count(L)) {
+        tab_off[L] = 0;
+        tab_sizes.push_back(L);
+      }
+    off_er += (long long)d.Ky * NC * d.Kx;
+    off_t1 += (long long)ny * NC * d.Kx;
+    off_h += d.Kh;
+    off_kx += d.Kx;
+    off_ky += d.Ky;
+    off_part += d.chunks;
+    b->patterns.emplace_back(patterns[r], patterns[r] + 3 * Kr);
+  }
+  long long tab_total = 0;
+  for (int L : tab_sizes) {
+    tab_off[L] = (int)tab_total;
+    tab_total += L;
+  }
+  for (auto& d : b->desc) {
+    d.tab_x = tab_off[d.nx];
+    d.tab_y = tab_off[d.ny];
+  }
+  int err = RF_OK;
+  int* d_hk = nullptr;
+  if (!err) err = balloc(&b->d_desc, n_rve, "batch");
+  if (!err) err = balloc(&b->d_stat, n_rve, "batch");
+  if (!err) err = cudaMallocHost(&b->h_stat, sizeof(BStat) * n_rve) == cudaSuccess ? RF_OK : RF_ERR_OOM;
+  if (!err) err = cudaMallocHost(&b->h_ndone, sizeof(int)) == cudaSuccess ? RF_OK : RF_ERR_OOM;
+  if (!err) err = balloc(&b->d_phase, all_phase.size(), "batch phase maps");
+  if (!err) err = balloc(&b->d_ER, off_er, "batch coefficients");
+  if (!err) err = balloc(&b->d_OUT, off_er, "batch coefficients");
+  if (!err) err = balloc(&b->d_T1, off_t1, "batch line transforms");
+  if (!err) err = balloc(&b->d_T1p, off_t1, "batch line transforms");
+  if (!err) err = balloc(&b->d_hidx, off_h, "batch pattern");
+  if (!err) err = balloc(&b->d_hn, off_h, "batch pattern");
+  if (!err) err = balloc(&d_hk, hk_all.size(), "batch pattern");
+  if (!err) err = balloc(&b->d_kx, off_kx, "batch pattern");
+  if (!err) err = balloc(&b->d_fac, off_kx, "batch pattern");
+  if (!err) err = balloc(&b->d_kym, off_ky, "batch pattern");
+  if (!err) err = balloc(&b->d_tab, tab_total, "batch tables");
+  if (!err) err = balloc(&b->d_part, off_part, "batch partials");
+  if (!err) err = balloc(&b->d_ndone, 1, "batch");
+  if (!err) err = balloc(&b->d_warm_off, n_rve, "batch");
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (err) return;
+    cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) err = bfail(e, "batch upload");
+  };
+  up(b->d_phase, all_phase.data(), all_phase.size());
+  up(b->d_hidx, hidx_all.data(), sizeof(HIdx) * hidx_all.size());
+  up(d_hk, hk_all.data(), sizeof(int) * hk_all.size());
+  up(b->d_kx, kx_all.data(), sizeof(int) * kx_all.size());
+  up(b->d_fac, fac_all.data(), sizeof(float) * fac_all.size());
+  up(b->d_kym, kym_all.data(), sizeof(int) * kym_all.size());
+  if (!err) {
+    // twiddle tables and wave vectors via the single-RVE setup kernels
+    rf_ctx tmp;
+    tmp.stream = b->stream;
+    for (int L : tab_sizes) {
+      tmp.nx = tmp.ny = tmp.nz = L;
+      tmp.d_twx = tmp.d_twy = tmp.d_twz = b->d_tab + tab_off[L];
+      if (!err) err = launch_setup_tables(&tmp);
+    }
+    long long h0 = 0;
+    for (int r = 0; r < n_rve && !err; ++r) {
+      const BDesc& d = b->desc[r];
+      tmp.nx = d.nx;
+      tmp.ny = d.ny;
+      tmp.nz = 1;
+      tmp.opt.green = opt->green;
+      tmp.d_hidx = b->d_hidx + h0;
+      tmp.d_hn = b->d_hn + h0;
+      err = launch_hinfo(&tmp, d_hk + 4 * h0, d.Kh);
+      h0 += d.Kh;
+    }
+    b->launches += tmp.launches;
+    tmp.d_twx = tmp.d_twy = tmp.d_twz = nullptr;
+    tmp.d_hidx = nullptr;
+    tmp.d_hn = nullptr;
+    if (!err && cudaStreamSynchronize(b->stream) != cudaSuccess) err = RF_ERR_CUDA;
+  }
+  if (d_hk) cudaFree(d_hk);
+  // work lists for the transform, Green and (initial) row stages
+  if (!err) {
+    std::vector<int> order(n_rve);
+    for (int i = 0; i < n_rve; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->desc[x].N > b->desc[y].N; });
+    std::vector<int2> inv, fwd, gam;
+    for (int r : order) {
+      const BDesc& d = b->desc[r];
+      for (int k = 0; k < d.mt_inv * d.nt; ++k) inv.push_back(make_int2(r, k));
+      for (int k = 0; k < d.mt_fwd * d.nt; ++k) fwd.push_back(make_int2(r, k));
+      for (int k = 0; k < d.chunks; ++k) gam.push_back(make_int2(r, k));
+    }
+    std::vector<int2>* lists[5] = {&inv, nullptr, &fwd, &gam, nullptr};
+    for (int s : {0, 2, 3}) {
+      if (!err) err = balloc(&b->d_items[s], lists[s]->size(), "batch items");
+      up(b->d_items[s], lists[s]->data(), sizeof(int2) * lists[s]->size());
+      b->n_items[s] = (int)lists[s]->size();
+    }
+    std::vector<long long> none(n_rve, -1);
+    up(b->d_warm_off, none.data(), sizeof(long long) * n_rve);
+    cudaFuncSetAttribute(kb_row, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
+  if (!err) {
+    std::vector<double> macro0(6 * (size_t)n_rve, 0.0);
+    for (int r = 0; r < n_rve; ++r) macro0[6 * r] = 0.01;
+    err = autotune(b, macro0.data());
+  }
+  if (err) {
+    std::string keep = rf_last_error();
+    rf_batch_destroy(b);
+    set_error(keep);
+    return err;
+  }
+  *out = b;
+  return RF_OK;
+}
+
+int rf_batch_solve(rf_batch* b, const double* macro, const float* const* warm,
+                   double* hom_stress, int32_t* iters, double* residuals, int32_t* status) {
+  if (!b || !macro) {
+    set_error("rf_batch_solve: null argument");
+    return RF_ERR_INVALID;
+  }
+  for (int r = 0; r < b->n; ++r)
+    for (int i = 2; i < 5; ++i)
+      if (macro[6 * r + i] != 0.0) {
+        set_error("rf_batch_solve: plane strain needs macro components 33, 23, 13 = 0");
+        return RF_ERR_INVALID;
+      }
+  bool use_warm = false;
+  if (warm) {
+    std::vector<long long> off(b->n, -1);
+    long long total = 0;
+    for (int r = 0; r < b->n; ++r)
+      if (warm[r]) {
+        off[r] = total;
+        total += (long long)b->desc[r].Kh * 6;
+      }
+    if (total > b->warm_total) {
+      if (b->d_warm) cudaFree(b->d_warm);
+      if (int e = balloc(&b->d_warm, total, "batch warm")) return e;
+      b->warm_total = total;
+    }
+    std::vector<float2> w6((size_t)std::max(total, 1LL));
+    for (int r = 0; r < b->n; ++r) {
+      if (!warm[r]) continue;
+      for (int h = 0; h < b->desc[r].Kh; ++h) {
+        const long long p = b->h_src[r][h];
+        for (int i = 0; i < 6; ++i)
+          w6[off[r] + (long long)h * 6 + i] =
+              make_float2(warm[r][(p * 6 + i) * 2], warm[r][(p * 6 + i) * 2 + 1]);
+      }
+    }
+    cudaError_t e = cudaMemcpy(b->d_warm, w6.data(), sizeof(float2) * std::max(total, 1LL),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_warm_off, off.data(), sizeof(long long) * b->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(e, "batch warm upload");
+    use_warm = true;
+  }
+  if (int e = run_solve(b, macro, use_warm)) return e;
+  // final pass: fields of the converged coefficients -> homogenised stresses
+  BArgs a0 = batch_args(b, 0);
+  a0.final_pass = 1;
+  kb_inv_y<<<b->grid, 256, 0, b->stream>>>(a0);
+  BArgs a1 = batch_args(b, 1);
+  a1.final_pass = 1;
+  kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
+  kb_sbar<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
+  b->launches += 3;
+  cudaError_t e = cudaMemcpyAsync(b->h_stat, b->d_stat, sizeof(BStat) * b->n,
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(e, "batch final pass");
+  int code = RF_OK;
+  b->last_max_iters = 0;
+  for (int r = 0; r < b->n; ++r) {
+    const BStat& s = b->h_stat[r];
+    if (hom_stress)
+      for (int i = 0; i < 6; ++i) hom_stress[6 * r + i] = s.sbar[i];
+    if (iters) iters[r] = s.iters;
+    if (residuals) residuals[r] = s.last_r;
+    int st = s.nonfinite ? RF_ERR_NONFINITE : (s.last_r < b->opt.tol ? RF_OK : RF_NOT_CONVERGED);
+    if (status) status[r] = st;
+    if (st != RF_OK && code == RF_OK) code = RF_NOT_CONVERGED;
+    b->last_max_iters = std::max(b->last_max_iters, s.iters);
+  }
+  return code;
+}
+
+int rf_batch_info(const rf_batch* b, int64_t* kernel_launches, int32_t* rows_per_item,
+                  int32_t* grid) {
+  if (!b) {
+    set_error("rf_batch_info: null batch");
+    return RF_ERR_INVALID;
+  }
+  if (kernel_launches) *kernel_launches = b->launches;
+  if (rows_per_item) *rows_per_item = b->R_choice[0];
+  if (grid) *grid = b->grid;
+  return RF_OK;
+}
+
+int rf_batch_destroy(rf_batch* b) {
+  if (!b) return RF_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  free_graphs(b);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_stat);
+  cudaFree(b->d_phase);
+  cudaFree(b->d_ER);
+  cudaFree(b->d_T1);
+  cudaFree(b->d_T1p);
+  cudaFree(b->d_OUT);
+  cudaFree(b->d_hidx);
+  cudaFree(b->d_hn);
+  cudaFree(b->d_kx);
+  cudaFree(b->d_fac);
+  cudaFree(b->d_kym);
+  cudaFree(b->d_tab);
+  cudaFree(b->d_part);
+  cudaFree(b->d_spart);
+  cudaFree(b->d_ndone);
+  cudaFree(b->d_warm);
+  cudaFree(b->d_warm_off);
+  for (int s = 0; s < 5; ++s) cudaFree(b->d_items[s]);
+  if (b->h_stat) cudaFreeHost(b->h_stat);
+  if (b->h_ndone) cudaFreeHost(b->h_ndone);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return RF_OK;
+}
+
+}  // extern "C"

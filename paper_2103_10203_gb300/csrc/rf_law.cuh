@@ -157,4 +157,22 @@ __device__ __forceinline__ double block_max_d(double v, double* red) {
   return t;
 }
 
+// Green operator of the isotropic reference medium applied to a symmetric tensor (Sec. 3):
+//   (Gamma : t)_ij = (n_i (t n)_j + n_j (t n)_i) / (2 mu0) - c n_i n_j (n . t . n),
+//   c = (lam0 + mu0) / (mu0 (lam0 + 2 mu0)), n = q / |q|.
+__device__ __forceinline__ void gamma6(const float4& n, const float* t, float inv2mu0, float cg,
+                                       float* o) {
+  // t: (11, 22, 33, 23, 13, 12)
+  const float v0 = t[0] * n.x + t[5] * n.y + t[4] * n.z;
+  const float v1 = t[5] * n.x + t[1] * n.y + t[3] * n.z;
+  const float v2 = t[4] * n.x + t[3] * n.y + t[2] * n.z;
+  const float nvn = n.x * v0 + n.y * v1 + n.z * v2;
+  o[0] = 2.f * n.x * v0 * inv2mu0 - cg * n.x * n.x * nvn;
+  o[1] = 2.f * n.y * v1 * inv2mu0 - cg * n.y * n.y * nvn;
+  o[2] = 2.f * n.z * v2 * inv2mu0 - cg * n.z * n.z * nvn;
+  o[3] = (n.y * v2 + n.z * v1) * inv2mu0 - cg * n.y * n.z * nvn;
+  o[4] = (n.x * v2 + n.z * v0) * inv2mu0 - cg * n.x * n.z * nvn;
+  o[5] = (n.x * v1 + n.y * v0) * inv2mu0 - cg * n.x * n.y * nvn;
+}
+
 }  // namespace rfk

@@ -77,6 +77,11 @@ def _load() -> C.CDLL:
         "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_adapted_noalloc": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64),
                                        P],
+        "rf_batch_create": [C.POINTER(P), i32, C.POINTER(rf_grid), P, i32, C.POINTER(rf_phase),
+                            P, P, C.POINTER(rf_options), P],
+        "rf_batch_solve": [P, P, P, P, P, P, P],
+        "rf_batch_info": [P, P, P, P],
+        "rf_batch_destroy": [P],
         "rf_set_tracing": [P, i32],
         "rf_get_stage_times": [P, P, P],
         "rf_reset_stage_times": [P],
@@ -98,7 +103,8 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_solve", "rf_solve_path", "rf_reset_path", "rf_get_fields",
             "rf_get_reduced_strain", "rf_get_state", "rf_set_state", "rf_get_info", "rf_destroy",
             "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error", "rf_set_tracing",
-            "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc"]
+            "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc",
+            "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy"]
 
 STAGES = ["inverse_z", "inverse_y", "row", "forward_y", "forward_z", "green", "check", "final"]
 
@@ -277,3 +283,58 @@ class Solver:
         i = rf_info()
         _check(lib.rf_get_info(self.ctx, C.byref(i)), allow_nc=False)
         return {k: getattr(i, k) for k, _ in rf_info._fields_}
+
+
+class BatchSolver:
+    """Many independent 2D RVEs solved together (rf_batch_create ... rf_batch_destroy)."""
+
+    def __init__(self, phase_maps, phases, patterns, stream=None, **opts):
+        self.n = len(phase_maps)
+        self.pms = [np.ascontiguousarray(p, dtype=np.uint8) for p in phase_maps]
+        self.pats = [np.ascontiguousarray(p, dtype=np.int32).reshape(-1, 3) for p in patterns]
+        self.K = [len(p) for p in self.pats]
+        grids = (rf_grid * self.n)()
+        for i, pm in enumerate(self.pms):
+            g = make_grid(pm.shape)
+            grids[i] = g
+        self._grids = grids
+        pm_ptrs = (C.c_void_p * self.n)(*[p.ctypes.data for p in self.pms])
+        pat_ptrs = (C.c_void_p * self.n)(*[p.ctypes.data for p in self.pats])
+        Ks = np.ascontiguousarray(self.K, dtype=np.int64)
+        self._phases = make_phases(phases)
+        self._opts = make_options(**opts)
+        self.b = C.c_void_p()
+        _check(lib.rf_batch_create(C.byref(self.b), self.n, grids, C.cast(pm_ptrs, C.c_void_p),
+                                   len(phases), self._phases, C.cast(pat_ptrs, C.c_void_p),
+                                   _ptr(Ks), C.byref(self._opts), stream), allow_nc=False)
+
+    def close(self):
+        if self.b:
+            lib.rf_batch_destroy(self.b)
+            self.b = C.c_void_p()
+
+    __del__ = close
+
+    def rf_batch_solve(self, macro, warm=None):
+        m = np.ascontiguousarray(macro, dtype=np.float64).reshape(self.n, 6)
+        sbar = np.zeros((self.n, 6))
+        its = np.zeros(self.n, np.int32)
+        res = np.zeros(self.n)
+        st = np.zeros(self.n, np.int32)
+        wp = None
+        keep = None
+        if warm is not None:
+            keep = [None if w is None else np.ascontiguousarray(w, dtype=np.float32) for w in warm]
+            arr = (C.c_void_p * self.n)(*[None if w is None else w.ctypes.data for w in keep])
+            wp = C.cast(arr, C.c_void_p)
+        code = _check(lib.rf_batch_solve(self.b, _ptr(m), wp, _ptr(sbar), _ptr(its), _ptr(res),
+                                         _ptr(st)))
+        del keep
+        return dict(sigma_bar=sbar, iters=its, residuals=res, status=st, converged=code == RF_OK)
+
+    def rf_batch_info(self) -> dict:
+        n = C.c_int64(0)
+        r = C.c_int32(0)
+        g = C.c_int32(0)
+        _check(lib.rf_batch_info(self.b, C.byref(n), C.byref(r), C.byref(g)), allow_nc=False)
+        return dict(kernel_launches=n.value, rows_per_item=r.value, grid=g.value)
