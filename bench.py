@@ -41,6 +41,8 @@ TOL = 1e-6
 MAX_ITER = 20000
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 256 << 20
+TRACE_NOTE = ("mean over the stage's launches of CUDA events recorded around it on the solver's "
+              "stream, in a second pass over the same steps (the timed steps run untraced)")
 
 
 def parse():
@@ -54,6 +56,8 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_tf32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--profile-updates", type=int, default=0,
+                   help="run only this many updates of the first increment (for ncu captures)")
     return p.parse_args()
 
 
@@ -174,24 +178,25 @@ def stage_work(name, info, shape, transform, nc=3, ns=4):
     return flops, byts
 
 
-def sources_sha():
+def sources_sha(files):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2103_10203_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in files:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed capture, if it matches the sources."""
+    """Per-launch DRAM bytes of `kernel` from the committed ncu capture, or None when a source
+    file the kernel is built from changed since the capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as fh:
-            d = json.load(fh)
-        if d.get("sources_sha") != sources_sha():
+            k = json.load(fh)["kernels"][kernel]
+        if k["sources_sha"] != sources_sha(k["sources"]):
             return None
-        return d["kernels"][kernel]["dram_bytes_per_launch"]
+        return k["dram_bytes_per_launch"]
     except Exception:
         return None
 
@@ -258,6 +263,15 @@ def main():
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     pattern = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
+    if args.profile_updates > 0:
+        s = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=0.0,
+                      max_iter=args.profile_updates, transform=args.transform,
+                      precision=args.precision)
+        out = s.rf_solve(path[0])
+        n_launch = s.rf_get_info()["kernel_launches"]
+        s.close()
+        print(json.dumps({"profile_updates": int(out["iters"]), "kernel_launches": n_launch}))
+        return 0
     solver = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER,
                        transform=args.transform, precision=args.precision)
     info = solver.rf_get_info()
@@ -273,8 +287,6 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    solver.rf_set_tracing(True)
-    solver.rf_reset_stage_times()
     launches0 = solver.rf_get_info()["kernel_launches"]
     iters, ms_steps, outs = 0, [], []
     with ClockSampler(gpu_id_for(torch, local)) as clk:
@@ -290,8 +302,16 @@ def main():
             iters += n
             outs.append(out)
         torch.cuda.synchronize()
-    launches = solver.rf_get_info()["kernel_launches"] - launches0
-    solver.rf_set_tracing(False)
+        launches = solver.rf_get_info()["kernel_launches"] - launches0
+        # the same steps again with per-stage CUDA events recorded on the solver's stream
+        # (captured into the update graphs); kept out of the timed steps above
+        solver.rf_set_tracing(True)
+        solver.rf_reset_stage_times()
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            step()
+        torch.cuda.synchronize()
+        solver.rf_set_tracing(False)
     stage = solver.rf_get_stage_times()
     total_ms = float(np.sum(ms_steps))
     if dist:
@@ -328,7 +348,7 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": tr, "kernel": kname, "stage": dom,
                 "launch_ms": dom_ms, "algorithmic_bytes_per_launch": byts,
-                "algorithmic_flops_per_launch": flops,
+                "algorithmic_flops_per_launch": flops, "launch_ms_source": TRACE_NOTE,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
     elif dom == "row" or dom.endswith("_y"):
         peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -338,7 +358,7 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": tr, "kernel": kname, "stage": dom,
                 "launch_ms": dom_ms, "algorithmic_flops_per_launch": flops,
-                "algorithmic_bytes_per_launch": byts,
+                "algorithmic_bytes_per_launch": byts, "launch_ms_source": TRACE_NOTE,
                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 FLOP x max SM clock"}
     else:
         roof = {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,

@@ -147,7 +147,7 @@ int get_graph(rf_ctx* c, int chunk, rf_ctx::GraphEntry** out) {
       *out = &g;
       return RF_OK;
     }
-  rf_ctx::GraphEntry g{chunk, c->tracing, nullptr, {}};
+  rf_ctx::GraphEntry g{chunk, c->tracing, nullptr, {}, 0};
   const size_t first = c->graph_traces.size();
   if (c->tracing) {
     // events are created before the capture begins
@@ -158,6 +158,7 @@ int get_graph(rf_ctx* c, int chunk, rf_ctx::GraphEntry** out) {
     }
   }
   const long long launched = c->launched_iters;
+  const long long kernels0 = c->launches;
   cudaGraph_t graph = nullptr;
   if (int e = ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture"))
     return e;
@@ -166,6 +167,8 @@ int get_graph(rf_ctx* c, int chunk, rf_ctx::GraphEntry** out) {
   for (int i = 0; i < chunk && !err; ++i) err = launch_iteration(c);
   c->capturing = false;
   c->launched_iters = launched;
+  g.kernels = c->launches - kernels0;   // counted when the graph is replayed
+  c->launches = kernels0;
   cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
   if (!err && ce != cudaSuccess) err = cuda_fail(ce, "end capture");
   if (!err) {
@@ -247,6 +250,7 @@ int run_iterations(rf_ctx* c) {
     const long long base = c->launched_iters;
     if (int e = ck(cudaGraphLaunch(g->exec, c->stream), "graph launch")) return e;
     c->launched_iters += chunk;
+    c->launches += g->kernels;
     if (int e = ck(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status),
                                    cudaMemcpyDeviceToHost, c->stream), "read status"))
       return e;

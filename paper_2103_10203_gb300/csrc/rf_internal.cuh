@@ -199,6 +199,7 @@ struct rf_ctx {
     bool tracing;
     cudaGraphExec_t exec;
     std::vector<int> trace_first;   // index into traces of each captured update
+    long long kernels;              // kernel nodes in the graph (counted at every replay)
   };
   std::vector<GraphEntry> graphs;
   bool own_stream = false;
