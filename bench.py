@@ -56,6 +56,12 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_tf32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+                   help="c2: 1024^2 J2 load path (the headline line); c4: batch of 4096 RVEs of "
+                        "uneven size vs per-RVE solves; c5: learned warm start vs plain start")
+    p.add_argument("--rves", type=int, default=4096, help="c4 / c5: RVEs in the solved batch")
+    p.add_argument("--train", type=int, default=50000, help="c5: training RVEs")
+    p.add_argument("--epochs", type=int, default=20, help="c5: training epochs")
     p.add_argument("--profile-updates", type=int, default=0,
                    help="run only this many updates of the first increment (for ncu captures)")
     return p.parse_args()
@@ -244,6 +250,157 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- c4 / c5 lines
+def _c4_rve(i):
+    from synth import make_config
+    c = make_config("c4", index=i)
+    return c["phase_map"], c["macro"]
+
+
+def _pool_map(fn, items, workers=16):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, items, chunksize=32))
+
+
+def _timed(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return out, e0.elapsed_time(e1)
+
+
+def run_batch(args, rf, torch):
+    """c4: one batched solve of `rves` RVEs (sides 64..256, K = 5 %) to 1e-6 vs the same RVEs
+    solved one context at a time (a sample of them, same FP32 DFT transforms)."""
+    from synth.configs import elastic_phases, k_target
+    n = args.rves
+    rv = _pool_map(_c4_rve, list(range(n)))
+    pms = [r[0] for r in rv]
+    macros = np.array([r[1] for r in rv])
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    pats = [rf.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size), stream=sh) for pm in pms]
+    ph = elastic_phases()
+    b = rf.BatchSolver(pms, ph, pats, stream=sh, tol=TOL, max_iter=2000, transform="dft")
+    vox = np.array([pm.size for pm in pms], np.float64)
+    for _ in range(args.warmup):
+        b.rf_batch_solve(macros)
+    l0 = b.rf_batch_info()["kernel_launches"]
+    ms, vi = [], 0.0
+    with ClockSampler(gpu_id_for(torch, torch.cuda.current_device())) as clk:
+        for _ in range(args.steps):
+            out, t = _timed(torch, stream, lambda: b.rf_batch_solve(macros))
+            ms.append(t)
+            vi += float(np.sum(out["iters"] * vox))
+    launches = b.rf_batch_info()["kernel_launches"] - l0
+    info = b.rf_batch_info()
+    its = out["iters"]
+    b.close()
+    # per-RVE contexts on a sample (every 8th RVE), solves timed back to back
+    samp = list(range(0, n, 8))
+    ctxs = [rf.Solver(pms[i], ph, pattern=pats[i], stream=sh, tol=TOL, max_iter=2000,
+                      transform="dft") for i in samp]
+    for c, i in zip(ctxs[:8], samp[:8]):
+        c.rf_solve(macros[i])
+    def solo():
+        its_ = 0.0
+        for c, i in zip(ctxs, samp):
+            its_ += c.rf_solve(macros[i])["iters"] * vox[i]
+        return its_
+    solo_vi, solo_ms = _timed(torch, stream, solo)
+    for c in ctxs:
+        c.close()
+    total_ms = float(np.sum(ms))
+    value = vi / (total_ms / 1e3)
+    bytes_per_vox_it = 49.0      # phase 1 B + strain in 12 B + tau out 12 B + line I/O 24 B
+    achieved = bytes_per_vox_it * value / 1e9
+    hbm = _hbm_peak()
+    line = {"metric": "RVE voxel-iterations/s to 1e-6 residual, batched (plain start)",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{n} 2D elastic fibre RVEs, sides U{{64,96,128,192,256}}, "
+                                   "vf U[0.2,0.5], r 8-24, K=5% adapted, FP32 pruned DFT",
+                       "voxels": int(vox.sum()), "tol": TOL,
+                       "l2": "working set larger than L2"},
+            "solves_per_s": n * args.steps / (total_ms / 1e3),
+            "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
+            "per_rve_launches": {"value": solo_vi / (solo_ms / 1e3), "unit": UNIT,
+                                 "sample": f"{len(samp)} of the RVEs (every 8th), one context "
+                                           "each, solved back to back"},
+            "batched_over_per_rve": value / (solo_vi / (solo_ms / 1e3)),
+            "gpu_launches": int(launches), "autotuned": info,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "whole update (five persistent kernels)",
+                         "algorithmic_bytes_per_voxel_iteration": bytes_per_vox_it},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def _c5_rves(seeds, side=128):
+    from paper_2103_10203_gb300 import warmstart as W
+    return W.population(seeds, side=side, workers=16)
+
+
+def run_learned(args, rf, torch):
+    """c5: train the warm-start network on solver-generated 128^2 solutions, then solve
+    `rves` held-out RVEs from the plain start and from the network's prediction."""
+    from paper_2103_10203_gb300 import warmstart as W
+    from synth.configs import elastic_phases
+    ph = elastic_phases()
+    t0 = time.perf_counter()
+    pms, macros = _c5_rves(range(500000, 500000 + args.train))
+    pats = W.patterns(pms, 0.05)
+    S = min(len(p) for p in pats)
+    net = rf.WarmStartNet(S, 512, 1024)
+    net.rf_mlp_set_params(W.init_params(net, 0))
+    ds = W.generate(net, pms, macros, pats, ph, chunk=8192)
+    del pms, pats
+    t1 = time.perf_counter()
+    losses = W.train(net, ds, epochs=args.epochs, batch=256, lr=1e-3, lr_final=2e-5)
+    t2 = time.perf_counter()
+    tp, tm = _c5_rves(range(900000, 900000 + args.rves))
+    tpat = W.patterns(tp, 0.05)
+    with ClockSampler(gpu_id_for(torch, torch.cuda.current_device())) as clk:
+        res = W.evaluate(net, tp, tm, tpat, ph, repeats=max(1, args.steps))
+    launches = net.rf_mlp_launches()
+    net.close()
+    pl, le = res["plain"], res["learned"]
+    line = {"metric": "solves/s to 1e-6 residual, learned-warm vs plain start",
+            "value": args.rves / (le["ms"] / 1e3), "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 0, "ms_per_step": le["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.rves} held-out 2D 128^2 elastic fibre RVEs (vf "
+                                   "U[0.2,0.5], r 8-24), K=5% adapted; network trained on "
+                                   f"{args.train} solver-generated solutions",
+                       "slots": S, "hidden": 512, "epochs": args.epochs, "tol": TOL},
+            "plain": {"solves_per_s": args.rves / (pl["ms"] / 1e3), "ms": pl["ms"],
+                      "iterations_mean": pl["iters_mean"], "iterations_max": pl["iters_max"],
+                      "voxel_iterations_per_s": pl["voxel_iterations"] / (pl["ms"] / 1e3)},
+            "learned": {"solves_per_s": args.rves / (le["ms"] / 1e3), "ms": le["ms"],
+                        "iterations_mean": le["iters_mean"], "iterations_max": le["iters_max"],
+                        "voxel_iterations_per_s": le["voxel_iterations"] / (le["ms"] / 1e3),
+                        "includes": "features + BF16 network inference + warm projection"},
+            "speedup": pl["ms"] / le["ms"],
+            "sigma_bar_max_abs_diff": float(np.max(np.abs(pl["sigma_bar"] - le["sigma_bar"]))),
+            "training": {"data_s": t1 - t0, "train_s": t2 - t1, "loss_first": losses[0],
+                         "loss_last": losses[-1], "network_launches": int(launches)},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def _hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p))["hbm_gbs"] if os.path.exists(p) else 6800.0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -257,6 +414,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2103_10203_gb300 import rf
+    if args.workload == "c4":
+        return run_batch(args, rf, torch)
+    if args.workload == "c5":
+        return run_learned(args, rf, torch)
 
     cfg, pm, K = workload()
     phases, path = cfg["phases"], cfg["path"]

@@ -101,7 +101,10 @@ typedef struct rf_phase {
  *             columns along x, its (ky, kx) rectangle along y, (kz, ky, kx) along z).
  *             RF_TRANSFORM_FFT: full FFTs along each axis restricted to the pattern (the
  *             transform the paper uses, Sec. 4); needs power-of-two sizes (Nz = 1 in 2D) and
- *             precision RF_PREC_FP32. Both compute the same restricted transform. */
+ *             precision RF_PREC_FP32. Both compute the same restricted transform.
+ *  fft_rows, fft_cols  FFT mode tiles: grid rows per row-kernel block and line columns per
+ *             column-kernel block (0 = chosen by timing a few launches of each candidate when
+ *             the pattern is set). Results do not depend on them. */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
@@ -110,7 +113,8 @@ typedef struct rf_options {
   int32_t precision;
   int32_t check_every;
   int32_t transform;
-  int32_t reserved[2];
+  int32_t fft_rows;
+  int32_t fft_cols;
 } rf_options;
 
 /* Run statistics of the last solve on a context. */

@@ -18,7 +18,8 @@ LIB = os.path.join(HERE, "librf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-DNDEBUG"]
-SOURCES = ["rf_api.cu", "rf_kernels.cu", "rf_pattern.cu", "rf_tc.cu", "rf_fft.cu", "rf_batch.cu"]
+SOURCES = ["rf_api.cu", "rf_kernels.cu", "rf_pattern.cu", "rf_tc.cu", "rf_fft.cu", "rf_batch.cu",
+           "rf_mlp.cu"]
 
 
 def _nvcc() -> str:
@@ -37,7 +38,8 @@ def _stale(objs_srcs) -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(os.path.dirname(HERE), "include", "rf.h"))
+    inc_dir = os.path.join(os.path.dirname(HERE), "include")
+    deps += [os.path.join(inc_dir, f) for f in os.listdir(inc_dir)]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

@@ -335,6 +335,8 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
     return invalid("options: unknown precision");
   if (opt->transform != RF_TRANSFORM_DFT && opt->transform != RF_TRANSFORM_FFT)
     return invalid("options: unknown transform");
+  if (opt->fft_rows < 0 || opt->fft_rows > 64 || opt->fft_cols < 0 || opt->fft_cols > 64)
+    return invalid("options: fft_rows and fft_cols in [0, 64]");
   if (opt->transform == RF_TRANSFORM_FFT) {
     auto pow2 = [](int v) { return v >= 2 && (v & (v - 1)) == 0; };
     if (opt->precision != RF_PREC_FP32)
@@ -553,7 +555,7 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
     if (int e = fft_geometry(c)) return e;
     c->splitB = c->splitC = 1;
   }
-  const int part_blocks = std::max(c->row_blocks, c->fft_blocks);
+  const int part_blocks = std::max(c->row_blocks, c->rows);   // any FFT row tile (R >= 1)
   const int splits = std::max(c->splitB, c->splitC);
   int err = dalloc(&c->d_kx, c->Kx, "pattern");
   if (!err) err = dalloc(&c->d_kym, c->Ky, "pattern");
@@ -567,7 +569,7 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err && c->dim == 3) err = dalloc(&c->d_T2, (size_t)c->nz * c->Ky * NCK, "line transforms");
   if (!err && c->dim == 3) err = dalloc(&c->d_T2f, (size_t)c->nz * c->Ky * NCK, "line transforms");
   if (!err) err = dalloc(&c->d_OUT, (size_t)splits * c->rect, "partials");
-  if (!err) err = dalloc(&c->d_part, (size_t)((c->Kh + 255) / 256), "partials");
+  if (!err) err = dalloc(&c->d_part, (size_t)((c->Kh + kGammaBlock - 1) / kGammaBlock), "partials");
   if (!err) err = dalloc(&c->d_counter, 1, "counter");
   if (!err) err = ck(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), c->stream), "memset");
   if (!err) err = dalloc(&c->d_sbar_part, (size_t)part_blocks * 6, "partials");
@@ -584,6 +586,7 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err) err = launch_hinfo(c, d_hk, c->Kh);
   if (!err && c->opt.precision != RF_PREC_FP32) err = tc_setup(c);
   if (!err) err = ck(cudaMemsetAsync(c->d_OUT, 0, sizeof(float2) * splits * c->rect, c->stream), "memset");
+  if (!err && c->opt.transform == RF_TRANSFORM_FFT) err = fft_autotune(c);
   if (!err) err = ck(cudaStreamSynchronize(c->stream), "pattern setup");
   if (d_hk) cudaFree(d_hk);
   if (!err) {

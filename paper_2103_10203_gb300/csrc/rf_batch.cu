@@ -16,6 +16,7 @@
 #include <tuple>
 #include <vector>
 
+#include "../../include/rf_mlp.h"
 #include "rf_internal.cuh"
 #include "rf_law.cuh"
 
@@ -37,6 +38,8 @@ struct BDesc {
   long long off_kx;      // int (kx values), float (fac)
   long long off_ky;      // int (ky mod ny)
   long long off_part;    // double, chunks
+  long long off_pat;     // pattern entries (int3 as given) and their half-index map
+  long long K;           // pattern size
   long long off_spart;   // double, row_items * 6
   int tab_x, tab_y;      // offsets into the twiddle buffer
   long long zero_base;   // ER offset (within the RVE) of the zero frequency
@@ -350,7 +353,11 @@ __global__ void kb_sbar(BArgs a, int n_rve) {
 }
 
 // starting coefficients: zero except the zero frequency N ebar, or projected warm starts
-__global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long* warm_off) {
+// Warm starts come either per half entry (warm + warm_off[r], host-reordered) or, when hsrc is
+// set, in pattern order from the device: slot p = hsrc[h] of RVE r at pwarm[(r S + p) 6 + i]
+// (p >= S: no start value).
+__global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long* warm_off,
+                        const float2* pwarm, const int* hsrc, int S) {
   const int r = blockIdx.x;
   if (r >= n_rve) return;
   const BDesc d = a.d[r];
@@ -359,18 +366,24 @@ __global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long*
   const long long rect = (long long)d.Ky * NC * d.Kx;
   for (long long i = threadIdx.x; i < rect; i += blockDim.x) er[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  if (warm && warm_off[r] >= 0) {
-    const float2* w6 = warm + warm_off[r];
+  if ((warm && warm_off[r] >= 0) || (pwarm && hsrc)) {
     const float lam0 = d.lam0, mu0 = d.mu0;
     for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
       const HIdx hi = a.hidx[d.off_h + h];
       const float4 n = a.hn[d.off_h + h];
       float outr[6] = {0, 0, 0, 0, 0, 0}, outi[6] = {0, 0, 0, 0, 0, 0};
-      if (hi.kind == 0) {
+      const float2* w6 = nullptr;
+      if (pwarm) {
+        const int p = hsrc[d.off_h + h];
+        if (p < S) w6 = pwarm + ((long long)r * S + p) * 6;
+      } else {
+        w6 = warm + warm_off[r] + (long long)h * 6;
+      }
+      if (hi.kind == 0 && w6) {
         float e_r[6], e_i[6];
         for (int i = 0; i < 6; ++i) {
-          e_r[i] = w6[h * 6 + i].x;
-          e_i[i] = w6[h * 6 + i].y;
+          e_r[i] = w6[i].x;
+          e_i[i] = w6[i].y;
         }
         e_r[2] = e_r[3] = e_r[4] = e_i[2] = e_i[3] = e_i[4] = 0.f;
         float sr[6], si[6];
@@ -394,6 +407,114 @@ __global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long*
     const int c = threadIdx.x;
     er[d.zero_base + (long long)c * d.Kx] =
         make_float2((float)((double)d.N * st.ebar[comp6<NC>(c)]), 0.f);
+  }
+}
+
+// Network inputs of RVE r (one CTA per RVE): g^(k_s) = sum_y exp(-2 pi i ky y / ny)
+// sum_x g(x, y) exp(-2 pi i kx x / nx) for the first min(S, K) pattern entries, as separable
+// sums: the x transform of a chunk of rows for every kx in [0, nx/2] (kx < 0 uses the
+// conjugate, g being real), then the y sum per slot. Twiddle indices are exact integers.
+constexpr int kFeatRows = 8;
+
+__global__ void kb_features(const BDesc* __restrict__ desc, const uint8_t* __restrict__ phase,
+                            const int* __restrict__ pat, const float2* __restrict__ tab,
+                            int incl, int S, float* X, int* valid) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const int r = blockIdx.x;
+  const BDesc d = desc[r];
+  const int nx = d.nx, ny = d.ny, hx = nx / 2 + 1;
+  const int Se = (int)min((long long)S, d.K);
+  float2* acc = reinterpret_cast<float2*>(fsm);              // [S]
+  float2* R = acc + S;                                       // [kFeatRows][hx]
+  float* gch = reinterpret_cast<float*>(R + kFeatRows * hx);  // [kFeatRows][nx]
+  const float2* twx = tab + d.tab_x;
+  const float2* twy = tab + d.tab_y;
+  const uint8_t* pm = phase + d.off_phase;
+  const int* pp = pat + 3 * d.off_pat;
+  for (int s = threadIdx.x; s < Se; s += blockDim.x) acc[s] = make_float2(0.f, 0.f);
+  for (int y0 = 0; y0 < ny; y0 += kFeatRows) {
+    const int nr = min(kFeatRows, ny - y0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x)
+      gch[i] = pm[(long long)y0 * nx + i] == incl ? 1.f : 0.f;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * hx; i += blockDim.x) {
+      const int yy = i / hx, kx = i % hx;
+      const float* gr = gch + yy * nx;
+      float re = 0.f, im = 0.f;
+      int m = 0;
+      for (int x = 0; x < nx; ++x) {
+        const float gv = gr[x];
+        const float2 w = twx[m];   // (cos, sin)(2 pi m / nx)
+        re = fmaf(gv, w.x, re);
+        im = fmaf(-gv, w.y, im);
+        m += kx;
+        if (m >= nx) m -= nx;
+      }
+      R[yy * hx + kx] = make_float2(re, im);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < Se; s += blockDim.x) {
+      const int kx = pp[3 * s], ky = pp[3 * s + 1];
+      const int ax = kx >= 0 ? kx : -kx;
+      const float cs = kx >= 0 ? 1.f : -1.f;
+      const int kym = ((ky % ny) + ny) % ny;
+      float2 a = acc[s];
+      int m = (int)(((long long)kym * y0) % ny);
+      for (int yy = 0; yy < nr; ++yy) {
+        const float2 v = R[yy * hx + ax];
+        const float vr = v.x, vi = cs * v.y;
+        const float2 w = twy[m];
+        // (vr + i vi) (cos - i sin)
+        a.x = fmaf(vr, w.x, fmaf(vi, w.y, a.x));
+        a.y = fmaf(vi, w.x, fmaf(-vr, w.y, a.y));
+        m += kym;
+        if (m >= ny) m -= ny;
+      }
+      acc[s] = a;
+    }
+  }
+  __syncthreads();
+  const float invN = 1.f / (float)d.N;
+  float* xr = X + (long long)r * 4 * S;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < Se)
+      f = make_float4(acc[s].x * invN, acc[s].y * invN, (float)pp[3 * s] / (float)nx,
+                      (float)pp[3 * s + 1] / (float)ny);
+    reinterpret_cast<float4*>(xr)[s] = f;
+  }
+  if (valid && threadIdx.x == 0) valid[r] = Se;
+}
+
+// converged coefficients in pattern order: out[(r S + p) 6 + v][2], pmap[p] = half index, or
+// -(h + 1) when entry p is the conjugate of half entry h
+__global__ void kb_reduced_strain(BArgs a, int n_rve, const int* __restrict__ pmap, int S,
+                                  float* out) {
+  const int r = blockIdx.x;
+  if (r >= n_rve) return;
+  const BDesc d = a.d[r];
+  const float2* er = a.ER + d.off_er;
+  for (int p = threadIdx.x; p < S; p += blockDim.x) {
+    float v[12];
+    for (int i = 0; i < 12; ++i) v[i] = 0.f;
+    if (p < d.K) {
+      const int m = pmap[d.off_pat + p];
+      const int h = m >= 0 ? m : -m - 1;
+      const float sg = m >= 0 ? 1.f : -1.f;
+      const HIdx hi = a.hidx[d.off_h + h];
+      const long long base = ((long long)hi.iy * NC) * d.Kx + hi.j;
+      for (int c = 0; c < NC; ++c) {
+        const float2 e = er[base + (long long)c * d.Kx];
+        const int v6 = comp6<NC>(c);
+        v[2 * v6] = e.x;
+        v[2 * v6 + 1] = sg * e.y;
+      }
+    }
+    float4* o = reinterpret_cast<float4*>(out + ((long long)r * S + p) * 12);
+    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+    o[2] = make_float4(v[8], v[9], v[10], v[11]);
   }
 }
 
@@ -431,6 +552,11 @@ struct rf_batch {
   int n_items[5] = {0, 0, 0, 0, 0};
   float2* d_warm = nullptr;
   long long* d_warm_off = nullptr;
+  int* d_pat = nullptr;     // patterns as given, concatenated [sum K][3]
+  int* d_pmap = nullptr;    // pattern entry -> half index (or -(h + 1) for the conjugate)
+  int* d_hsrc = nullptr;    // half index -> pattern entry
+  long long pat_total = 0;
+  int max_nx = 0;
   long long warm_total = 0;
   int grid = 0;
   size_t row_smem = 0;
@@ -605,10 +731,12 @@ int iterate(rf_batch* b) {
   return RF_OK;
 }
 
-int run_solve(rf_batch* b, const double* macro, bool use_warm) {
+int run_solve(rf_batch* b, const double* macro, bool use_warm, const float2* pwarm = nullptr,
+              int S = 0) {
   if (int e = set_status(b, macro)) return e;
   BArgs a = batch_args(b, -1);
-  kb_init<<<b->n, 256, 0, b->stream>>>(a, b->n, use_warm ? b->d_warm : nullptr, b->d_warm_off);
+  kb_init<<<b->n, 256, 0, b->stream>>>(a, b->n, use_warm ? b->d_warm : nullptr, b->d_warm_off,
+                                       pwarm, pwarm ? b->d_hsrc : nullptr, S);
   b->launches += 1;
   if (cudaGetLastError() != cudaSuccess) return bfail(cudaGetLastError(), "batch init");
   return iterate(b);
@@ -631,7 +759,8 @@ int autotune(rf_batch* b, const double* macro) {
     for (int gi = 0; gi < 3; ++gi) {
       b->grid = sms * Gc[gi];
       if (int e = set_status(b, macro)) return e;
-      kb_init<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, nullptr, b->d_warm_off);
+      kb_init<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, nullptr, b->d_warm_off,
+                                           nullptr, nullptr, 0);
       if (int e = launch_update(b)) return e;   // warm-up
       cudaEventRecord(e0, b->stream);
       for (int i = 0; i < 3; ++i)
@@ -652,6 +781,38 @@ int autotune(rf_batch* b, const double* macro) {
   for (int k = 0; k < 5; ++k) b->R_choice[k] = bestR;
   b->grid = sms * bestG;
   return build_row_items(b);
+}
+
+// final pass: fields of the converged coefficients -> homogenised stresses; per-RVE outputs
+int finish_solve(rf_batch* b, double* hom_stress, int32_t* iters, double* residuals,
+                 int32_t* status) {
+  // final pass: fields of the converged coefficients -> homogenised stresses
+  BArgs a0 = batch_args(b, 0);
+  a0.final_pass = 1;
+  kb_inv_y<<<b->grid, 256, 0, b->stream>>>(a0);
+  BArgs a1 = batch_args(b, 1);
+  a1.final_pass = 1;
+  kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
+  kb_sbar<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
+  b->launches += 3;
+  cudaError_t e = cudaMemcpyAsync(b->h_stat, b->d_stat, sizeof(BStat) * b->n,
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(e, "batch final pass");
+  int code = RF_OK;
+  b->last_max_iters = 0;
+  for (int r = 0; r < b->n; ++r) {
+    const BStat& s = b->h_stat[r];
+    if (hom_stress)
+      for (int i = 0; i < 6; ++i) hom_stress[6 * r + i] = s.sbar[i];
+    if (iters) iters[r] = s.iters;
+    if (residuals) residuals[r] = s.last_r;
+    int st = s.nonfinite ? RF_ERR_NONFINITE : (s.last_r < b->opt.tol ? RF_OK : RF_NOT_CONVERGED);
+    if (status) status[r] = st;
+    if (st != RF_OK && code == RF_OK) code = RF_NOT_CONVERGED;
+    b->last_max_iters = std::max(b->last_max_iters, s.iters);
+  }
+  return code;
 }
 
 }  // namespace
@@ -705,6 +866,8 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   std::vector<int> tab_sizes;     // distinct sizes
   std::map<int, int> tab_off;
   long long off_er = 0, off_t1 = 0, off_h = 0, off_kx = 0, off_ky = 0, off_part = 0;
+  long long off_pat = 0;
+  std::vector<int> pat_all, pmap_all, hsrc_all;
   b->desc.resize(n_rve);
   b->h_src.resize(n_rve);
   auto fail = [&](const char* msg) {
@@ -817,7 +980,17 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     for (long long p = 0; p < Kr; ++p) {
       const int kx = patterns[r][3 * p], ky = patterns[r][3 * p + 1];
       if (kx >= 0) b->h_src[r][hpos[std::make_tuple(kx, ky)]] = p;
+      pat_all.insert(pat_all.end(), {kx, ky, 0});
+      if (kx >= 0)
+        pmap_all.push_back((int)hpos[std::make_tuple(kx, ky)]);
+      else
+        pmap_all.push_back(-(int)hpos[std::make_tuple(-kx, sgn(wrp(-ky, ny), ny))] - 1);
     }
+    for (int h = 0; h < d.Kh; ++h) hsrc_all.push_back((int)b->h_src[r][h]);
+    d.off_pat = off_pat;
+    d.K = Kr;
+    off_pat += Kr;
+    b->max_nx = std::max(b->max_nx, nx);
     for (int j = 0; j < d.Kx; ++j) {
       kx_all.push_back(xs[j]);
       const bool self = (xs[j] == 0) || (nx % 2 == 0 && xs[j] == nx / 2);
@@ -867,6 +1040,10 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   if (!err) err = balloc(&b->d_part, off_part, "batch partials");
   if (!err) err = balloc(&b->d_ndone, 1, "batch");
   if (!err) err = balloc(&b->d_warm_off, n_rve, "batch");
+  if (!err) err = balloc(&b->d_pat, pat_all.size(), "batch pattern");
+  if (!err) err = balloc(&b->d_pmap, pmap_all.size(), "batch pattern");
+  if (!err) err = balloc(&b->d_hsrc, hsrc_all.size(), "batch pattern");
+  b->pat_total = off_pat;
   auto up = [&](void* dst, const void* src, size_t bytes) {
     if (err) return;
     cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -878,6 +1055,9 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   up(b->d_kx, kx_all.data(), sizeof(int) * kx_all.size());
   up(b->d_fac, fac_all.data(), sizeof(float) * fac_all.size());
   up(b->d_kym, kym_all.data(), sizeof(int) * kym_all.size());
+  up(b->d_pat, pat_all.data(), sizeof(int) * pat_all.size());
+  up(b->d_pmap, pmap_all.data(), sizeof(int) * pmap_all.size());
+  up(b->d_hsrc, hsrc_all.data(), sizeof(int) * hsrc_all.size());
   if (!err) {
     // twiddle tables and wave vectors via the single-RVE setup kernels
     rf_ctx tmp;
@@ -988,33 +1168,57 @@ int rf_batch_solve(rf_batch* b, const double* macro, const float* const* warm,
     use_warm = true;
   }
   if (int e = run_solve(b, macro, use_warm)) return e;
-  // final pass: fields of the converged coefficients -> homogenised stresses
-  BArgs a0 = batch_args(b, 0);
-  a0.final_pass = 1;
-  kb_inv_y<<<b->grid, 256, 0, b->stream>>>(a0);
-  BArgs a1 = batch_args(b, 1);
-  a1.final_pass = 1;
-  kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
-  kb_sbar<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
-  b->launches += 3;
-  cudaError_t e = cudaMemcpyAsync(b->h_stat, b->d_stat, sizeof(BStat) * b->n,
-                                  cudaMemcpyDeviceToHost, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  if (e != cudaSuccess) return bfail(e, "batch final pass");
-  int code = RF_OK;
-  b->last_max_iters = 0;
-  for (int r = 0; r < b->n; ++r) {
-    const BStat& s = b->h_stat[r];
-    if (hom_stress)
-      for (int i = 0; i < 6; ++i) hom_stress[6 * r + i] = s.sbar[i];
-    if (iters) iters[r] = s.iters;
-    if (residuals) residuals[r] = s.last_r;
-    int st = s.nonfinite ? RF_ERR_NONFINITE : (s.last_r < b->opt.tol ? RF_OK : RF_NOT_CONVERGED);
-    if (status) status[r] = st;
-    if (st != RF_OK && code == RF_OK) code = RF_NOT_CONVERGED;
-    b->last_max_iters = std::max(b->last_max_iters, s.iters);
+  return finish_solve(b, hom_stress, iters, residuals, status);
+}
+
+int rf_batch_features(rf_batch* b, int32_t inclusion_phase, int32_t n_slots, float* d_x,
+                      int32_t* d_valid) {
+  if (!b || !d_x) {
+    set_error("rf_batch_features: null argument");
+    return RF_ERR_INVALID;
   }
-  return code;
+  if (n_slots < 1 || n_slots > 16384 || inclusion_phase < 0 || inclusion_phase > 255 ||
+      (reinterpret_cast<uintptr_t>(d_x) & 15)) {
+    set_error("rf_batch_features: n_slots in [1, 16384], phase in [0, 255], d_x 16-byte aligned");
+    return RF_ERR_INVALID;
+  }
+  const size_t smem = sizeof(float2) * ((size_t)n_slots + (size_t)kFeatRows * (b->max_nx / 2 + 1)) +
+                      sizeof(float) * (size_t)kFeatRows * b->max_nx;
+  cudaFuncSetAttribute(kb_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kb_features<<<b->n, 256, smem, b->stream>>>(b->d_desc, b->d_phase, b->d_pat, b->d_tab,
+                                               inclusion_phase, n_slots, d_x, d_valid);
+  b->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : bfail(e, "rf_batch_features");
+}
+
+int rf_batch_reduced_strain(rf_batch* b, int32_t n_slots, float* d_coeffs) {
+  if (!b || !d_coeffs || n_slots < 1 || (reinterpret_cast<uintptr_t>(d_coeffs) & 15)) {
+    set_error("rf_batch_reduced_strain: invalid argument");
+    return RF_ERR_INVALID;
+  }
+  kb_reduced_strain<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, b->d_pmap, n_slots,
+                                                  d_coeffs);
+  b->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : bfail(e, "rf_batch_reduced_strain");
+}
+
+int rf_batch_solve_warm(rf_batch* b, const double* macro, const float* d_warm, int32_t n_slots,
+                        double* hom_stress, int32_t* iters, double* residuals, int32_t* status) {
+  if (!b || !macro || !d_warm || n_slots < 1 || (reinterpret_cast<uintptr_t>(d_warm) & 7)) {
+    set_error("rf_batch_solve_warm: invalid argument");
+    return RF_ERR_INVALID;
+  }
+  for (int r = 0; r < b->n; ++r)
+    for (int i = 2; i < 5; ++i)
+      if (macro[6 * r + i] != 0.0) {
+        set_error("rf_batch_solve_warm: plane strain needs macro components 33, 23, 13 = 0");
+        return RF_ERR_INVALID;
+      }
+  if (int e = run_solve(b, macro, false, reinterpret_cast<const float2*>(d_warm), n_slots))
+    return e;
+  return finish_solve(b, hom_stress, iters, residuals, status);
 }
 
 int rf_batch_info(const rf_batch* b, int64_t* kernel_launches, int32_t* rows_per_item,
@@ -1051,6 +1255,9 @@ int rf_batch_destroy(rf_batch* b) {
   cudaFree(b->d_ndone);
   cudaFree(b->d_warm);
   cudaFree(b->d_warm_off);
+  cudaFree(b->d_pat);
+  cudaFree(b->d_pmap);
+  cudaFree(b->d_hsrc);
   for (int s = 0; s < 5; ++s) cudaFree(b->d_items[s]);
   if (b->h_stat) cudaFreeHost(b->h_stat);
   if (b->h_ndone) cudaFreeHost(b->h_ndone);

@@ -9,6 +9,7 @@
 // scattered into full-length sequences for the inverse; the forward keeps only those values.
 // The transforms are out-of-place Stockham radix-4 (plus one radix-2 stage when log2 L is odd)
 // in shared memory, with an FP32 twiddle table computed in FP64.
+#include <algorithm>
 #include <cmath>
 
 #include "rf_internal.cuh"
@@ -422,12 +423,17 @@ static int fft_check(rf_ctx* c, const char* what) {
   return e == cudaSuccess ? RF_OK : cuda_fail(e, what);
 }
 
-static int cols_tile(int L) {
-  int C = 4096 / L;
-  if (C > 32) C = 32;
-  if (C < 1) C = 1;
-  return C;
+static size_t cols_smem(int L, int C) {
+  return ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)C * L) * sizeof(float2);
 }
+
+static size_t row_smem(int L, int nc, int Kx, int R) {
+  const int P = (R * nc + 1) / 2;
+  return ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)P * L) * sizeof(float2) + (size_t)Kx * sizeof(int) +
+         16;
+}
+
+constexpr size_t kFftSmemMax = 200 * 1024;
 
 static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, const int* in_list,
                     float2* out, long long out_bs, int out_rows, const int* out_list, int ncols,
@@ -443,31 +449,40 @@ static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, c
   a.out_list = out_list;
   a.ncols = ncols;
   a.L = L;
-  a.C = cols_tile(L);
+  a.C = std::max(1, std::min(c->fft_C, a.ncols));
   a.sign = sign;
   a.table = tab;
   a.done = done;
-  const size_t smem = ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)a.C * L) * sizeof(float2);
+  const size_t smem = cols_smem(L, a.C);
   dim3 grid((ncols + a.C - 1) / a.C, batch);
   k_fft_cols<<<grid, 256, smem, c->stream>>>(a);
   return fft_check(c, "fft cols");
 }
 
-int fft_geometry(rf_ctx* c) {
-  // rows per row-kernel block: about 6144 complex points per ping-pong buffer, even line count
-  const int L = c->nx;
-  int R = (2 * 6144) / (c->nc * L);
-  if (R < 1) R = 1;
-  if (R > c->rows) R = c->rows;
+// rows per row-kernel block (default: about 6144 complex points per ping-pong buffer) and
+// columns per column-kernel block (default: 4096 / L points); the autotuner may replace both
+static void set_rows(rf_ctx* c, int R) {
+  R = std::max(1, std::min(R, c->rows));
   c->fft_R = R;
   c->fft_blocks = (c->rows + R - 1) / R;
-  const int P = (R * c->nc + 1) / 2;
-  c->fft_smem = ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)P * L) * sizeof(float2) +
-                (size_t)c->Kx * sizeof(int) + 16;
-  if (c->fft_smem > 200 * 1024) {
+  c->fft_smem = row_smem(c->nx, c->nc, c->Kx, R);
+}
+
+int fft_geometry(rf_ctx* c) {
+  const int L = c->nx;
+  set_rows(c, c->opt.fft_rows > 0 ? c->opt.fft_rows : (2 * 6144) / (c->nc * L));
+  if (c->fft_smem > kFftSmemMax) {
     set_error("FFT mode: rows too long for the row kernel's shared memory");
     return RF_ERR_INVALID;
   }
+  int C = c->opt.fft_cols > 0 ? c->opt.fft_cols : std::max(1, std::min(32, 4096 / c->ny));
+  const int Lc = std::max(c->ny, c->dim == 3 ? c->nz : 1);
+  while (C > 1 && cols_smem(Lc, C) > kFftSmemMax) --C;
+  if (cols_smem(Lc, C) > kFftSmemMax) {
+    set_error("FFT mode: columns too long for the column kernel's shared memory");
+    return RF_ERR_INVALID;
+  }
+  c->fft_C = C;
   return RF_OK;
 }
 
@@ -563,6 +578,73 @@ int fft_forward_stages(rf_ctx* c, const int* done) {
   trace_stage(c, 3);
   return fft_cols(c, c->d_T1p, 0, c->ny, nullptr, c->d_OUT, 0, c->Ky, c->d_kym, NCK, c->ny, 1,
                   -1, c->d_twy, done);
+}
+
+static int tck(cudaError_t e, const char* what) { return e == cudaSuccess ? RF_OK : cuda_fail(e, what); }
+
+// Autotuner for the FFT tiles: each candidate runs one untimed launch and then four timed
+// launches of the stage it governs (CUDA events on the context's stream) on the context's own
+// buffers; the fastest candidate stays. Candidates that exceed shared memory are skipped.
+int fft_autotune(rf_ctx* c) {
+  if (c->opt.fft_rows > 0 && c->opt.fft_cols > 0) return RF_OK;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "tuner");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "tuner");
+  }
+  int err = RF_OK;
+  const int NCK = c->nc * c->Kx;
+  err = tck(cudaMemsetAsync(c->d_T1, 0, sizeof(float2) * (size_t)c->rows * NCK, c->stream), "tuner");
+  if (!err) err = tck(cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream), "tuner");
+  auto time_it = [&](auto&& run, float* ms) -> int {
+    if (int e = run()) return e;
+    cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < 4; ++i)
+      if (int e = run()) return e;
+    cudaEventRecord(e1, c->stream);
+    if (int e = tck(cudaEventSynchronize(e1), "tuner")) return e;
+    return tck(cudaEventElapsedTime(ms, e0, e1), "tuner");
+  };
+  if (!err && c->opt.fft_rows <= 0) {
+    float best = 1e30f;
+    int bestR = c->fft_R;
+    for (int R : {1, 2, 4, 8, 16}) {
+      if (R > c->rows || row_smem(c->nx, c->nc, c->Kx, R) > kFftSmemMax) continue;
+      set_rows(c, R);
+      float ms = 0.f;
+      err = time_it([&] { return launch_fft_row(c, nullptr, false, 0); }, &ms);
+      if (err) break;
+      if (ms < best) {
+        best = ms;
+        bestR = R;
+      }
+    }
+    set_rows(c, bestR);
+  }
+  if (!err && c->opt.fft_cols <= 0) {
+    const int Lc = std::max(c->ny, c->dim == 3 ? c->nz : 1);
+    float best = 1e30f;
+    int bestC = c->fft_C;
+    for (int C : {1, 2, 4, 8, 16, 32}) {
+      if (cols_smem(Lc, C) > kFftSmemMax) continue;
+      c->fft_C = C;
+      float ms = 0.f;
+      err = time_it([&] {
+        if (int e = fft_inverse_stages(c, nullptr)) return e;
+        return fft_forward_stages(c, nullptr);
+      }, &ms);
+      if (err) break;
+      if (ms < best) {
+        best = ms;
+        bestC = C;
+      }
+    }
+    c->fft_C = bestC;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return err;
 }
 
 }  // namespace rfk

@@ -24,6 +24,7 @@
 namespace rfk {
 
 constexpr int kMaxPhases = 16;
+constexpr int kGammaBlock = 128;   // threads per Green-operator block (one frequency each)
 
 struct DevPhase {
   float lam, mu, sy, H;
@@ -177,7 +178,7 @@ struct rf_ctx {
   float2* d_warm = nullptr;       // [Kh][6] warm-start staging
 
   // FFT transform mode
-  int fft_R = 0, fft_blocks = 0;
+  int fft_R = 0, fft_blocks = 0, fft_C = 0;
   size_t fft_smem = 0;
 
   // split-precision (tensor-core) transforms along x
@@ -246,6 +247,7 @@ int tc_setup(rf_ctx* c);
 int launch_tc_row(rf_ctx* c, const int* done);
 // rf_fft.cu
 int fft_geometry(rf_ctx* c);
+int fft_autotune(rf_ctx* c);
 int launch_fft_row(rf_ctx* c, const int* done, bool final_pass, int commit);
 int fft_inverse_stages(rf_ctx* c, const int* done);
 int fft_forward_stages(rf_ctx* c, const int* done);

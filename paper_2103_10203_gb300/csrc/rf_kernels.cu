@@ -303,7 +303,7 @@ __device__ void decide(const double* part, int n, Status* st, double* sh) {
 }
 
 template <int NC>
-__global__ __launch_bounds__(256) void k_gamma(GammaArgs a, double Nd) {
+__global__ __launch_bounds__(kGammaBlock) void k_gamma(GammaArgs a, double Nd) {
   __shared__ double red[8];
   __shared__ double sh[256];
   __shared__ bool last;
@@ -673,10 +673,10 @@ int launch_gamma_finalize(rf_ctx* c, int splits, const int* done) {
   g.counter = c->d_counter;
   g.part = c->d_part;
   g.done = done;
-  const unsigned gb = (unsigned)((c->Kh + 255) / 256);
+  const unsigned gb = (unsigned)((c->Kh + kGammaBlock - 1) / kGammaBlock);
   trace_stage(c, 5);
-  if (c->nc == 3) k_gamma<3><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
-  else k_gamma<6><<<gb, 256, 0, c->stream>>>(g, (double)c->N);
+  if (c->nc == 3) k_gamma<3><<<gb, kGammaBlock, 0, c->stream>>>(g, (double)c->N);
+  else k_gamma<6><<<gb, kGammaBlock, 0, c->stream>>>(g, (double)c->N);
   int e = launch_check(c, "gamma");
   trace_end(c);
   return e;

@@ -35,7 +35,7 @@ class rf_phase(C.Structure):
 class rf_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("green", C.c_int32),
                 ("ref_medium", C.c_int32), ("precision", C.c_int32), ("check_every", C.c_int32),
-                ("transform", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("transform", C.c_int32), ("fft_rows", C.c_int32), ("fft_cols", C.c_int32)]
 
 
 class rf_info(C.Structure):
@@ -43,6 +43,12 @@ class rf_info(C.Structure):
                 ("Kz", C.c_int32), ("last_iters", C.c_int32), ("last_residual", C.c_double),
                 ("kernel_launches", C.c_int64), ("j2_max_violation", C.c_double),
                 ("lambda0", C.c_double), ("mu0", C.c_double)]
+
+
+class rf_mlp_dims(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("n_in", C.c_int32), ("n_hidden", C.c_int32),
+                ("n_out", C.c_int32), ("max_batch", C.c_int32), ("pad", C.c_int32),
+                ("n_params", C.c_int64), ("adam_steps", C.c_int64)]
 
 
 class RFError(RuntimeError):
@@ -85,6 +91,22 @@ def _load() -> C.CDLL:
         "rf_set_tracing": [P, i32],
         "rf_get_stage_times": [P, P, P],
         "rf_reset_stage_times": [P],
+        "rf_mlp_create": [C.POINTER(P), i32, i32, i32, P],
+        "rf_mlp_get_dims": [P, C.POINTER(rf_mlp_dims)],
+        "rf_mlp_set_params": [P, P],
+        "rf_mlp_get_params": [P, P],
+        "rf_mlp_get_grads": [P, P],
+        "rf_mlp_forward": [P, i32, P, P, i32],
+        "rf_mlp_targets": [P, i32, P, P, P, P, P],
+        "rf_mlp_loss_grad": [P, i32, P, P, P, P, C.POINTER(dbl)],
+        "rf_mlp_adam": [P, C.c_float],
+        "rf_mlp_train_step": [P, i32, P, P, P, P, C.c_float, C.POINTER(dbl)],
+        "rf_mlp_predict_warm": [P, i32, P, P, P, P],
+        "rf_mlp_launches": [P, C.POINTER(i64)],
+        "rf_mlp_destroy": [P],
+        "rf_batch_features": [P, i32, i32, P, P],
+        "rf_batch_reduced_strain": [P, i32, P],
+        "rf_batch_solve_warm": [P, P, P, i32, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -104,7 +126,12 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_get_reduced_strain", "rf_get_state", "rf_set_state", "rf_get_info", "rf_destroy",
             "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error", "rf_set_tracing",
             "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc",
-            "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy"]
+            "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy",
+            "rf_batch_features", "rf_batch_reduced_strain", "rf_batch_solve_warm",
+            "rf_mlp_create", "rf_mlp_get_dims", "rf_mlp_set_params", "rf_mlp_get_params",
+            "rf_mlp_get_grads", "rf_mlp_forward", "rf_mlp_targets", "rf_mlp_loss_grad",
+            "rf_mlp_adam", "rf_mlp_train_step", "rf_mlp_predict_warm", "rf_mlp_launches",
+            "rf_mlp_destroy"]
 
 STAGES = ["inverse_z", "inverse_y", "row", "forward_y", "forward_z", "green", "check", "final"]
 
@@ -117,6 +144,17 @@ def _check(code, allow_nc=True):
 
 def _ptr(a):
     return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _dptr(t):
+    """Device pointer of a CUDA tensor (or None)."""
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
 
 
 def make_grid(shape) -> rf_grid:
@@ -141,12 +179,13 @@ def make_phases(table) -> C.Array:
 
 
 def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
-                 check_every=0, transform="dft") -> rf_options:
+                 check_every=0, transform="dft", fft_rows=0, fft_cols=0) -> rf_options:
     o = rf_options()
     o.tol, o.max_iter = float(tol), int(max_iter)
     o.green, o.ref_medium = GREEN[green], REF[ref]
     o.precision, o.check_every = PRECISION[precision], int(check_every)
     o.transform = TRANSFORM[transform]
+    o.fft_rows, o.fft_cols = int(fft_rows), int(fft_cols)
     return o
 
 
@@ -338,3 +377,131 @@ class BatchSolver:
         g = C.c_int32(0)
         _check(lib.rf_batch_info(self.b, C.byref(n), C.byref(r), C.byref(g)), allow_nc=False)
         return dict(kernel_launches=n.value, rows_per_item=r.value, grid=g.value)
+
+
+    # --- learned warm start hooks (include/rf_mlp.h); device buffers are torch CUDA tensors
+    def rf_batch_features(self, n_slots, inclusion_phase=1):
+        import torch
+        x = torch.empty((self.n, 4 * n_slots), dtype=torch.float32, device="cuda")
+        v = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        _check(lib.rf_batch_features(self.b, inclusion_phase, n_slots, _dptr(x), _dptr(v)),
+               allow_nc=False)
+        return x, v
+
+    def rf_batch_reduced_strain(self, n_slots):
+        import torch
+        c = torch.empty((self.n, n_slots, 6, 2), dtype=torch.float32, device="cuda")
+        _check(lib.rf_batch_reduced_strain(self.b, n_slots, _dptr(c)), allow_nc=False)
+        return c
+
+    def rf_batch_solve_warm(self, macro, d_warm, n_slots):
+        m = np.ascontiguousarray(macro, dtype=np.float64).reshape(self.n, 6)
+        sbar = np.zeros((self.n, 6))
+        its = np.zeros(self.n, np.int32)
+        res = np.zeros(self.n)
+        st = np.zeros(self.n, np.int32)
+        code = _check(lib.rf_batch_solve_warm(self.b, _ptr(m), _dptr(d_warm), n_slots, _ptr(sbar),
+                                              _ptr(its), _ptr(res), _ptr(st)))
+        return dict(sigma_bar=sbar, iters=its, residuals=res, status=st, converged=code == RF_OK)
+
+
+MLP_PRECISION = {"bf16": 0, "tf32": 1}
+
+
+class WarmStartNet:
+    """The warm-start network of include/rf_mlp.h (rf_mlp_create ... rf_mlp_destroy).
+
+    Device inputs and outputs are torch CUDA tensors (float32 / float64 / int32 as documented
+    in the header); parameters and gradients cross as flat float32 numpy arrays."""
+
+    def __init__(self, n_slots, n_hidden=512, max_batch=4096, stream=None):
+        self.net = C.c_void_p()
+        _check(lib.rf_mlp_create(C.byref(self.net), n_slots, n_hidden, max_batch,
+                                 _stream_handle(stream)), allow_nc=False)
+        self.dims = self.rf_mlp_get_dims()
+        self.S = n_slots
+
+    def close(self):
+        if self.net:
+            lib.rf_mlp_destroy(self.net)
+            self.net = C.c_void_p()
+
+    __del__ = close
+
+    def rf_mlp_get_dims(self) -> dict:
+        d = rf_mlp_dims()
+        _check(lib.rf_mlp_get_dims(self.net, C.byref(d)), allow_nc=False)
+        return {k: getattr(d, k) for k, _ in rf_mlp_dims._fields_}
+
+    def shapes(self):
+        S, H = self.dims["n_slots"], self.dims["n_hidden"]
+        return [(4 * S, H), (H,), (H, H), (H,), (H, 18 * S), (18 * S,)]
+
+    def rf_mlp_set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.dims["n_params"]
+        _check(lib.rf_mlp_set_params(self.net, _ptr(a)), allow_nc=False)
+
+    def rf_mlp_get_params(self):
+        a = np.zeros(self.dims["n_params"], np.float32)
+        _check(lib.rf_mlp_get_params(self.net, _ptr(a)), allow_nc=False)
+        return a
+
+    def rf_mlp_get_grads(self):
+        a = np.zeros(self.dims["n_params"], np.float32)
+        _check(lib.rf_mlp_get_grads(self.net, _ptr(a)), allow_nc=False)
+        return a
+
+    def split(self, flat):
+        out, o = [], 0
+        for sh in self.shapes():
+            n = int(np.prod(sh))
+            out.append(np.asarray(flat[o:o + n]).reshape(sh))
+            o += n
+        return out
+
+    def rf_mlp_forward(self, x, precision="bf16"):
+        import torch
+        out = torch.empty((x.shape[0], self.dims["n_out"]), dtype=torch.float32, device=x.device)
+        _check(lib.rf_mlp_forward(self.net, x.shape[0], _dptr(x), _dptr(out),
+                                  MLP_PRECISION[precision]), allow_nc=False)
+        return out
+
+    def rf_mlp_targets(self, coeffs, macro, nvox):
+        import torch
+        B = coeffs.shape[0]
+        t = torch.empty((B, 6 * self.S), dtype=torch.float32, device=coeffs.device)
+        e = torch.empty((B, 3), dtype=torch.float32, device=coeffs.device)
+        _check(lib.rf_mlp_targets(self.net, B, _dptr(coeffs), _dptr(macro), _dptr(nvox),
+                                  _dptr(t), _dptr(e)), allow_nc=False)
+        return t, e
+
+    def rf_mlp_loss_grad(self, x, t, e, valid, want_loss=True):
+        loss = C.c_double(0.0)
+        _check(lib.rf_mlp_loss_grad(self.net, x.shape[0], _dptr(x), _dptr(t), _dptr(e),
+                                    _dptr(valid), C.byref(loss) if want_loss else None),
+               allow_nc=False)
+        return loss.value if want_loss else None
+
+    def rf_mlp_adam(self, lr):
+        _check(lib.rf_mlp_adam(self.net, C.c_float(lr)), allow_nc=False)
+
+    def rf_mlp_train_step(self, x, t, e, valid, lr, want_loss=False):
+        loss = C.c_double(0.0)
+        _check(lib.rf_mlp_train_step(self.net, x.shape[0], _dptr(x), _dptr(t), _dptr(e),
+                                     _dptr(valid), C.c_float(lr),
+                                     C.byref(loss) if want_loss else None), allow_nc=False)
+        return loss.value if want_loss else None
+
+    def rf_mlp_predict_warm(self, x, macro, nvox):
+        import torch
+        B = x.shape[0]
+        out = torch.empty((B, self.S, 6, 2), dtype=torch.float32, device=x.device)
+        _check(lib.rf_mlp_predict_warm(self.net, B, _dptr(x), _dptr(macro), _dptr(nvox),
+                                       _dptr(out)), allow_nc=False)
+        return out
+
+    def rf_mlp_launches(self) -> int:
+        n = C.c_int64(0)
+        _check(lib.rf_mlp_launches(self.net, C.byref(n)), allow_nc=False)
+        return n.value

@@ -12,7 +12,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "rf.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                  if f.endswith(".h"))
     return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(rf_\w+)\s*\(", src, re.M)))
 
 
@@ -40,8 +42,8 @@ def test_struct_layouts_match_header(rf, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"rf_grid": rf.rf_grid, "rf_phase": rf.rf_phase, "rf_options": rf.rf_options,
-               "rf_info": rf.rf_info}
-    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rf.h"', "int main(void){"]
+               "rf_info": rf.rf_info, "rf_mlp_dims": rf.rf_mlp_dims}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rf_mlp.h"', "int main(void){"]
     for name, py in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for fname, _ in py._fields_:
@@ -104,3 +106,15 @@ def test_pattern_arguments_rejected_on_the_host(rf):
     code = rf.lib.rf_pattern_radial(C.byref(g3), 5, C.c_void_p(out.ctypes.data), 4, C.byref(K),
                                     None)
     assert code == -1 and b"2D" in rf.lib.rf_last_error()
+
+
+def test_network_and_batch_hooks_reject_invalid_arguments_on_the_host(rf):
+    net = C.c_void_p()
+    assert rf.lib.rf_mlp_create(C.byref(net), 10, 20, 8, None) == -1      # hidden % 16 != 0
+    assert b"n_hidden" in rf.lib.rf_last_error()
+    assert rf.lib.rf_mlp_create(C.byref(net), 0, 32, 8, None) == -1
+    assert rf.lib.rf_mlp_create(None, 4, 32, 8, None) == -1
+    assert rf.lib.rf_batch_features(None, 1, 4, None, None) == -1
+    assert rf.lib.rf_batch_reduced_strain(None, 4, None) == -1
+    assert rf.lib.rf_batch_solve_warm(None, None, None, 4, None, None, None, None) == -1
+    assert rf.lib.rf_mlp_destroy(None) == 0

@@ -381,6 +381,22 @@ def test_fft_transform_matches_oracle(lib, name, scheme, ref):
     assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
 
 
+@pytest.mark.parametrize("name", ["j2_64", "3d_rect"])
+@pytest.mark.parametrize("rows,cols", [(1, 1), (2, 32), (16, 3), (64, 64)])
+def test_fft_tiles_do_not_change_the_result(lib, name, rows, cols):
+    """Any row / column tile (the autotuner's choices, clamped to the grid) gives the oracle's
+    update at the benchmark spec's tolerances."""
+    pm, ph, macro, pat = _pow2_case(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=5, transform="fft", fft_rows=rows,
+                   fft_cols=cols)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=5)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
 def test_fft_transform_load_path_and_tolerance(lib):
     pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
     ph = j2_phases()
