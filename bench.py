@@ -357,18 +357,18 @@ def run_learned(args, rf, torch):
     t0 = time.perf_counter()
     pms, macros = _c5_rves(range(500000, 500000 + args.train))
     pats = W.patterns(pms, 0.05)
-    S = min(len(p) for p in pats)
-    net = rf.WarmStartNet(S, 512, 1024)
+    net = rf.WarmStartNet(512, 1024)
     net.rf_mlp_set_params(W.init_params(net, 0))
     ds = W.generate(net, pms, macros, pats, ph, chunk=8192)
     del pms, pats
     t1 = time.perf_counter()
-    losses = W.train(net, ds, epochs=args.epochs, batch=256, lr=1e-3, lr_final=2e-5)
+    losses = W.train(net, ds, epochs=args.epochs, batch=128, lr=1e-3, lr_final=2e-5)
     t2 = time.perf_counter()
     tp, tm = _c5_rves(range(900000, 900000 + args.rves))
     tpat = W.patterns(tp, 0.05)
     with ClockSampler(gpu_id_for(torch, torch.cuda.current_device())) as clk:
         res = W.evaluate(net, tp, tm, tpat, ph, repeats=max(1, args.steps))
+    del ds
     launches = net.rf_mlp_launches()
     net.close()
     pl, le = res["plain"], res["learned"]
@@ -380,7 +380,9 @@ def run_learned(args, rf, torch):
             "config": {"workload": f"{args.rves} held-out 2D 128^2 elastic fibre RVEs (vf "
                                    "U[0.2,0.5], r 8-24), K=5% adapted; network trained on "
                                    f"{args.train} solver-generated solutions",
-                       "slots": S, "hidden": 512, "epochs": args.epochs, "tol": TOL},
+                       "network": "48 descriptors -> 512 -> 512 -> 243 (27-term transfer "
+                                  "expansion per strain/direction pair)",
+                       "epochs": args.epochs, "tol": TOL},
             "plain": {"solves_per_s": args.rves / (pl["ms"] / 1e3), "ms": pl["ms"],
                       "iterations_mean": pl["iters_mean"], "iterations_max": pl["iters_max"],
                       "voxel_iterations_per_s": pl["voxel_iterations"] / (pl["ms"] / 1e3)},

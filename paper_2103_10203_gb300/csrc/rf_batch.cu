@@ -38,8 +38,6 @@ struct BDesc {
   long long off_kx;      // int (kx values), float (fac)
   long long off_ky;      // int (ky mod ny)
   long long off_part;    // double, chunks
-  long long off_pat;     // pattern entries (int3 as given) and their half-index map
-  long long K;           // pattern size
   long long off_spart;   // double, row_items * 6
   int tab_x, tab_y;      // offsets into the twiddle buffer
   long long zero_base;   // ER offset (within the RVE) of the zero frequency
@@ -353,11 +351,11 @@ __global__ void kb_sbar(BArgs a, int n_rve) {
 }
 
 // starting coefficients: zero except the zero frequency N ebar, or projected warm starts
-// Warm starts come either per half entry (warm + warm_off[r], host-reordered) or, when hsrc is
-// set, in pattern order from the device: slot p = hsrc[h] of RVE r at pwarm[(r S + p) 6 + i]
-// (p >= S: no start value).
+// Warm starts come either per half entry in the six-component layout (warm + warm_off[r],
+// host-reordered) or, when pwarm is set, from the device slot layout: components 11, 22, 12 of
+// half entry h of RVE r at pwarm[(off_h + h) 3 + c].
 __global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long* warm_off,
-                        const float2* pwarm, const int* hsrc, int S) {
+                        const float2* pwarm) {
   const int r = blockIdx.x;
   if (r >= n_rve) return;
   const BDesc d = a.d[r];
@@ -366,24 +364,26 @@ __global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long*
   const long long rect = (long long)d.Ky * NC * d.Kx;
   for (long long i = threadIdx.x; i < rect; i += blockDim.x) er[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  if ((warm && warm_off[r] >= 0) || (pwarm && hsrc)) {
+  if ((warm && warm_off[r] >= 0) || pwarm) {
     const float lam0 = d.lam0, mu0 = d.mu0;
     for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
       const HIdx hi = a.hidx[d.off_h + h];
       const float4 n = a.hn[d.off_h + h];
       float outr[6] = {0, 0, 0, 0, 0, 0}, outi[6] = {0, 0, 0, 0, 0, 0};
-      const float2* w6 = nullptr;
-      if (pwarm) {
-        const int p = hsrc[d.off_h + h];
-        if (p < S) w6 = pwarm + ((long long)r * S + p) * 6;
-      } else {
-        w6 = warm + warm_off[r] + (long long)h * 6;
-      }
-      if (hi.kind == 0 && w6) {
-        float e_r[6], e_i[6];
-        for (int i = 0; i < 6; ++i) {
-          e_r[i] = w6[i].x;
-          e_i[i] = w6[i].y;
+      if (hi.kind == 0) {
+        float e_r[6] = {0, 0, 0, 0, 0, 0}, e_i[6] = {0, 0, 0, 0, 0, 0};
+        if (pwarm) {
+          const float2* w3 = pwarm + (d.off_h + h) * 3;
+          for (int c = 0; c < NC; ++c) {
+            e_r[comp6<NC>(c)] = w3[c].x;
+            e_i[comp6<NC>(c)] = w3[c].y;
+          }
+        } else {
+          const float2* w6 = warm + warm_off[r] + (long long)h * 6;
+          for (int i = 0; i < 6; ++i) {
+            e_r[i] = w6[i].x;
+            e_i[i] = w6[i].y;
+          }
         }
         e_r[2] = e_r[3] = e_r[4] = e_i[2] = e_i[3] = e_i[4] = 0.f;
         float sr[6], si[6];
@@ -410,28 +410,48 @@ __global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long*
   }
 }
 
-// Network inputs of RVE r (one CTA per RVE): g^(k_s) = sum_y exp(-2 pi i ky y / ny)
-// sum_x g(x, y) exp(-2 pi i kx x / nx) for the first min(S, K) pattern entries, as separable
-// sums: the x transform of a chunk of rows for every kx in [0, nx/2] (kx < 0 uses the
-// conjugate, g being real), then the y sum per slot. Twiddle indices are exact integers.
+// Network inputs of RVE r (one CTA per RVE). gamma(k) = g^(k) / N at every half entry by
+// separable sums: the x transform of a chunk of rows for every kx in [0, nx/2], then the y sum
+// per entry, accumulated in the slot table. Then the 48 descriptors from the slots, with
+// per-value sums in a fixed order (radial bins decided in FP64 without contraction).
 constexpr int kFeatRows = 8;
+constexpr int kDescChunk = 512;
 
-__global__ void kb_features(const BDesc* __restrict__ desc, const uint8_t* __restrict__ phase,
-                            const int* __restrict__ pat, const float2* __restrict__ tab,
-                            int incl, int S, float* X, int* valid) {
+__device__ __forceinline__ int radial_bin(int kx, int ky, int nx, int ny) {
+  const double a = __ddiv_rn((double)kx, (double)nx), b = __ddiv_rn((double)ky, (double)ny);
+  const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+  const double f = floor(__dmul_rn(96.0, r));
+  return f >= 23.0 ? 23 : (int)f;
+}
+
+__global__ void kb_descriptors(BArgs a, int incl, int rve_base, float* X, rf_slot* slots) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int r = blockIdx.x;
-  const BDesc d = desc[r];
+  const BDesc d = a.d[r];
   const int nx = d.nx, ny = d.ny, hx = nx / 2 + 1;
-  const int Se = (int)min((long long)S, d.K);
-  float2* acc = reinterpret_cast<float2*>(fsm);              // [S]
-  float2* R = acc + S;                                       // [kFeatRows][hx]
-  float* gch = reinterpret_cast<float*>(R + kFeatRows * hx);  // [kFeatRows][nx]
-  const float2* twx = tab + d.tab_x;
-  const float2* twy = tab + d.tab_y;
-  const uint8_t* pm = phase + d.off_phase;
-  const int* pp = pat + 3 * d.off_pat;
-  for (int s = threadIdx.x; s < Se; s += blockDim.x) acc[s] = make_float2(0.f, 0.f);
+  float2* R = reinterpret_cast<float2*>(fsm);                      // [kFeatRows][hx]
+  float* gch = reinterpret_cast<float*>(R + kFeatRows * hx);       // [kFeatRows][nx]
+  const float2* twx = a.tab + d.tab_x;
+  const float2* twy = a.tab + d.tab_y;
+  const uint8_t* pm = a.phase + d.off_phase;
+  rf_slot* sl = slots + d.off_h;
+  const float invN = 1.f / (float)d.N;
+  for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
+    const HIdx hi = a.hidx[d.off_h + h];
+    const int kx = a.kx[d.off_kx + hi.j];
+    const int kym = a.kym[d.off_ky + hi.iy];
+    const int ky = kym <= ny / 2 ? kym : kym - ny;
+    rf_slot t;
+    t.g_re = 0.f;
+    t.g_im = 0.f;
+    t.a = (float)kx / (float)nx;
+    t.b = (float)ky / (float)ny;
+    t.weight = hi.kind == 0 ? a.hn[d.off_h + h].w : 0.f;
+    t.inv_n = invN;
+    t.rve = rve_base + r;
+    t.kind = hi.kind;
+    sl[h] = t;
+  }
   for (int y0 = 0; y0 < ny; y0 += kFeatRows) {
     const int nr = min(kFeatRows, ny - y0);
     __syncthreads();
@@ -454,67 +474,116 @@ __global__ void kb_features(const BDesc* __restrict__ desc, const uint8_t* __res
       R[yy * hx + kx] = make_float2(re, im);
     }
     __syncthreads();
-    for (int s = threadIdx.x; s < Se; s += blockDim.x) {
-      const int kx = pp[3 * s], ky = pp[3 * s + 1];
-      const int ax = kx >= 0 ? kx : -kx;
-      const float cs = kx >= 0 ? 1.f : -1.f;
-      const int kym = ((ky % ny) + ny) % ny;
-      float2 a = acc[s];
+    for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
+      const HIdx hi = a.hidx[d.off_h + h];
+      const int kx = a.kx[d.off_kx + hi.j];
+      const int kym = a.kym[d.off_ky + hi.iy];
+      float gr = sl[h].g_re, gi = sl[h].g_im;
       int m = (int)(((long long)kym * y0) % ny);
       for (int yy = 0; yy < nr; ++yy) {
-        const float2 v = R[yy * hx + ax];
-        const float vr = v.x, vi = cs * v.y;
+        const float2 v = R[yy * hx + kx];
         const float2 w = twy[m];
-        // (vr + i vi) (cos - i sin)
-        a.x = fmaf(vr, w.x, fmaf(vi, w.y, a.x));
-        a.y = fmaf(vi, w.x, fmaf(-vr, w.y, a.y));
+        // (v.x + i v.y) (cos - i sin)
+        gr = fmaf(v.x, w.x, fmaf(v.y, w.y, gr));
+        gi = fmaf(v.y, w.x, fmaf(-v.x, w.y, gi));
         m += kym;
         if (m >= ny) m -= ny;
       }
-      acc[s] = a;
+      sl[h].g_re = gr;
+      sl[h].g_im = gi;
     }
   }
   __syncthreads();
-  const float invN = 1.f / (float)d.N;
-  float* xr = X + (long long)r * 4 * S;
-  for (int s = threadIdx.x; s < S; s += blockDim.x) {
-    float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (s < Se)
-      f = make_float4(acc[s].x * invN, acc[s].y * invN, (float)pp[3 * s] / (float)nx,
-                      (float)pp[3 * s + 1] / (float)ny);
-    reinterpret_cast<float4*>(xr)[s] = f;
+  for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
+    sl[h].g_re *= invN;
+    sl[h].g_im *= invN;
   }
-  if (valid && threadIdx.x == 0) valid[r] = Se;
+  __syncthreads();
+  // descriptors: 24 bin sums and 4 x 4 band anisotropy sums over the nonzero frequencies
+  // (half entries weighted by multiplicity), each summed by one lane group in a fixed order
+  float* cb = reinterpret_cast<float*>(fsm);        // reuse: [kDescChunk] p, [4][kDescChunk] h
+  int* cbin = reinterpret_cast<int*>(cb + 5 * kDescChunk);
+  __shared__ float sums[40];
+  __shared__ float vf;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // this warp's values v = warp + nw q, q < 5
+  for (int c0 = 0; c0 < d.Kh; c0 += kDescChunk) {
+    const int m = min(kDescChunk, d.Kh - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int h = c0 + i;
+      const HIdx hi = a.hidx[d.off_h + h];
+      const rf_slot t = sl[h];
+      if (hi.kind == 1) {
+        vf = t.g_re;
+        cb[i] = 0.f;
+        cbin[i] = 0;
+        for (int q = 0; q < 4; ++q) cb[(1 + q) * kDescChunk + i] = 0.f;
+        continue;
+      }
+      const int kx = a.kx[d.off_kx + hi.j];
+      const int kym = a.kym[d.off_ky + hi.iy];
+      const int ky = kym <= ny / 2 ? kym : kym - ny;
+      cb[i] = a.hn[d.off_h + h].w * (t.g_re * t.g_re + t.g_im * t.g_im);
+      cbin[i] = radial_bin(kx, ky, nx, ny);
+      const float aa = t.a, bb = t.b, r2 = aa * aa + bb * bb;
+      const float c2 = (aa * aa - bb * bb) / r2, s2 = 2.f * aa * bb / r2;
+      cb[kDescChunk + i] = c2;
+      cb[2 * kDescChunk + i] = s2;
+      cb[3 * kDescChunk + i] = c2 * c2 - s2 * s2;
+      cb[4 * kDescChunk + i] = 2.f * s2 * c2;
+    }
+    __syncthreads();
+    for (int q = 0; q < 5; ++q) {
+      const int v = warp + nw * q;
+      if (v >= 40) break;
+      float s = 0.f;
+      if (v < 24) {
+        for (int i = lane; i < m; i += 32)
+          if (cbin[i] == v) s += cb[i];
+      } else {
+        const int band = (v - 24) >> 2, hm = (v - 24) & 3;
+        for (int i = lane; i < m; i += 32)
+          if (cbin[i] / 6 == band) s += cb[i] * cb[(1 + hm) * kDescChunk + i];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      acc[q] += s;
+    }
+  }
+  if (lane == 0)
+    for (int q = 0; q < 5; ++q) {
+      const int v = warp + nw * q;
+      if (v < 40) sums[v] = acc[q];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float* x = X + (long long)r * RF_MLP_IN;
+    float tot = 0.f;
+    x[0] = vf;
+    for (int i = 0; i < 24; ++i) {
+      x[1 + i] = sqrtf(sums[i]);
+      tot += sums[i];
+    }
+    for (int j = 0; j < 4; ++j) {
+      float bt = 0.f;
+      for (int i = 6 * j; i < 6 * j + 6; ++i) bt += sums[i];
+      for (int q = 0; q < 4; ++q) x[25 + 4 * j + q] = sums[24 + 4 * j + q] / (bt + 1e-12f);
+    }
+    x[41] = sqrtf(tot);
+    for (int i = 42; i < RF_MLP_IN; ++i) x[i] = 0.f;
+  }
 }
 
-// converged coefficients in pattern order: out[(r S + p) 6 + v][2], pmap[p] = half index, or
-// -(h + 1) when entry p is the conjugate of half entry h
-__global__ void kb_reduced_strain(BArgs a, int n_rve, const int* __restrict__ pmap, int S,
-                                  float* out) {
+// coefficients of the last solve at the slots: out[(off_h + h) 3 + c] (components 11, 22, 12)
+__global__ void kb_reduced_strain(BArgs a, float2* out) {
   const int r = blockIdx.x;
-  if (r >= n_rve) return;
   const BDesc d = a.d[r];
   const float2* er = a.ER + d.off_er;
-  for (int p = threadIdx.x; p < S; p += blockDim.x) {
-    float v[12];
-    for (int i = 0; i < 12; ++i) v[i] = 0.f;
-    if (p < d.K) {
-      const int m = pmap[d.off_pat + p];
-      const int h = m >= 0 ? m : -m - 1;
-      const float sg = m >= 0 ? 1.f : -1.f;
-      const HIdx hi = a.hidx[d.off_h + h];
-      const long long base = ((long long)hi.iy * NC) * d.Kx + hi.j;
-      for (int c = 0; c < NC; ++c) {
-        const float2 e = er[base + (long long)c * d.Kx];
-        const int v6 = comp6<NC>(c);
-        v[2 * v6] = e.x;
-        v[2 * v6 + 1] = sg * e.y;
-      }
-    }
-    float4* o = reinterpret_cast<float4*>(out + ((long long)r * S + p) * 12);
-    o[0] = make_float4(v[0], v[1], v[2], v[3]);
-    o[1] = make_float4(v[4], v[5], v[6], v[7]);
-    o[2] = make_float4(v[8], v[9], v[10], v[11]);
+  for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
+    const HIdx hi = a.hidx[d.off_h + h];
+    const long long base = ((long long)hi.iy * NC) * d.Kx + hi.j;
+    for (int c = 0; c < NC; ++c) out[(d.off_h + h) * 3 + c] = er[base + (long long)c * d.Kx];
   }
 }
 
@@ -552,10 +621,7 @@ struct rf_batch {
   int n_items[5] = {0, 0, 0, 0, 0};
   float2* d_warm = nullptr;
   long long* d_warm_off = nullptr;
-  int* d_pat = nullptr;     // patterns as given, concatenated [sum K][3]
-  int* d_pmap = nullptr;    // pattern entry -> half index (or -(h + 1) for the conjugate)
-  int* d_hsrc = nullptr;    // half index -> pattern entry
-  long long pat_total = 0;
+  long long n_slots = 0;    // half entries of all RVEs
   int max_nx = 0;
   long long warm_total = 0;
   int grid = 0;
@@ -731,12 +797,11 @@ int iterate(rf_batch* b) {
   return RF_OK;
 }
 
-int run_solve(rf_batch* b, const double* macro, bool use_warm, const float2* pwarm = nullptr,
-              int S = 0) {
+int run_solve(rf_batch* b, const double* macro, bool use_warm, const float2* pwarm = nullptr) {
   if (int e = set_status(b, macro)) return e;
   BArgs a = batch_args(b, -1);
   kb_init<<<b->n, 256, 0, b->stream>>>(a, b->n, use_warm ? b->d_warm : nullptr, b->d_warm_off,
-                                       pwarm, pwarm ? b->d_hsrc : nullptr, S);
+                                       pwarm);
   b->launches += 1;
   if (cudaGetLastError() != cudaSuccess) return bfail(cudaGetLastError(), "batch init");
   return iterate(b);
@@ -760,7 +825,7 @@ int autotune(rf_batch* b, const double* macro) {
       b->grid = sms * Gc[gi];
       if (int e = set_status(b, macro)) return e;
       kb_init<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, nullptr, b->d_warm_off,
-                                           nullptr, nullptr, 0);
+                                           nullptr);
       if (int e = launch_update(b)) return e;   // warm-up
       cudaEventRecord(e0, b->stream);
       for (int i = 0; i < 3; ++i)
@@ -866,8 +931,7 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   std::vector<int> tab_sizes;     // distinct sizes
   std::map<int, int> tab_off;
   long long off_er = 0, off_t1 = 0, off_h = 0, off_kx = 0, off_ky = 0, off_part = 0;
-  long long off_pat = 0;
-  std::vector<int> pat_all, pmap_all, hsrc_all;
+
   b->desc.resize(n_rve);
   b->h_src.resize(n_rve);
   auto fail = [&](const char* msg) {
@@ -980,16 +1044,7 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     for (long long p = 0; p < Kr; ++p) {
       const int kx = patterns[r][3 * p], ky = patterns[r][3 * p + 1];
       if (kx >= 0) b->h_src[r][hpos[std::make_tuple(kx, ky)]] = p;
-      pat_all.insert(pat_all.end(), {kx, ky, 0});
-      if (kx >= 0)
-        pmap_all.push_back((int)hpos[std::make_tuple(kx, ky)]);
-      else
-        pmap_all.push_back(-(int)hpos[std::make_tuple(-kx, sgn(wrp(-ky, ny), ny))] - 1);
     }
-    for (int h = 0; h < d.Kh; ++h) hsrc_all.push_back((int)b->h_src[r][h]);
-    d.off_pat = off_pat;
-    d.K = Kr;
-    off_pat += Kr;
     b->max_nx = std::max(b->max_nx, nx);
     for (int j = 0; j < d.Kx; ++j) {
       kx_all.push_back(xs[j]);
@@ -1040,10 +1095,7 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   if (!err) err = balloc(&b->d_part, off_part, "batch partials");
   if (!err) err = balloc(&b->d_ndone, 1, "batch");
   if (!err) err = balloc(&b->d_warm_off, n_rve, "batch");
-  if (!err) err = balloc(&b->d_pat, pat_all.size(), "batch pattern");
-  if (!err) err = balloc(&b->d_pmap, pmap_all.size(), "batch pattern");
-  if (!err) err = balloc(&b->d_hsrc, hsrc_all.size(), "batch pattern");
-  b->pat_total = off_pat;
+  b->n_slots = off_h;
   auto up = [&](void* dst, const void* src, size_t bytes) {
     if (err) return;
     cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -1055,9 +1107,6 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   up(b->d_kx, kx_all.data(), sizeof(int) * kx_all.size());
   up(b->d_fac, fac_all.data(), sizeof(float) * fac_all.size());
   up(b->d_kym, kym_all.data(), sizeof(int) * kym_all.size());
-  up(b->d_pat, pat_all.data(), sizeof(int) * pat_all.size());
-  up(b->d_pmap, pmap_all.data(), sizeof(int) * pmap_all.size());
-  up(b->d_hsrc, hsrc_all.data(), sizeof(int) * hsrc_all.size());
   if (!err) {
     // twiddle tables and wave vectors via the single-RVE setup kernels
     rf_ctx tmp;
@@ -1171,42 +1220,53 @@ int rf_batch_solve(rf_batch* b, const double* macro, const float* const* warm,
   return finish_solve(b, hom_stress, iters, residuals, status);
 }
 
-int rf_batch_features(rf_batch* b, int32_t inclusion_phase, int32_t n_slots, float* d_x,
-                      int32_t* d_valid) {
-  if (!b || !d_x) {
-    set_error("rf_batch_features: null argument");
+int rf_batch_slots(const rf_batch* b, int64_t* n_slots, int64_t* offsets) {
+  if (!b || !n_slots) {
+    set_error("rf_batch_slots: null argument");
     return RF_ERR_INVALID;
   }
-  if (n_slots < 1 || n_slots > 16384 || inclusion_phase < 0 || inclusion_phase > 255 ||
-      (reinterpret_cast<uintptr_t>(d_x) & 15)) {
-    set_error("rf_batch_features: n_slots in [1, 16384], phase in [0, 255], d_x 16-byte aligned");
-    return RF_ERR_INVALID;
+  *n_slots = b->n_slots;
+  if (offsets) {
+    for (int r = 0; r < b->n; ++r) offsets[r] = b->desc[r].off_h;
+    offsets[b->n] = b->n_slots;
   }
-  const size_t smem = sizeof(float2) * ((size_t)n_slots + (size_t)kFeatRows * (b->max_nx / 2 + 1)) +
-                      sizeof(float) * (size_t)kFeatRows * b->max_nx;
-  cudaFuncSetAttribute(kb_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kb_features<<<b->n, 256, smem, b->stream>>>(b->d_desc, b->d_phase, b->d_pat, b->d_tab,
-                                               inclusion_phase, n_slots, d_x, d_valid);
-  b->launches += 1;
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? RF_OK : bfail(e, "rf_batch_features");
+  return RF_OK;
 }
 
-int rf_batch_reduced_strain(rf_batch* b, int32_t n_slots, float* d_coeffs) {
-  if (!b || !d_coeffs || n_slots < 1 || (reinterpret_cast<uintptr_t>(d_coeffs) & 15)) {
+int rf_batch_descriptors(rf_batch* b, int32_t inclusion_phase, int32_t rve_base, float* d_x,
+                         rf_slot* d_slots) {
+  if (!b || !d_x || !d_slots || inclusion_phase < 0 || inclusion_phase > 255 || rve_base < 0 ||
+      (reinterpret_cast<uintptr_t>(d_x) & 15) || (reinterpret_cast<uintptr_t>(d_slots) & 15)) {
+    set_error("rf_batch_descriptors: invalid argument");
+    return RF_ERR_INVALID;
+  }
+  const size_t smem_dft = sizeof(float2) * (size_t)kFeatRows * (b->max_nx / 2 + 1) +
+                          sizeof(float) * (size_t)kFeatRows * b->max_nx;
+  const size_t smem_desc = (5 * sizeof(float) + sizeof(int)) * (size_t)kDescChunk;
+  const size_t smem = std::max(smem_dft, smem_desc);
+  cudaFuncSetAttribute(kb_descriptors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kb_descriptors<<<b->n, 256, smem, b->stream>>>(batch_args(b, -1), inclusion_phase, rve_base,
+                                                  d_x, d_slots);
+  b->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : bfail(e, "rf_batch_descriptors");
+}
+
+int rf_batch_reduced_strain(rf_batch* b, float* d_coeffs) {
+  if (!b || !d_coeffs || (reinterpret_cast<uintptr_t>(d_coeffs) & 15)) {
     set_error("rf_batch_reduced_strain: invalid argument");
     return RF_ERR_INVALID;
   }
-  kb_reduced_strain<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, b->d_pmap, n_slots,
-                                                  d_coeffs);
+  kb_reduced_strain<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1),
+                                                  reinterpret_cast<float2*>(d_coeffs));
   b->launches += 1;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? RF_OK : bfail(e, "rf_batch_reduced_strain");
 }
 
-int rf_batch_solve_warm(rf_batch* b, const double* macro, const float* d_warm, int32_t n_slots,
-                        double* hom_stress, int32_t* iters, double* residuals, int32_t* status) {
-  if (!b || !macro || !d_warm || n_slots < 1 || (reinterpret_cast<uintptr_t>(d_warm) & 7)) {
+int rf_batch_solve_warm(rf_batch* b, const double* macro, const float* d_warm, double* hom_stress,
+                        int32_t* iters, double* residuals, int32_t* status) {
+  if (!b || !macro || !d_warm || (reinterpret_cast<uintptr_t>(d_warm) & 7)) {
     set_error("rf_batch_solve_warm: invalid argument");
     return RF_ERR_INVALID;
   }
@@ -1216,8 +1276,7 @@ int rf_batch_solve_warm(rf_batch* b, const double* macro, const float* d_warm, i
         set_error("rf_batch_solve_warm: plane strain needs macro components 33, 23, 13 = 0");
         return RF_ERR_INVALID;
       }
-  if (int e = run_solve(b, macro, false, reinterpret_cast<const float2*>(d_warm), n_slots))
-    return e;
+  if (int e = run_solve(b, macro, false, reinterpret_cast<const float2*>(d_warm))) return e;
   return finish_solve(b, hom_stress, iters, residuals, status);
 }
 
@@ -1255,9 +1314,6 @@ int rf_batch_destroy(rf_batch* b) {
   cudaFree(b->d_ndone);
   cudaFree(b->d_warm);
   cudaFree(b->d_warm_off);
-  cudaFree(b->d_pat);
-  cudaFree(b->d_pmap);
-  cudaFree(b->d_hsrc);
   for (int s = 0; s < 5; ++s) cudaFree(b->d_items[s]);
   if (b->h_stat) cudaFreeHost(b->h_stat);
   if (b->h_ndone) cudaFreeHost(b->h_ndone);

@@ -1,6 +1,8 @@
-// Learned warm start: a three-layer GELU perceptron whose linear head contracts predicted
-// strain-concentration coefficients with the macroscopic strain direction (so the prediction
-// is linear in ebar, as the elastic fixed point of Sec. 4 is). Inference and training kernels.
+// Learned warm start: a three-layer GELU perceptron maps 48 descriptors of an RVE's phase
+// indicator to a real strain-transfer expansion over 27 angular/radial basis functions; the
+// head evaluates the transfer at every slot (frequency of the kx >= 0 half of the pattern) and
+// multiplies it with gamma(k) and the macroscopic strain direction, the structure of the
+// scheme's first update (Sec. 4 step c on the plain start). Inference and training kernels.
 //
 // GEMM C[M][N] = sum_k A(m, k) B(k, n) on the tensor cores (tcgen05): one 128 x 128 output tile
 // per CTA of 128 threads, accumulated in 128 FP32 tensor-memory columns. K is staged in
@@ -241,7 +243,10 @@ __global__ __launch_bounds__(128) void k_gemm(GemmArgs g) {
 }
 
 // ------------------------------------------------------------------------------------------
-// head, loss and its gradient: one thread per (sample, slot)
+// head over the slots (one CTA per RVE; the RVE's 243 coefficients staged in shared memory)
+constexpr int kBasis = RF_MLP_BASIS;
+constexpr int kOut = RF_MLP_OUT;
+
 __device__ __forceinline__ void unit_dir(const double* mac, float e[3], double* en_out) {
   const double en = sqrt(mac[0] * mac[0] + mac[1] * mac[1] + mac[2] * mac[2] +
                          2.0 * (mac[3] * mac[3] + mac[4] * mac[4] + mac[5] * mac[5]));
@@ -252,55 +257,151 @@ __device__ __forceinline__ void unit_dir(const double* mac, float e[3], double* 
   if (en_out) *en_out = en;
 }
 
-// count of valid output entries -> 1 / count
-__global__ void k_count(const int* valid, int B, int S, double* inv_count) {
-  __shared__ long long part[256];
-  long long c = 0;
-  for (int b = threadIdx.x; b < B; b += blockDim.x) c += 6LL * min(max(valid[b], 0), S);
-  part[threadIdx.x] = c;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
-    __syncthreads();
+// phi_n(a, b), n = 9 i + j: radial (1, 4 rho, 16 rho^2) x (1, cos 2t, sin 2t, ..., sin 8t) from
+// the rational forms of the harmonics; (a, b) != 0
+__device__ __forceinline__ void basis27(float a, float b, float* phi) {
+  const float r2 = a * a + b * b;
+  const float inv = 1.f / r2;
+  const float c2 = (a * a - b * b) * inv, s2 = 2.f * a * b * inv;
+  const float c4 = c2 * c2 - s2 * s2, s4 = 2.f * s2 * c2;
+  const float c6 = c4 * c2 - s4 * s2, s6 = s4 * c2 + c4 * s2;
+  const float c8 = c4 * c4 - s4 * s4, s8 = 2.f * s4 * c4;
+  const float h[9] = {1.f, c2, s2, c4, s4, c6, s6, c8, s8};
+  const float rho = 4.f * sqrtf(r2);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    phi[j] = h[j];
+    phi[9 + j] = h[j] * rho;
+    phi[18 + j] = h[j] * rho * rho;
   }
-  if (threadIdx.x == 0) *inv_count = part[0] > 0 ? 1.0 / (double)part[0] : 0.0;
 }
 
-// O [B][ldo] -> residual vs T [B][6S]; dO (in place over O) = 2 (p - t) e_d / count;
-// loss_sum += sum (p - t)^2 over valid entries (FP64)
-__global__ void k_head_loss(float* O, long long ldo, const float* __restrict__ T,
-                            const float* __restrict__ E, const int* __restrict__ valid, int B,
-                            int S, const double* inv_count, double* loss_sum) {
-  __shared__ double red[256];
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double l = 0.0;
-  if (i < (long long)B * S) {
-    const int b = (int)(i / S), s = (int)(i % S);
-    float* o = O + (long long)b * ldo + 18LL * s;
-    const float e0 = E[3 * b], e1 = E[3 * b + 1], e2 = E[3 * b + 2];
-    const bool on = s < valid[b];
-    const float sc = (float)(2.0 * *inv_count);
+// T_cd = sum_n C[cd][n] phi_n (C in shared memory, [9][27])
+__device__ __forceinline__ void transfer9(const float* C, const float* phi, float* T) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+  for (int k = 0; k < 9; ++k) {
+    float t = 0.f;
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        float* oc = o + c * 6 + r;   // o[((c * 3) + d) * 2 + r] for d = 0, 1, 2
-        const float p = oc[0] * e0 + oc[2] * e1 + oc[4] * e2;
-        const float res = on ? p - T[(long long)b * 6 * S + 6 * s + 2 * c + r] : 0.f;
-        l += (double)res * res;
-        const float gp = sc * res;
-        oc[0] = gp * e0;
-        oc[2] = gp * e1;
-        oc[4] = gp * e2;
-      }
+    for (int n = 0; n < kBasis; ++n) t = fmaf(C[k * kBasis + n], phi[n], t);
+    T[k] = t;
   }
-  red[threadIdx.x] = l;
+}
+
+// per RVE: squared-error and weight partials; per slot dT[cd] = w (Re(conj(res_c) g)) e_d,
+// unscaled (the 2 / count factor is applied in k_slot_reduce)
+__global__ __launch_bounds__(128) void k_slot_loss(const float* __restrict__ O, long long ldo,
+                                                   const float* __restrict__ E,
+                                                   const rf_slot* __restrict__ slots,
+                                                   const long long* __restrict__ off,
+                                                   const float* __restrict__ T, float* dT,
+                                                   long long base, double* part) {
+  __shared__ float C[kOut];
+  __shared__ double red[2][4];
+  const int r = blockIdx.x;
+  for (int i = threadIdx.x; i < kOut; i += blockDim.x) C[i] = O[(long long)r * ldo + i];
+  __syncthreads();
+  const float e0 = E[3 * r], e1 = E[3 * r + 1], e2 = E[3 * r + 2];
+  const long long s0 = off[r], s1 = off[r + 1];
+  double sq = 0.0, wsum = 0.0;
+  for (long long s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    const rf_slot sl = slots[s];
+    float* d = dT + (s - base) * 9;
+    if (sl.weight == 0.f) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) d[k] = 0.f;
+      continue;
+    }
+    float phi[kBasis], Tf[9];
+    basis27(sl.a, sl.b, phi);
+    transfer9(C, phi, Tf);
+    const float* t = T + s * 6;
+    float rr[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float m = Tf[c * 3] * e0 + Tf[c * 3 + 1] * e1 + Tf[c * 3 + 2] * e2;
+      const float pr = m * sl.g_re - t[2 * c], pi = m * sl.g_im - t[2 * c + 1];
+      sq += (double)sl.weight * ((double)pr * pr + (double)pi * pi);
+      rr[c] = sl.weight * (pr * sl.g_re + pi * sl.g_im);
+    }
+    wsum += 6.0 * sl.weight;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c * 3] = rr[c] * e0;
+      d[c * 3 + 1] = rr[c] * e1;
+      d[c * 3 + 2] = rr[c] * e2;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sq += __shfl_down_sync(0xffffffffu, sq, o);
+    wsum += __shfl_down_sync(0xffffffffu, wsum, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sq;
+    red[1][threadIdx.x >> 5] = wsum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    part[2 * r] = red[0][0] + red[0][1] + red[0][2] + red[0][3];
+    part[2 * r + 1] = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+  }
+}
+
+// loss = sum sq / sum w; scal[0] = 2 / sum w (gradient scale), scal[1] = loss
+__global__ void k_loss_total(const double* part, int B, double* scal) {
+  __shared__ double a[256], b[256];
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    x += part[2 * i];
+    y += part[2 * i + 1];
+  }
+  a[threadIdx.x] = x;
+  b[threadIdx.x] = y;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    if (threadIdx.x < s) {
+      a[threadIdx.x] += a[threadIdx.x + s];
+      b[threadIdx.x] += b[threadIdx.x + s];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && red[0] != 0.0) atomicAdd(loss_sum, red[0]);
+  if (threadIdx.x == 0) {
+    scal[0] = b[0] > 0.0 ? 2.0 / b[0] : 0.0;
+    scal[1] = b[0] > 0.0 ? a[0] / b[0] : 0.0;
+  }
+}
+
+// dO[r][cd 27 + n] = (2 / count) sum over the RVE's slots of dT[cd] phi_n (fixed order)
+__global__ __launch_bounds__(256) void k_slot_reduce(const rf_slot* __restrict__ slots,
+                                                     const long long* __restrict__ off,
+                                                     const float* __restrict__ dT,
+                                                     long long base, const double* scal,
+                                                     float* dO, long long ldo) {
+  constexpr int kSlots = 64;
+  __shared__ float ph[kSlots][kBasis + 1];
+  __shared__ float dt[kSlots][9];
+  const int r = blockIdx.x;
+  const long long s0 = off[r], s1 = off[r + 1];
+  const int k = threadIdx.x / kBasis, n = threadIdx.x % kBasis;   // k < 9 for threads < 243
+  float acc = 0.f;
+  for (long long c0 = s0; c0 < s1; c0 += kSlots) {
+    const int m = (int)min((long long)kSlots, s1 - c0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const rf_slot sl = slots[c0 + i];
+      if (sl.weight != 0.f) {
+        basis27(sl.a, sl.b, ph[i]);
+      } else {
+        for (int q = 0; q < kBasis; ++q) ph[i][q] = 0.f;
+      }
+    }
+    for (int i = threadIdx.x; i < m * 9; i += blockDim.x)
+      dt[i / 9][i % 9] = dT[(c0 - base + i / 9) * 9 + i % 9];
+    __syncthreads();
+    if (threadIdx.x < kOut)
+      for (int i = 0; i < m; ++i) acc = fmaf(dt[i][k], ph[i][n], acc);
+  }
+  if (threadIdx.x < kOut) dO[(long long)r * ldo + threadIdx.x] = (float)(scal[0] * (double)acc);
 }
 
 // db[n] = sum_b D[b][n]
@@ -327,51 +428,55 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   }
 }
 
-// targets t[b][(s*3 + c)*2 + r] = coeff[b][s][v(c)][r] / (N |ebar|), v = (0, 1, 5); e[b] = e^
-__global__ void k_targets(const float* __restrict__ coeffs, const double* __restrict__ macro,
-                          const double* __restrict__ nvox, int B, int S, float* t, float* E) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= (long long)B * S) return;
-  const int b = (int)(i / S), s = (int)(i % S);
+// targets t[s][2c + part] = coeff[s][c][part] / (N |ebar|); unit directions e[r]
+__global__ void k_slot_targets(const double* __restrict__ macro, const rf_slot* __restrict__ slots,
+                               const long long* __restrict__ off,
+                               const float* __restrict__ coeffs, float* t, float* E) {
+  const int r = blockIdx.x;
   float e[3];
   double en;
-  unit_dir(macro + 6LL * b, e, &en);
-  const double scale = en > 0.0 ? 1.0 / (nvox[b] * en) : 0.0;
-  const int vo[3] = {0, 1, 5};
-  for (int c = 0; c < 3; ++c)
-    for (int r = 0; r < 2; ++r)
-      t[(long long)b * 6 * S + 6 * s + 2 * c + r] =
-          (float)(coeffs[(((long long)b * S + s) * 6 + vo[c]) * 2 + r] * scale);
-  if (s == 0)
-    for (int d = 0; d < 3; ++d) E[3 * b + d] = e[d];
+  unit_dir(macro + 6LL * r, e, &en);
+  if (threadIdx.x < 3) E[3 * r + threadIdx.x] = e[threadIdx.x];
+  const float inv_en = en > 0.0 ? (float)(1.0 / en) : 0.f;
+  for (long long s = off[r] + threadIdx.x; s < off[r + 1]; s += blockDim.x) {
+    const float sc = slots[s].weight != 0.f ? slots[s].inv_n * inv_en : 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[s * 6 + i] = coeffs[s * 6 + i] * sc;
+  }
 }
 
-// warm coefficients [b][s][6][2] = N |ebar| p, p the head's prediction from O [B][ldo]
-__global__ void k_warm(const float* __restrict__ O, long long ldo,
-                       const double* __restrict__ macro, const double* __restrict__ nvox, int B,
-                       int S, float* out) {
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= (long long)B * S) return;
-  const int b = (int)(i / S), s = (int)(i % S);
+// warm[s][c][part] = N |ebar| p_c at regular slots, 0 elsewhere
+__global__ __launch_bounds__(128) void k_slot_predict(const float* __restrict__ O, long long ldo,
+                                                      const double* __restrict__ macro,
+                                                      const rf_slot* __restrict__ slots,
+                                                      const long long* __restrict__ off,
+                                                      float* warm) {
+  __shared__ float C[kOut];
+  const int r = blockIdx.x;
+  for (int i = threadIdx.x; i < kOut; i += blockDim.x) C[i] = O[(long long)r * ldo + i];
+  __syncthreads();
   float e[3];
   double en;
-  unit_dir(macro + 6LL * b, e, &en);
-  const float scale = (float)(nvox[b] * en);
-  const float* o = O + (long long)b * ldo + 18LL * s;
-  float* w = out + ((long long)b * S + s) * 12;
-  float p[6];
-  for (int c = 0; c < 3; ++c)
-    for (int r = 0; r < 2; ++r) {
-      const float* oc = o + c * 6 + r;
-      p[2 * c + r] = scale * (oc[0] * e[0] + oc[2] * e[1] + oc[4] * e[2]);
+  unit_dir(macro + 6LL * r, e, &en);
+  for (long long s = off[r] + threadIdx.x; s < off[r + 1]; s += blockDim.x) {
+    const rf_slot sl = slots[s];
+    float* w = warm + s * 6;
+    if (sl.weight == 0.f) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) w[i] = 0.f;
+      continue;
     }
-  w[0] = p[0];
-  w[1] = p[1];
-  w[2] = p[2];
-  w[3] = p[3];
-  for (int k = 4; k < 10; ++k) w[k] = 0.f;
-  w[10] = p[4];
-  w[11] = p[5];
+    float phi[kBasis], Tf[9];
+    basis27(sl.a, sl.b, phi);
+    transfer9(C, phi, Tf);
+    const float sc = (float)(en / (double)sl.inv_n);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float m = sc * (Tf[c * 3] * e[0] + Tf[c * 3 + 1] * e[1] + Tf[c * 3 + 2] * e[2]);
+      w[2 * c] = m * sl.g_re;
+      w[2 * c + 1] = m * sl.g_im;
+    }
+  }
 }
 
 }  // namespace mlp
@@ -386,7 +491,7 @@ struct rf_mlp {
   int dev = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int S = 0, in = 0, H = 0, out = 0, out_ld = 0, maxB = 0;
+  int in = RF_MLP_IN, H = 0, out = RF_MLP_OUT, out_ld = (RF_MLP_OUT + 3) & ~3, maxB = 0;
   long long n_params = 0;
   // padded device layout: offsets (floats) of W1, b1, W2, b2, W3, b3; total size
   long long off[6] = {0, 0, 0, 0, 0, 0};
@@ -394,7 +499,10 @@ struct rf_mlp {
   float *d_p = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
   float *d_Z1 = nullptr, *d_H1 = nullptr, *d_Z2 = nullptr, *d_H2 = nullptr, *d_O = nullptr;
   float *d_dZ1 = nullptr, *d_dZ2 = nullptr;
-  double* d_scal = nullptr;   // [0] 1/count, [1] loss sum
+  double* d_part = nullptr;   // [maxB][2] loss partials
+  double* d_scal = nullptr;   // [0] gradient scale 2 / count, [1] loss
+  float* d_dT = nullptr;      // [slots][9] per-slot transfer gradients (grown on demand)
+  long long dT_cap = 0;
   int* d_err = nullptr;
   double* h_scal = nullptr;   // pinned
   int* h_err = nullptr;       // pinned
@@ -449,9 +557,9 @@ GemmArgs args(const float* A, long long lda, const float* B, long long ldb, floa
   return g;
 }
 
-// forward through the three layers; Z1/Z2 kept when `keep` (training)
+// forward through the three layers into d_O [B][out_ld]; Z1/Z2 kept when `keep` (training)
 template <class E>
-int forward(rf_mlp* n, int B, const float* x, float* O, bool keep) {
+int forward(rf_mlp* n, int B, const float* x, bool keep) {
   const float* W1 = n->d_p + n->off[0];
   const float* b1 = n->d_p + n->off[1];
   const float* W2 = n->d_p + n->off[2];
@@ -468,15 +576,9 @@ int forward(rf_mlp* n, int B, const float* x, float* O, bool keep) {
   g.Zout = keep ? n->d_Z2 : nullptr;
   g.ldz = n->H;
   if (int e = gemm<E, true, false, EPI_BIAS_GELU>(n, g)) return e;
-  g = args(n->d_H2, n->H, W3, n->out_ld, O, n->out_ld, B, n->out, n->H, n->d_err);
+  g = args(n->d_H2, n->H, W3, n->out_ld, n->d_O, n->out_ld, B, n->out, n->H, n->d_err);
   g.bias = b3;
   return gemm<E, true, false, EPI_BIAS>(n, g);
-}
-
-int check_err(rf_mlp* n) {
-  // device error flag of the bounded waits (read when the host synchronises anyway)
-  if (*n->h_err) return mfail("a bounded device-side wait ran out in the network GEMM", RF_ERR_TIMEOUT);
-  return RF_OK;
 }
 
 int sync_read(rf_mlp* n) {
@@ -486,22 +588,27 @@ int sync_read(rf_mlp* n) {
     e = cudaMemcpyAsync(n->h_err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mlp readback");
-  return check_err(n);
+  if (*n->h_err)
+    return mfail("a bounded device-side wait ran out in the network GEMM", RF_ERR_TIMEOUT);
+  return RF_OK;
+}
+
+int slot_args_ok(rf_mlp* n, int B, const void* slots, const int64_t* off, bool train) {
+  if (!slots || !off) return mfail("network: null slot table or offsets");
+  if (B < 1 || (train && B > n->maxB)) return mfail("network: B must be in [1, max_batch]");
+  return RF_OK;
 }
 
 }  // namespace
 
 extern "C" {
 
-int rf_mlp_create(rf_mlp** out, int32_t n_slots, int32_t n_hidden, int32_t max_batch,
-                  void* stream) {
+int rf_mlp_create(rf_mlp** out, int32_t n_hidden, int32_t max_batch, void* stream) {
   set_error("");
   if (!out) return mfail("rf_mlp_create: null output");
   *out = nullptr;
-  if (n_slots < 1 || n_slots > (1 << 20) || n_hidden < 16 || n_hidden > 4096 ||
-      n_hidden % 16 || max_batch < 1 || max_batch > 65536)
-    return mfail("rf_mlp_create: n_slots >= 1, n_hidden % 16 == 0 in [16, 4096], "
-                 "max_batch in [1, 65536]");
+  if (n_hidden < 16 || n_hidden > 4096 || n_hidden % 16 || max_batch < 1 || max_batch > 65536)
+    return mfail("rf_mlp_create: n_hidden % 16 == 0 in [16, 4096], max_batch in [1, 65536]");
   rf_mlp* n = new rf_mlp();
   cudaGetDevice(&n->dev);
   n->stream = static_cast<cudaStream_t>(stream);
@@ -509,11 +616,7 @@ int rf_mlp_create(rf_mlp** out, int32_t n_slots, int32_t n_hidden, int32_t max_b
     cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking);
     n->own_stream = true;
   }
-  n->S = n_slots;
-  n->in = 4 * n_slots;
   n->H = n_hidden;
-  n->out = 18 * n_slots;
-  n->out_ld = (n->out + 3) & ~3;
   n->maxB = max_batch;
   n->n_params = (long long)n->in * n->H + n->H + (long long)n->H * n->H + n->H +
                 (long long)n->H * n->out + n->out;
@@ -542,6 +645,7 @@ int rf_mlp_create(rf_mlp** out, int32_t n_slots, int32_t n_hidden, int32_t max_b
   al(&n->d_dZ1, bh);
   al(&n->d_dZ2, bh);
   al(&n->d_O, bo);
+  al(&n->d_part, 2LL * max_batch);
   al(&n->d_scal, 2);
   al(&n->d_err, 1);
   if (okm && cudaMallocHost(&n->h_scal, 2 * sizeof(double)) != cudaSuccess) okm = false;
@@ -556,6 +660,7 @@ int rf_mlp_create(rf_mlp** out, int32_t n_slots, int32_t n_hidden, int32_t max_b
   cudaMemsetAsync(n->d_m, 0, sizeof(float) * n->total, n->stream);
   cudaMemsetAsync(n->d_v, 0, sizeof(float) * n->total, n->stream);
   cudaMemsetAsync(n->d_O, 0, sizeof(float) * bo, n->stream);
+  cudaMemsetAsync(n->d_scal, 0, 2 * sizeof(double), n->stream);
   cudaMemsetAsync(n->d_err, 0, sizeof(int), n->stream);
   if (cudaError_t e = cudaStreamSynchronize(n->stream); e != cudaSuccess) {
     rf_mlp_destroy(n);
@@ -567,12 +672,10 @@ int rf_mlp_create(rf_mlp** out, int32_t n_slots, int32_t n_hidden, int32_t max_b
 
 int rf_mlp_get_dims(const rf_mlp* n, rf_mlp_dims* d) {
   if (!n || !d) return mfail("rf_mlp_get_dims: null argument");
-  d->n_slots = n->S;
   d->n_in = n->in;
   d->n_hidden = n->H;
   d->n_out = n->out;
   d->max_batch = n->maxB;
-  d->pad = 0;
   d->n_params = n->n_params;
   d->adam_steps = n->adam_t;
   return RF_OK;
@@ -641,8 +744,8 @@ int rf_mlp_forward(rf_mlp* n, int32_t B, const float* d_x, float* d_out, int32_t
   if (!n || !d_x || !d_out) return mfail("rf_mlp_forward: null argument");
   if (B < 1 || B > n->maxB) return mfail("rf_mlp_forward: B must be in [1, max_batch]");
   if (!aligned16(d_x)) return mfail("rf_mlp_forward: d_x must be 16-byte aligned");
-  int e = precision == RF_MLP_TF32 ? forward<ETf32>(n, B, d_x, n->d_O, false)
-          : precision == RF_MLP_BF16 ? forward<EBf16>(n, B, d_x, n->d_O, false)
+  int e = precision == RF_MLP_TF32 ? forward<ETf32>(n, B, d_x, false)
+          : precision == RF_MLP_BF16 ? forward<EBf16>(n, B, d_x, false)
                                      : mfail("rf_mlp_forward: unknown precision");
   if (e) return e;
   cudaError_t ce = cudaMemcpy2DAsync(d_out, sizeof(float) * n->out, n->d_O,
@@ -652,30 +755,51 @@ int rf_mlp_forward(rf_mlp* n, int32_t B, const float* d_x, float* d_out, int32_t
   return sync_read(n);
 }
 
-int rf_mlp_targets(rf_mlp* n, int32_t B, const float* d_coeffs, const double* d_macro,
-                   const double* d_nvox, float* d_t, float* d_e) {
-  if (!n || !d_coeffs || !d_macro || !d_nvox || !d_t || !d_e)
-    return mfail("rf_mlp_targets: null argument");
-  if (B < 1) return mfail("rf_mlp_targets: B >= 1");
-  const long long items = (long long)B * n->S;
-  k_targets<<<(unsigned)((items + 255) / 256), 256, 0, n->stream>>>(d_coeffs, d_macro, d_nvox, B,
-                                                                    n->S, d_t, d_e);
+int rf_mlp_targets(rf_mlp* n, int32_t B, const double* d_macro, const rf_slot* d_slots,
+                   const int64_t* d_offsets, const float* d_coeffs, float* d_t, float* d_e) {
+  if (!n || !d_macro || !d_coeffs || !d_t || !d_e) return mfail("rf_mlp_targets: null argument");
+  if (int e = slot_args_ok(n, B, d_slots, d_offsets, false)) return e;
+  k_slot_targets<<<B, 128, 0, n->stream>>>(d_macro, d_slots,
+                                            reinterpret_cast<const long long*>(d_offsets),
+                                            d_coeffs, d_t, d_e);
   return launched(n, "rf_mlp_targets");
 }
 
-int rf_mlp_loss_grad(rf_mlp* n, int32_t B, const float* d_x, const float* d_t, const float* d_e,
-                     const int32_t* d_valid, double* loss) {
-  if (!n || !d_x || !d_t || !d_e || !d_valid) return mfail("rf_mlp_loss_grad: null argument");
-  if (B < 1 || B > n->maxB) return mfail("rf_mlp_loss_grad: B must be in [1, max_batch]");
+int rf_mlp_loss_grad(rf_mlp* n, int32_t B, const float* d_x, const float* d_e,
+                     const rf_slot* d_slots, const int64_t* d_offsets, const float* d_t,
+                     double* loss) {
+  if (!n || !d_x || !d_e || !d_t) return mfail("rf_mlp_loss_grad: null argument");
+  if (int e = slot_args_ok(n, B, d_slots, d_offsets, true)) return e;
   if (!aligned16(d_x)) return mfail("rf_mlp_loss_grad: d_x must be 16-byte aligned");
-  if (int e = forward<ETf32>(n, B, d_x, n->d_O, true)) return e;
-  cudaMemsetAsync(n->d_scal + 1, 0, sizeof(double), n->stream);
-  k_count<<<1, 256, 0, n->stream>>>(d_valid, B, n->S, n->d_scal);
-  if (int e = launched(n, "mlp count")) return e;
-  const long long items = (long long)B * n->S;
-  k_head_loss<<<(unsigned)((items + 255) / 256), 256, 0, n->stream>>>(
-      n->d_O, n->out_ld, d_t, d_e, d_valid, B, n->S, n->d_scal, n->d_scal + 1);
-  if (int e = launched(n, "mlp head loss")) return e;
+  const long long* off = reinterpret_cast<const long long*>(d_offsets);
+  // slots of this minibatch (host read of the two end offsets sizes the scratch)
+  long long ends[2] = {0, 0};
+  cudaError_t ce = cudaMemcpyAsync(&ends[0], off, sizeof(long long), cudaMemcpyDeviceToHost,
+                                   n->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(&ends[1], off + B, sizeof(long long), cudaMemcpyDeviceToHost, n->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(n->stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "rf_mlp_loss_grad offsets");
+  const long long nslots = ends[1] - ends[0];
+  if (nslots < 0) return mfail("rf_mlp_loss_grad: offsets must not decrease");
+  if (nslots > n->dT_cap) {
+    if (n->d_dT) cudaFree(n->d_dT);
+    n->d_dT = nullptr;
+    n->dT_cap = 0;
+    const long long cap = std::max(nslots + nslots / 4, 1LL << 16);
+    if (cudaMalloc(&n->d_dT, sizeof(float) * 9 * cap) != cudaSuccess)
+      return mfail("rf_mlp_loss_grad: out of device memory", RF_ERR_OOM);
+    n->dT_cap = cap;
+  }
+  if (int e = forward<ETf32>(n, B, d_x, true)) return e;
+  k_slot_loss<<<B, 128, 0, n->stream>>>(n->d_O, n->out_ld, d_e, d_slots, off, d_t, n->d_dT,
+                                         ends[0], n->d_part);
+  if (int e = launched(n, "mlp slot loss")) return e;
+  k_loss_total<<<1, 256, 0, n->stream>>>(n->d_part, B, n->d_scal);
+  if (int e = launched(n, "mlp loss total")) return e;
+  k_slot_reduce<<<B, 256, 0, n->stream>>>(d_slots, off, n->d_dT, ends[0], n->d_scal, n->d_O,
+                                           n->out_ld);
+  if (int e = launched(n, "mlp slot reduce")) return e;
   float* g = n->d_g;
   const float* W2 = n->d_p + n->off[2];
   const float* W3 = n->d_p + n->off[4];
@@ -708,7 +832,7 @@ int rf_mlp_loss_grad(rf_mlp* n, int32_t B, const float* d_x, const float* d_t, c
   if (int e = launched(n, "mlp colsum")) return e;
   if (loss) {
     if (int e = sync_read(n)) return e;
-    *loss = n->h_scal[1] * n->h_scal[0];
+    *loss = n->h_scal[1];
   }
   return RF_OK;
 }
@@ -725,25 +849,24 @@ int rf_mlp_adam(rf_mlp* n, float lr) {
   return launched(n, "rf_mlp_adam");
 }
 
-int rf_mlp_train_step(rf_mlp* n, int32_t B, const float* d_x, const float* d_t, const float* d_e,
-                      const int32_t* d_valid, float lr, double* loss) {
-  if (int e = rf_mlp_loss_grad(n, B, d_x, d_t, d_e, d_valid, loss)) return e;
+int rf_mlp_train_step(rf_mlp* n, int32_t B, const float* d_x, const float* d_e,
+                      const rf_slot* d_slots, const int64_t* d_offsets, const float* d_t,
+                      float lr, double* loss) {
+  if (int e = rf_mlp_loss_grad(n, B, d_x, d_e, d_slots, d_offsets, d_t, loss)) return e;
   return rf_mlp_adam(n, lr);
 }
 
 int rf_mlp_predict_warm(rf_mlp* n, int32_t B, const float* d_x, const double* d_macro,
-                        const double* d_nvox, float* d_coeffs) {
-  if (!n || !d_x || !d_macro || !d_nvox || !d_coeffs)
-    return mfail("rf_mlp_predict_warm: null argument");
-  if (B < 1) return mfail("rf_mlp_predict_warm: B >= 1");
+                        const rf_slot* d_slots, const int64_t* d_offsets, float* d_warm) {
+  if (!n || !d_x || !d_macro || !d_warm) return mfail("rf_mlp_predict_warm: null argument");
+  if (int e = slot_args_ok(n, B, d_slots, d_offsets, false)) return e;
   if (!aligned16(d_x)) return mfail("rf_mlp_predict_warm: d_x must be 16-byte aligned");
+  const long long* off = reinterpret_cast<const long long*>(d_offsets);
   for (int b0 = 0; b0 < B; b0 += n->maxB) {
     const int nb = std::min(n->maxB, B - b0);
-    if (int e = forward<EBf16>(n, nb, d_x + (long long)b0 * n->in, n->d_O, false)) return e;
-    const long long items = (long long)nb * n->S;
-    k_warm<<<(unsigned)((items + 255) / 256), 256, 0, n->stream>>>(
-        n->d_O, n->out_ld, d_macro + 6LL * b0, d_nvox + b0, nb, n->S,
-        d_coeffs + (long long)b0 * n->S * 12);
+    if (int e = forward<EBf16>(n, nb, d_x + (long long)b0 * n->in, false)) return e;
+    k_slot_predict<<<nb, 128, 0, n->stream>>>(n->d_O, n->out_ld, d_macro + 6LL * b0, d_slots,
+                                               off + b0, d_warm);
     if (int e = launched(n, "rf_mlp_predict_warm")) return e;
   }
   return RF_OK;
@@ -769,7 +892,9 @@ int rf_mlp_destroy(rf_mlp* n) {
   cudaFree(n->d_dZ1);
   cudaFree(n->d_dZ2);
   cudaFree(n->d_O);
+  cudaFree(n->d_part);
   cudaFree(n->d_scal);
+  cudaFree(n->d_dT);
   cudaFree(n->d_err);
   if (n->h_scal) cudaFreeHost(n->h_scal);
   if (n->h_err) cudaFreeHost(n->h_err);

@@ -46,9 +46,17 @@ class rf_info(C.Structure):
 
 
 class rf_mlp_dims(C.Structure):
-    _fields_ = [("n_slots", C.c_int32), ("n_in", C.c_int32), ("n_hidden", C.c_int32),
-                ("n_out", C.c_int32), ("max_batch", C.c_int32), ("pad", C.c_int32),
-                ("n_params", C.c_int64), ("adam_steps", C.c_int64)]
+    _fields_ = [("n_in", C.c_int32), ("n_hidden", C.c_int32), ("n_out", C.c_int32),
+                ("max_batch", C.c_int32), ("n_params", C.c_int64), ("adam_steps", C.c_int64)]
+
+
+class rf_slot(C.Structure):
+    _fields_ = [("g_re", C.c_float), ("g_im", C.c_float), ("a", C.c_float), ("b", C.c_float),
+                ("weight", C.c_float), ("inv_n", C.c_float), ("rve", C.c_int32),
+                ("kind", C.c_int32)]
+
+
+SLOT_FLOATS = 8   # an rf_slot is 32 bytes: device slot tables are float32 tensors [n][8]
 
 
 class RFError(RuntimeError):
@@ -91,22 +99,23 @@ def _load() -> C.CDLL:
         "rf_set_tracing": [P, i32],
         "rf_get_stage_times": [P, P, P],
         "rf_reset_stage_times": [P],
-        "rf_mlp_create": [C.POINTER(P), i32, i32, i32, P],
+        "rf_mlp_create": [C.POINTER(P), i32, i32, P],
         "rf_mlp_get_dims": [P, C.POINTER(rf_mlp_dims)],
         "rf_mlp_set_params": [P, P],
         "rf_mlp_get_params": [P, P],
         "rf_mlp_get_grads": [P, P],
         "rf_mlp_forward": [P, i32, P, P, i32],
-        "rf_mlp_targets": [P, i32, P, P, P, P, P],
-        "rf_mlp_loss_grad": [P, i32, P, P, P, P, C.POINTER(dbl)],
+        "rf_mlp_targets": [P, i32, P, P, P, P, P, P],
+        "rf_mlp_loss_grad": [P, i32, P, P, P, P, P, C.POINTER(dbl)],
         "rf_mlp_adam": [P, C.c_float],
-        "rf_mlp_train_step": [P, i32, P, P, P, P, C.c_float, C.POINTER(dbl)],
-        "rf_mlp_predict_warm": [P, i32, P, P, P, P],
+        "rf_mlp_train_step": [P, i32, P, P, P, P, P, C.c_float, C.POINTER(dbl)],
+        "rf_mlp_predict_warm": [P, i32, P, P, P, P, P],
         "rf_mlp_launches": [P, C.POINTER(i64)],
         "rf_mlp_destroy": [P],
-        "rf_batch_features": [P, i32, i32, P, P],
-        "rf_batch_reduced_strain": [P, i32, P],
-        "rf_batch_solve_warm": [P, P, P, i32, P, P, P, P],
+        "rf_batch_slots": [P, C.POINTER(i64), P],
+        "rf_batch_descriptors": [P, i32, i32, P, P],
+        "rf_batch_reduced_strain": [P, P],
+        "rf_batch_solve_warm": [P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -127,7 +136,8 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error", "rf_set_tracing",
             "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc",
             "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy",
-            "rf_batch_features", "rf_batch_reduced_strain", "rf_batch_solve_warm",
+            "rf_batch_slots", "rf_batch_descriptors", "rf_batch_reduced_strain",
+            "rf_batch_solve_warm",
             "rf_mlp_create", "rf_mlp_get_dims", "rf_mlp_set_params", "rf_mlp_get_params",
             "rf_mlp_get_grads", "rf_mlp_forward", "rf_mlp_targets", "rf_mlp_loss_grad",
             "rf_mlp_adam", "rf_mlp_train_step", "rf_mlp_predict_warm", "rf_mlp_launches",
@@ -380,46 +390,67 @@ class BatchSolver:
 
 
     # --- learned warm start hooks (include/rf_mlp.h); device buffers are torch CUDA tensors
-    def rf_batch_features(self, n_slots, inclusion_phase=1):
+    def rf_batch_slots(self):
+        """(total slot count, offsets [n_rve + 1] int64 numpy)."""
+        n = C.c_int64(0)
+        off = np.zeros(self.n + 1, np.int64)
+        _check(lib.rf_batch_slots(self.b, C.byref(n), _ptr(off)), allow_nc=False)
+        return n.value, off
+
+    def rf_batch_descriptors(self, inclusion_phase=1, rve_base=0):
+        """(descriptors x [n_rve, 48], slot table [slots, 8] float32 view of rf_slot)."""
         import torch
-        x = torch.empty((self.n, 4 * n_slots), dtype=torch.float32, device="cuda")
-        v = torch.empty(self.n, dtype=torch.int32, device="cuda")
-        _check(lib.rf_batch_features(self.b, inclusion_phase, n_slots, _dptr(x), _dptr(v)),
+        ns, _ = self.rf_batch_slots()
+        x = torch.empty((self.n, 48), dtype=torch.float32, device="cuda")
+        st = torch.empty((max(ns, 1), SLOT_FLOATS), dtype=torch.float32, device="cuda")
+        _check(lib.rf_batch_descriptors(self.b, inclusion_phase, rve_base, _dptr(x), _dptr(st)),
                allow_nc=False)
-        return x, v
+        return x, st[:ns]
 
-    def rf_batch_reduced_strain(self, n_slots):
+    def rf_batch_reduced_strain(self):
         import torch
-        c = torch.empty((self.n, n_slots, 6, 2), dtype=torch.float32, device="cuda")
-        _check(lib.rf_batch_reduced_strain(self.b, n_slots, _dptr(c)), allow_nc=False)
-        return c
+        ns, _ = self.rf_batch_slots()
+        c = torch.empty((max(ns, 1), 3, 2), dtype=torch.float32, device="cuda")
+        _check(lib.rf_batch_reduced_strain(self.b, _dptr(c)), allow_nc=False)
+        return c[:ns]
 
-    def rf_batch_solve_warm(self, macro, d_warm, n_slots):
+    def rf_batch_solve_warm(self, macro, d_warm):
         m = np.ascontiguousarray(macro, dtype=np.float64).reshape(self.n, 6)
         sbar = np.zeros((self.n, 6))
         its = np.zeros(self.n, np.int32)
         res = np.zeros(self.n)
         st = np.zeros(self.n, np.int32)
-        code = _check(lib.rf_batch_solve_warm(self.b, _ptr(m), _dptr(d_warm), n_slots, _ptr(sbar),
+        code = _check(lib.rf_batch_solve_warm(self.b, _ptr(m), _dptr(d_warm), _ptr(sbar),
                                               _ptr(its), _ptr(res), _ptr(st)))
         return dict(sigma_bar=sbar, iters=its, residuals=res, status=st, converged=code == RF_OK)
 
 
 MLP_PRECISION = {"bf16": 0, "tf32": 1}
+N_IN, N_BASIS, N_OUT = 48, 27, 243
 
 
 class WarmStartNet:
     """The warm-start network of include/rf_mlp.h (rf_mlp_create ... rf_mlp_destroy).
 
-    Device inputs and outputs are torch CUDA tensors (float32 / float64 / int32 as documented
-    in the header); parameters and gradients cross as flat float32 numpy arrays."""
+    Device inputs and outputs are torch CUDA tensors (float32 / float64 / int64 as documented
+    in the header; slot tables as float32 [n, 8] views of rf_slot); parameters and gradients
+    cross as flat float32 numpy arrays."""
 
-    def __init__(self, n_slots, n_hidden=512, max_batch=4096, stream=None):
+    def __init__(self, n_hidden=512, max_batch=4096, stream=None):
+        """stream: a torch.cuda.Stream; default torch's current stream, or a new stream when the
+        current one is the legacy default stream. Tensors the network reads must be produced in
+        order on this stream (make them inside `with torch.cuda.stream(net.stream)` and give
+        BatchSolver the handle net.stream.cuda_stream)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+            if stream.cuda_stream == 0:   # the legacy default stream: use a stream of our own
+                stream = torch.cuda.Stream()
+        self.stream = stream
         self.net = C.c_void_p()
-        _check(lib.rf_mlp_create(C.byref(self.net), n_slots, n_hidden, max_batch,
-                                 _stream_handle(stream)), allow_nc=False)
+        _check(lib.rf_mlp_create(C.byref(self.net), n_hidden, max_batch, _stream_handle(stream)),
+               allow_nc=False)
         self.dims = self.rf_mlp_get_dims()
-        self.S = n_slots
 
     def close(self):
         if self.net:
@@ -434,8 +465,8 @@ class WarmStartNet:
         return {k: getattr(d, k) for k, _ in rf_mlp_dims._fields_}
 
     def shapes(self):
-        S, H = self.dims["n_slots"], self.dims["n_hidden"]
-        return [(4 * S, H), (H,), (H, H), (H,), (H, 18 * S), (18 * S,)]
+        H = self.dims["n_hidden"]
+        return [(N_IN, H), (H,), (H, H), (H,), (H, N_OUT), (N_OUT,)]
 
     def rf_mlp_set_params(self, flat):
         a = np.ascontiguousarray(flat, dtype=np.float32)
@@ -462,44 +493,44 @@ class WarmStartNet:
 
     def rf_mlp_forward(self, x, precision="bf16"):
         import torch
-        out = torch.empty((x.shape[0], self.dims["n_out"]), dtype=torch.float32, device=x.device)
+        out = torch.empty((x.shape[0], N_OUT), dtype=torch.float32, device=x.device)
         _check(lib.rf_mlp_forward(self.net, x.shape[0], _dptr(x), _dptr(out),
                                   MLP_PRECISION[precision]), allow_nc=False)
         return out
 
-    def rf_mlp_targets(self, coeffs, macro, nvox):
+    def rf_mlp_targets(self, macro, slots, offsets, coeffs):
+        """macro [B, 6] float64, slots [n, 8], offsets [B + 1] int64, coeffs [n, 3, 2]."""
         import torch
-        B = coeffs.shape[0]
-        t = torch.empty((B, 6 * self.S), dtype=torch.float32, device=coeffs.device)
-        e = torch.empty((B, 3), dtype=torch.float32, device=coeffs.device)
-        _check(lib.rf_mlp_targets(self.net, B, _dptr(coeffs), _dptr(macro), _dptr(nvox),
-                                  _dptr(t), _dptr(e)), allow_nc=False)
+        B = macro.shape[0]
+        t = torch.empty((slots.shape[0], 6), dtype=torch.float32, device=slots.device)
+        e = torch.empty((B, 3), dtype=torch.float32, device=slots.device)
+        _check(lib.rf_mlp_targets(self.net, B, _dptr(macro), _dptr(slots), _dptr(offsets),
+                                  _dptr(coeffs), _dptr(t), _dptr(e)), allow_nc=False)
         return t, e
 
-    def rf_mlp_loss_grad(self, x, t, e, valid, want_loss=True):
+    def rf_mlp_loss_grad(self, x, e, slots, offsets, t, want_loss=True):
         loss = C.c_double(0.0)
-        _check(lib.rf_mlp_loss_grad(self.net, x.shape[0], _dptr(x), _dptr(t), _dptr(e),
-                                    _dptr(valid), C.byref(loss) if want_loss else None),
-               allow_nc=False)
+        _check(lib.rf_mlp_loss_grad(self.net, x.shape[0], _dptr(x), _dptr(e), _dptr(slots),
+                                    _dptr(offsets), _dptr(t),
+                                    C.byref(loss) if want_loss else None), allow_nc=False)
         return loss.value if want_loss else None
 
     def rf_mlp_adam(self, lr):
         _check(lib.rf_mlp_adam(self.net, C.c_float(lr)), allow_nc=False)
 
-    def rf_mlp_train_step(self, x, t, e, valid, lr, want_loss=False):
+    def rf_mlp_train_step(self, x, e, slots, offsets, t, lr, want_loss=False):
         loss = C.c_double(0.0)
-        _check(lib.rf_mlp_train_step(self.net, x.shape[0], _dptr(x), _dptr(t), _dptr(e),
-                                     _dptr(valid), C.c_float(lr),
+        _check(lib.rf_mlp_train_step(self.net, x.shape[0], _dptr(x), _dptr(e), _dptr(slots),
+                                     _dptr(offsets), _dptr(t), C.c_float(lr),
                                      C.byref(loss) if want_loss else None), allow_nc=False)
         return loss.value if want_loss else None
 
-    def rf_mlp_predict_warm(self, x, macro, nvox):
+    def rf_mlp_predict_warm(self, x, macro, slots, offsets):
         import torch
-        B = x.shape[0]
-        out = torch.empty((B, self.S, 6, 2), dtype=torch.float32, device=x.device)
-        _check(lib.rf_mlp_predict_warm(self.net, B, _dptr(x), _dptr(macro), _dptr(nvox),
-                                       _dptr(out)), allow_nc=False)
-        return out
+        out = torch.empty((max(slots.shape[0], 1), 3, 2), dtype=torch.float32, device=x.device)
+        _check(lib.rf_mlp_predict_warm(self.net, x.shape[0], _dptr(x), _dptr(macro),
+                                       _dptr(slots), _dptr(offsets), _dptr(out)), allow_nc=False)
+        return out[:slots.shape[0]]
 
     def rf_mlp_launches(self) -> int:
         n = C.c_int64(0)

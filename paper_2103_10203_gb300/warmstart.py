@@ -2,13 +2,15 @@
 
 Pipeline, all arithmetic in librf.so's kernels (this module only moves arguments):
   1. population: seeded fibre RVEs (synth) and their adapted patterns (rf_pattern_adapted),
-  2. training data: the batched solver converges every RVE (rf_batch_solve); rf_batch_features
-     and rf_batch_reduced_strain export network inputs and converged coefficients, and
-     rf_mlp_targets scales them into targets,
-  3. training: Adam on minibatches (rf_mlp_train_step, TF32 tensor-core GEMMs),
-  4. use: rf_batch_features -> rf_mlp_predict_warm (BF16 GEMMs) -> rf_batch_solve_warm.
+  2. training data: the batched solver converges every RVE (rf_batch_solve);
+     rf_batch_descriptors and rf_batch_reduced_strain export network inputs, slot tables and
+     converged coefficients, and rf_mlp_targets scales them into targets,
+  3. training: Adam on minibatches of RVEs (rf_mlp_train_step, TF32 tensor-core GEMMs),
+  4. use: rf_batch_descriptors -> rf_mlp_predict_warm (BF16 GEMMs) -> rf_batch_solve_warm.
 The convergence measure still decides when a warm-started solve stops, so its answer is the
-plain solve's answer to within the tolerance; only the iteration count changes.
+plain solve's answer to within the tolerance; only the iteration count changes. Batches,
+torch tensors and the network share the network's stream, so device buffers pass between them
+in stream order.
 """
 
 from __future__ import annotations
@@ -43,73 +45,90 @@ def population(seeds, side=128, r_range=(8.0, 24.0), vf_range=(0.2, 0.5), worker
     return [o[0] for o in out], np.array([o[1] for o in out])
 
 
-def patterns(phase_maps, ratio=0.05, inclusion_phase=1, stream=None):
-    """Adapted patterns (Sec. 4) with K = ceil(ratio N) for every RVE."""
+def patterns(phase_maps, ratio=0.05, inclusion_phase=1):
+    """Adapted patterns (Sec. 4) with K = ceil(ratio N) for every RVE (host arrays)."""
     from synth.configs import k_target
-    return [rf.rf_pattern_adapted(pm, inclusion_phase, k_target(ratio, pm.size), stream=stream)
+    return [rf.rf_pattern_adapted(pm, inclusion_phase, k_target(ratio, pm.size))
             for pm in phase_maps]
 
 
 class Dataset:
-    """Network inputs x [n][4S], targets t [n][6S], directions e [n][3], valid slots [n]
-    (torch CUDA tensors), plus the plain solves' iteration counts."""
+    """Network inputs x [n][48], unit directions e [n][3], slot table slots [slots][8], per-RVE
+    slot offsets [n + 1] (int64), targets t [slots][6] (torch CUDA tensors), plus the plain
+    solves' iteration counts."""
 
-    def __init__(self, x, t, e, valid, iters):
-        self.x, self.t, self.e, self.valid, self.iters = x, t, e, valid, iters
+    def __init__(self, x, e, slots, offsets, t, iters):
+        self.x, self.e, self.slots, self.offsets, self.t = x, e, slots, offsets, t
+        self.iters = iters
 
     def __len__(self):
         return self.x.shape[0]
 
 
 def generate(net, phase_maps, macros, pats, phases, tol=1e-6, max_iter=2000, chunk=4096,
-             inclusion_phase=1, stream=None):
+             inclusion_phase=1):
     """Training data from converged batched solves, `chunk` RVEs per batch."""
     import torch
-    S = net.S
-    xs, ts, es, vs, its = [], [], [], [], []
+    with torch.cuda.stream(net.stream):
+        return _generate(net, phase_maps, macros, pats, phases, tol, max_iter, chunk,
+                         inclusion_phase, net.stream.cuda_stream)
+
+
+def _generate(net, phase_maps, macros, pats, phases, tol, max_iter, chunk, inclusion_phase,
+              stream):
+    import torch
+    xs, es, sls, offs, ts, its = [], [], [], [], [], []
+    base = 0
     for c0 in range(0, len(phase_maps), chunk):
         sl = slice(c0, c0 + chunk)
         b = rf.BatchSolver(phase_maps[sl], phases, pats[sl], stream=stream, tol=tol,
                            max_iter=max_iter, transform="dft")
         m = np.asarray(macros[sl])
         out = b.rf_batch_solve(m)
-        x, v = b.rf_batch_features(S, inclusion_phase)
-        coeffs = b.rf_batch_reduced_strain(S)
+        x, slots = b.rf_batch_descriptors(inclusion_phase, rve_base=c0)
+        coeffs = b.rf_batch_reduced_strain()
+        _, off = b.rf_batch_slots()
+        d_off = torch.as_tensor(off, dtype=torch.int64, device="cuda")
         d_macro = torch.as_tensor(m, dtype=torch.float64, device="cuda")
-        d_nvox = torch.as_tensor([float(pm.size) for pm in phase_maps[sl]],
-                                 dtype=torch.float64, device="cuda")
-        t, e = net.rf_mlp_targets(coeffs, d_macro, d_nvox)
+        t, e = net.rf_mlp_targets(d_macro, slots, d_off, coeffs)
         torch.cuda.synchronize()
         b.close()
         xs.append(x)
-        ts.append(t)
         es.append(e)
-        vs.append(v)
+        sls.append(slots)
+        ts.append(t)
+        offs.append(off[:-1] + base)
+        base += int(off[-1])
         its.append(out["iters"])
-    return Dataset(torch.cat(xs), torch.cat(ts), torch.cat(es), torch.cat(vs),
+    offs.append(np.array([base], np.int64))
+    d_offsets = torch.as_tensor(np.concatenate(offs), dtype=torch.int64, device="cuda")
+    return Dataset(torch.cat(xs), torch.cat(es), torch.cat(sls), d_offsets, torch.cat(ts),
                    np.concatenate(its))
 
 
-def init_params(net, seed=0):
-    """LeCun-normal weights (variance 1 / fan_in), zero biases, as one flat float32 array."""
+def init_params(net, seed=0, out_scale=0.1):
+    """LeCun-normal weights (variance 1 / fan_in; the output layer scaled by out_scale), zero
+    biases, as one flat float32 array."""
     rng = np.random.default_rng(seed)
     parts = []
-    for sh in net.shapes():
+    shapes = net.shapes()
+    for i, sh in enumerate(shapes):
         if len(sh) == 2:
-            parts.append(rng.standard_normal(sh) / np.sqrt(sh[0]))
+            w = rng.standard_normal(sh) / np.sqrt(sh[0])
+            parts.append(w * (out_scale if i == len(shapes) - 2 else 1.0))
         else:
             parts.append(np.zeros(sh))
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 
-def train(net, ds, epochs=40, batch=256, lr=1e-3, lr_final=3e-5, seed=0, log=None):
-    """Adam over contiguous minibatches (the population is already in random order; each epoch
-    starts at a different offset), learning rate decayed geometrically to lr_final. Returns the
-    per-epoch mean training loss."""
+def train(net, ds, epochs=40, batch=64, lr=1e-3, lr_final=3e-5, seed=0, log=None):
+    """Adam over minibatches of consecutive RVEs (the population is already in random order;
+    each epoch starts at a different offset), learning rate decayed geometrically to lr_final.
+    Returns the per-epoch mean training loss (sampled)."""
     import torch
     n = len(ds)
-    if n < batch:
-        batch = n
+    batch = min(batch, n, net.dims["max_batch"])
+    torch.cuda.current_stream().synchronize()
     steps = max(1, n // batch)
     total = epochs * steps
     losses = []
@@ -117,37 +136,45 @@ def train(net, ds, epochs=40, batch=256, lr=1e-3, lr_final=3e-5, seed=0, log=Non
     k = 0
     for ep in range(epochs):
         off = int(rng.integers(0, n - steps * batch + 1)) if n > steps * batch else 0
-        acc = 0.0
+        acc, cnt = 0.0, 0
         for s in range(steps):
             a = off + s * batch
             rate = lr * (lr_final / lr) ** (k / max(1, total - 1))
-            want = s == steps - 1 or s % 16 == 0
-            loss = net.rf_mlp_train_step(ds.x[a:a + batch], ds.t[a:a + batch], ds.e[a:a + batch],
-                                         ds.valid[a:a + batch], rate, want_loss=want)
+            want = s == steps - 1 or s % 32 == 0
+            loss = net.rf_mlp_train_step(ds.x[a:a + batch], ds.e[a:a + batch], ds.slots,
+                                         ds.offsets[a:a + batch + 1], ds.t, rate, want_loss=want)
             if want:
-                acc = loss if acc == 0.0 else 0.5 * (acc + loss)
+                acc += loss
+                cnt += 1
             k += 1
-        losses.append(acc)
+        losses.append(acc / max(cnt, 1))
         if log:
-            log(f"epoch {ep}: loss {acc:.4e}")
+            log(f"epoch {ep}: loss {losses[-1]:.4e}")
     torch.cuda.synchronize()
     return losses
 
 
 def evaluate(net, phase_maps, macros, pats, phases, tol=1e-6, max_iter=2000, inclusion_phase=1,
-             stream=None, repeats=1):
+             repeats=1):
     """Plain vs learned-warm batched solves of the same RVEs; times (CUDA events on the batch
-    stream) include the features and the network inference for the learned start."""
+    stream) include the descriptors and the network inference for the learned start."""
     import torch
-    S = net.S
+    with torch.cuda.stream(net.stream):
+        return _evaluate(net, phase_maps, macros, pats, phases, tol, max_iter, inclusion_phase,
+                         repeats)
+
+
+def _evaluate(net, phase_maps, macros, pats, phases, tol, max_iter, inclusion_phase, repeats):
+    import torch
+    stream = net.stream.cuda_stream
     b = rf.BatchSolver(phase_maps, phases, pats, stream=stream, tol=tol, max_iter=max_iter,
                        transform="dft")
     m = np.asarray(macros)
     d_macro = torch.as_tensor(m, dtype=torch.float64, device="cuda")
-    d_nvox = torch.as_tensor([float(pm.size) for pm in phase_maps], dtype=torch.float64,
-                             device="cuda")
+    _, off = b.rf_batch_slots()
+    d_off = torch.as_tensor(off, dtype=torch.int64, device="cuda")
     vox = np.array([pm.size for pm in phase_maps], dtype=np.float64)
-    st = torch.cuda.current_stream() if stream is None else stream
+    st = net.stream
     res = {}
     for mode in ("plain", "learned"):
         ms = []
@@ -159,9 +186,9 @@ def evaluate(net, phase_maps, macros, pats, phases, tol=1e-6, max_iter=2000, inc
             if mode == "plain":
                 out = b.rf_batch_solve(m)
             else:
-                x, _ = b.rf_batch_features(S, inclusion_phase)
-                w = net.rf_mlp_predict_warm(x, d_macro, d_nvox)
-                out = b.rf_batch_solve_warm(m, w, S)
+                x, slots = b.rf_batch_descriptors(inclusion_phase)
+                w = net.rf_mlp_predict_warm(x, d_macro, slots, d_off)
+                out = b.rf_batch_solve_warm(m, w)
             e1.record(st)
             e1.synchronize()
             wall = time.perf_counter() - t0

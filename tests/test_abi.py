@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(rf, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"rf_grid": rf.rf_grid, "rf_phase": rf.rf_phase, "rf_options": rf.rf_options,
-               "rf_info": rf.rf_info, "rf_mlp_dims": rf.rf_mlp_dims}
+               "rf_info": rf.rf_info, "rf_mlp_dims": rf.rf_mlp_dims, "rf_slot": rf.rf_slot}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rf_mlp.h"', "int main(void){"]
     for name, py in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -110,11 +110,13 @@ def test_pattern_arguments_rejected_on_the_host(rf):
 
 def test_network_and_batch_hooks_reject_invalid_arguments_on_the_host(rf):
     net = C.c_void_p()
-    assert rf.lib.rf_mlp_create(C.byref(net), 10, 20, 8, None) == -1      # hidden % 16 != 0
+    assert rf.lib.rf_mlp_create(C.byref(net), 20, 8, None) == -1      # hidden % 16 != 0
     assert b"n_hidden" in rf.lib.rf_last_error()
-    assert rf.lib.rf_mlp_create(C.byref(net), 0, 32, 8, None) == -1
-    assert rf.lib.rf_mlp_create(None, 4, 32, 8, None) == -1
-    assert rf.lib.rf_batch_features(None, 1, 4, None, None) == -1
-    assert rf.lib.rf_batch_reduced_strain(None, 4, None) == -1
-    assert rf.lib.rf_batch_solve_warm(None, None, None, 4, None, None, None, None) == -1
+    assert rf.lib.rf_mlp_create(C.byref(net), 32, 0, None) == -1
+    assert rf.lib.rf_mlp_create(None, 32, 8, None) == -1
+    n = C.c_int64(0)
+    assert rf.lib.rf_batch_slots(None, C.byref(n), None) == -1
+    assert rf.lib.rf_batch_descriptors(None, 1, 0, None, None) == -1
+    assert rf.lib.rf_batch_reduced_strain(None, None) == -1
+    assert rf.lib.rf_batch_solve_warm(None, None, None, None, None, None, None) == -1
     assert rf.lib.rf_mlp_destroy(None) == 0

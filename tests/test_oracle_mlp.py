@@ -1,8 +1,8 @@
-"""Pins of the warm-start network oracle: GELU against its closed form and values, gradients
-against central finite differences, the head's index layout against one-hot outputs, Adam against
-a hand-worked first step, features against the DFT definition and the zero frequency's volume
-fraction, and the premise of the head (the elastic fixed point is linear in ebar) against the
-scheme itself."""
+"""Pins of the warm-start network oracle: GELU against its table value and derivative, the
+harmonics against trigonometry, the head against the scheme's first update (Born term, Sec. 4
+step c on the plain start), gradients against central finite differences, Adam against a
+hand-worked step, descriptors against symmetry and sum rules, and the premise of the head
+(the elastic fixed point is linear in ebar) against the scheme itself."""
 
 import math
 
@@ -10,7 +10,8 @@ import numpy as np
 
 import oracle as O
 from oracle import mlp
-from synth import centred_disc
+from oracle.rf_oracle import green_operator, isotropic_stiffness, wave_vector
+from synth import centred_disc, laminate, random_discs
 from synth.configs import elastic_phases
 
 
@@ -25,48 +26,114 @@ def test_gelu_values_and_derivative():
     assert np.allclose(mlp.gelu_grad(z), fd, atol=1e-8)
 
 
-def test_head_layout_one_hot():
-    S = 3
-    ehat = np.array([[0.2, -0.5, 0.7]])
-    for s in range(S):
-        for c in range(3):
-            for d in range(3):
-                for r in range(2):
-                    Oo = np.zeros((1, 18 * S))
-                    Oo[0, ((s * 3 + c) * 3 + d) * 2 + r] = 1.0
-                    P = mlp.head(Oo, ehat)
-                    want = np.zeros((1, 6 * S))
-                    want[0, (s * 3 + c) * 2 + r] = ehat[0, d]
-                    assert np.array_equal(P, want)
+def test_harmonics_and_basis_layout():
+    rng = np.random.default_rng(0)
+    a, b = rng.standard_normal(50), rng.standard_normal(50)
+    t = np.arctan2(b, a)
+    h = mlp.harmonics(a, b)
+    want = [np.ones(50)]
+    for m in (2, 4, 6, 8):
+        want += [np.cos(m * t), np.sin(m * t)]
+    assert np.allclose(h, np.array(want), atol=1e-12)
+    phi = mlp.basis(a, b)
+    rho = np.hypot(a, b) / mlp.RHO_REF
+    assert np.allclose(phi[:9], h) and np.allclose(phi[9:18], h * rho)
+    assert np.allclose(phi[18:], h * rho ** 2)
+
+
+def _first_update_transfer(n1, n2, lam0, mu0):
+    """-Gamma^(n) : (C_f - C_m) : E_d, components (11, 22, 12), continuous operator."""
+    ph = elastic_phases()
+    dC = isotropic_stiffness(ph[1]["lam"] - ph[0]["lam"], ph[1]["mu"] - ph[0]["mu"])
+    q = np.zeros((len(n1), 3))
+    q[:, 0], q[:, 1] = n1, n2
+    G = green_operator(q, lam0, mu0)
+    E = np.zeros((3, 3, 3))
+    E[0, 0, 0] = 1
+    E[1, 1, 1] = 1
+    E[2, 0, 1] = E[2, 1, 0] = 1
+    T = -np.einsum("kijab,abcd,ecd->kije", G, dC, E)
+    return np.stack([T[:, 0, 0, :], T[:, 1, 1, :], T[:, 0, 1, :]], axis=1)   # [n, c, d]
+
+
+def test_head_reproduces_the_first_update():
+    """Fit the 27-term expansion to the Born transfer of one geometry, then the head with those
+    coefficients must give the scheme's first update on ANOTHER geometry and macro strain
+    exactly (the transfer depends on the direction of k only, degree 4 in it)."""
+    ph = elastic_phases()
+    pmA = random_discs(24, (2.0, 5.0), 0.3, seed=1)
+    patA = O.pattern_adapted(pmA, 1, 120)
+    lam0 = 0.5 * (ph[0]["lam"] + ph[1]["lam"])
+    mu0 = 0.5 * (ph[0]["mu"] + ph[1]["mu"])
+    stA = mlp.slots(pmA, 1, patA)
+    nA = np.hypot(stA["a"], stA["b"])
+    T = _first_update_transfer(stA["a"] / nA, stA["b"] / nA, lam0, mu0)      # [n, 3, 3]
+    phi = mlp.basis(stA["a"], stA["b"])                                      # [27, n]
+    C, *_ = np.linalg.lstsq(phi.T, T.reshape(-1, 9), rcond=None)             # [27, 9]
+    o = C.T.ravel()                                                           # [(c 3 + d) 27 + n]
+    pmB = random_discs(32, (2.0, 6.0), 0.4, seed=7)
+    patB = O.pattern_adapted(pmB, 1, 150)
+    macro = np.array([0.004, -0.007, 0, 0, 0, 0.003])
+    r = O.solve(pmB, ph, macro, patB, tol=0.0, max_iter=1, scheme="continuous")
+    _, null = wave_vector(np.asarray(patB), (32, 32, 1), "continuous")
+    stB = mlp.slots(pmB, 1, patB, null)
+    e, en = mlp.unit_direction(macro)
+    p = mlp.head(o, stB, e)
+    want = mlp.targets(r.eps_hat, pmB.size, macro, stB)
+    assert np.allclose(p, want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
+    # conjugate frequencies get conjugate predictions (T is real and even)
+    pat = np.asarray(patB)
+    pos = {(int(kx), int(ky)): i for i, (kx, ky, _) in enumerate(pat[stB["index"]])}
+    for i, (kx, ky, _) in enumerate(pat[stB["index"]]):
+        j = pos.get((-int(kx), -int(ky)))
+        if j is not None:
+            assert np.allclose(p[j], np.conj(p[i]))
+
+
+def test_head_one_hot_and_linearity():
+    pm = random_discs(16, (2.0, 4.0), 0.3, seed=3)
+    st = mlp.slots(pm, 1, O.pattern_adapted(pm, 1, 30))
+    phi = mlp.basis(st["a"], st["b"])
+    e = np.array([0.3, -0.5, 0.8])
+    for c in range(3):
+        for d in range(3):
+            for n in (0, 5, 13, 26):
+                o = np.zeros(mlp.N_OUT)
+                o[(c * 3 + d) * mlp.N_BASIS + n] = 1.0
+                p = mlp.head(o, st, e)
+                want = np.zeros_like(p)
+                want[:, c] = phi[n] * st["g"] * e[d]
+                assert np.allclose(p, want)
+    o = np.random.default_rng(1).standard_normal(mlp.N_OUT)
+    assert np.allclose(mlp.head(o, st, 2 * e - e[::-1]),
+                       2 * mlp.head(o, st, e) - mlp.head(o, st, e[::-1]))
 
 
 def test_gradients_match_finite_differences():
     rng = np.random.default_rng(0)
-    S, hid, B = 2, 6, 3
-    shapes = [(4 * S, hid), (hid,), (hid, hid), (hid,), (hid, 18 * S), (18 * S,)]
-    params = [rng.standard_normal(s) * 0.5 for s in shapes]
-    X = rng.standard_normal((B, 4 * S))
-    T = rng.standard_normal((B, 6 * S))
-    ehat = rng.standard_normal((B, 3))
-    mask = np.ones((B, 6 * S))
-    mask[1, 6:] = 0.0          # sample 1 has one valid slot
-    loss, grads = mlp.loss_and_grads(params, X, T, ehat, mask)
+    hid, B = 6, 3
+    shapes = [(mlp.N_DESC, hid), (hid,), (hid, hid), (hid,), (hid, mlp.N_OUT), (mlp.N_OUT,)]
+    params = [rng.standard_normal(s) * 0.3 for s in shapes]
+    X = rng.standard_normal((B, mlp.N_DESC))
+    tables, targets = [], []
+    for r in range(B):
+        n = [5, 0, 9][r]                      # an RVE with no slots contributes nothing
+        tables.append(dict(g=rng.standard_normal(n) + 1j * rng.standard_normal(n),
+                           a=rng.uniform(-0.5, 0.5, n), b=rng.uniform(0.01, 0.5, n),
+                           index=np.arange(n)))
+        targets.append(rng.standard_normal((n, 3)) + 1j * rng.standard_normal((n, 3)))
+    E = rng.standard_normal((B, 3))
+    loss, grads = mlp.loss_and_grads(params, X, tables, targets, E)
     h = 1e-6
     for p, g in zip(params, grads):
         for idx in [tuple(rng.integers(0, n) for n in p.shape) for _ in range(5)]:
             old = p[idx]
             p[idx] = old + h
-            lp, _ = mlp.loss_and_grads(params, X, T, ehat, mask)
+            lp, _ = mlp.loss_and_grads(params, X, tables, targets, E)
             p[idx] = old - h
-            lm, _ = mlp.loss_and_grads(params, X, T, ehat, mask)
+            lm, _ = mlp.loss_and_grads(params, X, tables, targets, E)
             p[idx] = old
-            assert math.isclose(g[idx], (lp - lm) / (2 * h), rel_tol=1e-6, abs_tol=1e-9)
-    # output units of slot 1 get gradient only from the samples where slot 1 is valid
-    X1 = X.copy()
-    mask_only1 = np.zeros_like(mask)
-    mask_only1[1] = mask[1]
-    _, g1 = mlp.loss_and_grads(params, X1, T, ehat, mask_only1)
-    assert np.all(g1[5][18:] == 0)
+            assert math.isclose(g[idx], (lp - lm) / (2 * h), rel_tol=1e-6, abs_tol=1e-10)
 
 
 def test_adam_first_step():
@@ -79,30 +146,46 @@ def test_adam_first_step():
     assert np.allclose(m[0], 0.1 * g[0]) and np.allclose(v[0], 0.001 * g[0] ** 2)
 
 
-def test_features_match_definition():
-    pm = centred_disc(12, 0.3)
-    pat = np.array([[0, 0, 0], [1, 2, 0], [-1, -2, 0]])
-    f = mlp.features(pm, 1, pat, 4)
-    assert np.isclose(f[0], pm.mean()) and f[1] == 0.0      # g^(0)/N = volume fraction
-    gh = np.fft.fft2((pm == 1).astype(float))[2, 1] / pm.size
-    assert np.isclose(f[4], gh.real) and np.isclose(f[5], gh.imag)
-    assert np.allclose(f[6:8], [1 / 12, 2 / 12])
-    assert np.isclose(f[8], gh.real) and np.isclose(f[9], -gh.imag)   # conjugate frequency
-    assert np.all(f[12:16] == 0)                               # missing slot
+def _full_pattern(n):
+    return np.array([[kx, ky, 0] for ky in range(-(n - 1) // 2, n // 2 + 1)
+                     for kx in range(-(n - 1) // 2, n // 2 + 1)])
 
 
-def test_targets_and_warm_coefficients_round_trip():
+def test_descriptors_sum_rules_and_symmetry():
+    pm = centred_disc(24, 0.3)
+    pat = _full_pattern(24)
+    x = mlp.descriptors(pm, 1, pat)
+    assert np.isclose(x[0], pm.mean())
+    # Parseval: all nonzero power = vf - vf^2 (g^2 = g), split over the radial bins
+    assert np.isclose(x[41] ** 2, pm.mean() - pm.mean() ** 2)
+    assert np.isclose(np.sum(x[1:25] ** 2), x[41] ** 2)
+    # a centred pixel disc is symmetric under 90-degree rotation and mirrors: no cos 2t, sin 2t
+    assert np.allclose(x[25:41:4], 0, atol=1e-12) and np.allclose(x[26:41:4], 0, atol=1e-12)
+    assert np.all(x[42:] == 0)
+    # a laminate along x has all its power at ky = 0 (t = 0): cos 2t = cos 4t = 1 in every band
+    lam = laminate((24, 24), (14, 10))           # layers normal to x: power only at ky = 0
+    xl = mlp.descriptors(lam, 1, pat)
+    band = [xl[25 + 4 * j:29 + 4 * j] for j in range(4) if xl[1 + 6 * j:7 + 6 * j].any()]
+    assert band
+    for c2, s2, c4, s4 in band:
+        assert np.isclose(c2, 1.0) and np.isclose(s2, 0.0, atol=1e-12)
+        assert np.isclose(c4, 1.0) and np.isclose(s4, 0.0, atol=1e-12)
+
+
+def test_targets_pick_the_slot_components():
     rng = np.random.default_rng(3)
-    K, S, N = 7, 5, 144
+    pm = random_discs(16, (2.0, 4.0), 0.3, seed=5)
+    pat = O.pattern_adapted(pm, 1, 20)
+    st = mlp.slots(pm, 1, pat)
+    K = len(pat)
     eh = rng.standard_normal((K, 3, 3)) + 1j * rng.standard_normal((K, 3, 3))
     eh = 0.5 * (eh + eh.transpose(0, 2, 1))
     macro = np.array([0.01, -0.004, 0, 0, 0, 0.003])
-    t = mlp.targets(eh, N, macro, S)
-    w = mlp.warm_coefficients(t, N, macro, K)
-    for s in range(S):
-        assert np.allclose(w[s, [0, 1, 5], 0], [eh[s, 0, 0].real, eh[s, 1, 1].real, eh[s, 0, 1].real])
-        assert np.allclose(w[s, [0, 1, 5], 1], [eh[s, 0, 0].imag, eh[s, 1, 1].imag, eh[s, 0, 1].imag])
-    assert np.all(w[S:] == 0) and np.all(w[:, 2:5] == 0)
+    t = mlp.targets(eh, pm.size, macro, st)
+    _, en = mlp.unit_direction(macro)
+    i = st["index"]
+    assert np.allclose(t[:, 2], eh[i, 0, 1] / (pm.size * en))
+    assert len(i) == K - 1 and not np.any(np.all(np.asarray(pat)[i, :2] == 0, axis=1))
 
 
 def test_elastic_fixed_point_is_linear_in_macro_strain():
@@ -117,7 +200,3 @@ def test_elastic_fixed_point_is_linear_in_macro_strain():
     r2 = O.solve(pm, ph, e2, pat, tol=0.0, max_iter=6)
     r12 = O.solve(pm, ph, 2 * e1 - 3 * e2, pat, tol=0.0, max_iter=6)
     assert np.allclose(r12.eps_hat, 2 * r1.eps_hat - 3 * r2.eps_hat, rtol=1e-10, atol=1e-12)
-    # so does the target scaled by 1/(N |ebar|), contracted with the unit direction
-    t1 = mlp.targets(r1.eps_hat, pm.size, e1, 10)
-    t1s = mlp.targets(O.solve(pm, ph, 5 * e1, pat, tol=0.0, max_iter=6).eps_hat, pm.size, 5 * e1, 10)
-    assert np.allclose(t1, t1s, rtol=1e-10, atol=1e-14)
