@@ -149,7 +149,6 @@ struct FftRowArgs {
 
 template <int NC, bool PLASTIC, bool FINAL>
 __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
-  if (!FINAL && a.done && *a.done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.Nx;
   const int S = a.R * NC;              // real lines in this block
@@ -167,6 +166,8 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   for (int i = tid; i < a.Kx; i += blockDim.x) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
   for (int i = tid; i < P * L; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  grid_dep_wait();
+  if (!FINAL && a.done && *a.done) return;   // the same flag value for every thread
   __syncthreads();
   // spectra: line s = r * NC + c is the real (s even) or imaginary (s odd) carrier of p = s / 2
   // coefficients are loaded in register batches (both carriers), then scattered: the real
@@ -371,7 +372,6 @@ struct FftColArgs {
 
 // columns [col0, col0 + C) of a row-major [rows][ncols] array, batched over blockIdx.y
 __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
-  if (a.done && *a.done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, C = a.C;
   float2* tw = reinterpret_cast<float2*>(smem);
@@ -384,6 +384,8 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
   stage_twiddles(a.table, L, tw);
   if (a.in_list)
     for (int i = threadIdx.x; i < C * L; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  grid_dep_wait();
+  if (a.done && *a.done) return;   // the same flag value for every thread of the block
   __syncthreads();
   // loads are issued in batches of 8 per thread before they are stored, so their latencies overlap
   const int total = a.in_rows * C;
@@ -455,7 +457,8 @@ static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, c
   a.done = done;
   const size_t smem = cols_smem(L, a.C);
   dim3 grid((ncols + a.C - 1) / a.C, batch);
-  k_fft_cols<<<grid, 256, smem, c->stream>>>(a);
+  cudaError_t e = launch_pdl(k_fft_cols, grid, dim3(256), smem, c->stream, a);
+  if (e != cudaSuccess) return cuda_fail(e, "fft cols");
   return fft_check(c, "fft cols");
 }
 
@@ -520,7 +523,13 @@ void init_attributes_fft() {
 
 template <int NC, bool PL, bool FIN>
 static int fft_row_launch(rf_ctx* c, const FftRowArgs& a) {
-  k_fft_row<NC, PL, FIN><<<c->fft_blocks, 256, c->fft_smem, c->stream>>>(a);
+  if (FIN) {
+    k_fft_row<NC, PL, FIN><<<c->fft_blocks, 256, c->fft_smem, c->stream>>>(a);
+  } else {
+    cudaError_t e = launch_pdl(k_fft_row<NC, PL, FIN>, dim3(c->fft_blocks), dim3(256),
+                               c->fft_smem, c->stream, a);
+    if (e != cudaSuccess) return cuda_fail(e, "fft row");
+  }
   return fft_check(c, "fft row");
 }
 

@@ -230,6 +230,30 @@ struct rf_ctx {
 };
 
 namespace rfk {
+
+// Programmatic dependent launch: the kernel may be scheduled while its predecessor in the stream
+// drains; it runs its independent prologue (tables, shared-memory setup) and then calls
+// grid_dep_wait() before it reads anything the predecessor writes. Every block reaches the wait
+// before it exits, so completion stays transitive along the chain. Without the launch attribute
+// the wait returns at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // kernels.cu
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);

@@ -309,14 +309,16 @@ __global__ __launch_bounds__(kGammaBlock) void k_gamma(GammaArgs a, double Nd) {
   __shared__ bool last;
   const long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const bool act = h < a.Kh;
-  // independent loads first (flag, indices, wave vector), so that they overlap
-  const int dn = a.done ? __ldcg(a.done) : 0;
+  // the pattern's indices and wave vectors do not depend on the previous kernel: load them
+  // before waiting for it
   HIdx hi{0, 0, 0, 2};
   float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
   if (act) {
     hi = a.hidx[h];
     n = a.hn[h];
   }
+  grid_dep_wait();
+  const int dn = a.done ? __ldcg(a.done) : 0;
   if (dn) return;
   float diff = 0.f;
   if (act) {
@@ -675,8 +677,10 @@ int launch_gamma_finalize(rf_ctx* c, int splits, const int* done) {
   g.done = done;
   const unsigned gb = (unsigned)((c->Kh + kGammaBlock - 1) / kGammaBlock);
   trace_stage(c, 5);
-  if (c->nc == 3) k_gamma<3><<<gb, kGammaBlock, 0, c->stream>>>(g, (double)c->N);
-  else k_gamma<6><<<gb, kGammaBlock, 0, c->stream>>>(g, (double)c->N);
+  const cudaError_t le =
+      c->nc == 3 ? launch_pdl(k_gamma<3>, dim3(gb), dim3(kGammaBlock), 0, c->stream, g, (double)c->N)
+                 : launch_pdl(k_gamma<6>, dim3(gb), dim3(kGammaBlock), 0, c->stream, g, (double)c->N);
+  if (le != cudaSuccess) return cuda_fail(le, "gamma");
   int e = launch_check(c, "gamma");
   trace_end(c);
   return e;
