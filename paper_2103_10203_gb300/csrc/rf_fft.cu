@@ -23,28 +23,30 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Stage-major twiddles: for the radix-4 stage with sub-transform size Ns the butterfly at
-// position k < Ns needs exp(+2 pi i r k / (4 Ns)), r = 1, 2, 3; they are stored contiguously in k
-// (three arrays per stage) so that neighbouring threads read neighbouring words. A final
-// radix-2 stage (log2 L odd) stores exp(+2 pi i k / (2 Ns)). Total entries < 3 L / 2.
-// Built once per block from the global table tab[t] = exp(+2 pi i t / L).
+// Shared-memory layout of the line buffers: element i lives at sw(i), which permutes the low four
+// index bits by the next four, so that the stride-16 stores of a first radix-16 stage fall into
+// different banks while unit-stride accesses stay conflict-free.
+__device__ __forceinline__ int sw(int i) { return i ^ ((i >> 4) & 15); }
+
+// Stage plan for length L = 2^lg: radix-16 stages while four index bits remain, then one radix-4
+// stage if two remain, then one radix-2 stage if one remains. Stage-major twiddles: a stage with
+// sub-transform size Ns and radix R needs exp(+2 pi i r k / (R Ns)), r = 1..R-1, k < Ns, stored
+// as R - 1 arrays contiguous in k (neighbouring threads read neighbouring words). Built once per
+// block from the global table tab[t] = exp(+2 pi i t / L). Total entries < L.
 __device__ int stage_twiddles(const float2* tab, int L, float2* tw) {
   int off = 0;
   int Ns = 1;
-  while (Ns * 4 <= L) {
-    const int step = L / (4 * Ns);
-    for (int k = threadIdx.x; k < Ns; k += blockDim.x) {
-      tw[off + k] = tab[k * step];
-      tw[off + Ns + k] = tab[2 * k * step];
-      tw[off + 2 * Ns + k] = tab[3 * k * step];
+  for (int R : {16, 4, 2}) {
+    while (Ns * R <= L) {
+      const int step = L / (R * Ns);
+      for (int i = threadIdx.x; i < (R - 1) * Ns; i += blockDim.x) {
+        const int r = 1 + i / Ns, k = i - (r - 1) * Ns;
+        tw[off + i] = tab[r * k * step];
+      }
+      off += (R - 1) * Ns;
+      Ns *= R;
+      if (R != 16) break;   // at most one radix-4 and one radix-2 stage
     }
-    off += 3 * Ns;
-    Ns *= 4;
-  }
-  if (Ns < L) {
-    const int step = L / (2 * Ns);
-    for (int k = threadIdx.x; k < Ns; k += blockDim.x) tw[off + k] = tab[k * step];
-    off += Ns;
   }
   return off;
 }
@@ -55,23 +57,86 @@ __host__ __device__ constexpr int ilog2(int v) {
   return r;
 }
 
+// v0..v3 <- their 4-point DFT with kernel exp(sign 2 pi i r q / 4)
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, int sign) {
+  const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y);
+  const float2 d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
+  const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y);
+  const float2 d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
+  const float2 id13 = sign < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
+  a0 = make_float2(s02.x + s13.x, s02.y + s13.y);
+  a1 = make_float2(d02.x + id13.x, d02.y + id13.y);
+  a2 = make_float2(s02.x - s13.x, s02.y - s13.y);
+  a3 = make_float2(d02.x - id13.x, d02.y - id13.y);
+}
+
+// 16-point DFT in registers as 4 x 4 (n = n1 + 4 n2, q = q2 + 4 q1): 4-point DFTs over n2,
+// the twiddles exp(sign 2 pi i n1 q2 / 16), 4-point DFTs over n1. Result X[q] lands in
+// v[4 (q & 3) + (q >> 2)].
+__device__ __forceinline__ void dft16(float2* v, int sign) {
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) dft4(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12], sign);
+  // cos and sin of 2 pi m / 16 for m = 1, 2, 3 (exact constants of the 16-point kernel)
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+  const float sg = sign < 0 ? -1.f : 1.f;
+  // (n1, q2) -> m = n1 q2 in {1, 2, 3, 2, 4, 6, 3, 6, 9}
+  const float2 w[10] = {make_float2(1.f, 0.f),     make_float2(c1, sg * s1),
+                        make_float2(h, sg * h),     make_float2(s1, sg * c1),
+                        make_float2(0.f, sg),       make_float2(-s1, sg * c1),
+                        make_float2(-h, sg * h),    make_float2(-c1, sg * s1),
+                        make_float2(-1.f, 0.f),     make_float2(-c1, -sg * s1)};
+#pragma unroll
+  for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+    for (int q2 = 1; q2 < 4; ++q2) v[n1 + 4 * q2] = cmul(v[n1 + 4 * q2], w[n1 * q2]);
+#pragma unroll
+  for (int q2 = 0; q2 < 4; ++q2) dft4(v[4 * q2], v[4 * q2 + 1], v[4 * q2 + 2], v[4 * q2 + 3], sign);
+}
+
 // Batched in-shared-memory FFT of P sequences of length L = 2^lg, sign -1 forward, +1 inverse
-// (unnormalised). Sequence p occupies [p * L, (p + 1) * L) of both buffers. Out-of-place
-// Stockham radix-4 with a final radix-2 stage when lg is odd. Returns the buffer holding the
-// result. The whole block calls it.
+// (unnormalised). Sequence p occupies [p L, (p + 1) L) of both buffers (swizzled by sw).
+// Out-of-place Stockham stages after the plan above. Returns the buffer holding the result. The
+// whole block calls it.
 __device__ float2* fft_block(float2* in, float2* out, const float2* tw, int lg, int P, int sign) {
   const int L = 1 << lg;
-  const int lq = lg - 2;          // log2 (L / 4)
-  const int q = L >> 2;
   int off = 0;
-  int ls = 0;                     // log2 Ns
-  while (ls + 2 <= lg) {
-    const int Ns = 1 << ls;
+  int ls = 0;   // log2 Ns
+  while (ls + 4 <= lg) {   // radix-16
+    const int Ns = 1 << ls, lq = lg - 4, q = L >> 4;
     for (int u = threadIdx.x; u < (P << lq); u += blockDim.x) {
       const int p = u >> lq, j = u & (q - 1);
-      const float2* src = in + (p << lg);
-      float2* dst = out + (p << lg);
-      float2 v0 = src[j], v1 = src[j + q], v2 = src[j + 2 * q], v3 = src[j + 3 * q];
+      const int base_in = (p << lg) + j;
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = in[sw(base_in + r * q)];
+      const int k = j & (Ns - 1);
+      if (ls > 0) {
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+          float2 w = tw[off + (r - 1) * Ns + k];
+          if (sign < 0) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+      }
+      dft16(v, sign);
+      const int base = (p << lg) + ((j >> ls) << (ls + 4)) + k;
+#pragma unroll
+      for (int qq = 0; qq < 16; ++qq) out[sw(base + qq * Ns)] = v[4 * (qq & 3) + (qq >> 2)];
+    }
+    __syncthreads();
+    float2* t = in;
+    in = out;
+    out = t;
+    off += 15 * Ns;
+    ls += 4;
+  }
+  if (ls + 2 <= lg) {   // one radix-4 stage
+    const int Ns = 1 << ls, lq = lg - 2, q = L >> 2;
+    for (int u = threadIdx.x; u < (P << lq); u += blockDim.x) {
+      const int p = u >> lq, j = u & (q - 1);
+      const int base_in = (p << lg) + j;
+      float2 v0 = in[sw(base_in)], v1 = in[sw(base_in + q)], v2 = in[sw(base_in + 2 * q)],
+             v3 = in[sw(base_in + 3 * q)];
       const int k = j & (Ns - 1);
       if (ls > 0) {
         float2 w1 = tw[off + k], w2 = tw[off + Ns + k], w3 = tw[off + 2 * Ns + k];
@@ -84,17 +149,12 @@ __device__ float2* fft_block(float2* in, float2* out, const float2* tw, int lg, 
         v2 = cmul(v2, w2);
         v3 = cmul(v3, w3);
       }
-      const float2 s02 = make_float2(v0.x + v2.x, v0.y + v2.y);
-      const float2 d02 = make_float2(v0.x - v2.x, v0.y - v2.y);
-      const float2 s13 = make_float2(v1.x + v3.x, v1.y + v3.y);
-      const float2 d13 = make_float2(v1.x - v3.x, v1.y - v3.y);
-      // sign * i * d13
-      const float2 id13 = sign < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
-      const int base = ((j >> ls) << (ls + 2)) + k;
-      dst[base] = make_float2(s02.x + s13.x, s02.y + s13.y);
-      dst[base + Ns] = make_float2(d02.x + id13.x, d02.y + id13.y);
-      dst[base + 2 * Ns] = make_float2(s02.x - s13.x, s02.y - s13.y);
-      dst[base + 3 * Ns] = make_float2(d02.x - id13.x, d02.y - id13.y);
+      dft4(v0, v1, v2, v3, sign);
+      const int base = (p << lg) + ((j >> ls) << (ls + 2)) + k;
+      out[sw(base)] = v0;
+      out[sw(base + Ns)] = v1;
+      out[sw(base + 2 * Ns)] = v2;
+      out[sw(base + 3 * Ns)] = v3;
     }
     __syncthreads();
     float2* t = in;
@@ -104,20 +164,18 @@ __device__ float2* fft_block(float2* in, float2* out, const float2* tw, int lg, 
     ls += 2;
   }
   if (ls < lg) {   // one radix-2 stage
-    const int Ns = 1 << ls;
-    const int h = L >> 1, lh = lg - 1;
+    const int Ns = 1 << ls, lh = lg - 1, h = L >> 1;
     for (int u = threadIdx.x; u < (P << lh); u += blockDim.x) {
       const int p = u >> lh, j = u & (h - 1);
-      const float2* src = in + (p << lg);
-      float2* dst = out + (p << lg);
-      float2 v0 = src[j], v1 = src[j + h];
+      const int base_in = (p << lg) + j;
+      float2 v0 = in[sw(base_in)], v1 = in[sw(base_in + h)];
       const int k = j & (Ns - 1);
       float2 w = tw[off + k];
       if (sign < 0) w.y = -w.y;
       v1 = cmul(v1, w);
-      const int base = ((j >> ls) << (ls + 1)) + k;
-      dst[base] = make_float2(v0.x + v1.x, v0.y + v1.y);
-      dst[base + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+      const int base = (p << lg) + ((j >> ls) << (ls + 1)) + k;
+      out[sw(base)] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      out[sw(base + Ns)] = make_float2(v0.x - v1.x, v0.y - v1.y);
     }
     __syncthreads();
     in = out;
@@ -199,9 +257,9 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
       const int k = kxs[j];
       const bool self = (k == 0) || (2 * k == L);
       if (self) t.y = 0.f;
-      float2* z = b0 + (size_t)p * L;
-      z[k] = t;
-      if (!self) z[L - k] = make_float2(t.x, -t.y);
+      const int zb0 = p * L;
+      b0[sw(zb0 + k)] = t;
+      if (!self) b0[sw(zb0 + L - k)] = make_float2(t.x, -t.y);
     }
     __syncthreads();
 #pragma unroll
@@ -214,12 +272,14 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
       const int k = kxs[j];
       const bool self = (k == 0) || (2 * k == L);
       if (self) t.y = 0.f;
-      float2* z = b0 + (size_t)p * L;
-      z[k].x -= t.y;        // add i * t at k and i * conj(t) at L - k
-      z[k].y += t.x;
+      const int zb0 = p * L;
+      float2& zk = b0[sw(zb0 + k)];
+      zk.x -= t.y;        // add i * t at k and i * conj(t) at L - k
+      zk.y += t.x;
       if (!self) {
-        z[L - k].x += t.y;
-        z[L - k].y += t.x;
+        float2& zm = b0[sw(zb0 + L - k)];
+        zm.x += t.y;
+        zm.y += t.x;
       }
     }
     __syncthreads();
@@ -257,7 +317,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int s = r * NC + c;
-        const float2 z = zb[(size_t)(s >> 1) * L + x];
+        const float2 z = zb[sw((s >> 1) * L + x)];
         e[c] = ((s & 1) ? z.y : z.x) * a.invN;
       }
       float tau6[6] = {0, 0, 0, 0, 0, 0};
@@ -322,7 +382,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int s = r * NC + c;
-          float* dst = reinterpret_cast<float*>(other + (size_t)(s >> 1) * L + x);
+          float* dst = reinterpret_cast<float*>(other + sw((s >> 1) * L + x));
           dst[s & 1] = tau6[comp6<NC>(c)];
         }
       }
@@ -339,7 +399,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   }
   // an odd line count leaves the last sequence's imaginary carrier unused: zero it
   if (S & 1)
-    for (int x = tid; x < L; x += blockDim.x) other[(size_t)(P - 1) * L + x].y = 0.f;
+    for (int x = tid; x < L; x += blockDim.x) other[sw((P - 1) * L + x)].y = 0.f;
   __syncthreads();
   float2* zf = fft_block(other, zb, tw, lg, P, -1);
   for (int u = tid; u < S * a.Kx; u += blockDim.x) {
@@ -347,8 +407,8 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
     const int r = s / NC, c = s - r * NC, row = row0 + r;
     if (row >= a.rows) continue;
     const int k = kxs[j];
-    const float2* z = zf + (size_t)(s >> 1) * L;
-    const float2 zk = z[k], zm = z[(L - k) & (L - 1)];
+    const int zb0 = (s >> 1) * L;
+    const float2 zk = zf[sw(zb0 + k)], zm = zf[sw(zb0 + ((L - k) & (L - 1)))];
     float2 out;
     if ((s & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
@@ -405,7 +465,7 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      if (dst[u] >= 0) b0[dst[u]] = v[u];
+      if (dst[u] >= 0) b0[sw(dst[u])] = v[u];
   }
   __syncthreads();
   const float2* z = fft_block(b0, b1, tw, ilog2(L), C, a.sign);
@@ -413,7 +473,7 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
     const int r = i / C, cc = i - r * C, col = col0 + cc;
     if (col >= a.ncols) continue;
     const int pos = a.out_list ? a.out_list[r] : r;
-    out[(long long)r * a.ncols + col] = z[(size_t)cc * L + pos];
+    out[(long long)r * a.ncols + col] = z[sw(cc * L + pos)];
   }
 }
 
