@@ -56,9 +56,10 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_tf32"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
-                   help="c2: 1024^2 J2 load path (the headline line); c4: batch of 4096 RVEs of "
-                        "uneven size vs per-RVE solves; c5: learned warm start vs plain start")
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                   help="c2: 1024^2 J2 load path (the headline line); c3: 128^3 elastic spheres, "
+                        "split-BF16 tensor-core transforms; c4: batch of 4096 RVEs of uneven size "
+                        "vs per-RVE solves; c5: learned warm start vs plain start")
     p.add_argument("--rves", type=int, default=4096, help="c4 / c5: RVEs in the solved batch")
     p.add_argument("--train", type=int, default=50000, help="c5: training RVEs")
     p.add_argument("--epochs", type=int, default=20, help="c5: training epochs")
@@ -398,6 +399,96 @@ def run_learned(args, rf, torch):
     print(json.dumps(line), flush=True)
 
 
+def _tc_mma_flops(nx, rows, nc, Kx):
+    """Tensor-core FLOPs one k_tc_row launch issues (split operands: 3 products per GEMM), from
+    the kernel's tiling: 128-wide x slices, R rows per block (tensor-memory limit), Qp = R nc
+    padded to 16, the j' = 2 Kx range padded to 128."""
+    jt = (2 * Kx + 127) // 128
+    R = 16 if nc == 3 else 8
+    qp = lambda r: ((r * nc + 15) // 16) * 16
+    while R > 1 and qp(R) * (1 + jt) > 512:
+        R -= 1
+    blocks = ((nx + 127) // 128) * ((rows + R - 1) // R)
+    per_block = 3 * 2 * 128 * qp(R) * (jt * 128) * 2      # inverse + forward GEMMs
+    return blocks * per_block
+
+
+def run_3d(args, rf, torch):
+    """c3: one elastic 128^3 solve to 1e-6 from the plain start per step, split-BF16 tensor-core
+    x transforms (pruned DFT); the FP32 FFT mode timed beside it."""
+    from synth import make_config
+    cfg = make_config("c3")
+    pm, ph, macro = cfg["phase_map"], cfg["phases"], cfg["macro"]
+    K = cfg["k_target"]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    pattern = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
+    prec = args.precision if args.precision != "fp32" else "split_bf16"
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(solver, steps, warmup):
+        for _ in range(warmup):
+            solver.rf_solve(macro)
+        ms, its = [], 0
+        for s in range(steps):
+            flush.fill_(float(s))
+            out, t = _timed(torch, stream, lambda: solver.rf_solve(macro))
+            ms.append(t)
+            its += out["iters"]
+        return float(np.sum(ms)), its, out
+
+    solver = rf.Solver(pm, ph, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER,
+                       transform="dft", precision=prec)
+    info = solver.rf_get_info()
+    l0 = info["kernel_launches"]
+    with ClockSampler(gpu_id_for(torch, torch.cuda.current_device())) as clk:
+        total_ms, its, out = timed(solver, args.steps, args.warmup)
+        launches = solver.rf_get_info()["kernel_launches"] - l0
+        solver.rf_set_tracing(True)
+        solver.rf_reset_stage_times()
+        for _ in range(args.steps):
+            solver.rf_solve(macro)
+        solver.rf_set_tracing(False)
+    stage = solver.rf_get_stage_times()
+    solver.close()
+    fft = rf.Solver(pm, ph, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER,
+                    transform="fft", precision="fp32")
+    f_ms, f_its, _ = timed(fft, 1, 1)
+    fft.close()
+    nz, ny, nx = pm.shape
+    N = pm.size
+    value = its * N / (total_ms / 1e3)
+    row_ms = stage["row"][0] / max(1, stage["row"][1])
+    mma = _tc_mma_flops(nx, ny * nz, 6, info["Kx"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+    peak = peaks["bf16_tflops"] if prec == "split_bf16" else peaks["bf16_tflops"] / 2
+    achieved = mma / (row_ms / 1e3) / 1e12
+    real = {k: v for k, v in stage.items() if v[1] > 0}
+    line = {"metric": "RVE voxel-iterations/s to 1e-6 residual (plain start)", "value": value,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"split_bf16": "bf16x3", "split_tf32": "tf32x3"}[prec],
+            "data": "synthetic",
+            "config": {"workload": "3D 128^3 elastic spheres (vf 0.25, r 6-12), random symmetric "
+                                   "macro strain, adapted reduced set K=2%",
+                       "K": int(K), "tol": TOL, "transform": "dft", "precision": prec,
+                       "l2": "flushed before every timed step (256 MB write)"},
+            "iterations_per_solve": its / args.steps, "gpu_launches": int(launches),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_tc_row", "launch_ms": row_ms,
+                         "mma_flops_per_launch": mma,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 burst)"
+                                        + ("" if prec == "split_bf16" else " / 2 (TF32 nominal ratio)")},
+            "stage_share": {k: round(v[0] / sum(x[0] for x in real.values()), 4)
+                            for k, v in real.items()},
+            "fft_fp32": {"value": f_its * N / (f_ms / 1e3), "unit": UNIT, "iterations": f_its},
+            "clocks": clk.summary(),
+            "sigma_bar": [float(x) for x in out["sigma_bar"]]}
+    print(json.dumps(line), flush=True)
+
+
 def _hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(p))["hbm_gbs"] if os.path.exists(p) else 6800.0
@@ -416,6 +507,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2103_10203_gb300 import rf
+    if args.workload == "c3":
+        return run_3d(args, rf, torch)
     if args.workload == "c4":
         return run_batch(args, rf, torch)
     if args.workload == "c5":
