@@ -134,6 +134,9 @@ void free_graphs(rf_ctx* c) {
   for (auto& g : c->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
+  if (c->while_exec) cudaGraphExecDestroy(c->while_exec);
+  c->while_exec = nullptr;
+  c->while_failed = false;
   for (auto& t : c->graph_traces)
     for (int i = 0; i <= t.n; ++i)
       if (t.ev[i]) cudaEventDestroy(t.ev[i]);
@@ -180,6 +183,65 @@ int get_graph(rf_ctx* c, int chunk, rf_ctx::GraphEntry** out) {
   for (size_t i = first; i < c->graph_traces.size(); ++i) g.trace_first.push_back((int)i);
   c->graphs.push_back(g);
   *out = &c->graphs.back();
+  return RF_OK;
+}
+
+// One graph for a whole solve: a conditional while node whose body is kWhileBody updates; the
+// Green kernel's last block clears the condition when it sets the done flag (converged, capped,
+// non-finite or timed out), so the loop ends with the body in which the solve finished (updates
+// after that return at once). If the graph cannot be built here, the solve falls back to
+// replayed chunks of updates.
+constexpr int kWhileBody = 8;
+
+int get_while_graph(rf_ctx* c) {
+  if (c->while_exec || c->while_failed) return RF_OK;
+  cudaGraph_t graph = nullptr;
+  auto give_up = [&]() {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    c->while_failed = true;
+    return RF_OK;
+  };
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return give_up();
+  cudaGraphConditionalHandle h = 0;
+  if (cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+    return give_up();
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) != cudaSuccess) return give_up();
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  c->while_cond = h;
+  const long long launched = c->launched_iters;
+  const long long kernels0 = c->launches;
+  if (cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return give_up();
+  const bool tr = c->tracing;
+  c->tracing = false;
+  c->capturing = true;
+  c->capturing_while = true;
+  int err = RF_OK;
+  for (int i = 0; i < kWhileBody && !err; ++i) err = launch_iteration(c);
+  c->capturing = false;
+  c->capturing_while = false;
+  c->tracing = tr;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->stream, &captured);
+  c->launched_iters = launched;
+  c->while_kernels = c->launches - kernels0;
+  c->launches = kernels0;
+  if (err || ce != cudaSuccess) {
+    set_error("");
+    return give_up();
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) return give_up();
+  cudaGraphDestroy(graph);
+  c->while_exec = exec;
   return RF_OK;
 }
 
@@ -244,7 +306,16 @@ int init_status(rf_ctx* c, const double* macro) {
 int run_iterations(rf_ctx* c) {
   const int maxchunk = c->opt.check_every > 0 ? c->opt.check_every : 32;
   int chunk = std::min(4, maxchunk);
-  for (;;) {
+  if (!c->tracing) get_while_graph(c);
+  if (!c->tracing && c->while_exec) {
+    if (int e = ck(cudaGraphLaunch(c->while_exec, c->stream), "graph launch")) return e;
+    if (int e = ck(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status),
+                                   cudaMemcpyDeviceToHost, c->stream), "read status"))
+      return e;
+    if (int e = ck(cudaStreamSynchronize(c->stream), "iterate")) return e;
+    c->launched_iters = c->h_status->iters;
+    c->launches += c->while_kernels * ((c->h_status->iters + kWhileBody - 1) / kWhileBody);
+  } else for (;;) {
     rf_ctx::GraphEntry* g = nullptr;
     if (int e = get_graph(c, chunk, &g)) return e;
     const long long base = c->launched_iters;

@@ -112,6 +112,9 @@ struct GammaArgs {
   unsigned* counter;    // blocks finished (reset to 0 by the last block)
   double* part;         // [gridDim.x]
   const int* done;
+  // while-loop graph: the last block clears the loop condition when it sets done
+  cudaGraphConditionalHandle cond;
+  int use_cond;
 };
 
 }  // namespace rfk
@@ -203,6 +206,12 @@ struct rf_ctx {
     long long kernels;              // kernel nodes in the graph (counted at every replay)
   };
   std::vector<GraphEntry> graphs;
+  // one-launch solve: a conditional while node whose body is one update (untraced solves)
+  cudaGraphExec_t while_exec = nullptr;
+  cudaGraphConditionalHandle while_cond = 0;
+  long long while_kernels = 0;   // kernel nodes per body
+  bool while_failed = false;     // this pattern's graph could not be built: use chunks
+  bool capturing_while = false;
   bool own_stream = false;
   bool capturing = false;
 

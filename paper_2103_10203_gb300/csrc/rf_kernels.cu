@@ -296,7 +296,7 @@ __device__ void decide(const double* part, int n, Status* st, double* sh) {
     if (!isfinite(r)) {
       st->nonfinite = 1;
       st->done = 1;
-    } else if (r < st->tol || st->iters >= st->max_iter) {
+    } else if (r < st->tol || st->iters >= st->max_iter || st->timeout) {
       st->done = 1;
     }
   }
@@ -395,7 +395,11 @@ __global__ __launch_bounds__(kGammaBlock) void k_gamma(GammaArgs a, double Nd) {
   if (last) {
     __threadfence();
     decide(a.part, gridDim.x, a.status, sh);
-    if (threadIdx.x == 0) *a.counter = 0u;
+    if (threadIdx.x == 0) {
+      *a.counter = 0u;
+      // the only call site of the loop condition: one thread of one block per update
+      if (a.use_cond && a.status->done) cudaGraphSetConditional(a.cond, 0u);
+    }
   }
 }
 
@@ -675,6 +679,8 @@ int launch_gamma_finalize(rf_ctx* c, int splits, const int* done) {
   g.counter = c->d_counter;
   g.part = c->d_part;
   g.done = done;
+  g.cond = c->while_cond;
+  g.use_cond = c->capturing_while ? 1 : 0;
   const unsigned gb = (unsigned)((c->Kh + kGammaBlock - 1) / kGammaBlock);
   trace_stage(c, 5);
   const cudaError_t le =
