@@ -517,7 +517,7 @@ static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, c
   a.done = done;
   const size_t smem = cols_smem(L, a.C);
   dim3 grid((ncols + a.C - 1) / a.C, batch);
-  cudaError_t e = launch_pdl(k_fft_cols, grid, dim3(256), smem, c->stream, a);
+  cudaError_t e = launch_pdl(k_fft_cols, grid, dim3(c->fft_col_threads), smem, c->stream, a);
   if (e != cudaSuccess) return cuda_fail(e, "fft cols");
   return fft_check(c, "fft cols");
 }
@@ -584,9 +584,9 @@ void init_attributes_fft() {
 template <int NC, bool PL, bool FIN>
 static int fft_row_launch(rf_ctx* c, const FftRowArgs& a) {
   if (FIN) {
-    k_fft_row<NC, PL, FIN><<<c->fft_blocks, 256, c->fft_smem, c->stream>>>(a);
+    k_fft_row<NC, PL, FIN><<<c->fft_blocks, c->fft_row_threads, c->fft_smem, c->stream>>>(a);
   } else {
-    cudaError_t e = launch_pdl(k_fft_row<NC, PL, FIN>, dim3(c->fft_blocks), dim3(256),
+    cudaError_t e = launch_pdl(k_fft_row<NC, PL, FIN>, dim3(c->fft_blocks), dim3(c->fft_row_threads),
                                c->fft_smem, c->stream, a);
     if (e != cudaSuccess) return cuda_fail(e, "fft row");
   }
@@ -677,39 +677,51 @@ int fft_autotune(rf_ctx* c) {
   };
   if (!err && c->opt.fft_rows <= 0) {
     float best = 1e30f;
-    int bestR = c->fft_R;
+    int bestR = c->fft_R, bestT = c->fft_row_threads;
     for (int R : {1, 2, 4, 8, 16}) {
       if (R > c->rows || row_smem(c->nx, c->nc, c->Kx, R) > kFftSmemMax) continue;
-      set_rows(c, R);
-      float ms = 0.f;
-      err = time_it([&] { return launch_fft_row(c, nullptr, false, 0); }, &ms);
-      if (err) break;
-      if (ms < best) {
-        best = ms;
-        bestR = R;
+      for (int T : {128, 256}) {
+        set_rows(c, R);
+        c->fft_row_threads = T;
+        float ms = 0.f;
+        err = time_it([&] { return launch_fft_row(c, nullptr, false, 0); }, &ms);
+        if (err) break;
+        if (ms < best) {
+          best = ms;
+          bestR = R;
+          bestT = T;
+        }
       }
+      if (err) break;
     }
     set_rows(c, bestR);
+    c->fft_row_threads = bestT;
   }
   if (!err && c->opt.fft_cols <= 0) {
     const int Lc = std::max(c->ny, c->dim == 3 ? c->nz : 1);
     float best = 1e30f;
-    int bestC = c->fft_C;
+    int bestC = c->fft_C, bestT = c->fft_col_threads;
     for (int C : {1, 2, 4, 8, 16, 32}) {
       if (cols_smem(Lc, C) > kFftSmemMax) continue;
-      c->fft_C = C;
-      float ms = 0.f;
-      err = time_it([&] {
-        if (int e = fft_inverse_stages(c, nullptr)) return e;
-        return fft_forward_stages(c, nullptr);
-      }, &ms);
-      if (err) break;
-      if (ms < best) {
-        best = ms;
-        bestC = C;
+      for (int T : {64, 128, 256}) {
+        c->fft_C = C;
+        c->fft_col_threads = T;
+        float ms = 0.f;
+        err = time_it([&] {
+          if (int e = fft_inverse_stages(c, nullptr)) return e;
+          return fft_forward_stages(c, nullptr);
+        }, &ms);
+        if (err) break;
+        if (ms < best) {
+          best = ms;
+          bestC = C;
+          bestT = T;
+        }
       }
+      if (err) break;
     }
     c->fft_C = bestC;
+    c->fft_col_threads = bestT;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -182,6 +182,7 @@ struct rf_ctx {
 
   // FFT transform mode
   int fft_R = 0, fft_blocks = 0, fft_C = 0;
+  int fft_row_threads = 256, fft_col_threads = 256;   // block sizes (autotuned with the tiles)
   size_t fft_smem = 0;
 
   // split-precision (tensor-core) transforms along x
