@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/rf_mlp.h"
+#include "rf_fftcore.cuh"
 #include "rf_internal.cuh"
 #include "rf_law.cuh"
 
@@ -40,6 +41,7 @@ struct BDesc {
   long long off_part;    // double, chunks
   long long off_spart;   // double, row_items * 6
   int tab_x, tab_y;      // offsets into the twiddle buffer
+  int fft;               // row items use FFTs along x (Nx = 2^b or 3 2^b), else the pruned DFT
   long long zero_base;   // ER offset (within the RVE) of the zero frequency
   float lam0, mu0, inv2mu0, cgam;
 };
@@ -153,6 +155,106 @@ __global__ __launch_bounds__(256) void kb_fwd_y(BArgs a) {
 
 // row tiles: R rows of one RVE; inverse x transform, law, forward x transform (FINAL: stress
 // partials instead of the forward transform)
+// Row item by FFTs along x (the transform mode of the single-RVE solver, for Nx = 2^b or 3 2^b):
+// two real lines per complex sequence, Hermitian completion of the lines' kx >= 0 coefficients,
+// inverse FFT, elastic law and polarization per voxel, forward FFT, separation of the two lines'
+// spectra at the pattern's kx columns. Final pass: homogenised-stress partials instead.
+__device__ void row_item_fft(const BArgs& a, int2 w, const BDesc& d, unsigned char* smem,
+                             double* red) {
+  using namespace fftc;
+  const int L = d.nx, Kx = d.Kx, R = d.R;
+  const int row0 = w.y * R;
+  const int nr = min(R, d.rows - row0);
+  const int S = nr * NC, P = (S + 1) / 2;
+  const int span = ((P * L + 15) / 16) * 16;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* b0 = tw + L;
+  float2* b1 = b0 + span;
+  int* kxs = reinterpret_cast<int*>(b1 + span);
+  const int tid = threadIdx.x;
+  stage_twiddles(a.tab + d.tab_x, L, tw);
+  for (int i = tid; i < Kx; i += blockDim.x) kxs[i] = a.kx[d.off_kx + i];
+  for (int i = tid; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // z_p = line 2p + i line 2p+1: z[k] = ta + i tb, z[L - k] = conj(ta) + i conj(tb)
+  const float2* Tg = a.T1 + d.off_t1 + (long long)row0 * NC * Kx;
+  for (int u = tid; u < P * Kx; u += blockDim.x) {
+    const int p = u / Kx, j = u - p * Kx;
+    const int s0 = 2 * p, s1 = s0 + 1;
+    float2 ta = Tg[(long long)s0 * Kx + j];   // line s = r NC + c is row r, component c
+    float2 tb = s1 < S ? Tg[(long long)s1 * Kx + j] : make_float2(0.f, 0.f);
+    const int k = kxs[j];
+    const bool self = (k == 0) || (2 * k == L);
+    if (self) {
+      ta.y = 0.f;
+      tb.y = 0.f;
+    }
+    b0[sw(p * L + k)] = make_float2(ta.x - tb.y, ta.y + tb.x);
+    if (!self) b0[sw(p * L + L - k)] = make_float2(ta.x + tb.y, tb.x - ta.y);
+  }
+  __syncthreads();
+  float2* zb = fft_block(b0, b1, tw, L, P, +1);
+  float2* other = (zb == b0) ? b1 : b0;
+  const float invN = 1.f / (float)d.N;
+  double sb[6] = {0, 0, 0, 0, 0, 0};
+  for (int v = tid; v < nr * L; v += blockDim.x) {
+    const int r = v / L, x = v - r * L;
+    float e[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int sl = r * NC + c;
+      const float2 z = zb[sw((sl >> 1) * L + x)];
+      e[c] = ((sl & 1) ? z.y : z.x) * invN;
+    }
+    float e6[6];
+    comp_to6<NC>(e, e6);
+    const long long g = (long long)(row0 + r) * L + x;
+    const DevPhase ph = a.law.ph[a.phase[d.off_phase + g]];
+    float ep[6] = {0, 0, 0, 0, 0, 0};
+    LawOut o;
+    stress6<false>(e6, ph, ep, 0.f, o);
+    if (a.final_pass) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
+    } else {
+      const float tr = e6[0] + e6[1] + e6[2];
+      float tau6[6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (d.lam0 * tr + 2.f * d.mu0 * e6[i]);
+#pragma unroll
+      for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * d.mu0 * e6[i];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int sl = r * NC + c;
+        float* dst = reinterpret_cast<float*>(other + sw((sl >> 1) * L + x));
+        dst[sl & 1] = tau6[comp6<NC>(c)];
+      }
+    }
+  }
+  if (a.final_pass) {
+    for (int i = 0; i < 6; ++i) {
+      const double t = block_sum_d(sb[i], red);
+      if (tid == 0) a.spart[d.off_spart + (long long)w.y * 6 + i] = t;
+    }
+    return;
+  }
+  if (S & 1)
+    for (int x = tid; x < L; x += blockDim.x) other[sw((P - 1) * L + x)].y = 0.f;
+  __syncthreads();
+  float2* zf = fft_block(other, zb, tw, L, P, -1);
+  float2* To = a.T1p + d.off_t1 + (long long)row0 * NC * Kx;
+  for (int u = tid; u < S * Kx; u += blockDim.x) {
+    const int sl = u / Kx, j = u - sl * Kx;
+    const int k = kxs[j];
+    const int base = (sl >> 1) * L;
+    const float2 zk = zf[sw(base + k)], zm = zf[sw(base + (k == 0 ? 0 : L - k))];
+    float2 out;
+    if ((sl & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    To[(long long)sl * Kx + j] = out;
+  }
+}
+
 __global__ __launch_bounds__(256) void kb_row(BArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[8];
@@ -160,6 +262,12 @@ __global__ __launch_bounds__(256) void kb_row(BArgs a) {
     const int2 w = a.items[it];
     if (!a.final_pass && rve_done(a, w.x)) continue;
     const BDesc d = a.d[w.x];
+    if (d.fft) {
+      __syncthreads();   // the previous item's shared-memory reads are done
+      row_item_fft(a, w, d, smem, red);
+      __syncthreads();
+      continue;
+    }
     const int Nx = d.nx, Kx = d.Kx, R = d.R;
     const int row0 = w.y * R;
     const int nr = min(R, d.rows - row0);
@@ -627,6 +735,7 @@ struct rf_batch {
   int grid = 0;
   size_t row_smem = 0;
   int R_choice[5] = {0, 0, 0, 0, 0};   // rows per row item, per size class (autotuned)
+  bool use_fft = true;                 // FFT row items where Nx allows
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
   long long launches = 0;
   int last_max_iters = 0;
@@ -702,9 +811,15 @@ int build_row_items(rf_batch* b) {
     d.R = std::max(1, std::min(b->R_choice[size_class(std::max(d.nx, d.ny))], d.rows));
     d.row_items = (d.rows + d.R - 1) / d.R;
     for (int k = 0; k < d.row_items; ++k) items.push_back(make_int2(r, k));
-    const size_t s = (size_t)d.nx * sizeof(float2) + (size_t)d.R * NC * d.Kx * sizeof(float2) +
-                     (size_t)d.Kx * 8 + (size_t)d.R * NC * d.nx * sizeof(float) + 64;
-    smem = std::max(smem, s);
+    const size_t s_dft = (size_t)d.nx * sizeof(float2) + (size_t)d.R * NC * d.Kx * sizeof(float2) +
+                         (size_t)d.Kx * 8 + (size_t)d.R * NC * d.nx * sizeof(float) + 64;
+    const int P = (d.R * NC + 1) / 2;
+    const size_t span = (((size_t)P * d.nx + 15) / 16) * 16;
+    const size_t s_fft = (size_t)d.nx * sizeof(float2) + 2 * span * sizeof(float2) +
+                         (size_t)d.Kx * sizeof(int) + 64;
+    const int p2 = d.nx % 3 == 0 ? d.nx / 3 : d.nx;
+    d.fft = (b->use_fft && p2 >= 1 && (p2 & (p2 - 1)) == 0 && s_fft <= 160 * 1024) ? 1 : 0;
+    smem = std::max(smem, d.fft ? s_fft : s_dft);
   }
   for (int r = 0; r < b->n; ++r) {
     b->desc[r].off_spart = spart;

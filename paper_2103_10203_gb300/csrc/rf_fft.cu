@@ -7,183 +7,22 @@
 // transforms forward and separates the two lines' spectra at the pattern's kx columns.
 // Along y and z (column kernel): sparse spectra (the pattern's distinct ky or kz values) are
 // scattered into full-length sequences for the inverse; the forward keeps only those values.
-// The transforms are out-of-place Stockham radix-4 (plus one radix-2 stage when log2 L is odd)
-// in shared memory, with an FP32 twiddle table computed in FP64.
+// The transforms are out-of-place Stockham stages in shared memory (rf_fftcore.cuh), with an
+// FP32 twiddle table computed in FP64.
 #include <algorithm>
 #include <cmath>
 
+#include "rf_fftcore.cuh"
 #include "rf_internal.cuh"
 #include "rf_law.cuh"
 
 namespace rfk {
 
-namespace {
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// Shared-memory layout of the line buffers: element i lives at sw(i), which permutes the low four
-// index bits by the next four, so that the stride-16 stores of a first radix-16 stage fall into
-// different banks while unit-stride accesses stay conflict-free.
-__device__ __forceinline__ int sw(int i) { return i ^ ((i >> 4) & 15); }
-
-// Stage plan for length L = 2^lg: radix-16 stages while four index bits remain, then one radix-4
-// stage if two remain, then one radix-2 stage if one remains. Stage-major twiddles: a stage with
-// sub-transform size Ns and radix R needs exp(+2 pi i r k / (R Ns)), r = 1..R-1, k < Ns, stored
-// as R - 1 arrays contiguous in k (neighbouring threads read neighbouring words). Built once per
-// block from the global table tab[t] = exp(+2 pi i t / L). Total entries < L.
-__device__ int stage_twiddles(const float2* tab, int L, float2* tw) {
-  int off = 0;
-  int Ns = 1;
-  for (int R : {16, 4, 2}) {
-    while (Ns * R <= L) {
-      const int step = L / (R * Ns);
-      for (int i = threadIdx.x; i < (R - 1) * Ns; i += blockDim.x) {
-        const int r = 1 + i / Ns, k = i - (r - 1) * Ns;
-        tw[off + i] = tab[r * k * step];
-      }
-      off += (R - 1) * Ns;
-      Ns *= R;
-      if (R != 16) break;   // at most one radix-4 and one radix-2 stage
-    }
-  }
-  return off;
-}
-
-__host__ __device__ constexpr int ilog2(int v) {
-  int r = 0;
-  while ((1 << r) < v) ++r;
-  return r;
-}
-
-// v0..v3 <- their 4-point DFT with kernel exp(sign 2 pi i r q / 4)
-__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3, int sign) {
-  const float2 s02 = make_float2(a0.x + a2.x, a0.y + a2.y);
-  const float2 d02 = make_float2(a0.x - a2.x, a0.y - a2.y);
-  const float2 s13 = make_float2(a1.x + a3.x, a1.y + a3.y);
-  const float2 d13 = make_float2(a1.x - a3.x, a1.y - a3.y);
-  const float2 id13 = sign < 0 ? make_float2(d13.y, -d13.x) : make_float2(-d13.y, d13.x);
-  a0 = make_float2(s02.x + s13.x, s02.y + s13.y);
-  a1 = make_float2(d02.x + id13.x, d02.y + id13.y);
-  a2 = make_float2(s02.x - s13.x, s02.y - s13.y);
-  a3 = make_float2(d02.x - id13.x, d02.y - id13.y);
-}
-
-// 16-point DFT in registers as 4 x 4 (n = n1 + 4 n2, q = q2 + 4 q1): 4-point DFTs over n2,
-// the twiddles exp(sign 2 pi i n1 q2 / 16), 4-point DFTs over n1. Result X[q] lands in
-// v[4 (q & 3) + (q >> 2)].
-__device__ __forceinline__ void dft16(float2* v, int sign) {
-#pragma unroll
-  for (int n1 = 0; n1 < 4; ++n1) dft4(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12], sign);
-  // cos and sin of 2 pi m / 16 for m = 1, 2, 3 (exact constants of the 16-point kernel)
-  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
-  const float sg = sign < 0 ? -1.f : 1.f;
-  // (n1, q2) -> m = n1 q2 in {1, 2, 3, 2, 4, 6, 3, 6, 9}
-  const float2 w[10] = {make_float2(1.f, 0.f),     make_float2(c1, sg * s1),
-                        make_float2(h, sg * h),     make_float2(s1, sg * c1),
-                        make_float2(0.f, sg),       make_float2(-s1, sg * c1),
-                        make_float2(-h, sg * h),    make_float2(-c1, sg * s1),
-                        make_float2(-1.f, 0.f),     make_float2(-c1, -sg * s1)};
-#pragma unroll
-  for (int n1 = 1; n1 < 4; ++n1)
-#pragma unroll
-    for (int q2 = 1; q2 < 4; ++q2) v[n1 + 4 * q2] = cmul(v[n1 + 4 * q2], w[n1 * q2]);
-#pragma unroll
-  for (int q2 = 0; q2 < 4; ++q2) dft4(v[4 * q2], v[4 * q2 + 1], v[4 * q2 + 2], v[4 * q2 + 3], sign);
-}
-
-// Batched in-shared-memory FFT of P sequences of length L = 2^lg, sign -1 forward, +1 inverse
-// (unnormalised). Sequence p occupies [p L, (p + 1) L) of both buffers (swizzled by sw).
-// Out-of-place Stockham stages after the plan above. Returns the buffer holding the result. The
-// whole block calls it.
-__device__ float2* fft_block(float2* in, float2* out, const float2* tw, int lg, int P, int sign) {
-  const int L = 1 << lg;
-  int off = 0;
-  int ls = 0;   // log2 Ns
-  while (ls + 4 <= lg) {   // radix-16
-    const int Ns = 1 << ls, lq = lg - 4, q = L >> 4;
-    for (int u = threadIdx.x; u < (P << lq); u += blockDim.x) {
-      const int p = u >> lq, j = u & (q - 1);
-      const int base_in = (p << lg) + j;
-      float2 v[16];
-#pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = in[sw(base_in + r * q)];
-      const int k = j & (Ns - 1);
-      if (ls > 0) {
-#pragma unroll
-        for (int r = 1; r < 16; ++r) {
-          float2 w = tw[off + (r - 1) * Ns + k];
-          if (sign < 0) w.y = -w.y;
-          v[r] = cmul(v[r], w);
-        }
-      }
-      dft16(v, sign);
-      const int base = (p << lg) + ((j >> ls) << (ls + 4)) + k;
-#pragma unroll
-      for (int qq = 0; qq < 16; ++qq) out[sw(base + qq * Ns)] = v[4 * (qq & 3) + (qq >> 2)];
-    }
-    __syncthreads();
-    float2* t = in;
-    in = out;
-    out = t;
-    off += 15 * Ns;
-    ls += 4;
-  }
-  if (ls + 2 <= lg) {   // one radix-4 stage
-    const int Ns = 1 << ls, lq = lg - 2, q = L >> 2;
-    for (int u = threadIdx.x; u < (P << lq); u += blockDim.x) {
-      const int p = u >> lq, j = u & (q - 1);
-      const int base_in = (p << lg) + j;
-      float2 v0 = in[sw(base_in)], v1 = in[sw(base_in + q)], v2 = in[sw(base_in + 2 * q)],
-             v3 = in[sw(base_in + 3 * q)];
-      const int k = j & (Ns - 1);
-      if (ls > 0) {
-        float2 w1 = tw[off + k], w2 = tw[off + Ns + k], w3 = tw[off + 2 * Ns + k];
-        if (sign < 0) {
-          w1.y = -w1.y;
-          w2.y = -w2.y;
-          w3.y = -w3.y;
-        }
-        v1 = cmul(v1, w1);
-        v2 = cmul(v2, w2);
-        v3 = cmul(v3, w3);
-      }
-      dft4(v0, v1, v2, v3, sign);
-      const int base = (p << lg) + ((j >> ls) << (ls + 2)) + k;
-      out[sw(base)] = v0;
-      out[sw(base + Ns)] = v1;
-      out[sw(base + 2 * Ns)] = v2;
-      out[sw(base + 3 * Ns)] = v3;
-    }
-    __syncthreads();
-    float2* t = in;
-    in = out;
-    out = t;
-    off += 3 * Ns;
-    ls += 2;
-  }
-  if (ls < lg) {   // one radix-2 stage
-    const int Ns = 1 << ls, lh = lg - 1, h = L >> 1;
-    for (int u = threadIdx.x; u < (P << lh); u += blockDim.x) {
-      const int p = u >> lh, j = u & (h - 1);
-      const int base_in = (p << lg) + j;
-      float2 v0 = in[sw(base_in)], v1 = in[sw(base_in + h)];
-      const int k = j & (Ns - 1);
-      float2 w = tw[off + k];
-      if (sign < 0) w.y = -w.y;
-      v1 = cmul(v1, w);
-      const int base = (p << lg) + ((j >> ls) << (ls + 1)) + k;
-      out[sw(base)] = make_float2(v0.x + v1.x, v0.y + v1.y);
-      out[sw(base + Ns)] = make_float2(v0.x - v1.x, v0.y - v1.y);
-    }
-    __syncthreads();
-    in = out;
-  }
-  return in;
-}
-
-}  // namespace
+using fftc::cmul;
+using fftc::fft_block;
+using fftc::ilog2;
+using fftc::stage_twiddles;
+using fftc::sw;
 
 struct FftRowArgs {
   const float2* T;      // [rows][NC][Kx]
@@ -219,7 +58,6 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   __shared__ DevPhase phs[kMaxPhases];
   const int tid = threadIdx.x;
   const int row0 = blockIdx.x * a.R;
-  const int lg = ilog2(L);
   stage_twiddles(a.table, L, tw);
   for (int i = tid; i < a.Kx; i += blockDim.x) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
@@ -284,7 +122,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
     }
     __syncthreads();
   }
-  float2* zb = fft_block(b0, b1, tw, lg, P, +1);
+  float2* zb = fft_block(b0, b1, tw, L, P, +1);
   float2* other = (zb == b0) ? b1 : b0;
   double sb[6] = {0, 0, 0, 0, 0, 0};
   double vmax = 0.0;
@@ -401,7 +239,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   if (S & 1)
     for (int x = tid; x < L; x += blockDim.x) other[sw((P - 1) * L + x)].y = 0.f;
   __syncthreads();
-  float2* zf = fft_block(other, zb, tw, lg, P, -1);
+  float2* zf = fft_block(other, zb, tw, L, P, -1);
   for (int u = tid; u < S * a.Kx; u += blockDim.x) {
     const int s = u / a.Kx, j = u - s * a.Kx;
     const int r = s / NC, c = s - r * NC, row = row0 + r;
@@ -468,7 +306,7 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
       if (dst[u] >= 0) b0[sw(dst[u])] = v[u];
   }
   __syncthreads();
-  const float2* z = fft_block(b0, b1, tw, ilog2(L), C, a.sign);
+  const float2* z = fft_block(b0, b1, tw, L, C, a.sign);
   for (int i = threadIdx.x; i < a.out_rows * C; i += blockDim.x) {
     const int r = i / C, cc = i - r * C, col = col0 + cc;
     if (col >= a.ncols) continue;

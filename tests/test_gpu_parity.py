@@ -463,3 +463,30 @@ def test_fft_transform_rejects_non_power_of_two(lib):
     with pytest.raises(lib.RFError):
         lib.Solver(np.zeros((32, 32), np.uint8), elastic_phases(), transform="fft",
                    precision="split_bf16")
+
+
+@pytest.mark.parametrize("transform", ["fft", "dft"])
+def test_traced_chunked_and_untraced_while_graph_solves_agree(lib, transform):
+    """Untraced solves run as one conditional-while graph; traced solves replay chunks of
+    updates with stage events. Same kernels and tiles in the same order: identical results
+    (the FFT tiles are pinned: the autotuner's choice changes rounding), and the stage
+    accounting covers the stages the mode runs."""
+    pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
+    ph = j2_phases()
+    pat = O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    path = uniaxial_path(20, 0.02)[::5]
+    res = {}
+    for traced in (False, True):
+        s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform=transform,
+                       fft_rows=2, fft_cols=4)
+        s.rf_set_tracing(traced)
+        res[traced] = s.rf_solve_path(path)
+        st = s.rf_get_stage_times()
+        info = s.rf_get_info()
+        s.close()
+        if traced:
+            assert st["row"][1] == int(np.sum(res[traced]["iters"])) and st["row"][0] > 0
+            assert st["green"][1] == st["row"][1] and st["final"][1] == len(path)
+        assert info["kernel_launches"] > 0
+    assert np.array_equal(res[False]["iters"], res[True]["iters"])
+    assert np.array_equal(res[False]["sigma_bar"], res[True]["sigma_bar"])
