@@ -100,7 +100,7 @@ typedef struct rf_phase {
  *  transform  RF_TRANSFORM_DFT: pruned separable DFT (only the pattern's distinct kx >= 0
  *             columns along x, its (ky, kx) rectangle along y, (kz, ky, kx) along z).
  *             RF_TRANSFORM_FFT: full FFTs along each axis restricted to the pattern (the
- *             transform the paper uses, Sec. 4); needs power-of-two sizes (Nz = 1 in 2D) and
+ *             transform the paper uses, Sec. 4); needs sizes 2^b or 3 * 2^b (Nz = 1 in 2D) and
  *             precision RF_PREC_FP32. Both compute the same restricted transform.
  *  fft_rows, fft_cols  FFT mode tiles: grid rows per row-kernel block and line columns per
  *             column-kernel block (0 = chosen by timing a few launches of each candidate when

@@ -409,11 +409,15 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (opt->fft_rows < 0 || opt->fft_rows > 64 || opt->fft_cols < 0 || opt->fft_cols > 64)
     return invalid("options: fft_rows and fft_cols in [0, 64]");
   if (opt->transform == RF_TRANSFORM_FFT) {
-    auto pow2 = [](int v) { return v >= 2 && (v & (v - 1)) == 0; };
+    // 2^b or 3 * 2^b (the FFT stages are radix 16, 4, 2 and one radix-3)
+    auto pow2 = [](int v) {
+      const int p = (v % 3 == 0) ? v / 3 : v;
+      return v >= 2 && p >= 1 && (p & (p - 1)) == 0;
+    };
     if (opt->precision != RF_PREC_FP32)
       return invalid("options: the FFT transform runs in FP32 precision only");
     if (!pow2(grid->n[0]) || !pow2(grid->n[1]) || (grid->dim == 3 && !pow2(grid->n[2])))
-      return invalid("options: the FFT transform needs power-of-two grid sizes (>= 2)");
+      return invalid("options: the FFT transform needs grid sizes 2^b or 3 * 2^b (>= 2)");
   }
 
   rf_ctx* c = new rf_ctx();

@@ -1,5 +1,5 @@
 // FFT transform mode: steps b and d of Sec. 4 as full FFTs along each axis restricted to the
-// reduced set (the paper's own choice of transform), for power-of-two grid sizes, FP32.
+// reduced set (the paper's own choice of transform), for grid sizes 2^b or 3 * 2^b, FP32.
 //
 // Along x (row kernel, fused with the law): two real lines are packed into one complex
 // sequence z = a + i b; the inverse builds z's spectrum from the lines' kx >= 0 coefficients
@@ -20,7 +20,6 @@ namespace rfk {
 
 using fftc::cmul;
 using fftc::fft_block;
-using fftc::ilog2;
 using fftc::stage_twiddles;
 using fftc::sw;
 
@@ -52,7 +51,8 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   const int P = (S + 1) / 2;           // packed complex sequences
   float2* tw = reinterpret_cast<float2*>(smem);    // stage twiddles, < 3 L / 2 entries
   float2* b0 = tw + (3 * L) / 2 + 1;
-  float2* b1 = b0 + (size_t)P * L;
+  const int span = ((P * L + 15) / 16) * 16;   // the swizzle permutes within 16-element blocks
+  float2* b1 = b0 + span;
   int* kxs = reinterpret_cast<int*>(b1 + (size_t)P * L);
   __shared__ double red[8];
   __shared__ DevPhase phs[kMaxPhases];
@@ -61,7 +61,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   stage_twiddles(a.table, L, tw);
   for (int i = tid; i < a.Kx; i += blockDim.x) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
-  for (int i = tid; i < P * L; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
   grid_dep_wait();
   if (!FINAL && a.done && *a.done) return;   // the same flag value for every thread
   __syncthreads();
@@ -246,7 +246,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
     if (row >= a.rows) continue;
     const int k = kxs[j];
     const int zb0 = (s >> 1) * L;
-    const float2 zk = zf[sw(zb0 + k)], zm = zf[sw(zb0 + ((L - k) & (L - 1)))];
+    const float2 zk = zf[sw(zb0 + k)], zm = zf[sw(zb0 + (k == 0 ? 0 : L - k))];
     float2 out;
     if ((s & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
@@ -274,14 +274,15 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
   const int L = a.L, C = a.C;
   float2* tw = reinterpret_cast<float2*>(smem);
   float2* b0 = tw + (3 * L) / 2 + 1;
-  float2* b1 = b0 + (size_t)C * L;
+  const int span = ((C * L + 15) / 16) * 16;   // the swizzle permutes within 16-element blocks
+  float2* b1 = b0 + span;
   const int col0 = blockIdx.x * C;
   const long long b = blockIdx.y;
   const float2* in = a.in + b * a.in_bstride;
   float2* out = a.out + b * a.out_bstride;
   stage_twiddles(a.table, L, tw);
   if (a.in_list)
-    for (int i = threadIdx.x; i < C * L; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
   grid_dep_wait();
   if (a.done && *a.done) return;   // the same flag value for every thread of the block
   __syncthreads();
@@ -324,12 +325,13 @@ static int fft_check(rf_ctx* c, const char* what) {
 }
 
 static size_t cols_smem(int L, int C) {
-  return ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)C * L) * sizeof(float2);
+  return ((size_t)(3 * L) / 2 + 1 + 2 * (((size_t)C * L + 15) / 16) * 16) * sizeof(float2);
 }
 
 static size_t row_smem(int L, int nc, int Kx, int R) {
   const int P = (R * nc + 1) / 2;
-  return ((size_t)(3 * L) / 2 + 1 + 2 * (size_t)P * L) * sizeof(float2) + (size_t)Kx * sizeof(int) +
+  return ((size_t)(3 * L) / 2 + 1 + 2 * (((size_t)P * L + 15) / 16) * 16) * sizeof(float2) +
+         (size_t)Kx * sizeof(int) +
          16;
 }
 

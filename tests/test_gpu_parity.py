@@ -357,13 +357,21 @@ def _pow2_case(name):
     if name == "rect":
         pm = (np.random.default_rng(5).random((32, 128)) < 0.3).astype(np.uint8)
         return pm, elastic_phases(), random_macro_strain(9, 2), O.pattern_adapted(pm, 1, 300)
+    if name == "three":   # sides 3 * 2^b: the radix-3 stage
+        pm = np.ascontiguousarray(random_discs(48, (3.0, 6.0), 0.35, seed=12)[:24])   # 24 x 48
+        return pm, j2_phases(), np.array([0.02, 0, 0, 0, 0, 0.003]), \
+            O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    if name == "3d_three":
+        pm = (np.random.default_rng(7).random((6, 12, 16)) < 0.3).astype(np.uint8)
+        return pm, elastic_phases(), random_macro_strain(11, 3), O.pattern_adapted(pm, 1, 150)
     if name == "3d_rect":
         pm = (np.random.default_rng(6).random((8, 16, 32)) < 0.3).astype(np.uint8)
         return pm, elastic_phases(), random_macro_strain(10, 3), O.pattern_adapted(pm, 1, 200)
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["c1", "fullset", "3d", "j2_64", "rect", "3d_rect"])
+@pytest.mark.parametrize("name", ["c1", "fullset", "3d", "j2_64", "rect", "3d_rect", "three",
+                                  "3d_three"])
 @pytest.mark.parametrize("scheme,ref", [("rotated", "minmax"), ("continuous", "volume")])
 def test_fft_transform_matches_oracle(lib, name, scheme, ref):
     pm, ph, macro, pat = _pow2_case(name)
@@ -456,8 +464,8 @@ def test_fft_full_size_c3_first_iterations(lib):
     assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
 
 
-def test_fft_transform_rejects_non_power_of_two(lib):
-    pm = np.zeros((24, 40), np.uint8)
+def test_fft_transform_rejects_unsupported_sizes(lib):
+    pm = np.zeros((24, 40), np.uint8)        # 40 = 5 * 8
     with pytest.raises(lib.RFError):
         lib.Solver(pm, elastic_phases(), transform="fft")
     with pytest.raises(lib.RFError):
