@@ -326,8 +326,8 @@ def run_batch(args, rf, torch):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{n} 2D elastic fibre RVEs, sides U{{64,96,128,192,256}}, "
-                                   "vf U[0.2,0.5], r 8-24, K=5% adapted, FP32 (x transforms "
-                                   "by FFT for sides 2^b and 3*2^b, y by pruned DFT)",
+                                   "vf U[0.2,0.5], r 8-24, K=5% adapted, FP32 (FFT transforms "
+                                   "along x and y for sides 2^b and 3*2^b, else pruned DFT)",
                        "voxels": int(vox.sum()), "tol": TOL,
                        "l2": "working set larger than L2"},
             "solves_per_s": n * args.steps / (total_ms / 1e3),

@@ -42,6 +42,7 @@ struct BDesc {
   long long off_spart;   // double, row_items * 6
   int tab_x, tab_y;      // offsets into the twiddle buffer
   int fft;               // row items use FFTs along x (Nx = 2^b or 3 2^b), else the pruned DFT
+  int fft_y, cy;         // y transforms by FFT over groups of cy line columns (Ny = 2^b, 3 2^b)
   long long zero_base;   // ER offset (within the RVE) of the zero frequency
   float lam0, mu0, inv2mu0, cgam;
 };
@@ -127,13 +128,69 @@ __device__ void dft_tile(const float2* in, float2* out, int M, int N, int K, con
   }
 }
 
+// Column item by FFTs along y: cy consecutive line columns (of the NC Kx per row) of one RVE.
+// Inverse: the pattern's ky rows of ER scattered into full columns, FFT, all Ny rows of T1.
+// Forward: all Ny rows of T1p, FFT, the pattern's ky rows into OUT. Loads in batches of 8.
+__device__ void col_item_fft(const BArgs& a, int g, const BDesc& d, unsigned char* smem,
+                             int sign) {
+  using namespace fftc;
+  const int L = d.ny, NCK = NC * d.Kx;
+  const int c0 = g * d.cy, cc_n = min(d.cy, NCK - c0);
+  const int span = ((cc_n * L + 15) / 16) * 16;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* b0 = tw + L;
+  float2* b1 = b0 + span;
+  stage_twiddles(a.tab + d.tab_y, L, tw);
+  const int* kym = a.kym + d.off_ky;
+  if (sign > 0)
+    for (int i = threadIdx.x; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2* src = sign > 0 ? a.ER + d.off_er : a.T1p + d.off_t1;
+  const int rows_in = sign > 0 ? d.Ky : L;
+  const int tot = rows_in * cc_n;
+  for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * blockDim.x) {
+    float2 v[8];
+    int dst[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * blockDim.x;
+      dst[u] = -1;
+      v[u] = make_float2(0.f, 0.f);
+      if (i < tot) {
+        const int r = i / cc_n, cc = i - r * cc_n;
+        v[u] = src[(long long)r * NCK + c0 + cc];
+        dst[u] = cc * L + (sign > 0 ? kym[r] : r);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (dst[u] >= 0) b0[sw(dst[u])] = v[u];
+  }
+  __syncthreads();
+  const float2* z = fft_block(b0, b1, tw, L, cc_n, sign);
+  float2* dstg = sign > 0 ? a.T1 + d.off_t1 : a.OUT + d.off_er;
+  const int rows_out = sign > 0 ? L : d.Ky;
+  for (int i = threadIdx.x; i < rows_out * cc_n; i += blockDim.x) {
+    const int r = i / cc_n, cc = i - r * cc_n;
+    dstg[(long long)r * NCK + c0 + cc] = z[sw(cc * L + (sign > 0 ? r : kym[r]))];
+  }
+  __syncthreads();   // the next item reuses the buffers
+}
+
+constexpr int kColFft = 1 << 30;   // item flag: FFT column group (else a DFT tile index)
+
 __global__ __launch_bounds__(256) void kb_inv_y(BArgs a) {
   __shared__ float2 xs[32][64];
   __shared__ float2 ws[32][33];
+  extern __shared__ __align__(16) unsigned char csm[];
   for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     const int2 w = a.items[it];
     if (!a.final_pass && rve_done(a, w.x)) continue;   // the final pass covers every RVE
     const BDesc d = a.d[w.x];
+    if (w.y & kColFft) {
+      col_item_fft(a, w.y & ~kColFft, d, csm, +1);
+      continue;
+    }
     const int mt = w.y / d.nt, nt = w.y % d.nt;
     dft_tile(a.ER + d.off_er, a.T1 + d.off_t1, d.ny, NC * d.Kx, d.Ky, nullptr, a.kym + d.off_ky,
              a.tab + d.tab_y, d.ny, +1, mt * 32, nt * 64, xs, ws);
@@ -143,10 +200,15 @@ __global__ __launch_bounds__(256) void kb_inv_y(BArgs a) {
 __global__ __launch_bounds__(256) void kb_fwd_y(BArgs a) {
   __shared__ float2 xs[32][64];
   __shared__ float2 ws[32][33];
+  extern __shared__ __align__(16) unsigned char csm[];
   for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     const int2 w = a.items[it];
     if (rve_done(a, w.x)) continue;
     const BDesc d = a.d[w.x];
+    if (w.y & kColFft) {
+      col_item_fft(a, w.y & ~kColFft, d, csm, -1);
+      continue;
+    }
     const int mt = w.y / d.nt, nt = w.y % d.nt;
     dft_tile(a.T1p + d.off_t1, a.OUT + d.off_er, d.Ky, NC * d.Kx, d.ny, a.kym + d.off_ky,
              nullptr, a.tab + d.tab_y, d.ny, -1, mt * 32, nt * 64, xs, ws);
@@ -735,7 +797,8 @@ struct rf_batch {
   int grid = 0;
   size_t row_smem = 0;
   int R_choice[5] = {0, 0, 0, 0, 0};   // rows per row item, per size class (autotuned)
-  bool use_fft = true;                 // FFT row items where Nx allows
+  bool use_fft = true;                 // FFT row and column items where the sides allow
+  size_t col_smem = 0;                 // dynamic shared memory of the column kernels
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
   long long launches = 0;
   int last_max_iters = 0;
@@ -780,9 +843,9 @@ BArgs batch_args(rf_batch* b, int stage) {
 
 int launch_update(rf_batch* b) {
   const int G = b->grid;
-  kb_inv_y<<<G, 256, 0, b->stream>>>(batch_args(b, 0));
+  kb_inv_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 0));
   kb_row<<<G, 256, b->row_smem, b->stream>>>(batch_args(b, 1));
-  kb_fwd_y<<<G, 256, 0, b->stream>>>(batch_args(b, 2));
+  kb_fwd_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 2));
   kb_gamma<<<G, 256, 0, b->stream>>>(batch_args(b, 3));
   kb_decide<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
   b->launches += 5;
@@ -969,7 +1032,7 @@ int finish_solve(rf_batch* b, double* hom_stress, int32_t* iters, double* residu
   // final pass: fields of the converged coefficients -> homogenised stresses
   BArgs a0 = batch_args(b, 0);
   a0.final_pass = 1;
-  kb_inv_y<<<b->grid, 256, 0, b->stream>>>(a0);
+  kb_inv_y<<<b->grid, 256, b->col_smem, b->stream>>>(a0);
   BArgs a1 = batch_args(b, 1);
   a1.final_pass = 1;
   kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
@@ -1146,6 +1209,13 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     d.nt = (NC * d.Kx + 63) / 64;
     d.mt_inv = (ny + 31) / 32;
     d.mt_fwd = (d.Ky + 31) / 32;
+    {
+      const int p2 = ny % 3 == 0 ? ny / 3 : ny;
+      d.cy = std::max(1, std::min(16, 4096 / ny));
+      const size_t cs = ((size_t)ny + 2 * ((((size_t)d.cy * ny) + 15) / 16) * 16) * sizeof(float2);
+      d.fft_y = (b->use_fft && (p2 & (p2 - 1)) == 0 && cs <= 120 * 1024) ? 1 : 0;
+      if (d.fft_y) b->col_smem = std::max(b->col_smem, cs);
+    }
     d.zero_base = ((long long)pos(ys, 0) * NC) * d.Kx + pos(xs, 0);
     std::map<std::tuple<int, int>, long long> hpos;
     b->h_src[r].assign(d.Kh, 0);
@@ -1259,8 +1329,16 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     std::vector<int2> inv, fwd, gam;
     for (int r : order) {
       const BDesc& d = b->desc[r];
-      for (int k = 0; k < d.mt_inv * d.nt; ++k) inv.push_back(make_int2(r, k));
-      for (int k = 0; k < d.mt_fwd * d.nt; ++k) fwd.push_back(make_int2(r, k));
+      if (d.fft_y) {
+        const int groups = (NC * d.Kx + d.cy - 1) / d.cy;
+        for (int k = 0; k < groups; ++k) {
+          inv.push_back(make_int2(r, k | kColFft));
+          fwd.push_back(make_int2(r, k | kColFft));
+        }
+      } else {
+        for (int k = 0; k < d.mt_inv * d.nt; ++k) inv.push_back(make_int2(r, k));
+        for (int k = 0; k < d.mt_fwd * d.nt; ++k) fwd.push_back(make_int2(r, k));
+      }
       for (int k = 0; k < d.chunks; ++k) gam.push_back(make_int2(r, k));
     }
     std::vector<int2>* lists[5] = {&inv, nullptr, &fwd, &gam, nullptr};
@@ -1272,6 +1350,8 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     std::vector<long long> none(n_rve, -1);
     up(b->d_warm_off, none.data(), sizeof(long long) * n_rve);
     cudaFuncSetAttribute(kb_row, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(kb_inv_y, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(kb_fwd_y, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   }
   if (!err) {
     std::vector<double> macro0(6 * (size_t)n_rve, 0.0);
