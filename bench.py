@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--cpu-iters", type=int, default=4, help="oracle updates in the CPU sample")
     p.add_argument("--transform", default="fft", choices=["fft", "dft"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_tf32"])
+    p.add_argument("--fft-rows", type=int, default=0,
+                   help="c2 FFT mode: rows per row-kernel block (0: autotuned)")
+    p.add_argument("--fft-cols", type=int, default=0,
+                   help="c2 FFT mode: columns per column-kernel block (0: autotuned)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
@@ -520,18 +524,23 @@ def main():
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     pattern = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
+    tiles = {}
+    if args.transform == "fft":
+        tiles = dict(fft_rows=args.fft_rows, fft_cols=args.fft_cols)
     if args.profile_updates > 0:
         s = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=0.0,
                       max_iter=args.profile_updates, transform=args.transform,
-                      precision=args.precision)
+                      precision=args.precision, **tiles)
         out = s.rf_solve(path[0])
         n_launch = s.rf_get_info()["kernel_launches"]
         s.close()
         print(json.dumps({"profile_updates": int(out["iters"]), "kernel_launches": n_launch}))
         return 0
     solver = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER,
-                       transform=args.transform, precision=args.precision)
+                       transform=args.transform, precision=args.precision, **tiles)
     info = solver.rf_get_info()
+    tile_info = {k: info[k] for k in ("fft_rows", "fft_row_threads", "fft_cols",
+                                      "fft_col_threads")} if args.transform == "fft" else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -657,6 +666,7 @@ def main():
                 "solves_per_s": solves,
                 "iterations_per_step": iters / args.steps, "e2e": e2e,
                 "gpu_launches": int(launches), "roofline": roof, "stage_share": stage_share,
+                "tiles": tile_info,
                 "cpu_baseline": cpu, "clocks": clocks,
                 "precision": {"fp32": "FP32 transforms and law",
                               "split_bf16": "BF16 hi+lo tensor-core x transforms, FP32 law",

@@ -127,6 +127,10 @@ typedef struct rf_info {
   int64_t kernel_launches;/* kernels this context has launched so far */
   double j2_max_violation;/* FP64 check of the last commit: max |sigma_eq - (sy + H a)| / sy */
   double lambda0, mu0;    /* reference medium in use */
+  int32_t fft_rows;       /* FFT mode: rows per row-kernel block (set or autotuned), else 0 */
+  int32_t fft_row_threads;/* FFT mode: threads per row-kernel block, else 0 */
+  int32_t fft_cols;       /* FFT mode: columns per column-kernel block, else 0 */
+  int32_t fft_col_threads;/* FFT mode: threads per column-kernel block, else 0 */
 } rf_info;
 
 /* Create a solver context for one microstructure.

@@ -885,6 +885,11 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   info->j2_max_violation = c->last_viol;
   info->lambda0 = c->lam0;
   info->mu0 = c->mu0;
+  const bool fft = c->opt.transform == RF_TRANSFORM_FFT;
+  info->fft_rows = fft ? c->fft_R : 0;
+  info->fft_row_threads = fft ? c->fft_row_threads : 0;
+  info->fft_cols = fft ? c->fft_C : 0;
+  info->fft_col_threads = fft ? c->fft_col_threads : 0;
   return RF_OK;
 }
 

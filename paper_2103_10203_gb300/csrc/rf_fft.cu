@@ -53,7 +53,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   float2* b0 = tw + (3 * L) / 2 + 1;
   const int span = ((P * L + 15) / 16) * 16;   // the swizzle permutes within 16-element blocks
   float2* b1 = b0 + span;
-  int* kxs = reinterpret_cast<int*>(b1 + (size_t)P * L);
+  int* kxs = reinterpret_cast<int*>(b1 + span);   // past b1's rounded span
   __shared__ double red[8];
   __shared__ DevPhase phs[kMaxPhases];
   const int tid = threadIdx.x;
@@ -491,9 +491,10 @@ int fft_forward_stages(rf_ctx* c, const int* done) {
 
 static int tck(cudaError_t e, const char* what) { return e == cudaSuccess ? RF_OK : cuda_fail(e, what); }
 
-// Autotuner for the FFT tiles: each candidate runs one untimed launch and then four timed
-// launches of the stage it governs (CUDA events on the context's stream) on the context's own
-// buffers; the fastest candidate stays. Candidates that exceed shared memory are skipped.
+// Autotuner for the FFT tiles: each candidate runs one untimed launch and then three timed groups
+// of three launches of the stage it governs (CUDA events on the context's stream) on the
+// context's own buffers; the candidate with the fastest group stays. Candidates that exceed
+// shared memory are skipped.
 int fft_autotune(rf_ctx* c) {
   if (c->opt.fft_rows > 0 && c->opt.fft_cols > 0) return RF_OK;
   cudaEvent_t e0, e1;
@@ -506,14 +507,22 @@ int fft_autotune(rf_ctx* c) {
   const int NCK = c->nc * c->Kx;
   err = tck(cudaMemsetAsync(c->d_T1, 0, sizeof(float2) * (size_t)c->rows * NCK, c->stream), "tuner");
   if (!err) err = tck(cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream), "tuner");
+  // the fastest of three timed groups of three launches (one untimed launch first): the
+  // minimum is robust to a stray slow launch, so repeated tunings of one pattern agree
   auto time_it = [&](auto&& run, float* ms) -> int {
     if (int e = run()) return e;
-    cudaEventRecord(e0, c->stream);
-    for (int i = 0; i < 4; ++i)
-      if (int e = run()) return e;
-    cudaEventRecord(e1, c->stream);
-    if (int e = tck(cudaEventSynchronize(e1), "tuner")) return e;
-    return tck(cudaEventElapsedTime(ms, e0, e1), "tuner");
+    *ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      for (int i = 0; i < 3; ++i)
+        if (int e = run()) return e;
+      cudaEventRecord(e1, c->stream);
+      if (int e = tck(cudaEventSynchronize(e1), "tuner")) return e;
+      float t = 0.f;
+      if (int e = tck(cudaEventElapsedTime(&t, e0, e1), "tuner")) return e;
+      *ms = std::min(*ms, t);
+    }
+    return RF_OK;
   };
   if (!err && c->opt.fft_rows <= 0) {
     float best = 1e30f;

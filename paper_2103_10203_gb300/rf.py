@@ -42,7 +42,9 @@ class rf_info(C.Structure):
     _fields_ = [("K", C.c_int64), ("K_half", C.c_int64), ("Kx", C.c_int32), ("Ky", C.c_int32),
                 ("Kz", C.c_int32), ("last_iters", C.c_int32), ("last_residual", C.c_double),
                 ("kernel_launches", C.c_int64), ("j2_max_violation", C.c_double),
-                ("lambda0", C.c_double), ("mu0", C.c_double)]
+                ("lambda0", C.c_double), ("mu0", C.c_double), ("fft_rows", C.c_int32),
+                ("fft_row_threads", C.c_int32), ("fft_cols", C.c_int32),
+                ("fft_col_threads", C.c_int32)]
 
 
 class rf_mlp_dims(C.Structure):

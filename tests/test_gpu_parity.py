@@ -405,6 +405,26 @@ def test_fft_tiles_do_not_change_the_result(lib, name, rows, cols):
     assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
 
 
+@pytest.mark.parametrize("shape,rows,cols", [((12, 12), 1, 1), ((24, 6), 2, 3), ((8, 24), 2, 5),
+                                             ((6, 12, 6), 1, 2)])
+def test_fft_small_sides(lib, shape, rows, cols):
+    """Sides 6, 12, 24 (radix-4/2 stages and the radix-3 stage only) with tiles whose packed
+    lines do not fill whole 16-element swizzle blocks."""
+    rng = np.random.default_rng(sum(shape) + rows)
+    pm = (rng.random(shape) < 0.35).astype(np.uint8)
+    ph = j2_phases() if len(shape) == 2 else elastic_phases()
+    macro = np.array([0.02, 0, 0, 0, 0, 0.003]) if len(shape) == 2 else random_macro_strain(3, 3)
+    pat = O.pattern_adapted(pm, 1, max(8, pm.size // 4))
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=5, transform="fft", fft_rows=rows,
+                   fft_cols=cols)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=5)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
 def test_fft_transform_load_path_and_tolerance(lib):
     pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
     ph = j2_phases()
