@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include "rf_fftcore.cuh"
 #include "rf_internal.cuh"
 
 namespace rfk {
@@ -458,9 +459,9 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   c->ns = any_plastic ? (c->dim == 2 ? 4 : 7) : 0;
   int err = dalloc(&c->d_phase, N, "phase map");
   if (!err && c->ns) err = dalloc(&c->d_state, (size_t)c->ns * N, "state");
-  if (!err) err = dalloc(&c->d_twx, c->nx, "tables");
-  if (!err) err = dalloc(&c->d_twy, c->ny, "tables");
-  if (!err) err = dalloc(&c->d_twz, c->nz, "tables");
+  if (!err) err = dalloc(&c->d_twx, rfk::fftc::table_len(c->nx), "tables");
+  if (!err) err = dalloc(&c->d_twy, rfk::fftc::table_len(c->ny), "tables");
+  if (!err) err = dalloc(&c->d_twz, rfk::fftc::table_len(c->nz), "tables");
   if (!err) err = dalloc(&c->d_status, 1, "status");
   if (!err) err = dalloc(&c->d_sbar, 8, "sbar");
   if (!err) err = dalloc(&c->d_eps, 6 * (size_t)N, "fields");

@@ -140,7 +140,7 @@ __device__ void col_item_fft(const BArgs& a, int g, const BDesc& d, unsigned cha
   float2* tw = reinterpret_cast<float2*>(smem);
   float2* b0 = tw + L;
   float2* b1 = b0 + span;
-  stage_twiddles(a.tab + d.tab_y, L, tw);
+  copy_twiddles(a.tab + d.tab_y, L, tw);
   const int* kym = a.kym + d.off_ky;
   if (sign > 0)
     for (int i = threadIdx.x; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
@@ -234,7 +234,7 @@ __device__ void row_item_fft(const BArgs& a, int2 w, const BDesc& d, unsigned ch
   float2* b1 = b0 + span;
   int* kxs = reinterpret_cast<int*>(b1 + span);
   const int tid = threadIdx.x;
-  stage_twiddles(a.tab + d.tab_x, L, tw);
+  copy_twiddles(a.tab + d.tab_x, L, tw);
   for (int i = tid; i < Kx; i += blockDim.x) kxs[i] = a.kx[d.off_kx + i];
   for (int i = tid; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
   __syncthreads();
@@ -1251,9 +1251,9 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     b->patterns.emplace_back(patterns[r], patterns[r] + 3 * Kr);
   }
   long long tab_total = 0;
-  for (int L : tab_sizes) {
+  for (int L : tab_sizes) {   // even lengths keep every stage table 16-byte aligned
     tab_off[L] = (int)tab_total;
-    tab_total += L;
+    tab_total += fftc::table_len(L);
   }
   for (auto& d : b->desc) {
     d.tab_x = tab_off[d.nx];

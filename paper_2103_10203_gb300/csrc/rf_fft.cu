@@ -20,7 +20,7 @@ namespace rfk {
 
 using fftc::cmul;
 using fftc::fft_block;
-using fftc::stage_twiddles;
+using fftc::copy_twiddles;
 using fftc::sw;
 
 struct FftRowArgs {
@@ -29,7 +29,7 @@ struct FftRowArgs {
   const uint8_t* phase;
   float* state;
   const int* kx;
-  const float2* table;  // exp(+2 pi i t / Nx)
+  const float2* table;  // twiddle buffer of length Nx (rf_fftcore.cuh)
   int Nx, Kx, rows, R;
   long long N;
   float invN;
@@ -58,7 +58,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   __shared__ DevPhase phs[kMaxPhases];
   const int tid = threadIdx.x;
   const int row0 = blockIdx.x * a.R;
-  stage_twiddles(a.table, L, tw);
+  copy_twiddles(a.table, L, tw);
   for (int i = tid; i < a.Kx; i += blockDim.x) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
   for (int i = tid; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
@@ -280,7 +280,7 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
   const long long b = blockIdx.y;
   const float2* in = a.in + b * a.in_bstride;
   float2* out = a.out + b * a.out_bstride;
-  stage_twiddles(a.table, L, tw);
+  copy_twiddles(a.table, L, tw);
   if (a.in_list)
     for (int i = threadIdx.x; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
   grid_dep_wait();

@@ -43,9 +43,19 @@ __host__ __device__ inline int twiddle_count(int L) {
   return n;
 }
 
-// Stage-major twiddles, built once per block from tab[t] = exp(+2 pi i t / L): a stage of radix
-// R and size Ns stores exp(+2 pi i r k / (R Ns)), r = 1..R-1, k < Ns, as R - 1 arrays contiguous
-// in k (neighbouring threads read neighbouring words).
+// Twiddle buffer of one length L: tab[t] = exp(+2 pi i t / L) for t < L, then (from entry
+// stage_offset(L), 16-byte aligned when the buffer is) the stage-major table below, padded to an
+// even count. Buffers of several lengths placed back to back keep that alignment.
+__host__ __device__ inline int stage_offset(int L) { return (L + 1) & ~1; }
+__host__ __device__ inline int stage_len(int L) {
+  const int n = (twiddle_count(L) + 1) & ~1;
+  return n < 2 ? 2 : n;
+}
+__host__ __device__ inline int table_len(int L) { return stage_offset(L) + stage_len(L); }
+
+// Stage-major twiddles from tab[t] = exp(+2 pi i t / L): a stage of radix R and size Ns stores
+// exp(+2 pi i r k / (R Ns)), r = 1..R-1, k < Ns, as R - 1 arrays contiguous in k (neighbouring
+// threads read neighbouring words). The whole block calls it; tw may be global or shared.
 __device__ inline void stage_twiddles(const float2* tab, int L, float2* tw) {
   const int p2 = (L % 3 == 0) ? L / 3 : L;
   int off = 0, Ns = 1;
@@ -66,6 +76,27 @@ __device__ inline void stage_twiddles(const float2* tab, int L, float2* tw) {
     for (int i = threadIdx.x; i < 2 * Ns; i += blockDim.x) {
       const int r = 1 + i / Ns, k = i - (r - 1) * Ns;
       tw[off + i] = tab[r * k * step];
+    }
+  }
+}
+
+// Copies the stage-major table of a twiddle buffer into shared memory (tw 16-byte aligned, room
+// for stage_len(L) entries): independent 16-byte loads issued back to back, then the stores.
+__device__ __forceinline__ void copy_twiddles(const float2* __restrict__ buf, int L, float2* tw) {
+  const float4* src = reinterpret_cast<const float4*>(buf + stage_offset(L));
+  float4* dst = reinterpret_cast<float4*>(tw);
+  const int n4 = stage_len(L) / 2;
+  for (int i0 = threadIdx.x; i0 < n4; i0 += 4 * blockDim.x) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n4) v[u] = __ldg(src + i);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n4) dst[i] = v[u];
     }
   }
 }

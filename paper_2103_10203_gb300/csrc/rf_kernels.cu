@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "rf_fftcore.cuh"
 #include "rf_internal.cuh"
 #include "rf_law.cuh"
 
@@ -28,6 +29,14 @@ __global__ void k_twiddle(float2* t, int L) {
     sincospi(2.0 * (double)i / (double)L, &s, &c);
     t[i] = make_float2((float)c, (float)s);
   }
+}
+
+// Stage-major table of a twiddle buffer (rf_fftcore.cuh), one block, after k_twiddle wrote tab.
+__global__ void k_stage_table(float2* buf, int L) {
+  float2* st = buf + fftc::stage_offset(L);
+  fftc::stage_twiddles(buf, L, st);
+  for (int i = fftc::twiddle_count(L) + threadIdx.x; i < fftc::stage_len(L); i += blockDim.x)
+    st[i] = make_float2(0.f, 0.f);
 }
 
 // hk: [Kh][4] = (kx, ky, kz, multiplicity). Writes unit wave vector and the frequency kind.
@@ -529,13 +538,17 @@ static int dft(rf_ctx* c, const float2* in, int in_splits, long long in_split_st
   return launch_check(c, "dft_axis");
 }
 
+// twiddle buffers of fftc::table_len(n) entries per axis: plain table, then stage-major table
 int launch_setup_tables(rf_ctx* c) {
-  k_twiddle<<<(c->nx + 255) / 256, 256, 0, c->stream>>>(c->d_twx, c->nx);
-  if (int e = launch_check(c, "twiddle x")) return e;
-  k_twiddle<<<(c->ny + 255) / 256, 256, 0, c->stream>>>(c->d_twy, c->ny);
-  if (int e = launch_check(c, "twiddle y")) return e;
-  k_twiddle<<<(c->nz + 255) / 256, 256, 0, c->stream>>>(c->d_twz, c->nz);
-  return launch_check(c, "twiddle z");
+  const int n[3] = {c->nx, c->ny, c->nz};
+  float2* t[3] = {c->d_twx, c->d_twy, c->d_twz};
+  for (int a = 0; a < 3; ++a) {
+    k_twiddle<<<(n[a] + 255) / 256, 256, 0, c->stream>>>(t[a], n[a]);
+    if (int e = launch_check(c, "twiddle table")) return e;
+    k_stage_table<<<1, 256, 0, c->stream>>>(t[a], n[a]);
+    if (int e = launch_check(c, "twiddle stage table")) return e;
+  }
+  return RF_OK;
 }
 
 int launch_hinfo(rf_ctx* c, const int* d_hk, long long Kh) {
