@@ -136,7 +136,7 @@ __device__ void col_item_fft(const BArgs& a, int g, const BDesc& d, unsigned cha
   using namespace fftc;
   const int L = d.ny, NCK = NC * d.Kx;
   const int c0 = g * d.cy, cc_n = min(d.cy, NCK - c0);
-  const int span = ((cc_n * L + 15) / 16) * 16;
+  const int span = span_of(cc_n * L);
   float2* tw = reinterpret_cast<float2*>(smem);
   float2* b0 = tw + L;
   float2* b1 = b0 + span;
@@ -228,7 +228,7 @@ __device__ void row_item_fft(const BArgs& a, int2 w, const BDesc& d, unsigned ch
   const int row0 = w.y * R;
   const int nr = min(R, d.rows - row0);
   const int S = nr * NC, P = (S + 1) / 2;
-  const int span = ((P * L + 15) / 16) * 16;
+  const int span = span_of(P * L);
   float2* tw = reinterpret_cast<float2*>(smem);
   float2* b0 = tw + L;
   float2* b1 = b0 + span;
@@ -877,7 +877,7 @@ int build_row_items(rf_batch* b) {
     const size_t s_dft = (size_t)d.nx * sizeof(float2) + (size_t)d.R * NC * d.Kx * sizeof(float2) +
                          (size_t)d.Kx * 8 + (size_t)d.R * NC * d.nx * sizeof(float) + 64;
     const int P = (d.R * NC + 1) / 2;
-    const size_t span = (((size_t)P * d.nx + 15) / 16) * 16;
+    const size_t span = (size_t)fftc::span_of(P * d.nx);
     const size_t s_fft = (size_t)d.nx * sizeof(float2) + 2 * span * sizeof(float2) +
                          (size_t)d.Kx * sizeof(int) + 64;
     const int p2 = d.nx % 3 == 0 ? d.nx / 3 : d.nx;
@@ -1212,7 +1212,7 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     {
       const int p2 = ny % 3 == 0 ? ny / 3 : ny;
       d.cy = std::max(1, std::min(16, 4096 / ny));
-      const size_t cs = ((size_t)ny + 2 * ((((size_t)d.cy * ny) + 15) / 16) * 16) * sizeof(float2);
+      const size_t cs = ((size_t)ny + 2 * (size_t)fftc::span_of(d.cy * ny)) * sizeof(float2);
       d.fft_y = (b->use_fft && (p2 & (p2 - 1)) == 0 && cs <= 120 * 1024) ? 1 : 0;
       if (d.fft_y) b->col_smem = std::max(b->col_smem, cs);
     }

@@ -31,6 +31,7 @@ struct FftRowArgs {
   const int* kx;
   const float2* table;  // twiddle buffer of length Nx (rf_fftcore.cuh)
   int Nx, Kx, rows, R;
+  FastDiv dL, dKx;      // division by Nx and Kx
   long long N;
   float invN;
   LawParams law;
@@ -49,9 +50,9 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   const int L = a.Nx;
   const int S = a.R * NC;              // real lines in this block
   const int P = (S + 1) / 2;           // packed complex sequences
-  float2* tw = reinterpret_cast<float2*>(smem);    // stage twiddles, < 3 L / 2 entries
-  float2* b0 = tw + (3 * L) / 2 + 1;
-  const int span = ((P * L + 15) / 16) * 16;   // the swizzle permutes within 16-element blocks
+  float2* tw = reinterpret_cast<float2*>(smem);    // stage twiddles
+  float2* b0 = tw + fftc::stage_len(L);
+  const int span = fftc::span_of(P * L);
   float2* b1 = b0 + span;
   int* kxs = reinterpret_cast<int*>(b1 + span);   // past b1's rounded span
   __shared__ double red[8];
@@ -80,7 +81,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
         tl[pass][m] = make_float2(0.f, 0.f);
         const int u = base + tid + m * blockDim.x;
         if (u < nsc) {
-          const int p = u / a.Kx, j = u - p * a.Kx;
+          const int p = fdiv(u, a.dKx), j = u - p * a.Kx;
           const int s = 2 * p + pass;
           const int r = s / NC, c = s - r * NC, row = row0 + r;
           if (s < S && row < a.rows) tl[pass][m] = a.T[((long long)row * NC + c) * a.Kx + j];
@@ -90,7 +91,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
     for (int m = 0; m < kBatch; ++m) {
       const int u = base + tid + m * blockDim.x;
       if (u >= nsc) continue;
-      const int p = u / a.Kx, j = u - p * a.Kx;
+      const int p = fdiv(u, a.dKx), j = u - p * a.Kx;
       float2 t = tl[0][m];
       const int k = kxs[j];
       const bool self = (k == 0) || (2 * k == L);
@@ -104,7 +105,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
     for (int m = 0; m < kBatch; ++m) {
       const int u = base + tid + m * blockDim.x;
       if (u >= nsc) continue;
-      const int p = u / a.Kx, j = u - p * a.Kx;
+      const int p = fdiv(u, a.dKx), j = u - p * a.Kx;
       if (2 * p + 1 >= S) continue;
       float2 t = tl[1][m];
       const int k = kxs[j];
@@ -135,7 +136,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
 #pragma unroll
     for (int u = 0; u < kVox; ++u) {
       const int v = vb + tid + u * blockDim.x;
-      const int r = v / L, x = v - r * L, row = row0 + r;
+      const int r = fdiv(v, a.dL), x = v - r * L, row = row0 + r;
       pid[u] = 0;
       if (v < a.R * L && row < a.rows) {
         const long long g = (long long)row * L + x;
@@ -150,7 +151,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
     for (int u = 0; u < kVox; ++u) {
       const int v = vb + tid + u * blockDim.x;
       if (v >= a.R * L) continue;
-      const int r = v / L, x = v - r * L, row = row0 + r;
+      const int r = fdiv(v, a.dL), x = v - r * L, row = row0 + r;
       float e[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -241,7 +242,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   __syncthreads();
   float2* zf = fft_block(other, zb, tw, L, P, -1);
   for (int u = tid; u < S * a.Kx; u += blockDim.x) {
-    const int s = u / a.Kx, j = u - s * a.Kx;
+    const int s = fdiv(u, a.dKx), j = u - s * a.Kx;
     const int r = s / NC, c = s - r * NC, row = row0 + r;
     if (row >= a.rows) continue;
     const int k = kxs[j];
@@ -264,6 +265,7 @@ struct FftColArgs {
   int out_rows;
   const int* out_list;    // nullable: output row i = position out_list[i]
   int ncols, L, C, sign;
+  FastDiv dC;
   const float2* table;
   const int* done;
 };
@@ -273,8 +275,8 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.L, C = a.C;
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* b0 = tw + (3 * L) / 2 + 1;
-  const int span = ((C * L + 15) / 16) * 16;   // the swizzle permutes within 16-element blocks
+  float2* b0 = tw + fftc::stage_len(L);
+  const int span = fftc::span_of(C * L);
   float2* b1 = b0 + span;
   const int col0 = blockIdx.x * C;
   const long long b = blockIdx.y;
@@ -297,7 +299,7 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
       v[u] = make_float2(0.f, 0.f);
       dst[u] = -1;
       if (i < total) {
-        const int r = i / C, cc = i - r * C, col = col0 + cc;
+        const int r = fdiv(i, a.dC), cc = i - r * C, col = col0 + cc;
         if (col < a.ncols) v[u] = in[(long long)r * a.ncols + col];
         dst[u] = cc * L + (a.in_list ? a.in_list[r] : r);
       }
@@ -309,7 +311,7 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
   __syncthreads();
   const float2* z = fft_block(b0, b1, tw, L, C, a.sign);
   for (int i = threadIdx.x; i < a.out_rows * C; i += blockDim.x) {
-    const int r = i / C, cc = i - r * C, col = col0 + cc;
+    const int r = fdiv(i, a.dC), cc = i - r * C, col = col0 + cc;
     if (col >= a.ncols) continue;
     const int pos = a.out_list ? a.out_list[r] : r;
     out[(long long)r * a.ncols + col] = z[sw(cc * L + pos)];
@@ -325,12 +327,12 @@ static int fft_check(rf_ctx* c, const char* what) {
 }
 
 static size_t cols_smem(int L, int C) {
-  return ((size_t)(3 * L) / 2 + 1 + 2 * (((size_t)C * L + 15) / 16) * 16) * sizeof(float2);
+  return ((size_t)fftc::stage_len(L) + 2 * (size_t)fftc::span_of(C * L)) * sizeof(float2);
 }
 
 static size_t row_smem(int L, int nc, int Kx, int R) {
   const int P = (R * nc + 1) / 2;
-  return ((size_t)(3 * L) / 2 + 1 + 2 * (((size_t)P * L + 15) / 16) * 16) * sizeof(float2) +
+  return ((size_t)fftc::stage_len(L) + 2 * (size_t)fftc::span_of(P * L)) * sizeof(float2) +
          (size_t)Kx * sizeof(int) +
          16;
 }
@@ -352,6 +354,7 @@ static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, c
   a.ncols = ncols;
   a.L = L;
   a.C = std::max(1, std::min(c->fft_C, a.ncols));
+  a.dC = make_fastdiv((unsigned)a.C);
   a.sign = sign;
   a.table = tab;
   a.done = done;
@@ -399,6 +402,8 @@ static FftRowArgs fft_row_args(rf_ctx* c, const int* done) {
   a.table = c->d_twx;
   a.Nx = c->nx;
   a.Kx = c->Kx;
+  a.dL = make_fastdiv((unsigned)c->nx);
+  a.dKx = make_fastdiv((unsigned)std::max(1, c->Kx));
   a.rows = c->rows;
   a.R = c->fft_R;
   a.N = c->N;

@@ -6,9 +6,11 @@
 // radix-3 stage when 3 divides L. A stage of radix R with sub-transform size Ns reads element
 // j + r L / R (r < R), multiplies it by exp(sign 2 pi i r k / (R Ns)) with k = j mod Ns, takes
 // the R-point DFT and writes output q to (j / Ns) R Ns + k + q Ns. Sequence p occupies
-// [p L, (p + 1) L) of both buffers; element i lives at sw(i), which permutes the low four index
-// bits by the next four (stride-16 stores then hit different banks, unit-stride accesses stay
-// conflict-free). Buffers must span a multiple of 16 elements so that sw stays inside them.
+// [p L, (p + 1) L) of both buffers; element i lives at sw(i) = i + i / 16 (one pad entry after
+// every 16: stride-16 stores then hit different banks, unit-stride accesses stay
+// conflict-free). Because sw(x + m n) = sw(x) + m (n + n / 16) whenever n is a multiple of 16
+// (or the m-run stays inside one 16-entry block), a stage addresses its R operands from one
+// swizzled base with a fixed stride. Buffers hold span_of(n) entries for n elements.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,7 +22,13 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ int sw(int i) { return i ^ ((i >> 4) & 15); }
+__device__ __forceinline__ int sw(int i) { return i + (i >> 4); }
+// distance between sw(x) and sw(x + n) for n a multiple of 16
+__device__ __forceinline__ int sw_stride(int n) { return n + (n >> 4); }
+
+// entries a buffer needs to hold n elements (even, so that buffers placed back to back keep
+// 16-byte alignment)
+__host__ __device__ inline int span_of(int n) { return (n + (n >> 4) + 2) & ~1; }
 
 __host__ __device__ constexpr int ilog2(int v) {
   int r = 0;
@@ -158,13 +166,21 @@ __device__ inline float2* fft_block(float2* in, float2* out, const float2* tw, i
   int ls = 0;   // log2 Ns
   while (ls + 4 <= lb) {   // radix-16
     const int Ns = 1 << ls, q = L >> 4;
+    const bool lin = (q & 15) == 0;
+    const int pq = sw_stride(q), pn = sw_stride(Ns);
     for (int u = threadIdx.x; u < P * q; u += blockDim.x) {
       int p, j;
       split_item(u, q, pow2, ilog2(L) - 4, p, j);
       const int base_in = p * L + j;
       float2 v[16];
+      if (lin) {
+        const float2* src = in + sw(base_in);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) v[r] = in[sw(base_in + r * q)];
+        for (int r = 0; r < 16; ++r) v[r] = src[r * pq];
+      } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = in[sw(base_in + r * q)];
+      }
       const int k = j & (Ns - 1);
       if (ls > 0) {
 #pragma unroll
@@ -175,9 +191,10 @@ __device__ inline float2* fft_block(float2* in, float2* out, const float2* tw, i
         }
       }
       dft16(v, sign);
-      const int base = p * L + ((j >> ls) << (ls + 4)) + k;
+      // Ns is 1 (base a multiple of 16) or a multiple of 16: always one base and a stride
+      float2* dst = out + sw(p * L + ((j >> ls) << (ls + 4)) + k);
 #pragma unroll
-      for (int qq = 0; qq < 16; ++qq) out[sw(base + qq * Ns)] = v[4 * (qq & 3) + (qq >> 2)];
+      for (int qq = 0; qq < 16; ++qq) dst[qq * pn] = v[4 * (qq & 3) + (qq >> 2)];
     }
     __syncthreads();
     float2* t = in;
@@ -188,12 +205,26 @@ __device__ inline float2* fft_block(float2* in, float2* out, const float2* tw, i
   }
   if (ls + 2 <= lb) {   // one radix-4 stage
     const int Ns = 1 << ls, q = L >> 2;
+    const bool lin = (q & 15) == 0;
+    const bool lout = (Ns & 15) == 0 || (Ns == 1 && (L & 15) == 0);
+    const int pq = sw_stride(q), pn = sw_stride(Ns);
     for (int u = threadIdx.x; u < P * q; u += blockDim.x) {
       int p, j;
       split_item(u, q, pow2, ilog2(L) - 2, p, j);
       const int base_in = p * L + j;
-      float2 v0 = in[sw(base_in)], v1 = in[sw(base_in + q)], v2 = in[sw(base_in + 2 * q)],
-             v3 = in[sw(base_in + 3 * q)];
+      float2 v0, v1, v2, v3;
+      if (lin) {
+        const float2* src = in + sw(base_in);
+        v0 = src[0];
+        v1 = src[pq];
+        v2 = src[2 * pq];
+        v3 = src[3 * pq];
+      } else {
+        v0 = in[sw(base_in)];
+        v1 = in[sw(base_in + q)];
+        v2 = in[sw(base_in + 2 * q)];
+        v3 = in[sw(base_in + 3 * q)];
+      }
       const int k = j & (Ns - 1);
       if (ls > 0) {
         float2 w1 = tw[off + k], w2 = tw[off + Ns + k], w3 = tw[off + 2 * Ns + k];
@@ -208,10 +239,18 @@ __device__ inline float2* fft_block(float2* in, float2* out, const float2* tw, i
       }
       dft4(v0, v1, v2, v3, sign);
       const int base = p * L + ((j >> ls) << (ls + 2)) + k;
-      out[sw(base)] = v0;
-      out[sw(base + Ns)] = v1;
-      out[sw(base + 2 * Ns)] = v2;
-      out[sw(base + 3 * Ns)] = v3;
+      if (lout) {
+        float2* dst = out + sw(base);
+        dst[0] = v0;
+        dst[pn] = v1;
+        dst[2 * pn] = v2;
+        dst[3 * pn] = v3;
+      } else {
+        out[sw(base)] = v0;
+        out[sw(base + Ns)] = v1;
+        out[sw(base + 2 * Ns)] = v2;
+        out[sw(base + 3 * Ns)] = v3;
+      }
     }
     __syncthreads();
     float2* t = in;

@@ -241,6 +241,24 @@ struct rf_ctx {
 
 namespace rfk {
 
+// Division by a kernel-invariant divisor d in [1, 2^31) as a multiply-high, an add and a shift
+// (round-up multiplier method of Granlund and Montgomery, 1994): with s = ceil(log2 d) and
+// m = floor(2^32 (2^s - d) / d) + 1, n / d = (umulhi(n, m) + n) >> s for 0 <= n < 2^31.
+struct FastDiv {
+  unsigned m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned s = 0;
+  while ((1ull << s) < d) ++s;
+  const unsigned long long m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+  return FastDiv{(unsigned)m, s};
+}
+
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+  return (int)((__umulhi((unsigned)n, f.m) + (unsigned)n) >> f.s);
+}
+
 // Programmatic dependent launch: the kernel may be scheduled while its predecessor in the stream
 // drains; it runs its independent prologue (tables, shared-memory setup) and then calls
 // grid_dep_wait() before it reads anything the predecessor writes. Every block reaches the wait
