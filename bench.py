@@ -51,13 +51,15 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--cpu-iters", type=int, default=4, help="oracle updates in the CPU sample")
+    p.add_argument("--cpu-iters", type=int, default=12, help="oracle updates in the CPU sample")
     p.add_argument("--transform", default="fft", choices=["fft", "dft"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_tf32"])
     p.add_argument("--fft-rows", type=int, default=0,
                    help="c2 FFT mode: rows per row-kernel block (0: autotuned)")
     p.add_argument("--fft-cols", type=int, default=0,
                    help="c2 FFT mode: columns per column-kernel block (0: autotuned)")
+    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1],
+                   help="c2 FFT mode: fused column phase on (1), off (-1), or timed (0)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
@@ -184,6 +186,10 @@ def stage_work(name, info, shape, transform, nc=3, ns=4):
             flops = nc * Kx * 5 * ny * math.log2(ny)
         else:
             flops = 8.0 * ny * Ky * nc * Kx
+    elif name == "column_phase":
+        # forward and inverse y transforms of all line columns, Green operator at the pattern
+        byts = 2 * ny * nc * Kx * 8 + 2 * info["K_half"] * nc * 8
+        flops = 2 * nc * Kx * 5 * ny * math.log2(ny)
     else:
         flops, byts = 0.0, 0.0
     return flops, byts
@@ -526,11 +532,14 @@ def main():
     pattern = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
     tiles = {}
     if args.transform == "fft":
-        tiles = dict(fft_rows=args.fft_rows, fft_cols=args.fft_cols)
+        tiles = dict(fft_rows=args.fft_rows, fft_cols=args.fft_cols, fft_fuse=args.fft_fuse)
     if args.profile_updates > 0:
         s = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=0.0,
                       max_iter=args.profile_updates, transform=args.transform,
                       precision=args.precision, **tiles)
+        # traced mode replays plain chunk graphs (the same kernels) instead of the graph with
+        # a conditional while node, whose kernel nodes a profiler cannot capture one by one
+        s.rf_set_tracing(True)
         out = s.rf_solve(path[0])
         n_launch = s.rf_get_info()["kernel_launches"]
         s.close()
@@ -540,7 +549,8 @@ def main():
                        transform=args.transform, precision=args.precision, **tiles)
     info = solver.rf_get_info()
     tile_info = {k: info[k] for k in ("fft_rows", "fft_row_threads", "fft_cols",
-                                      "fft_col_threads")} if args.transform == "fft" else None
+                                      "fft_col_threads", "fft_fused", "fft_fuse_kx",
+                                      "fft_fuse_threads")} if args.transform == "fft" else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -600,12 +610,13 @@ def main():
     clocks = clk.summary()
     sm_max = clocks["sm_max_mhz"] or 2070.0
     props = torch.cuda.get_device_properties(local)
-    kernel_names = {("fft", "row"): "k_fft_row", ("fft", "inverse_y"): "k_fft_cols",
+    kernel_names = {("fft", "row"): "k_fft_row", ("fft", "column_phase"): "k_fft_colphase",
+                    ("fft", "inverse_y"): "k_fft_cols",
                     ("fft", "forward_y"): "k_fft_cols", ("dft", "row"): "k_row",
                     ("dft", "inverse_y"): "k_dft_axis", ("dft", "forward_y"): "k_dft_axis"}
     if args.precision != "fp32" and dom == "row":
         kernel_names[("dft", "row")] = "k_tc_row"
-    if args.transform == "fft" and dom in ("row", "inverse_y", "forward_y"):
+    if args.transform == "fft" and dom in ("row", "inverse_y", "forward_y", "column_phase"):
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
         kname = kernel_names[("fft", dom)]

@@ -104,7 +104,14 @@ typedef struct rf_phase {
  *             precision RF_PREC_FP32. Both compute the same restricted transform.
  *  fft_rows, fft_cols  FFT mode tiles: grid rows per row-kernel block and line columns per
  *             column-kernel block (0 = chosen by timing a few launches of each candidate when
- *             the pattern is set). Results do not depend on them. */
+ *             the pattern is set). Results do not depend on them.
+ *  fft_fuse   2D FFT mode: 1 runs the forward transform along y, the Green-operator update with
+ *             the convergence decision and the inverse transform along y of every group of kx
+ *             columns in one kernel (steps b to d of Sec. 4 between two row passes); -1 keeps
+ *             three kernels; 0 = chosen by timing both when the pattern is set. Must be 0 or -1
+ *             in 3D. The two give the same update up to the order of FP64 summation in the
+ *             convergence measure.
+ *  fft_fuse_kx  kx columns per block of the fused kernel (0 = chosen by timing; 1..16). */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
@@ -115,6 +122,8 @@ typedef struct rf_options {
   int32_t transform;
   int32_t fft_rows;
   int32_t fft_cols;
+  int32_t fft_fuse;
+  int32_t fft_fuse_kx;
 } rf_options;
 
 /* Run statistics of the last solve on a context. */
@@ -131,6 +140,9 @@ typedef struct rf_info {
   int32_t fft_row_threads;/* FFT mode: threads per row-kernel block, else 0 */
   int32_t fft_cols;       /* FFT mode: columns per column-kernel block, else 0 */
   int32_t fft_col_threads;/* FFT mode: threads per column-kernel block, else 0 */
+  int32_t fft_fused;      /* 1 when the fused column phase is in use (see fft_fuse), else 0 */
+  int32_t fft_fuse_kx;    /* kx columns per fused block, else 0 */
+  int32_t fft_fuse_threads;/* threads per fused block, else 0 */
 } rf_info;
 
 /* Create a solver context for one microstructure.
@@ -192,7 +204,8 @@ int rf_get_info(const rf_ctx* ctx, rf_info* info);
  * that did work (not the ones skipped after convergence) are accumulated per stage.
  * Stages: 0 inverse transform along z, 1 inverse along y, 2 row kernel (transforms along x,
  * constitutive law, polarization), 3 forward along y, 4 forward along z, 5 Green-operator
- * update, 6 convergence check, 7 final pass (fields, homogenised stress, commit).
+ * update with the convergence decision, 6 fused column phase (2D FFT mode with fft_fuse:
+ * stages 3, 5 and 1 in one kernel), 7 final pass (fields, homogenised stress, commit).
  * rf_get_stage_times fills ms_total[8] (milliseconds) and counts[8] (launches timed). */
 int rf_set_tracing(rf_ctx* ctx, int on);
 int rf_get_stage_times(const rf_ctx* ctx, double ms_total[8], int64_t counts[8]);

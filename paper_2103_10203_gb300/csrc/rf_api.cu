@@ -269,6 +269,9 @@ void free_pattern(rf_ctx* c) {
   dfree(c->d_phiF);
   dfree(c->d_Tout);
   dfree(c->d_tc_err);
+  dfree(c->d_jptr);
+  dfree(c->d_jlist);
+  c->fft_fused = false;
   c->have_pattern = false;
   c->fields_valid = false;
 }
@@ -307,6 +310,15 @@ int init_status(rf_ctx* c, const double* macro) {
 int run_iterations(rf_ctx* c) {
   const int maxchunk = c->opt.check_every > 0 ? c->opt.check_every : 32;
   int chunk = std::min(4, maxchunk);
+  if (c->fft_fused) {
+    // a fused update ends with the inverse transform along y of its new coefficients, so the
+    // first one needs the line transforms of the start coefficients
+    const bool tr = c->tracing;
+    c->tracing = false;
+    const int e = fft_inverse_stages(c, nullptr);
+    c->tracing = tr;
+    if (e) return e;
+  }
   if (!c->tracing) get_while_graph(c);
   if (!c->tracing && c->while_exec) {
     if (int e = ck(cudaGraphLaunch(c->while_exec, c->stream), "graph launch")) return e;
@@ -409,6 +421,10 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
     return invalid("options: unknown transform");
   if (opt->fft_rows < 0 || opt->fft_rows > 64 || opt->fft_cols < 0 || opt->fft_cols > 64)
     return invalid("options: fft_rows and fft_cols in [0, 64]");
+  if (opt->fft_fuse < -1 || opt->fft_fuse > 1 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
+    return invalid("options: fft_fuse in {-1, 0, 1}, fft_fuse_kx in [0, 16]");
+  if (opt->fft_fuse == 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))
+    return invalid("options: fft_fuse = 1 needs the FFT transform on a 2D grid");
   if (opt->transform == RF_TRANSFORM_FFT) {
     // 2^b or 3 * 2^b (the FFT stages are radix 16, 4, 2 and one radix-3)
     auto pow2 = [](int v) {
@@ -645,7 +661,29 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err && c->dim == 3) err = dalloc(&c->d_T2, (size_t)c->nz * c->Ky * NCK, "line transforms");
   if (!err && c->dim == 3) err = dalloc(&c->d_T2f, (size_t)c->nz * c->Ky * NCK, "line transforms");
   if (!err) err = dalloc(&c->d_OUT, (size_t)splits * c->rect, "partials");
-  if (!err) err = dalloc(&c->d_part, (size_t)((c->Kh + kGammaBlock - 1) / kGammaBlock), "partials");
+  // block partials of the convergence measure: Green kernel blocks, or fused blocks (<= Kx)
+  if (!err)
+    err = dalloc(&c->d_part,
+                 (size_t)std::max<long long>((c->Kh + kGammaBlock - 1) / kGammaBlock, c->Kx),
+                 "partials");
+  const bool fuse_ok = c->opt.transform == RF_TRANSFORM_FFT && c->dim == 2 && c->opt.fft_fuse >= 0;
+  if (!err && fuse_ok) {
+    // half-pattern entries grouped by kx index (counting sort) for the fused column phase
+    std::vector<int> jptr(c->Kx + 1, 0), jlist(std::max<long long>(c->Kh, 1));
+    for (long long h = 0; h < c->Kh; ++h) ++jptr[c->h_hidx[h].j + 1];
+    for (int j = 0; j < c->Kx; ++j) jptr[j + 1] += jptr[j];
+    std::vector<int> fill(jptr.begin(), jptr.end() - 1);
+    for (long long h = 0; h < c->Kh; ++h) jlist[fill[c->h_hidx[h].j]++] = (int)h;
+    err = dalloc(&c->d_jptr, jptr.size(), "pattern");
+    if (!err) err = dalloc(&c->d_jlist, jlist.size(), "pattern");
+    if (!err)
+      err = ck(cudaMemcpy(c->d_jptr, jptr.data(), sizeof(int) * jptr.size(), cudaMemcpyHostToDevice),
+               "up");
+    if (!err)
+      err = ck(cudaMemcpy(c->d_jlist, jlist.data(), sizeof(int) * jlist.size(),
+                          cudaMemcpyHostToDevice),
+               "up");
+  }
   if (!err) err = dalloc(&c->d_counter, 1, "counter");
   if (!err) err = ck(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), c->stream), "memset");
   if (!err) err = dalloc(&c->d_sbar_part, (size_t)part_blocks * 6, "partials");
@@ -891,6 +929,9 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   info->fft_row_threads = fft ? c->fft_row_threads : 0;
   info->fft_cols = fft ? c->fft_C : 0;
   info->fft_col_threads = fft ? c->fft_col_threads : 0;
+  info->fft_fused = c->fft_fused ? 1 : 0;
+  info->fft_fuse_kx = c->fft_fused ? c->fft_M : 0;
+  info->fft_fuse_threads = c->fft_fused ? c->fft_M_threads : 0;
   return RF_OK;
 }
 

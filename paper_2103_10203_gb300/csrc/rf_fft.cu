@@ -11,6 +11,7 @@
 // FP32 twiddle table computed in FP64.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "rf_fftcore.cuh"
 #include "rf_internal.cuh"
@@ -318,6 +319,154 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
   }
 }
 
+// Fused column phase (2D): steps b to d of Sec. 4 between two row passes for a group of M
+// consecutive kx columns with all NC components. The forward transforms along y of the
+// polarization lines give tau^ at every ky; the Green operator of the reference medium
+// (Sec. 3) turns tau^ into the new strain coefficients at the group's pattern entries
+// (eps^ = -Gamma0 : tau^, N ebar at the zero frequency, 0 at null frequencies), which are
+// stored, summed into the convergence measure (FP64 block partials; the last block takes the
+// decision) and scattered into zeroed columns for the inverse transforms along y. Frequencies
+// of different kx never meet in these steps, so each group is independent of the others.
+struct ColPhaseArgs {
+  const float2* T1p;      // [ny][NC][Kx] polarization line coefficients (row pass output)
+  float2* T1;             // [ny][NC][Kx] strain line coefficients (next row pass input)
+  float2* ER;             // [Ky][NC][Kx] strain coefficients on the (ky, kx) rectangle
+  const int* jptr;        // [Kx + 1]
+  const int* jlist;       // half-pattern entries grouped by kx index
+  const HIdx* hidx;
+  const float4* hn;       // unit wave vector and multiplicity
+  const int* kym;         // position (ky mod Ny) of each rectangle row
+  const float2* table;    // twiddle buffer of length Ny
+  int Kx, L, M;
+  FastDiv dC;             // division by NC * M
+  float inv2mu0, cgam;
+  Status* st;
+  unsigned* counter;      // blocks finished (reset to 0 by the last block)
+  double* part;           // [gridDim.x]
+  const int* done;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
+};
+
+template <int NC>
+__global__ __launch_bounds__(256) void k_fft_colphase(ColPhaseArgs a, double Nd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const int L = a.L, M = a.M, C = NC * M;   // sequence q = jj NC + c
+  const int j0 = blockIdx.x * M;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* b0 = tw + fftc::stage_len(L);
+  const int span = fftc::span_of(C * L);
+  float2* b1 = b0 + span;
+  copy_twiddles(a.table, L, tw);
+  const int e0 = a.jptr[j0], e1 = a.jptr[min(j0 + M, a.Kx)];
+  grid_dep_wait();
+  if (a.done && __ldcg(a.done)) return;   // the same flag value for every thread of the grid
+  // polarization lines of the group, loads in batches of 8 (kx past the last column read 0)
+  const int tot = L * C;
+  for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * blockDim.x) {
+    float2 v[8];
+    int dst[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = make_float2(0.f, 0.f);
+      dst[u] = -1;
+      if (i < tot) {
+        const int y = fdiv(i, a.dC), q = i - y * C;
+        const int jj = q / NC, c = q - jj * NC;
+        if (j0 + jj < a.Kx) v[u] = a.T1p[((long long)y * NC + c) * a.Kx + j0 + jj];
+        dst[u] = q * L + y;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (dst[u] >= 0) b0[sw(dst[u])] = v[u];
+  }
+  __syncthreads();
+  const float2* z = fft_block(b0, b1, tw, L, C, -1);
+  float2* w = (z == b0) ? b1 : b0;   // free after the last stage's barrier
+  for (int i = threadIdx.x; i < span; i += blockDim.x) w[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  double diff = 0.0;
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int h = a.jlist[e];
+    const HIdx hi = a.hidx[h];
+    const float4 n = a.hn[h];
+    const int jj = hi.j - j0, pos = a.kym[hi.iy];
+    const long long base = ((long long)hi.iy * NC) * a.Kx + hi.j;
+    float er[NC], ei[NC];
+    if (hi.kind == 1) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        er[c] = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
+        ei[c] = 0.f;
+      }
+    } else if (hi.kind == 2) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) er[c] = ei[c] = 0.f;
+    } else {
+      float tr[NC], ti[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float2 t = z[sw((jj * NC + c) * L + pos)];
+        tr[c] = t.x;
+        ti[c] = t.y;
+      }
+      float t6[6], o6[6];
+      comp_to6<NC>(tr, t6);
+      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) er[c] = -o6[comp6<NC>(c)];
+      comp_to6<NC>(ti, t6);
+      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
+    }
+    float d = 0.f;   // one frequency's squared increment (at most six non-negative terms)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float2 old = a.ER[base + (long long)c * a.Kx];
+      const float dr = er[c] - old.x, di = ei[c] - old.y;
+      const float wc = (comp6<NC>(c) >= 3) ? 2.f : 1.f;   // Frobenius: shear counted twice
+      d = fmaf(n.w * wc, dr * dr + di * di, d);
+      const float2 nv = make_float2(er[c], ei[c]);
+      a.ER[base + (long long)c * a.Kx] = nv;
+      w[sw((jj * NC + c) * L + pos)] = nv;
+    }
+    diff += (double)d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = diff;
+  __syncthreads();   // also orders the scattered coefficients before the inverse transforms
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    a.part[blockIdx.x] = t;
+    __threadfence();
+    last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    decide(a.part, gridDim.x, a.st, sh);
+    if (threadIdx.x == 0) {
+      *a.counter = 0u;
+      // the only call site of the loop condition in this mode: one thread of one block
+      if (a.use_cond && a.st->done) cudaGraphSetConditional(a.cond, 0u);
+    }
+  }
+  const float2* zi = fft_block(w, const_cast<float2*>(z), tw, L, C, +1);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int y = fdiv(i, a.dC), q = i - y * C;
+    const int jj = q / NC, c = q - jj * NC;
+    if (j0 + jj < a.Kx) a.T1[((long long)y * NC + c) * a.Kx + j0 + jj] = zi[sw(q * L + y)];
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // host side
 static int fft_check(rf_ctx* c, const char* what) {
@@ -338,6 +487,10 @@ static size_t row_smem(int L, int nc, int Kx, int R) {
 }
 
 constexpr size_t kFftSmemMax = 200 * 1024;
+
+static size_t colphase_smem(int L, int nc, int M) {
+  return ((size_t)fftc::stage_len(L) + 2 * (size_t)fftc::span_of(nc * M * L)) * sizeof(float2);
+}
 
 static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, const int* in_list,
                     float2* out, long long out_bs, int out_rows, const int* out_list, int ncols,
@@ -389,6 +542,21 @@ int fft_geometry(rf_ctx* c) {
     return RF_ERR_INVALID;
   }
   c->fft_C = C;
+  // fused column phase (2D): kx columns per block within shared memory
+  c->fft_fused = false;
+  c->fft_M = std::max(1, std::min(c->opt.fft_fuse_kx > 0 ? c->opt.fft_fuse_kx : 1, c->Kx));
+  c->fft_M_threads = 256;
+  if (c->dim == 2 && c->opt.fft_fuse >= 0) {
+    while (c->fft_M > 1 && colphase_smem(c->ny, c->nc, c->fft_M) > kFftSmemMax) --c->fft_M;
+    const bool fits = colphase_smem(c->ny, c->nc, c->fft_M) <= kFftSmemMax;
+    if (c->opt.fft_fuse == 1) {
+      if (!fits) {
+        set_error("FFT mode: columns too long for the fused column kernel's shared memory");
+        return RF_ERR_INVALID;
+      }
+      c->fft_fused = true;
+    }
+  }
   return RF_OK;
 }
 
@@ -416,6 +584,7 @@ static FftRowArgs fft_row_args(rf_ctx* c, const int* done) {
 void init_attributes_fft() {
   const int s = 200 * 1024;
   cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_colphase<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_fft_row<3, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_fft_row<3, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_fft_row<3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
@@ -494,6 +663,39 @@ int fft_forward_stages(rf_ctx* c, const int* done) {
                   -1, c->d_twy, done);
 }
 
+int launch_fft_colphase(rf_ctx* c, const int* done) {
+  ColPhaseArgs a{};
+  a.T1p = c->d_T1p;
+  a.T1 = c->d_T1;
+  a.ER = c->d_ER;
+  a.jptr = c->d_jptr;
+  a.jlist = c->d_jlist;
+  a.hidx = c->d_hidx;
+  a.hn = c->d_hn;
+  a.kym = c->d_kym;
+  a.table = c->d_twy;
+  a.Kx = c->Kx;
+  a.L = c->ny;
+  a.M = c->fft_M;
+  a.dC = make_fastdiv((unsigned)(c->nc * c->fft_M));
+  a.inv2mu0 = (float)(0.5 / c->mu0);
+  a.cgam = (float)((c->lam0 + c->mu0) / (c->mu0 * (c->lam0 + 2.0 * c->mu0)));
+  a.st = c->d_status;
+  a.counter = c->d_counter;
+  a.part = c->d_part;
+  a.done = done;
+  a.cond = c->while_cond;
+  a.use_cond = c->capturing_while ? 1 : 0;
+  trace_stage(c, 6);
+  const dim3 grid((unsigned)((c->Kx + c->fft_M - 1) / c->fft_M));
+  cudaError_t e = launch_pdl(k_fft_colphase<3>, grid, dim3(c->fft_M_threads),
+                             colphase_smem(c->ny, c->nc, c->fft_M), c->stream, a, (double)c->N);
+  if (e != cudaSuccess) return cuda_fail(e, "fft column phase");
+  const int r = fft_check(c, "fft column phase");
+  trace_end(c);
+  return r;
+}
+
 static int tck(cudaError_t e, const char* what) { return e == cudaSuccess ? RF_OK : cuda_fail(e, what); }
 
 // Autotuner for the FFT tiles: each candidate runs one untimed launch and then three timed groups
@@ -501,7 +703,12 @@ static int tck(cudaError_t e, const char* what) { return e == cudaSuccess ? RF_O
 // context's own buffers; the candidate with the fastest group stays. Candidates that exceed
 // shared memory are skipped.
 int fft_autotune(rf_ctx* c) {
-  if (c->opt.fft_rows > 0 && c->opt.fft_cols > 0) return RF_OK;
+  // fused column phase: compared with the three separate kernels (fft_fuse = 0), or only its
+  // block shape chosen (fft_fuse = 1 without fft_fuse_kx)
+  const bool fuse_auto = c->dim == 2 && c->opt.fft_fuse == 0 && c->d_jptr &&
+                         colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
+  const bool fuse_shape = c->fft_fused && c->opt.fft_fuse_kx == 0;
+  if (c->opt.fft_rows > 0 && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape) return RF_OK;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "tuner");
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -512,6 +719,9 @@ int fft_autotune(rf_ctx* c) {
   const int NCK = c->nc * c->Kx;
   err = tck(cudaMemsetAsync(c->d_T1, 0, sizeof(float2) * (size_t)c->rows * NCK, c->stream), "tuner");
   if (!err) err = tck(cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream), "tuner");
+  if (!err)
+    err = tck(cudaMemsetAsync(c->d_T1p, 0, sizeof(float2) * (size_t)c->rows * NCK, c->stream),
+              "tuner");
   // the fastest of three timed groups of three launches (one untimed launch first): the
   // minimum is robust to a stray slow launch, so repeated tunings of one pattern agree
   auto time_it = [&](auto&& run, float* ms) -> int {
@@ -576,6 +786,39 @@ int fft_autotune(rf_ctx* c) {
     }
     c->fft_C = bestC;
     c->fft_col_threads = bestT;
+  }
+  if (!err && (fuse_auto || fuse_shape)) {
+    const std::vector<int> Ms = c->opt.fft_fuse_kx > 0 ? std::vector<int>{c->opt.fft_fuse_kx}
+                                                       : std::vector<int>{1, 2, 4};
+    float best = 1e30f;
+    int bestM = c->fft_M, bestT = c->fft_M_threads;
+    for (int M : Ms) {
+      if (M > std::max(1, c->Kx) || colphase_smem(c->ny, c->nc, M) > kFftSmemMax) continue;
+      for (int T : {128, 256}) {
+        c->fft_M = M;
+        c->fft_M_threads = T;
+        float ms = 0.f;
+        err = time_it([&] { return launch_fft_colphase(c, nullptr); }, &ms);
+        if (err) break;
+        if (ms < best) {
+          best = ms;
+          bestM = M;
+          bestT = T;
+        }
+      }
+      if (err) break;
+    }
+    c->fft_M = bestM;
+    c->fft_M_threads = bestT;
+    if (!err && fuse_auto) {
+      float sep = 1e30f;
+      err = time_it([&] {
+        if (int e = fft_forward_stages(c, nullptr)) return e;
+        if (int e = launch_gamma_finalize(c, 1, nullptr)) return e;
+        return fft_inverse_stages(c, nullptr);
+      }, &sep);
+      c->fft_fused = !err && best < sep;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

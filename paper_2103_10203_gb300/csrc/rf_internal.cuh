@@ -184,6 +184,11 @@ struct rf_ctx {
   int fft_R = 0, fft_blocks = 0, fft_C = 0;
   int fft_row_threads = 256, fft_col_threads = 256;   // block sizes (autotuned with the tiles)
   size_t fft_smem = 0;
+  // fused column phase (2D): forward y + Green operator + decision + inverse y per kx group
+  bool fft_fused = false;
+  int fft_M = 1, fft_M_threads = 256;   // kx columns and threads per fused block
+  int* d_jptr = nullptr;                // [Kx + 1] offsets of each kx's entries in d_jlist
+  int* d_jlist = nullptr;               // half-pattern entries grouped by kx index
 
   // split-precision (tensor-core) transforms along x
   unsigned char* d_phiI = nullptr;
@@ -259,6 +264,29 @@ __device__ __forceinline__ int fdiv(int n, FastDiv f) {
   return (int)((__umulhi((unsigned)n, f.m) + (unsigned)n) >> f.s);
 }
 
+// convergence decision from the block partials, in a fixed summation order (one block)
+__device__ inline void decide(const double* part, int n, Status* st, double* sh) {
+  if (threadIdx.x >= 32) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) s += __ldcg(part + i);
+  sh[threadIdx.x] = s;
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < 32; ++i) tot += sh[i];
+    double r = sqrt(tot * st->inv_n2);
+    if (st->enorm > 0.0) r /= st->enorm;
+    st->iters += 1;
+    st->last_r = r;
+    if (!isfinite(r)) {
+      st->nonfinite = 1;
+      st->done = 1;
+    } else if (r < st->tol || st->iters >= st->max_iter || st->timeout) {
+      st->done = 1;
+    }
+  }
+}
+
 // Programmatic dependent launch: the kernel may be scheduled while its predecessor in the stream
 // drains; it runs its independent prologue (tables, shared-memory setup) and then calls
 // grid_dep_wait() before it reads anything the predecessor writes. Every block reaches the wait
@@ -303,6 +331,8 @@ int fft_autotune(rf_ctx* c);
 int launch_fft_row(rf_ctx* c, const int* done, bool final_pass, int commit);
 int fft_inverse_stages(rf_ctx* c, const int* done);
 int fft_forward_stages(rf_ctx* c, const int* done);
+int launch_fft_colphase(rf_ctx* c, const int* done);
+int launch_gamma_finalize(rf_ctx* c, int splits, const int* done);
 void trace_begin(rf_ctx* c, long long idx);
 void trace_stage(rf_ctx* c, int stage);
 void trace_end(rf_ctx* c);

@@ -288,28 +288,6 @@ __global__ __launch_bounds__(256) void k_row(RowArgs a) {
 
 // ------------------------------------------------------------------------------------------
 
-// convergence decision from the block partials, in a fixed summation order (one block)
-__device__ void decide(const double* part, int n, Status* st, double* sh) {
-  if (threadIdx.x >= 32) return;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) s += __ldcg(part + i);
-  sh[threadIdx.x] = s;
-  __syncwarp();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int i = 0; i < 32; ++i) tot += sh[i];
-    double r = sqrt(tot * st->inv_n2);
-    if (st->enorm > 0.0) r /= st->enorm;
-    st->iters += 1;
-    st->last_r = r;
-    if (!isfinite(r)) {
-      st->nonfinite = 1;
-      st->done = 1;
-    } else if (r < st->tol || st->iters >= st->max_iter || st->timeout) {
-      st->done = 1;
-    }
-  }
-}
 
 template <int NC>
 __global__ __launch_bounds__(kGammaBlock) void k_gamma(GammaArgs a, double Nd) {
@@ -633,6 +611,13 @@ int launch_iteration(rf_ctx* c) {
   const int* done = &c->d_status->done;
   trace_begin(c, c->launched_iters++);
   const bool fftm = c->opt.transform == RF_TRANSFORM_FFT;
+  if (fftm && c->fft_fused) {
+    // row pass, then forward y + Green operator + decision + inverse y in one kernel (the
+    // inverse of the start coefficients runs once before the first update)
+    trace_stage(c, 2);
+    if (int e = launch_fft_row(c, done, false, 0)) return e;
+    return launch_fft_colphase(c, done);
+  }
   if (fftm) {
     if (int e = fft_inverse_stages(c, done)) return e;
     trace_stage(c, 2);

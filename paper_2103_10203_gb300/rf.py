@@ -35,7 +35,8 @@ class rf_phase(C.Structure):
 class rf_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("green", C.c_int32),
                 ("ref_medium", C.c_int32), ("precision", C.c_int32), ("check_every", C.c_int32),
-                ("transform", C.c_int32), ("fft_rows", C.c_int32), ("fft_cols", C.c_int32)]
+                ("transform", C.c_int32), ("fft_rows", C.c_int32), ("fft_cols", C.c_int32),
+                ("fft_fuse", C.c_int32), ("fft_fuse_kx", C.c_int32)]
 
 
 class rf_info(C.Structure):
@@ -44,7 +45,8 @@ class rf_info(C.Structure):
                 ("kernel_launches", C.c_int64), ("j2_max_violation", C.c_double),
                 ("lambda0", C.c_double), ("mu0", C.c_double), ("fft_rows", C.c_int32),
                 ("fft_row_threads", C.c_int32), ("fft_cols", C.c_int32),
-                ("fft_col_threads", C.c_int32)]
+                ("fft_col_threads", C.c_int32), ("fft_fused", C.c_int32),
+                ("fft_fuse_kx", C.c_int32), ("fft_fuse_threads", C.c_int32)]
 
 
 class rf_mlp_dims(C.Structure):
@@ -145,7 +147,8 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_mlp_adam", "rf_mlp_train_step", "rf_mlp_predict_warm", "rf_mlp_launches",
             "rf_mlp_destroy"]
 
-STAGES = ["inverse_z", "inverse_y", "row", "forward_y", "forward_z", "green", "check", "final"]
+STAGES = ["inverse_z", "inverse_y", "row", "forward_y", "forward_z", "green", "column_phase",
+          "final"]
 
 
 def _check(code, allow_nc=True):
@@ -191,13 +194,15 @@ def make_phases(table) -> C.Array:
 
 
 def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
-                 check_every=0, transform="dft", fft_rows=0, fft_cols=0) -> rf_options:
+                 check_every=0, transform="dft", fft_rows=0, fft_cols=0, fft_fuse=0,
+                 fft_fuse_kx=0) -> rf_options:
     o = rf_options()
     o.tol, o.max_iter = float(tol), int(max_iter)
     o.green, o.ref_medium = GREEN[green], REF[ref]
     o.precision, o.check_every = PRECISION[precision], int(check_every)
     o.transform = TRANSFORM[transform]
     o.fft_rows, o.fft_cols = int(fft_rows), int(fft_cols)
+    o.fft_fuse, o.fft_fuse_kx = int(fft_fuse), int(fft_fuse_kx)
     return o
 
 

@@ -425,6 +425,74 @@ def test_fft_small_sides(lib, shape, rows, cols):
     assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
 
 
+@pytest.mark.parametrize("name,kx", [("j2_64", 1), ("j2_64", 3), ("rect", 2), ("three", 4),
+                                     ("c1", 1), ("fullset", 2)])
+def test_fft_fused_column_phase_matches_oracle(lib, name, kx):
+    """Forward y, Green operator, decision and inverse y in one kernel per group of kx columns
+    (a group count that leaves a partial last group included): the oracle's updates."""
+    pm, ph, macro, pat = _pow2_case(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=6, transform="fft", fft_fuse=1,
+                   fft_fuse_kx=kx)
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    coeffs = s.rf_get_reduced_strain()
+    info = s.rf_get_info()
+    s.close()
+    assert info["fft_fused"] == 1 and info["fft_fuse_kx"] == min(kx, info["Kx"])
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=6)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    want = np.stack([r.eps_hat[:, i, j] for (i, j) in VOIGT], axis=1)
+    assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
+
+
+@pytest.mark.parametrize("shape", [(12, 12), (24, 6), (8, 24)])
+def test_fft_fused_column_phase_small_sides(lib, shape):
+    rng = np.random.default_rng(sum(shape))
+    pm = (rng.random(shape) < 0.35).astype(np.uint8)
+    ph = j2_phases()
+    macro = np.array([0.02, 0, 0, 0, 0, 0.003])
+    pat = O.pattern_adapted(pm, 1, max(8, pm.size // 4))
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=5, transform="fft", fft_fuse=1)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=5)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
+def test_fft_fused_and_separate_column_phases_agree(lib):
+    """Full load path to the tolerance: the fused and the three-kernel column phases take the
+    same decisions (iteration counts within one: FP64 sums in another order) and reach the same
+    answer."""
+    cfg = make_config("c2", n=256)
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    res = {}
+    for fuse in (-1, 1):
+        s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform="fft",
+                       fft_fuse=fuse)
+        res[fuse] = (s.rf_solve_path(uniaxial_path(20, 0.02)[::5]), s.rf_get_fields()[0])
+        s.close()
+    (a, ea), (b, eb) = res[-1], res[1]
+    assert a["converged"] and b["converged"]
+    assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
+    assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
+    assert rel(eb, ea) <= 2e-5
+
+
+def test_fft_fuse_option_checks(lib):
+    pm = np.zeros((8, 16, 16), np.uint8)
+    with pytest.raises(lib.RFError):   # fused column phase is 2D only
+        lib.Solver(pm, elastic_phases(), transform="fft", fft_fuse=1)
+    with pytest.raises(lib.RFError):
+        lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="dft", fft_fuse=1)
+    with pytest.raises(lib.RFError):
+        lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="fft", fft_fuse=2)
+
+
 def test_fft_transform_load_path_and_tolerance(lib):
     pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
     ph = j2_phases()
@@ -493,12 +561,12 @@ def test_fft_transform_rejects_unsupported_sizes(lib):
                    precision="split_bf16")
 
 
-@pytest.mark.parametrize("transform", ["fft", "dft"])
-def test_traced_chunked_and_untraced_while_graph_solves_agree(lib, transform):
+@pytest.mark.parametrize("transform,fuse", [("fft", -1), ("fft", 1), ("dft", 0)])
+def test_traced_chunked_and_untraced_while_graph_solves_agree(lib, transform, fuse):
     """Untraced solves run as one conditional-while graph; traced solves replay chunks of
     updates with stage events. Same kernels and tiles in the same order: identical results
-    (the FFT tiles are pinned: the autotuner's choice changes rounding), and the stage
-    accounting covers the stages the mode runs."""
+    (the FFT tiles and the column-phase choice are pinned: the autotuner's choice changes
+    rounding), and the stage accounting covers the stages the mode runs."""
     pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
     ph = j2_phases()
     pat = O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
@@ -506,15 +574,17 @@ def test_traced_chunked_and_untraced_while_graph_solves_agree(lib, transform):
     res = {}
     for traced in (False, True):
         s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform=transform,
-                       fft_rows=2, fft_cols=4)
+                       fft_rows=2, fft_cols=4, fft_fuse=fuse, fft_fuse_kx=2 if fuse > 0 else 0)
         s.rf_set_tracing(traced)
         res[traced] = s.rf_solve_path(path)
         st = s.rf_get_stage_times()
         info = s.rf_get_info()
         s.close()
+        assert info["fft_fused"] == (1 if fuse > 0 else 0)
         if traced:
             assert st["row"][1] == int(np.sum(res[traced]["iters"])) and st["row"][0] > 0
-            assert st["green"][1] == st["row"][1] and st["final"][1] == len(path)
+            decision = "column_phase" if fuse > 0 else "green"
+            assert st[decision][1] == st["row"][1] and st["final"][1] == len(path)
         assert info["kernel_launches"] > 0
     assert np.array_equal(res[False]["iters"], res[True]["iters"])
     assert np.array_equal(res[False]["sigma_bar"], res[True]["sigma_bar"])
