@@ -65,16 +65,15 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
   for (int i = tid; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
   grid_dep_wait();
-  if (!FINAL && a.done && *a.done) return;   // the same flag value for every thread
-  __syncthreads();
+  const int dn = (!FINAL && a.done) ? *a.done : 0;   // the same flag value for every thread
   // spectra: line s = r * NC + c is the real (s even) or imaginary (s odd) carrier of p = s / 2
   // coefficients are loaded in register batches (both carriers), then scattered: the real
   // carriers write, and after a barrier the imaginary carriers add. The batch loop's trip count
   // is the same for every thread (it contains barriers).
   constexpr int kBatch = 8;
   const int nsc = P * a.Kx;
-  for (int base = 0; base < nsc; base += kBatch * blockDim.x) {
-    float2 tl[2][kBatch];
+  float2 tl[2][kBatch];
+  auto load_batch = [&](int base) {
 #pragma unroll
     for (int pass = 0; pass < 2; ++pass)
 #pragma unroll
@@ -88,6 +87,13 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
           if (s < S && row < a.rows) tl[pass][m] = a.T[((long long)row * NC + c) * a.Kx + j];
         }
       }
+  };
+  // the first batch goes out together with the flag (discarded if it is set)
+  load_batch(0);
+  if (dn) return;
+  __syncthreads();   // the zeroed buffer
+  for (int base = 0; base < nsc; base += kBatch * blockDim.x) {
+    if (base > 0) load_batch(base);
 #pragma unroll
     for (int m = 0; m < kBatch; ++m) {
       const int u = base + tid + m * blockDim.x;
@@ -287,13 +293,13 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
   if (a.in_list)
     for (int i = threadIdx.x; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
   grid_dep_wait();
-  if (a.done && *a.done) return;   // the same flag value for every thread of the block
-  __syncthreads();
-  // loads are issued in batches of 8 per thread before they are stored, so their latencies overlap
+  // loads are issued in batches of 8 per thread before they are stored, so their latencies
+  // overlap; the first batch goes out together with the flag (discarded if it is set)
+  const int dn = a.done ? *a.done : 0;   // the same flag value for every thread of the block
   const int total = a.in_rows * C;
-  for (int i0 = threadIdx.x; i0 < total; i0 += 8 * blockDim.x) {
-    float2 v[8];
-    int dst[8];
+  float2 v[8];
+  int dst[8];
+  auto load_batch = [&](int i0) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int i = i0 + u * blockDim.x;
@@ -305,9 +311,17 @@ __global__ __launch_bounds__(256) void k_fft_cols(FftColArgs a) {
         dst[u] = cc * L + (a.in_list ? a.in_list[r] : r);
       }
     }
+  };
+  load_batch(threadIdx.x);
+  if (dn) return;
+  __syncthreads();   // the zeroed buffer
+  for (int i0 = threadIdx.x;;) {
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (dst[u] >= 0) b0[sw(dst[u])] = v[u];
+    i0 += 8 * blockDim.x;
+    if (i0 >= total) break;
+    load_batch(i0);
   }
   __syncthreads();
   const float2* z = fft_block(b0, b1, tw, L, C, a.sign);

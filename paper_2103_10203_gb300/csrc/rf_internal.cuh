@@ -264,16 +264,28 @@ __device__ __forceinline__ int fdiv(int n, FastDiv f) {
   return (int)((__umulhi((unsigned)n, f.m) + (unsigned)n) >> f.s);
 }
 
-// convergence decision from the block partials, in a fixed summation order (one block)
+// Convergence decision from the block partials, in a fixed summation order. The whole block
+// calls it (block size <= 1024, sh >= 32 entries): each thread sums a fixed strided subset with
+// its loads issued four at a time, then warp trees and the warp sums in order.
 __device__ inline void decide(const double* part, int n, Status* st, double* sh) {
-  if (threadIdx.x >= 32) return;
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += 32) s += __ldcg(part + i);
-  sh[threadIdx.x] = s;
-  __syncwarp();
+  for (int i0 = threadIdx.x; i0 < n; i0 += 4 * blockDim.x) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = i < n ? __ldcg(part + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += v[u];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
   if (threadIdx.x == 0) {
     double tot = 0.0;
-    for (int i = 0; i < 32; ++i) tot += sh[i];
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) tot += sh[w];
     double r = sqrt(tot * st->inv_n2);
     if (st->enorm > 0.0) r /= st->enorm;
     st->iters += 1;

@@ -305,19 +305,22 @@ __global__ __launch_bounds__(kGammaBlock) void k_gamma(GammaArgs a, double Nd) {
     n = a.hn[h];
   }
   grid_dep_wait();
+  // the update's inputs are loaded together with the flag (they are discarded if it is set)
   const int dn = a.done ? __ldcg(a.done) : 0;
-  if (dn) return;
-  float diff = 0.f;
+  const long long base = ((long long)(hi.iz * a.Ky + hi.iy) * NC) * a.Kx + hi.j;
+  const float2* __restrict__ out = a.OUT + base;
+  float2* __restrict__ er_p = a.ER + base;
+  float2 tv[NC], old[NC];
   if (act) {
-    const long long base = ((long long)(hi.iz * a.Ky + hi.iy) * NC) * a.Kx + hi.j;
-    const float2* __restrict__ out = a.OUT + base;
-    float2* __restrict__ er_p = a.ER + base;
-    float2 tv[NC], old[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       tv[c] = out[c * a.Kx];
       old[c] = er_p[c * a.Kx];
     }
+  }
+  if (dn) return;
+  float diff = 0.f;
+  if (act) {
     for (int s = 1; s < a.splits; ++s) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
