@@ -723,6 +723,24 @@ int fft_autotune(rf_ctx* c) {
                          colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
   const bool fuse_shape = c->fft_fused && c->opt.fft_fuse_kx == 0;
   if (c->opt.fft_rows > 0 && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape) return RF_OK;
+  rf_ctx::Tuned& tu = c->tuned;
+  if (tu.valid && tu.Kx == c->Kx && tu.Ky == c->Ky && tu.Kz == c->Kz) {
+    // same transform shapes as the last tuning on this context: same choice
+    if (c->opt.fft_rows <= 0) {
+      set_rows(c, tu.R);
+      c->fft_row_threads = tu.row_threads;
+    }
+    if (c->opt.fft_cols <= 0) {
+      c->fft_C = tu.C;
+      c->fft_col_threads = tu.col_threads;
+    }
+    if (fuse_auto || fuse_shape) {
+      c->fft_M = tu.M;
+      c->fft_M_threads = tu.M_threads;
+      if (fuse_auto) c->fft_fused = tu.fused;
+    }
+    return RF_OK;
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "tuner");
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -836,6 +854,19 @@ int fft_autotune(rf_ctx* c) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (!err) {
+    tu.valid = true;
+    tu.Kx = c->Kx;
+    tu.Ky = c->Ky;
+    tu.Kz = c->Kz;
+    tu.R = c->fft_R;
+    tu.row_threads = c->fft_row_threads;
+    tu.C = c->fft_C;
+    tu.col_threads = c->fft_col_threads;
+    tu.M = c->fft_M;
+    tu.M_threads = c->fft_M_threads;
+    tu.fused = c->fft_fused;
+  }
   return err;
 }
 

@@ -189,6 +189,13 @@ struct rf_ctx {
   int fft_M = 1, fft_M_threads = 256;   // kx columns and threads per fused block
   int* d_jptr = nullptr;                // [Kx + 1] offsets of each kx's entries in d_jlist
   int* d_jlist = nullptr;               // half-pattern entries grouped by kx index
+  // last autotuned choice, reused when a new pattern has the same distinct kx, ky, kz counts
+  struct Tuned {
+    bool valid = false;
+    int Kx = 0, Ky = 0, Kz = 0;
+    int R = 0, row_threads = 0, C = 0, col_threads = 0, M = 0, M_threads = 0;
+    bool fused = false;
+  } tuned;
 
   // split-precision (tensor-core) transforms along x
   unsigned char* d_phiI = nullptr;

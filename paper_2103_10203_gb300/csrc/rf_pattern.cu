@@ -8,6 +8,7 @@
 // is found by binary search over the key with device-side counting.
 // Radial pattern (Sec. 4.1): L equiangular rasterised lines; the same selection machinery
 // ranks pairs by (not on a line, |k|^2, index).
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <mutex>
@@ -94,6 +95,142 @@ __global__ void k_axis_f64(const double2* in, double2* out, int L, int N, long l
 #pragma unroll
   for (int i = 0; i < 4; ++i)
     if (m0 + i < L) ob[(long long)(m0 + i) * N + n] = make_double2(ar[i], ai[i]);
+}
+
+// FP64 Stockham FFTs (forward, exp(-2 pi i m n / L)) for lengths L = 2^b or 3 * 2^b: radix-4
+// stages, one radix-2 stage, then one radix-3 stage. A stage of radix R and sub-transform size
+// Ns reads element j + r L / R, multiplies it by exp(-2 pi i r k / (R Ns)) with k = j mod Ns
+// (tab[t] = exp(-2 pi i t / L)), takes the R-point DFT and writes output q to
+// (j / Ns) R Ns + k + q Ns. The zero frequency only meets the exact factor 1, so for 0/1 data it
+// is an exact sum. C sequences of length L lie back to back in both shared buffers; returns
+// the buffer holding the result. The whole block calls it.
+__device__ __forceinline__ double2 cm64(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 add64(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 sub64(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+
+__device__ double2* fft64_block(double2* in, double2* out, const double2* tab, int L, int C) {
+  const int p2 = (L % 3 == 0) ? L / 3 : L;
+  int Ns = 1;
+  auto swap = [&] {
+    __syncthreads();
+    double2* t = in;
+    in = out;
+    out = t;
+  };
+  while (Ns * 4 <= p2) {
+    const int q = L / 4, step = L / (4 * Ns);
+    for (int u = threadIdx.x; u < C * q; u += blockDim.x) {
+      const int p = u / q, j = u - p * q, k = j % Ns;
+      const double2* src = in + (long long)p * L + j;
+      double2 a0 = src[0], a1 = src[q], a2 = src[2 * q], a3 = src[3 * q];
+      if (Ns > 1) {
+        a1 = cm64(a1, tab[k * step]);
+        a2 = cm64(a2, tab[2 * k * step]);
+        a3 = cm64(a3, tab[3 * k * step]);
+      }
+      const double2 s02 = add64(a0, a2), d02 = sub64(a0, a2);
+      const double2 s13 = add64(a1, a3), d13 = sub64(a1, a3);
+      const double2 md13 = make_double2(d13.y, -d13.x);   // -i (a1 - a3)
+      double2* dst = out + (long long)p * L + (j / Ns) * 4 * Ns + k;
+      dst[0] = add64(s02, s13);
+      dst[Ns] = add64(d02, md13);
+      dst[2 * Ns] = sub64(s02, s13);
+      dst[3 * Ns] = sub64(d02, md13);
+    }
+    swap();
+    Ns *= 4;
+  }
+  if (Ns * 2 <= p2) {
+    const int q = L / 2, step = L / (2 * Ns);
+    for (int u = threadIdx.x; u < C * q; u += blockDim.x) {
+      const int p = u / q, j = u - p * q, k = j % Ns;
+      const double2* src = in + (long long)p * L + j;
+      double2 a0 = src[0], a1 = src[q];
+      if (Ns > 1) a1 = cm64(a1, tab[k * step]);
+      double2* dst = out + (long long)p * L + (j / Ns) * 2 * Ns + k;
+      dst[0] = add64(a0, a1);
+      dst[Ns] = sub64(a0, a1);
+    }
+    swap();
+    Ns *= 2;
+  }
+  if (p2 != L) {   // Ns = L / 3: j = k < Ns, outputs j, j + Ns, j + 2 Ns
+    const double h = 0.86602540378443864676;   // sqrt(3) / 2
+    for (int u = threadIdx.x; u < C * Ns; u += blockDim.x) {
+      const int p = u / Ns, j = u - p * Ns;
+      const double2* src = in + (long long)p * L + j;
+      double2 a0 = src[0], a1 = src[Ns], a2 = src[2 * Ns];
+      if (Ns > 1) {
+        a1 = cm64(a1, tab[j]);
+        a2 = cm64(a2, tab[2 * j]);
+      }
+      // X0 = a0 + s, X1,2 = a0 - s / 2 -+ i sqrt(3)/2 (a1 - a2)
+      const double2 sm = add64(a1, a2), d = sub64(a1, a2);
+      const double2 m = make_double2(a0.x - 0.5 * sm.x, a0.y - 0.5 * sm.y);
+      double2* dst = out + (long long)p * L + j;
+      dst[0] = add64(a0, sm);
+      dst[Ns] = make_double2(m.x + h * d.y, m.y - h * d.x);
+      dst[2 * Ns] = make_double2(m.x - h * d.y, m.y + h * d.x);
+    }
+    swap();
+  }
+  return in;
+}
+
+constexpr size_t kFft64Smem = 96 * 1024;
+
+bool fft64_length(int L) {
+  const int p2 = (L % 3 == 0) ? L / 3 : L;
+  return L >= 1 && (p2 & (p2 - 1)) == 0 && 2 * (size_t)L * sizeof(double2) <= kFft64Smem;
+}
+
+// sequences per block for length L within the shared-memory budget
+int fft64_lines(int L, int cap) {
+  return std::max(1, std::min(cap, (int)(kFft64Smem / (2 * (size_t)L * sizeof(double2)))));
+}
+
+// out[row][kx] = FFT along x of the indicator of `incl` on C rows per block
+__global__ void k_g_rows_fft(const uint8_t* pm, int incl, int nx, long long rows, int C,
+                             const double2* tab, double2* out) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double2* b0 = reinterpret_cast<double2*>(sm);
+  double2* b1 = b0 + (size_t)C * nx;
+  const long long row0 = (long long)blockIdx.x * C;
+  for (int i = threadIdx.x; i < C * nx; i += blockDim.x) {
+    const long long g = row0 * nx + i;
+    b0[i] = make_double2((row0 + i / nx < rows && pm[g] == incl) ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  const double2* z = fft64_block(b0, b1, tab, nx, C);
+  for (int i = threadIdx.x; i < C * nx; i += blockDim.x)
+    if (row0 + i / nx < rows) out[row0 * nx + i] = z[i];
+}
+
+// out[b][m][n] = sum_k exp(-2 pi i m k / L) in[b][k][n] by FFT, C columns n per block
+__global__ void k_cols_fft64(const double2* in, double2* out, int L, int ncols, long long bstride,
+                             int C, const double2* tab) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double2* b0 = reinterpret_cast<double2*>(sm);
+  double2* b1 = b0 + (size_t)C * L;
+  const int col0 = blockIdx.x * C;
+  const double2* ib = in + blockIdx.y * bstride;
+  double2* ob = out + blockIdx.y * bstride;
+  for (int i = threadIdx.x; i < C * L; i += blockDim.x) {
+    const int y = i / C, c = i - y * C, col = col0 + c;
+    b0[c * L + y] = col < ncols ? ib[(long long)y * ncols + col] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  const double2* z = fft64_block(b0, b1, tab, L, C);
+  for (int i = threadIdx.x; i < C * L; i += blockDim.x) {
+    const int y = i / C, c = i - y * C, col = col0 + c;
+    if (col < ncols) ob[(long long)y * ncols + col] = z[c * L + y];
+  }
 }
 
 // keys at canonical pair members (array order [z][y][x]); others get ~0
@@ -379,6 +516,60 @@ int select_and_compact(const Grid3& g, unsigned long long* key, int* lin, int* s
 
 }  // namespace
 
+// DFT of the inclusion indicator along x, y and z (FP64) from the device phase map: FFTs for
+// sides 2^b and 3 * 2^b, dense DFTs (exact table sums along x) otherwise. Uses A and B
+// ([N] each) and the tables tx, ty, tz ([side] each); *G receives the buffer holding g^.
+int indicator_transform(const Grid3& g, const uint8_t* d_pm, int incl, double2* A, double2* B,
+                        double2* tx, double2* ty, double2* tz, double2** G, cudaStream_t s) {
+  k_table_f64<<<(g.nx + 255) / 256, 256, 0, s>>>(tx, g.nx);
+  k_table_f64<<<(g.ny + 255) / 256, 256, 0, s>>>(ty, g.ny);
+  k_table_f64<<<(g.nz + 255) / 256, 256, 0, s>>>(tz, g.nz);
+  const long long rows = g.N / g.nx;
+  if (fft64_length(g.nx)) {
+    const int C = fft64_lines(g.nx, 16);
+    if (int e = check(cudaFuncSetAttribute(k_g_rows_fft, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kFft64Smem), "pattern: smem attribute"))
+      return e;
+    k_g_rows_fft<<<(unsigned)((rows + C - 1) / C), 256, 2 * (size_t)C * g.nx * sizeof(double2), s>>>(
+        d_pm, incl, g.nx, rows, C, tx, A);
+  } else {
+    const size_t smem = (size_t)g.nx * (sizeof(double2) + sizeof(float));
+    if (int e = check(cudaFuncSetAttribute(k_g_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           100 * 1024), "pattern: smem attribute"))
+      return e;
+    k_g_rows<<<(unsigned)rows, 256, smem, s>>>(d_pm, incl, g.nx, tx, A);
+  }
+  if (int e = check(cudaGetLastError(), "g rows")) return e;
+  if (int e = check(cudaFuncSetAttribute(k_cols_fft64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kFft64Smem), "pattern: smem attribute"))
+    return e;
+  // along y: batch z, k = y, n = kx
+  if (fft64_length(g.ny)) {
+    const int C = fft64_lines(g.ny, 8);
+    dim3 grd((g.nx + C - 1) / C, g.nz);
+    k_cols_fft64<<<grd, 256, 2 * (size_t)C * g.ny * sizeof(double2), s>>>(
+        A, B, g.ny, g.nx, (long long)g.ny * g.nx, C, ty);
+  } else {
+    dim3 grd((g.nx + 127) / 128, (g.ny + 3) / 4, g.nz);
+    k_axis_f64<<<grd, 128, 0, s>>>(A, B, g.ny, g.nx, (long long)g.ny * g.nx, ty);
+  }
+  *G = B;
+  if (g.nz > 1) {
+    const int Nn = g.ny * g.nx;
+    if (fft64_length(g.nz)) {
+      const int C = fft64_lines(g.nz, 8);
+      dim3 grd((Nn + C - 1) / C, 1);
+      k_cols_fft64<<<grd, 256, 2 * (size_t)C * g.nz * sizeof(double2), s>>>(B, A, g.nz, Nn, 0, C,
+                                                                             tz);
+    } else {
+      dim3 grd((Nn + 127) / 128, (g.nz + 3) / 4, 1);
+      k_axis_f64<<<grd, 128, 0, s>>>(B, A, g.nz, Nn, 0, tz);
+    }
+    *G = A;
+  }
+  return check(cudaGetLastError(), "g axes");
+}
+
 int pattern_adapted(const rf_grid* grid, const uint8_t* pm_host, int incl, long long k_target,
                     int32_t* out, long long cap, long long* K_out, cudaStream_t s) {
   Grid3 g;
@@ -403,26 +594,8 @@ int pattern_adapted(const rf_grid* grid, const uint8_t* pm_host, int incl, long 
   }
   if (int e = check(cudaMemcpyAsync(d_pm, pm_host, g.N, cudaMemcpyHostToDevice, s), "upload"))
     return e;
-  k_table_f64<<<(g.nx + 255) / 256, 256, 0, s>>>(tx, g.nx);
-  k_table_f64<<<(g.ny + 255) / 256, 256, 0, s>>>(ty, g.ny);
-  k_table_f64<<<(g.nz + 255) / 256, 256, 0, s>>>(tz, g.nz);
-  const size_t smem = (size_t)g.nx * (sizeof(double2) + sizeof(float));
-  cudaFuncSetAttribute(k_g_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-  k_g_rows<<<(unsigned)(g.N / g.nx), 256, smem, s>>>(d_pm, incl, g.nx, tx, A);
-  if (int e = check(cudaGetLastError(), "g rows")) return e;
-  // along y: batch z, k = y, n = kx
-  {
-    dim3 grd((g.nx + 127) / 128, (g.ny + 3) / 4, g.nz);
-    k_axis_f64<<<grd, 128, 0, s>>>(A, B, g.ny, g.nx, (long long)g.ny * g.nx, ty);
-  }
-  double2* G = B;
-  if (g.nz > 1) {
-    const int Nn = g.ny * g.nx;
-    dim3 grd((Nn + 127) / 128, (g.nz + 3) / 4, 1);
-    k_axis_f64<<<grd, 128, 0, s>>>(B, A, g.nz, Nn, 0, tz);
-    G = A;
-  }
-  if (int e = check(cudaGetLastError(), "g axes")) return e;
+  double2* G = nullptr;
+  if (int e = indicator_transform(g, d_pm, incl, A, B, tx, ty, tz, &G, s)) return e;
   k_keys<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(G, nullptr, g, key, lin, size);
   if (int e = check(cudaGetLastError(), "keys")) return e;
   return select_and_compact(g, key, lin, size, k_target, out, cap, K_out, s, sc);
@@ -566,25 +739,8 @@ int pattern_adapted_noalloc(const rf_grid* grid, const uint8_t* pm_host, int inc
   // same kernels as rf_pattern_adapted
   if (int e = check(cudaMemcpyAsync(d_pm, pm_host, g.N, cudaMemcpyHostToDevice, s), "upload"))
     return e;
-  k_table_f64<<<(g.nx + 255) / 256, 256, 0, s>>>(tx, g.nx);
-  k_table_f64<<<(g.ny + 255) / 256, 256, 0, s>>>(ty, g.ny);
-  k_table_f64<<<(g.nz + 255) / 256, 256, 0, s>>>(tz, g.nz);
-  const size_t smem = (size_t)g.nx * (sizeof(double2) + sizeof(float));
-  if (int e = check(cudaFuncSetAttribute(k_g_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         100 * 1024), "noalloc: smem attribute"))
-    return e;
-  k_g_rows<<<(unsigned)(g.N / g.nx), 256, smem, s>>>(d_pm, incl, g.nx, tx, A);
-  {
-    dim3 grd((g.nx + 127) / 128, (g.ny + 3) / 4, g.nz);
-    k_axis_f64<<<grd, 128, 0, s>>>(A, B, g.ny, g.nx, (long long)g.ny * g.nx, ty);
-  }
-  double2* G = B;
-  if (g.nz > 1) {
-    const int Nn = g.ny * g.nx;
-    dim3 grd((Nn + 127) / 128, (g.nz + 3) / 4, 1);
-    k_axis_f64<<<grd, 128, 0, s>>>(B, A, g.nz, Nn, 0, tz);
-    G = A;
-  }
+  double2* G = nullptr;
+  if (int e = indicator_transform(g, d_pm, incl, A, B, tx, ty, tz, &G, s)) return e;
   k_keys<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(G, nullptr, g, key, lin, size);
   if (int e = check(cudaGetLastError(), "noalloc: keys")) return e;
 
