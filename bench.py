@@ -550,7 +550,8 @@ def main():
     info = solver.rf_get_info()
     tile_info = {k: info[k] for k in ("fft_rows", "fft_row_threads", "fft_cols",
                                       "fft_col_threads", "fft_fused", "fft_fuse_kx",
-                                      "fft_fuse_threads")} if args.transform == "fft" else None
+                                      "fft_fuse_threads", "fft_row_blocks")} \
+        if args.transform == "fft" else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step():

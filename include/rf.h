@@ -111,7 +111,11 @@ typedef struct rf_phase {
  *             three kernels; 0 = chosen by timing both when the pattern is set. Must be 0 or -1
  *             in 3D. The two give the same update up to the order of FP64 summation in the
  *             convergence measure.
- *  fft_fuse_kx  kx columns per block of the fused kernel (0 = chosen by timing; 1..16). */
+ *  fft_fuse_kx  kx columns per block of the fused kernel (0 = chosen by timing; 1..16).
+ *  fft_row_blocks  FFT mode: run the row kernel on this many blocks with the grid rows spread
+ *             evenly (blocks differ by at most one row; clamped to the row count), instead of
+ *             tiles of fft_rows; 0 = fft_rows or the autotuner (which also times such
+ *             partitions over whole multiples of the SM count). */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
@@ -124,6 +128,7 @@ typedef struct rf_options {
   int32_t fft_cols;
   int32_t fft_fuse;
   int32_t fft_fuse_kx;
+  int32_t fft_row_blocks;
 } rf_options;
 
 /* Run statistics of the last solve on a context. */
@@ -143,6 +148,8 @@ typedef struct rf_info {
   int32_t fft_fused;      /* 1 when the fused column phase is in use (see fft_fuse), else 0 */
   int32_t fft_fuse_kx;    /* kx columns per fused block, else 0 */
   int32_t fft_fuse_threads;/* threads per fused block, else 0 */
+  int32_t fft_row_blocks; /* FFT mode: row-kernel blocks (fft_rows is the largest block's row
+                           * count; blocks may hold one row fewer to balance the SMs), else 0 */
 } rf_info;
 
 /* Create a solver context for one microstructure.

@@ -421,6 +421,7 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
     return invalid("options: unknown transform");
   if (opt->fft_rows < 0 || opt->fft_rows > 64 || opt->fft_cols < 0 || opt->fft_cols > 64)
     return invalid("options: fft_rows and fft_cols in [0, 64]");
+  if (opt->fft_row_blocks < 0) return invalid("options: fft_row_blocks >= 0");
   if (opt->fft_fuse < -1 || opt->fft_fuse > 1 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
     return invalid("options: fft_fuse in {-1, 0, 1}, fft_fuse_kx in [0, 16]");
   if (opt->fft_fuse == 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))
@@ -932,6 +933,7 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   info->fft_fused = c->fft_fused ? 1 : 0;
   info->fft_fuse_kx = c->fft_fused ? c->fft_M : 0;
   info->fft_fuse_threads = c->fft_fused ? c->fft_M_threads : 0;
+  info->fft_row_blocks = fft ? c->fft_blocks : 0;
   return RF_OK;
 }
 

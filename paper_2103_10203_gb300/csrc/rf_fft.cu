@@ -31,7 +31,9 @@ struct FftRowArgs {
   float* state;
   const int* kx;
   const float2* table;  // twiddle buffer of length Nx (rf_fftcore.cuh)
-  int Nx, Kx, rows, R;
+  int Nx, Kx, rows;
+  int rbase, rextra;    // block b holds rows [b rbase + min(b, rextra), ...): rbase rows, one
+                        // more for b < rextra
   FastDiv dL, dKx;      // division by Nx and Kx
   long long N;
   float invN;
@@ -49,7 +51,9 @@ template <int NC, bool PLASTIC, bool FINAL>
 __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.Nx;
-  const int S = a.R * NC;              // real lines in this block
+  const int row0 = blockIdx.x * a.rbase + min((int)blockIdx.x, a.rextra);
+  const int R = a.rbase + ((int)blockIdx.x < a.rextra ? 1 : 0);   // rows of this block
+  const int S = R * NC;                // real lines in this block
   const int P = (S + 1) / 2;           // packed complex sequences
   float2* tw = reinterpret_cast<float2*>(smem);    // stage twiddles
   float2* b0 = tw + fftc::stage_len(L);
@@ -59,7 +63,6 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   __shared__ double red[8];
   __shared__ DevPhase phs[kMaxPhases];
   const int tid = threadIdx.x;
-  const int row0 = blockIdx.x * a.R;
   copy_twiddles(a.table, L, tw);
   for (int i = tid; i < a.Kx; i += blockDim.x) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
@@ -137,7 +140,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   const float lam0 = a.law.lam0, mu0 = a.law.mu0;
   constexpr int kVox = 4;
   constexpr int NS = NC == 3 ? 4 : 7;
-  for (int vb = 0; vb < a.R * L; vb += kVox * blockDim.x) {
+  for (int vb = 0; vb < R * L; vb += kVox * blockDim.x) {
     int pid[kVox];
     float stv[kVox][NS];
 #pragma unroll
@@ -145,7 +148,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
       const int v = vb + tid + u * blockDim.x;
       const int r = fdiv(v, a.dL), x = v - r * L, row = row0 + r;
       pid[u] = 0;
-      if (v < a.R * L && row < a.rows) {
+      if (v < R * L && row < a.rows) {
         const long long g = (long long)row * L + x;
         pid[u] = a.phase[g];
         if (PLASTIC) {
@@ -157,7 +160,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
 #pragma unroll
     for (int u = 0; u < kVox; ++u) {
       const int v = vb + tid + u * blockDim.x;
-      if (v >= a.R * L) continue;
+      if (v >= R * L) continue;
       const int r = fdiv(v, a.dL), x = v - r * L, row = row0 + r;
       float e[NC];
 #pragma unroll
@@ -537,13 +540,28 @@ static int fft_cols(rf_ctx* c, const float2* in, long long in_bs, int in_rows, c
 static void set_rows(rf_ctx* c, int R) {
   R = std::max(1, std::min(R, c->rows));
   c->fft_R = R;
+  c->fft_rbase = R;
+  c->fft_rextra = 0;
   c->fft_blocks = (c->rows + R - 1) / R;
   c->fft_smem = row_smem(c->nx, c->nc, c->Kx, R);
 }
 
+// nb blocks holding floor(rows / nb) or one more rows each, the larger blocks first: when the
+// first wave places one block per SM and nb is a multiple of the SM count, every SM ends up
+// with a balanced share of rows
+static void set_rows_balanced(rf_ctx* c, int nb) {
+  nb = std::max(1, std::min(nb, c->rows));
+  c->fft_rbase = c->rows / nb;
+  c->fft_rextra = c->rows % nb;
+  c->fft_R = c->fft_rbase + (c->fft_rextra > 0 ? 1 : 0);
+  c->fft_blocks = nb;
+  c->fft_smem = row_smem(c->nx, c->nc, c->Kx, c->fft_R);
+}
+
 int fft_geometry(rf_ctx* c) {
   const int L = c->nx;
-  set_rows(c, c->opt.fft_rows > 0 ? c->opt.fft_rows : (2 * 6144) / (c->nc * L));
+  if (c->opt.fft_row_blocks > 0) set_rows_balanced(c, c->opt.fft_row_blocks);
+  else set_rows(c, c->opt.fft_rows > 0 ? c->opt.fft_rows : (2 * 6144) / (c->nc * L));
   if (c->fft_smem > kFftSmemMax) {
     set_error("FFT mode: rows too long for the row kernel's shared memory");
     return RF_ERR_INVALID;
@@ -587,7 +605,8 @@ static FftRowArgs fft_row_args(rf_ctx* c, const int* done) {
   a.dL = make_fastdiv((unsigned)c->nx);
   a.dKx = make_fastdiv((unsigned)std::max(1, c->Kx));
   a.rows = c->rows;
-  a.R = c->fft_R;
+  a.rbase = c->fft_rbase;
+  a.rextra = c->fft_rextra;
   a.N = c->N;
   a.invN = (float)(1.0 / (double)c->N);
   a.law = c->law;
@@ -722,12 +741,14 @@ int fft_autotune(rf_ctx* c) {
   const bool fuse_auto = c->dim == 2 && c->opt.fft_fuse == 0 && c->d_jptr &&
                          colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
   const bool fuse_shape = c->fft_fused && c->opt.fft_fuse_kx == 0;
-  if (c->opt.fft_rows > 0 && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape) return RF_OK;
+  const bool rows_pinned = c->opt.fft_rows > 0 || c->opt.fft_row_blocks > 0;
+  if (rows_pinned && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape) return RF_OK;
   rf_ctx::Tuned& tu = c->tuned;
   if (tu.valid && tu.Kx == c->Kx && tu.Ky == c->Ky && tu.Kz == c->Kz) {
     // same transform shapes as the last tuning on this context: same choice
-    if (c->opt.fft_rows <= 0) {
-      set_rows(c, tu.R);
+    if (!rows_pinned) {
+      if (tu.row_blocks_balanced) set_rows_balanced(c, tu.row_blocks_balanced);
+      else set_rows(c, tu.R);
       c->fft_row_threads = tu.row_threads;
     }
     if (c->opt.fft_cols <= 0) {
@@ -771,26 +792,43 @@ int fft_autotune(rf_ctx* c) {
     }
     return RF_OK;
   };
-  if (!err && c->opt.fft_rows <= 0) {
+  if (!err && !rows_pinned) {
+    // uniform tiles of R rows, and balanced partitions over k blocks per SM
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+    struct Cand {
+      int R, nb;   // nb > 0: balanced over nb blocks
+    };
+    std::vector<Cand> cands;
+    for (int R : {1, 2, 4, 8, 16})
+      if (R <= c->rows && row_smem(c->nx, c->nc, c->Kx, R) <= kFftSmemMax) cands.push_back({R, 0});
+    for (int k = 1; sms > 0 && k <= 8; ++k) {
+      const int nb = k * sms;
+      if (nb >= c->rows || c->rows % nb == 0) continue;   // uniform tiles cover these
+      const int Rmax = c->rows / nb + 1;
+      if (row_smem(c->nx, c->nc, c->Kx, Rmax) <= kFftSmemMax) cands.push_back({Rmax, nb});
+    }
     float best = 1e30f;
-    int bestR = c->fft_R, bestT = c->fft_row_threads;
-    for (int R : {1, 2, 4, 8, 16}) {
-      if (R > c->rows || row_smem(c->nx, c->nc, c->Kx, R) > kFftSmemMax) continue;
+    Cand bestC{c->fft_R, 0};
+    int bestT = c->fft_row_threads;
+    for (const Cand& cd : cands) {
       for (int T : {128, 256}) {
-        set_rows(c, R);
+        if (cd.nb) set_rows_balanced(c, cd.nb);
+        else set_rows(c, cd.R);
         c->fft_row_threads = T;
         float ms = 0.f;
         err = time_it([&] { return launch_fft_row(c, nullptr, false, 0); }, &ms);
         if (err) break;
         if (ms < best) {
           best = ms;
-          bestR = R;
+          bestC = cd;
           bestT = T;
         }
       }
       if (err) break;
     }
-    set_rows(c, bestR);
+    if (bestC.nb) set_rows_balanced(c, bestC.nb);
+    else set_rows(c, bestC.R);
     c->fft_row_threads = bestT;
   }
   if (!err && c->opt.fft_cols <= 0) {
@@ -860,6 +898,7 @@ int fft_autotune(rf_ctx* c) {
     tu.Ky = c->Ky;
     tu.Kz = c->Kz;
     tu.R = c->fft_R;
+    tu.row_blocks_balanced = c->fft_rextra > 0 ? c->fft_blocks : 0;
     tu.row_threads = c->fft_row_threads;
     tu.C = c->fft_C;
     tu.col_threads = c->fft_col_threads;

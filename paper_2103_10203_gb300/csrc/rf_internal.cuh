@@ -182,6 +182,7 @@ struct rf_ctx {
 
   // FFT transform mode
   int fft_R = 0, fft_blocks = 0, fft_C = 0;
+  int fft_rbase = 0, fft_rextra = 0;    // row partition (see set_rows_balanced)
   int fft_row_threads = 256, fft_col_threads = 256;   // block sizes (autotuned with the tiles)
   size_t fft_smem = 0;
   // fused column phase (2D): forward y + Green operator + decision + inverse y per kx group
@@ -194,6 +195,7 @@ struct rf_ctx {
     bool valid = false;
     int Kx = 0, Ky = 0, Kz = 0;
     int R = 0, row_threads = 0, C = 0, col_threads = 0, M = 0, M_threads = 0;
+    int row_blocks_balanced = 0;
     bool fused = false;
   } tuned;
 

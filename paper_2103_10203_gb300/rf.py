@@ -36,7 +36,8 @@ class rf_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("green", C.c_int32),
                 ("ref_medium", C.c_int32), ("precision", C.c_int32), ("check_every", C.c_int32),
                 ("transform", C.c_int32), ("fft_rows", C.c_int32), ("fft_cols", C.c_int32),
-                ("fft_fuse", C.c_int32), ("fft_fuse_kx", C.c_int32)]
+                ("fft_fuse", C.c_int32), ("fft_fuse_kx", C.c_int32),
+                ("fft_row_blocks", C.c_int32)]
 
 
 class rf_info(C.Structure):
@@ -46,7 +47,8 @@ class rf_info(C.Structure):
                 ("lambda0", C.c_double), ("mu0", C.c_double), ("fft_rows", C.c_int32),
                 ("fft_row_threads", C.c_int32), ("fft_cols", C.c_int32),
                 ("fft_col_threads", C.c_int32), ("fft_fused", C.c_int32),
-                ("fft_fuse_kx", C.c_int32), ("fft_fuse_threads", C.c_int32)]
+                ("fft_fuse_kx", C.c_int32), ("fft_fuse_threads", C.c_int32),
+                ("fft_row_blocks", C.c_int32)]
 
 
 class rf_mlp_dims(C.Structure):
@@ -195,7 +197,7 @@ def make_phases(table) -> C.Array:
 
 def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
                  check_every=0, transform="dft", fft_rows=0, fft_cols=0, fft_fuse=0,
-                 fft_fuse_kx=0) -> rf_options:
+                 fft_fuse_kx=0, fft_row_blocks=0) -> rf_options:
     o = rf_options()
     o.tol, o.max_iter = float(tol), int(max_iter)
     o.green, o.ref_medium = GREEN[green], REF[ref]
@@ -203,6 +205,7 @@ def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precisi
     o.transform = TRANSFORM[transform]
     o.fft_rows, o.fft_cols = int(fft_rows), int(fft_cols)
     o.fft_fuse, o.fft_fuse_kx = int(fft_fuse), int(fft_fuse_kx)
+    o.fft_row_blocks = int(fft_row_blocks)
     return o
 
 

@@ -493,6 +493,27 @@ def test_fft_fuse_option_checks(lib):
         lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="fft", fft_fuse=2)
 
 
+@pytest.mark.parametrize("name,blocks", [("j2_64", 5), ("j2_64", 64), ("j2_64", 1000),
+                                         ("3d_rect", 9), ("three", 7)])
+def test_fft_balanced_row_blocks(lib, name, blocks):
+    """Row kernel on `blocks` blocks with the rows spread evenly (blocks of unequal row counts,
+    packed sequences with an unused carrier in some blocks): the oracle's update."""
+    pm, ph, macro, pat = _pow2_case(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=5, transform="fft",
+                   fft_row_blocks=blocks, fft_cols=2)
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    info = s.rf_get_info()
+    s.close()
+    rows = pm.size // pm.shape[-1]
+    assert info["fft_row_blocks"] == min(blocks, rows)
+    assert info["fft_rows"] == -(-rows // min(blocks, rows))
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=5)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
 def test_fft_transform_load_path_and_tolerance(lib):
     pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
     ph = j2_phases()
