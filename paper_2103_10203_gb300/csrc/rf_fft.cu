@@ -48,7 +48,7 @@ struct FftRowArgs {
 };
 
 template <int NC, bool PLASTIC, bool FINAL>
-__global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
+__global__ __launch_bounds__(512) void k_fft_row(FftRowArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = a.Nx;
   const int row0 = blockIdx.x * a.rbase + min((int)blockIdx.x, a.rextra);
@@ -60,7 +60,7 @@ __global__ __launch_bounds__(256) void k_fft_row(FftRowArgs a) {
   const int span = fftc::span_of(P * L);
   float2* b1 = b0 + span;
   int* kxs = reinterpret_cast<int*>(b1 + span);   // past b1's rounded span
-  __shared__ double red[8];
+  __shared__ double red[32];   // one entry per warp
   __shared__ DevPhase phs[kMaxPhases];
   const int tid = threadIdx.x;
   copy_twiddles(a.table, L, tw);
@@ -812,7 +812,7 @@ int fft_autotune(rf_ctx* c) {
     Cand bestC{c->fft_R, 0};
     int bestT = c->fft_row_threads;
     for (const Cand& cd : cands) {
-      for (int T : {128, 256}) {
+      for (int T : {128, 256, 512}) {
         if (cd.nb) set_rows_balanced(c, cd.nb);
         else set_rows(c, cd.R);
         c->fft_row_threads = T;
