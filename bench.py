@@ -58,8 +58,9 @@ def parse():
                    help="c2 FFT mode: rows per row-kernel block (0: autotuned)")
     p.add_argument("--fft-cols", type=int, default=0,
                    help="c2 FFT mode: columns per column-kernel block (0: autotuned)")
-    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1],
-                   help="c2 FFT mode: fused column phase on (1), off (-1), or timed (0)")
+    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2],
+                   help="c2 FFT mode column phase: three kernels (-1), one fused kernel (1), "
+                        "Green operator inside the inverse y kernel (2), or timed (0)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],

@@ -105,12 +105,13 @@ typedef struct rf_phase {
  *  fft_rows, fft_cols  FFT mode tiles: grid rows per row-kernel block and line columns per
  *             column-kernel block (0 = chosen by timing a few launches of each candidate when
  *             the pattern is set). Results do not depend on them.
- *  fft_fuse   2D FFT mode: 1 runs the forward transform along y, the Green-operator update with
- *             the convergence decision and the inverse transform along y of every group of kx
- *             columns in one kernel (steps b to d of Sec. 4 between two row passes); -1 keeps
- *             three kernels; 0 = chosen by timing both when the pattern is set. Must be 0 or -1
- *             in 3D. The two give the same update up to the order of FP64 summation in the
- *             convergence measure.
+ *  fft_fuse   2D FFT mode, how the column phase between two row passes runs: -1 three kernels
+ *             (forward y, Green-operator update with the convergence decision, inverse y);
+ *             1 one kernel per group of kx columns (steps b to d of Sec. 4 fused); 2 forward y,
+ *             then the Green-operator update and decision inside the inverse y kernel; 0 =
+ *             chosen by timing the three when the pattern is set. Must be 0 or -1 in 3D. All
+ *             give the same update up to the order of FP64 summation in the convergence
+ *             measure.
  *  fft_fuse_kx  kx columns per block of the fused kernel (0 = chosen by timing; 1..16).
  *  fft_row_blocks  FFT mode: run the row kernel on this many blocks with the grid rows spread
  *             evenly (blocks differ by at most one row; clamped to the row count), instead of
@@ -145,7 +146,7 @@ typedef struct rf_info {
   int32_t fft_row_threads;/* FFT mode: threads per row-kernel block, else 0 */
   int32_t fft_cols;       /* FFT mode: columns per column-kernel block, else 0 */
   int32_t fft_col_threads;/* FFT mode: threads per column-kernel block, else 0 */
-  int32_t fft_fused;      /* 1 when the fused column phase is in use (see fft_fuse), else 0 */
+  int32_t fft_fused;      /* column-phase mode in use (see fft_fuse): 0, 1 or 2 */
   int32_t fft_fuse_kx;    /* kx columns per fused block, else 0 */
   int32_t fft_fuse_threads;/* threads per fused block, else 0 */
   int32_t fft_row_blocks; /* FFT mode: row-kernel blocks (fft_rows is the largest block's row
@@ -211,8 +212,9 @@ int rf_get_info(const rf_ctx* ctx, rf_info* info);
  * that did work (not the ones skipped after convergence) are accumulated per stage.
  * Stages: 0 inverse transform along z, 1 inverse along y, 2 row kernel (transforms along x,
  * constitutive law, polarization), 3 forward along y, 4 forward along z, 5 Green-operator
- * update with the convergence decision, 6 fused column phase (2D FFT mode with fft_fuse:
- * stages 3, 5 and 1 in one kernel), 7 final pass (fields, homogenised stress, commit).
+ * update with the convergence decision (with fft_fuse 2 it includes the inverse along y),
+ * 6 fused column phase (fft_fuse 1: stages 3, 5 and 1 in one kernel), 7 final pass (fields,
+ * homogenised stress, commit).
  * rf_get_stage_times fills ms_total[8] (milliseconds) and counts[8] (launches timed). */
 int rf_set_tracing(rf_ctx* ctx, int on);
 int rf_get_stage_times(const rf_ctx* ctx, double ms_total[8], int64_t counts[8]);

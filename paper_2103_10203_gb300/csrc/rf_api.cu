@@ -271,7 +271,9 @@ void free_pattern(rf_ctx* c) {
   dfree(c->d_tc_err);
   dfree(c->d_jptr);
   dfree(c->d_jlist);
-  c->fft_fused = false;
+  dfree(c->d_jent);
+  dfree(c->d_jn);
+  c->fft_colmode = kColSeparate;
   c->have_pattern = false;
   c->fields_valid = false;
 }
@@ -310,8 +312,8 @@ int init_status(rf_ctx* c, const double* macro) {
 int run_iterations(rf_ctx* c) {
   const int maxchunk = c->opt.check_every > 0 ? c->opt.check_every : 32;
   int chunk = std::min(4, maxchunk);
-  if (c->fft_fused) {
-    // a fused update ends with the inverse transform along y of its new coefficients, so the
+  if (c->fft_colmode != kColSeparate) {
+    // these updates end with the inverse transform along y of their new coefficients, so the
     // first one needs the line transforms of the start coefficients
     const bool tr = c->tracing;
     c->tracing = false;
@@ -422,10 +424,10 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (opt->fft_rows < 0 || opt->fft_rows > 64 || opt->fft_cols < 0 || opt->fft_cols > 64)
     return invalid("options: fft_rows and fft_cols in [0, 64]");
   if (opt->fft_row_blocks < 0) return invalid("options: fft_row_blocks >= 0");
-  if (opt->fft_fuse < -1 || opt->fft_fuse > 1 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
-    return invalid("options: fft_fuse in {-1, 0, 1}, fft_fuse_kx in [0, 16]");
-  if (opt->fft_fuse == 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))
-    return invalid("options: fft_fuse = 1 needs the FFT transform on a 2D grid");
+  if (opt->fft_fuse < -1 || opt->fft_fuse > 2 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
+    return invalid("options: fft_fuse in {-1, 0, 1, 2}, fft_fuse_kx in [0, 16]");
+  if (opt->fft_fuse >= 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))
+    return invalid("options: fft_fuse 1 or 2 needs the FFT transform on a 2D grid");
   if (opt->transform == RF_TRANSFORM_FFT) {
     // 2^b or 3 * 2^b (the FFT stages are radix 16, 4, 2 and one radix-3)
     auto pow2 = [](int v) {
@@ -662,10 +664,12 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err && c->dim == 3) err = dalloc(&c->d_T2, (size_t)c->nz * c->Ky * NCK, "line transforms");
   if (!err && c->dim == 3) err = dalloc(&c->d_T2f, (size_t)c->nz * c->Ky * NCK, "line transforms");
   if (!err) err = dalloc(&c->d_OUT, (size_t)splits * c->rect, "partials");
-  // block partials of the convergence measure: Green kernel blocks, or fused blocks (<= Kx)
+  // block partials of the convergence measure: Green kernel blocks, or column blocks of the
+  // fused modes (<= NC Kx)
   if (!err)
     err = dalloc(&c->d_part,
-                 (size_t)std::max<long long>((c->Kh + kGammaBlock - 1) / kGammaBlock, c->Kx),
+                 (size_t)std::max<long long>((c->Kh + kGammaBlock - 1) / kGammaBlock,
+                                             (long long)c->nc * c->Kx),
                  "partials");
   const bool fuse_ok = c->opt.transform == RF_TRANSFORM_FFT && c->dim == 2 && c->opt.fft_fuse >= 0;
   if (!err && fuse_ok) {
@@ -677,6 +681,8 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
     for (long long h = 0; h < c->Kh; ++h) jlist[fill[c->h_hidx[h].j]++] = (int)h;
     err = dalloc(&c->d_jptr, jptr.size(), "pattern");
     if (!err) err = dalloc(&c->d_jlist, jlist.size(), "pattern");
+    if (!err) err = dalloc(&c->d_jent, jlist.size(), "pattern");
+    if (!err) err = dalloc(&c->d_jn, jlist.size(), "pattern");
     if (!err)
       err = ck(cudaMemcpy(c->d_jptr, jptr.data(), sizeof(int) * jptr.size(), cudaMemcpyHostToDevice),
                "up");
@@ -699,6 +705,7 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err) err = ck(cudaMemcpyAsync(c->d_hidx, c->h_hidx.data(), sizeof(HIdx) * c->Kh, cudaMemcpyHostToDevice, c->stream), "up");
   if (!err) err = ck(cudaMemcpyAsync(d_hk, hk.data(), sizeof(int) * hk.size(), cudaMemcpyHostToDevice, c->stream), "up");
   if (!err) err = launch_hinfo(c, d_hk, c->Kh);
+  if (!err && c->d_jent) err = launch_gather_jentries(c);
   if (!err && c->opt.precision != RF_PREC_FP32) err = tc_setup(c);
   if (!err) err = ck(cudaMemsetAsync(c->d_OUT, 0, sizeof(float2) * splits * c->rect, c->stream), "memset");
   if (!err && c->opt.transform == RF_TRANSFORM_FFT) err = fft_autotune(c);
@@ -930,9 +937,9 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   info->fft_row_threads = fft ? c->fft_row_threads : 0;
   info->fft_cols = fft ? c->fft_C : 0;
   info->fft_col_threads = fft ? c->fft_col_threads : 0;
-  info->fft_fused = c->fft_fused ? 1 : 0;
-  info->fft_fuse_kx = c->fft_fused ? c->fft_M : 0;
-  info->fft_fuse_threads = c->fft_fused ? c->fft_M_threads : 0;
+  info->fft_fused = c->fft_colmode;
+  info->fft_fuse_kx = c->fft_colmode == kColFused ? c->fft_M : 0;
+  info->fft_fuse_threads = c->fft_colmode == kColFused ? c->fft_M_threads : 0;
   info->fft_row_blocks = fft ? c->fft_blocks : 0;
   return RF_OK;
 }

@@ -484,6 +484,210 @@ __global__ __launch_bounds__(256) void k_fft_colphase(ColPhaseArgs a, double Nd)
   }
 }
 
+// Green operator inside the inverse transform along y (2D): a block takes C line columns
+// (column col = c Kx + kx) and, for every pattern entry of each column's kx, reads tau^ of all
+// NC components from the forward transform's rectangle, applies eps^ = -Gamma0 : tau^ (Sec. 3,
+// Sec. 4 step c; N ebar at the zero frequency, 0 at null frequencies) and keeps its own
+// component c: stored to ER, summed into the convergence measure (FP64 block partials; the
+// last block takes the decision) and scattered into the zeroed column for the inverse FFT
+// (Sec. 4 step d). Each frequency's operator is evaluated once per component; nothing else is
+// shared between blocks.
+struct GreenInvArgs {
+  const float2* OUT;      // [Ky][NC][Kx] tau^ on the (ky, kx) rectangle
+  float2* ER;             // [Ky][NC][Kx]
+  float2* T1;             // [ny][NC][Kx]
+  const int* jptr;        // [Kx + 1]
+  const int2* jent;       // kx-grouped entries: rectangle row iy, frequency kind
+  const float4* jn;       // kx-grouped entries: unit wave vector, multiplicity
+  const int* kym;
+  const float2* table;    // twiddle buffer of length Ny
+  int Kx, L, C, ncols;
+  FastDiv dC, dKx;
+  float inv2mu0, cgam;
+  Status* st;
+  unsigned* counter;
+  double* part;
+  const int* done;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
+};
+
+template <int NC>
+__global__ __launch_bounds__(256) void k_fft_green_inv(GreenInvArgs a, double Nd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  __shared__ double sh[32];
+  __shared__ bool last;
+  __shared__ int cbeg[65], ckx[64], cc_[64];   // flattened entry ranges of the block's columns
+  const int L = a.L, C = a.C;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* b0 = tw + fftc::stage_len(L);
+  const int span = fftc::span_of(C * L);
+  float2* b1 = b0 + span;
+  const int col0 = blockIdx.x * C;
+  const int ncc = min(C, a.ncols - col0);
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int cc = 0; cc < ncc; ++cc) {
+      const int col = col0 + cc, c = fdiv(col, a.dKx), kx = col - c * a.Kx;
+      cbeg[cc] = t;
+      ckx[cc] = kx;
+      cc_[cc] = c;
+      t += a.jptr[kx + 1] - a.jptr[kx];
+    }
+    cbeg[ncc] = t;
+  }
+  copy_twiddles(a.table, L, tw);
+  for (int i = threadIdx.x; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // the entries' data does not depend on the previous kernel: load it before waiting
+  constexpr int kE = 4;
+  const int tot = cbeg[ncc];
+  int ecc[kE], epos[kE], eiy[kE], ekind[kE];
+  float4 en[kE];
+#pragma unroll
+  for (int u = 0; u < kE; ++u) {
+    const int t = threadIdx.x + u * blockDim.x;
+    ecc[u] = -1;
+    if (t < tot) {
+      int cc = 0;
+      while (t >= cbeg[cc + 1]) ++cc;
+      const int e = a.jptr[ckx[cc]] + (t - cbeg[cc]);
+      const int2 en2 = a.jent[e];
+      ecc[u] = cc;
+      eiy[u] = en2.x;
+      ekind[u] = en2.y;
+      en[u] = a.jn[e];
+      epos[u] = a.kym[en2.x];
+    }
+  }
+  grid_dep_wait();
+  if (a.done && __ldcg(a.done)) return;   // the same flag value for every thread of the grid
+  double diff = 0.0;
+  // tau^ (all components) and the old coefficient of every entry, loads issued together
+  float2 tv[kE][NC], old[kE];
+#pragma unroll
+  for (int u = 0; u < kE; ++u) {
+    if (ecc[u] < 0) continue;
+    const long long base = ((long long)eiy[u] * NC) * a.Kx + ckx[ecc[u]];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) tv[u][q] = a.OUT[base + (long long)q * a.Kx];
+    old[u] = a.ER[base + (long long)cc_[ecc[u]] * a.Kx];
+  }
+#pragma unroll
+  for (int u = 0; u < kE; ++u) {
+    if (ecc[u] < 0) continue;
+    const int c = cc_[ecc[u]];
+    float er, ei;
+    if (ekind[u] == 1) {
+      er = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
+      ei = 0.f;
+    } else if (ekind[u] == 2) {
+      er = ei = 0.f;
+    } else {
+      float tr[NC], ti[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        tr[q] = tv[u][q].x;
+        ti[q] = tv[u][q].y;
+      }
+      float t6[6], o6[6], o6i[6];
+      comp_to6<NC>(tr, t6);
+      gamma6(en[u], t6, a.inv2mu0, a.cgam, o6);
+      comp_to6<NC>(ti, t6);
+      gamma6(en[u], t6, a.inv2mu0, a.cgam, o6i);
+      er = 0.f;
+      ei = 0.f;
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        if (q == c) {
+          er = -o6[comp6<NC>(q)];
+          ei = -o6i[comp6<NC>(q)];
+        }
+    }
+    const float dr = er - old[u].x, di = ei - old[u].y;
+    const int c6 = NC == 3 ? (c == 2 ? 5 : c) : c;
+    const float wc = c6 >= 3 ? 2.f : 1.f;   // Frobenius: shear counted twice
+    diff += (double)(en[u].w * wc * (dr * dr + di * di));
+    const float2 nv = make_float2(er, ei);
+    a.ER[((long long)eiy[u] * NC + c) * a.Kx + ckx[ecc[u]]] = nv;
+    b0[sw(ecc[u] * L + epos[u])] = nv;
+  }
+  // entries beyond kE per thread (columns denser than kE x blockDim entries together)
+  for (int t = threadIdx.x + kE * blockDim.x; t < tot; t += blockDim.x) {
+    int cc = 0;
+    while (t >= cbeg[cc + 1]) ++cc;
+    const int e = a.jptr[ckx[cc]] + (t - cbeg[cc]);
+    const int2 en2 = a.jent[e];
+    const float4 n = a.jn[e];
+    const int c = cc_[cc], kx = ckx[cc];
+    const long long base = ((long long)en2.x * NC) * a.Kx + kx;
+    float er, ei;
+    if (en2.y == 1) {
+      er = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
+      ei = 0.f;
+    } else if (en2.y == 2) {
+      er = ei = 0.f;
+    } else {
+      float tr[NC], ti[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const float2 tq = a.OUT[base + (long long)q * a.Kx];
+        tr[q] = tq.x;
+        ti[q] = tq.y;
+      }
+      float t6[6], o6[6], o6i[6];
+      comp_to6<NC>(tr, t6);
+      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
+      comp_to6<NC>(ti, t6);
+      gamma6(n, t6, a.inv2mu0, a.cgam, o6i);
+      er = 0.f;
+      ei = 0.f;
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        if (q == c) {
+          er = -o6[comp6<NC>(q)];
+          ei = -o6i[comp6<NC>(q)];
+        }
+    }
+    float2* erp = a.ER + base + (long long)c * a.Kx;
+    const float2 o = *erp;
+    const float dr = er - o.x, di = ei - o.y;
+    const int c6 = NC == 3 ? (c == 2 ? 5 : c) : c;
+    const float wc = c6 >= 3 ? 2.f : 1.f;
+    diff += (double)(n.w * wc * (dr * dr + di * di));
+    const float2 nv = make_float2(er, ei);
+    *erp = nv;
+    b0[sw(cc * L + a.kym[en2.x])] = nv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = diff;
+  __syncthreads();   // also orders the scattered coefficients before the transforms
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    a.part[blockIdx.x] = t;
+    __threadfence();
+    last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    decide(a.part, gridDim.x, a.st, sh);
+    if (threadIdx.x == 0) {
+      *a.counter = 0u;
+      // the only call site of the loop condition in this mode: one thread of one block
+      if (a.use_cond && a.st->done) cudaGraphSetConditional(a.cond, 0u);
+    }
+  }
+  const float2* z = fft_block(b0, b1, tw, L, C, +1);
+  for (int i = threadIdx.x; i < L * C; i += blockDim.x) {
+    const int y = fdiv(i, a.dC), cc = i - y * C, col = col0 + cc;
+    if (col < a.ncols) a.T1[(long long)y * a.ncols + col] = z[sw(cc * L + y)];
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // host side
 static int fft_check(rf_ctx* c, const char* what) {
@@ -575,7 +779,7 @@ int fft_geometry(rf_ctx* c) {
   }
   c->fft_C = C;
   // fused column phase (2D): kx columns per block within shared memory
-  c->fft_fused = false;
+  c->fft_colmode = kColSeparate;
   c->fft_M = std::max(1, std::min(c->opt.fft_fuse_kx > 0 ? c->opt.fft_fuse_kx : 1, c->Kx));
   c->fft_M_threads = 256;
   if (c->dim == 2 && c->opt.fft_fuse >= 0) {
@@ -586,7 +790,9 @@ int fft_geometry(rf_ctx* c) {
         set_error("FFT mode: columns too long for the fused column kernel's shared memory");
         return RF_ERR_INVALID;
       }
-      c->fft_fused = true;
+      c->fft_colmode = kColFused;
+    } else if (c->opt.fft_fuse == 2) {
+      c->fft_colmode = kColGreenInv;
     }
   }
   return RF_OK;
@@ -618,6 +824,7 @@ void init_attributes_fft() {
   const int s = 200 * 1024;
   cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_fft_colphase<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_fft_green_inv<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_fft_row<3, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_fft_row<3, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_fft_row<3, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
@@ -729,6 +936,40 @@ int launch_fft_colphase(rf_ctx* c, const int* done) {
   return r;
 }
 
+int launch_fft_green_inv(rf_ctx* c, const int* done) {
+  GreenInvArgs a{};
+  a.OUT = c->d_OUT;
+  a.ER = c->d_ER;
+  a.T1 = c->d_T1;
+  a.jptr = c->d_jptr;
+  a.jent = c->d_jent;
+  a.jn = c->d_jn;
+  a.kym = c->d_kym;
+  a.table = c->d_twy;
+  a.Kx = c->Kx;
+  a.L = c->ny;
+  a.ncols = c->nc * c->Kx;
+  a.C = std::max(1, std::min(c->fft_C, a.ncols));
+  a.dC = make_fastdiv((unsigned)a.C);
+  a.dKx = make_fastdiv((unsigned)std::max(1, c->Kx));
+  a.inv2mu0 = (float)(0.5 / c->mu0);
+  a.cgam = (float)((c->lam0 + c->mu0) / (c->mu0 * (c->lam0 + 2.0 * c->mu0)));
+  a.st = c->d_status;
+  a.counter = c->d_counter;
+  a.part = c->d_part;
+  a.done = done;
+  a.cond = c->while_cond;
+  a.use_cond = c->capturing_while ? 1 : 0;
+  trace_stage(c, 5);
+  const dim3 grid((unsigned)((a.ncols + a.C - 1) / a.C));
+  cudaError_t e = launch_pdl(k_fft_green_inv<3>, grid, dim3(c->fft_col_threads),
+                             cols_smem(c->ny, a.C), c->stream, a, (double)c->N);
+  if (e != cudaSuccess) return cuda_fail(e, "fft green + inverse");
+  const int r = fft_check(c, "fft green + inverse");
+  trace_end(c);
+  return r;
+}
+
 static int tck(cudaError_t e, const char* what) { return e == cudaSuccess ? RF_OK : cuda_fail(e, what); }
 
 // Autotuner for the FFT tiles: each candidate runs one untimed launch and then three timed groups
@@ -740,7 +981,7 @@ int fft_autotune(rf_ctx* c) {
   // block shape chosen (fft_fuse = 1 without fft_fuse_kx)
   const bool fuse_auto = c->dim == 2 && c->opt.fft_fuse == 0 && c->d_jptr &&
                          colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
-  const bool fuse_shape = c->fft_fused && c->opt.fft_fuse_kx == 0;
+  const bool fuse_shape = c->fft_colmode == kColFused && c->opt.fft_fuse_kx == 0;
   const bool rows_pinned = c->opt.fft_rows > 0 || c->opt.fft_row_blocks > 0;
   if (rows_pinned && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape) return RF_OK;
   rf_ctx::Tuned& tu = c->tuned;
@@ -758,7 +999,7 @@ int fft_autotune(rf_ctx* c) {
     if (fuse_auto || fuse_shape) {
       c->fft_M = tu.M;
       c->fft_M_threads = tu.M_threads;
-      if (fuse_auto) c->fft_fused = tu.fused;
+      if (fuse_auto) c->fft_colmode = tu.colmode;
     }
     return RF_OK;
   }
@@ -881,13 +1122,21 @@ int fft_autotune(rf_ctx* c) {
     c->fft_M = bestM;
     c->fft_M_threads = bestT;
     if (!err && fuse_auto) {
-      float sep = 1e30f;
+      // the three modes of the column phase, each timed over one update's column work
+      float sep = 1e30f, gi = 1e30f;
       err = time_it([&] {
         if (int e = fft_forward_stages(c, nullptr)) return e;
         if (int e = launch_gamma_finalize(c, 1, nullptr)) return e;
         return fft_inverse_stages(c, nullptr);
       }, &sep);
-      c->fft_fused = !err && best < sep;
+      if (!err)
+        err = time_it([&] {
+          if (int e = fft_forward_stages(c, nullptr)) return e;
+          return launch_fft_green_inv(c, nullptr);
+        }, &gi);
+      c->fft_colmode = kColSeparate;
+      if (!err && gi < sep && gi <= best) c->fft_colmode = kColGreenInv;
+      else if (!err && best < sep) c->fft_colmode = kColFused;
     }
   }
   cudaEventDestroy(e0);
@@ -904,7 +1153,7 @@ int fft_autotune(rf_ctx* c) {
     tu.col_threads = c->fft_col_threads;
     tu.M = c->fft_M;
     tu.M_threads = c->fft_M_threads;
-    tu.fused = c->fft_fused;
+    tu.colmode = c->fft_colmode;
   }
   return err;
 }

@@ -185,18 +185,22 @@ struct rf_ctx {
   int fft_rbase = 0, fft_rextra = 0;    // row partition (see set_rows_balanced)
   int fft_row_threads = 256, fft_col_threads = 256;   // block sizes (autotuned with the tiles)
   size_t fft_smem = 0;
-  // fused column phase (2D): forward y + Green operator + decision + inverse y per kx group
-  bool fft_fused = false;
+  // 2D column phase: 0 forward y, Green kernel, inverse y; 1 one fused kernel per kx group
+  // (kColFused); 2 forward y, then the Green operator inside the inverse y kernel
+  // (kColGreenInv). Modes 1 and 2 start a solve with one inverse y of the start coefficients.
+  int fft_colmode = 0;
   int fft_M = 1, fft_M_threads = 256;   // kx columns and threads per fused block
   int* d_jptr = nullptr;                // [Kx + 1] offsets of each kx's entries in d_jlist
   int* d_jlist = nullptr;               // half-pattern entries grouped by kx index
+  int2* d_jent = nullptr;               // in d_jlist order: (rectangle row iy, frequency kind)
+  float4* d_jn = nullptr;               // in d_jlist order: unit wave vector, multiplicity
   // last autotuned choice, reused when a new pattern has the same distinct kx, ky, kz counts
   struct Tuned {
     bool valid = false;
     int Kx = 0, Ky = 0, Kz = 0;
     int R = 0, row_threads = 0, C = 0, col_threads = 0, M = 0, M_threads = 0;
     int row_blocks_balanced = 0;
-    bool fused = false;
+    int colmode = 0;
   } tuned;
 
   // split-precision (tensor-core) transforms along x
@@ -353,6 +357,9 @@ int launch_fft_row(rf_ctx* c, const int* done, bool final_pass, int commit);
 int fft_inverse_stages(rf_ctx* c, const int* done);
 int fft_forward_stages(rf_ctx* c, const int* done);
 int launch_fft_colphase(rf_ctx* c, const int* done);
+int launch_fft_green_inv(rf_ctx* c, const int* done);
+int launch_gather_jentries(rf_ctx* c);
+constexpr int kColSeparate = 0, kColFused = 1, kColGreenInv = 2;
 int launch_gamma_finalize(rf_ctx* c, int splits, const int* done);
 void trace_begin(rf_ctx* c, long long idx);
 void trace_stage(rf_ctx* c, int stage);

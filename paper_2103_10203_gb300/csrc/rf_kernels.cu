@@ -538,6 +538,24 @@ int launch_hinfo(rf_ctx* c, const int* d_hk, long long Kh) {
   return launch_check(c, "hinfo");
 }
 
+// per-entry data of the half pattern in kx-grouped order (read without an indirection by the
+// Green operator inside the inverse y kernel)
+__global__ void k_gather_jentries(const int* jlist, const HIdx* hidx, const float4* hn, long long Kh,
+                                  int2* ent, float4* nn) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= Kh) return;
+  const int h = jlist[e];
+  ent[e] = make_int2(hidx[h].iy, hidx[h].kind);
+  nn[e] = hn[h];
+}
+
+int launch_gather_jentries(rf_ctx* c) {
+  if (c->Kh <= 0) return RF_OK;
+  k_gather_jentries<<<(unsigned)((c->Kh + 255) / 256), 256, 0, c->stream>>>(
+      c->d_jlist, c->d_hidx, c->d_hn, c->Kh, c->d_jent, c->d_jn);
+  return launch_check(c, "gather entries");
+}
+
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist) {
   k_phase_hist<<<304, 256, 0, c->stream>>>(c->d_phase, c->N, d_hist);
   return launch_check(c, "phase_hist");
@@ -614,12 +632,19 @@ int launch_iteration(rf_ctx* c) {
   const int* done = &c->d_status->done;
   trace_begin(c, c->launched_iters++);
   const bool fftm = c->opt.transform == RF_TRANSFORM_FFT;
-  if (fftm && c->fft_fused) {
+  if (fftm && c->fft_colmode == kColFused) {
     // row pass, then forward y + Green operator + decision + inverse y in one kernel (the
     // inverse of the start coefficients runs once before the first update)
     trace_stage(c, 2);
     if (int e = launch_fft_row(c, done, false, 0)) return e;
     return launch_fft_colphase(c, done);
+  }
+  if (fftm && c->fft_colmode == kColGreenInv) {
+    // row pass, forward y, then the Green operator + decision inside the inverse y kernel
+    trace_stage(c, 2);
+    if (int e = launch_fft_row(c, done, false, 0)) return e;
+    if (int e = fft_forward_stages(c, done)) return e;
+    return launch_fft_green_inv(c, done);
   }
   if (fftm) {
     if (int e = fft_inverse_stages(c, done)) return e;

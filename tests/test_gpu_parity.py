@@ -425,20 +425,27 @@ def test_fft_small_sides(lib, shape, rows, cols):
     assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
 
 
-@pytest.mark.parametrize("name,kx", [("j2_64", 1), ("j2_64", 3), ("rect", 2), ("three", 4),
-                                     ("c1", 1), ("fullset", 2)])
-def test_fft_fused_column_phase_matches_oracle(lib, name, kx):
-    """Forward y, Green operator, decision and inverse y in one kernel per group of kx columns
-    (a group count that leaves a partial last group included): the oracle's updates."""
+@pytest.mark.parametrize("name,kx,fuse", [("j2_64", 1, 1), ("j2_64", 3, 1), ("rect", 2, 1),
+                                          ("three", 4, 1), ("c1", 1, 1), ("fullset", 2, 1),
+                                          ("j2_64", 1, 2), ("rect", 3, 2), ("three", 1, 2),
+                                          ("c1", 5, 2), ("fullset", 2, 2)])
+def test_fft_fused_column_phase_matches_oracle(lib, name, kx, fuse):
+    """fuse 1: forward y, Green operator, decision and inverse y in one kernel per group of kx
+    columns (a group count that leaves a partial last group included); fuse 2: the Green
+    operator and decision inside the inverse y kernel (kx here is the column tile). Both give
+    the oracle's updates."""
     pm, ph, macro, pat = _pow2_case(name)
-    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=6, transform="fft", fft_fuse=1,
-                   fft_fuse_kx=kx)
+    tiles = dict(fft_fuse_kx=kx) if fuse == 1 else dict(fft_cols=kx)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=6, transform="fft", fft_fuse=fuse,
+                   **tiles)
     out = s.rf_solve(macro)
     eps, sig, _ = s.rf_get_fields()
     coeffs = s.rf_get_reduced_strain()
     info = s.rf_get_info()
     s.close()
-    assert info["fft_fused"] == 1 and info["fft_fuse_kx"] == min(kx, info["Kx"])
+    assert info["fft_fused"] == fuse
+    if fuse == 1:
+        assert info["fft_fuse_kx"] == min(kx, info["Kx"])
     r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=6)
     assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
     assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
@@ -447,14 +454,15 @@ def test_fft_fused_column_phase_matches_oracle(lib, name, kx):
     assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
 
 
-@pytest.mark.parametrize("shape", [(12, 12), (24, 6), (8, 24)])
-def test_fft_fused_column_phase_small_sides(lib, shape):
+@pytest.mark.parametrize("shape,fuse", [((12, 12), 1), ((24, 6), 1), ((8, 24), 1), ((12, 12), 2),
+                                        ((24, 6), 2)])
+def test_fft_fused_column_phase_small_sides(lib, shape, fuse):
     rng = np.random.default_rng(sum(shape))
     pm = (rng.random(shape) < 0.35).astype(np.uint8)
     ph = j2_phases()
     macro = np.array([0.02, 0, 0, 0, 0, 0.003])
     pat = O.pattern_adapted(pm, 1, max(8, pm.size // 4))
-    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=5, transform="fft", fft_fuse=1)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=5, transform="fft", fft_fuse=fuse)
     out = s.rf_solve(macro)
     eps, _, _ = s.rf_get_fields()
     s.close()
@@ -471,16 +479,18 @@ def test_fft_fused_and_separate_column_phases_agree(lib):
     pm, ph = cfg["phase_map"], cfg["phases"]
     pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
     res = {}
-    for fuse in (-1, 1):
+    for fuse in (-1, 1, 2):
         s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform="fft",
                        fft_fuse=fuse)
         res[fuse] = (s.rf_solve_path(uniaxial_path(20, 0.02)[::5]), s.rf_get_fields()[0])
         s.close()
-    (a, ea), (b, eb) = res[-1], res[1]
-    assert a["converged"] and b["converged"]
-    assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
-    assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
-    assert rel(eb, ea) <= 2e-5
+    a, ea = res[-1]
+    for fuse in (1, 2):
+        b, eb = res[fuse]
+        assert a["converged"] and b["converged"]
+        assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
+        assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
+        assert rel(eb, ea) <= 2e-5
 
 
 def test_fft_fuse_option_checks(lib):
@@ -490,7 +500,9 @@ def test_fft_fuse_option_checks(lib):
     with pytest.raises(lib.RFError):
         lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="dft", fft_fuse=1)
     with pytest.raises(lib.RFError):
-        lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="fft", fft_fuse=2)
+        lib.Solver(pm, elastic_phases(), transform="fft", fft_fuse=2)
+    with pytest.raises(lib.RFError):
+        lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="fft", fft_fuse=3)
 
 
 @pytest.mark.parametrize("name,blocks", [("j2_64", 5), ("j2_64", 64), ("j2_64", 1000),
@@ -582,7 +594,7 @@ def test_fft_transform_rejects_unsupported_sizes(lib):
                    precision="split_bf16")
 
 
-@pytest.mark.parametrize("transform,fuse", [("fft", -1), ("fft", 1), ("dft", 0)])
+@pytest.mark.parametrize("transform,fuse", [("fft", -1), ("fft", 1), ("fft", 2), ("dft", 0)])
 def test_traced_chunked_and_untraced_while_graph_solves_agree(lib, transform, fuse):
     """Untraced solves run as one conditional-while graph; traced solves replay chunks of
     updates with stage events. Same kernels and tiles in the same order: identical results
@@ -601,10 +613,10 @@ def test_traced_chunked_and_untraced_while_graph_solves_agree(lib, transform, fu
         st = s.rf_get_stage_times()
         info = s.rf_get_info()
         s.close()
-        assert info["fft_fused"] == (1 if fuse > 0 else 0)
+        assert info["fft_fused"] == max(fuse, 0)
         if traced:
             assert st["row"][1] == int(np.sum(res[traced]["iters"])) and st["row"][0] > 0
-            decision = "column_phase" if fuse > 0 else "green"
+            decision = "column_phase" if fuse == 1 else "green"
             assert st[decision][1] == st["row"][1] and st["final"][1] == len(path)
         assert info["kernel_launches"] > 0
     assert np.array_equal(res[False]["iters"], res[True]["iters"])
