@@ -267,6 +267,10 @@ void free_pattern(rf_ctx* c) {
   dfree(c->d_warm);
   dfree(c->d_phiI);
   dfree(c->d_phiF);
+  for (TcAxis* ax : {&c->tc_yf, &c->tc_yi, &c->tc_zf, &c->tc_zi}) {
+    dfree(ax->A);
+    *ax = TcAxis{};
+  }
   dfree(c->d_Tout);
   dfree(c->d_tc_err);
   dfree(c->d_jptr);
@@ -650,6 +654,8 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
     if (int e = fft_geometry(c)) return e;
     c->splitB = c->splitC = 1;
   }
+  // the split-precision modes run the y and z transforms on the tensor cores, one output slice
+  if (c->opt.precision != RF_PREC_FP32) c->splitB = c->splitC = 1;
   const int part_blocks = std::max(c->row_blocks, c->rows);   // any FFT row tile (R >= 1)
   const int splits = std::max(c->splitB, c->splitC);
   int err = dalloc(&c->d_kx, c->Kx, "pattern");

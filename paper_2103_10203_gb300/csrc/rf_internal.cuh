@@ -119,6 +119,12 @@ struct GammaArgs {
 
 }  // namespace rfk
 
+// split-precision transform along y or z: precomputed A tiles (see rf_tc.cu)
+struct TcAxis {
+  unsigned char* A = nullptr;
+  int M = 0, K = 0, nMT = 0, nKC = 0;
+};
+
 struct rf_ctx {
   int dev = 0;
   int dim = 2, nx = 1, ny = 1, nz = 1, nc = 3, ns = 0;
@@ -206,6 +212,7 @@ struct rf_ctx {
   // split-precision (tensor-core) transforms along x
   unsigned char* d_phiI = nullptr;
   unsigned char* d_phiF = nullptr;
+  TcAxis tc_yf, tc_yi, tc_zf, tc_zi;   // forward / inverse along y and z
   float* d_Tout = nullptr;        // [nXS][rows][NC][2 Kx] partial forward sums per x slice
   int* d_tc_err = nullptr;
   int tc_nXS = 0, tc_nJT = 0, tc_nJC = 0, tc_nXC = 0, tc_R = 0, tc_Qp = 0;
@@ -357,6 +364,9 @@ int launch_fft_row(rf_ctx* c, const int* done, bool final_pass, int commit);
 int fft_inverse_stages(rf_ctx* c, const int* done);
 int fft_forward_stages(rf_ctx* c, const int* done);
 int launch_fft_colphase(rf_ctx* c, const int* done);
+int launch_tc_axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits,
+                   long long in_split_stride, long long in_bstride, float2* out,
+                   long long out_bstride, int N, int batch, const int* done);
 int launch_fft_green_inv(rf_ctx* c, const int* done);
 int launch_gather_jentries(rf_ctx* c);
 constexpr int kColSeparate = 0, kColFused = 1, kColGreenInv = 2;

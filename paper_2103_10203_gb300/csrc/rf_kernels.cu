@@ -610,22 +610,35 @@ static int row_dispatch(rf_ctx* c, const RowArgs& a, bool final_pass) {
 
 int launch_gamma_finalize(rf_ctx* c, int splits, const int* done);
 
+// transforms along y and z: tensor cores (split operands) in the split-precision modes, the
+// SIMT DFT otherwise
+static int axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits, long long iss,
+                long long ibs, float2* out, int out_splits, long long oss, long long obs, int M,
+                int N, int K, int batch, const int* mvals, const int* kvals, const float2* tab,
+                int L, int sign, const int* done) {
+  if (c->opt.precision != RF_PREC_FP32)
+    return launch_tc_axis(c, ax, in, in_splits, iss, ibs, out, obs, N, batch, done);
+  return dft(c, in, in_splits, iss, ibs, out, out_splits, oss, obs, M, N, K, batch, mvals, kvals,
+             tab, L, sign, done);
+}
+
 static int inverse_stages(rf_ctx* c, const int* done) {
   const int NCK = c->nc * c->Kx;
   if (c->dim == 3) {
     // along z: T2[z][ky][c][kx] = sum_kz exp(+..kz z) ER[kz][ky][c][kx]
     trace_stage(c, 0);
-    if (int e = dft(c, c->d_ER, 1, 0, 0, c->d_T2, 1, 0, 0, c->nz, c->Ky * NCK, c->Kz, 1, nullptr,
-                    c->d_kzm, c->d_twz, c->nz, +1, done))
+    if (int e = axis(c, c->tc_zi, c->d_ER, 1, 0, 0, c->d_T2, 1, 0, 0, c->nz, c->Ky * NCK, c->Kz,
+                     1, nullptr, c->d_kzm, c->d_twz, c->nz, +1, done))
       return e;
     // along y, batched over z
     trace_stage(c, 1);
-    return dft(c, c->d_T2, 1, 0, (long long)c->Ky * NCK, c->d_T1, 1, 0, (long long)c->ny * NCK,
-               c->ny, NCK, c->Ky, c->nz, nullptr, c->d_kym, c->d_twy, c->ny, +1, done);
+    return axis(c, c->tc_yi, c->d_T2, 1, 0, (long long)c->Ky * NCK, c->d_T1, 1, 0,
+                (long long)c->ny * NCK, c->ny, NCK, c->Ky, c->nz, nullptr, c->d_kym, c->d_twy,
+                c->ny, +1, done);
   }
   trace_stage(c, 1);
-  return dft(c, c->d_ER, 1, 0, 0, c->d_T1, 1, 0, 0, c->ny, NCK, c->Ky, 1, nullptr, c->d_kym,
-             c->d_twy, c->ny, +1, done);
+  return axis(c, c->tc_yi, c->d_ER, 1, 0, 0, c->d_T1, 1, 0, 0, c->ny, NCK, c->Ky, 1, nullptr,
+              c->d_kym, c->d_twy, c->ny, +1, done);
 }
 
 int launch_iteration(rf_ctx* c) {
@@ -670,17 +683,17 @@ int launch_iteration(rf_ctx* c) {
   const long long fstride = (long long)c->rows * NCK;
   trace_stage(c, 3);
   if (c->dim == 3) {
-    if (int e = dft(c, fin, fsplits, fstride, (long long)c->ny * NCK, c->d_T2f, 1, 0,
-                    (long long)c->Ky * NCK, c->Ky, NCK, c->ny, c->nz, c->d_kym, nullptr, c->d_twy,
-                    c->ny, -1, done))
+    if (int e = axis(c, c->tc_yf, fin, fsplits, fstride, (long long)c->ny * NCK, c->d_T2f, 1, 0,
+                     (long long)c->Ky * NCK, c->Ky, NCK, c->ny, c->nz, c->d_kym, nullptr,
+                     c->d_twy, c->ny, -1, done))
       return e;
     trace_stage(c, 4);
-    if (int e = dft(c, c->d_T2f, 1, 0, 0, c->d_OUT, c->splitC, outstride, 0, c->Kz,
-                    c->Ky * NCK, c->nz, 1, c->d_kzm, nullptr, c->d_twz, c->nz, -1, done))
+    if (int e = axis(c, c->tc_zf, c->d_T2f, 1, 0, 0, c->d_OUT, c->splitC, outstride, 0, c->Kz,
+                     c->Ky * NCK, c->nz, 1, c->d_kzm, nullptr, c->d_twz, c->nz, -1, done))
       return e;
   } else {
-    if (int e = dft(c, fin, fsplits, fstride, 0, c->d_OUT, c->splitB, outstride, 0, c->Ky, NCK,
-                    c->ny, 1, c->d_kym, nullptr, c->d_twy, c->ny, -1, done))
+    if (int e = axis(c, c->tc_yf, fin, fsplits, fstride, 0, c->d_OUT, c->splitB, outstride, 0,
+                     c->Ky, NCK, c->ny, 1, c->d_kym, nullptr, c->d_twy, c->ny, -1, done))
       return e;
   }
   return launch_gamma_finalize(c, (c->dim == 3) ? c->splitC : c->splitB, done);

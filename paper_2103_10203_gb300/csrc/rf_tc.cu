@@ -14,8 +14,16 @@
 // canonical no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix). The
 // twiddle tiles are precomputed per pattern in that exact layout and staged into shared memory
 // with bulk asynchronous copies; every mbarrier wait is bounded and reports a timeout.
+//
+// The transforms along y and z (Sec. 4 steps b and d on the reduced rectangle) run on the tensor
+// cores as well, as one real GEMM per axis and direction: complex out[m][n] = sum_k W[m][k]
+// in[k][n] with W = exp(sign 2 pi i mv kv / L), written with real and imaginary parts
+// interleaved, D[2m + 0] = sum_k (Wr, -Wi) . (Xr, Xi) and D[2m + 1] = sum_k (Wi, Wr) . (Xr, Xi),
+// so that A = W is 2M x 2K, B = X is 2K x N and D is 2M x N (64 complex outputs per 128-lane
+// tile). A is precomputed per pattern; X is split into hi + lo while it is staged.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "rf_internal.cuh"
@@ -320,6 +328,211 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
 
 }  // namespace tc
 
+namespace tc {
+
+// A tiles of one axis transform: tile (mt, g) covers complex rows [64 mt, 64 mt + 64) and
+// elements [g per, (g + 1) per) of 2K; hi and lo parts back to back (2 x 16 KB per tile)
+template <class E>
+__global__ void k_axis_tiles(int M, int K, const int* mvals, const int* kvals, const float2* tab,
+                             int L, int sign, int nMT, int nKC, unsigned char* A) {
+  constexpr int per = kChunkBytes / E::kBytes;
+  const long long total = (long long)nMT * nKC * kTile * per;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(i % per);
+    const int r = (int)((i / per) % kTile);
+    const long long t = i / ((long long)per * kTile);
+    const int g = (int)(t % nKC), mt = (int)(t / nKC);
+    const int m = mt * 64 + (r >> 1);
+    const int kp = g * per + e, k = kp >> 1;
+    float v = 0.f;
+    if (m < M && k < K) {
+      const long long mv = mvals ? mvals[m] : m, kv = kvals ? kvals[k] : k;
+      float2 w = tab[(int)((mv * kv) % L)];   // (cos, sin)(2 pi mv kv / L)
+      if (sign < 0) w.y = -w.y;
+      const bool im_row = r & 1, im_col = kp & 1;
+      v = im_row ? (im_col ? w.x : w.y) : (im_col ? -w.y : w.x);
+    }
+    unsigned char* base = A + ((long long)(mt * nKC + g) * 2) * kTileBytes;
+    put_split<E>(base, base + kTileBytes, cm_off(r, e * E::kBytes, kChunkBytes), v);
+  }
+}
+
+// hi + lo split of one 16-byte core-matrix row segment (8 BF16 or 4 TF32 values)
+template <class E>
+__device__ __forceinline__ void split_seg(const float* x, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+  if constexpr (E::kBytes == 2) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
+      h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[i]) : "f"(x[i]));
+      const float r = x[i] - __uint_as_float(h[i]);
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[i]) : "f"(r));
+    }
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+struct TcAxisArgs {
+  const float2* in;       // [in_splits][batch][K][N] (the splits are summed)
+  int in_splits;
+  long long in_split_stride, in_bstride;
+  float2* out;            // [batch][M][N]
+  long long out_bstride;
+  const unsigned char* A;
+  int M, N, K, nKC, NT, lNT;   // lNT = log2(NT)
+  uint32_t tmem_cols;
+  const int* done;
+  int* err;
+};
+
+// one CTA: 64 complex output rows (blockIdx.y) x NT columns (blockIdx.x) of one batch entry
+// (blockIdx.z); 128 threads, one per accumulator lane
+template <class E>
+__global__ __launch_bounds__(128) void k_tc_axis(TcAxisArgs a) {
+  if (a.done && *a.done) return;
+  constexpr int per = kChunkBytes / E::kBytes;   // K elements per chunk
+  constexpr int kc = per / 2;                    // complex k per chunk
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* As = smem;                          // hi, lo: 2 x 16 KB
+  unsigned char* Bs = smem + 2 * kTileBytes;         // hi, lo: 2 x NT x 128 B
+  const int bbytes = a.NT * kChunkBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + 2 * bbytes);   // [0] A copy, [1] MMAs
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int n0 = blockIdx.x * a.NT, mt = blockIdx.y;
+  const long long b = blockIdx.z;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t id_mma = idesc<E>(kTile, a.NT);
+  const float2* inb = a.in + b * a.in_bstride;
+  bool ok = true;
+  for (int g = 0; g < a.nKC; ++g) {
+    // the buffers are free once the previous chunk's MMAs completed
+    if (g > 0 && !mbar_wait(&bars[1], (g - 1) & 1)) atomicOr(s_err, 1);
+    __syncthreads();
+    ok = (*s_err == 0);
+    if (!ok) break;   // uniform: every thread read s_err after the same barrier
+    if (tid == 0)
+      bulk_load(As, a.A + ((long long)(mt * a.nKC + g) * 2) * kTileBytes, 2 * kTileBytes,
+                &bars[0]);
+    // B chunk: item i = (row nn, 16-byte segment sg) holds cps complex k of column n0 + nn;
+    // consecutive threads take consecutive columns (coalesced loads), each batch issues all its
+    // loads before the splits, and every segment goes to shared memory as one 16-byte store
+    constexpr int cps = 8 / E::kBytes;   // complex values per 16-byte segment
+    const int items = a.NT * (kChunkBytes / 16);
+    for (int i0 = tid; i0 < items; i0 += 4 * blockDim.x) {
+      float2 v[4][cps];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const int nn = i & (a.NT - 1), sg = i >> a.lNT, n = n0 + nn;
+#pragma unroll
+        for (int q = 0; q < cps; ++q) {
+          const int k = g * kc + sg * cps + q;
+          v[u][q] = make_float2(0.f, 0.f);
+          if (i < items && k < a.K && n < a.N) {
+            const float2* p = inb + (long long)k * a.N + n;
+            v[u][q] = p[0];
+            for (int t = 1; t < a.in_splits; ++t) {
+              const float2 w = p[t * a.in_split_stride];
+              v[u][q].x += w.x;
+              v[u][q].y += w.y;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= items) continue;
+        const int nn = i & (a.NT - 1), sg = i >> a.lNT;
+        uint4 hi, lo;
+        split_seg<E>(reinterpret_cast<const float*>(v[u]), hi, lo);
+        const uint32_t off = cm_off(nn, sg * 16, kChunkBytes);
+        *reinterpret_cast<uint4*>(Bs + off) = hi;
+        *reinterpret_cast<uint4*>(Bs + bbytes + off) = lo;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      if (!mbar_wait(&bars[0], g & 1)) {
+        atomicOr(s_err, 1);
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a_hi = smem_u32(As), a_lo = a_hi + kTileBytes;
+        const uint32_t b_hi = smem_u32(Bs), b_lo = b_hi + bbytes;
+        const uint32_t sbo = (kChunkBytes / 16) * 128;
+        for (int st = 0; st < kChunkBytes / 32; ++st) {
+          const uint32_t o = st * 256;
+          const uint64_t ah = make_desc(a_hi + o, 128, sbo), al = make_desc(a_lo + o, 128, sbo);
+          const uint64_t bh = make_desc(b_hi + o, 128, sbo), bl = make_desc(b_lo + o, 128, sbo);
+          const uint32_t first = (g == 0 && st == 0) ? 0u : 1u;
+          mma<E>(tmem, ah, bh, id_mma, first);
+          mma<E>(tmem, ah, bl, id_mma, 1u);
+          mma<E>(tmem, al, bh, id_mma, 1u);
+        }
+        mma_commit(&bars[1]);
+      }
+    }
+  }
+  if (ok && !mbar_wait(&bars[1], (a.nKC - 1) & 1)) atomicOr(s_err, 1);
+  __syncthreads();
+  ok = (*s_err == 0);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // lane tid holds D row tid: the real (even) or imaginary (odd) part of output m
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const int m = mt * 64 + (tid >> 1);
+    float2* ob = a.out + b * a.out_bstride + (long long)m * a.N;
+    for (int c0 = 0; c0 < a.NT; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float w = __shfl_xor_sync(0xffffffffu, v[i], 1);
+        const int n = n0 + c0 + i;
+        if (!(tid & 1) && m < a.M && n < a.N) ob[n] = make_float2(v[i], w);
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(a.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(a.tmem_cols));
+}
+
+}  // namespace tc
+
 // ------------------------------------------------------------------------------------------
 // host side
 int tc_setup(rf_ctx* c) {
@@ -366,6 +579,39 @@ int tc_setup(rf_ctx* c) {
   c->launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "phi tiles");
+  // A tiles of the transforms along y (and z): forward (rows = pattern values, K = positions)
+  // and inverse (rows = positions, K = pattern values)
+  struct AxisSpec {
+    TcAxis* dst;
+    int M, K;
+    const int* mvals;
+    const int* kvals;
+    const float2* tab;
+    int L, sign;
+  };
+  AxisSpec specs[4] = {{&c->tc_yf, c->Ky, c->ny, c->d_kym, nullptr, c->d_twy, c->ny, -1},
+                       {&c->tc_yi, c->ny, c->Ky, nullptr, c->d_kym, c->d_twy, c->ny, +1},
+                       {&c->tc_zf, c->Kz, c->nz, c->d_kzm, nullptr, c->d_twz, c->nz, -1},
+                       {&c->tc_zi, c->nz, c->Kz, nullptr, c->d_kzm, c->d_twz, c->nz, +1}};
+  for (int i = 0; i < (c->dim == 3 ? 4 : 2); ++i) {
+    const AxisSpec& sp = specs[i];
+    TcAxis& ax = *sp.dst;
+    ax.M = sp.M;
+    ax.K = sp.K;
+    ax.nMT = (sp.M + 63) / 64;
+    ax.nKC = (2 * sp.K + per - 1) / per;
+    e = cudaMalloc(&ax.A, (size_t)ax.nMT * ax.nKC * 2 * kTileBytes);
+    if (e != cudaSuccess) return cuda_fail(e, "axis tiles");
+    if (bf)
+      k_axis_tiles<EBf16><<<304, 256, 0, c->stream>>>(sp.M, sp.K, sp.mvals, sp.kvals, sp.tab,
+                                                      sp.L, sp.sign, ax.nMT, ax.nKC, ax.A);
+    else
+      k_axis_tiles<ETf32><<<304, 256, 0, c->stream>>>(sp.M, sp.K, sp.mvals, sp.kvals, sp.tab,
+                                                      sp.L, sp.sign, ax.nMT, ax.nKC, ax.A);
+    c->launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "axis tiles");
+  }
   const int tau_rb = kTile * bytes;
   // force one CTA per SM when it needs all 512 tensor-memory columns
   size_t smem = 4 * kTileBytes + 4 * (size_t)Qp * kChunkBytes + 2 * (size_t)Qp * tau_rb + 64;
@@ -374,9 +620,50 @@ int tc_setup(rf_ctx* c) {
   return RF_OK;
 }
 
+// One transform along y or z on the tensor cores (see the top of this file); the column tile
+// NT is the largest of 256, 128, 64, 32 that still gives about two CTAs per SM.
+int launch_tc_axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits,
+                   long long in_split_stride, long long in_bstride, float2* out,
+                   long long out_bstride, int N, int batch, const int* done) {
+  using namespace tc;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+  int NT = 256;
+  while (NT > 32 && (long long)((N + NT - 1) / NT) * ax.nMT * batch < 2LL * sms) NT >>= 1;
+  TcAxisArgs a{};
+  a.in = in;
+  a.in_splits = in_splits;
+  a.in_split_stride = in_split_stride;
+  a.in_bstride = in_bstride;
+  a.out = out;
+  a.out_bstride = out_bstride;
+  a.A = ax.A;
+  a.M = ax.M;
+  a.N = N;
+  a.K = ax.K;
+  a.nKC = ax.nKC;
+  a.NT = NT;
+  a.lNT = 0;
+  while ((1 << a.lNT) < NT) ++a.lNT;
+  a.tmem_cols = (uint32_t)std::max(32, NT);
+  a.done = done;
+  a.err = &c->d_status->timeout;
+  const size_t smem = 2 * kTileBytes + 2 * (size_t)NT * kChunkBytes + 64;
+  dim3 grid((N + NT - 1) / NT, ax.nMT, batch);
+  if (c->opt.precision == RF_PREC_SPLIT_BF16)
+    k_tc_axis<EBf16><<<grid, 128, smem, c->stream>>>(a);
+  else
+    k_tc_axis<ETf32><<<grid, 128, smem, c->stream>>>(a);
+  c->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : cuda_fail(e, "tc axis");
+}
+
 void init_attributes_tc() {
   using namespace tc;
   const int s = 200 * 1024;
+  cudaFuncSetAttribute(k_tc_axis<EBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_tc_axis<ETf32>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_tc_row<EBf16, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_tc_row<EBf16, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_tc_row<EBf16, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
