@@ -75,6 +75,31 @@ __global__ void k_phi_tiles(const int* kx, int Kx, int Nx, const float2* tab, in
   }
 }
 
+// hi + lo split of one 16-byte core-matrix row segment (8 BF16 or 4 TF32 values)
+template <class E>
+__device__ __forceinline__ void split_seg(const float* x, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+  if constexpr (E::kBytes == 2) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
+      h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[i]) : "f"(x[i]));
+      const float r = x[i] - __uint_as_float(h[i]);
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[i]) : "f"(r));
+    }
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 // ------------------------------------------------------------------------------------------
 struct TcRowArgs {
   const float2* T;        // [rows][NC][Kx]
@@ -160,23 +185,44 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
       bulk_load(A, src, 2 * kTileBytes, &bars[b]);
     }
     if (g < a.nJC && ok) {
-      // Tq chunk: rows q, K = j' in [g * per, (g + 1) * per)
-      for (int i = tid; i < a.Qp * (per / 2); i += blockDim.x) {
-        const int q = i / (per / 2), kp = i % (per / 2);
-        const int jp = g * per + 2 * kp;
-        const int j = jp >> 1;
-        float vr = 0.f, vi = 0.f;
-        if (q < Q && j < a.Kx) {
-          const int r = q / NC, c = q % NC, row = row0 + r;
-          if (row < a.rows) {
-            const float2 t = a.T[((long long)row * NC + c) * a.Kx + j];
-            const float f = a.fac[j];
-            vr = f * t.x;
-            vi = f * t.y;
+      // Tq chunk: rows q, K = j' in [g * per, (g + 1) * per). Item i = (row q, 16-byte segment
+      // sg) with the row's low three bits fastest, so that a warp's 16-byte stores fill whole
+      // core matrices; each batch issues all its loads before the splits.
+      constexpr int cps = 8 / E::kBytes;   // complex values per segment
+      const int items = a.Qp * (kChunkBytes / 16);
+      for (int i0 = tid; i0 < items; i0 += 4 * blockDim.x) {
+        float v[4][2 * cps];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * blockDim.x;
+          const int q = ((i >> 6) << 3) | (i & 7), sg = (i >> 3) & 7;
+          const int r = q / NC, c = q - r * NC, row = row0 + r;
+          const bool live = i < items && q < Q && row < a.rows;
+          const float2* tp = a.T + ((long long)row * NC + c) * a.Kx;
+#pragma unroll
+          for (int qq = 0; qq < cps; ++qq) {
+            const int j = g * (per / 2) + sg * cps + qq;
+            float2 t = make_float2(0.f, 0.f);
+            float f = 0.f;
+            if (live && j < a.Kx) {
+              t = tp[j];
+              f = a.fac[j];
+            }
+            v[u][2 * qq] = f * t.x;
+            v[u][2 * qq + 1] = f * t.y;
           }
         }
-        put_split<E>(Tb, Tb + tq_bytes, cm_off(q, 2 * kp * E::kBytes, kChunkBytes), vr);
-        put_split<E>(Tb, Tb + tq_bytes, cm_off(q, (2 * kp + 1) * E::kBytes, kChunkBytes), vi);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * blockDim.x;
+          if (i >= items) continue;
+          const int q = ((i >> 6) << 3) | (i & 7), sg = (i >> 3) & 7;
+          uint4 hi, lo;
+          split_seg<E>(v[u], hi, lo);
+          const uint32_t off = cm_off(q, sg * 16, kChunkBytes);
+          *reinterpret_cast<uint4*>(Tb + off) = hi;
+          *reinterpret_cast<uint4*>(Tb + tq_bytes + off) = lo;
+        }
       }
     }
     if (g == a.nJC) {
@@ -356,31 +402,6 @@ __global__ void k_axis_tiles(int M, int K, const int* mvals, const int* kvals, c
     unsigned char* base = A + ((long long)(mt * nKC + g) * 2) * kTileBytes;
     put_split<E>(base, base + kTileBytes, cm_off(r, e * E::kBytes, kChunkBytes), v);
   }
-}
-
-// hi + lo split of one 16-byte core-matrix row segment (8 BF16 or 4 TF32 values)
-template <class E>
-__device__ __forceinline__ void split_seg(const float* x, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
-  if constexpr (E::kBytes == 2) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * i]), h1 = __float2bfloat16_rn(x[2 * i + 1]);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * i] - __bfloat162float(h0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * i + 1] - __bfloat162float(h1));
-      h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-      l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h[i]) : "f"(x[i]));
-      const float r = x[i] - __uint_as_float(h[i]);
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[i]) : "f"(r));
-    }
-  }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 struct TcAxisArgs {
