@@ -449,6 +449,16 @@ def run_3d(args, rf, torch):
             its += out["iters"]
         return float(np.sum(ms)), its, out
 
+    if args.profile_updates > 0:
+        # a fixed number of traced updates (plain chunk graphs) for profiler captures
+        s = rf.Solver(pm, ph, pattern=pattern, stream=sh, tol=0.0, max_iter=args.profile_updates,
+                      transform="dft", precision=prec)
+        s.rf_set_tracing(True)
+        out = s.rf_solve(macro)
+        n_launch = s.rf_get_info()["kernel_launches"]
+        s.close()
+        print(json.dumps({"profile_updates": int(out["iters"]), "kernel_launches": n_launch}))
+        return 0
     solver = rf.Solver(pm, ph, pattern=pattern, stream=sh, tol=TOL, max_iter=MAX_ITER,
                        transform="dft", precision=prec)
     info = solver.rf_get_info()
