@@ -418,9 +418,10 @@ struct TcAxisArgs {
 };
 
 // one CTA: 64 complex output rows (blockIdx.y) x NT columns (blockIdx.x) of one batch entry
-// (blockIdx.z); 128 threads, one per accumulator lane
+// (blockIdx.z); 256 threads stage the operands, warps 0-3 (one thread per accumulator lane)
+// read the result
 template <class E>
-__global__ __launch_bounds__(128) void k_tc_axis(TcAxisArgs a) {
+__global__ __launch_bounds__(256) void k_tc_axis(TcAxisArgs a) {
   if (a.done && *a.done) return;
   constexpr int per = kChunkBytes / E::kBytes;   // K elements per chunk
   constexpr int kc = per / 2;                    // complex k per chunk
@@ -527,7 +528,7 @@ __global__ __launch_bounds__(128) void k_tc_axis(TcAxisArgs a) {
   __syncthreads();
   ok = (*s_err == 0);
   asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok) {
+  if (ok && tid < 128) {
     // lane tid holds D row tid: the real (even) or imaginary (odd) part of output m
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const int m = mt * 64 + (tid >> 1);
@@ -672,9 +673,9 @@ int launch_tc_axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits,
   const size_t smem = 2 * kTileBytes + 2 * (size_t)NT * kChunkBytes + 64;
   dim3 grid((N + NT - 1) / NT, ax.nMT, batch);
   if (c->opt.precision == RF_PREC_SPLIT_BF16)
-    k_tc_axis<EBf16><<<grid, 128, smem, c->stream>>>(a);
+    k_tc_axis<EBf16><<<grid, 256, smem, c->stream>>>(a);
   else
-    k_tc_axis<ETf32><<<grid, 128, smem, c->stream>>>(a);
+    k_tc_axis<ETf32><<<grid, 256, smem, c->stream>>>(a);
   c->launches += 1;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? RF_OK : cuda_fail(e, "tc axis");
