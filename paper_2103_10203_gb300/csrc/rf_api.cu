@@ -246,8 +246,18 @@ int get_while_graph(rf_ctx* c) {
   return RF_OK;
 }
 
+// forgets the current pattern; its device buffers stay for the next one (palloc)
 void free_pattern(rf_ctx* c) {
   free_graphs(c);
+  for (TcAxis* ax : {&c->tc_yf, &c->tc_yi, &c->tc_zf, &c->tc_zi}) {
+    ax->M = ax->K = ax->nMT = ax->nKC = 0;
+  }
+  c->fft_colmode = kColSeparate;
+  c->have_pattern = false;
+  c->fields_valid = false;
+}
+
+void release_pattern_buffers(rf_ctx* c) {
   dfree(c->d_kx);
   dfree(c->d_kym);
   dfree(c->d_kzm);
@@ -267,19 +277,15 @@ void free_pattern(rf_ctx* c) {
   dfree(c->d_warm);
   dfree(c->d_phiI);
   dfree(c->d_phiF);
-  for (TcAxis* ax : {&c->tc_yf, &c->tc_yi, &c->tc_zf, &c->tc_zi}) {
-    dfree(ax->A);
-    *ax = TcAxis{};
-  }
+  for (TcAxis* ax : {&c->tc_yf, &c->tc_yi, &c->tc_zf, &c->tc_zi}) dfree(ax->A);
   dfree(c->d_Tout);
   dfree(c->d_tc_err);
   dfree(c->d_jptr);
   dfree(c->d_jlist);
   dfree(c->d_jent);
   dfree(c->d_jn);
-  c->fft_colmode = kColSeparate;
-  c->have_pattern = false;
-  c->fields_valid = false;
+  dfree(c->d_hk);
+  c->pcap.clear();
 }
 
 int reset_path_state(rf_ctx* c) {
@@ -538,30 +544,39 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   const int n[3] = {c->nx, c->ny, c->nz};
   // signed range (-N/2, N/2]: -(N-1)/2 <= k <= N/2 with integer division
   auto in_range = [](int k, int nn) { return k >= -((nn - 1) / 2) && k <= nn / 2; };
-  std::map<std::tuple<int, int, int>, long long> index;
+  // frequencies as unique linear keys (offset signed indices), sorted once: duplicate,
+  // conjugate and position lookups are binary searches
+  auto key = [&](int kx, int ky, int kz) {
+    return ((long long)(kz + (n[2] - 1) / 2) * n[1] + (ky + (n[1] - 1) / 2)) * n[0] +
+           (kx + (n[0] - 1) / 2);
+  };
+  std::vector<long long> keys(K);
   int zeros = 0;
   for (long long p = 0; p < K; ++p) {
     const int kx = freqs[3 * p], ky = freqs[3 * p + 1], kz = freqs[3 * p + 2];
     if (!in_range(kx, n[0]) || !in_range(ky, n[1]) || !in_range(kz, n[2]))
       return invalid("rf_set_pattern: frequency outside the signed range (-N/2, N/2]");
-    if (!index.emplace(std::make_tuple(kx, ky, kz), p).second)
-      return invalid("rf_set_pattern: duplicate frequency");
     if (kx == 0 && ky == 0 && kz == 0) ++zeros;
+    keys[p] = key(kx, ky, kz);
   }
+  std::sort(keys.begin(), keys.end());
+  if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
+    return invalid("rf_set_pattern: duplicate frequency");
   if (zeros != 1) return invalid("rf_set_pattern: the zero frequency must be present");
   auto conj = [&](int kx, int ky, int kz) {
     return std::make_tuple(signed_of(wrapi(-kx, n[0]), n[0]), signed_of(wrapi(-ky, n[1]), n[1]),
                            signed_of(wrapi(-kz, n[2]), n[2]));
   };
-  for (const auto& kv : index) {
-    auto [kx, ky, kz] = kv.first;
-    if (!index.count(conj(kx, ky, kz)))
+  for (long long p = 0; p < K; ++p) {
+    auto [cx, cy, cz] = conj(freqs[3 * p], freqs[3 * p + 1], freqs[3 * p + 2]);
+    if (!std::binary_search(keys.begin(), keys.end(), key(cx, cy, cz)))
       return invalid("rf_set_pattern: pattern is not closed under k -> -k");
   }
   // half set: kx >= 0, sorted by (kx, ky, kz)
   std::vector<std::tuple<int, int, int>> H;
-  for (const auto& kv : index)
-    if (std::get<0>(kv.first) >= 0) H.push_back(kv.first);
+  H.reserve(K / 2 + 2);
+  for (long long p = 0; p < K; ++p)
+    if (freqs[3 * p] >= 0) H.emplace_back(freqs[3 * p], freqs[3 * p + 1], freqs[3 * p + 2]);
   std::sort(H.begin(), H.end());
   std::vector<int> xs, ys, zs;
   for (auto& t : H) {
@@ -583,19 +598,20 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   c->Ky = (int)ys.size();
   c->Kz = (int)zs.size();
   c->pat.assign(freqs, freqs + 3 * K);
-  std::map<std::tuple<int, int, int>, long long> hpos;
-  for (long long h = 0; h < c->Kh; ++h) hpos[H[h]] = h;
+  auto hpos = [&](const std::tuple<int, int, int>& t) {
+    return (long long)(std::lower_bound(H.begin(), H.end(), t) - H.begin());
+  };
   c->map_h.assign(K, 0);
   c->map_conj.assign(K, 0);
   c->h_src.assign(c->Kh, -1);
   for (long long p = 0; p < K; ++p) {
     const int kx = freqs[3 * p], ky = freqs[3 * p + 1], kz = freqs[3 * p + 2];
     if (kx >= 0) {
-      c->map_h[p] = hpos[std::make_tuple(kx, ky, kz)];
+      c->map_h[p] = hpos(std::make_tuple(kx, ky, kz));
       c->map_conj[p] = 0;
       c->h_src[c->map_h[p]] = p;
     } else {
-      c->map_h[p] = hpos[conj(kx, ky, kz)];
+      c->map_h[p] = hpos(conj(kx, ky, kz));
       c->map_conj[p] = 1;
     }
   }
@@ -658,22 +674,22 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (c->opt.precision != RF_PREC_FP32) c->splitB = c->splitC = 1;
   const int part_blocks = std::max(c->row_blocks, c->rows);   // any FFT row tile (R >= 1)
   const int splits = std::max(c->splitB, c->splitC);
-  int err = dalloc(&c->d_kx, c->Kx, "pattern");
-  if (!err) err = dalloc(&c->d_kym, c->Ky, "pattern");
-  if (!err) err = dalloc(&c->d_kzm, c->Kz, "pattern");
-  if (!err) err = dalloc(&c->d_fac, c->Kx, "pattern");
-  if (!err) err = dalloc(&c->d_hidx, c->Kh, "pattern");
-  if (!err) err = dalloc(&c->d_hn, c->Kh, "pattern");
-  if (!err) err = dalloc(&c->d_ER, c->rect, "coefficients");
-  if (!err) err = dalloc(&c->d_T1, (size_t)c->rows * NCK, "line transforms");
-  if (!err) err = dalloc(&c->d_T1p, (size_t)c->rows * NCK, "line transforms");
-  if (!err && c->dim == 3) err = dalloc(&c->d_T2, (size_t)c->nz * c->Ky * NCK, "line transforms");
-  if (!err && c->dim == 3) err = dalloc(&c->d_T2f, (size_t)c->nz * c->Ky * NCK, "line transforms");
-  if (!err) err = dalloc(&c->d_OUT, (size_t)splits * c->rect, "partials");
+  int err = palloc(c, &c->d_kx, c->Kx, "pattern");
+  if (!err) err = palloc(c, &c->d_kym, c->Ky, "pattern");
+  if (!err) err = palloc(c, &c->d_kzm, c->Kz, "pattern");
+  if (!err) err = palloc(c, &c->d_fac, c->Kx, "pattern");
+  if (!err) err = palloc(c, &c->d_hidx, c->Kh, "pattern");
+  if (!err) err = palloc(c, &c->d_hn, c->Kh, "pattern");
+  if (!err) err = palloc(c, &c->d_ER, c->rect, "coefficients");
+  if (!err) err = palloc(c, &c->d_T1, (size_t)c->rows * NCK, "line transforms");
+  if (!err) err = palloc(c, &c->d_T1p, (size_t)c->rows * NCK, "line transforms");
+  if (!err && c->dim == 3) err = palloc(c, &c->d_T2, (size_t)c->nz * c->Ky * NCK, "line transforms");
+  if (!err && c->dim == 3) err = palloc(c, &c->d_T2f, (size_t)c->nz * c->Ky * NCK, "line transforms");
+  if (!err) err = palloc(c, &c->d_OUT, (size_t)splits * c->rect, "partials");
   // block partials of the convergence measure: Green kernel blocks, or column blocks of the
   // fused modes (<= NC Kx)
   if (!err)
-    err = dalloc(&c->d_part,
+    err = palloc(c, &c->d_part,
                  (size_t)std::max<long long>((c->Kh + kGammaBlock - 1) / kGammaBlock,
                                              (long long)c->nc * c->Kx),
                  "partials");
@@ -685,10 +701,10 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
     for (int j = 0; j < c->Kx; ++j) jptr[j + 1] += jptr[j];
     std::vector<int> fill(jptr.begin(), jptr.end() - 1);
     for (long long h = 0; h < c->Kh; ++h) jlist[fill[c->h_hidx[h].j]++] = (int)h;
-    err = dalloc(&c->d_jptr, jptr.size(), "pattern");
-    if (!err) err = dalloc(&c->d_jlist, jlist.size(), "pattern");
-    if (!err) err = dalloc(&c->d_jent, jlist.size(), "pattern");
-    if (!err) err = dalloc(&c->d_jn, jlist.size(), "pattern");
+    err = palloc(c, &c->d_jptr, jptr.size(), "pattern");
+    if (!err) err = palloc(c, &c->d_jlist, jlist.size(), "pattern");
+    if (!err) err = palloc(c, &c->d_jent, jlist.size(), "pattern");
+    if (!err) err = palloc(c, &c->d_jn, jlist.size(), "pattern");
     if (!err)
       err = ck(cudaMemcpy(c->d_jptr, jptr.data(), sizeof(int) * jptr.size(), cudaMemcpyHostToDevice),
                "up");
@@ -697,13 +713,13 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
                           cudaMemcpyHostToDevice),
                "up");
   }
-  if (!err) err = dalloc(&c->d_counter, 1, "counter");
+  if (!err) err = palloc(c, &c->d_counter, 1, "counter");
   if (!err) err = ck(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), c->stream), "memset");
-  if (!err) err = dalloc(&c->d_sbar_part, (size_t)part_blocks * 6, "partials");
-  if (!err) err = dalloc(&c->d_viol_part, (size_t)part_blocks, "partials");
-  if (!err) err = dalloc(&c->d_warm, (size_t)c->Kh * 6, "warm");
-  int* d_hk = nullptr;
-  if (!err) err = dalloc(&d_hk, hk.size(), "pattern");
+  if (!err) err = palloc(c, &c->d_sbar_part, (size_t)part_blocks * 6, "partials");
+  if (!err) err = palloc(c, &c->d_viol_part, (size_t)part_blocks, "partials");
+  if (!err) err = palloc(c, &c->d_warm, (size_t)c->Kh * 6, "warm");
+  if (!err) err = palloc(c, &c->d_hk, hk.size(), "pattern");
+  int* d_hk = c->d_hk;
   if (!err) err = ck(cudaMemcpyAsync(c->d_kx, xs.data(), sizeof(int) * c->Kx, cudaMemcpyHostToDevice, c->stream), "up");
   if (!err) err = ck(cudaMemcpyAsync(c->d_kym, kym.data(), sizeof(int) * c->Ky, cudaMemcpyHostToDevice, c->stream), "up");
   if (!err) err = ck(cudaMemcpyAsync(c->d_kzm, kzm.data(), sizeof(int) * c->Kz, cudaMemcpyHostToDevice, c->stream), "up");
@@ -716,7 +732,6 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err) err = ck(cudaMemsetAsync(c->d_OUT, 0, sizeof(float2) * splits * c->rect, c->stream), "memset");
   if (!err && c->opt.transform == RF_TRANSFORM_FFT) err = fft_autotune(c);
   if (!err) err = ck(cudaStreamSynchronize(c->stream), "pattern setup");
-  if (d_hk) cudaFree(d_hk);
   if (!err) {
     // frequency kinds back to the host copy (zero / null flags)
     err = ck(cudaMemcpy(c->h_hidx.data(), c->d_hidx, sizeof(HIdx) * c->Kh, cudaMemcpyDeviceToHost),
@@ -984,6 +999,7 @@ int rf_destroy(rf_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
   free_pattern(c);
+  release_pattern_buffers(c);
   dfree(c->d_phase);
   dfree(c->d_state);
   dfree(c->d_twx);

@@ -17,6 +17,7 @@
 
 #include <cstdint>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/rf.h"
@@ -213,6 +214,9 @@ struct rf_ctx {
   unsigned char* d_phiI = nullptr;
   unsigned char* d_phiF = nullptr;
   TcAxis tc_yf, tc_yi, tc_zf, tc_zi;   // forward / inverse along y and z
+  // capacities of the pattern-scoped device buffers (kept across patterns, see palloc)
+  std::unordered_map<const void*, size_t> pcap;
+  int* d_hk = nullptr;                 // pattern upload staging
   float* d_Tout = nullptr;        // [nXS][rows][NC][2 Kx] partial forward sums per x slice
   int* d_tc_err = nullptr;
   int tc_nXS = 0, tc_nJT = 0, tc_nJC = 0, tc_nXC = 0, tc_R = 0, tc_Qp = 0;
@@ -345,6 +349,25 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 // kernels.cu
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
+
+// Pattern-scoped device buffers live as long as their context and grow when a new pattern
+// needs more room: cudaFree synchronises the device, so re-allocating a dozen buffers for every
+// rf_set_pattern costs milliseconds. Buffers are released in rf_destroy.
+template <class T>
+inline int palloc(rf_ctx* c, T** p, size_t n, const char* what) {
+  if (n == 0) n = 1;
+  const size_t bytes = n * sizeof(T);
+  auto it = c->pcap.find(p);
+  if (*p && it != c->pcap.end() && it->second >= bytes) return RF_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+    c->pcap.erase(p);
+    return cuda_fail(cudaGetLastError(), what);
+  }
+  c->pcap[p] = bytes;
+  return RF_OK;
+}
 int launch_iteration(rf_ctx* c);
 int launch_inverse(rf_ctx* c);
 int launch_final(rf_ctx* c, int commit);

@@ -583,12 +583,15 @@ int tc_setup(rf_ctx* c) {
   c->tc_cols = cols;
   const size_t tile_pairs_I = (size_t)c->tc_nXS * c->tc_nJC;
   const size_t tile_pairs_F = (size_t)c->tc_nJT * c->tc_nXS * c->tc_nXC;
-  cudaError_t e = cudaMalloc(&c->d_phiI, tile_pairs_I * 2 * kTileBytes);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_phiF, tile_pairs_F * 2 * kTileBytes);
-  if (e == cudaSuccess)
-    e = cudaMalloc(&c->d_Tout, sizeof(float) * (size_t)c->tc_nXS * c->rows * c->nc * 2 * c->Kx);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_tc_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream);
+  if (int er = palloc(c, &c->d_phiI, tile_pairs_I * 2 * kTileBytes, "split precision buffers"))
+    return er;
+  if (int er = palloc(c, &c->d_phiF, tile_pairs_F * 2 * kTileBytes, "split precision buffers"))
+    return er;
+  if (int er = palloc(c, &c->d_Tout, (size_t)c->tc_nXS * c->rows * c->nc * 2 * c->Kx,
+                      "split precision buffers"))
+    return er;
+  if (int er = palloc(c, &c->d_tc_err, 1, "split precision buffers")) return er;
+  cudaError_t e = cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "split precision buffers");
   if (bf)
     k_phi_tiles<EBf16><<<608, 256, 0, c->stream>>>(c->d_kx, c->Kx, c->nx, c->d_twx, c->tc_nXS,
@@ -622,8 +625,8 @@ int tc_setup(rf_ctx* c) {
     ax.K = sp.K;
     ax.nMT = (sp.M + 63) / 64;
     ax.nKC = (2 * sp.K + per - 1) / per;
-    e = cudaMalloc(&ax.A, (size_t)ax.nMT * ax.nKC * 2 * kTileBytes);
-    if (e != cudaSuccess) return cuda_fail(e, "axis tiles");
+    if (int er = palloc(c, &ax.A, (size_t)ax.nMT * ax.nKC * 2 * kTileBytes, "axis tiles"))
+      return er;
     if (bf)
       k_axis_tiles<EBf16><<<304, 256, 0, c->stream>>>(sp.M, sp.K, sp.mvals, sp.kvals, sp.tab,
                                                       sp.L, sp.sign, ax.nMT, ax.nKC, ax.A);
