@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16", "split_tf32"])
     p.add_argument("--fft-rows", type=int, default=0,
                    help="c2 FFT mode: rows per row-kernel block (0: autotuned)")
+    p.add_argument("--fft-row-blocks", type=int, default=0,
+                   help="c2 FFT mode: row-kernel blocks with the rows spread evenly (0: autotuned)")
     p.add_argument("--fft-cols", type=int, default=0,
                    help="c2 FFT mode: columns per column-kernel block (0: autotuned)")
     p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2],
@@ -543,7 +545,8 @@ def main():
     pattern = rf.rf_pattern_adapted(pm, 1, K, stream=sh)
     tiles = {}
     if args.transform == "fft":
-        tiles = dict(fft_rows=args.fft_rows, fft_cols=args.fft_cols, fft_fuse=args.fft_fuse)
+        tiles = dict(fft_rows=args.fft_rows, fft_cols=args.fft_cols, fft_fuse=args.fft_fuse,
+                     fft_row_blocks=args.fft_row_blocks)
     if args.profile_updates > 0:
         s = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=0.0,
                       max_iter=args.profile_updates, transform=args.transform,
