@@ -41,6 +41,7 @@ struct BDesc {
   long long off_part;    // double, chunks
   long long off_spart;   // double, row_items * 6
   int tab_x, tab_y;      // offsets into the twiddle buffer
+  FastDiv dKx, dnx;      // division by Kx and Nx
   int fft;               // row items use FFTs along x (Nx = 2^b or 3 2^b), else the pruned DFT
   int fft_y, cy;         // y transforms by FFT over groups of cy line columns (Ny = 2^b, 3 2^b)
   long long zero_base;   // ER offset (within the RVE) of the zero frequency
@@ -238,58 +239,89 @@ __device__ void row_item_fft(const BArgs& a, int2 w, const BDesc& d, unsigned ch
   for (int i = tid; i < Kx; i += blockDim.x) kxs[i] = a.kx[d.off_kx + i];
   for (int i = tid; i < span; i += blockDim.x) b0[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  // z_p = line 2p + i line 2p+1: z[k] = ta + i tb, z[L - k] = conj(ta) + i conj(tb)
+  // z_p = line 2p + i line 2p+1: z[k] = ta + i tb, z[L - k] = conj(ta) + i conj(tb); the
+  // coefficients are loaded four (p, j) at a time before they are scattered
   const float2* Tg = a.T1 + d.off_t1 + (long long)row0 * NC * Kx;
-  for (int u = tid; u < P * Kx; u += blockDim.x) {
-    const int p = u / Kx, j = u - p * Kx;
-    const int s0 = 2 * p, s1 = s0 + 1;
-    float2 ta = Tg[(long long)s0 * Kx + j];   // line s = r NC + c is row r, component c
-    float2 tb = s1 < S ? Tg[(long long)s1 * Kx + j] : make_float2(0.f, 0.f);
-    const int k = kxs[j];
-    const bool self = (k == 0) || (2 * k == L);
-    if (self) {
-      ta.y = 0.f;
-      tb.y = 0.f;
+  for (int u0 = tid; u0 < P * Kx; u0 += 4 * blockDim.x) {
+    float2 ta[4], tb[4];
+    int jj[4], pp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int u = u0 + q * blockDim.x;
+      pp[q] = -1;
+      if (u < P * Kx) {
+        const int p = fdiv(u, d.dKx), j = u - p * Kx;
+        const int s0 = 2 * p, s1 = s0 + 1;
+        ta[q] = Tg[(long long)s0 * Kx + j];   // line s = r NC + c is row r, component c
+        tb[q] = s1 < S ? Tg[(long long)s1 * Kx + j] : make_float2(0.f, 0.f);
+        pp[q] = p;
+        jj[q] = j;
+      }
     }
-    b0[sw(p * L + k)] = make_float2(ta.x - tb.y, ta.y + tb.x);
-    if (!self) b0[sw(p * L + L - k)] = make_float2(ta.x + tb.y, tb.x - ta.y);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (pp[q] < 0) continue;
+      const int k = kxs[jj[q]];
+      const bool self = (k == 0) || (2 * k == L);
+      if (self) {
+        ta[q].y = 0.f;
+        tb[q].y = 0.f;
+      }
+      b0[sw(pp[q] * L + k)] = make_float2(ta[q].x - tb[q].y, ta[q].y + tb[q].x);
+      if (!self) b0[sw(pp[q] * L + L - k)] = make_float2(ta[q].x + tb[q].y, tb[q].x - ta[q].y);
+    }
   }
   __syncthreads();
   float2* zb = fft_block(b0, b1, tw, L, P, +1);
   float2* other = (zb == b0) ? b1 : b0;
   const float invN = 1.f / (float)d.N;
   double sb[6] = {0, 0, 0, 0, 0, 0};
-  for (int v = tid; v < nr * L; v += blockDim.x) {
-    const int r = v / L, x = v - r * L;
-    float e[NC];
+  // phase ids four voxels at a time, loaded before the law runs on them
+  for (int v0 = tid; v0 < nr * L; v0 += 4 * blockDim.x) {
+    uint8_t pid[4];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int sl = r * NC + c;
-      const float2 z = zb[sw((sl >> 1) * L + x)];
-      e[c] = ((sl & 1) ? z.y : z.x) * invN;
+    for (int q = 0; q < 4; ++q) {
+      const int v = v0 + q * blockDim.x;
+      pid[q] = 0;
+      if (v < nr * L) {
+        const int r = fdiv(v, d.dnx), x = v - r * L;
+        pid[q] = a.phase[d.off_phase + (long long)(row0 + r) * L + x];
+      }
     }
-    float e6[6];
-    comp_to6<NC>(e, e6);
-    const long long g = (long long)(row0 + r) * L + x;
-    const DevPhase ph = a.law.ph[a.phase[d.off_phase + g]];
-    float ep[6] = {0, 0, 0, 0, 0, 0};
-    LawOut o;
-    stress6<false>(e6, ph, ep, 0.f, o);
-    if (a.final_pass) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
-    } else {
-      const float tr = e6[0] + e6[1] + e6[2];
-      float tau6[6];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (d.lam0 * tr + 2.f * d.mu0 * e6[i]);
-#pragma unroll
-      for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * d.mu0 * e6[i];
+    for (int q = 0; q < 4; ++q) {
+      const int v = v0 + q * blockDim.x;
+      if (v >= nr * L) continue;
+      const int r = fdiv(v, d.dnx), x = v - r * L;
+      float e[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int sl = r * NC + c;
-        float* dst = reinterpret_cast<float*>(other + sw((sl >> 1) * L + x));
-        dst[sl & 1] = tau6[comp6<NC>(c)];
+        const float2 z = zb[sw((sl >> 1) * L + x)];
+        e[c] = ((sl & 1) ? z.y : z.x) * invN;
+      }
+      float e6[6];
+      comp_to6<NC>(e, e6);
+      const DevPhase ph = a.law.ph[pid[q]];
+      float ep[6] = {0, 0, 0, 0, 0, 0};
+      LawOut o;
+      stress6<false>(e6, ph, ep, 0.f, o);
+      if (a.final_pass) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
+      } else {
+        const float tr = e6[0] + e6[1] + e6[2];
+        float tau6[6];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (d.lam0 * tr + 2.f * d.mu0 * e6[i]);
+#pragma unroll
+        for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * d.mu0 * e6[i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int sl = r * NC + c;
+          float* dst = reinterpret_cast<float*>(other + sw((sl >> 1) * L + x));
+          dst[sl & 1] = tau6[comp6<NC>(c)];
+        }
       }
     }
   }
@@ -306,7 +338,7 @@ __device__ void row_item_fft(const BArgs& a, int2 w, const BDesc& d, unsigned ch
   float2* zf = fft_block(other, zb, tw, L, P, -1);
   float2* To = a.T1p + d.off_t1 + (long long)row0 * NC * Kx;
   for (int u = tid; u < S * Kx; u += blockDim.x) {
-    const int sl = u / Kx, j = u - sl * Kx;
+    const int sl = fdiv(u, d.dKx), j = u - sl * Kx;
     const int k = kxs[j];
     const int base = (sl >> 1) * L;
     const float2 zk = zf[sw(base + k)], zm = zf[sw(base + (k == 0 ? 0 : L - k))];
@@ -1258,6 +1290,8 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   for (auto& d : b->desc) {
     d.tab_x = tab_off[d.nx];
     d.tab_y = tab_off[d.ny];
+    d.dKx = make_fastdiv((unsigned)std::max(1, d.Kx));
+    d.dnx = make_fastdiv((unsigned)d.nx);
   }
   int err = RF_OK;
   int* d_hk = nullptr;
