@@ -616,7 +616,7 @@ __global__ void kb_init(BArgs a, int n_rve, const float2* warm, const long long*
 // separable sums: the x transform of a chunk of rows for every kx in [0, nx/2], then the y sum
 // per entry, accumulated in the slot table. Then the 48 descriptors from the slots, with
 // per-value sums in a fixed order (radial bins decided in FP64 without contraction).
-constexpr int kFeatRows = 8;
+constexpr int kFeatRows = 32;
 constexpr int kDescChunk = 512;
 
 __device__ __forceinline__ int radial_bin(int kx, int ky, int nx, int ny) {
@@ -626,21 +626,41 @@ __device__ __forceinline__ int radial_bin(int kx, int ky, int nx, int ny) {
   return f >= 23.0 ? 23 : (int)f;
 }
 
+__host__ __device__ inline bool desc_fft(int n) {
+  const int p2 = (n % 3 == 0) ? n / 3 : n;
+  return n >= 2 && (p2 & (p2 - 1)) == 0;
+}
+
 __global__ void kb_descriptors(BArgs a, int incl, int rve_base, float* X, rf_slot* slots) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int r = blockIdx.x;
   const BDesc d = a.d[r];
-  const int nx = d.nx, ny = d.ny, hx = nx / 2 + 1;
-  float2* R = reinterpret_cast<float2*>(fsm);                      // [kFeatRows][hx]
-  float* gch = reinterpret_cast<float*>(R + kFeatRows * hx);       // [kFeatRows][nx]
+  const int nx = d.nx, ny = d.ny, Kx = d.Kx;
+  // gamma at the half pattern: DFT of the indicator along x at the pattern's kx values for a
+  // chunk of rows, then along y at each entry's ky; accumulators stay in shared memory
+  // FFT rows for sides 2^b and 3 2^b: twiddles [stage_len(nx)], two packed-row buffers of
+  // kFeatRows / 2 sequences; otherwise the indicator rows [kFeatRows][nx] for the DFT
+  const bool fft = desc_fft(nx);
+  const int spanf = fftc::span_of((kFeatRows / 2) * nx);
+  float2* R = reinterpret_cast<float2*>(fsm);                 // [kFeatRows][Kx]
+  float* accr = reinterpret_cast<float*>(R + kFeatRows * Kx);  // [Kh]
+  float* acci = accr + d.Kh;                                   // [Kh]
+  unsigned char* work = reinterpret_cast<unsigned char*>(acci + d.Kh);
+  work += (16 - (reinterpret_cast<uintptr_t>(work) & 15)) & 15;
+  float* gch = reinterpret_cast<float*>(work);                 // DFT rows
+  float2* tw = reinterpret_cast<float2*>(work);                // FFT rows
+  float2* f0 = tw + fftc::stage_len(nx);
+  float2* f1 = f0 + spanf;
+  if (fft) fftc::copy_twiddles(a.tab + d.tab_x, nx, tw);
   const float2* twx = a.tab + d.tab_x;
   const float2* twy = a.tab + d.tab_y;
   const uint8_t* pm = a.phase + d.off_phase;
+  const int* kxl = a.kx + d.off_kx;
   rf_slot* sl = slots + d.off_h;
   const float invN = 1.f / (float)d.N;
   for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
     const HIdx hi = a.hidx[d.off_h + h];
-    const int kx = a.kx[d.off_kx + hi.j];
+    const int kx = kxl[hi.j];
     const int kym = a.kym[d.off_ky + hi.iy];
     const int ky = kym <= ny / 2 ? kym : kym - ny;
     rf_slot t;
@@ -653,37 +673,60 @@ __global__ void kb_descriptors(BArgs a, int incl, int rve_base, float* X, rf_slo
     t.rve = rve_base + r;
     t.kind = hi.kind;
     sl[h] = t;
+    accr[h] = 0.f;
+    acci[h] = 0.f;
   }
   for (int y0 = 0; y0 < ny; y0 += kFeatRows) {
     const int nr = min(kFeatRows, ny - y0);
     __syncthreads();
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x)
-      gch[i] = pm[(long long)y0 * nx + i] == incl ? 1.f : 0.f;
-    __syncthreads();
-    for (int i = threadIdx.x; i < nr * hx; i += blockDim.x) {
-      const int yy = i / hx, kx = i % hx;
-      const float* gr = gch + yy * nx;
-      float re = 0.f, im = 0.f;
-      int m = 0;
-      for (int x = 0; x < nx; ++x) {
-        const float gv = gr[x];
-        const float2 w = twx[m];   // (cos, sin)(2 pi m / nx)
-        re = fmaf(gv, w.x, re);
-        im = fmaf(-gv, w.y, im);
-        m += kx;
-        if (m >= nx) m -= nx;
+    if (fft) {
+      // rows 2p and 2p + 1 as the real and imaginary carriers of sequence p
+      const int P = (nr + 1) / 2;
+      for (int i = threadIdx.x; i < P * nx; i += blockDim.x) {
+        const int p = i / nx, x = i - p * nx;
+        const int ya = 2 * p, yb = ya + 1;
+        const float ga = pm[(long long)(y0 + ya) * nx + x] == incl ? 1.f : 0.f;
+        const float gb = yb < nr && pm[(long long)(y0 + yb) * nx + x] == incl ? 1.f : 0.f;
+        f0[fftc::sw(i)] = make_float2(ga, gb);
       }
-      R[yy * hx + kx] = make_float2(re, im);
+      __syncthreads();
+      const float2* z = fftc::fft_block(f0, f1, tw, nx, P, -1);
+      for (int i = threadIdx.x; i < nr * Kx; i += blockDim.x) {
+        const int yy = i / Kx, j = i - yy * Kx;
+        const int k = kxl[j], base = (yy >> 1) * nx;
+        const float2 zk = z[fftc::sw(base + k)], zm = z[fftc::sw(base + (k == 0 ? 0 : nx - k))];
+        R[yy * Kx + j] = (yy & 1) == 0 ? make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y))
+                                       : make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      }
+    } else {
+      for (int i = threadIdx.x; i < nr * nx; i += blockDim.x)
+        gch[i] = pm[(long long)y0 * nx + i] == incl ? 1.f : 0.f;
+      __syncthreads();
+      for (int i = threadIdx.x; i < nr * Kx; i += blockDim.x) {
+        const int yy = i / Kx, j = i - yy * Kx;
+        const int kx = kxl[j];
+        const float* gr = gch + yy * nx;
+        float re = 0.f, im = 0.f;
+        int m = 0;
+        for (int x = 0; x < nx; ++x) {
+          const float gv = gr[x];
+          const float2 w = twx[m];   // (cos, sin)(2 pi m / nx)
+          re = fmaf(gv, w.x, re);
+          im = fmaf(-gv, w.y, im);
+          m += kx;
+          if (m >= nx) m -= nx;
+        }
+        R[yy * Kx + j] = make_float2(re, im);
+      }
     }
     __syncthreads();
     for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
       const HIdx hi = a.hidx[d.off_h + h];
-      const int kx = a.kx[d.off_kx + hi.j];
       const int kym = a.kym[d.off_ky + hi.iy];
-      float gr = sl[h].g_re, gi = sl[h].g_im;
+      float gr = accr[h], gi = acci[h];
       int m = (int)(((long long)kym * y0) % ny);
       for (int yy = 0; yy < nr; ++yy) {
-        const float2 v = R[yy * hx + kx];
+        const float2 v = R[yy * Kx + hi.j];
         const float2 w = twy[m];
         // (v.x + i v.y) (cos - i sin)
         gr = fmaf(v.x, w.x, fmaf(v.y, w.y, gr));
@@ -691,14 +734,14 @@ __global__ void kb_descriptors(BArgs a, int incl, int rve_base, float* X, rf_slo
         m += kym;
         if (m >= ny) m -= ny;
       }
-      sl[h].g_re = gr;
-      sl[h].g_im = gi;
+      accr[h] = gr;
+      acci[h] = gi;
     }
   }
   __syncthreads();
   for (int h = threadIdx.x; h < d.Kh; h += blockDim.x) {
-    sl[h].g_re *= invN;
-    sl[h].g_im *= invN;
+    sl[h].g_re = accr[h] * invN;
+    sl[h].g_im = acci[h] * invN;
   }
   __syncthreads();
   // descriptors: 24 bin sums and 4 x 4 band anisotropy sums over the nonzero frequencies
@@ -1469,8 +1512,15 @@ int rf_batch_descriptors(rf_batch* b, int32_t inclusion_phase, int32_t rve_base,
     set_error("rf_batch_descriptors: invalid argument");
     return RF_ERR_INVALID;
   }
-  const size_t smem_dft = sizeof(float2) * (size_t)kFeatRows * (b->max_nx / 2 + 1) +
-                          sizeof(float) * (size_t)kFeatRows * b->max_nx;
+  size_t smem_dft = 0;
+  for (const BDesc& d : b->desc) {
+    const size_t rows = desc_fft(d.nx) ? ((size_t)fftc::stage_len(d.nx) +
+                                 2 * (size_t)fftc::span_of((kFeatRows / 2) * d.nx)) *
+                                    sizeof(float2)
+                              : sizeof(float) * (size_t)kFeatRows * d.nx;
+    smem_dft = std::max(smem_dft, sizeof(float2) * (size_t)kFeatRows * d.Kx +
+                                      sizeof(float) * 2 * (size_t)d.Kh + 16 + rows);
+  }
   const size_t smem_desc = (5 * sizeof(float) + sizeof(int)) * (size_t)kDescChunk;
   const size_t smem = std::max(smem_dft, smem_desc);
   cudaFuncSetAttribute(kb_descriptors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
