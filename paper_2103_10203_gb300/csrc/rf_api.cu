@@ -544,40 +544,68 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   const int n[3] = {c->nx, c->ny, c->nz};
   // signed range (-N/2, N/2]: -(N-1)/2 <= k <= N/2 with integer division
   auto in_range = [](int k, int nn) { return k >= -((nn - 1) / 2) && k <= nn / 2; };
-  // frequencies as unique linear keys (offset signed indices), sorted once: duplicate,
-  // conjugate and position lookups are binary searches
+  // frequencies as unique linear keys (offset signed indices); duplicate, conjugate and
+  // position lookups go through a dense index over the key space for grids up to 4 Mi voxels,
+  // else through one sorted key vector and binary searches
   auto key = [&](int kx, int ky, int kz) {
     return ((long long)(kz + (n[2] - 1) / 2) * n[1] + (ky + (n[1] - 1) / 2)) * n[0] +
            (kx + (n[0] - 1) / 2);
   };
-  std::vector<long long> keys(K);
+  const bool dense = c->N <= (4LL << 20);
+  std::vector<int32_t> at;      // dense: pattern index of each key, -1 if absent
+  std::vector<long long> keys;  // sparse: sorted keys
+  if (dense) at.assign((size_t)c->N, -1);
+  else keys.resize(K);
   int zeros = 0;
   for (long long p = 0; p < K; ++p) {
     const int kx = freqs[3 * p], ky = freqs[3 * p + 1], kz = freqs[3 * p + 2];
     if (!in_range(kx, n[0]) || !in_range(ky, n[1]) || !in_range(kz, n[2]))
       return invalid("rf_set_pattern: frequency outside the signed range (-N/2, N/2]");
     if (kx == 0 && ky == 0 && kz == 0) ++zeros;
-    keys[p] = key(kx, ky, kz);
+    const long long k = key(kx, ky, kz);
+    if (dense) {
+      if (at[k] >= 0) return invalid("rf_set_pattern: duplicate frequency");
+      at[k] = (int32_t)p;
+    } else {
+      keys[p] = k;
+    }
   }
-  std::sort(keys.begin(), keys.end());
-  if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
-    return invalid("rf_set_pattern: duplicate frequency");
+  if (!dense) {
+    std::sort(keys.begin(), keys.end());
+    if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
+      return invalid("rf_set_pattern: duplicate frequency");
+  }
   if (zeros != 1) return invalid("rf_set_pattern: the zero frequency must be present");
   auto conj = [&](int kx, int ky, int kz) {
     return std::make_tuple(signed_of(wrapi(-kx, n[0]), n[0]), signed_of(wrapi(-ky, n[1]), n[1]),
                            signed_of(wrapi(-kz, n[2]), n[2]));
   };
+  auto present = [&](long long k) {
+    return dense ? at[k] >= 0 : std::binary_search(keys.begin(), keys.end(), k);
+  };
   for (long long p = 0; p < K; ++p) {
     auto [cx, cy, cz] = conj(freqs[3 * p], freqs[3 * p + 1], freqs[3 * p + 2]);
-    if (!std::binary_search(keys.begin(), keys.end(), key(cx, cy, cz)))
+    if (!present(key(cx, cy, cz)))
       return invalid("rf_set_pattern: pattern is not closed under k -> -k");
   }
-  // half set: kx >= 0, sorted by (kx, ky, kz)
-  std::vector<std::tuple<int, int, int>> H;
-  H.reserve(K / 2 + 2);
+  // half set: kx >= 0, sorted by (kx, ky, kz) through packed keys
+  auto hkey = [&](int kx, int ky, int kz) {
+    return ((long long)kx * n[1] + (ky + (n[1] - 1) / 2)) * n[2] + (kz + (n[2] - 1) / 2);
+  };
+  std::vector<long long> hk_sorted;
+  hk_sorted.reserve(K / 2 + 2);
   for (long long p = 0; p < K; ++p)
-    if (freqs[3 * p] >= 0) H.emplace_back(freqs[3 * p], freqs[3 * p + 1], freqs[3 * p + 2]);
-  std::sort(H.begin(), H.end());
+    if (freqs[3 * p] >= 0) hk_sorted.push_back(hkey(freqs[3 * p], freqs[3 * p + 1], freqs[3 * p + 2]));
+  std::sort(hk_sorted.begin(), hk_sorted.end());
+  std::vector<std::tuple<int, int, int>> H(hk_sorted.size());
+  for (size_t h = 0; h < hk_sorted.size(); ++h) {
+    const long long v = hk_sorted[h];
+    const int kz = (int)(v % n[2]) - (n[2] - 1) / 2;
+    const long long r = v / n[2];
+    const int ky = (int)(r % n[1]) - (n[1] - 1) / 2;
+    const int kx = (int)(r / n[1]);
+    H[h] = std::make_tuple(kx, ky, kz);
+  }
   std::vector<int> xs, ys, zs;
   for (auto& t : H) {
     xs.push_back(std::get<0>(t));
@@ -598,8 +626,17 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   c->Ky = (int)ys.size();
   c->Kz = (int)zs.size();
   c->pat.assign(freqs, freqs + 3 * K);
+  // half-set position of each frequency: the dense index now holds h, else a binary search
+  if (dense)
+    for (long long h = 0; h < c->Kh; ++h) {
+      auto [kx, ky, kz] = H[h];
+      at[key(kx, ky, kz)] = (int32_t)h;
+    }
   auto hpos = [&](const std::tuple<int, int, int>& t) {
-    return (long long)(std::lower_bound(H.begin(), H.end(), t) - H.begin());
+    auto [kx, ky, kz] = t;
+    if (dense) return (long long)at[key(kx, ky, kz)];
+    return (long long)(std::lower_bound(hk_sorted.begin(), hk_sorted.end(), hkey(kx, ky, kz)) -
+                       hk_sorted.begin());
   };
   c->map_h.assign(K, 0);
   c->map_conj.assign(K, 0);
