@@ -292,6 +292,34 @@ __global__ void k_count_le(const unsigned long long* key, const int* lin, const 
   if (threadIdx.x == 0 && sh[0]) atomicAdd(out, sh[0]);
 }
 
+// Weighted histogram for the radix search of the threshold: entries with a valid key and
+// (phase 0) key - base in [0, 256 << shift), or (phase 1) key == vhi and lin - base in
+// [0, 256 << shift), add their pair size to bucket ((value - base) >> shift).
+__global__ void k_key_hist(const unsigned long long* key, const int* lin, const int* size,
+                           long long N, int phase, unsigned long long vhi,
+                           unsigned long long base, int shift, unsigned long long* hist) {
+  __shared__ unsigned long long sh[256];
+  sh[threadIdx.x] = 0;
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long k = key[i];
+    if (k == ~0ull) continue;
+    unsigned long long v;
+    if (phase == 0) {
+      v = k;
+    } else {
+      if (k != vhi) continue;
+      v = (unsigned long long)(unsigned)lin[i];
+    }
+    if (v < base) continue;
+    const unsigned long long b = (v - base) >> shift;
+    if (b < 256) atomicAdd(&sh[b], (unsigned long long)size[i]);
+  }
+  __syncthreads();
+  if (sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
+}
+
 // flags in signed-linear order
 __global__ void k_flags(const unsigned long long* key, const int* lin, Grid3 g,
                         unsigned long long thi, int tlin, int* flags) {
@@ -471,25 +499,38 @@ int select_and_compact(const Grid3& g, unsigned long long* key, int* lin, int* s
     set_error("pattern: k_target exceeds the number of frequencies");
     return RF_ERR_INVALID;
   }
-  // smallest key_hi with count >= k_target
-  unsigned long long lo = 0, hi = (1ull << 63);
-  while (lo < hi) {
-    unsigned long long mid = lo + (hi - lo) / 2;
-    unsigned long long c = 0;
-    if (int e = count(mid, INT_MAX, c)) return e;
-    if ((long long)c >= k_target) hi = mid;
-    else lo = mid + 1;
-  }
-  const unsigned long long thi = lo;
-  long long llo = 0, lhi = g.N;
-  while (llo < lhi) {
-    long long mid = llo + (lhi - llo) / 2;
-    unsigned long long c = 0;
-    if (int e = count(thi, (int)mid, c)) return e;
-    if ((long long)c >= k_target) lhi = mid;
-    else llo = mid + 1;
-  }
-  const int tlin = (int)llo;
+  // The threshold is the smallest (key, lin) in the total order whose count of entries at or
+  // below it reaches k_target. Radix passes of 8 bits from the top, each one weighted
+  // histogram (one host read): first over the key, then over lin among entries with that key.
+  unsigned long long* d_hist = sc.get<unsigned long long>(256);
+  unsigned long long* h_hist = nullptr;
+  if (!d_hist) return RF_ERR_OOM;
+  if (int e = check(cudaMallocHost(&h_hist, 256 * sizeof(unsigned long long)), "pinned")) return e;
+  PinFree pf2{h_hist};
+  unsigned long long below = 0;   // weighted count of entries strictly below the current base
+  auto radix = [&](int phase, unsigned long long vhi, int top_shift,
+                   unsigned long long& base) -> int {
+    base = 0;
+    for (int shift = top_shift; shift >= 0; shift -= 8) {
+      if (int e = check(cudaMemsetAsync(d_hist, 0, 256 * sizeof(unsigned long long), s), "memset"))
+        return e;
+      k_key_hist<<<304, 256, 0, s>>>(key, lin, size, g.N, phase, vhi, base, shift, d_hist);
+      if (int e = check(cudaGetLastError(), "key histogram")) return e;
+      if (int e = check(cudaMemcpyAsync(h_hist, d_hist, 256 * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, s), "copy histogram"))
+        return e;
+      if (int e = check(cudaStreamSynchronize(s), "sync histogram")) return e;
+      int b = 0;
+      while (b < 255 && (long long)(below + h_hist[b]) < k_target) below += h_hist[b++];
+      base += (unsigned long long)b << shift;
+    }
+    return RF_OK;
+  };
+  unsigned long long thi = 0, tl = 0;
+  if (int e = radix(0, 0, 56, thi)) return e;
+  // `below` now counts the entries with key < thi
+  if (int e = radix(1, thi, 24, tl)) return e;
+  const int tlin = (int)tl;
   unsigned long long K = 0;
   if (int e = count(thi, tlin, K)) return e;
   *K_out = (long long)K;
