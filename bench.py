@@ -84,6 +84,19 @@ def dist_info():
     return ws, rank, local
 
 
+def combine_ranks(dist, total_ms, units, device):
+    """Whole-job timing of independent replicas: the slowest rank's timed total and the units
+    all ranks processed (dist None: one process)."""
+    if dist is None:
+        return float(total_ms), float(units)
+    import torch
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(v)
+    return float(t.item()), float(v.item())
+
+
 def workload():
     from synth import make_config
     from synth.configs import k_target
@@ -604,16 +617,7 @@ def main():
         torch.cuda.synchronize()
         solver.rf_set_tracing(False)
     stage = solver.rf_get_stage_times()
-    total_ms = float(np.sum(ms_steps))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        v = torch.tensor([float(iters)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(v)
-        all_iters = float(v.item())
-    else:
-        all_iters = float(iters)
+    total_ms, all_iters = combine_ranks(dist, float(np.sum(ms_steps)), iters, "cuda")
     value = all_iters * pm.size / (total_ms / 1000.0)
     solves = ws * args.steps / (total_ms / 1000.0)
 
