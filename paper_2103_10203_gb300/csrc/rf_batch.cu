@@ -472,31 +472,7 @@ __global__ __launch_bounds__(256) void kb_gamma(BArgs a) {
         old[c] = erp[c * d.Kx];
       }
       float er[NC], ei[NC];
-      if (hi.kind == 1) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          er[c] = (float)((double)d.N * st.ebar[comp6<NC>(c)]);
-          ei[c] = 0.f;
-        }
-      } else if (hi.kind == 2) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) er[c] = ei[c] = 0.f;
-      } else {
-        float tr[NC], ti[NC], t6[6], o6[6];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          tr[c] = tv[c].x;
-          ti[c] = tv[c].y;
-        }
-        comp_to6<NC>(tr, t6);
-        gamma6(n, t6, d.inv2mu0, d.cgam, o6);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) er[c] = -o6[comp6<NC>(c)];
-        comp_to6<NC>(ti, t6);
-        gamma6(n, t6, d.inv2mu0, d.cgam, o6);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
-      }
+      green_update<NC>(hi.kind, n, tv, st.ebar, (double)d.N, d.inv2mu0, d.cgam, er, ei);
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const float dr = er[c] - old[c].x, di = ei[c] - old[c].y;

@@ -414,34 +414,11 @@ __global__ __launch_bounds__(256) void k_fft_colphase(ColPhaseArgs a, double Nd)
     const float4 n = a.hn[h];
     const int jj = hi.j - j0, pos = a.kym[hi.iy];
     const long long base = ((long long)hi.iy * NC) * a.Kx + hi.j;
+    float2 tv[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) tv[c] = z[sw((jj * NC + c) * L + pos)];
     float er[NC], ei[NC];
-    if (hi.kind == 1) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        er[c] = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
-        ei[c] = 0.f;
-      }
-    } else if (hi.kind == 2) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) er[c] = ei[c] = 0.f;
-    } else {
-      float tr[NC], ti[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float2 t = z[sw((jj * NC + c) * L + pos)];
-        tr[c] = t.x;
-        ti[c] = t.y;
-      }
-      float t6[6], o6[6];
-      comp_to6<NC>(tr, t6);
-      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) er[c] = -o6[comp6<NC>(c)];
-      comp_to6<NC>(ti, t6);
-      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
-    }
+    green_update<NC>(hi.kind, n, tv, a.st->ebar, Nd, a.inv2mu0, a.cgam, er, ei);
     float d = 0.f;   // one frequency's squared increment (at most six non-negative terms)
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -578,33 +555,14 @@ __global__ __launch_bounds__(256) void k_fft_green_inv(GreenInvArgs a, double Nd
   for (int u = 0; u < kE; ++u) {
     if (ecc[u] < 0) continue;
     const int c = cc_[ecc[u]];
-    float er, ei;
-    if (ekind[u] == 1) {
-      er = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
-      ei = 0.f;
-    } else if (ekind[u] == 2) {
-      er = ei = 0.f;
-    } else {
-      float tr[NC], ti[NC];
+    float erc[NC], eic[NC], er = 0.f, ei = 0.f;
+    green_update<NC>(ekind[u], en[u], tv[u], a.st->ebar, Nd, a.inv2mu0, a.cgam, erc, eic);
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        tr[q] = tv[u][q].x;
-        ti[q] = tv[u][q].y;
+    for (int q = 0; q < NC; ++q)   // keep this block's component (no dynamic register index)
+      if (q == c) {
+        er = erc[q];
+        ei = eic[q];
       }
-      float t6[6], o6[6], o6i[6];
-      comp_to6<NC>(tr, t6);
-      gamma6(en[u], t6, a.inv2mu0, a.cgam, o6);
-      comp_to6<NC>(ti, t6);
-      gamma6(en[u], t6, a.inv2mu0, a.cgam, o6i);
-      er = 0.f;
-      ei = 0.f;
-#pragma unroll
-      for (int q = 0; q < NC; ++q)
-        if (q == c) {
-          er = -o6[comp6<NC>(q)];
-          ei = -o6i[comp6<NC>(q)];
-        }
-    }
     const float dr = er - old[u].x, di = ei - old[u].y;
     const int c6 = NC == 3 ? (c == 2 ? 5 : c) : c;
     const float wc = c6 >= 3 ? 2.f : 1.f;   // Frobenius: shear counted twice
@@ -622,34 +580,18 @@ __global__ __launch_bounds__(256) void k_fft_green_inv(GreenInvArgs a, double Nd
     const float4 n = a.jn[e];
     const int c = cc_[cc], kx = ckx[cc];
     const long long base = ((long long)en2.x * NC) * a.Kx + kx;
-    float er, ei;
-    if (en2.y == 1) {
-      er = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
-      ei = 0.f;
-    } else if (en2.y == 2) {
-      er = ei = 0.f;
-    } else {
-      float tr[NC], ti[NC];
+    float2 tq[NC];
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const float2 tq = a.OUT[base + (long long)q * a.Kx];
-        tr[q] = tq.x;
-        ti[q] = tq.y;
+    for (int q = 0; q < NC; ++q)
+      tq[q] = en2.y == 0 ? a.OUT[base + (long long)q * a.Kx] : make_float2(0.f, 0.f);
+    float erc[NC], eic[NC], er = 0.f, ei = 0.f;
+    green_update<NC>(en2.y, n, tq, a.st->ebar, Nd, a.inv2mu0, a.cgam, erc, eic);
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      if (q == c) {
+        er = erc[q];
+        ei = eic[q];
       }
-      float t6[6], o6[6], o6i[6];
-      comp_to6<NC>(tr, t6);
-      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
-      comp_to6<NC>(ti, t6);
-      gamma6(n, t6, a.inv2mu0, a.cgam, o6i);
-      er = 0.f;
-      ei = 0.f;
-#pragma unroll
-      for (int q = 0; q < NC; ++q)
-        if (q == c) {
-          er = -o6[comp6<NC>(q)];
-          ei = -o6i[comp6<NC>(q)];
-        }
-    }
     float2* erp = a.ER + base + (long long)c * a.Kx;
     const float2 o = *erp;
     const float dr = er - o.x, di = ei - o.y;

@@ -330,32 +330,7 @@ __global__ __launch_bounds__(kGammaBlock) void k_gamma(GammaArgs a, double Nd) {
       }
     }
     float er[NC], ei[NC];
-    if (hi.kind == 1) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        er[c] = (float)(Nd * a.st->ebar[comp6<NC>(c)]);
-        ei[c] = 0.f;
-      }
-    } else if (hi.kind == 2) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) er[c] = ei[c] = 0.f;
-    } else {
-      float tr[NC], ti[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        tr[c] = tv[c].x;
-        ti[c] = tv[c].y;
-      }
-      float t6[6], o6[6];
-      comp_to6<NC>(tr, t6);
-      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) er[c] = -o6[comp6<NC>(c)];
-      comp_to6<NC>(ti, t6);
-      gamma6(n, t6, a.inv2mu0, a.cgam, o6);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
-    }
+    green_update<NC>(hi.kind, n, tv, a.st->ebar, Nd, a.inv2mu0, a.cgam, er, ei);
     const float mult = n.w;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {

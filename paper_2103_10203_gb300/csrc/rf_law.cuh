@@ -175,4 +175,38 @@ __device__ __forceinline__ void gamma6(const float4& n, const float* t, float in
   o[5] = (n.x * v1 + n.y * v0) * inv2mu0 - cg * n.x * n.y * nvn;
 }
 
+// New strain coefficients at one half-pattern frequency (Sec. 4 step c) from tau^ of its NC
+// components: N ebar at the zero frequency (kind 1), 0 where the operator is null (kind 2),
+// otherwise eps^ = -Gamma0 : tau^ applied to the real and to the imaginary parts.
+template <int NC>
+__device__ __forceinline__ void green_update(int kind, const float4& n, const float2* tv,
+                                             const double* ebar, double Nd, float inv2mu0,
+                                             float cg, float* er, float* ei) {
+  if (kind == 1) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      er[c] = (float)(Nd * ebar[comp6<NC>(c)]);
+      ei[c] = 0.f;
+    }
+  } else if (kind == 2) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) er[c] = ei[c] = 0.f;
+  } else {
+    float tr[NC], ti[NC], t6[6], o6[6];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      tr[c] = tv[c].x;
+      ti[c] = tv[c].y;
+    }
+    comp_to6<NC>(tr, t6);
+    gamma6(n, t6, inv2mu0, cg, o6);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) er[c] = -o6[comp6<NC>(c)];
+    comp_to6<NC>(ti, t6);
+    gamma6(n, t6, inv2mu0, cg, o6);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ei[c] = -o6[comp6<NC>(c)];
+  }
+}
+
 }  // namespace rfk
