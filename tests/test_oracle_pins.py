@@ -263,6 +263,108 @@ def test_homogeneous_j2_path_one_step_per_increment():
         assert np.isclose(sbar[n, 0], s11, rtol=1e-12) and np.isclose(sbar[n, 1], s22, rtol=1e-12)
 
 
+def test_homogeneous_j2_load_unload_reload_closed_form():
+    """Uniaxial strain eps_11 up to 2 %, back to 1.6 %, then on to 2.5 % (Sec. 2: yield
+    function, associative flow, linear isotropic hardening; Sec. 5.2: incremental loading).
+
+    In uniaxial strain the plastic flow keeps the fixed direction diag(1, -1/2, -1/2), so with
+    S = 2 mu e - 3 mu alpha the stresses are s11 = kappa e + 2 S / 3, s22 = s33 = kappa e - S / 3.
+    While loading, S sits on the yield surface (S = sy + H alpha). On unloading alpha stays at
+    its largest value and the response is elastic (|S| < sy + H alpha, checked below). On
+    reloading the yield surface is met again exactly at the largest strain reached so far and
+    the hardening branch continues. So alpha = max(0, (2 mu e_max - sy) / (3 mu + H)) with
+    e_max the largest strain so far. A path solver that did not carry the internal variables
+    from one increment to the next would return to the yield surface on unloading instead."""
+    lam, mu, sy, H = 40.4, 26.9, 0.25, 1.0
+    kappa = lam + 2 * mu / 3
+    strains = [0.005, 0.01, 0.015, 0.02, 0.018, 0.016, 0.018, 0.02, 0.022, 0.025]
+    path = np.zeros((len(strains), 6))
+    path[:, 0] = strains
+    pm = np.zeros((4, 6), np.uint8)
+    ph = phase_table([(lam, mu, sy, H, 1)])
+    sbar, iters, res = O.solve_path(pm, ph, path, np.zeros((1, 3), np.int64), tol=1e-10)
+    assert np.all(iters == 1)
+    emax = 0.0
+    for n, e in enumerate(strains):
+        emax = max(emax, e)
+        alpha = max(0.0, (2 * mu * emax - sy) / (3 * mu + H))
+        S = 2 * mu * e - 3 * mu * alpha
+        assert abs(S) <= sy + H * alpha + 1e-12          # on or inside the yield surface
+        if e < emax:
+            assert abs(S) < sy + H * alpha - 1e-3         # unloading is strictly elastic
+        assert np.isclose(sbar[n, 0], kappa * e + 2 * S / 3, rtol=1e-12, atol=1e-15), n
+        assert np.isclose(sbar[n, 1], kappa * e - S / 3, rtol=1e-12, atol=1e-15), n
+        assert np.isclose(sbar[n, 2], kappa * e - S / 3, rtol=1e-12, atol=1e-15), n
+    assert np.allclose(res.alpha, alpha, rtol=1e-12)
+
+
+def _implicit_j2_point(eps, eps_p, alpha, lam, mu, sy, H):
+    """One backward-Euler increment of the J2 model at a material point, solved as a nonlinear
+    system instead of the closed-form radial return: unknowns sigma (3x3 symmetric, six
+    entries) and the plastic multiplier dg >= 0, equations
+        sigma = C : (eps - eps_p - dg * n(sigma)),  n = 3/2 dev(sigma) / sigma_eq(sigma)
+        sigma_eq(sigma) = sy + H (alpha + dg)
+    (Sec. 2: flow normal to the von Mises surface, consistency on yielding). Elastic when the
+    trial stress lies inside the surface."""
+    from scipy.optimize import fsolve
+
+    C = O.isotropic_stiffness(lam, mu)
+    iu = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+
+    def to_t(v):
+        t = np.zeros((3, 3))
+        for a, (i, j) in enumerate(iu):
+            t[i, j] = t[j, i] = v[a]
+        return t
+
+    def seq_dev(s):
+        d = s - np.trace(s) / 3 * np.eye(3)
+        return np.sqrt(1.5 * np.sum(d * d)), d
+
+    trial = np.einsum("ijkl,kl->ij", C, eps - eps_p)
+    if seq_dev(trial)[0] <= sy + H * alpha:
+        return trial, eps_p, alpha
+
+    # unknowns scaled to order one: sigma / sy and dg * mu / sy
+    def F(u):
+        s, dg = to_t(u[:6]) * sy, u[6] * sy / mu
+        q, d = seq_dev(s)
+        n = 1.5 * d / q
+        r1 = s - np.einsum("ijkl,kl->ij", C, eps - eps_p - dg * n)
+        r2 = q - (sy + H * (alpha + dg))
+        return np.concatenate([[r1[i, j] for (i, j) in iu], [r2]]) / sy
+
+    u0 = np.concatenate([[trial[i, j] / sy for (i, j) in iu], [0.0]])
+    u, info, ok, msg = fsolve(F, u0, xtol=1e-13, full_output=True)
+    assert np.max(np.abs(F(u))) < 1e-12, msg
+    s, dg = to_t(u[:6]) * sy, u[6] * sy / mu
+    q, d = seq_dev(s)
+    return s, eps_p + dg * 1.5 * d / q, alpha + dg
+
+
+def test_homogeneous_j2_non_proportional_path_matches_implicit_integration():
+    """Shear first, then normal strain on top (plane strain, eps_33 = 0): the second increment
+    starts from the plastic strain the first one left, in a different direction, so the answer
+    depends on the committed internal variables. Checked against a backward-Euler integration
+    of the J2 model solved as a nonlinear system."""
+    lam, mu, sy, H = 40.4, 26.9, 0.25, 1.0
+    path = np.array([[0.0, 0.0, 0, 0, 0, 0.01],
+                     [0.01, 0.0, 0, 0, 0, 0.01],
+                     [0.01, -0.006, 0, 0, 0, 0.004]])
+    pm = np.zeros((3, 5), np.uint8)
+    ph = phase_table([(lam, mu, sy, H, 1)])
+    sbar, iters, res = O.solve_path(pm, ph, path, np.zeros((1, 3), np.int64), tol=1e-10)
+    assert np.all(iters == 1)
+    eps_p, alpha = np.zeros((3, 3)), 0.0
+    for n in range(len(path)):
+        s, eps_p, alpha = _implicit_j2_point(O.vec6_to_tensor(path[n]), eps_p, alpha,
+                                             lam, mu, sy, H)
+        want = O.tensor_to_vec6(s)
+        assert np.allclose(sbar[n], want, rtol=1e-9, atol=1e-12), (n, sbar[n], want)
+    assert alpha > 0 and np.allclose(res.alpha, alpha, rtol=1e-9)
+    assert np.allclose(res.eps_p[0, 0, 0], eps_p, atol=1e-12)
+
+
 # ----------------------------------------------------------------------------- brute force
 def test_reduced_fixed_point_equals_dense_galerkin_solve():
     pm = np.zeros((8, 8), np.uint8)
