@@ -5,7 +5,7 @@
 // rank the conjugate pairs (k, -k). Ranking key (smaller first): quantised amplitude
 // round(|g^| / |g^(0)| * 2^30) descending, |k|^2 ascending, signed linear index ascending.
 // Pairs are taken whole until at least k_target frequencies are held; the selection threshold
-// is found by binary search over the key with device-side counting.
+// is found by radix passes over weighted histograms of the key (device-side counting).
 // Radial pattern (Sec. 4.1): L equiangular rasterised lines; the same selection machinery
 // ranks pairs by (not on a line, |k|^2, index).
 #include <algorithm>
@@ -470,27 +470,37 @@ int validate_grid(const rf_grid* g, Grid3& out) {
   return RF_OK;
 }
 
-// shared selection + compaction on keys already in `key/lin/size`
-int select_and_compact(const Grid3& g, unsigned long long* key, int* lin, int* size,
-                       long long k_target, int32_t* out_host, long long cap, long long* K_out,
-                       cudaStream_t s, Scratch& sc) {
-  unsigned long long* d_cnt = sc.get<unsigned long long>(1);
-  unsigned long long* h_cnt = nullptr;
-  if (!d_cnt) return RF_ERR_OOM;
-  if (int e = check(cudaMallocHost(&h_cnt, sizeof(unsigned long long)), "pinned")) return e;
-  struct PinFree {
-    void* p;
-    ~PinFree() { cudaFreeHost(p); }
-  } pf{h_cnt};
+// Selection of the pattern from keys already in `key/lin/size`, shared by every entry point.
+// The caller provides the scratch: device d_cnt [1], d_hist [256], flags [N], tot [N/1024 + 2]
+// and d_out [3 K] (K becomes known after the threshold search, so d_out is asked for through
+// `out_buf`), and host h_cnt [1], h_hist [256] (pinned or pageable).
+struct SelectScratch {
+  unsigned long long* d_cnt;
+  unsigned long long* d_hist;
+  int* flags;
+  int* tot;
+  unsigned long long* h_cnt;
+  unsigned long long* h_hist;
+};
+
+// Threshold of the selection: the smallest (key, lin) in the total order whose weighted count of
+// entries at or below it reaches k_target, found by radix passes of 8 bits from the top (one
+// weighted histogram and one host read each), first over the whole 64-bit key, then over lin
+// among the entries with that key. *K receives the number of frequencies at or below it.
+int select_threshold(const Grid3& g, const unsigned long long* key, const int* lin,
+                     const int* size, long long k_target, cudaStream_t s,
+                     const SelectScratch& ss, unsigned long long* thi_out, int* tlin_out,
+                     long long* K) {
   auto count = [&](unsigned long long vhi, int vlin, unsigned long long& res) -> int {
-    if (int e = check(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s), "memset")) return e;
-    k_count_le<<<304, 256, 0, s>>>(key, lin, size, g.N, vhi, vlin, d_cnt);
+    if (int e = check(cudaMemsetAsync(ss.d_cnt, 0, sizeof(unsigned long long), s), "memset"))
+      return e;
+    k_count_le<<<304, 256, 0, s>>>(key, lin, size, g.N, vhi, vlin, ss.d_cnt);
     if (int e = check(cudaGetLastError(), "count_le")) return e;
-    if (int e = check(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(unsigned long long),
+    if (int e = check(cudaMemcpyAsync(ss.h_cnt, ss.d_cnt, sizeof(unsigned long long),
                                       cudaMemcpyDeviceToHost, s), "copy count"))
       return e;
     if (int e = check(cudaStreamSynchronize(s), "sync count")) return e;
-    res = *h_cnt;
+    res = *ss.h_cnt;
     return RF_OK;
   };
   unsigned long long total = 0;
@@ -499,60 +509,97 @@ int select_and_compact(const Grid3& g, unsigned long long* key, int* lin, int* s
     set_error("pattern: k_target exceeds the number of frequencies");
     return RF_ERR_INVALID;
   }
-  // The threshold is the smallest (key, lin) in the total order whose count of entries at or
-  // below it reaches k_target. Radix passes of 8 bits from the top, each one weighted
-  // histogram (one host read): first over the key, then over lin among entries with that key.
-  unsigned long long* d_hist = sc.get<unsigned long long>(256);
-  unsigned long long* h_hist = nullptr;
-  if (!d_hist) return RF_ERR_OOM;
-  if (int e = check(cudaMallocHost(&h_hist, 256 * sizeof(unsigned long long)), "pinned")) return e;
-  PinFree pf2{h_hist};
   unsigned long long below = 0;   // weighted count of entries strictly below the current base
   auto radix = [&](int phase, unsigned long long vhi, int top_shift,
                    unsigned long long& base) -> int {
     base = 0;
     for (int shift = top_shift; shift >= 0; shift -= 8) {
-      if (int e = check(cudaMemsetAsync(d_hist, 0, 256 * sizeof(unsigned long long), s), "memset"))
+      if (int e = check(cudaMemsetAsync(ss.d_hist, 0, 256 * sizeof(unsigned long long), s),
+                        "memset"))
         return e;
-      k_key_hist<<<304, 256, 0, s>>>(key, lin, size, g.N, phase, vhi, base, shift, d_hist);
+      k_key_hist<<<304, 256, 0, s>>>(key, lin, size, g.N, phase, vhi, base, shift, ss.d_hist);
       if (int e = check(cudaGetLastError(), "key histogram")) return e;
-      if (int e = check(cudaMemcpyAsync(h_hist, d_hist, 256 * sizeof(unsigned long long),
+      if (int e = check(cudaMemcpyAsync(ss.h_hist, ss.d_hist, 256 * sizeof(unsigned long long),
                                         cudaMemcpyDeviceToHost, s), "copy histogram"))
         return e;
       if (int e = check(cudaStreamSynchronize(s), "sync histogram")) return e;
       int b = 0;
-      while (b < 255 && (long long)(below + h_hist[b]) < k_target) below += h_hist[b++];
+      while (b < 255 && (long long)(below + ss.h_hist[b]) < k_target) below += ss.h_hist[b++];
       base += (unsigned long long)b << shift;
     }
     return RF_OK;
   };
   unsigned long long thi = 0, tl = 0;
-  if (int e = radix(0, 0, 56, thi)) return e;
+  if (int e = radix(0, 0, 56, thi)) return e;   // bits 63..0 of the key
   // `below` now counts the entries with key < thi
-  if (int e = radix(1, thi, 24, tl)) return e;
-  const int tlin = (int)tl;
-  unsigned long long K = 0;
-  if (int e = count(thi, tlin, K)) return e;
-  *K_out = (long long)K;
-  if ((long long)K > cap) {
-    set_error("pattern: output capacity too small");
+  if (int e = radix(1, thi, 24, tl)) return e;  // bits 31..0 of lin
+  unsigned long long k = 0;
+  if (int e = count(thi, (int)tl, k)) return e;
+  if ((long long)k < k_target) {
+    set_error("pattern: threshold search ended below k_target");
     return RF_ERR_INVALID;
   }
-  int* flags = sc.get<int>(g.N);
+  *thi_out = thi;
+  *tlin_out = (int)tl;
+  *K = (long long)k;
+  return RF_OK;
+}
+
+// Flags of the selected frequencies in signed-linear order, their compaction into d_out [3 K]
+// and the copy to the host.
+int compact_selection(const Grid3& g, const unsigned long long* key, const int* lin,
+                      unsigned long long thi, int tlin, long long K, int* d_out,
+                      int32_t* out_host, cudaStream_t s, const SelectScratch& ss) {
   const long long nb = (g.N + 1023) / 1024;
-  int* tot = sc.get<int>(nb + 1);
-  int* d_out = sc.get<int>(3 * (K > 0 ? K : 1));
-  if (!flags || !tot || !d_out) return RF_ERR_OOM;
-  const unsigned gb = (unsigned)((g.N + 255) / 256);
-  k_flags<<<gb, 256, 0, s>>>(key, lin, g, thi, tlin, flags);
-  k_block_totals<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot);
-  k_scan_totals<<<1, 32, 0, s>>>(tot, (int)nb);
-  k_compact<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot, g, d_out, (long long)K);
+  k_flags<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(key, lin, g, thi, tlin, ss.flags);
+  k_block_totals<<<(unsigned)nb, 1024, 0, s>>>(ss.flags, g.N, ss.tot);
+  k_scan_totals<<<1, 32, 0, s>>>(ss.tot, (int)nb);
+  k_compact<<<(unsigned)nb, 1024, 0, s>>>(ss.flags, g.N, ss.tot, g, d_out, K);
   if (int e = check(cudaGetLastError(), "compact")) return e;
   if (int e = check(cudaMemcpyAsync(out_host, d_out, sizeof(int) * 3 * K, cudaMemcpyDeviceToHost,
                                     s), "copy pattern"))
     return e;
   return check(cudaStreamSynchronize(s), "sync pattern");
+}
+
+// Selection with scratch from cudaMalloc / cudaMallocHost (the allocating entry points).
+int select_and_compact(const Grid3& g, unsigned long long* key, int* lin, int* size,
+                       long long k_target, int32_t* out_host, long long cap, long long* K_out,
+                       cudaStream_t s, Scratch& sc) {
+  SelectScratch ss{};
+  ss.d_cnt = sc.get<unsigned long long>(1);
+  ss.d_hist = sc.get<unsigned long long>(256);
+  ss.flags = sc.get<int>(g.N);
+  ss.tot = sc.get<int>((g.N + 1023) / 1024 + 2);
+  if (!ss.d_cnt || !ss.d_hist || !ss.flags || !ss.tot) {
+    set_error("pattern: out of device memory");
+    return RF_ERR_OOM;
+  }
+  if (int e = check(cudaMallocHost(&ss.h_cnt, sizeof(unsigned long long)), "pinned")) return e;
+  struct PinFree {
+    void* p;
+    ~PinFree() {
+      if (p) cudaFreeHost(p);
+    }
+  } pf{ss.h_cnt};
+  if (int e = check(cudaMallocHost(&ss.h_hist, 256 * sizeof(unsigned long long)), "pinned"))
+    return e;
+  PinFree pf2{ss.h_hist};
+  unsigned long long thi = 0;
+  int tlin = 0;
+  long long K = 0;
+  if (int e = select_threshold(g, key, lin, size, k_target, s, ss, &thi, &tlin, &K)) return e;
+  *K_out = K;
+  if (K > cap) {
+    set_error("pattern: output capacity too small");
+    return RF_ERR_INVALID;
+  }
+  int* d_out = sc.get<int>(3 * (K > 0 ? K : 1));
+  if (!d_out) {
+    set_error("pattern: out of device memory");
+    return RF_ERR_OOM;
+  }
+  return compact_selection(g, key, lin, thi, tlin, K, d_out, out_host, s, ss);
 }
 
 }  // namespace
@@ -711,6 +758,7 @@ constexpr size_t kNoAllocBytes =
     + 3 * align256(kNoAllocMaxVoxels * sizeof(int))               // lin, size, flags
     + align256((kNoAllocMaxVoxels / 1024 + 2) * sizeof(int))      // scan totals
     + align256(sizeof(unsigned long long))                        // counter
+    + align256(256 * sizeof(unsigned long long))                  // histogram
     + align256(3 * kNoAllocMaxVoxels * sizeof(int));              // output frequencies
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -775,9 +823,10 @@ int pattern_adapted_noalloc(const rf_grid* grid, const uint8_t* pm_host, int inc
   int* flags = reinterpret_cast<int*>(carve(kNoAllocMaxVoxels * sizeof(int)));
   int* tot = reinterpret_cast<int*>(carve((kNoAllocMaxVoxels / 1024 + 2) * sizeof(int)));
   auto* d_cnt = reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long)));
+  auto* d_hist = reinterpret_cast<unsigned long long*>(carve(256 * sizeof(unsigned long long)));
   int* d_out = reinterpret_cast<int*>(carve(3 * kNoAllocMaxVoxels * sizeof(int)));
 
-  // same kernels as rf_pattern_adapted
+  // the transform and key kernels of rf_pattern_adapted
   if (int e = check(cudaMemcpyAsync(d_pm, pm_host, g.N, cudaMemcpyHostToDevice, s), "upload"))
     return e;
   double2* G = nullptr;
@@ -785,61 +834,21 @@ int pattern_adapted_noalloc(const rf_grid* grid, const uint8_t* pm_host, int inc
   k_keys<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(G, nullptr, g, key, lin, size);
   if (int e = check(cudaGetLastError(), "noalloc: keys")) return e;
 
-  // selection: the counter is the only scratch that must start at zero; it is cleared
-  // before every count
-  unsigned long long h_cnt = 0;
-  auto count = [&](unsigned long long vhi, int vlin, unsigned long long& res) -> int {
-    if (int e = check(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s), "memset"))
-      return e;
-    k_count_le<<<304, 256, 0, s>>>(key, lin, size, g.N, vhi, vlin, d_cnt);
-    if (int e = check(cudaGetLastError(), "count_le")) return e;
-    if (int e = check(cudaMemcpyAsync(&h_cnt, d_cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s),
-                      "copy count"))
-      return e;
-    if (int e = check(cudaStreamSynchronize(s), "sync count")) return e;
-    res = h_cnt;
-    return RF_OK;
-  };
-  unsigned long long total = 0;
-  if (int e = count(~0ull - 1, INT_MAX, total)) return e;
-  if ((long long)total < k_target) {
-    set_error("pattern: k_target exceeds the number of frequencies");
-    return RF_ERR_INVALID;
-  }
-  unsigned long long lo = 0, hi = (1ull << 63);
-  while (lo < hi) {
-    unsigned long long mid = lo + (hi - lo) / 2, c = 0;
-    if (int e = count(mid, INT_MAX, c)) return e;
-    if ((long long)c >= k_target) hi = mid;
-    else lo = mid + 1;
-  }
-  const unsigned long long thi = lo;
-  long long llo = 0, lhi = g.N;
-  while (llo < lhi) {
-    long long mid = llo + (lhi - llo) / 2;
-    unsigned long long c = 0;
-    if (int e = count(thi, (int)mid, c)) return e;
-    if ((long long)c >= k_target) lhi = mid;
-    else llo = mid + 1;
-  }
-  const int tlin = (int)llo;
-  unsigned long long K = 0;
-  if (int e = count(thi, tlin, K)) return e;
-  *K_out = (long long)K;
-  if ((long long)K > cap) {
+  // the selection code of rf_pattern_adapted, on carved scratch and host buffers on the stack
+  // (pageable: the copies complete before each read); the counter and the histogram, the only
+  // scratch that must start at zero, are cleared before every use
+  unsigned long long h_cnt = 0, h_hist[256];
+  const SelectScratch ss{d_cnt, d_hist, flags, tot, &h_cnt, h_hist};
+  unsigned long long thi = 0;
+  int tlin = 0;
+  long long K = 0;
+  if (int e = select_threshold(g, key, lin, size, k_target, s, ss, &thi, &tlin, &K)) return e;
+  *K_out = K;
+  if (K > cap) {
     set_error("pattern: output capacity too small");
     return RF_ERR_INVALID;
   }
-  const long long nb = (g.N + 1023) / 1024;
-  k_flags<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(key, lin, g, thi, tlin, flags);
-  k_block_totals<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot);
-  k_scan_totals<<<1, 32, 0, s>>>(tot, (int)nb);
-  k_compact<<<(unsigned)nb, 1024, 0, s>>>(flags, g.N, tot, g, d_out, (long long)K);
-  if (int e = check(cudaGetLastError(), "noalloc: compact")) return e;
-  if (int e = check(cudaMemcpyAsync(out_host, d_out, sizeof(int) * 3 * K,
-                                    cudaMemcpyDeviceToHost, s), "copy pattern"))
-    return e;
-  return check(cudaStreamSynchronize(s), "sync pattern");
+  return compact_selection(g, key, lin, thi, tlin, K, d_out, out_host, s, ss);
 }
 
 

@@ -28,6 +28,24 @@ def test_noalloc_pattern_matches_allocating_entry_point_twice_in_a_row(lib):
         assert np.array_equal(second, want)
 
 
+def test_noalloc_pattern_matches_where_amplitudes_vanish(lib):
+    """Cases where many selected frequencies have a quantised amplitude of zero (their ranking
+    keys lie in the top half of the key range): a map without inclusion voxels, a laminate
+    once K exceeds its nonzero axis, and the full set K = N. Both entry points and the oracle
+    must give the same pattern."""
+    import oracle as O
+    from synth import laminate
+    cases = [(np.zeros((32, 48), np.uint8), 37),
+             (laminate((64, 64), (20, 45)), 205),
+             ((np.random.default_rng(3).random((12, 20)) < 0.3).astype(np.uint8), 240)]
+    for pm, K in cases:
+        want = lib.rf_pattern_adapted(pm, 1, K)
+        assert np.array_equal(want, O.pattern_adapted(pm, 1, K))
+        for _ in range(2):
+            got = lib.rf_pattern_adapted_noalloc(pm, 1, K)
+            assert len(got) >= K and np.array_equal(got, want)
+
+
 def test_noalloc_rejects_grids_beyond_its_static_scratch(lib):
     pm = np.zeros((257, 256), np.uint8)          # 65792 voxels > 65536
     g = lib.make_grid(pm.shape)
