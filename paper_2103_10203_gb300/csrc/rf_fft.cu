@@ -414,9 +414,10 @@ __global__ __launch_bounds__(256) void k_fft_colphase(ColPhaseArgs a, double Nd)
     const float4 n = a.hn[h];
     const int jj = hi.j - j0, pos = a.kym[hi.iy];
     const long long base = ((long long)hi.iy * NC) * a.Kx + hi.j;
-    float2 tv[NC];
+    float2 tv[NC];   // tau^ is read only where the operator uses it (regular frequencies)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) tv[c] = z[sw((jj * NC + c) * L + pos)];
+    for (int c = 0; c < NC; ++c)
+      tv[c] = hi.kind == 0 ? z[sw((jj * NC + c) * L + pos)] : make_float2(0.f, 0.f);
     float er[NC], ei[NC];
     green_update<NC>(hi.kind, n, tv, a.st->ebar, Nd, a.inv2mu0, a.cgam, er, ei);
     float d = 0.f;   // one frequency's squared increment (at most six non-negative terms)
