@@ -312,7 +312,7 @@ def run_batch(args, rf, torch):
     sh = stream.cuda_stream
     pats = [rf.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size), stream=sh) for pm in pms]
     ph = elastic_phases()
-    b = rf.BatchSolver(pms, ph, pats, stream=sh, tol=TOL, max_iter=2000, transform="dft")
+    b = rf.BatchSolver(pms, ph, pats, stream=sh, tol=TOL, max_iter=2000, transform="fft")
     vox = np.array([pm.size for pm in pms], np.float64)
     for _ in range(args.warmup):
         b.rf_batch_solve(macros)
@@ -330,7 +330,7 @@ def run_batch(args, rf, torch):
     # per-RVE contexts on a sample (every 8th RVE), solves timed back to back
     samp = list(range(0, n, 8))
     ctxs = [rf.Solver(pms[i], ph, pattern=pats[i], stream=sh, tol=TOL, max_iter=2000,
-                      transform="dft") for i in samp]
+                      transform="fft") for i in samp]
     for c, i in zip(ctxs[:8], samp[:8]):
         c.rf_solve(macros[i])
     def solo():

@@ -26,6 +26,17 @@
  * iteration cap was reached, outputs are written. Negative values are hard errors; outputs
  * are then unspecified. rf_last_error() returns a message for the calling thread (owned by
  * the library, valid until the thread's next call). No C++ exception crosses this ABI.
+ *  RF_ERR_NONFINITE  a NaN or infinite input (modulus, macroscopic strain or stress), or a
+ *                    convergence measure / homogenised stress that became non-finite on the
+ *                    device (e.g. FP32 overflow).
+ *  RF_ERR_DIVERGED   the convergence measure exceeded both 1e4 times its smallest value in the
+ *                    solve and 1e-3: the basic scheme contracts only for a reference medium
+ *                    that bounds the phases well enough (Sec. 3); RF_REF_VOLUME with a stiff
+ *                    minority phase can violate that.
+ *  RF_ERR_TIMEOUT    a bounded device-side wait of a tensor-core kernel ran out (see
+ *                    rf_options.wait_limit); the kernels drain their copies and matrix
+ *                    products in flight and release tensor memory before they return, so the
+ *                    CUDA context stays usable.
  *
  * Ownership: the caller owns every pointer it passes; inputs are copied before the call
  * returns unless stated otherwise. Outputs go to caller-owned buffers of the documented size.
@@ -116,7 +127,13 @@ typedef struct rf_phase {
  *  fft_row_blocks  FFT mode: run the row kernel on this many blocks with the grid rows spread
  *             evenly (blocks differ by at most one row; clamped to the row count), instead of
  *             tiles of fft_rows; 0 = fft_rows or the autotuner (which also times such
- *             partitions over whole multiples of the SM count). */
+ *             partitions over whole multiples of the SM count).
+ *  wait_limit  split-precision modes: polls of every bounded mbarrier wait in the tensor-core
+ *             kernels before the wait gives up and the solve returns RF_ERR_TIMEOUT (0 = the
+ *             library default, 2^26 polls); >= 0.
+ *  stall_test  split-precision modes, for testing the timeout path: when 1, every tensor-core
+ *             kernel first waits on a barrier that nothing completes, so the bounded wait runs
+ *             out after wait_limit polls and the solve returns RF_ERR_TIMEOUT. 0 otherwise. */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
@@ -130,6 +147,9 @@ typedef struct rf_options {
   int32_t fft_fuse;
   int32_t fft_fuse_kx;
   int32_t fft_row_blocks;
+  int64_t wait_limit;
+  int32_t stall_test;
+  int32_t reserved;
 } rf_options;
 
 /* Run statistics of the last solve on a context. */
@@ -266,20 +286,28 @@ int rf_pattern_radial(const rf_grid* grid, int64_t k_target, int32_t* freqs_out,
  * Sec. 1), each with its own grid (sides 2..1024, any size), phase map, adapted pattern and
  * macroscopic strain, solved together on one GPU. Every update of all unconverged RVEs is a fixed
  * sequence of persistent kernels walking (RVE, tile) work lists; RVEs leave the work as they
- * converge. Elastic phases only, plane strain, FP32 pruned-DFT transforms (options.transform =
- * RF_TRANSFORM_DFT, precision RF_PREC_FP32), FP64 convergence measure and homogenised stress.
- * Same convergence measure and rules as rf_solve.
+ * converge, and a whole solve is one CUDA graph launch (a conditional while node over a few
+ * updates, ended on the device once every RVE is done). Elastic phases only, plane strain, FP32
+ * transforms (precision RF_PREC_FP32):
+ *   options.transform = RF_TRANSFORM_FFT: FFTs along x and y, restricted to each pattern, for
+ *     RVEs whose sides are 2^b or 3 * 2^b; the pruned DFT for the other sides;
+ *   options.transform = RF_TRANSFORM_DFT: the pruned separable DFT for every RVE.
+ * FP64 convergence measure and homogenised stress; the same convergence measure and rules
+ * (converged, capped, non-finite, diverged) as rf_solve, per RVE.
  *  rf_batch_create: grids[n_rve]; phase_maps[n_rve] HOST uint8 pointers; phases shared by all
  *  RVEs; patterns[n_rve] HOST int32 [K[r]][3] pointers (rules of rf_set_pattern, kz = 0); all
- *  inputs are copied. Chooses rows per work item and the persistent grid size by timing a few
- *  updates (autotuner). stream as in rf_create.
+ *  inputs are copied. Chooses the rows per row work item for each size class of RVE (largest
+ *  side <= 64, <= 96, <= 128, <= 192, larger) and the persistent grid size by timing updates
+ *  of the whole batch (autotuner). stream as in rf_create.
  *  rf_batch_solve: macro [n_rve][6]; warm nullable, else warm[r] nullable HOST float
  *  [K[r]][6][2] start coefficients (projected as in rf_solve); outputs (each nullable):
  *  hom_stress [n_rve][6], iters [n_rve], residuals [n_rve], status [n_rve] (RF_OK,
- *  RF_NOT_CONVERGED or RF_ERR_NONFINITE per RVE). Returns RF_OK when every RVE converged,
- *  RF_NOT_CONVERGED otherwise, or a hard error.
- *  rf_batch_info: kernels launched so far (graph replays included), chosen rows per row item,
- *  persistent grid size. */
+ *  RF_NOT_CONVERGED, RF_ERR_NONFINITE or RF_ERR_DIVERGED per RVE). Returns RF_OK when every
+ *  RVE converged, RF_NOT_CONVERGED otherwise, or a hard error (RF_ERR_NONFINITE for a
+ *  non-finite macroscopic strain).
+ *  rf_batch_info: kernels launched so far (graph replays included), the rows per row item
+ *  chosen for each of the five size classes (rows_per_item: int32 [5], nullable), persistent
+ *  grid size. */
 typedef struct rf_batch rf_batch;
 int rf_batch_create(rf_batch** batch, int32_t n_rve, const rf_grid* grids,
                     const uint8_t* const* phase_maps, int32_t n_phases, const rf_phase* phases,

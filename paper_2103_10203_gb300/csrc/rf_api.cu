@@ -309,11 +309,12 @@ int init_status(rf_ctx* c, const double* macro) {
   s.max_iter = c->opt.max_iter;
   s.nonfinite = 0;
   s.timeout = 0;
-  s.pad = 0;
+  s.diverged = 0;
   s.tol = c->opt.tol;
   s.enorm = frob6(macro);
   s.inv_n2 = 1.0 / ((double)c->N * (double)c->N);
   s.last_r = 0.0;
+  s.rmin = HUGE_VAL;
   for (int i = 0; i < 6; ++i) s.ebar[i] = macro[i];
   return ck(cudaMemcpyAsync(c->d_status, c->h_status, sizeof(Status), cudaMemcpyHostToDevice,
                             c->stream), "upload status");
@@ -365,6 +366,12 @@ int run_iterations(rf_ctx* c) {
     set_error("convergence measure is not finite");
     return RF_ERR_NONFINITE;
   }
+  if (c->h_status->diverged) {
+    set_error("the fixed-point iteration diverged: the convergence measure grew past 1e4 times "
+              "its smallest value (the reference medium does not bound the phases enough for "
+              "the basic scheme to contract)");
+    return RF_ERR_DIVERGED;
+  }
   return RF_OK;
 }
 
@@ -389,7 +396,10 @@ int finish(rf_ctx* c, int commit, double* sbar) {
 
 int check_macro(const rf_ctx* c, const double* m) {
   for (int i = 0; i < 6; ++i)
-    if (!std::isfinite(m[i])) return invalid("macroscopic strain is not finite");
+    if (!std::isfinite(m[i])) {
+      set_error("macroscopic strain is not finite");
+      return RF_ERR_NONFINITE;
+    }
   if (c->dim == 2 && (m[2] != 0.0 || m[3] != 0.0 || m[4] != 0.0))
     return invalid("2D (plane strain): macro strain components 33, 23, 13 must be zero");
   return RF_OK;
@@ -415,7 +425,12 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (n_phases < 1 || n_phases > kMaxPhases) return invalid("n_phases must be in [1, 16]");
   for (int p = 0; p < n_phases; ++p) {
     const rf_phase& ph = phases[p];
-    if (!(ph.mu > 0.0) || !(ph.lambda + 2.0 * ph.mu / 3.0 > 0.0) || !std::isfinite(ph.lambda))
+    if (!std::isfinite(ph.lambda) || !std::isfinite(ph.mu) ||
+        (ph.plastic && (!std::isfinite(ph.sigma_y0) || !std::isfinite(ph.hardening)))) {
+      set_error("phase moduli must be finite");
+      return RF_ERR_NONFINITE;
+    }
+    if (!(ph.mu > 0.0) || !(ph.lambda + 2.0 * ph.mu / 3.0 > 0.0))
       return invalid("phase moduli must satisfy mu > 0 and lambda + 2 mu / 3 > 0");
     if (ph.plastic && (!(ph.sigma_y0 > 0.0) || !(ph.hardening >= 0.0) ||
                        !std::isfinite(ph.sigma_y0) || !std::isfinite(ph.hardening)))
@@ -434,6 +449,10 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (opt->fft_rows < 0 || opt->fft_rows > 64 || opt->fft_cols < 0 || opt->fft_cols > 64)
     return invalid("options: fft_rows and fft_cols in [0, 64]");
   if (opt->fft_row_blocks < 0) return invalid("options: fft_row_blocks >= 0");
+  if (opt->wait_limit < 0 || (opt->stall_test != 0 && opt->stall_test != 1))
+    return invalid("options: wait_limit >= 0, stall_test 0 or 1");
+  if (opt->stall_test && opt->precision == RF_PREC_FP32)
+    return invalid("options: stall_test applies to the split-precision modes only");
   if (opt->fft_fuse < -1 || opt->fft_fuse > 2 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
     return invalid("options: fft_fuse in {-1, 0, 1, 2}, fft_fuse_kx in [0, 16]");
   if (opt->fft_fuse >= 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))

@@ -5,10 +5,13 @@
 // (RVE, tile) items in a fixed order (largest RVEs first) with a stride of the grid size:
 //   inverse y transform tiles, row tiles (x transforms + law), forward y transform tiles,
 //   Green-operator chunks (with squared-increment partials), per-RVE convergence decisions.
-// Items of converged RVEs return at once. Chunks of updates are captured as CUDA graphs and
-// replayed until every RVE has converged or hit its cap. Elastic phases, plane strain (NC = 3),
-// pruned DFT transforms in FP32; convergence measure and homogenised stress in FP64.
-// Row tiles and the persistent grid size are chosen per batch by a timing autotuner.
+// Items of converged RVEs return at once. A solve is one CUDA graph launch: a conditional while
+// node whose body is a few updates; the decision kernel's last block clears the loop condition
+// once every RVE is done (converged, capped, non-finite or diverged). Elastic phases, plane
+// strain (NC = 3), FP32 transforms: FFT items along x and y for sides 2^b and 3 2^b with
+// options.transform = RF_TRANSFORM_FFT, pruned-DFT items otherwise; convergence measure and
+// homogenised stress in FP64. Rows per row item (per size class) and the persistent grid size
+// are chosen per batch by a timing autotuner.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -50,7 +53,8 @@ struct BDesc {
 
 struct BStat {
   int done, iters, nonfinite, max_iter;
-  double tol, enorm, inv_n2, last_r;
+  int diverged, pad;
+  double tol, enorm, inv_n2, last_r, rmin;
   double ebar[6];
   double sbar[6];
 };
@@ -76,6 +80,11 @@ struct BArgs {
   int* n_done;
   LawParams law;
   int final_pass;
+  // while-loop graph: the decision kernel's last block clears the loop condition when every
+  // RVE is done
+  unsigned* counter;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
 };
 
 __device__ __forceinline__ bool rve_done(const BArgs& a, int r) { return a.st[r].done != 0; }
@@ -494,8 +503,10 @@ __global__ __launch_bounds__(256) void kb_gamma(BArgs a) {
   }
 }
 
-// one thread per RVE: convergence measure from its partials (fixed order), decision
+// one thread per RVE: convergence measure from its partials (fixed order), decision (the rules
+// of the single-RVE solver: non-finite, diverged, converged or capped)
 __global__ void kb_decide(BArgs a, int n_rve) {
+  __shared__ bool last;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rve; r += gridDim.x * blockDim.x) {
     BStat& st = a.st[r];
     if (st.done) continue;
@@ -506,13 +517,30 @@ __global__ void kb_decide(BArgs a, int n_rve) {
     if (st.enorm > 0.0) rr /= st.enorm;
     st.iters += 1;
     st.last_r = rr;
+    st.rmin = fmin(st.rmin, rr);
     if (!isfinite(rr)) {
       st.nonfinite = 1;
+      st.done = 1;
+    } else if (rr > kDivergeRatio * st.rmin && rr > kDivergeFloor) {
+      st.diverged = 1;
       st.done = 1;
     } else if (rr < st.tol || st.iters >= st.max_iter) {
       st.done = 1;
     }
     if (st.done) atomicAdd(a.n_done, 1);
+  }
+  if (!a.use_cond) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    *a.counter = 0u;
+    // the only call site of the loop condition: one thread of one block per update
+    if (atomicAdd(a.n_done, 0) >= n_rve) cudaGraphSetConditional(a.cond, 0u);
   }
 }
 
@@ -851,6 +879,13 @@ struct rf_batch {
   bool use_fft = true;                 // FFT row and column items where the sides allow
   size_t col_smem = 0;                 // dynamic shared memory of the column kernels
   std::vector<std::pair<int, cudaGraphExec_t>> graphs;
+  // one-launch solve: conditional while node over kBatchBody updates
+  cudaGraphExec_t while_exec = nullptr;
+  cudaGraphConditionalHandle while_cond = 0;
+  bool while_failed = false;
+  bool capturing_while = false;
+  bool last_while = false;         // the last solve ran as the while graph
+  unsigned* d_counter = nullptr;   // finished blocks of the decision kernel
   long long launches = 0;
   int last_max_iters = 0;
 };
@@ -889,6 +924,9 @@ BArgs batch_args(rf_batch* b, int stage) {
   a.spart = b->d_spart;
   a.n_done = b->d_ndone;
   a.law = b->law;
+  a.counter = b->d_counter;
+  a.cond = b->while_cond;
+  a.use_cond = b->capturing_while ? 1 : 0;
   return a;
 }
 
@@ -959,6 +997,59 @@ int build_row_items(rf_batch* b) {
 void free_graphs(rf_batch* b) {
   for (auto& g : b->graphs) cudaGraphExecDestroy(g.second);
   b->graphs.clear();
+  if (b->while_exec) cudaGraphExecDestroy(b->while_exec);
+  b->while_exec = nullptr;
+  b->while_failed = false;
+}
+
+// One graph for a whole batched solve: a conditional while node whose body is kBatchBody
+// updates; the decision kernel's last block clears the condition once every RVE is done, so the
+// loop ends with the body in which the last RVE finished (later updates skip every item). If
+// the graph cannot be built, the solve replays chunks of updates and polls the done count.
+constexpr int kBatchBody = 4;
+
+int while_graph(rf_batch* b) {
+  if (b->while_exec || b->while_failed) return RF_OK;
+  cudaGraph_t graph = nullptr;
+  auto give_up = [&]() {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    b->while_failed = true;
+    return RF_OK;
+  };
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return give_up();
+  cudaGraphConditionalHandle h = 0;
+  if (cudaGraphConditionalHandleCreate(&h, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+    return give_up();
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) != cudaSuccess) return give_up();
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  b->while_cond = h;
+  if (cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return give_up();
+  const long long launched = b->launches;
+  b->capturing_while = true;
+  int err = RF_OK;
+  for (int i = 0; i < kBatchBody && !err; ++i) err = launch_update(b);
+  b->capturing_while = false;
+  b->launches = launched;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(b->stream, &captured);
+  if (err || ce != cudaSuccess) {
+    set_error("");
+    return give_up();
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) return give_up();
+  cudaGraphDestroy(graph);
+  b->while_exec = exec;
+  return RF_OK;
 }
 
 int graph_for(rf_batch* b, int chunk, cudaGraphExec_t* out) {
@@ -1000,6 +1091,7 @@ int set_status(rf_batch* b, const double* macro) {
                         2.0 * (m[3] * m[3] + m[4] * m[4] + m[5] * m[5]));
     const double N = (double)b->desc[r].N;
     s.inv_n2 = 1.0 / (N * N);
+    s.rmin = HUGE_VAL;
   }
   cudaError_t e = cudaMemcpyAsync(b->d_stat, b->h_stat, sizeof(BStat) * b->n,
                                   cudaMemcpyHostToDevice, b->stream);
@@ -1007,8 +1099,20 @@ int set_status(rf_batch* b, const double* macro) {
   return e == cudaSuccess ? RF_OK : bfail(e, "batch status");
 }
 
-// iterate until every RVE is done; returns the number of chunks
+// iterate until every RVE is done: one while-graph launch, or replayed chunks of updates with
+// a host read of the done count after each
 int iterate(rf_batch* b) {
+  if (int e = while_graph(b)) return e;
+  if (b->while_exec) {
+    cudaError_t e = cudaGraphLaunch(b->while_exec, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->h_ndone, b->d_ndone, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(e, "batch iterate");
+    b->last_while = true;   // kernels launched are counted from the iterations in finish_solve
+    return RF_OK;
+  }
+  b->last_while = false;
   const int maxchunk = b->opt.check_every > 0 ? b->opt.check_every : 16;
   int chunk = std::min(4, maxchunk);
   for (;;) {
@@ -1036,45 +1140,79 @@ int run_solve(rf_batch* b, const double* macro, bool use_warm, const float2* pwa
   return iterate(b);
 }
 
-// autotuner: rows per row item per size class (and the persistent grid), timed on updates
+// Autotuner: rows per row item for each size class present (coordinate descent: one class at
+// a time, the others held), then the persistent grid size, each candidate timed as the fastest
+// of three groups of two updates of the whole batch (CUDA events on the batch's stream).
 int autotune(rf_batch* b, const double* macro) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
   const int Rc[4] = {1, 2, 4, 8};
   const int Gc[3] = {2, 4, 8};
+  bool present[5] = {false, false, false, false, false};
+  for (const BDesc& d : b->desc) present[size_class(std::max(d.nx, d.ny))] = true;
   cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float best = 1e30f;
-  int bestR = 2, bestG = 4;
-  for (int ri = 0; ri < 4; ++ri) {
-    for (int k = 0; k < 5; ++k) b->R_choice[k] = Rc[ri];
-    if (int e = build_row_items(b)) return e;
-    for (int gi = 0; gi < 3; ++gi) {
-      b->grid = sms * Gc[gi];
-      if (int e = set_status(b, macro)) return e;
-      kb_init<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, nullptr, b->d_warm_off,
-                                           nullptr);
-      if (int e = launch_update(b)) return e;   // warm-up
+  if (cudaEventCreate(&e0) != cudaSuccess) return bfail(cudaGetLastError(), "batch tuner");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bfail(cudaGetLastError(), "batch tuner");
+  }
+  auto time_updates = [&](float* ms) -> int {
+    if (int e = set_status(b, macro)) return e;
+    kb_init<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, nullptr, b->d_warm_off,
+                                         nullptr);
+    if (int e = launch_update(b)) return e;   // warm-up
+    *ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(e0, b->stream);
-      for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 2; ++i)
         if (int e = launch_update(b)) return e;
       cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return bfail(cudaGetLastError(), "batch tuner");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      *ms = std::min(*ms, t);
+    }
+    return RF_OK;
+  };
+  int err = RF_OK;
+  for (int k = 0; k < 5; ++k) b->R_choice[k] = 2;
+  b->grid = sms * 4;
+  for (int k = 0; k < 5 && !err; ++k) {
+    if (!present[k]) continue;
+    float best = 1e30f;
+    int bestR = b->R_choice[k];
+    for (int R : Rc) {
+      b->R_choice[k] = R;
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      err = build_row_items(b);
+      if (!err) err = time_updates(&ms);
+      if (err) break;
       if (ms < best) {
         best = ms;
-        bestR = Rc[ri];
-        bestG = Gc[gi];
+        bestR = R;
       }
     }
+    b->R_choice[k] = bestR;
+  }
+  if (!err) err = build_row_items(b);
+  if (!err) {
+    float best = 1e30f;
+    int bestG = 4;
+    for (int G : Gc) {
+      b->grid = sms * G;
+      float ms = 0.f;
+      err = time_updates(&ms);
+      if (err) break;
+      if (ms < best) {
+        best = ms;
+        bestG = G;
+      }
+    }
+    b->grid = sms * bestG;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (int k = 0; k < 5; ++k) b->R_choice[k] = bestR;
-  b->grid = sms * bestG;
-  return build_row_items(b);
+  return err;
 }
 
 // final pass: fields of the converged coefficients -> homogenised stresses; per-RVE outputs
@@ -1101,11 +1239,15 @@ int finish_solve(rf_batch* b, double* hom_stress, int32_t* iters, double* residu
       for (int i = 0; i < 6; ++i) hom_stress[6 * r + i] = s.sbar[i];
     if (iters) iters[r] = s.iters;
     if (residuals) residuals[r] = s.last_r;
-    int st = s.nonfinite ? RF_ERR_NONFINITE : (s.last_r < b->opt.tol ? RF_OK : RF_NOT_CONVERGED);
+    const int st = s.nonfinite ? RF_ERR_NONFINITE
+                   : s.diverged ? RF_ERR_DIVERGED
+                                : (s.last_r < b->opt.tol ? RF_OK : RF_NOT_CONVERGED);
     if (status) status[r] = st;
     if (st != RF_OK && code == RF_OK) code = RF_NOT_CONVERGED;
     b->last_max_iters = std::max(b->last_max_iters, s.iters);
   }
+  if (b->last_while)   // bodies of kBatchBody updates of five kernels each
+    b->launches += 5LL * kBatchBody * ((b->last_max_iters + kBatchBody - 1) / kBatchBody);
   return code;
 }
 
@@ -1127,21 +1269,30 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     set_error("rf_batch_create: n_phases must be in [1, 16]");
     return RF_ERR_INVALID;
   }
-  for (int p = 0; p < n_phases; ++p)
+  for (int p = 0; p < n_phases; ++p) {
+    if (!std::isfinite(phases[p].lambda) || !std::isfinite(phases[p].mu)) {
+      set_error("rf_batch_create: phase moduli must be finite");
+      return RF_ERR_NONFINITE;
+    }
     if (phases[p].plastic || !(phases[p].mu > 0.0) ||
         !(phases[p].lambda + 2.0 * phases[p].mu / 3.0 > 0.0)) {
       set_error("rf_batch_create: elastic phases with mu > 0, lambda + 2 mu / 3 > 0 only");
       return RF_ERR_INVALID;
     }
-  if (opt->transform != RF_TRANSFORM_DFT || opt->precision != RF_PREC_FP32 || opt->max_iter < 1 ||
-      !(opt->tol >= 0.0) || (opt->green != 0 && opt->green != 1)) {
-    set_error("rf_batch_create: options must select FP32 DFT transforms");
+  }
+  if ((opt->transform != RF_TRANSFORM_DFT && opt->transform != RF_TRANSFORM_FFT) ||
+      opt->precision != RF_PREC_FP32 || opt->max_iter < 1 || !(opt->tol >= 0.0) ||
+      (opt->green != 0 && opt->green != 1) ||
+      (opt->ref_medium != RF_REF_MINMAX && opt->ref_medium != RF_REF_VOLUME)) {
+    set_error("rf_batch_create: options must select FP32 precision, the DFT or FFT transform, "
+              "tol >= 0, max_iter >= 1 and a known Green operator and reference medium");
     return RF_ERR_INVALID;
   }
   rf_batch* b = new rf_batch();
   cudaGetDevice(&b->dev);
   b->n = n_rve;
   b->opt = *opt;
+  b->use_fft = opt->transform == RF_TRANSFORM_FFT;
   b->stream = static_cast<cudaStream_t>(stream);
   if (!b->stream) {
     cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
@@ -1332,6 +1483,9 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   if (!err) err = balloc(&b->d_tab, tab_total, "batch tables");
   if (!err) err = balloc(&b->d_part, off_part, "batch partials");
   if (!err) err = balloc(&b->d_ndone, 1, "batch");
+  if (!err) err = balloc(&b->d_counter, 1, "batch");
+  if (!err && cudaMemset(b->d_counter, 0, sizeof(unsigned)) != cudaSuccess)
+    err = bfail(cudaGetLastError(), "batch");
   if (!err) err = balloc(&b->d_warm_off, n_rve, "batch");
   b->n_slots = off_h;
   auto up = [&](void* dst, const void* src, size_t bytes) {
@@ -1427,6 +1581,11 @@ int rf_batch_solve(rf_batch* b, const double* macro, const float* const* warm,
     set_error("rf_batch_solve: null argument");
     return RF_ERR_INVALID;
   }
+  for (int i = 0; i < 6 * b->n; ++i)
+    if (!std::isfinite(macro[i])) {
+      set_error("rf_batch_solve: macroscopic strain is not finite");
+      return RF_ERR_NONFINITE;
+    }
   for (int r = 0; r < b->n; ++r)
     for (int i = 2; i < 5; ++i)
       if (macro[6 * r + i] != 0.0) {
@@ -1525,6 +1684,11 @@ int rf_batch_solve_warm(rf_batch* b, const double* macro, const float* d_warm, d
     set_error("rf_batch_solve_warm: invalid argument");
     return RF_ERR_INVALID;
   }
+  for (int i = 0; i < 6 * b->n; ++i)
+    if (!std::isfinite(macro[i])) {
+      set_error("rf_batch_solve_warm: macroscopic strain is not finite");
+      return RF_ERR_NONFINITE;
+    }
   for (int r = 0; r < b->n; ++r)
     for (int i = 2; i < 5; ++i)
       if (macro[6 * r + i] != 0.0) {
@@ -1542,7 +1706,8 @@ int rf_batch_info(const rf_batch* b, int64_t* kernel_launches, int32_t* rows_per
     return RF_ERR_INVALID;
   }
   if (kernel_launches) *kernel_launches = b->launches;
-  if (rows_per_item) *rows_per_item = b->R_choice[0];
+  if (rows_per_item)
+    for (int k = 0; k < 5; ++k) rows_per_item[k] = b->R_choice[k];
   if (grid) *grid = b->grid;
   return RF_OK;
 }
@@ -1567,6 +1732,7 @@ int rf_batch_destroy(rf_batch* b) {
   cudaFree(b->d_part);
   cudaFree(b->d_spart);
   cudaFree(b->d_ndone);
+  cudaFree(b->d_counter);
   cudaFree(b->d_warm);
   cudaFree(b->d_warm_off);
   for (int s = 0; s < 5; ++s) cudaFree(b->d_items[s]);

@@ -47,18 +47,24 @@ struct HIdx {
 };
 
 struct Status {
-  int done;       // set when converged, capped, or non-finite
+  int done;       // set when converged, capped, non-finite, diverged or timed out
   int iters;      // fixed-point updates of this solve
   int max_iter;
   int nonfinite;
   int timeout;    // a bounded device-side wait ran out
-  int pad;
+  int diverged;   // the measure grew past kDivergeRatio times its minimum (and kDivergeFloor)
   double tol;
   double enorm;   // Frobenius norm of ebar (0: absolute measure)
   double inv_n2;  // 1 / N^2 (Parseval)
   double last_r;
+  double rmin;    // smallest measure of this solve so far
   double ebar[6];
 };
+
+// Divergence rule of the convergence decision: the measure exceeds both kDivergeRatio times
+// its smallest value in the solve and kDivergeFloor (relative to |ebar|).
+constexpr double kDivergeRatio = 1e4;
+constexpr double kDivergeFloor = 1e-3;
 
 struct DftAxisArgs {
   const float2* in;
@@ -314,8 +320,12 @@ __device__ inline void decide(const double* part, int n, Status* st, double* sh)
     if (st->enorm > 0.0) r /= st->enorm;
     st->iters += 1;
     st->last_r = r;
+    st->rmin = fmin(st->rmin, r);
     if (!isfinite(r)) {
       st->nonfinite = 1;
+      st->done = 1;
+    } else if (r > kDivergeRatio * st->rmin && r > kDivergeFloor) {
+      st->diverged = 1;
       st->done = 1;
     } else if (r < st->tol || st->iters >= st->max_iter || st->timeout) {
       st->done = 1;

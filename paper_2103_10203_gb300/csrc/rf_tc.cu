@@ -115,6 +115,8 @@ struct TcRowArgs {
   LawParams law;
   const int* done;
   int* err;
+  long wait_limit;   // polls per bounded wait
+  int stall;         // test hook: first wait on a barrier that nothing completes
 };
 
 }  // namespace tc
@@ -132,8 +134,9 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
   const int tq_bytes = a.Qp * kChunkBytes;
   unsigned char* tau = bufT + 4 * tq_bytes;                    // (hi, lo) Qp x tau_rb
   const int tau_bytes = a.Qp * tau_rb;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tau + 2 * tau_bytes);   // lbar[2], mbar[2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  // lbar[2], mbar[2], and a barrier that nothing completes (the stall test)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tau + 2 * tau_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
   int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -143,7 +146,7 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
   const int Q = a.R * NC;
 
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -163,18 +166,26 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
   const uint32_t id_mma = idesc<E>(kTile, a.Qp);
   // Failures (a bounded wait that ran out) are combined in s_err at CTA barriers, so that every
   // thread takes the same path through barriers and warp-collective tensor-memory loads.
-  bool ok = true;
+  if (a.stall) {
+    if (tid == 0 && !mbar_wait(&bars[4], 0, a.wait_limit)) atomicOr(s_err, 1);
+    __syncthreads();
+  }
+  bool ok = (*s_err == 0);
+  // phases issued by thread 0 on the copy barriers (nl) and the product barriers (nm); each
+  // barrier has at most one issued phase that no successful wait has seen
+  int nl[2] = {0, 0}, nm[2] = {0, 0};
 
-  for (int g = 0; g < n_stages; ++g) {
+  for (int g = 0; ok && g < n_stages; ++g) {
     const int b = g & 1;
     unsigned char* A = bufA + b * 2 * kTileBytes;
     unsigned char* Tb = bufT + b * 2 * tq_bytes;
     // buffer b is free once the MMAs of stage g - 2 completed
-    if (g >= 2 && !mbar_wait(&bars[2 + b], ((g - 2) >> 1) & 1)) {
+    if (g >= 2 && !mbar_wait(&bars[2 + b], ((g - 2) >> 1) & 1, a.wait_limit)) {
       ok = false;
       atomicOr(s_err, 1);
     }
     if (tid == 0 && ok) {
+      ++nl[b];
       const unsigned char* src;
       if (g < a.nJC) {
         src = a.phiI + ((long long)(xs * a.nJC + g) * 2) * kTileBytes;
@@ -227,7 +238,8 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
     }
     if (g == a.nJC) {
       // law: D1 complete (stage nJC - 1 committed); eps for x = this thread's lane
-      if (!mbar_wait(&bars[2 + ((a.nJC - 1) & 1)], ((a.nJC - 1) >> 1) & 1)) atomicOr(s_err, 1);
+      if (!mbar_wait(&bars[2 + ((a.nJC - 1) & 1)], ((a.nJC - 1) >> 1) & 1, a.wait_limit))
+        atomicOr(s_err, 1);
       __syncthreads();
       ok = (*s_err == 0);
     }
@@ -294,7 +306,7 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0 && *s_err == 0) {
-      if (!mbar_wait(&bars[b], (g >> 1) & 1)) {
+      if (!mbar_wait(&bars[b], (g >> 1) & 1, a.wait_limit)) {
         atomicOr(s_err, 1);
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -330,6 +342,7 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
           }
         }
         mma_commit(&bars[2 + b]);
+        ++nm[b];
       }
     }
     __syncthreads();
@@ -339,7 +352,7 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
   // all MMAs done: wait for the last stage's commit
   if (ok) {
     const int gl = n_stages - 1;
-    if (!mbar_wait(&bars[2 + (gl & 1)], (gl >> 1) & 1)) atomicOr(s_err, 1);
+    if (!mbar_wait(&bars[2 + (gl & 1)], (gl >> 1) & 1, a.wait_limit)) atomicOr(s_err, 1);
   }
   __syncthreads();
   ok = (*s_err == 0);
@@ -363,7 +376,13 @@ __global__ __launch_bounds__(128) void k_tc_row(TcRowArgs a) {
       }
     }
   } else if (tid == 0) {
+    // a wait gave up: report it, then let the copies and products in flight finish (each
+    // barrier's last issued phase, with the default limit) before tensor memory is released
     atomicExch(a.err, 1);
+    for (int b = 0; b < 2; ++b) {
+      if (nl[b] > 0) mbar_wait(&bars[b], (nl[b] - 1) & 1);
+      if (nm[b] > 0) mbar_wait(&bars[2 + b], (nm[b] - 1) & 1);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -415,6 +434,8 @@ struct TcAxisArgs {
   uint32_t tmem_cols;
   const int* done;
   int* err;
+  long wait_limit;   // polls per bounded wait
+  int stall;         // test hook: first wait on a barrier that nothing completes
 };
 
 // one CTA: 64 complex output rows (blockIdx.y) x NT columns (blockIdx.x) of one batch entry
@@ -429,8 +450,9 @@ __global__ __launch_bounds__(256) void k_tc_axis(TcAxisArgs a) {
   unsigned char* As = smem;                          // hi, lo: 2 x 16 KB
   unsigned char* Bs = smem + 2 * kTileBytes;         // hi, lo: 2 x NT x 128 B
   const int bbytes = a.NT * kChunkBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + 2 * bbytes);   // [0] A copy, [1] MMAs
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  // [0] A copy, [1] MMAs, [2] a barrier that nothing completes (the stall test)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bs + 2 * bbytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
   int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int n0 = blockIdx.x * a.NT, mt = blockIdx.y;
@@ -438,6 +460,7 @@ __global__ __launch_bounds__(256) void k_tc_axis(TcAxisArgs a) {
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -453,16 +476,20 @@ __global__ __launch_bounds__(256) void k_tc_axis(TcAxisArgs a) {
   const uint32_t tmem = *tmem_slot;
   const uint32_t id_mma = idesc<E>(kTile, a.NT);
   const float2* inb = a.in + b * a.in_bstride;
+  if (a.stall && tid == 0 && !mbar_wait(&bars[2], 0, a.wait_limit)) atomicOr(s_err, 1);
   bool ok = true;
+  int nl = 0, nm = 0;   // phases thread 0 issued on the copy and the product barrier
   for (int g = 0; g < a.nKC; ++g) {
     // the buffers are free once the previous chunk's MMAs completed
-    if (g > 0 && !mbar_wait(&bars[1], (g - 1) & 1)) atomicOr(s_err, 1);
+    if (g > 0 && !mbar_wait(&bars[1], (g - 1) & 1, a.wait_limit)) atomicOr(s_err, 1);
     __syncthreads();
     ok = (*s_err == 0);
     if (!ok) break;   // uniform: every thread read s_err after the same barrier
-    if (tid == 0)
+    if (tid == 0) {
       bulk_load(As, a.A + ((long long)(mt * a.nKC + g) * 2) * kTileBytes, 2 * kTileBytes,
                 &bars[0]);
+      ++nl;
+    }
     // B chunk: item i = (row nn, 16-byte segment sg) holds cps complex k of column n0 + nn;
     // consecutive threads take consecutive columns (coalesced loads), each batch issues all its
     // loads before the splits, and every segment goes to shared memory as one 16-byte store
@@ -504,7 +531,7 @@ __global__ __launch_bounds__(256) void k_tc_axis(TcAxisArgs a) {
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
-      if (!mbar_wait(&bars[0], g & 1)) {
+      if (!mbar_wait(&bars[0], g & 1, a.wait_limit)) {
         atomicOr(s_err, 1);
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -521,10 +548,11 @@ __global__ __launch_bounds__(256) void k_tc_axis(TcAxisArgs a) {
           mma<E>(tmem, al, bh, id_mma, 1u);
         }
         mma_commit(&bars[1]);
+        ++nm;
       }
     }
   }
-  if (ok && !mbar_wait(&bars[1], (a.nKC - 1) & 1)) atomicOr(s_err, 1);
+  if (ok && !mbar_wait(&bars[1], (a.nKC - 1) & 1, a.wait_limit)) atomicOr(s_err, 1);
   __syncthreads();
   ok = (*s_err == 0);
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -544,7 +572,12 @@ __global__ __launch_bounds__(256) void k_tc_axis(TcAxisArgs a) {
       }
     }
   } else if (tid == 0) {
+    // a wait gave up: report it, then let the copy and the products in flight finish (the
+    // last issued phase of each barrier, with the default limit) before tensor memory is
+    // released
     atomicExch(a.err, 1);
+    if (nl > 0) mbar_wait(&bars[0], (nl - 1) & 1);
+    if (nm > 0) mbar_wait(&bars[1], (nm - 1) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -673,6 +706,8 @@ int launch_tc_axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits,
   a.tmem_cols = (uint32_t)std::max(32, NT);
   a.done = done;
   a.err = &c->d_status->timeout;
+  a.wait_limit = c->opt.wait_limit > 0 ? (long)c->opt.wait_limit : kWaitLimit;
+  a.stall = c->opt.stall_test;
   const size_t smem = 2 * kTileBytes + 2 * (size_t)NT * kChunkBytes + 64;
   dim3 grid((N + NT - 1) / NT, ax.nMT, batch);
   if (c->opt.precision == RF_PREC_SPLIT_BF16)
@@ -731,6 +766,8 @@ int launch_tc_row(rf_ctx* c, const int* done) {
   a.law = c->law;
   a.done = done;
   a.err = &c->d_status->timeout;
+  a.wait_limit = c->opt.wait_limit > 0 ? (long)c->opt.wait_limit : tc::kWaitLimit;
+  a.stall = c->opt.stall_test;
   const bool bf = c->opt.precision == RF_PREC_SPLIT_BF16;
   const bool pl = c->has_plastic;
   if (c->nc == 3) {

@@ -37,7 +37,8 @@ class rf_options(C.Structure):
                 ("ref_medium", C.c_int32), ("precision", C.c_int32), ("check_every", C.c_int32),
                 ("transform", C.c_int32), ("fft_rows", C.c_int32), ("fft_cols", C.c_int32),
                 ("fft_fuse", C.c_int32), ("fft_fuse_kx", C.c_int32),
-                ("fft_row_blocks", C.c_int32)]
+                ("fft_row_blocks", C.c_int32), ("wait_limit", C.c_int64),
+                ("stall_test", C.c_int32), ("reserved", C.c_int32)]
 
 
 class rf_info(C.Structure):
@@ -197,7 +198,7 @@ def make_phases(table) -> C.Array:
 
 def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
                  check_every=0, transform="dft", fft_rows=0, fft_cols=0, fft_fuse=0,
-                 fft_fuse_kx=0, fft_row_blocks=0) -> rf_options:
+                 fft_fuse_kx=0, fft_row_blocks=0, wait_limit=0, stall_test=0) -> rf_options:
     o = rf_options()
     o.tol, o.max_iter = float(tol), int(max_iter)
     o.green, o.ref_medium = GREEN[green], REF[ref]
@@ -206,6 +207,7 @@ def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precisi
     o.fft_rows, o.fft_cols = int(fft_rows), int(fft_cols)
     o.fft_fuse, o.fft_fuse_kx = int(fft_fuse), int(fft_fuse_kx)
     o.fft_row_blocks = int(fft_row_blocks)
+    o.wait_limit, o.stall_test = int(wait_limit), int(stall_test)
     return o
 
 
@@ -392,11 +394,13 @@ class BatchSolver:
         return dict(sigma_bar=sbar, iters=its, residuals=res, status=st, converged=code == RF_OK)
 
     def rf_batch_info(self) -> dict:
+        """kernel_launches, rows_per_item for the size classes (largest side <= 64, 96, 128,
+        192, larger), persistent grid size."""
         n = C.c_int64(0)
-        r = C.c_int32(0)
+        r = np.zeros(5, np.int32)
         g = C.c_int32(0)
-        _check(lib.rf_batch_info(self.b, C.byref(n), C.byref(r), C.byref(g)), allow_nc=False)
-        return dict(kernel_launches=n.value, rows_per_item=r.value, grid=g.value)
+        _check(lib.rf_batch_info(self.b, C.byref(n), _ptr(r), C.byref(g)), allow_nc=False)
+        return dict(kernel_launches=n.value, rows_per_item=[int(x) for x in r], grid=g.value)
 
 
     # --- learned warm start hooks (include/rf_mlp.h); device buffers are torch CUDA tensors

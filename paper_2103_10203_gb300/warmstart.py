@@ -82,7 +82,7 @@ def _generate(net, phase_maps, macros, pats, phases, tol, max_iter, chunk, inclu
     for c0 in range(0, len(phase_maps), chunk):
         sl = slice(c0, c0 + chunk)
         b = rf.BatchSolver(phase_maps[sl], phases, pats[sl], stream=stream, tol=tol,
-                           max_iter=max_iter, transform="dft")
+                           max_iter=max_iter, transform="fft")
         m = np.asarray(macros[sl])
         out = b.rf_batch_solve(m)
         x, slots = b.rf_batch_descriptors(inclusion_phase, rve_base=c0)
@@ -168,7 +168,7 @@ def _evaluate(net, phase_maps, macros, pats, phases, tol, max_iter, inclusion_ph
     import torch
     stream = net.stream.cuda_stream
     b = rf.BatchSolver(phase_maps, phases, pats, stream=stream, tol=tol, max_iter=max_iter,
-                       transform="dft")
+                       transform="fft")
     m = np.asarray(macros)
     d_macro = torch.as_tensor(m, dtype=torch.float64, device="cuda")
     _, off = b.rf_batch_slots()

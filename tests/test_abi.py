@@ -120,3 +120,26 @@ def test_network_and_batch_hooks_reject_invalid_arguments_on_the_host(rf):
     assert rf.lib.rf_batch_reduced_strain(None, None) == -1
     assert rf.lib.rf_batch_solve_warm(None, None, None, None, None, None, None) == -1
     assert rf.lib.rf_mlp_destroy(None) == 0
+
+
+def test_non_finite_moduli_are_rejected_on_the_host(rf):
+    """NaN or infinite moduli give RF_ERR_NONFINITE before any device work (single context and
+    batch)."""
+    from synth import phase_table
+    pm = np.zeros((8, 8), np.uint8)
+    for bad in ([(np.nan, 1.0, 0, 0, 0)], [(1.0, np.inf, 0, 0, 0)], [(1.0, 1.0, np.nan, 1.0, 1)]):
+        code, ctx = _create(rf, pm, phase_table(bad))
+        assert code == -3 and not ctx.value
+        assert b"finite" in rf.lib.rf_last_error()
+    g = (rf.rf_grid * 1)(rf.make_grid(pm.shape))
+    pat = np.zeros((1, 3), np.int32)
+    pm_ptrs = (C.c_void_p * 1)(pm.ctypes.data)
+    pat_ptrs = (C.c_void_p * 1)(pat.ctypes.data)
+    Ks = np.ones(1, np.int64)
+    opts = rf.make_options()
+    b = C.c_void_p()
+    ph = rf.make_phases(phase_table([(np.nan, 1.0, 0, 0, 0)]))
+    code = rf.lib.rf_batch_create(C.byref(b), 1, g, C.cast(pm_ptrs, C.c_void_p), 1, ph,
+                                  C.cast(pat_ptrs, C.c_void_p), C.c_void_p(Ks.ctypes.data),
+                                  C.byref(opts), None)
+    assert code == -3 and not b.value

@@ -31,15 +31,17 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def test_batch_matches_single_solves(lib):
+@pytest.mark.parametrize("transform", ["dft", "fft"])
+def test_batch_matches_single_solves(lib, transform):
     ph = elastic_phases()
     pms, pats, macros = population(14)
-    b = lib.BatchSolver(pms, ph, pats, tol=1e-6, max_iter=2000)
+    b = lib.BatchSolver(pms, ph, pats, tol=1e-6, max_iter=2000, transform=transform)
     out = b.rf_batch_solve(macros)
     info = b.rf_batch_info()
     b.close()
     assert out["converged"] and np.all(out["status"] == 0)
-    assert info["rows_per_item"] in (1, 2, 4, 8) and info["grid"] > 0
+    assert len(info["rows_per_item"]) == 5 and info["grid"] > 0
+    assert all(r in (1, 2, 4, 8) for r in info["rows_per_item"])
     for i, (pm, pat) in enumerate(zip(pms, pats)):
         s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=2000)
         one = s.rf_solve(macros[i])
@@ -48,10 +50,11 @@ def test_batch_matches_single_solves(lib):
         assert rel(out["sigma_bar"][i], one["sigma_bar"]) <= 2e-6, i
 
 
-def test_batch_matches_oracle_at_fixed_update_counts(lib):
+@pytest.mark.parametrize("transform", ["dft", "fft"])
+def test_batch_matches_oracle_at_fixed_update_counts(lib, transform):
     ph = elastic_phases()
     pms, pats, macros = population(9, seed0=300)
-    b = lib.BatchSolver(pms, ph, pats, tol=0.0, max_iter=5)
+    b = lib.BatchSolver(pms, ph, pats, tol=0.0, max_iter=5, transform=transform)
     out = b.rf_batch_solve(macros)
     b.close()
     assert np.all(out["iters"] == 5) and np.all(out["status"] == 1)
@@ -94,3 +97,72 @@ def test_batch_rejects_plastic_phases_and_bad_patterns(lib):
     bad = [pats[0][1:], pats[1]]
     with pytest.raises(lib.RFError):
         lib.BatchSolver(pms, elastic_phases(), bad)
+
+
+def half_order(pat):
+    """The batch's slot order of one RVE: pattern frequencies with kx >= 0, sorted by (kx, ky)."""
+    return sorted((int(k[0]), int(k[1])) for k in pat if k[0] >= 0)
+
+
+@pytest.mark.parametrize("transform", ["fft", "dft"])
+def test_batch_reduced_coefficients_match_oracle_at_full_sizes(lib, transform):
+    """Sides 64, 96, 128, 192 and 256 (the FE-FFT population's sizes: radix-2 and radix-3 FFT
+    items along x and y, or pruned-DFT items), a fixed number of updates, every reduced strain
+    coefficient compared with the oracle's (relative L2 per RVE <= 1e-5), and the homogenised
+    stress (<= 1e-6)."""
+    ph = elastic_phases()
+    pms, pats, macros = [], [], []
+    for i, side in enumerate((64, 96, 128, 192, 256)):
+        c = make_config("c4", n=side, index=i)
+        pms.append(c["phase_map"])
+        pats.append(lib.rf_pattern_adapted(c["phase_map"], 1, c["k_target"]))
+        macros.append(c["macro"])
+    macros = np.array(macros)
+    b = lib.BatchSolver(pms, ph, pats, tol=0.0, max_iter=4, transform=transform)
+    out = b.rf_batch_solve(macros)
+    coeffs = b.rf_batch_reduced_strain().cpu().numpy()
+    _, off = b.rf_batch_slots()
+    b.close()
+    assert np.all(out["iters"] == 4)
+    for i, (pm, pat) in enumerate(zip(pms, pats)):
+        r = O.solve(pm, ph, macros[i], pat, tol=0.0, max_iter=4)
+        at = {(int(k[0]), int(k[1])): p for p, k in enumerate(pat)}
+        hs = half_order(pat)
+        assert off[i + 1] - off[i] == len(hs)
+        want = np.array([[r.eps_hat[at[k], 0, 0], r.eps_hat[at[k], 1, 1], r.eps_hat[at[k], 0, 1]]
+                         for k in hs])
+        got = coeffs[off[i]:off[i + 1], :, 0] + 1j * coeffs[off[i]:off[i + 1], :, 1]
+        assert rel(got, want) <= 1e-5, (i, rel(got, want))
+        assert rel(out["sigma_bar"][i], r.sigma_bar) <= 1e-6, i
+
+
+def test_batch_reports_divergence_and_non_finite_input(lib):
+    """A reference medium from volume averages with a stiff minority phase (contrast 1000 at
+    5 % volume) violates the contraction condition of the basic scheme: the measure grows by
+    about 11x per update (the oracle shows it) and the RVE ends with RF_ERR_DIVERGED, while a
+    homogeneous RVE beside it converges. A NaN macroscopic strain is rejected with
+    RF_ERR_NONFINITE."""
+    from synth import phase_table
+    ph = phase_table([(1.0, 1.0, 0, 0, 0), (1000.0, 1000.0, 0, 0, 0)])
+    good = np.zeros((32, 32), np.uint8)
+    bad = np.zeros((32, 32), np.uint8)
+    bad[10:17, 12:19] = 1                          # about 5 % stiff phase
+    pats = [O.pattern_adapted(pm, 1, k_target(0.1, pm.size)) for pm in (good, bad)]
+    macro = np.array([[0.01, 0, 0, 0, 0, 0.002]] * 2)
+    r = O.solve(bad, ph, macro[1], pats[1], tol=0.0, max_iter=6, ref="volume",
+                keep_history=True)
+    assert r.history[-1] > 1e4 * min(r.history)
+    b = lib.BatchSolver([good, bad], ph, pats, tol=1e-6, max_iter=500, ref="volume",
+                        transform="fft")
+    out = b.rf_batch_solve(macro)
+    assert out["status"][0] == 0 and out["status"][1] == -4 and not out["converged"]
+    assert out["iters"][1] < 20
+    with pytest.raises(lib.RFError) as e:
+        b.rf_batch_solve(np.array([[np.nan, 0, 0, 0, 0, 0], [0.01, 0, 0, 0, 0, 0]]))
+    assert e.value.code == -3
+    b.close()
+    s = lib.Solver(bad, ph, pattern=pats[1], tol=1e-6, max_iter=500, ref="volume")
+    with pytest.raises(lib.RFError) as e:
+        s.rf_solve(macro[1])
+    assert e.value.code == -4
+    s.close()

@@ -585,6 +585,51 @@ def test_fft_full_size_c3_first_iterations(lib):
     assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
 
 
+def test_fft_full_size_c2_load_path_with_commits(lib):
+    """The 1024^2 J2 composite in the bench's launch configuration (FFT mode, autotuned tiles)
+    over three increments into the plastic range (0.5 %, 1 %, 1.5 %), three updates each, with
+    the internal variables committed after each increment: homogenised stress per increment
+    (<= 1e-6), strain field (<= 1e-5) and accumulated plastic strain (<= 1e-4) against the
+    oracle replaying the same update counts."""
+    cfg = make_config("c2")
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    path = cfg["path"][[4, 9, 14]]
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft")
+    out = s.rf_solve_path(path)
+    eps, _, alpha = s.rf_get_fields()
+    s.close()
+    assert list(out["iters"]) == [3, 3, 3]
+    sbar_ref, _, r = O.solve_path(pm, ph, path, pat, fixed_iters=[3, 3, 3])
+    for n in range(len(path)):
+        assert rel(out["sigma_bar"][n], sbar_ref[n]) <= SBAR_TOL, n
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert alpha.max() > 0 and rel(alpha, r.alpha[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "split_tf32"])
+def test_split_precision_full_size_c3(lib, prec):
+    """128^3 elastic spheres, K = 2 % adapted, all transforms on the tensor cores with split
+    operands (the bench's c3 configuration), two updates: strain, stress, reduced coefficients
+    and homogenised stress against the oracle at the split-mode tolerance (3e-5, derived above);
+    the measured errors are printed for the record."""
+    cfg = make_config("c3")
+    pm, ph, macro = cfg["phase_map"], cfg["phases"], cfg["macro"]
+    pat = lib.rf_pattern_adapted(pm, 1, cfg["k_target"])
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=2, precision=prec)
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    coeffs = s.rf_get_reduced_strain()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=2)
+    want = np.stack([r.eps_hat[:, i, j] for (i, j) in VOIGT], axis=1)
+    errs = dict(eps=rel(eps, vec6_field(r.eps)), sig=rel(sig, vec6_field(r.sigma)),
+                coeffs=rel(coeffs[..., 0] + 1j * coeffs[..., 1], want),
+                sbar=rel(out["sigma_bar"], r.sigma_bar))
+    print(prec, errs)
+    assert all(v <= SPLIT_TOL for v in errs.values()), errs
+
+
 def test_fft_transform_rejects_unsupported_sizes(lib):
     pm = np.zeros((24, 40), np.uint8)        # 40 = 5 * 8
     with pytest.raises(lib.RFError):
