@@ -240,6 +240,22 @@ int rf_set_tracing(rf_ctx* ctx, int on);
 int rf_get_stage_times(const rf_ctx* ctx, double ms_total[8], int64_t counts[8]);
 int rf_reset_stage_times(rf_ctx* ctx);
 
+/* Compatibility step (Sec. 5.1, also applied in Sec. 5.2 and 5.3): the Lippmann-Schwinger
+ * equation solved once on the full set of frequencies from the fields of the last reduced solve.
+ * Reading: one update of the basic scheme with every frequency of the grid, starting from the
+ * reduced strain field (its coefficients on the pattern; all other frequencies zero):
+ *   tau = sigma(eps) - C0 : eps, eps_c^(xi) = -Gamma0(xi) : tau^(xi) for xi != 0,
+ *   eps_c^(0) = N ebar (ebar of the last solve or increment), 0 at null frequencies,
+ * then sigma_c = sigma(eps_c), with the internal variables the context holds (after
+ * rf_solve_path: those committed for its last increment; nothing is committed here).
+ * The context's fields (rf_get_fields) are replaced by eps_c, sigma_c; hom_stress (nullable)
+ * receives the volume average of sigma_c. The reduced coefficients and the load-path state are
+ * unchanged. The first call builds a second context on the same grid with the full set of
+ * frequencies (FFT transforms when the sides are 2^b or 3 * 2^b, else the pruned DFT) and keeps
+ * it until the phase map changes or the context is destroyed.
+ * Errors: RF_ERR_STATE if no solve has produced fields yet; RF_ERR_OOM; RF_ERR_NONFINITE. */
+int rf_compat(rf_ctx* ctx, double hom_stress[6]);
+
 /* Destroy a context and free its device memory. NULL is accepted. */
 int rf_destroy(rf_ctx* ctx);
 

@@ -21,7 +21,9 @@ from .rf_oracle import (  # noqa: F401
     inverse_reduced,
     isotropic_stiffness,
     SolveResult,
+    compat,
     errors,
+    full_pattern,
     green_operator,
     law,
     pattern_adapted,

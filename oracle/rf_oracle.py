@@ -358,6 +358,42 @@ def solve_path(phase_map, phases, path, pattern, tol=1e-6, max_iter=1000, scheme
     return sbar, iters, res
 
 
+def full_pattern(shape_zyx) -> np.ndarray:
+    """Every frequency of the grid (the unreduced set), int [N, 3] as (kx, ky, kz)."""
+    kx, ky, kz = _signed_grid(shape_zyx)
+    return np.stack([kx.ravel(), ky.ravel(), kz.ravel()], axis=1).astype(np.int64)
+
+
+def compat(phase_map, phases, eps, macro_strain, scheme="rotated", ref="minmax", eps_p=None,
+           alpha=None):
+    """Compatibility step (Sec. 5.1): the Lippmann-Schwinger equation solved once on the full set
+    of frequencies from the fields of a reduced solve. Reading: one update of the basic scheme
+    with every frequency (steps a-d of Sec. 4 with the unreduced set), starting from the reduced
+    strain field `eps` [Nz,Ny,Nx,3,3] with the internal variables (eps_p, alpha) held fixed:
+        tau = sigma(eps) - C0 : eps,  eps_c^(xi) = -Gamma0(xi) : tau^(xi) (xi != 0),
+        eps_c^(0) = N ebar, 0 at null frequencies,
+    then sigma_c = sigma(eps_c). Returns (eps_c, sigma_c, sigma_bar_c)."""
+    pm = _as_grid(phase_map)
+    nz, ny, nx = pm.shape
+    N = pm.size
+    ebar = vec6_to_tensor(macro_strain)
+    lam, mu, sy, H, plastic = _materials(phases, pm)
+    lam0, mu0 = reference_medium(phases, pm, ref)
+    full = full_pattern(pm.shape)
+    q, null = wave_vector(full, (nx, ny, nz), scheme)
+    Gam = green_operator(q, lam0, mu0)
+    eps = np.asarray(eps, float).reshape(nz, ny, nx, 3, 3)
+    sigma, _, _, _ = law(eps, lam, mu, sy, H, plastic, eps_p, alpha)
+    tau = sigma - _c0_apply(eps, lam0, mu0)
+    th = forward_reduced(tau, full)
+    eh = -np.einsum("kijab,kab->kij", Gam, th)
+    eh[null] = 0.0
+    eh[np.all(full == 0, axis=1)] = N * ebar
+    eps_c = inverse_reduced(eh, full, pm.shape)
+    sigma_c, _, _, _ = law(eps_c, lam, mu, sy, H, plastic, eps_p, alpha)
+    return eps_c, sigma_c, tensor_to_vec6(sigma_c.reshape(-1, 3, 3).mean(axis=0))
+
+
 # --------------------------------------------------------------------------- patterns
 def _signed_grid(shape_zyx):
     nz, ny, nx = shape_zyx

@@ -537,6 +537,8 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
 int rf_set_phase_map(rf_ctx* c, const uint8_t* pm) {
   if (!c || !pm) return invalid("rf_set_phase_map: null argument");
   DeviceGuard dg(c->dev);
+  rf_destroy(c->compat);   // the full-set context holds the old phase map
+  c->compat = nullptr;
   if (int e = ck(cudaMemcpyAsync(c->d_phase, pm, c->N, cudaMemcpyHostToDevice, c->stream),
                  "upload phase map"))
     return e;
@@ -548,6 +550,8 @@ int rf_set_phase_map(rf_ctx* c, const uint8_t* pm) {
 int rf_set_phase_map_device(rf_ctx* c, const uint8_t* d_pm) {
   if (!c || !d_pm) return invalid("rf_set_phase_map_device: null argument");
   DeviceGuard dg(c->dev);
+  rf_destroy(c->compat);
+  c->compat = nullptr;
   if (int e = ck(cudaMemcpyAsync(c->d_phase, d_pm, c->N, cudaMemcpyDeviceToDevice, c->stream),
                  "copy phase map"))
     return e;
@@ -1048,6 +1052,8 @@ int rf_reset_stage_times(rf_ctx* c) {
 int rf_destroy(rf_ctx* c) {
   if (!c) return RF_OK;
   DeviceGuard dg(c->dev);
+  rf_destroy(c->compat);
+  c->compat = nullptr;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   trace_collect(c, 0);
@@ -1070,6 +1076,85 @@ int rf_destroy(rf_ctx* c) {
   if (c->h_sbar) cudaFreeHost(c->h_sbar);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+  return RF_OK;
+}
+
+int rf_compat(rf_ctx* c, double hom_stress[6]) {
+  if (!c) return invalid("rf_compat: null context");
+  if (!c->have_pattern || !c->fields_valid) {
+    set_error("rf_compat: no solve has produced a reduced solution yet");
+    return RF_ERR_STATE;
+  }
+  DeviceGuard dg(c->dev);
+  if (!c->compat) {
+    // the full set of frequencies on the same grid, phases and Green operator; FFT transforms
+    // where the sizes allow, one update per solve
+    std::vector<uint8_t> pm((size_t)c->N);
+    if (int e = ck(cudaMemcpyAsync(pm.data(), c->d_phase, c->N, cudaMemcpyDeviceToHost,
+                                   c->stream), "compat: phase map"))
+      return e;
+    if (int e = ck(cudaStreamSynchronize(c->stream), "compat: phase map")) return e;
+    auto fft_ok = [](int v) {
+      const int p = (v % 3 == 0) ? v / 3 : v;
+      return v >= 2 && (p & (p - 1)) == 0;
+    };
+    rf_options o{};
+    o.tol = 0.0;
+    o.max_iter = 1;
+    o.green = c->opt.green;
+    o.ref_medium = c->opt.ref_medium;
+    o.precision = RF_PREC_FP32;
+    o.transform = (fft_ok(c->nx) && fft_ok(c->ny) && (c->dim == 2 || fft_ok(c->nz)))
+                      ? RF_TRANSFORM_FFT : RF_TRANSFORM_DFT;
+    const rf_grid g{c->dim, {c->nx, c->ny, c->nz}};
+    rf_ctx* f = nullptr;
+    if (int e = rf_create(&f, &g, c->n_phases, c->phases, pm.data(), &o, c->stream)) return e;
+    std::vector<int32_t> full((size_t)3 * c->N);
+    long long p = 0;
+    for (int iz = 0; iz < c->nz; ++iz)
+      for (int iy = 0; iy < c->ny; ++iy)
+        for (int ix = 0; ix < c->nx; ++ix, ++p) {
+          full[3 * p] = ix - (c->nx - 1) / 2;
+          full[3 * p + 1] = iy - (c->ny - 1) / 2;
+          full[3 * p + 2] = iz - (c->nz - 1) / 2;
+        }
+    if (int e = rf_set_pattern(f, full.data(), c->N)) {
+      std::string keep = g_err;
+      rf_destroy(f);
+      g_err = keep;
+      return e;
+    }
+    c->compat = f;
+  }
+  rf_ctx* f = c->compat;
+  DeviceGuard dg2(f->dev);
+  if (c->ns && f->ns)
+    if (int e = ck(cudaMemcpyAsync(f->d_state, c->d_state, sizeof(float) * c->ns * c->N,
+                                   cudaMemcpyDeviceToDevice, c->stream), "compat: state"))
+      return e;
+  if (int e = ck(cudaMemsetAsync(f->d_ER, 0, sizeof(float2) * f->rect, c->stream), "compat"))
+    return e;
+  if (int e = launch_scatter_full(c, f)) return e;
+  if (int e = init_status(f, c->prev_macro)) return e;
+  const int st = run_iterations(f);
+  if (st < 0) return st;
+  double sbar[6];
+  if (int e = finish(f, 0, sbar)) return e;
+  const size_t n6 = sizeof(float) * 6 * (size_t)c->N;
+  if (int e = ck(cudaMemcpyAsync(c->d_eps, f->d_eps, n6, cudaMemcpyDeviceToDevice, c->stream),
+                 "compat: fields"))
+    return e;
+  if (int e = ck(cudaMemcpyAsync(c->d_sig, f->d_sig, n6, cudaMemcpyDeviceToDevice, c->stream),
+                 "compat: fields"))
+    return e;
+  if (int e = ck(cudaMemcpyAsync(c->d_alpha, f->d_alpha, sizeof(float) * c->N,
+                                 cudaMemcpyDeviceToDevice, c->stream), "compat: fields"))
+    return e;
+  if (int e = ck(cudaStreamSynchronize(c->stream), "compat")) return e;
+  c->launches += f->launches;
+  f->launches = 0;
+  if (hom_stress)
+    for (int i = 0; i < 6; ++i) hom_stress[i] = sbar[i];
   return RF_OK;
 }
 

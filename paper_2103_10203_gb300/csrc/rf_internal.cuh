@@ -232,6 +232,10 @@ struct rf_ctx {
   // load-path state
   double prev_macro[6] = {0, 0, 0, 0, 0, 0};
 
+  // compatibility step: a context on the same grid with the full set of frequencies (created
+  // by the first rf_compat, dropped when the phase map changes)
+  rf_ctx* compat = nullptr;
+
   // CUDA graphs of update chunks (replayed instead of per-kernel launches)
   struct TraceIter;
   struct GraphEntry {
@@ -386,6 +390,7 @@ int launch_hinfo(rf_ctx* c, const int* d_hk, long long Kh);
 int launch_reset_er(rf_ctx* c, const double* ebar6, double scale_old);
 int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* ebar6);
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist);
+int launch_scatter_full(rf_ctx* c, rf_ctx* full);
 long long zero_base(const rf_ctx* c);
 // rf_tc.cu
 int tc_setup(rf_ctx* c);

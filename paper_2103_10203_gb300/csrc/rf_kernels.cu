@@ -531,6 +531,40 @@ int launch_gather_jentries(rf_ctx* c) {
   return launch_check(c, "gather entries");
 }
 
+// Coefficients of a reduced context scattered into the rectangle of a full-set context on the
+// same grid (whose distinct values are kx = 0..Nx/2, every ky and kz in signed order); the full
+// rectangle is zeroed first by the caller.
+template <int NC>
+__global__ void k_scatter_full(const float2* ER, const HIdx* hidx, const int* kxv, const int* kym,
+                               const int* kzm, long long Kh, int Kx, int Ky, int nx, int ny, int nz,
+                               int fKx, int fKy, float2* fER) {
+  const long long h = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (h >= Kh) return;
+  const HIdx hi = hidx[h];
+  const int kx = kxv[hi.j];
+  const int ky = kym[hi.iy] <= ny / 2 ? kym[hi.iy] : kym[hi.iy] - ny;
+  const int kz = kzm[hi.iz] <= nz / 2 ? kzm[hi.iz] : kzm[hi.iz] - nz;
+  const long long src = ((long long)(hi.iz * Ky + hi.iy) * NC) * Kx + hi.j;
+  const long long dst =
+      ((long long)((kz + (nz - 1) / 2) * fKy + (ky + (ny - 1) / 2)) * NC) * fKx + kx;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) fER[dst + (long long)c * fKx] = ER[src + (long long)c * Kx];
+  (void)nx;
+}
+
+int launch_scatter_full(rf_ctx* c, rf_ctx* f) {
+  const unsigned gb = (unsigned)((c->Kh + 255) / 256);
+  if (c->nc == 3)
+    k_scatter_full<3><<<gb, 256, 0, c->stream>>>(c->d_ER, c->d_hidx, c->d_kx, c->d_kym, c->d_kzm,
+                                                 c->Kh, c->Kx, c->Ky, c->nx, c->ny, c->nz, f->Kx,
+                                                 f->Ky, f->d_ER);
+  else
+    k_scatter_full<6><<<gb, 256, 0, c->stream>>>(c->d_ER, c->d_hidx, c->d_kx, c->d_kym, c->d_kzm,
+                                                 c->Kh, c->Kx, c->Ky, c->nx, c->ny, c->nz, f->Kx,
+                                                 f->Ky, f->d_ER);
+  return launch_check(c, "scatter to the full set");
+}
+
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist) {
   k_phase_hist<<<304, 256, 0, c->stream>>>(c->d_phase, c->N, d_hist);
   return launch_check(c, "phase_hist");

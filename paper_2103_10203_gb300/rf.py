@@ -94,6 +94,7 @@ def _load() -> C.CDLL:
         "rf_set_state": [P, P, C.c_size_t],
         "rf_get_info": [P, C.POINTER(rf_info)],
         "rf_destroy": [P],
+        "rf_compat": [P, P],
         "rf_pattern_adapted": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_adapted_noalloc": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64),
@@ -144,7 +145,7 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc",
             "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy",
             "rf_batch_slots", "rf_batch_descriptors", "rf_batch_reduced_strain",
-            "rf_batch_solve_warm",
+            "rf_batch_solve_warm", "rf_compat",
             "rf_mlp_create", "rf_mlp_get_dims", "rf_mlp_set_params", "rf_mlp_get_params",
             "rf_mlp_get_grads", "rf_mlp_forward", "rf_mlp_targets", "rf_mlp_loss_grad",
             "rf_mlp_adam", "rf_mlp_train_step", "rf_mlp_predict_warm", "rf_mlp_launches",
@@ -300,6 +301,13 @@ class Solver:
         res = np.zeros(n)
         code = _check(lib.rf_solve_path(self.ctx, n, _ptr(p), _ptr(sbar), _ptr(its), _ptr(res)))
         return dict(sigma_bar=sbar, iters=its, residuals=res, converged=code == RF_OK)
+
+    def rf_compat(self):
+        """Compatibility step (one full-set update from the last reduced solve); the fields
+        of rf_get_fields become the step's. Returns the homogenised stress [6]."""
+        sbar = np.zeros(6)
+        _check(lib.rf_compat(self.ctx, _ptr(sbar)), allow_nc=False)
+        return sbar
 
     def rf_reset_path(self):
         _check(lib.rf_reset_path(self.ctx), allow_nc=False)

@@ -531,3 +531,59 @@ def test_reference_medium_fixes_the_contraction_ratio():
     h = np.array(r.history)
     assert np.allclose(h[2:8] / h[1:7], rho * abs(1 - 2 * f), rtol=1e-9)
     assert O.reference_medium(TWO_PHASE, pm) == (0.5 * sum(TWO_PHASE["lam"]), 0.5 * sum(mu))
+
+
+# ----------------------------------------------------------------------------- compatibility step
+def test_compat_step_leaves_a_full_set_solution_unchanged():
+    """The converged solution on the full set of frequencies is a fixed point of the full-set
+    update, so the compatibility step (one full-set update, Sec. 5.1) must return it unchanged
+    (elastic and J2 with frozen internal variables)."""
+    from synth.configs import j2_phases
+    pm = random_discs(16, (2.0, 4.0), 0.35, seed=3)
+    for ph, ebar in ((TWO_PHASE, np.array([0.01, -0.004, 0, 0, 0, 0.003])),
+                     (j2_phases(), np.array([0.02, 0, 0, 0, 0, 0.004]))):
+        full = O.full_pattern(_as_grid(pm).shape)
+        assert len(full) == pm.size
+        r = O.solve(pm, ph, ebar, full, tol=1e-13, max_iter=20000)
+        assert r.converged
+        eps_c, sig_c, sbar_c = O.compat(pm, ph, r.eps, ebar)
+        assert np.allclose(eps_c, r.eps, rtol=0, atol=1e-11 * np.abs(r.eps).max())
+        assert np.allclose(sbar_c, r.sigma_bar, rtol=1e-10, atol=1e-14)
+
+
+def test_compat_step_output_is_compatible_with_the_macro_strain():
+    """The step's strain field has mean ebar and, at every nonzero frequency with a nonzero
+    wave vector, lies in the range of the compatible projector Gamma0 C0 (closed form above):
+    eps^(xi) = sym(q (x) u) for some u."""
+    pm = centred_disc(12, 0.3)
+    ebar = np.array([0.01, 0.003, 0, 0, 0, -0.002])
+    pat = O.pattern_adapted(pm, 1, 19)
+    r = O.solve(pm, TWO_PHASE, ebar, pat, tol=1e-10)
+    eps_c, _, _ = O.compat(pm, TWO_PHASE, r.eps, ebar)
+    assert np.allclose(eps_c.reshape(-1, 3, 3).mean(axis=0), O.vec6_to_tensor(ebar), atol=1e-15)
+    g = _as_grid(pm)
+    full = O.full_pattern(g.shape)
+    q, null = O.wave_vector(full, (g.shape[2], g.shape[1], g.shape[0]))
+    lam0, mu0 = O.reference_medium(TWO_PHASE, pm)
+    Gcf = gamma_closed_form(q, lam0, mu0)
+    eh = O.forward_reduced(eps_c, full)
+    C0 = O.isotropic_stiffness(lam0, mu0)
+    for m in range(len(full)):
+        if null[m] or not np.any(full[m]):
+            continue
+        proj = np.einsum("ijab,abkl,kl->ij", Gcf[m], C0, eh[m])
+        assert np.allclose(proj, eh[m], atol=1e-12 * max(1.0, np.abs(eh).max()))
+
+
+def test_compat_step_on_a_laminate_gives_the_closed_form():
+    """For layers normal to x the reduced solution on the k_y = 0 axis is already exact; the
+    compatibility step must reproduce the laminate closed form (uniform sigma_11, sigma_12)."""
+    pm = laminate((6, 16), (5, 11))
+    ebar = np.array([0.01, -0.004, 0, 0, 0, 0.003])
+    pat = O.pattern_adapted(pm, 1, 16)
+    r = O.solve(pm, TWO_PHASE, ebar, pat, tol=1e-13, max_iter=5000)
+    _, sig_c, _ = O.compat(pm, TWO_PHASE, r.eps, ebar)
+    f = np.array([np.mean(pm == 0), np.mean(pm == 1)])
+    s11, s12, _, _, _ = laminate_closed_form(TWO_PHASE["lam"], TWO_PHASE["mu"], f, ebar)
+    assert np.allclose(sig_c[..., 0, 0], s11, rtol=1e-10)
+    assert np.allclose(sig_c[..., 0, 1], s12, rtol=1e-10)
