@@ -256,6 +256,16 @@ int rf_reset_stage_times(rf_ctx* ctx);
  * Errors: RF_ERR_STATE if no solve has produced fields yet; RF_ERR_OOM; RF_ERR_NONFINITE. */
 int rf_compat(rf_ctx* ctx, double hom_stress[6]);
 
+/* Error measures of Sec. 5 between the fields a context holds now (after a solve or
+ * rf_compat) and those of a reference context on the same grid and device (typically a solve
+ * with the full set of frequencies):
+ *   Ebar = |sbar - sbar_ref| / |sbar_ref|,
+ *   E    = (1/N) sum_x |sigma(x) - sigma_ref(x)| / |sigma_ref(x)|,
+ * Frobenius norms with both shear entries counted; voxels where |sigma_ref| = 0 add nothing.
+ * Computed on the device in FP64 on ctx's stream (ref's stream is synchronised first).
+ * Errors: RF_ERR_INVALID for different grids or devices; RF_ERR_STATE without fields. */
+int rf_stress_errors(rf_ctx* ctx, const rf_ctx* ref, double* Ebar, double* E);
+
 /* Destroy a context and free its device memory. NULL is accepted. */
 int rf_destroy(rf_ctx* ctx);
 

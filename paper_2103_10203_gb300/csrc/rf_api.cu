@@ -389,6 +389,7 @@ int finish(rf_ctx* c, int commit, double* sbar) {
       set_error("homogenised stress is not finite");
       return RF_ERR_NONFINITE;
     }
+    c->last_sbar[i] = c->h_sbar[i];
     if (sbar) sbar[i] = c->h_sbar[i];
   }
   return RF_OK;
@@ -515,6 +516,7 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (!err) err = dalloc(&c->d_eps, 6 * (size_t)N, "fields");
   if (!err) err = dalloc(&c->d_sig, 6 * (size_t)N, "fields");
   if (!err) err = dalloc(&c->d_alpha, (size_t)N, "fields");
+  if (!err) err = dalloc(&c->d_err, kErrBlocks + 2, "error partials");
   if (!err) err = ck(cudaMallocHost(&c->h_status, sizeof(Status)), "pinned");
   if (!err) err = ck(cudaMallocHost(&c->h_sbar, 8 * sizeof(double)), "pinned");
   if (!err)
@@ -1072,6 +1074,7 @@ int rf_destroy(rf_ctx* c) {
   dfree(c->d_eps);
   dfree(c->d_sig);
   dfree(c->d_alpha);
+  dfree(c->d_err);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_sbar) cudaFreeHost(c->h_sbar);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1153,8 +1156,31 @@ int rf_compat(rf_ctx* c, double hom_stress[6]) {
   if (int e = ck(cudaStreamSynchronize(c->stream), "compat")) return e;
   c->launches += f->launches;
   f->launches = 0;
+  for (int i = 0; i < 6; ++i) c->last_sbar[i] = sbar[i];
   if (hom_stress)
     for (int i = 0; i < 6; ++i) hom_stress[i] = sbar[i];
+  return RF_OK;
+}
+
+int rf_stress_errors(rf_ctx* c, const rf_ctx* ref, double* Ebar, double* E) {
+  if (!c || !ref || !Ebar || !E) return invalid("rf_stress_errors: null argument");
+  if (c->nx != ref->nx || c->ny != ref->ny || c->nz != ref->nz || c->dev != ref->dev)
+    return invalid("rf_stress_errors: contexts on different grids or devices");
+  if (!c->fields_valid || !ref->fields_valid) {
+    set_error("rf_stress_errors: both contexts need fields from a solve");
+    return RF_ERR_STATE;
+  }
+  DeviceGuard dg(c->dev);
+  if (ref->stream != c->stream)
+    if (int e = ck(cudaStreamSynchronize(ref->stream), "stress errors")) return e;
+  if (int e = launch_stress_errors(c, ref->d_sig, c->last_sbar, ref->last_sbar)) return e;
+  double out[2] = {0.0, 0.0};
+  if (int e = ck(cudaMemcpyAsync(out, c->d_err + kErrBlocks, sizeof out, cudaMemcpyDeviceToHost,
+                                 c->stream), "stress errors"))
+    return e;
+  if (int e = ck(cudaStreamSynchronize(c->stream), "stress errors")) return e;
+  *Ebar = out[0];
+  *E = out[1];
   return RF_OK;
 }
 

@@ -236,6 +236,9 @@ struct rf_ctx {
   // by the first rf_compat, dropped when the phase map changes)
   rf_ctx* compat = nullptr;
 
+  double last_sbar[6] = {0, 0, 0, 0, 0, 0};   // homogenised stress of the fields held now
+  double* d_err = nullptr;                    // [kErrBlocks + 2] partials of rf_stress_errors
+
   // CUDA graphs of update chunks (replayed instead of per-kernel launches)
   struct TraceIter;
   struct GraphEntry {
@@ -391,6 +394,9 @@ int launch_reset_er(rf_ctx* c, const double* ebar6, double scale_old);
 int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* ebar6);
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist);
 int launch_scatter_full(rf_ctx* c, rf_ctx* full);
+constexpr int kErrBlocks = 304;
+int launch_stress_errors(rf_ctx* c, const float* sig_ref, const double* sbar,
+                         const double* sbar_ref);
 long long zero_base(const rf_ctx* c);
 // rf_tc.cu
 int tc_setup(rf_ctx* c);

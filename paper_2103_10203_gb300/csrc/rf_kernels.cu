@@ -565,6 +565,58 @@ int launch_scatter_full(rf_ctx* c, rf_ctx* f) {
   return launch_check(c, "scatter to the full set");
 }
 
+// Error measures of Sec. 5 between two stress fields [6][N] (tensor shear components, counted
+// twice in the Frobenius norm): per block, the sum over its voxels of |sig - ref| / |ref| in FP64
+// (voxels with |ref| = 0 add nothing), in a fixed order.
+__global__ __launch_bounds__(256) void k_stress_err(const float* sig, const float* ref,
+                                                    long long N, double* part) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
+       g += (long long)gridDim.x * blockDim.x) {
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const double w = i < 3 ? 1.0 : 2.0;
+      const double r = ref[i * N + g], d = (double)sig[i * N + g] - r;
+      num += w * d * d;
+      den += w * r * r;
+    }
+    if (den > 0.0) acc += sqrt(num) / sqrt(den);
+  }
+  const double t = block_sum_d(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// E = sum of the block partials / N; Ebar from the two homogenised stresses. out[0] = Ebar,
+// out[1] = E.
+__global__ void k_stress_err_final(const double* part, int nb, long long N, double a0, double a1,
+                                   double a2, double a3, double a4, double a5, double r0,
+                                   double r1, double r2, double r3, double r4, double r5,
+                                   double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[b];
+  const double a[6] = {a0, a1, a2, a3, a4, a5}, r[6] = {r0, r1, r2, r3, r4, r5};
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < 6; ++i) {
+    const double w = i < 3 ? 1.0 : 2.0;
+    num += w * (a[i] - r[i]) * (a[i] - r[i]);
+    den += w * r[i] * r[i];
+  }
+  out[0] = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+  out[1] = s / (double)N;
+}
+
+int launch_stress_errors(rf_ctx* c, const float* sig_ref, const double* sb, const double* sr) {
+  k_stress_err<<<kErrBlocks, 256, 0, c->stream>>>(c->d_sig, sig_ref, c->N, c->d_err);
+  if (int e = launch_check(c, "stress errors")) return e;
+  k_stress_err_final<<<1, 32, 0, c->stream>>>(c->d_err, kErrBlocks, c->N, sb[0], sb[1], sb[2],
+                                              sb[3], sb[4], sb[5], sr[0], sr[1], sr[2], sr[3],
+                                              sr[4], sr[5], c->d_err + kErrBlocks);
+  return launch_check(c, "stress errors");
+}
+
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist) {
   k_phase_hist<<<304, 256, 0, c->stream>>>(c->d_phase, c->N, d_hist);
   return launch_check(c, "phase_hist");

@@ -95,6 +95,7 @@ def _load() -> C.CDLL:
         "rf_get_info": [P, C.POINTER(rf_info)],
         "rf_destroy": [P],
         "rf_compat": [P, P],
+        "rf_stress_errors": [P, P, P, P],
         "rf_pattern_adapted": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_adapted_noalloc": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64),
@@ -145,7 +146,7 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc",
             "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy",
             "rf_batch_slots", "rf_batch_descriptors", "rf_batch_reduced_strain",
-            "rf_batch_solve_warm", "rf_compat",
+            "rf_batch_solve_warm", "rf_compat", "rf_stress_errors",
             "rf_mlp_create", "rf_mlp_get_dims", "rf_mlp_set_params", "rf_mlp_get_params",
             "rf_mlp_get_grads", "rf_mlp_forward", "rf_mlp_targets", "rf_mlp_loss_grad",
             "rf_mlp_adam", "rf_mlp_train_step", "rf_mlp_predict_warm", "rf_mlp_launches",
@@ -308,6 +309,12 @@ class Solver:
         sbar = np.zeros(6)
         _check(lib.rf_compat(self.ctx, _ptr(sbar)), allow_nc=False)
         return sbar
+
+    def rf_stress_errors(self, ref: "Solver"):
+        """(Ebar, E) of Sec. 5 between this context's fields and those of `ref`."""
+        eb, e = C.c_double(0.0), C.c_double(0.0)
+        _check(lib.rf_stress_errors(self.ctx, ref.ctx, C.byref(eb), C.byref(e)), allow_nc=False)
+        return eb.value, e.value
 
     def rf_reset_path(self):
         _check(lib.rf_reset_path(self.ctx), allow_nc=False)

@@ -8,7 +8,10 @@ composites with several circular inclusions (Sec. 5.2).
 """
 
 from .microstructure import (  # noqa: F401
+    centred_annulus,
     centred_disc,
+    centred_ellipse,
+    centred_square,
     centred_sphere,
     laminate,
     random_discs,

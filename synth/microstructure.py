@@ -28,8 +28,38 @@ def centred_sphere(n: int, vf: float) -> np.ndarray:
     """One sphere centred in an n^3 cell, radius (3 vf n^3 / (4 pi))^(1/3) (Sec. 5.3 shape)."""
     c = (n - 1) / 2.0
     r = (3.0 * vf * n ** 3 / (4.0 * np.pi)) ** (1.0 / 3.0)
-    z, y, x = np.mgrid[0:n, 0:n, 0:n]
+    z, y, x = np.ogrid[0:n, 0:n, 0:n]
     return (((x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2) <= r * r).astype(np.uint8)
+
+
+def centred_annulus(n: int, vf: float, inner: float = 0.5) -> np.ndarray:
+    """One ring centred in an n x n cell (Sec. 5.1, annular inclusion): inner radius = `inner`
+    times the outer radius, ring area vf n^2."""
+    c = (n - 1) / 2.0
+    ro = np.sqrt(vf * n * n / (np.pi * (1.0 - inner * inner)))
+    ri = inner * ro
+    y, x = np.ogrid[0:n, 0:n]
+    d2 = (x - c) ** 2 + (y - c) ** 2
+    return ((d2 <= ro * ro) & (d2 > ri * ri)).astype(np.uint8)
+
+
+def centred_ellipse(n: int, vf: float, aspect: float = 2.0) -> np.ndarray:
+    """One ellipse centred in an n x n cell (Sec. 5.1, elliptical inclusion): semi-axis along x
+    `aspect` times the one along y, area vf n^2."""
+    c = (n - 1) / 2.0
+    b = np.sqrt(vf * n * n / (np.pi * aspect))
+    a = aspect * b
+    y, x = np.ogrid[0:n, 0:n]
+    return (((x - c) / a) ** 2 + ((y - c) / b) ** 2 <= 1.0).astype(np.uint8)
+
+
+def centred_square(n: int, vf: float) -> np.ndarray:
+    """One axis-aligned square centred in an n x n cell (Sec. 5.1, quadratic inclusion), side
+    sqrt(vf) n."""
+    c = (n - 1) / 2.0
+    h = 0.5 * np.sqrt(vf) * n
+    y, x = np.ogrid[0:n, 0:n]
+    return ((np.abs(x - c) <= h) & (np.abs(y - c) <= h)).astype(np.uint8)
 
 
 def laminate(shape: tuple, widths: tuple) -> np.ndarray:
