@@ -65,15 +65,20 @@ def parse():
                         "Green operator inside the inverse y kernel (2), or timed (0)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "paper"],
                    help="c2: 1024^2 J2 load path (the headline line); c3: 128^3 elastic spheres, "
                         "split-BF16 tensor-core transforms; c4: batch of 4096 RVEs of uneven size "
-                        "vs per-RVE solves; c5: learned warm start vs plain start")
+                        "vs per-RVE solves; c5: learned warm start vs plain start; paper: the "
+                        "pattern study on the paper-shaped inputs of Sec. 5 (256^2, 256^3)")
     p.add_argument("--rves", type=int, default=4096, help="c4 / c5: RVEs in the solved batch")
     p.add_argument("--train", type=int, default=50000, help="c5: training RVEs")
     p.add_argument("--epochs", type=int, default=20, help="c5: training epochs")
     p.add_argument("--profile-updates", type=int, default=0,
                    help="run only this many updates of the first increment (for ncu captures)")
+    p.add_argument("--no-study", action="store_true",
+                   help="c2: skip the pattern study (K = 1/5/10 %%, adapted vs radial vs full set)")
+    p.add_argument("--no-sub", action="store_true",
+                   help="c2: skip the bounded c4 and c5 summaries folded into the line")
     return p.parse_args()
 
 
@@ -300,11 +305,10 @@ def _timed(torch, stream, fn):
     return out, e0.elapsed_time(e1)
 
 
-def run_batch(args, rf, torch):
-    """c4: one batched solve of `rves` RVEs (sides 64..256, K = 5 %) to 1e-6 vs the same RVEs
-    solved one context at a time (a sample of them, same FP32 DFT transforms)."""
+def batch_summary(rf, torch, n, steps, warmup, sample_every=8):
+    """c4: one batched solve of `n` RVEs (sides 64..256, K = 5 %) to 1e-6 vs the same RVEs solved
+    one context at a time (every `sample_every`-th RVE, same FP32 FFT transforms)."""
     from synth.configs import elastic_phases, k_target
-    n = args.rves
     rv = _pool_map(_c4_rve, list(range(n)))
     pms = [r[0] for r in rv]
     macros = np.array([r[1] for r in rv])
@@ -314,12 +318,12 @@ def run_batch(args, rf, torch):
     ph = elastic_phases()
     b = rf.BatchSolver(pms, ph, pats, stream=sh, tol=TOL, max_iter=2000, transform="fft")
     vox = np.array([pm.size for pm in pms], np.float64)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.rf_batch_solve(macros)
     l0 = b.rf_batch_info()["kernel_launches"]
     ms, vi = [], 0.0
     with ClockSampler(gpu_id_for(torch, torch.cuda.current_device())) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             out, t = _timed(torch, stream, lambda: b.rf_batch_solve(macros))
             ms.append(t)
             vi += float(np.sum(out["iters"] * vox))
@@ -327,12 +331,12 @@ def run_batch(args, rf, torch):
     info = b.rf_batch_info()
     its = out["iters"]
     b.close()
-    # per-RVE contexts on a sample (every 8th RVE), solves timed back to back
-    samp = list(range(0, n, 8))
+    samp = list(range(0, n, sample_every))
     ctxs = [rf.Solver(pms[i], ph, pattern=pats[i], stream=sh, tol=TOL, max_iter=2000,
                       transform="fft") for i in samp]
     for c, i in zip(ctxs[:8], samp[:8]):
         c.rf_solve(macros[i])
+
     def solo():
         its_ = 0.0
         for c, i in zip(ctxs, samp):
@@ -346,9 +350,9 @@ def run_batch(args, rf, torch):
     bytes_per_vox_it = 49.0      # phase 1 B + strain in 12 B + tau out 12 B + line I/O 24 B
     achieved = bytes_per_vox_it * value / 1e9
     hbm = _hbm_peak()
-    line = {"metric": "RVE voxel-iterations/s to 1e-6 residual, batched (plain start)",
-            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+    return {"metric": "RVE voxel-iterations/s to 1e-6 residual, batched (plain start)",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": total_ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{n} 2D elastic fibre RVEs, sides U{{64,96,128,192,256}}, "
@@ -356,11 +360,12 @@ def run_batch(args, rf, torch):
                                    "along x and y for sides 2^b and 3*2^b, else pruned DFT)",
                        "voxels": int(vox.sum()), "tol": TOL,
                        "l2": "working set larger than L2"},
-            "solves_per_s": n * args.steps / (total_ms / 1e3),
+            "solves_per_s": n * steps / (total_ms / 1e3),
             "iterations_mean": float(np.mean(its)), "iterations_max": int(np.max(its)),
             "per_rve_launches": {"value": solo_vi / (solo_ms / 1e3), "unit": UNIT,
-                                 "sample": f"{len(samp)} of the RVEs (every 8th), one context "
-                                           "each, solved back to back"},
+                                 "sample": f"{len(samp)} of the RVEs (every {sample_every}th), "
+                                           "one context each (FFT transforms), solved back to "
+                                           "back"},
             "batched_over_per_rve": value / (solo_vi / (solo_ms / 1e3)),
             "gpu_launches": int(launches), "autotuned": info,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -368,7 +373,10 @@ def run_batch(args, rf, torch):
                          "kernel": "whole update (five persistent kernels)",
                          "algorithmic_bytes_per_voxel_iteration": bytes_per_vox_it},
             "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+
+
+def run_batch(args, rf, torch):
+    print(json.dumps(batch_summary(rf, torch, args.rves, args.steps, args.warmup)), flush=True)
 
 
 def _c5_rves(seeds, side=128):
@@ -376,54 +384,84 @@ def _c5_rves(seeds, side=128):
     return W.population(seeds, side=side, workers=16)
 
 
-def run_learned(args, rf, torch):
-    """c5: train the warm-start network on solver-generated 128^2 solutions, then solve
-    `rves` held-out RVEs from the plain start and from the network's prediction."""
+def learned_summary(rf, torch, n_train, n_test, epochs, steps, single_sample=128):
+    """c5: train the warm-start network on `n_train` solver-generated 128^2 solutions, then solve
+    `n_test` held-out RVEs from the plain start and from the network's prediction (batched, FP32
+    FFT), beside the plain FP32 single-RVE solver and the split-BF16 single-RVE solver on a
+    sample of the same RVEs (the forms the batched, warm-started solve is measured against)."""
     from paper_2103_10203_gb300 import warmstart as W
     from synth.configs import elastic_phases
     ph = elastic_phases()
     t0 = time.perf_counter()
-    pms, macros = _c5_rves(range(500000, 500000 + args.train))
+    pms, macros = _c5_rves(range(500000, 500000 + n_train))
     pats = W.patterns(pms, 0.05)
     net = rf.WarmStartNet(512, 1024)
     net.rf_mlp_set_params(W.init_params(net, 0))
     ds = W.generate(net, pms, macros, pats, ph, chunk=8192)
     del pms, pats
     t1 = time.perf_counter()
-    losses = W.train(net, ds, epochs=args.epochs, batch=128, lr=1e-3, lr_final=2e-5)
+    losses = W.train(net, ds, epochs=epochs, batch=128, lr=1e-3, lr_final=2e-5)
     t2 = time.perf_counter()
-    tp, tm = _c5_rves(range(900000, 900000 + args.rves))
+    tp, tm = _c5_rves(range(900000, 900000 + n_test))
     tpat = W.patterns(tp, 0.05)
     with ClockSampler(gpu_id_for(torch, torch.cuda.current_device())) as clk:
-        res = W.evaluate(net, tp, tm, tpat, ph, repeats=max(1, args.steps))
+        res = W.evaluate(net, tp, tm, tpat, ph, repeats=max(1, steps))
     del ds
     launches = net.rf_mlp_launches()
     net.close()
+    # single-RVE forms on a sample: plain FP32 FFT and split-BF16 tensor-core transforms
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    samp = list(range(min(single_sample, n_test)))
+    single = {}
+    for name, kw in (("fp32_fft", dict(transform="fft")),
+                     ("split_bf16", dict(transform="dft", precision="split_bf16"))):
+        ctxs = [rf.Solver(tp[i], ph, pattern=tpat[i], stream=sh, tol=TOL, max_iter=2000, **kw)
+                for i in samp]
+        for c, i in zip(ctxs[:4], samp[:4]):
+            c.rf_solve(tm[i])
+        its = []
+
+        def solo():
+            for c, i in zip(ctxs, samp):
+                its.append(c.rf_solve(tm[i])["iters"])
+        _, t = _timed(torch, stream, solo)
+        for c in ctxs:
+            c.close()
+        single[name] = {"solves_per_s": len(samp) / (t / 1e3), "iterations_mean": float(np.mean(its)),
+                        "sample": f"{len(samp)} held-out RVEs, one context each, back to back"}
     pl, le = res["plain"], res["learned"]
-    line = {"metric": "solves/s to 1e-6 residual, learned-warm vs plain start",
-            "value": args.rves / (le["ms"] / 1e3), "unit": "solves/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": 0, "ms_per_step": le["ms"],
+    learned_sps = n_test / (le["ms"] / 1e3)
+    return {"metric": "solves/s to 1e-6 residual, learned-warm vs plain start",
+            "value": learned_sps, "unit": "solves/s", "n_gpus": 1,
+            "steps": steps, "warmup": 0, "ms_per_step": le["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{args.rves} held-out 2D 128^2 elastic fibre RVEs (vf "
+            "config": {"workload": f"{n_test} held-out 2D 128^2 elastic fibre RVEs (vf "
                                    "U[0.2,0.5], r 8-24), K=5% adapted; network trained on "
-                                   f"{args.train} solver-generated solutions",
+                                   f"{n_train} solver-generated solutions",
                        "network": "48 descriptors -> 512 -> 512 -> 243 (27-term transfer "
                                   "expansion per strain/direction pair)",
-                       "epochs": args.epochs, "tol": TOL},
-            "plain": {"solves_per_s": args.rves / (pl["ms"] / 1e3), "ms": pl["ms"],
+                       "epochs": epochs, "tol": TOL},
+            "plain": {"solves_per_s": n_test / (pl["ms"] / 1e3), "ms": pl["ms"],
                       "iterations_mean": pl["iters_mean"], "iterations_max": pl["iters_max"],
                       "voxel_iterations_per_s": pl["voxel_iterations"] / (pl["ms"] / 1e3)},
-            "learned": {"solves_per_s": args.rves / (le["ms"] / 1e3), "ms": le["ms"],
+            "learned": {"solves_per_s": learned_sps, "ms": le["ms"],
                         "iterations_mean": le["iters_mean"], "iterations_max": le["iters_max"],
                         "voxel_iterations_per_s": le["voxel_iterations"] / (le["ms"] / 1e3),
                         "includes": "features + BF16 network inference + warm projection"},
             "speedup": pl["ms"] / le["ms"],
+            "single_rve": single,
+            "batched_learned_over_single_fp32": learned_sps / single["fp32_fft"]["solves_per_s"],
             "sigma_bar_max_abs_diff": float(np.max(np.abs(pl["sigma_bar"] - le["sigma_bar"]))),
             "training": {"data_s": t1 - t0, "train_s": t2 - t1, "loss_first": losses[0],
                          "loss_last": losses[-1], "network_launches": int(launches)},
             "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+
+
+def run_learned(args, rf, torch):
+    print(json.dumps(learned_summary(rf, torch, args.train, args.rves, args.epochs, args.steps)),
+          flush=True)
 
 
 def _tc_mma_flops(nx, rows, nc, Kx):
@@ -526,6 +564,96 @@ def run_3d(args, rf, torch):
     print(json.dumps(line), flush=True)
 
 
+def c2_pattern_study(rf, torch, pm, phases, path, stream, flush, steps=2):
+    """Config 2's K in {1, 5, 10} %, adapted vs fixed radial pattern (Sec. 5.2's comparison on
+    the 1024^2 J2 composite): time per load path (CUDA events, L2 flushed before each) and the
+    Sec. 5 errors of the last increment's stress against the full set of frequencies, before
+    and after the compatibility step."""
+    from paper_2103_10203_gb300 import sweep
+    from synth.configs import k_target
+    sh = stream.cuda_stream
+    opts = dict(stream=sh, tol=TOL, max_iter=MAX_ITER, transform="fft")
+    ref = rf.Solver(pm, phases, pattern=sweep.full_pattern(pm.shape), **opts)
+    ref.rf_solve_path(path)
+    ref.rf_reset_path()
+    flush.fill_(-1.0)
+    ref_out, ref_ms = _timed(torch, stream, lambda: ref.rf_solve_path(path))
+    rows = []
+    try:
+        for R in (0.01, 0.05, 0.10):
+            K = k_target(R, pm.size)
+            for kind in ("adapted", "radial"):
+                pat = sweep.pattern(kind, pm, K, stream=sh)
+                s = rf.Solver(pm, phases, pattern=pat, **opts)
+                s.rf_solve_path(path)               # warm-up: graph built, tiles tuned
+                ms, its = [], 0
+                for k in range(steps):
+                    flush.fill_(float(k))
+                    s.rf_reset_path()
+                    out, t = _timed(torch, stream, lambda: s.rf_solve_path(path))
+                    ms.append(t)
+                    its += int(np.sum(out["iters"]))
+                eb, e = s.rf_stress_errors(ref)
+                s.rf_compat()
+                ebc, ec = s.rf_stress_errors(ref)
+                s.close()
+                rows.append({"ratio": R, "pattern": kind, "K": int(len(pat)),
+                             "ms_per_path": float(np.mean(ms)), "updates_per_path": its / steps,
+                             "voxel_iterations_per_s": its * pm.size / (float(np.sum(ms)) / 1e3),
+                             "Ebar": eb, "E": e, "Ebar_compat": ebc, "E_compat": ec})
+    finally:
+        ref.close()
+    return {"reference": {"K": int(pm.size), "ms_per_path": ref_ms,
+                          "updates_per_path": int(np.sum(ref_out["iters"]))},
+            "errors": "Sec. 5: Ebar = |sbar - sbar_full| / |sbar_full|, E = mean over voxels of "
+                      "|sigma - sigma_full| / |sigma_full|, at the last increment",
+            "rows": rows}
+
+
+def run_paper(args, rf, torch):
+    """Pattern study on the paper-shaped inputs (Sec. 5): one inclusion of four shapes (256^2),
+    several inclusions elastic and elastoplastic (256^2, 100 increments), one sphere (256^3),
+    at the paper's percentages R of frequencies, against the full set of frequencies."""
+    from paper_2103_10203_gb300 import sweep
+    from synth import make_config
+    from synth.configs import PAPER_RATIOS
+    sh = torch.cuda.current_stream().cuda_stream
+    out = {"metric": "stress errors against the full set of frequencies, adapted vs fixed radial "
+                     "pattern (Sec. 5)", "unit": "relative error", "n_gpus": 1,
+           "data": "synthetic", "tol": TOL, "studies": {}}
+    t0 = time.perf_counter()
+    with ClockSampler(gpu_id_for(torch, torch.cuda.current_device())) as clk:
+        for shape in ("circle", "annulus", "ellipse", "square"):
+            c = make_config("p51", shape=shape)
+            rows, ref = sweep.pattern_study(c["phase_map"], c["phases"], PAPER_RATIOS,
+                                            macro=c["macro"], stream=sh)
+            out["studies"][f"p51_{shape}"] = {"reference": ref, "rows": rows}
+        c = make_config("p52")
+        rows, ref = sweep.pattern_study(c["phase_map"], c["phases"], PAPER_RATIOS,
+                                        macro=c["macro"], stream=sh)
+        out["studies"]["p52_elastic"] = {"reference": ref, "rows": rows}
+        c = make_config("p52", plastic=True)
+        rows, ref = sweep.pattern_study(c["phase_map"], c["phases"], PAPER_RATIOS,
+                                        path=c["path"], max_iter=200000, stream=sh)
+        out["studies"]["p52_j2_100_increments"] = {"reference": ref, "rows": rows}
+        c = make_config("p53")
+        rows, ref = sweep.pattern_study(c["phase_map"], c["phases"],
+                                        (0.0039, 0.0078, 0.0154, 0.0306, 0.0602),
+                                        macro=c["macro"], kinds=("adapted",), stream=sh)
+        for r in rows:
+            r["ms_per_update"] = 1e3 * r["solve_s"] / max(1, r["iters"])
+        ref["ms_per_update"] = 1e3 * ref["solve_s"] / max(1, ref["iters"])
+        out["studies"]["p53_sphere_256cube"] = {"reference": ref, "rows": rows}
+    j2 = {r["pattern"]: r for r in out["studies"]["p52_j2_100_increments"]["rows"]
+          if r["ratio"] == 0.0154}
+    out["value"] = j2["adapted"]["E"]
+    out["value_is"] = "E of the adapted pattern at R = 1.54 % (several inclusions, J2 matrix)"
+    out["radial_E_same_R"] = j2["radial"]["E"]
+    out["wall_s"] = time.perf_counter() - t0
+    out["clocks"] = clk.summary()
+    print(json.dumps(out), flush=True)
+
+
 def _hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(p))["hbm_gbs"] if os.path.exists(p) else 6800.0
@@ -550,6 +678,8 @@ def main():
         return run_batch(args, rf, torch)
     if args.workload == "c5":
         return run_learned(args, rf, torch)
+    if args.workload == "paper":
+        return run_paper(args, rf, torch)
 
     cfg, pm, K = workload()
     phases, path = cfg["phases"], cfg["path"]
@@ -682,9 +812,37 @@ def main():
         e2e = {"value": e_iters * pm.size / e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # compatibility step on the last solved path (the first call builds the full-set context)
+    solver.rf_compat()
+    compat_ms = []
+    for k in range(3):
+        _, t = _timed(torch, stream, solver.rf_compat)
+        compat_ms.append(t)
+    compat = {"ms": float(np.mean(compat_ms)),
+              "what": "one full-set Lippmann-Schwinger update from the reduced solution "
+                      "(Sec. 5.1), fields and homogenised stress",
+              "per_reduced_update_ms": float(np.sum(ms_steps)) / max(1, iters)}
+
+    study = None
+    if rank == 0 and not args.no_study:
+        try:
+            study = c2_pattern_study(rf, torch, pm, phases, path, stream, flush)
+        except Exception as ex:   # reported, never fatal for the headline line
+            study = {"error": repr(ex)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_sample(pm, phases, pattern, args.cpu_iters)
+
+    subs = {}
+    if rank == 0 and ws == 1 and not args.no_sub:
+        for key, fn in (("c4", lambda: batch_summary(rf, torch, 2048, 2, 3, sample_every=16)),
+                        ("c5", lambda: learned_summary(rf, torch, 8192, 1024, 8, 2,
+                                                       single_sample=64))):
+            try:
+                subs[key] = fn()
+            except Exception as ex:
+                subs[key] = {"error": repr(ex)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -697,7 +855,9 @@ def main():
                 "iterations_per_step": iters / args.steps, "e2e": e2e,
                 "gpu_launches": int(launches), "roofline": roof, "stage_share": stage_share,
                 "tiles": tile_info,
-                "cpu_baseline": cpu, "clocks": clocks,
+                "cpu_baseline": cpu, "clocks": clocks, "compat": compat,
+                "pattern_study": study,
+                "c4_bounded": subs.get("c4"), "c5_bounded": subs.get("c5"),
                 "precision": {"fp32": "FP32 transforms and law",
                               "split_bf16": "BF16 hi+lo tensor-core x transforms, FP32 law",
                               "split_tf32": "TF32 hi+lo tensor-core x transforms, FP32 law"}
