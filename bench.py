@@ -415,7 +415,8 @@ def learned_summary(rf, torch, n_train, n_test, epochs, steps, single_sample=128
     samp = list(range(min(single_sample, n_test)))
     single = {}
     for name, kw in (("fp32_fft", dict(transform="fft")),
-                     ("split_bf16", dict(transform="dft", precision="split_bf16"))):
+                     ("split_bf16", dict(transform="dft", precision="split_bf16")),
+                     ("split_tf32", dict(transform="dft", precision="split_tf32"))):
         ctxs = [rf.Solver(tp[i], ph, pattern=tpat[i], stream=sh, tol=TOL, max_iter=2000, **kw)
                 for i in samp]
         for c, i in zip(ctxs[:4], samp[:4]):
@@ -429,6 +430,7 @@ def learned_summary(rf, torch, n_train, n_test, epochs, steps, single_sample=128
         for c in ctxs:
             c.close()
         single[name] = {"solves_per_s": len(samp) / (t / 1e3), "iterations_mean": float(np.mean(its)),
+                        "iterations_max": int(np.max(its)),
                         "sample": f"{len(samp)} held-out RVEs, one context each, back to back"}
     pl, le = res["plain"], res["learned"]
     learned_sps = n_test / (le["ms"] / 1e3)

@@ -74,6 +74,7 @@ def pattern_study(phase_map, phases, ratios, macro=None, path=None,
                     row = dict(ratio=R, pattern=kind, K=int(len(pat)), iters=iters,
                                solve_s=secs, Ebar=eb, E=e)
                     if compat:
+                        s.rf_compat()     # the first call builds the full-set context
                         t0 = time.perf_counter()
                         s.rf_compat()
                         row["compat_s"] = time.perf_counter() - t0
