@@ -209,6 +209,27 @@ int rf_solve(rf_ctx* ctx, const double macro[6], const float* warm, double hom_s
 int rf_solve_path(rf_ctx* ctx, int32_t n_steps, const double* path, double* hom_stress,
                   int32_t* iters, double* residuals);
 
+/* Mixed macroscopic control, as an FE-FFT coupling prescribes it at a Gauss point (Sec. 1):
+ * for each component i of the six (order 11,22,33,23,13,12, tensor shear), control[i] = 0
+ * prescribes the macroscopic strain ebar_i = target[i], control[i] = 1 the average stress
+ * <sigma>_i = target[i]. In 2D (plane strain) components 33, 23, 13 must be strain-controlled
+ * with target 0. Every update sets the zero frequency to N E, where E takes the prescribed
+ * strains and solves (C0 : E)_i = target_i - <tau>_i for the stress-controlled components,
+ * <tau> = tau^(0) / N (the averaged Lippmann-Schwinger equation <sigma> = C0 : <eps> + <tau>),
+ * in FP64 on the device. The start is E0 (the same rule with <tau> = 0), and the convergence
+ * measure is normalised by |E0| instead of |ebar|; otherwise as rf_solve.
+ * hom_strain (nullable) receives E of the last update (the macroscopic strain reached).
+ * rf_solve_path_mixed: path[n_steps][6] of targets with one control for all increments; each
+ * increment starts from the last converged strain plus the increments of the strain-controlled
+ * components, commits as rf_solve_path; hom_stress and hom_strain are [n_steps][6].
+ * Errors: RF_ERR_INVALID (control not 0/1, 2D out-of-plane components), RF_ERR_NONFINITE. */
+int rf_solve_mixed(rf_ctx* ctx, const int32_t control[6], const double target[6],
+                   const float* warm, double hom_stress[6], double hom_strain[6], int32_t* iters,
+                   double* residual);
+int rf_solve_path_mixed(rf_ctx* ctx, const int32_t control[6], int32_t n_steps,
+                        const double* path, double* hom_stress, double* hom_strain,
+                        int32_t* iters, double* residuals);
+
 /* Reset the load-path state (strain and internal variables) to zero. */
 int rf_reset_path(rf_ctx* ctx);
 

@@ -222,6 +222,39 @@ def inverse_reduced(coeffs: np.ndarray, pattern: np.ndarray, shape_zyx) -> np.nd
     return f.real
 
 
+# --------------------------------------------------------------------------- mixed control
+def stiffness_matrix6(lam, mu) -> np.ndarray:
+    """[6, 6] matrix A of the isotropic stiffness on six-vectors (11,22,33,23,13,12) with TENSOR
+    shear: sigma_a = sum_b A[a, b] e_b, where a shear entry e_b stands for both eps_kl and eps_lk
+    (hence the factor 2 on shear columns)."""
+    C = isotropic_stiffness(lam, mu)
+    A = np.zeros((6, 6))
+    for a, (i, j) in enumerate(VOIGT):
+        for b, (k, l) in enumerate(VOIGT):
+            A[a, b] = C[i, j, k, l] * (1.0 if k == l else 2.0)
+    return A
+
+
+def mixed_macro_strain(control, target, tau_mean, lam0, mu0, dim) -> np.ndarray:
+    """Macroscopic strain E under mixed control (six-vectors, tensor shear). Where control_i = 0
+    the strain is prescribed, E_i = target_i; where control_i = 1 the average stress is
+    prescribed, and averaging the Lippmann-Schwinger equation (<eps> = E, <sigma> = C0 : E +
+    <tau>) gives (C0 : E)_i = target_i - <tau>_i, solved for those E_i with the others held.
+    In plane strain (dim 2) E_33 = E_23 = E_13 = 0."""
+    control = np.asarray(control, int)
+    target = np.asarray(target, float)
+    A = stiffness_matrix6(lam0, mu0)
+    E = np.where(control == 0, target, 0.0)
+    if dim == 2:
+        E[2:5] = 0.0
+    P = np.flatnonzero(control == 1)
+    Q = np.flatnonzero(control == 0)
+    if len(P):
+        rhs = target[P] - np.real(np.asarray(tau_mean))[P] - A[np.ix_(P, Q)] @ E[Q]
+        E[P] = np.linalg.solve(A[np.ix_(P, P)], rhs)
+    return E
+
+
 # --------------------------------------------------------------------------- solver
 @dataclasses.dataclass
 class SolveResult:
@@ -235,6 +268,7 @@ class SolveResult:
     eps_p: np.ndarray | None   # internal variables after the return map at eps
     alpha: np.ndarray | None
     history: list
+    macro_strain: np.ndarray | None = None   # six-vector E = <eps> (mixed control)
 
 
 def _materials(phases, pm):
@@ -250,8 +284,15 @@ def _c0_apply(eps, lam0, mu0):
 
 def solve(phase_map, phases, macro_strain, pattern, tol=1e-6, max_iter=1000,
           scheme="rotated", ref="minmax", eps_p=None, alpha=None, eps0=None,
-          warm_hat=None, keep_history=False) -> SolveResult:
+          warm_hat=None, keep_history=False, control=None) -> SolveResult:
     """Reduced fixed-point scheme of Sec. 4 (steps a-d) for one macroscopic strain.
+
+    control   optional six ints: 1 where `macro_strain` holds a prescribed average STRESS
+              component instead of a strain component (mixed control for FE-FFT coupling,
+              Sec. 1). The zero frequency of every update is then N E with E from
+              `mixed_macro_strain` and <tau> = tau^(0) / N; the convergence measure is
+              normalised by |E0|, E0 the macro strain of the same rule with <tau> = 0 (also the
+              plain start).
 
     eps0      optional starting strain field (load-path continuation); default eps = ebar.
     warm_hat  optional starting coefficients [K,3,3] on the pattern; they are projected onto
@@ -264,10 +305,16 @@ def solve(phase_map, phases, macro_strain, pattern, tol=1e-6, max_iter=1000,
     pm = _as_grid(phase_map)
     nz, ny, nx = pm.shape
     N = pm.size
-    ebar = vec6_to_tensor(macro_strain)
-    enorm = np.sqrt(_frob2(ebar))
     lam, mu, sy, H, plastic = _materials(phases, pm)
     lam0, mu0 = reference_medium(phases, pm, ref)
+    dim = 2 if nz == 1 else 3
+    if control is not None:
+        target = np.asarray(macro_strain, float)
+        E = mixed_macro_strain(control, target, np.zeros(6), lam0, mu0, dim)
+    else:
+        E = np.asarray(macro_strain, float)
+    ebar = vec6_to_tensor(E)
+    enorm = np.sqrt(_frob2(ebar))
 
     pattern = np.asarray(pattern, np.int64)
     is_zero = np.all(pattern == 0, axis=1)
@@ -304,6 +351,10 @@ def solve(phase_map, phases, macro_strain, pattern, tol=1e-6, max_iter=1000,
         # c) Lippmann-Schwinger update on the reduced set
         eh = -np.einsum("kijab,kab->kij", Gam, th)
         eh[null] = 0.0
+        if control is not None:
+            E = mixed_macro_strain(control, target, tensor_to_vec6(th[is_zero][0] / N),
+                                   lam0, mu0, dim)
+            ebar = vec6_to_tensor(E)
         eh[is_zero] = N * ebar
         # d) back to the grid
         eps_new = inverse(eh)
@@ -322,18 +373,22 @@ def solve(phase_map, phases, macro_strain, pattern, tol=1e-6, max_iter=1000,
     return SolveResult(eps=eps, sigma=sigma, sigma_bar=sbar, iters=it, residual=float(r),
                        converged=bool(r < tol), eps_hat=eh,
                        eps_p=eps_p_new if has_plastic else None,
-                       alpha=alpha_new if has_plastic else None, history=history)
+                       alpha=alpha_new if has_plastic else None, history=history,
+                       macro_strain=tensor_to_vec6(ebar))
 
 
 def solve_path(phase_map, phases, path, pattern, tol=1e-6, max_iter=1000, scheme="rotated",
-               ref="minmax", fixed_iters=None):
+               ref="minmax", fixed_iters=None, control=None):
     """Load path of macroscopic strains path[n] (n = 0..T-1), one increment at a time.
 
     Internal variables are frozen during the iterations of an increment and committed from the
     return map at its converged strain; increment n starts from eps_{n-1} + (ebar_n - ebar_{n-1}).
     fixed_iters: optional per-increment update counts (tol is then ignored), to replay a path
     iterate by iterate.
-    Returns (sigma_bar [T,6], iters [T], last SolveResult).
+    control: optional mixed control (see `solve`); path[n] then holds the targets, and increment
+    n starts from eps_{n-1} plus the increments of the strain-controlled components only.
+    Returns (sigma_bar [T,6], iters [T], last SolveResult); with control, the last result's
+    macro_strain holds the macroscopic strain reached at the last increment.
     """
     pm = _as_grid(phase_map)
     path = np.asarray(path, float)
@@ -344,15 +399,16 @@ def solve_path(phase_map, phases, path, pattern, tol=1e-6, max_iter=1000, scheme
     sbar = np.zeros((len(path), 6))
     iters = np.zeros(len(path), int)
     res = None
+    strain_part = np.ones(6) if control is None else (np.asarray(control) == 0).astype(float)
     for n, e in enumerate(path):
-        eps0 = None if eps is None else eps + vec6_to_tensor(e - prev)
+        eps0 = None if eps is None else eps + vec6_to_tensor(strain_part * (e - prev))
         t_n, m_n = (tol, max_iter) if fixed_iters is None else (0.0, int(fixed_iters[n]))
         res = solve(pm, phases, e, pattern, t_n, m_n, scheme, ref, eps_p=eps_p,
-                    alpha=alpha, eps0=eps0)
+                    alpha=alpha, eps0=eps0, control=control)
         if res.eps_p is not None:
             eps_p, alpha = res.eps_p, res.alpha
         eps = res.eps
-        prev = e
+        prev = e if control is None else np.where(strain_part > 0, e, res.macro_strain)
         sbar[n] = res.sigma_bar
         iters[n] = res.iters
     return sbar, iters, res

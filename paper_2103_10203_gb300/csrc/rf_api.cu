@@ -301,9 +301,58 @@ int reset_path_state(rf_ctx* c) {
   return RF_OK;
 }
 
-int init_status(rf_ctx* c, const double* macro) {
+// Mixed control (host side of the device rule in rf_law.cuh, with <tau> = 0): the macroscopic
+// strain of a homogeneous reference medium under the targets, used as the start and as the
+// normalisation of the convergence measure.
+void mixed_start(const rf_ctx* c, const int32_t* control, const double* target, double* E) {
+  const double l = c->lam0, m = c->mu0;
+  auto A = [&](int a, int b) {
+    if (a < 3 && b < 3) return l + (a == b ? 2.0 * m : 0.0);
+    return a == b ? 2.0 * m : 0.0;
+  };
+  int P[6], np = 0;
+  for (int i = 0; i < 6; ++i) {
+    E[i] = control[i] ? 0.0 : target[i];
+    if (control[i]) P[np++] = i;
+  }
+  double M[6][7];
+  for (int r = 0; r < np; ++r) {
+    double rhs = target[P[r]];
+    for (int j = 0; j < 6; ++j)
+      if (!control[j]) rhs -= A(P[r], j) * E[j];
+    for (int q = 0; q < np; ++q) M[r][q] = A(P[r], P[q]);
+    M[r][np] = rhs;
+  }
+  for (int k = 0; k < np; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < np; ++r)
+      if (std::fabs(M[r][k]) > std::fabs(M[piv][k])) piv = r;
+    if (piv != k)
+      for (int q = 0; q <= np; ++q) std::swap(M[k][q], M[piv][q]);
+    for (int r = k + 1; r < np; ++r) {
+      const double f = M[r][k] / M[k][k];
+      for (int q = k; q <= np; ++q) M[r][q] -= f * M[k][q];
+    }
+  }
+  for (int k = np - 1; k >= 0; --k) {
+    double v = M[k][np];
+    for (int q = k + 1; q < np; ++q) v -= M[k][q] * E[P[q]];
+    E[P[k]] = v / M[k][k];
+  }
+}
+
+int init_status(rf_ctx* c, const double* macro, const int32_t* control = nullptr,
+                const double* target = nullptr) {
   c->launched_iters = 0;
   Status& s = *c->h_status;
+  s.mixed = control ? 1 : 0;
+  s.pad2 = 0;
+  for (int i = 0; i < 6; ++i) {
+    s.control[i] = control ? control[i] : 0;
+    s.target[i] = target ? target[i] : macro[i];
+  }
+  s.lam0 = c->lam0;
+  s.mu0 = c->mu0;
   s.done = 0;
   s.iters = 0;
   s.max_iter = c->opt.max_iter;
@@ -392,6 +441,22 @@ int finish(rf_ctx* c, int commit, double* sbar) {
     c->last_sbar[i] = c->h_sbar[i];
     if (sbar) sbar[i] = c->h_sbar[i];
   }
+  return RF_OK;
+}
+
+int check_mixed(const rf_ctx* c, const int32_t* control, const double* target) {
+  for (int i = 0; i < 6; ++i) {
+    if (control[i] != 0 && control[i] != 1) return invalid("mixed control: entries must be 0 or 1");
+    if (!std::isfinite(target[i])) {
+      set_error("mixed control: target is not finite");
+      return RF_ERR_NONFINITE;
+    }
+  }
+  if (c->dim == 2)
+    for (int i = 2; i < 5; ++i)
+      if (control[i] || target[i] != 0.0)
+        return invalid("mixed control in 2D (plane strain): components 33, 23, 13 are strains "
+                       "fixed at zero");
   return RF_OK;
 }
 
@@ -848,6 +913,84 @@ int rf_solve(rf_ctx* c, const double macro[6], const float* warm, double hom_str
   if (iters) *iters = c->last_iters;
   if (residual) *residual = c->last_residual;
   return c->last_residual < c->opt.tol ? RF_OK : RF_NOT_CONVERGED;
+}
+
+int rf_solve_mixed(rf_ctx* c, const int32_t control[6], const double target[6], const float* warm,
+                   double hom_stress[6], double hom_strain[6], int32_t* iters, double* residual) {
+  if (!c || !control || !target) return invalid("rf_solve_mixed: null argument");
+  if (!c->have_pattern) {
+    set_error("rf_solve_mixed: no pattern set");
+    return RF_ERR_STATE;
+  }
+  if (int e = check_mixed(c, control, target)) return e;
+  DeviceGuard dg(c->dev);
+  double E0[6];
+  mixed_start(c, control, target, E0);
+  if (int e = init_status(c, E0, control, target)) return e;
+  if (warm) {
+    std::vector<float2> w6((size_t)c->Kh * 6);
+    for (long long h = 0; h < c->Kh; ++h) {
+      const long long p = c->h_src[h];
+      for (int i = 0; i < 6; ++i)
+        w6[h * 6 + i] = make_float2(warm[(p * 6 + i) * 2], warm[(p * 6 + i) * 2 + 1]);
+    }
+    if (int e = ck(cudaMemcpyAsync(c->d_warm, w6.data(), sizeof(float2) * w6.size(),
+                                   cudaMemcpyHostToDevice, c->stream), "upload warm"))
+      return e;
+    if (int e = ck(cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream), "memset"))
+      return e;
+    if (int e = launch_warm_project(c, c->d_warm, E0)) return e;
+    if (int e = ck(cudaStreamSynchronize(c->stream), "warm")) return e;
+  } else {
+    if (int e = launch_reset_er(c, E0, 0.0)) return e;
+  }
+  int st = run_iterations(c);
+  if (st < 0) return st;
+  double E[6];
+  for (int i = 0; i < 6; ++i) E[i] = c->h_status->ebar[i];
+  if (int e = finish(c, 0, hom_stress)) return e;
+  for (int i = 0; i < 6; ++i) {
+    c->prev_macro[i] = E[i];
+    if (hom_strain) hom_strain[i] = E[i];
+  }
+  if (iters) *iters = c->last_iters;
+  if (residual) *residual = c->last_residual;
+  return c->last_residual < c->opt.tol ? RF_OK : RF_NOT_CONVERGED;
+}
+
+int rf_solve_path_mixed(rf_ctx* c, const int32_t control[6], int32_t n_steps, const double* path,
+                        double* hom_stress, double* hom_strain, int32_t* iters,
+                        double* residuals) {
+  if (!c || !control || !path || n_steps < 1) return invalid("rf_solve_path_mixed: invalid arguments");
+  if (!c->have_pattern) {
+    set_error("rf_solve_path_mixed: no pattern set");
+    return RF_ERR_STATE;
+  }
+  for (int n = 0; n < n_steps; ++n)
+    if (int e = check_mixed(c, control, path + 6 * n)) return e;
+  DeviceGuard dg(c->dev);
+  int status = RF_OK;
+  for (int n = 0; n < n_steps; ++n) {
+    const double* t = path + 6 * n;
+    double d[6], E0[6];
+    for (int i = 0; i < 6; ++i) d[i] = control[i] ? 0.0 : t[i] - c->prev_macro[i];
+    mixed_start(c, control, t, E0);
+    if (int e = init_status(c, E0, control, t)) return e;
+    if (int e = launch_reset_er(c, d, 1.0)) return e;
+    int st = run_iterations(c);
+    if (st < 0) return st;
+    double E[6];
+    for (int i = 0; i < 6; ++i) E[i] = c->h_status->ebar[i];
+    if (int e = finish(c, 1, hom_stress ? hom_stress + 6 * n : nullptr)) return e;
+    for (int i = 0; i < 6; ++i) {
+      c->prev_macro[i] = E[i];
+      if (hom_strain) hom_strain[6 * n + i] = E[i];
+    }
+    if (iters) iters[n] = c->last_iters;
+    if (residuals) residuals[n] = c->last_residual;
+    if (!(c->last_residual < c->opt.tol)) status = RF_NOT_CONVERGED;
+  }
+  return status;
 }
 
 int rf_solve_path(rf_ctx* c, int32_t n_steps, const double* path, double* hom_stress,

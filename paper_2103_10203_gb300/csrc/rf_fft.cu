@@ -414,12 +414,22 @@ __global__ __launch_bounds__(256) void k_fft_colphase(ColPhaseArgs a, double Nd)
     const float4 n = a.hn[h];
     const int jj = hi.j - j0, pos = a.kym[hi.iy];
     const long long base = ((long long)hi.iy * NC) * a.Kx + hi.j;
-    float2 tv[NC];   // tau^ is read only where the operator uses it (regular frequencies)
+    // tau^ is read only where it is used: regular frequencies, and the zero frequency under
+    // mixed control
+    const bool mixed0 = hi.kind == 1 && a.st->mixed;
+    float2 tv[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c)
-      tv[c] = hi.kind == 0 ? z[sw((jj * NC + c) * L + pos)] : make_float2(0.f, 0.f);
+      tv[c] = (hi.kind == 0 || mixed0) ? z[sw((jj * NC + c) * L + pos)] : make_float2(0.f, 0.f);
     float er[NC], ei[NC];
-    green_update<NC>(hi.kind, n, tv, a.st->ebar, Nd, a.inv2mu0, a.cgam, er, ei);
+    const double* eb = a.st->ebar;
+    double em[6];
+    if (mixed0) {
+      mixed_macro<NC>(tv, Nd, a.st, em);
+      for (int i = 0; i < 6; ++i) a.st->ebar[i] = em[i];
+      eb = em;
+    }
+    green_update<NC>(hi.kind, n, tv, eb, Nd, a.inv2mu0, a.cgam, er, ei);
     float d = 0.f;   // one frequency's squared increment (at most six non-negative terms)
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -557,7 +567,15 @@ __global__ __launch_bounds__(256) void k_fft_green_inv(GreenInvArgs a, double Nd
     if (ecc[u] < 0) continue;
     const int c = cc_[ecc[u]];
     float erc[NC], eic[NC], er = 0.f, ei = 0.f;
-    green_update<NC>(ekind[u], en[u], tv[u], a.st->ebar, Nd, a.inv2mu0, a.cgam, erc, eic);
+    const double* eb = a.st->ebar;
+    double em[6];
+    if (ekind[u] == 1 && a.st->mixed) {   // one of NC blocks (component c) meets it; c 0 writes
+      mixed_macro<NC>(tv[u], Nd, a.st, em);
+      if (c == 0)
+        for (int i = 0; i < 6; ++i) a.st->ebar[i] = em[i];
+      eb = em;
+    }
+    green_update<NC>(ekind[u], en[u], tv[u], eb, Nd, a.inv2mu0, a.cgam, erc, eic);
 #pragma unroll
     for (int q = 0; q < NC; ++q)   // keep this block's component (no dynamic register index)
       if (q == c) {
@@ -581,12 +599,21 @@ __global__ __launch_bounds__(256) void k_fft_green_inv(GreenInvArgs a, double Nd
     const float4 n = a.jn[e];
     const int c = cc_[cc], kx = ckx[cc];
     const long long base = ((long long)en2.x * NC) * a.Kx + kx;
+    const bool mixed0 = en2.y == 1 && a.st->mixed;
     float2 tq[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
-      tq[q] = en2.y == 0 ? a.OUT[base + (long long)q * a.Kx] : make_float2(0.f, 0.f);
+      tq[q] = (en2.y == 0 || mixed0) ? a.OUT[base + (long long)q * a.Kx] : make_float2(0.f, 0.f);
     float erc[NC], eic[NC], er = 0.f, ei = 0.f;
-    green_update<NC>(en2.y, n, tq, a.st->ebar, Nd, a.inv2mu0, a.cgam, erc, eic);
+    const double* eb = a.st->ebar;
+    double em[6];
+    if (mixed0) {
+      mixed_macro<NC>(tq, Nd, a.st, em);
+      if (c == 0)
+        for (int i = 0; i < 6; ++i) a.st->ebar[i] = em[i];
+      eb = em;
+    }
+    green_update<NC>(en2.y, n, tq, eb, Nd, a.inv2mu0, a.cgam, erc, eic);
 #pragma unroll
     for (int q = 0; q < NC; ++q)
       if (q == c) {

@@ -58,7 +58,14 @@ struct Status {
   double inv_n2;  // 1 / N^2 (Parseval)
   double last_r;
   double rmin;    // smallest measure of this solve so far
-  double ebar[6];
+  double ebar[6]; // macroscopic strain (mixed control: the one of the last update)
+  // mixed macroscopic control: component i of `target` is an average stress where
+  // control[i] = 1, a strain where 0; lam0, mu0 of the reference medium in FP64
+  int mixed;
+  int control[6];
+  int pad2;
+  double target[6];
+  double lam0, mu0;
 };
 
 // Divergence rule of the convergence decision: the measure exceeds both kDivergeRatio times

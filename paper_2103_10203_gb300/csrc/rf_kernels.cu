@@ -330,7 +330,14 @@ __global__ __launch_bounds__(kGammaBlock) void k_gamma(GammaArgs a, double Nd) {
       }
     }
     float er[NC], ei[NC];
-    green_update<NC>(hi.kind, n, tv, a.st->ebar, Nd, a.inv2mu0, a.cgam, er, ei);
+    const double* eb = a.st->ebar;
+    double em[6];
+    if (hi.kind == 1 && a.st->mixed) {   // the one zero-frequency thread of the update
+      mixed_macro<NC>(tv, Nd, a.st, em);
+      for (int i = 0; i < 6; ++i) a.status->ebar[i] = em[i];
+      eb = em;
+    }
+    green_update<NC>(hi.kind, n, tv, eb, Nd, a.inv2mu0, a.cgam, er, ei);
     const float mult = n.w;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {

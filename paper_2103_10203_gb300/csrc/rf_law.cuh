@@ -175,6 +175,58 @@ __device__ __forceinline__ void gamma6(const float4& n, const float* t, float in
   o[5] = (n.x * v1 + n.y * v0) * inv2mu0 - cg * n.x * n.y * nvn;
 }
 
+// Macroscopic strain E under mixed control from the zero frequency of tau (tv = tau^(0) of the
+// NC components, <tau> = tau^(0) / N): E_i = target_i where the strain is prescribed; where the
+// average stress is prescribed, (C0 : E)_i = target_i - <tau>_i with the other components held
+// (the averaged Lippmann-Schwinger equation <sigma> = C0 : <eps> + <tau>), solved in FP64 by
+// Gaussian elimination with partial pivoting. C0 acts on six-vectors with tensor shear:
+// normal rows lam0 + 2 mu0 delta_ij, shear columns 2 mu0. In plane strain E_33 = E_23 = E_13 = 0.
+template <int NC>
+__device__ inline void mixed_macro(const float2* tv, double Nd, const Status* st, double* E) {
+  double t6[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < NC; ++c) t6[comp6<NC>(c)] = (double)tv[c].x / Nd;
+  const double l = st->lam0, m = st->mu0;
+  auto A = [&](int a, int b) -> double {
+    if (a < 3 && b < 3) return l + (a == b ? 2.0 * m : 0.0);
+    return a == b ? 2.0 * m : 0.0;
+  };
+  int P[6], np = 0;
+  for (int i = 0; i < 6; ++i) {
+    E[i] = st->control[i] ? 0.0 : st->target[i];
+    if (NC == 3 && i >= 2 && i <= 4) E[i] = 0.0;
+    if (st->control[i]) P[np++] = i;
+  }
+  double M[6][7];
+  for (int r = 0; r < np; ++r) {
+    double rhs = st->target[P[r]] - t6[P[r]];
+    for (int j = 0; j < 6; ++j)
+      if (!st->control[j]) rhs -= A(P[r], j) * E[j];
+    for (int q = 0; q < np; ++q) M[r][q] = A(P[r], P[q]);
+    M[r][np] = rhs;
+  }
+  for (int k = 0; k < np; ++k) {
+    int piv = k;
+    for (int r = k + 1; r < np; ++r)
+      if (fabs(M[r][k]) > fabs(M[piv][k])) piv = r;
+    if (piv != k)
+      for (int q = 0; q <= np; ++q) {
+        const double t = M[k][q];
+        M[k][q] = M[piv][q];
+        M[piv][q] = t;
+      }
+    for (int r = k + 1; r < np; ++r) {
+      const double f = M[r][k] / M[k][k];
+      for (int q = k; q <= np; ++q) M[r][q] -= f * M[k][q];
+    }
+  }
+  for (int k = np - 1; k >= 0; --k) {
+    double v = M[k][np];
+    for (int q = k + 1; q < np; ++q) v -= M[k][q] * E[P[q]];
+    E[P[k]] = v / M[k][k];
+  }
+}
+
 // New strain coefficients at one half-pattern frequency (Sec. 4 step c) from tau^ of its NC
 // components: N ebar at the zero frequency (kind 1), 0 where the operator is null (kind 2),
 // otherwise eps^ = -Gamma0 : tau^ applied to the real and to the imaginary parts.

@@ -95,6 +95,8 @@ def _load() -> C.CDLL:
         "rf_get_info": [P, C.POINTER(rf_info)],
         "rf_destroy": [P],
         "rf_compat": [P, P],
+        "rf_solve_mixed": [P, P, P, P, P, P, P, P],
+        "rf_solve_path_mixed": [P, P, i32, P, P, P, P, P],
         "rf_stress_errors": [P, P, P, P],
         "rf_pattern_adapted": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
@@ -146,7 +148,8 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc",
             "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy",
             "rf_batch_slots", "rf_batch_descriptors", "rf_batch_reduced_strain",
-            "rf_batch_solve_warm", "rf_compat", "rf_stress_errors",
+            "rf_batch_solve_warm", "rf_compat", "rf_stress_errors", "rf_solve_mixed",
+            "rf_solve_path_mixed",
             "rf_mlp_create", "rf_mlp_get_dims", "rf_mlp_set_params", "rf_mlp_get_params",
             "rf_mlp_get_grads", "rf_mlp_forward", "rf_mlp_targets", "rf_mlp_loss_grad",
             "rf_mlp_adam", "rf_mlp_train_step", "rf_mlp_predict_warm", "rf_mlp_launches",
@@ -315,6 +318,31 @@ class Solver:
         eb, e = C.c_double(0.0), C.c_double(0.0)
         _check(lib.rf_stress_errors(self.ctx, ref.ctx, C.byref(eb), C.byref(e)), allow_nc=False)
         return eb.value, e.value
+
+    def rf_solve_mixed(self, control, target, warm=None):
+        """Mixed control: control[i] = 1 prescribes the average stress target[i], 0 the strain."""
+        ctl = np.ascontiguousarray(control, dtype=np.int32)
+        t = np.ascontiguousarray(target, dtype=np.float64)
+        w = None if warm is None else np.ascontiguousarray(warm, dtype=np.float32)
+        sbar, ebar = np.zeros(6), np.zeros(6)
+        it = C.c_int32(0)
+        res = C.c_double(0)
+        code = _check(lib.rf_solve_mixed(self.ctx, _ptr(ctl), _ptr(t), _ptr(w), _ptr(sbar),
+                                         _ptr(ebar), C.byref(it), C.byref(res)))
+        return dict(sigma_bar=sbar, strain_bar=ebar, iters=it.value, residual=res.value,
+                    converged=code == RF_OK)
+
+    def rf_solve_path_mixed(self, control, path):
+        ctl = np.ascontiguousarray(control, dtype=np.int32)
+        p = np.ascontiguousarray(path, dtype=np.float64).reshape(-1, 6)
+        n = len(p)
+        sbar, ebar = np.zeros((n, 6)), np.zeros((n, 6))
+        its = np.zeros(n, np.int32)
+        res = np.zeros(n)
+        code = _check(lib.rf_solve_path_mixed(self.ctx, _ptr(ctl), n, _ptr(p), _ptr(sbar),
+                                              _ptr(ebar), _ptr(its), _ptr(res)))
+        return dict(sigma_bar=sbar, strain_bar=ebar, iters=its, residuals=res,
+                    converged=code == RF_OK)
 
     def rf_reset_path(self):
         _check(lib.rf_reset_path(self.ctx), allow_nc=False)

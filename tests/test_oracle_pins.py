@@ -587,3 +587,54 @@ def test_compat_step_on_a_laminate_gives_the_closed_form():
     s11, s12, _, _, _ = laminate_closed_form(TWO_PHASE["lam"], TWO_PHASE["mu"], f, ebar)
     assert np.allclose(sig_c[..., 0, 0], s11, rtol=1e-10)
     assert np.allclose(sig_c[..., 0, 1], s12, rtol=1e-10)
+
+
+# ----------------------------------------------------------------------------- mixed control
+def test_mixed_control_homogeneous_plane_strain_uniaxial_stress():
+    """One phase, eps_11 = e prescribed, sigma_22 = sigma_12 = 0 prescribed (plane strain):
+    eps_22 = -lam / (lam + 2 mu) e and sigma_11 = 4 mu (lam + mu) / (lam + 2 mu) e."""
+    lam, mu, e = 3.0, 1.7, 0.01
+    pm = np.zeros((6, 8), np.uint8)
+    ph = phase_table([(lam, mu, 0, 0, 0)])
+    r = O.solve(pm, ph, np.array([e, 0, 0, 0, 0, 0]), np.zeros((1, 3), np.int64), tol=1e-13,
+                control=[0, 1, 0, 0, 0, 1])
+    assert np.isclose(r.macro_strain[1], -lam / (lam + 2 * mu) * e, rtol=1e-12)
+    assert np.isclose(r.sigma_bar[0], 4 * mu * (lam + mu) / (lam + 2 * mu) * e, rtol=1e-12)
+    assert abs(r.sigma_bar[1]) < 1e-14 and abs(r.sigma_bar[5]) < 1e-14
+
+
+def test_mixed_control_laminate_closed_form():
+    """Layers normal to x with sigma_11 = s and sigma_12 = t prescribed, eps_22 = e22 prescribed:
+    sigma_11 and sigma_12 are uniform, eps_22 = e22 in every layer, so eps_11 of phase p is
+    (s - lam_p e22) / (lam_p + 2 mu_p) and eps_12 is t / (2 mu_p); the macro strain is their
+    volume average (the Reuss side of the laminate)."""
+    pm = laminate((6, 16), (5, 11))
+    s, t, e22 = 0.4, -0.05, -0.002
+    pat = O.pattern_adapted(pm, 1, 16)
+    r = O.solve(pm, TWO_PHASE, np.array([s, e22, 0, 0, 0, t]), pat, tol=1e-13, max_iter=20000,
+                control=[1, 0, 0, 0, 0, 1])
+    f = np.array([np.mean(pm == 0), np.mean(pm == 1)])
+    lam, mu = TWO_PHASE["lam"], TWO_PHASE["mu"]
+    e11 = np.sum(f * (s - lam * e22) / (lam + 2 * mu))
+    e12 = np.sum(f * t / (2 * mu))
+    assert np.isclose(r.macro_strain[0], e11, rtol=1e-10)
+    assert np.isclose(r.macro_strain[5], e12, rtol=1e-10)
+    assert np.isclose(r.macro_strain[1], e22, rtol=1e-14)
+    assert np.allclose(r.sigma[..., 0, 0], s, rtol=1e-10)
+    assert np.allclose(r.sigma[..., 0, 1], t, rtol=1e-10)
+
+
+@pytest.mark.parametrize("plastic", [False, True])
+def test_mixed_control_recovers_the_strain_controlled_solution(plastic):
+    """Prescribing the average stresses a strain-controlled solve produced (and its other strain
+    components) must return that solve's macro strain and fields: the fixed point is unique."""
+    from synth.configs import j2_phases
+    pm = random_discs(16, (2.0, 4.0), 0.35, seed=3)
+    ph = j2_phases() if plastic else TWO_PHASE
+    ebar = np.array([0.02, -0.004, 0, 0, 0, 0.003])
+    pat = O.pattern_adapted(pm, 1, 37)
+    a = O.solve(pm, ph, ebar, pat, tol=1e-12, max_iter=20000)
+    target = np.array([a.sigma_bar[0], ebar[1], 0, 0, 0, a.sigma_bar[5]])
+    b = O.solve(pm, ph, target, pat, tol=1e-12, max_iter=20000, control=[1, 0, 0, 0, 0, 1])
+    assert np.allclose(b.macro_strain, ebar, rtol=1e-8, atol=1e-13)
+    assert np.allclose(b.eps, a.eps, atol=1e-9 * np.abs(a.eps).max())
