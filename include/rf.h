@@ -220,8 +220,10 @@ int rf_solve_path(rf_ctx* ctx, int32_t n_steps, const double* path, double* hom_
  * measure is normalised by |E0| instead of |ebar|; otherwise as rf_solve.
  * hom_strain (nullable) receives E of the last update (the macroscopic strain reached).
  * rf_solve_path_mixed: path[n_steps][6] of targets with one control for all increments; each
- * increment starts from the last converged strain plus the increments of the strain-controlled
- * components, commits as rf_solve_path; hom_stress and hom_strain are [n_steps][6].
+ * increment starts from the last converged strain plus the reference medium's response (the
+ * rule above with <tau> = 0) to the increment of the targets, stress increments measured from
+ * the last homogenised stress (from the zero state: E0); commits as rf_solve_path; hom_stress
+ * and hom_strain are [n_steps][6].
  * Errors: RF_ERR_INVALID (control not 0/1, 2D out-of-plane components), RF_ERR_NONFINITE. */
 int rf_solve_mixed(rf_ctx* ctx, const int32_t control[6], const double target[6],
                    const float* warm, double hom_stress[6], double hom_strain[6], int32_t* iters,

@@ -386,7 +386,10 @@ def solve_path(phase_map, phases, path, pattern, tol=1e-6, max_iter=1000, scheme
     fixed_iters: optional per-increment update counts (tol is then ignored), to replay a path
     iterate by iterate.
     control: optional mixed control (see `solve`); path[n] then holds the targets, and increment
-    n starts from eps_{n-1} plus the increments of the strain-controlled components only.
+    n starts from eps_{n-1} plus the reference medium's response to the increment of the
+    targets: mixed_macro_strain applied (with <tau> = 0) to the strain-target increments and the
+    stress-target increments measured from the last homogenised stress (from the zero state
+    this is the plain start E0).
     Returns (sigma_bar [T,6], iters [T], last SolveResult); with control, the last result's
     macro_strain holds the macroscopic strain reached at the last increment.
     """
@@ -399,16 +402,28 @@ def solve_path(phase_map, phases, path, pattern, tol=1e-6, max_iter=1000, scheme
     sbar = np.zeros((len(path), 6))
     iters = np.zeros(len(path), int)
     res = None
-    strain_part = np.ones(6) if control is None else (np.asarray(control) == 0).astype(float)
+    prev_s = np.zeros(6)
+    if control is not None:
+        ctl = np.asarray(control, int)
+        lam0, mu0 = reference_medium(phases, pm, ref)
+        dim = 2 if pm.shape[0] == 1 else 3
     for n, e in enumerate(path):
-        eps0 = None if eps is None else eps + vec6_to_tensor(strain_part * (e - prev))
+        if eps is None:
+            eps0 = None
+        elif control is None:
+            eps0 = eps + vec6_to_tensor(e - prev)
+        else:
+            incr = np.where(ctl == 1, e - prev_s, e - prev)
+            eps0 = eps + vec6_to_tensor(mixed_macro_strain(ctl, incr, np.zeros(6), lam0, mu0,
+                                                           dim))
         t_n, m_n = (tol, max_iter) if fixed_iters is None else (0.0, int(fixed_iters[n]))
         res = solve(pm, phases, e, pattern, t_n, m_n, scheme, ref, eps_p=eps_p,
                     alpha=alpha, eps0=eps0, control=control)
         if res.eps_p is not None:
             eps_p, alpha = res.eps_p, res.alpha
         eps = res.eps
-        prev = e if control is None else np.where(strain_part > 0, e, res.macro_strain)
+        prev = e if control is None else res.macro_strain
+        prev_s = res.sigma_bar
         sbar[n] = res.sigma_bar
         iters[n] = res.iters
     return sbar, iters, res

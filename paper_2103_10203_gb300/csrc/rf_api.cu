@@ -290,6 +290,7 @@ void release_pattern_buffers(rf_ctx* c) {
 
 int reset_path_state(rf_ctx* c) {
   for (double& v : c->prev_macro) v = 0.0;
+  for (double& v : c->prev_sbar) v = 0.0;
   if (c->d_ER)
     if (int e = ck(cudaMemsetAsync(c->d_ER, 0, sizeof(float2) * c->rect, c->stream), "memset ER"))
       return e;
@@ -909,7 +910,10 @@ int rf_solve(rf_ctx* c, const double macro[6], const float* warm, double hom_str
   int st = run_iterations(c);
   if (st < 0) return st;
   if (int e = finish(c, 0, hom_stress)) return e;
-  for (int i = 0; i < 6; ++i) c->prev_macro[i] = macro[i];
+  for (int i = 0; i < 6; ++i) {
+    c->prev_macro[i] = macro[i];
+    c->prev_sbar[i] = c->last_sbar[i];
+  }
   if (iters) *iters = c->last_iters;
   if (residual) *residual = c->last_residual;
   return c->last_residual < c->opt.tol ? RF_OK : RF_NOT_CONVERGED;
@@ -951,6 +955,7 @@ int rf_solve_mixed(rf_ctx* c, const int32_t control[6], const double target[6], 
   if (int e = finish(c, 0, hom_stress)) return e;
   for (int i = 0; i < 6; ++i) {
     c->prev_macro[i] = E[i];
+    c->prev_sbar[i] = c->last_sbar[i];
     if (hom_strain) hom_strain[i] = E[i];
   }
   if (iters) *iters = c->last_iters;
@@ -972,8 +977,11 @@ int rf_solve_path_mixed(rf_ctx* c, const int32_t control[6], int32_t n_steps, co
   int status = RF_OK;
   for (int n = 0; n < n_steps; ++n) {
     const double* t = path + 6 * n;
-    double d[6], E0[6];
-    for (int i = 0; i < 6; ++i) d[i] = control[i] ? 0.0 : t[i] - c->prev_macro[i];
+    // start: the last converged strain plus the reference medium's response to the increment
+    // of the targets (stress increments measured from the last homogenised stress)
+    double incr[6], d[6], E0[6];
+    for (int i = 0; i < 6; ++i) incr[i] = control[i] ? t[i] - c->prev_sbar[i] : t[i] - c->prev_macro[i];
+    mixed_start(c, control, incr, d);
     mixed_start(c, control, t, E0);
     if (int e = init_status(c, E0, control, t)) return e;
     if (int e = launch_reset_er(c, d, 1.0)) return e;
@@ -984,6 +992,7 @@ int rf_solve_path_mixed(rf_ctx* c, const int32_t control[6], int32_t n_steps, co
     if (int e = finish(c, 1, hom_stress ? hom_stress + 6 * n : nullptr)) return e;
     for (int i = 0; i < 6; ++i) {
       c->prev_macro[i] = E[i];
+      c->prev_sbar[i] = c->last_sbar[i];
       if (hom_strain) hom_strain[6 * n + i] = E[i];
     }
     if (iters) iters[n] = c->last_iters;
@@ -1013,7 +1022,10 @@ int rf_solve_path(rf_ctx* c, int32_t n_steps, const double* path, double* hom_st
     int st = run_iterations(c);
     if (st < 0) return st;
     if (int e = finish(c, 1, hom_stress ? hom_stress + 6 * n : nullptr)) return e;
-    for (int i = 0; i < 6; ++i) c->prev_macro[i] = m[i];
+    for (int i = 0; i < 6; ++i) {
+      c->prev_macro[i] = m[i];
+      c->prev_sbar[i] = c->last_sbar[i];
+    }
     if (iters) iters[n] = c->last_iters;
     if (residuals) residuals[n] = c->last_residual;
     if (!(c->last_residual < c->opt.tol)) status = RF_NOT_CONVERGED;
@@ -1083,6 +1095,7 @@ struct StateHeader {
   int64_t N, rect;
   int32_t nc, ns;
   double prev_macro[6];
+  double prev_sbar[6];
 };
 
 int rf_get_state(rf_ctx* c, void* buf, size_t* bytes) {
@@ -1099,8 +1112,11 @@ int rf_get_state(rf_ctx* c, void* buf, size_t* bytes) {
   }
   if (*bytes < need) return invalid("rf_get_state: buffer too small");
   DeviceGuard dg(c->dev);
-  StateHeader h{0x52465354415445ull, c->N, c->rect, c->nc, c->ns, {0}};
-  for (int i = 0; i < 6; ++i) h.prev_macro[i] = c->prev_macro[i];
+  StateHeader h{0x52465354415446ull, c->N, c->rect, c->nc, c->ns, {0}, {0}};
+  for (int i = 0; i < 6; ++i) {
+    h.prev_macro[i] = c->prev_macro[i];
+    h.prev_sbar[i] = c->prev_sbar[i];
+  }
   char* p = static_cast<char*>(buf);
   std::memcpy(p, &h, sizeof h);
   p += sizeof h;
@@ -1127,7 +1143,7 @@ int rf_set_state(rf_ctx* c, const void* buf, size_t bytes) {
   std::memcpy(&h, buf, sizeof h);
   const size_t need = sizeof(StateHeader) + sizeof(float2) * c->rect +
                       sizeof(float) * (size_t)c->ns * c->N;
-  if (h.magic != 0x52465354415445ull || h.N != c->N || h.rect != c->rect || h.nc != c->nc ||
+  if (h.magic != 0x52465354415446ull || h.N != c->N || h.rect != c->rect || h.nc != c->nc ||
       h.ns != c->ns || bytes < need)
     return invalid("rf_set_state: state does not match this context");
   DeviceGuard dg(c->dev);
@@ -1140,7 +1156,10 @@ int rf_set_state(rf_ctx* c, const void* buf, size_t bytes) {
     if (int e = ck(cudaMemcpyAsync(c->d_state, p, sizeof(float) * c->ns * c->N,
                                    cudaMemcpyHostToDevice, c->stream), "restore"))
       return e;
-  for (int i = 0; i < 6; ++i) c->prev_macro[i] = h.prev_macro[i];
+  for (int i = 0; i < 6; ++i) {
+    c->prev_macro[i] = h.prev_macro[i];
+    c->prev_sbar[i] = h.prev_sbar[i];
+  }
   c->fields_valid = false;
   return ck(cudaStreamSynchronize(c->stream), "set state");
 }

@@ -236,8 +236,9 @@ struct rf_ctx {
   unsigned tc_cols = 0;
   size_t tc_smem = 0;
 
-  // load-path state
+  // load-path state: macroscopic strain and homogenised stress of the last solve or increment
   double prev_macro[6] = {0, 0, 0, 0, 0, 0};
+  double prev_sbar[6] = {0, 0, 0, 0, 0, 0};
 
   // compatibility step: a context on the same grid with the full set of frequencies (created
   // by the first rf_compat, dropped when the phase map changes)
