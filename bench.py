@@ -60,9 +60,10 @@ def parse():
                    help="c2 FFT mode: row-kernel blocks with the rows spread evenly (0: autotuned)")
     p.add_argument("--fft-cols", type=int, default=0,
                    help="c2 FFT mode: columns per column-kernel block (0: autotuned)")
-    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2],
+    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2, 3],
                    help="c2 FFT mode column phase: three kernels (-1), one fused kernel (1), "
-                        "Green operator inside the inverse y kernel (2), or timed (0)")
+                        "Green operator inside the inverse y kernel (2), the persistent solve "
+                        "(3), or timed (0)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "paper"],
@@ -767,6 +768,11 @@ def main():
                     ("dft", "inverse_y"): "k_dft_axis", ("dft", "forward_y"): "k_dft_axis"}
     if args.precision != "fp32" and dom == "row":
         kernel_names[("dft", "row")] = "k_tc_row"
+    if tile_info and tile_info.get("fft_fused") == 3:
+        # the persistent solve: one kernel; its stages are the row and the column phase, each
+        # timed up to its grid barrier by global-timer stamps of block 0
+        kernel_names[("fft", "row")] = "k_persist2d (row phase)"
+        kernel_names[("fft", "column_phase")] = "k_persist2d (column phase)"
     if args.transform == "fft" and dom in ("row", "inverse_y", "forward_y", "column_phase"):
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0

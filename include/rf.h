@@ -119,10 +119,12 @@ typedef struct rf_phase {
  *  fft_fuse   2D FFT mode, how the column phase between two row passes runs: -1 three kernels
  *             (forward y, Green-operator update with the convergence decision, inverse y);
  *             1 one kernel per group of kx columns (steps b to d of Sec. 4 fused); 2 forward y,
- *             then the Green-operator update and decision inside the inverse y kernel; 0 =
- *             chosen by timing the three when the pattern is set. Must be 0 or -1 in 3D. All
- *             give the same update up to the order of FP64 summation in the convergence
- *             measure.
+ *             then the Green-operator update and decision inside the inverse y kernel; 3 the
+ *             persistent solve: one cooperative launch per solve runs every update (row phase,
+ *             grid barrier, column phase per kx, grid barrier, decision) with the grid
+ *             co-resident (one or two blocks per SM); 0 = chosen by timing when the pattern is
+ *             set. Must be 0 or -1 in 3D. All give the same update up to the order of FP64
+ *             summation in the convergence measure.
  *  fft_fuse_kx  kx columns per block of the fused kernel (0 = chosen by timing; 1..16).
  *  fft_row_blocks  FFT mode: run the row kernel on this many blocks with the grid rows spread
  *             evenly (blocks differ by at most one row; clamped to the row count), instead of
@@ -166,11 +168,12 @@ typedef struct rf_info {
   int32_t fft_row_threads;/* FFT mode: threads per row-kernel block, else 0 */
   int32_t fft_cols;       /* FFT mode: columns per column-kernel block, else 0 */
   int32_t fft_col_threads;/* FFT mode: threads per column-kernel block, else 0 */
-  int32_t fft_fused;      /* column-phase mode in use (see fft_fuse): 0, 1 or 2 */
+  int32_t fft_fused;      /* column-phase mode in use (see fft_fuse): 0, 1, 2 or 3 */
   int32_t fft_fuse_kx;    /* kx columns per fused block, else 0 */
   int32_t fft_fuse_threads;/* threads per fused block, else 0 */
   int32_t fft_row_blocks; /* FFT mode: row-kernel blocks (fft_rows is the largest block's row
-                           * count; blocks may hold one row fewer to balance the SMs), else 0 */
+                           * count; blocks may hold one row fewer to balance the SMs), else 0;
+                           * the persistent solve's grid (and fft_row_threads its block size) */
 } rf_info;
 
 /* Create a solver context for one microstructure.

@@ -43,6 +43,7 @@ void init_attributes(int dev) {
   init_attributes_kernels();
   init_attributes_tc();
   init_attributes_fft();
+  init_attributes_persist();
   g_attr_done[dev] = true;
 }
 
@@ -285,6 +286,8 @@ void release_pattern_buffers(rf_ctx* c) {
   dfree(c->d_jent);
   dfree(c->d_jn);
   dfree(c->d_hk);
+  dfree(c->d_bar);
+  dfree(c->d_ptrace);
   c->pcap.clear();
 }
 
@@ -370,10 +373,41 @@ int init_status(rf_ctx* c, const double* macro, const int32_t* control = nullptr
                             c->stream), "upload status");
 }
 
+// Persistent 2D solve: one cooperative launch runs the updates; traced solves record the phase
+// stamps of every update (row phase, column phase, each up to its grid barrier).
+int run_persistent(rf_ctx* c) {
+  const int cap = c->tracing ? std::min(c->opt.max_iter, 8192) : 0;
+  if (cap > 0)
+    if (int e = palloc(c, &c->d_ptrace, 3 * (size_t)cap, "trace")) return e;
+  if (int e = launch_persist_solve(c, cap > 0 ? c->d_ptrace : nullptr, cap)) return e;
+  if (int e = ck(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status), cudaMemcpyDeviceToHost,
+                                 c->stream), "read status"))
+    return e;
+  if (int e = ck(cudaStreamSynchronize(c->stream), "persistent solve")) return e;
+  c->launched_iters = c->h_status->iters;
+  if (cap > 0) {
+    const int n = std::min(cap, c->h_status->iters);
+    std::vector<unsigned long long> t(3 * (size_t)std::max(n, 1));
+    if (n > 0) {
+      if (int e = ck(cudaMemcpy(t.data(), c->d_ptrace, sizeof(unsigned long long) * 3 * n,
+                                cudaMemcpyDeviceToHost), "read trace"))
+        return e;
+      for (int u = 0; u < n; ++u) {
+        c->stage_ms[2] += 1e-6 * (double)(t[3 * u + 1] - t[3 * u]);
+        c->stage_ms[6] += 1e-6 * (double)(t[3 * u + 2] - t[3 * u + 1]);
+        c->stage_n[2] += 1;
+        c->stage_n[6] += 1;
+      }
+    }
+  }
+  return RF_OK;
+}
+
 int run_iterations(rf_ctx* c) {
   const int maxchunk = c->opt.check_every > 0 ? c->opt.check_every : 32;
   int chunk = std::min(4, maxchunk);
-  if (c->fft_colmode != kColSeparate) {
+  const bool persistent = c->fft_colmode == kColPersistent;
+  if (!persistent && c->fft_colmode != kColSeparate) {
     // these updates end with the inverse transform along y of their new coefficients, so the
     // first one needs the line transforms of the start coefficients
     const bool tr = c->tracing;
@@ -382,8 +416,10 @@ int run_iterations(rf_ctx* c) {
     c->tracing = tr;
     if (e) return e;
   }
-  if (!c->tracing) get_while_graph(c);
-  if (!c->tracing && c->while_exec) {
+  if (!persistent && !c->tracing) get_while_graph(c);
+  if (persistent) {
+    if (int e = run_persistent(c)) return e;
+  } else if (!c->tracing && c->while_exec) {
     if (int e = ck(cudaGraphLaunch(c->while_exec, c->stream), "graph launch")) return e;
     if (int e = ck(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status),
                                    cudaMemcpyDeviceToHost, c->stream), "read status"))
@@ -409,7 +445,8 @@ int run_iterations(rf_ctx* c) {
   c->last_iters = c->h_status->iters;
   c->last_residual = c->h_status->last_r;
   if (c->h_status->timeout) {
-    set_error("a bounded device-side wait ran out in the tensor-core transform");
+    set_error(persistent ? "a grid barrier of the persistent solve ran out of its wait limit"
+                         : "a bounded device-side wait ran out in the tensor-core transform");
     return RF_ERR_TIMEOUT;
   }
   if (c->h_status->nonfinite) {
@@ -520,10 +557,10 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
     return invalid("options: wait_limit >= 0, stall_test 0 or 1");
   if (opt->stall_test && opt->precision == RF_PREC_FP32)
     return invalid("options: stall_test applies to the split-precision modes only");
-  if (opt->fft_fuse < -1 || opt->fft_fuse > 2 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
-    return invalid("options: fft_fuse in {-1, 0, 1, 2}, fft_fuse_kx in [0, 16]");
+  if (opt->fft_fuse < -1 || opt->fft_fuse > 3 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
+    return invalid("options: fft_fuse in {-1, 0, 1, 2, 3}, fft_fuse_kx in [0, 16]");
   if (opt->fft_fuse >= 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))
-    return invalid("options: fft_fuse 1 or 2 needs the FFT transform on a 2D grid");
+    return invalid("options: fft_fuse 1, 2 or 3 needs the FFT transform on a 2D grid");
   if (opt->transform == RF_TRANSFORM_FFT) {
     // 2^b or 3 * 2^b (the FFT stages are radix 16, 4, 2 and one radix-3)
     auto pow2 = [](int v) {
@@ -590,6 +627,7 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
              "upload phase map");
   if (!err && c->d_state)
     err = ck(cudaMemsetAsync(c->d_state, 0, sizeof(float) * c->ns * N, c->stream), "state");
+  if (!err) err = ck(cudaMemsetAsync(c->d_status, 0, sizeof(Status), c->stream), "status");
   if (!err) err = launch_setup_tables(c);
   if (!err) err = update_reference(c);
   if (err) {
@@ -856,6 +894,13 @@ int rf_set_pattern(rf_ctx* c, const int32_t* freqs, int64_t K) {
   if (!err) err = ck(cudaMemcpyAsync(d_hk, hk.data(), sizeof(int) * hk.size(), cudaMemcpyHostToDevice, c->stream), "up");
   if (!err) err = launch_hinfo(c, d_hk, c->Kh);
   if (!err && c->d_jent) err = launch_gather_jentries(c);
+  if (!err && fuse_ok && c->dim == 2) {
+    // persistent solve: barrier words and a first geometry (needed when forced, optional for
+    // the autotuner)
+    const int pe = persist_setup(c);
+    if (pe && c->opt.fft_fuse == 3) err = pe;
+    else if (pe) set_error("");
+  }
   if (!err && c->opt.precision != RF_PREC_FP32) err = tc_setup(c);
   if (!err) err = ck(cudaMemsetAsync(c->d_OUT, 0, sizeof(float2) * splits * c->rect, c->stream), "memset");
   if (!err && c->opt.transform == RF_TRANSFORM_FFT) err = fft_autotune(c);
@@ -1186,6 +1231,11 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   info->fft_fuse_kx = c->fft_colmode == kColFused ? c->fft_M : 0;
   info->fft_fuse_threads = c->fft_colmode == kColFused ? c->fft_M_threads : 0;
   info->fft_row_blocks = fft ? c->fft_blocks : 0;
+  if (c->fft_colmode == kColPersistent) {
+    info->fft_row_blocks = c->persist_G;
+    info->fft_row_threads = c->persist_threads;
+    info->fft_rows = (c->rows + c->persist_G - 1) / c->persist_G;
+  }
   return RF_OK;
 }
 

@@ -11,6 +11,7 @@
 // FP32 twiddle table computed in FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "rf_fftcore.cuh"
@@ -755,6 +756,7 @@ int fft_geometry(rf_ctx* c) {
   if (c->dim == 2 && c->opt.fft_fuse >= 0) {
     while (c->fft_M > 1 && colphase_smem(c->ny, c->nc, c->fft_M) > kFftSmemMax) --c->fft_M;
     const bool fits = colphase_smem(c->ny, c->nc, c->fft_M) <= kFftSmemMax;
+    if (c->opt.fft_fuse == 3) c->fft_colmode = kColPersistent;   // geometry set with the pattern
     if (c->opt.fft_fuse == 1) {
       if (!fits) {
         set_error("FFT mode: columns too long for the fused column kernel's shared memory");
@@ -953,7 +955,12 @@ int fft_autotune(rf_ctx* c) {
                          colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
   const bool fuse_shape = c->fft_colmode == kColFused && c->opt.fft_fuse_kx == 0;
   const bool rows_pinned = c->opt.fft_rows > 0 || c->opt.fft_row_blocks > 0;
-  if (rows_pinned && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape) return RF_OK;
+  // the persistent solve: compared with the other modes (fft_fuse 0) or only its geometry
+  // chosen (fft_fuse 3); needs the barrier words set up with the pattern
+  const bool persist_auto = c->dim == 2 && c->d_jptr && c->d_bar &&
+                            (c->opt.fft_fuse == 0 || c->opt.fft_fuse == 3);
+  if (rows_pinned && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape && !persist_auto)
+    return RF_OK;
   rf_ctx::Tuned& tu = c->tuned;
   if (tu.valid && tu.Kx == c->Kx && tu.Ky == c->Ky && tu.Kz == c->Kz) {
     // same transform shapes as the last tuning on this context: same choice
@@ -970,6 +977,10 @@ int fft_autotune(rf_ctx* c) {
       c->fft_M = tu.M;
       c->fft_M_threads = tu.M_threads;
       if (fuse_auto) c->fft_colmode = tu.colmode;
+    }
+    if (persist_auto && tu.persist_per_sm > 0 &&
+        persist_geometry(c, tu.persist_threads, tu.persist_per_sm)) {
+      if (c->opt.fft_fuse == 0 && tu.colmode == kColPersistent) c->fft_colmode = kColPersistent;
     }
     return RF_OK;
   }
@@ -1109,6 +1120,77 @@ int fft_autotune(rf_ctx* c) {
       else if (!err && best < sep) c->fft_colmode = kColFused;
     }
   }
+  if (!err && persist_auto) {
+    // per-update time of the best separate-kernel mode against the persistent solve (one launch
+    // of 8 updates with tol = 0; its start adds one inverse pass, which counts against it)
+    float t_np = 1e30f;
+    const int mode_np = c->fft_colmode == kColPersistent ? kColSeparate : c->fft_colmode;
+    if (c->opt.fft_fuse == 0) {
+      const int keep = c->fft_colmode;
+      c->fft_colmode = mode_np;
+      err = time_it([&] {
+        if (mode_np == kColFused) {
+          if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
+          return launch_fft_colphase(c, nullptr);
+        }
+        if (mode_np == kColGreenInv) {
+          if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
+          if (int e = fft_forward_stages(c, nullptr)) return e;
+          return launch_fft_green_inv(c, nullptr);
+        }
+        if (int e = fft_inverse_stages(c, nullptr)) return e;
+        if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
+        if (int e = fft_forward_stages(c, nullptr)) return e;
+        return launch_gamma_finalize(c, 1, nullptr);
+      }, &t_np);
+      t_np /= 3.f;
+      c->fft_colmode = keep;
+    }
+    constexpr int kUpd = 8;
+    Status& hs = *c->h_status;
+    std::memset(&hs, 0, sizeof(Status));
+    hs.max_iter = kUpd;
+    hs.tol = 0.0;
+    hs.enorm = 1.0;
+    hs.inv_n2 = 1.0 / ((double)c->N * (double)c->N);
+    hs.rmin = HUGE_VAL;
+    hs.lam0 = c->lam0;
+    hs.mu0 = c->mu0;
+    float best = 1e30f;
+    int bestT = 0, bestK = 0;
+    const int cand[4][2] = {{512, 2}, {256, 2}, {512, 1}, {256, 1}};
+    for (const auto& cd : cand) {
+      if (err || !persist_geometry(c, cd[0], cd[1])) continue;
+      float ms = 1e30f;
+      const int e = time_it([&] {
+        if (int e2 = tck(cudaMemcpyAsync(c->d_status, c->h_status, sizeof(Status),
+                                         cudaMemcpyHostToDevice, c->stream), "tuner"))
+          return e2;
+        return launch_persist_solve(c, nullptr, 0);
+      }, &ms);
+      if (e) {   // a launch the device refuses (co-residency) is not a candidate
+        cudaGetLastError();
+        set_error("");
+        continue;
+      }
+      ms /= 3.f * kUpd;
+      if (ms < best) {
+        best = ms;
+        bestT = cd[0];
+        bestK = cd[1];
+      }
+    }
+    if (bestT > 0) {
+      persist_geometry(c, bestT, bestK);
+      if (c->opt.fft_fuse == 3 || best < t_np) c->fft_colmode = kColPersistent;
+      else c->fft_colmode = mode_np;
+    } else if (c->opt.fft_fuse == 3) {
+      set_error("persistent solve: no cooperative launch of this pattern succeeded");
+      err = RF_ERR_CUDA;
+    } else {
+      c->fft_colmode = mode_np;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!err) {
@@ -1124,6 +1206,8 @@ int fft_autotune(rf_ctx* c) {
     tu.M = c->fft_M;
     tu.M_threads = c->fft_M_threads;
     tu.colmode = c->fft_colmode;
+    tu.persist_per_sm = c->persist_per_sm;
+    tu.persist_threads = c->persist_threads;
   }
   return err;
 }

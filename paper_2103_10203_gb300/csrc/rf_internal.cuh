@@ -210,6 +210,12 @@ struct rf_ctx {
   // (kColGreenInv). Modes 1 and 2 start a solve with one inverse y of the start coefficients.
   int fft_colmode = 0;
   int fft_M = 1, fft_M_threads = 256;   // kx columns and threads per fused block
+  // persistent 2D solve (column mode kColPersistent): grid, block size, dynamic shared memory,
+  // grid-barrier words, per-update phase stamps of traced solves
+  int persist_G = 0, persist_threads = 512, persist_per_sm = 0;
+  size_t persist_smem = 0;
+  unsigned* d_bar = nullptr;
+  unsigned long long* d_ptrace = nullptr;
   int* d_jptr = nullptr;                // [Kx + 1] offsets of each kx's entries in d_jlist
   int* d_jlist = nullptr;               // half-pattern entries grouped by kx index
   int2* d_jent = nullptr;               // in d_jlist order: (rectangle row iy, frequency kind)
@@ -221,6 +227,7 @@ struct rf_ctx {
     int R = 0, row_threads = 0, C = 0, col_threads = 0, M = 0, M_threads = 0;
     int row_blocks_balanced = 0;
     int colmode = 0;
+    int persist_per_sm = 0, persist_threads = 0;
   } tuned;
 
   // split-precision (tensor-core) transforms along x
@@ -421,7 +428,13 @@ int launch_tc_axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits,
                    long long out_bstride, int N, int batch, const int* done);
 int launch_fft_green_inv(rf_ctx* c, const int* done);
 int launch_gather_jentries(rf_ctx* c);
-constexpr int kColSeparate = 0, kColFused = 1, kColGreenInv = 2;
+constexpr int kColSeparate = 0, kColFused = 1, kColGreenInv = 2, kColPersistent = 3;
+// rf_persist.cu
+bool persist_geometry(rf_ctx* c, int threads, int per_sm);
+int launch_persist_solve(rf_ctx* c, unsigned long long* trace, int trace_cap);
+int launch_persist_final(rf_ctx* c, int commit);
+void init_attributes_persist();
+int persist_setup(rf_ctx* c);
 int launch_gamma_finalize(rf_ctx* c, int splits, const int* done);
 void trace_begin(rf_ctx* c, long long idx);
 void trace_stage(rf_ctx* c, int stage);

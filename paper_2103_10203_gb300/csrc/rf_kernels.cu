@@ -804,6 +804,17 @@ int launch_final(rf_ctx* c, int commit) {
   trace_stage(c, 7);
   const bool tr = c->tracing;
   c->tracing = false;   // the whole final pass is one stage
+  if (c->opt.transform == RF_TRANSFORM_FFT && c->fft_colmode == kColPersistent) {
+    // the persistent solve leaves the strain lines of the final coefficients in its layout
+    const int ie = launch_persist_final(c, commit);
+    c->tracing = tr;
+    if (ie) return ie;
+    k_reduce_sbar<<<1, 256, 0, c->stream>>>(c->d_sbar_part, c->d_viol_part, c->persist_G,
+                                            1.0 / (double)c->N, c->d_sbar);
+    int e = launch_check(c, "reduce_sbar");
+    trace_end(c);
+    return e;
+  }
   if (c->opt.transform == RF_TRANSFORM_FFT) {
     int ie = fft_inverse_stages(c, nullptr);
     if (!ie) ie = launch_fft_row(c, nullptr, true, commit);

@@ -182,7 +182,7 @@ __device__ __forceinline__ void gamma6(const float4& n, const float* t, float in
 // Gaussian elimination with partial pivoting. C0 acts on six-vectors with tensor shear:
 // normal rows lam0 + 2 mu0 delta_ij, shear columns 2 mu0. In plane strain E_33 = E_23 = E_13 = 0.
 template <int NC>
-__device__ inline void mixed_macro(const float2* tv, double Nd, const Status* st, double* E) {
+__device__ __noinline__ void mixed_macro(const float2* tv, double Nd, const Status* st, double* E) {
   double t6[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int c = 0; c < NC; ++c) t6[comp6<NC>(c)] = (double)tv[c].x / Nd;

@@ -23,7 +23,8 @@ def vec6_field(t):
 
 
 MODES = [dict(transform="dft"), dict(transform="fft", fft_fuse=-1),
-         dict(transform="fft", fft_fuse=1), dict(transform="fft", fft_fuse=2)]
+         dict(transform="fft", fft_fuse=1), dict(transform="fft", fft_fuse=2),
+         dict(transform="fft", fft_fuse=3)]
 
 
 @pytest.mark.parametrize("mode", range(len(MODES)))

@@ -471,6 +471,54 @@ def test_fft_fused_column_phase_small_sides(lib, shape, fuse):
     assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
 
 
+@pytest.mark.parametrize("name", ["c1", "fullset", "j2_64", "rect", "three"])
+def test_fft_persistent_solve_matches_oracle(lib, name):
+    """fft_fuse 3: every update of the solve in one cooperative launch (row phase, grid barrier,
+    column phase per kx with the Green operator, grid barrier, decision), line transforms in
+    column-major layout; the oracle's updates at the FP32 parity tolerances."""
+    pm, ph, macro, pat = _pow2_case(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=6, transform="fft", fft_fuse=3)
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    coeffs = s.rf_get_reduced_strain()
+    info = s.rf_get_info()
+    s.close()
+    assert info["fft_fused"] == 3 and info["fft_row_blocks"] > 0 and out["iters"] == 6
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=6)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    want = np.stack([r.eps_hat[:, i, j] for (i, j) in VOIGT], axis=1)
+    assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
+
+
+def test_fft_persistent_solve_load_path_and_tracing(lib):
+    """A J2 load path to the tolerance: the persistent solve takes the three-kernel mode's
+    decisions (update counts within one: FP64 sums in another order) and reaches its answer;
+    traced solves stamp every update's row and column phases."""
+    cfg = make_config("c2", n=256)
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    path = uniaxial_path(20, 0.02)[::5]
+    res = {}
+    for fuse in (-1, 3):
+        s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform="fft",
+                       fft_fuse=fuse)
+        s.rf_set_tracing(fuse == 3)
+        res[fuse] = (s.rf_solve_path(path), s.rf_get_fields()[0])
+        st = s.rf_get_stage_times()
+        s.close()
+        if fuse == 3:
+            n = int(np.sum(res[fuse][0]["iters"]))
+            assert st["row"][1] == n and st["column_phase"][1] == n and st["row"][0] > 0
+            assert st["final"][1] == len(path)
+    (a, ea), (b, eb) = res[-1], res[3]
+    assert a["converged"] and b["converged"]
+    assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
+    assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
+    assert rel(eb, ea) <= 2e-5
+
+
 def test_fft_fused_and_separate_column_phases_agree(lib):
     """Full load path to the tolerance: the fused and the three-kernel column phases take the
     same decisions (iteration counts within one: FP64 sums in another order) and reach the same
@@ -502,7 +550,9 @@ def test_fft_fuse_option_checks(lib):
     with pytest.raises(lib.RFError):
         lib.Solver(pm, elastic_phases(), transform="fft", fft_fuse=2)
     with pytest.raises(lib.RFError):
-        lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="fft", fft_fuse=3)
+        lib.Solver(pm, elastic_phases(), transform="fft", fft_fuse=3)
+    with pytest.raises(lib.RFError):
+        lib.Solver(np.zeros((16, 16), np.uint8), elastic_phases(), transform="fft", fft_fuse=4)
 
 
 @pytest.mark.parametrize("name,blocks", [("j2_64", 5), ("j2_64", 64), ("j2_64", 1000),
