@@ -123,7 +123,8 @@ typedef struct rf_phase {
  *             persistent solve: one cooperative launch per solve runs every update (row phase,
  *             grid barrier, column phase per kx, grid barrier, decision) with the grid
  *             co-resident (one or two blocks per SM); 0 = chosen by timing when the pattern is
- *             set. Must be 0 or -1 in 3D. All give the same update up to the order of FP64
+ *             set (the persistent solve only when fft_rows and fft_row_blocks are 0). Must be 0
+ *             or -1 in 3D. All give the same update up to the order of FP64
  *             summation in the convergence measure.
  *  fft_fuse_kx  kx columns per block of the fused kernel (0 = chosen by timing; 1..16).
  *  fft_row_blocks  FFT mode: run the row kernel on this many blocks with the grid rows spread

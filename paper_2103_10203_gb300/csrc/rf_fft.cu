@@ -955,10 +955,11 @@ int fft_autotune(rf_ctx* c) {
                          colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
   const bool fuse_shape = c->fft_colmode == kColFused && c->opt.fft_fuse_kx == 0;
   const bool rows_pinned = c->opt.fft_rows > 0 || c->opt.fft_row_blocks > 0;
-  // the persistent solve: compared with the other modes (fft_fuse 0) or only its geometry
-  // chosen (fft_fuse 3); needs the barrier words set up with the pattern
+  // the persistent solve: compared with the other modes (fft_fuse 0, unless the row kernel's
+  // tiles are pinned) or only its geometry chosen (fft_fuse 3); needs the barrier words set up
+  // with the pattern
   const bool persist_auto = c->dim == 2 && c->d_jptr && c->d_bar &&
-                            (c->opt.fft_fuse == 0 || c->opt.fft_fuse == 3);
+                            ((c->opt.fft_fuse == 0 && !rows_pinned) || c->opt.fft_fuse == 3);
   if (rows_pinned && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape && !persist_auto)
     return RF_OK;
   rf_ctx::Tuned& tu = c->tuned;
