@@ -30,7 +30,6 @@
 
 namespace rfk {
 
-using fftc::copy_twiddles;
 using fftc::fft_block;
 using fftc::span_of;
 using fftc::stage_len;
@@ -390,13 +389,13 @@ __global__ __launch_bounds__(TPB, 2) void k_persist2d(const __grid_constant__ Pe
   __shared__ int s_flag;
   __shared__ int s_done;
   const int tid = threadIdx.x, nt = blockDim.x;
-  float2* twx = reinterpret_cast<float2*>(smem);
-  float2* twy = twx + stage_len(a.Nx);
-  float2* b0 = twy + stage_len(a.Ny);
+  // the stage-major twiddle tables are read from global memory (read-only for the launch, so
+  // L1-cached), which leaves shared memory to the two work buffers of two CTAs per SM
+  const float2* twx = a.twx + fftc::stage_offset(a.Nx);
+  const float2* twy = a.twy + fftc::stage_offset(a.Ny);
+  float2* b0 = reinterpret_cast<float2*>(smem);
   float2* b1 = b0 + a.span_buf;
   int* kxs = reinterpret_cast<int*>(b1 + a.span_buf);
-  copy_twiddles(a.twx, a.Nx, twx);
-  copy_twiddles(a.twy, a.Ny, twy);
   for (int i = tid; i < a.Kx; i += nt) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += nt) phs[i] = a.law.ph[i];
   __syncthreads();
@@ -482,12 +481,10 @@ __global__ __launch_bounds__(512) void k_persist_final(const __grid_constant__ P
   __shared__ double red[32];
   __shared__ DevPhase phs[kMaxPhases];
   const int tid = threadIdx.x, nt = blockDim.x;
-  float2* twx = reinterpret_cast<float2*>(smem);
-  float2* twy = twx + stage_len(a.Nx);
-  float2* b0 = twy + stage_len(a.Ny);
+  const float2* twx = a.twx + fftc::stage_offset(a.Nx);
+  float2* b0 = reinterpret_cast<float2*>(smem);
   float2* b1 = b0 + a.span_buf;
   int* kxs = reinterpret_cast<int*>(b1 + a.span_buf);
-  copy_twiddles(a.twx, a.Nx, twx);
   for (int i = tid; i < a.Kx; i += nt) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += nt) phs[i] = a.law.ph[i];
   __syncthreads();
@@ -498,11 +495,12 @@ __global__ __launch_bounds__(512) void k_persist_final(const __grid_constant__ P
 // host side
 namespace {
 
+constexpr size_t kPersistSmemMax = 227 * 1024;   // dynamic shared memory per block (sm_103a)
+
 size_t persist_smem(const rf_ctx* c, int R) {
   const int P = (R * 3 + 1) / 2;
   const int span = std::max(span_of(P * c->nx), span_of(3 * c->ny));
-  return ((size_t)stage_len(c->nx) + stage_len(c->ny) + 2 * (size_t)span) * sizeof(float2) +
-         (size_t)c->Kx * sizeof(int) + 16;
+  return 2 * (size_t)span * sizeof(float2) + (size_t)c->Kx * sizeof(int) + 16;
 }
 
 template <bool PL>
@@ -572,7 +570,7 @@ bool persist_geometry(rf_ctx* c, int threads, int per_sm) {
   if (G < 1) return false;
   const int R = c->rows / G + (c->rows % G ? 1 : 0);
   const size_t smem = persist_smem(c, R);
-  if (smem > 200 * 1024) return false;
+  if (smem > kPersistSmemMax) return false;
   if (threads != 256 && threads != 512) return false;
   int occ = 0;
   const void* k = c->has_plastic ? persist_kernel<true>(threads) : persist_kernel<false>(threads);
@@ -603,11 +601,11 @@ int persist_setup(rf_ctx* c) {
 void init_attributes_persist() {
   for (const void* k : {(const void*)k_persist2d<true, 512>, (const void*)k_persist2d<true, 256>,
                         (const void*)k_persist2d<false, 512>, (const void*)k_persist2d<false, 256>})
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPersistSmemMax);
   cudaFuncSetAttribute(k_persist_final<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
+                       (int)kPersistSmemMax);
   cudaFuncSetAttribute(k_persist_final<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
+                       (int)kPersistSmemMax);
 }
 
 // One cooperative launch: the start's inverse along y, then updates until the decision ends the
