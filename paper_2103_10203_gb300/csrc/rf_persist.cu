@@ -495,7 +495,9 @@ __global__ __launch_bounds__(512) void k_persist_final(const __grid_constant__ P
 // host side
 namespace {
 
-constexpr size_t kPersistSmemMax = 227 * 1024;   // dynamic shared memory per block (sm_103a)
+// dynamic shared memory per block: the 227 KB per-block limit of sm_103a less room for the
+// kernels' static shared memory
+constexpr size_t kPersistSmemMax = 226 * 1024;
 
 size_t persist_smem(const rf_ctx* c, int R) {
   const int P = (R * 3 + 1) / 2;
@@ -606,6 +608,7 @@ void init_attributes_persist() {
                        (int)kPersistSmemMax);
   cudaFuncSetAttribute(k_persist_final<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)kPersistSmemMax);
+  cudaGetLastError();   // a refused attribute only narrows the geometries that fit
 }
 
 // One cooperative launch: the start's inverse along y, then updates until the decision ends the
