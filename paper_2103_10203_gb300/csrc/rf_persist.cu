@@ -113,7 +113,7 @@ __device__ bool grid_sync(unsigned* bar, long limit, int* s_flag) {
 
 // Row phase of one CTA (see the top of the file). FINAL: fields, homogenised-stress partials,
 // FP64 check of the return map and the commit, instead of the forward transform.
-template <bool PLASTIC, bool FINAL>
+template <bool PLASTIC, bool FINAL, int kVox>
 __device__ void p_row(const PersistArgs& a, const float2* tw, float2* b0, float2* b1,
                       const int* kxs, const DevPhase* phs, double* red) {
   constexpr int NC = 3, NS = 4;
@@ -183,7 +183,6 @@ __device__ void p_row(const PersistArgs& a, const float2* tw, float2* b0, float2
   double sb[6] = {0, 0, 0, 0, 0, 0};
   double vmax = 0.0;
   const float lam0 = a.law.lam0, mu0 = a.law.mu0;
-  constexpr int kVox = 4;
   for (int vb = 0; vb < R * L; vb += kVox * nt) {
     int pid[kVox];
     float stv[kVox][NS];
@@ -316,9 +315,23 @@ __device__ double p_col(const PersistArgs& a, int j, bool full, const float2* tw
   float2* w = b0;
   float2* scratch = b1;
   if (full) {
-    for (int i = tid; i < NC * L; i += nt) {
-      const int c = fdiv(i, a.dNy), y = i - c * L;
-      b0[sw(i)] = __ldcg(a.T1p + (long long)(c * Kx + j) * L + y);
+    // the NC columns of this kx, loads issued kL at a time before their stores
+    constexpr int kL = 8;
+    for (int i0 = tid; i0 < NC * L; i0 += kL * nt) {
+      float2 v[kL];
+#pragma unroll
+      for (int u = 0; u < kL; ++u) {
+        const int i = i0 + u * nt;
+        if (i < NC * L) {
+          const int c = fdiv(i, a.dNy), y = i - c * L;
+          v[u] = __ldcg(a.T1p + (long long)(c * Kx + j) * L + y);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kL; ++u) {
+        const int i = i0 + u * nt;
+        if (i < NC * L) b0[sw(i)] = v[u];
+      }
     }
     __syncthreads();
     z = fft_block(b0, b1, tw, L, NC, -1);
@@ -327,20 +340,47 @@ __device__ double p_col(const PersistArgs& a, int j, bool full, const float2* tw
   }
   for (int i = tid; i < span; i += nt) w[i] = make_float2(0.f, 0.f);
   __syncthreads();
-  float diff = 0.f;   // summed in FP64 below; one frequency's squared increment in FP32
-  double dsum = 0.0;
+  double dsum = 0.0;   // FP64 sum of the frequencies' squared increments (each in FP32)
   const int e0 = a.jptr[j], e1 = a.jptr[j + 1];
-  for (int e = e0 + tid; e < e1; e += nt) {
-    const int2 en = a.jent[e];
-    const int pos = a.kym[en.x];
-    const long long base = (long long)en.x * NC * Kx + j;
-    if (full) {
-      const float4 n = a.jn[e];
-      const bool mixed0 = en.y == 1 && a.st->mixed;
+  // the entries of this kx, kE per thread at a time: their indices, then their positions and
+  // old coefficients, each group of loads issued together
+  constexpr int kE = 2;
+  for (int eb0 = e0 + tid; eb0 < e1; eb0 += kE * nt) {
+    int2 en[kE];
+    float4 n[kE];
+    int pos[kE];
+    float2 old[kE][NC];
+#pragma unroll
+    for (int u = 0; u < kE; ++u) {
+      const int e = eb0 + u * nt;
+      en[u] = make_int2(0, -1);
+      if (e < e1) {
+        en[u] = a.jent[e];
+        if (full) n[u] = a.jn[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kE; ++u) {
+      if (en[u].y < 0) continue;
+      pos[u] = a.kym[en[u].x];
+      const long long base = (long long)en[u].x * NC * Kx + j;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) old[u][c] = __ldcg(a.ER + base + (long long)c * Kx);
+    }
+#pragma unroll
+    for (int u = 0; u < kE; ++u) {
+      if (en[u].y < 0) continue;
+      const long long base = (long long)en[u].x * NC * Kx + j;
+      if (!full) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) w[sw(c * L + pos[u])] = old[u][c];
+        continue;
+      }
+      const bool mixed0 = en[u].y == 1 && a.st->mixed;
       float2 tv[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c)
-        tv[c] = (en.y == 0 || mixed0) ? z[sw(c * L + pos)] : make_float2(0.f, 0.f);
+        tv[c] = (en[u].y == 0 || mixed0) ? z[sw(c * L + pos[u])] : make_float2(0.f, 0.f);
       const double* eb = a.st->ebar;
       double em[6];
       if (mixed0) {
@@ -349,22 +389,18 @@ __device__ double p_col(const PersistArgs& a, int j, bool full, const float2* tw
         eb = em;
       }
       float er[NC], ei[NC];
-      green_update<NC>(en.y, n, tv, eb, a.Nd, a.inv2mu0, a.cgam, er, ei);
-      diff = 0.f;
+      green_update<NC>(en[u].y, n[u], tv, eb, a.Nd, a.inv2mu0, a.cgam, er, ei);
+      float diff = 0.f;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const float2 old = __ldcg(a.ER + base + (long long)c * Kx);
-        const float dr = er[c] - old.x, di = ei[c] - old.y;
+        const float dr = er[c] - old[u][c].x, di = ei[c] - old[u][c].y;
         const float wc = (comp6<NC>(c) >= 3) ? 2.f : 1.f;   // Frobenius: shear counted twice
-        diff = fmaf(n.w * wc, dr * dr + di * di, diff);
+        diff = fmaf(n[u].w * wc, dr * dr + di * di, diff);
         const float2 nv = make_float2(er[c], ei[c]);
         a.ER[base + (long long)c * Kx] = nv;
-        w[sw(c * L + pos)] = nv;
+        w[sw(c * L + pos[u])] = nv;
       }
       dsum += (double)diff;
-    } else {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) w[sw(c * L + pos)] = __ldcg(a.ER + base + (long long)c * Kx);
     }
   }
   double t = 0.0;
@@ -379,10 +415,10 @@ __device__ double p_col(const PersistArgs& a, int j, bool full, const float2* tw
   return t;
 }
 
-// TPB threads per block, two blocks per SM (the register budget follows: 64 per thread at 512,
-// 128 at 256)
+// TPB threads per block: 256 (two blocks per SM) or 512 (one block per SM), 128 registers per
+// thread either way
 template <bool PLASTIC, int TPB>
-__global__ __launch_bounds__(TPB, 2) void k_persist2d(const __grid_constant__ PersistArgs a) {
+__global__ __launch_bounds__(TPB, 512 / TPB) void k_persist2d(const __grid_constant__ PersistArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[32];
   __shared__ DevPhase phs[kMaxPhases];
@@ -416,7 +452,7 @@ __global__ __launch_bounds__(TPB, 2) void k_persist2d(const __grid_constant__ Pe
   }
   if (a.trace && blockIdx.x == 0 && tid == 0) s_tupd = global_ns();
   for (int u = 0;; ++u) {
-    p_row<PLASTIC, false>(a, twx, b0, b1, kxs, phs, red);
+    p_row<PLASTIC, false, 4>(a, twx, b0, b1, kxs, phs, red);
     if (!grid_sync(a.bar, a.bar_limit, &s_flag)) {
       if (tid == 0) atomicExch(&a.st->timeout, 1);
       return;
@@ -488,7 +524,7 @@ __global__ __launch_bounds__(512) void k_persist_final(const __grid_constant__ P
   for (int i = tid; i < a.Kx; i += nt) kxs[i] = a.kx[i];
   for (int i = tid; i < kMaxPhases; i += nt) phs[i] = a.law.ph[i];
   __syncthreads();
-  p_row<PLASTIC, true>(a, twx, b0, b1, kxs, phs, red);
+  p_row<PLASTIC, true, 4>(a, twx, b0, b1, kxs, phs, red);
 }
 
 // ------------------------------------------------------------------------------------------
