@@ -127,8 +127,10 @@ __device__ void p_row(const PersistArgs& a, const float2* tw, float2* b0, float2
   __syncthreads();
   // line coefficients: item u = q R + r with q = c Kx + j (R consecutive rows of one line column
   // are contiguous); line s = r NC + c is the real (s even) or imaginary (s odd) carrier of
-  // sequence s / 2. A batch loads first, then the real carriers write, then (after a barrier)
-  // the imaginary carriers add. The batch loop's trip count is the same for every thread.
+  // sequence s / 2. The two carriers of a sequence can fall in different batches, so both add
+  // into the zeroed buffer: per batch the real carriers first, then (after a barrier) the
+  // imaginary ones, one writer per location in each pass. The batch loop's trip count is the
+  // same for every thread.
   constexpr int kB = 8;
   const int nsc = S * Kx;
   for (int base = 0; base < nsc; base += kB * nt) {
@@ -155,8 +157,14 @@ __device__ void p_row(const PersistArgs& a, const float2* tw, float2* b0, float2
       float2 v = t[m];
       if (self) v.y = 0.f;
       const int zb0 = (sl[m] >> 1) * L;
-      b0[sw(zb0 + k)] = v;
-      if (!self) b0[sw(zb0 + L - k)] = make_float2(v.x, -v.y);
+      float2& zk = b0[sw(zb0 + k)];   // add v at k and conj(v) at L - k
+      zk.x += v.x;
+      zk.y += v.y;
+      if (!self) {
+        float2& zm = b0[sw(zb0 + L - k)];
+        zm.x += v.x;
+        zm.y -= v.y;
+      }
     }
     __syncthreads();
 #pragma unroll

@@ -492,6 +492,23 @@ def test_fft_persistent_solve_matches_oracle(lib, name):
     assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
 
 
+def test_fft_persistent_solve_full_size_c2(lib):
+    """The 1024^2 J2 composite in the persistent solve: a row block's line coefficients span
+    several load batches here (12 lines x 250 kx against 8 loads per thread), so the two carriers
+    of a packed sequence meet across batches. Three updates against the oracle."""
+    cfg = make_config("c2")
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    macro = np.array([0.02, 0, 0, 0, 0, 0])
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft", fft_fuse=3)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    s.close()
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=3)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
 def test_fft_persistent_solve_load_path_and_tracing(lib):
     """A J2 load path to the tolerance: the persistent solve takes the three-kernel mode's
     decisions (update counts within one: FP64 sums in another order) and reaches its answer;
