@@ -657,6 +657,40 @@ def run_paper(args, rf, torch):
     print(json.dumps(out), flush=True)
 
 
+def voxel_sweep(rf, torch, reps=20):
+    """The unfused constitutive sweep (step a on its own) over the 1024^2 J2 composite tiled 4 x 4
+    to 4096^2 (16.8 M voxels, fields far larger than L2): strain planes in, polarization planes
+    out, phase map and J2 state read; 41 bytes per voxel. Achieved bandwidth from CUDA events
+    over `reps` launches against the measured HBM copy bandwidth."""
+    from synth import make_config
+    cfg = make_config("c2")
+    pm = np.ascontiguousarray(np.tile(cfg["phase_map"], (4, 4)))
+    N = pm.size
+    s = rf.Solver(pm, cfg["phases"])
+    g = torch.Generator(device="cuda").manual_seed(7)
+    eps = (torch.rand((3, N), device="cuda", generator=g) - 0.5) * 0.04
+    tau = torch.empty_like(eps)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        s.rf_law_sweep(eps, tau)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s.rf_law_sweep(eps, tau)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    s.close()
+    bpv = 3 * 4 + 1 + 4 * 4 + 3 * 4
+    hbm = _hbm_peak()
+    achieved = bpv * N / (ms / 1e3) / 1e9
+    return {"kernel": "k_law_sweep<3, J2>", "voxels": int(N), "bytes_per_voxel": bpv,
+            "launch_ms": ms, "achieved_GBs": achieved, "peak_GBs": hbm, "frac": achieved / hbm,
+            "what": "strain 12 B + phase 1 B + J2 state 16 B in, polarization 12 B out per voxel; "
+                    "4096^2 tiling of the 1024^2 J2 composite, fields larger than L2"}
+
+
 def _hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(p))["hbm_gbs"] if os.path.exists(p) else 6800.0
@@ -831,6 +865,12 @@ def main():
                       "(Sec. 5.1), fields and homogenised stress",
               "per_reduced_update_ms": float(np.sum(ms_steps)) / max(1, iters)}
 
+    sweep_line = None
+    try:
+        sweep_line = voxel_sweep(rf, torch)
+    except Exception as ex:
+        sweep_line = {"error": repr(ex)}
+
     study = None
     if rank == 0 and not args.no_study:
         try:
@@ -864,6 +904,7 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof, "stage_share": stage_share,
                 "tiles": tile_info,
                 "cpu_baseline": cpu, "clocks": clocks, "compat": compat,
+                "unfused_voxel_sweep": sweep_line,
                 "pattern_study": study,
                 "c4_bounded": subs.get("c4"), "c5_bounded": subs.get("c5"),
                 "precision": {"fp32": "FP32 transforms and law",

@@ -283,6 +283,16 @@ int rf_reset_stage_times(rf_ctx* ctx);
  * Errors: RF_ERR_STATE if no solve has produced fields yet; RF_ERR_OOM; RF_ERR_NONFINITE. */
 int rf_compat(rf_ctx* ctx, double hom_stress[6]);
 
+/* Constitutive sweep on its own (step a of Sec. 4, unfused): for every voxel,
+ * tau = sigma(eps) - C0 : eps with the context's phase map, phases, reference medium and internal
+ * variables (held fixed), from strain planes in DEVICE memory.
+ *  d_eps: DEVICE float [NC][N] (NC = 3 in 2D: 11, 22, 12; 6 in 3D: 11, 22, 33, 23, 13, 12),
+ *  d_tau: DEVICE float [NC][N] output, d_sig: nullable DEVICE float [NC][N] stress output.
+ *  N must be a multiple of 4 and the pointers 16-byte aligned (16-byte loads and stores).
+ * Asynchronous: enqueued on the context's stream. The fused solver runs the same law inside its
+ * row kernels; this entry point exists to measure and use the sweep by itself. */
+int rf_law_sweep(rf_ctx* ctx, const float* d_eps, float* d_tau, float* d_sig);
+
 /* Error measures of Sec. 5 between the fields a context holds now (after a solve or
  * rf_compat) and those of a reference context on the same grid and device (typically a solve
  * with the full set of frequencies):

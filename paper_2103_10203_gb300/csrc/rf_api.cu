@@ -1374,6 +1374,16 @@ int rf_compat(rf_ctx* c, double hom_stress[6]) {
   return RF_OK;
 }
 
+int rf_law_sweep(rf_ctx* c, const float* d_eps, float* d_tau, float* d_sig) {
+  if (!c || !d_eps || !d_tau) return invalid("rf_law_sweep: null argument");
+  if (c->N % 4 != 0) return invalid("rf_law_sweep: the voxel count must be a multiple of 4");
+  auto mis = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; };
+  if (mis(d_eps) || mis(d_tau) || (d_sig && mis(d_sig)))
+    return invalid("rf_law_sweep: field pointers must be 16-byte aligned");
+  DeviceGuard dg(c->dev);
+  return launch_law_sweep(c, d_eps, d_tau, d_sig);
+}
+
 int rf_stress_errors(rf_ctx* c, const rf_ctx* ref, double* Ebar, double* E) {
   if (!c || !ref || !Ebar || !E) return invalid("rf_stress_errors: null argument");
   if (c->nx != ref->nx || c->ny != ref->ny || c->nz != ref->nz || c->dev != ref->dev)

@@ -409,6 +409,7 @@ int launch_reset_er(rf_ctx* c, const double* ebar6, double scale_old);
 int launch_warm_project(rf_ctx* c, const float2* d_warm6, const double* ebar6);
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist);
 int launch_scatter_full(rf_ctx* c, rf_ctx* full);
+int launch_law_sweep(rf_ctx* c, const float* eps, float* tau, float* sig);
 constexpr int kErrBlocks = 304;
 int launch_stress_errors(rf_ctx* c, const float* sig_ref, const double* sbar,
                          const double* sbar_ref);

@@ -11,6 +11,7 @@
 //   finalize: convergence measure (FP64), device flag      criterion of Sec. 3
 // Every kernel returns at once when the device flag says the solve is done, so the host can
 // enqueue several iterations between checks without changing the result.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -622,6 +623,97 @@ int launch_stress_errors(rf_ctx* c, const float* sig_ref, const double* sb, cons
                                               sb[3], sb[4], sb[5], sr[0], sr[1], sr[2], sr[3],
                                               sr[4], sr[5], c->d_err + kErrBlocks);
   return launch_check(c, "stress errors");
+}
+
+// Constitutive sweep on its own (step a of Sec. 4 unfused): tau = sigma(eps) - C0 : eps per voxel
+// from strain planes in device memory, four consecutive voxels per thread with 16-byte loads and
+// stores of every plane (N a multiple of 4, planes 16-byte aligned), grid-stride over the
+// voxels. State frozen (read only).
+template <int NC, bool PLASTIC>
+__global__ __launch_bounds__(256) void k_law_sweep(const float* __restrict__ eps,
+                                                   const uint8_t* __restrict__ phase,
+                                                   const float* __restrict__ state, long long N,
+                                                   LawParams law, float* __restrict__ tau,
+                                                   float* __restrict__ sig) {
+  constexpr int NS = NC == 3 ? 4 : 7;
+  __shared__ DevPhase phs[kMaxPhases];
+  for (int i = threadIdx.x; i < kMaxPhases; i += blockDim.x) phs[i] = law.ph[i];
+  __syncthreads();
+  const long long n4 = N >> 2;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4;
+       q += (long long)gridDim.x * blockDim.x) {
+    float4 e4[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) e4[c] = __ldcs(reinterpret_cast<const float4*>(eps + c * N) + q);
+    const uchar4 p4 = __ldcs(reinterpret_cast<const uchar4*>(phase) + q);
+    float4 s4[NS];
+    if (PLASTIC) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) s4[i] = __ldcs(reinterpret_cast<const float4*>(state + i * N) + q);
+    }
+    float4 t4[NC], o4[NC];
+    const uint8_t pid[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      auto pick = [v](const float4& f) { return v == 0 ? f.x : v == 1 ? f.y : v == 2 ? f.z : f.w; };
+      float e[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) e[c] = pick(e4[c]);
+      float e6[6];
+      comp_to6<NC>(e, e6);
+      float ep[6] = {0, 0, 0, 0, 0, 0};
+      float alpha = 0.f;
+      if (PLASTIC) {
+        if (NC == 3) {
+          ep[0] = pick(s4[0]);
+          ep[1] = pick(s4[1]);
+          ep[5] = pick(s4[2]);
+          ep[2] = -(ep[0] + ep[1]);
+          alpha = pick(s4[3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) ep[i] = pick(s4[i]);
+          alpha = pick(s4[6]);
+        }
+      }
+      LawOut o;
+      stress6<PLASTIC>(e6, phs[pid[v]], ep, alpha, o);
+      const float tr = e6[0] + e6[1] + e6[2];
+      float tau6[6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (law.lam0 * tr + 2.f * law.mu0 * e6[i]);
+#pragma unroll
+      for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * law.mu0 * e6[i];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float* tp = reinterpret_cast<float*>(&t4[c]);
+        float* sp = reinterpret_cast<float*>(&o4[c]);
+        tp[v] = tau6[comp6<NC>(c)];
+        sp[v] = o.s[comp6<NC>(c)];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      __stcs(reinterpret_cast<float4*>(tau + c * N) + q, t4[c]);
+      if (sig) __stcs(reinterpret_cast<float4*>(sig + c * N) + q, o4[c]);
+    }
+  }
+}
+
+int launch_law_sweep(rf_ctx* c, const float* eps, float* tau, float* sig) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+  const long long n4 = c->N >> 2;
+  const int grid = (int)std::max(1LL, std::min<long long>(8LL * sms, (n4 + 255) / 256));
+  const bool pl = c->has_plastic;
+  if (c->nc == 3) {
+    if (pl) k_law_sweep<3, true><<<grid, 256, 0, c->stream>>>(eps, c->d_phase, c->d_state, c->N, c->law, tau, sig);
+    else k_law_sweep<3, false><<<grid, 256, 0, c->stream>>>(eps, c->d_phase, c->d_state, c->N, c->law, tau, sig);
+  } else {
+    if (pl) k_law_sweep<6, true><<<grid, 256, 0, c->stream>>>(eps, c->d_phase, c->d_state, c->N, c->law, tau, sig);
+    else k_law_sweep<6, false><<<grid, 256, 0, c->stream>>>(eps, c->d_phase, c->d_state, c->N, c->law, tau, sig);
+  }
+  return launch_check(c, "law sweep");
 }
 
 int launch_phase_hist(rf_ctx* c, unsigned long long* d_hist) {

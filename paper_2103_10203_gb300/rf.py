@@ -98,6 +98,7 @@ def _load() -> C.CDLL:
         "rf_solve_mixed": [P, P, P, P, P, P, P, P],
         "rf_solve_path_mixed": [P, P, i32, P, P, P, P, P],
         "rf_stress_errors": [P, P, P, P],
+        "rf_law_sweep": [P, P, P, P],
         "rf_pattern_adapted": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_radial": [C.POINTER(rf_grid), i64, P, i64, C.POINTER(i64), P],
         "rf_pattern_adapted_noalloc": [C.POINTER(rf_grid), P, i32, i64, P, i64, C.POINTER(i64),
@@ -149,6 +150,7 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy",
             "rf_batch_slots", "rf_batch_descriptors", "rf_batch_reduced_strain",
             "rf_batch_solve_warm", "rf_compat", "rf_stress_errors", "rf_solve_mixed",
+            "rf_law_sweep",
             "rf_solve_path_mixed",
             "rf_mlp_create", "rf_mlp_get_dims", "rf_mlp_set_params", "rf_mlp_get_params",
             "rf_mlp_get_grads", "rf_mlp_forward", "rf_mlp_targets", "rf_mlp_loss_grad",
@@ -343,6 +345,11 @@ class Solver:
                                               _ptr(ebar), _ptr(its), _ptr(res)))
         return dict(sigma_bar=sbar, strain_bar=ebar, iters=its, residuals=res,
                     converged=code == RF_OK)
+
+    def rf_law_sweep(self, eps, tau, sig=None):
+        """Unfused constitutive sweep on CUDA tensors eps, tau (and sig) of shape [NC, N] float32
+        (enqueued on the context's stream)."""
+        _check(lib.rf_law_sweep(self.ctx, _dptr(eps), _dptr(tau), _dptr(sig)), allow_nc=False)
 
     def rf_reset_path(self):
         _check(lib.rf_reset_path(self.ctx), allow_nc=False)

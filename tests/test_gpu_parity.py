@@ -733,3 +733,41 @@ def test_traced_chunked_and_untraced_while_graph_solves_agree(lib, transform, fu
         assert info["kernel_launches"] > 0
     assert np.array_equal(res[False]["iters"], res[True]["iters"])
     assert np.array_equal(res[False]["sigma_bar"], res[True]["sigma_bar"])
+
+
+# ----------------------------------------------------------------------------- unfused sweep
+@pytest.mark.parametrize("dim,plastic", [(2, False), (2, True), (3, False), (3, True)])
+def test_unfused_law_sweep_matches_oracle(lib, dim, plastic):
+    """rf_law_sweep (step a on its own): tau = sigma(eps) - C0 : eps per voxel from random strain
+    planes (magnitude 2 %, so the J2 matrix yields from the virgin state), against the oracle's
+    law and reference medium; FP32 return map against FP64 at 1e-5 of the largest stress."""
+    import torch
+    rng = np.random.default_rng(dim * 10 + plastic)
+    shape = (36, 44) if dim == 2 else (8, 12, 14)
+    pm = (rng.random(shape) < 0.4).astype(np.uint8)
+    ph = j2_phases() if plastic else elastic_phases()
+    nc = 3 if dim == 2 else 6
+    N = pm.size
+    eps = rng.uniform(-0.02, 0.02, size=(nc, N)).astype(np.float32)
+    s = lib.Solver(pm, ph)
+    d_eps = torch.as_tensor(eps, device="cuda")
+    d_tau = torch.empty_like(d_eps)
+    d_sig = torch.empty_like(d_eps)
+    s.rf_law_sweep(d_eps, d_tau, d_sig)
+    torch.cuda.synchronize()
+    s.close()
+    comps = [(0, 0), (1, 1), (0, 1)] if dim == 2 else VOIGT
+    e = np.zeros((N, 3, 3))
+    for a, (i, j) in enumerate(comps):
+        e[:, i, j] = e[:, j, i] = eps[a]
+    pmf = pm.ravel()
+    sig, _, _, _ = O.law(e, ph["lam"][pmf], ph["mu"][pmf], ph["sigma_y0"][pmf],
+                         ph["hardening"][pmf], ph["plastic"][pmf] != 0)
+    lam0, mu0 = O.reference_medium(ph, pm)
+    tr = np.trace(e, axis1=1, axis2=2)[:, None, None]
+    tau = sig - (lam0 * tr * np.eye(3) + 2 * mu0 * e)
+    want_tau = np.stack([tau[:, i, j] for (i, j) in comps])
+    want_sig = np.stack([sig[:, i, j] for (i, j) in comps])
+    scale = np.abs(want_sig).max()
+    assert np.abs(d_tau.cpu().numpy() - want_tau).max() <= 1e-5 * scale
+    assert np.abs(d_sig.cpu().numpy() - want_sig).max() <= 1e-5 * scale
