@@ -66,11 +66,12 @@ def parse():
                         "(3), or timed (0)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "paper"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "paper", "sweep"],
                    help="c2: 1024^2 J2 load path (the headline line); c3: 128^3 elastic spheres, "
                         "split-BF16 tensor-core transforms; c4: batch of 4096 RVEs of uneven size "
                         "vs per-RVE solves; c5: learned warm start vs plain start; paper: the "
-                        "pattern study on the paper-shaped inputs of Sec. 5 (256^2, 256^3)")
+                        "pattern study on the paper-shaped inputs of Sec. 5 (256^2, 256^3); "
+                        "sweep: the unfused constitutive sweep alone (4096^2)")
     p.add_argument("--rves", type=int, default=4096, help="c4 / c5: RVEs in the solved batch")
     p.add_argument("--train", type=int, default=50000, help="c5: training RVEs")
     p.add_argument("--epochs", type=int, default=20, help="c5: training epochs")
@@ -717,6 +718,9 @@ def main():
         return run_learned(args, rf, torch)
     if args.workload == "paper":
         return run_paper(args, rf, torch)
+    if args.workload == "sweep":
+        print(json.dumps(voxel_sweep(rf, torch)), flush=True)
+        return 0
 
     cfg, pm, K = workload()
     phases, path = cfg["phases"], cfg["path"]
