@@ -667,11 +667,11 @@ def voxel_sweep(rf, torch, reps=20):
     cfg = make_config("c2")
     pm = np.ascontiguousarray(np.tile(cfg["phase_map"], (4, 4)))
     N = pm.size
-    s = rf.Solver(pm, cfg["phases"])
+    stream = torch.cuda.current_stream()
+    s = rf.Solver(pm, cfg["phases"], stream=stream.cuda_stream)   # events on the same stream
     g = torch.Generator(device="cuda").manual_seed(7)
     eps = (torch.rand((3, N), device="cuda", generator=g) - 0.5) * 0.04
     tau = torch.empty_like(eps)
-    stream = torch.cuda.current_stream()
     for _ in range(3):
         s.rf_law_sweep(eps, tau)
     torch.cuda.synchronize()
