@@ -667,14 +667,17 @@ def voxel_sweep(rf, torch, reps=20):
     cfg = make_config("c2")
     pm = np.ascontiguousarray(np.tile(cfg["phase_map"], (4, 4)))
     N = pm.size
-    stream = torch.cuda.current_stream()
-    s = rf.Solver(pm, cfg["phases"], stream=stream.cuda_stream)   # events on the same stream
-    g = torch.Generator(device="cuda").manual_seed(7)
-    eps = (torch.rand((3, N), device="cuda", generator=g) - 0.5) * 0.04
-    tau = torch.empty_like(eps)
+    # an explicit stream for the solver and the events: the sweep is asynchronous, and a
+    # context given the legacy stream makes a stream of its own
+    stream = torch.cuda.Stream()
+    s = rf.Solver(pm, cfg["phases"], stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        g = torch.Generator(device="cuda").manual_seed(7)
+        eps = (torch.rand((3, N), device="cuda", generator=g) - 0.5) * 0.04
+        tau = torch.empty_like(eps)
     for _ in range(3):
         s.rf_law_sweep(eps, tau)
-    torch.cuda.synchronize()
+    stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
