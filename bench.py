@@ -64,6 +64,9 @@ def parse():
                    help="c2 FFT mode column phase: three kernels (-1), one fused kernel (1), "
                         "Green operator inside the inverse y kernel (2), the persistent solve "
                         "(3), or timed (0)")
+    p.add_argument("--fft-row-warps", type=int, default=0, choices=[-1, 0, 2, 4],
+                   help="c2 FFT mode: warps per block of the warp-FFT row kernel (-1: the "
+                        "shared-memory row kernel, 0: timed)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "paper", "sweep"],
@@ -733,7 +736,7 @@ def main():
     tiles = {}
     if args.transform == "fft":
         tiles = dict(fft_rows=args.fft_rows, fft_cols=args.fft_cols, fft_fuse=args.fft_fuse,
-                     fft_row_blocks=args.fft_row_blocks)
+                     fft_row_blocks=args.fft_row_blocks, fft_row_warps=args.fft_row_warps)
     if args.profile_updates > 0:
         s = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=0.0,
                       max_iter=args.profile_updates, transform=args.transform,
@@ -751,7 +754,7 @@ def main():
     info = solver.rf_get_info()
     tile_info = {k: info[k] for k in ("fft_rows", "fft_row_threads", "fft_cols",
                                       "fft_col_threads", "fft_fused", "fft_fuse_kx",
-                                      "fft_fuse_threads", "fft_row_blocks")} \
+                                      "fft_fuse_threads", "fft_row_blocks", "fft_row_warps")} \
         if args.transform == "fft" else None
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -809,6 +812,8 @@ def main():
                     ("dft", "inverse_y"): "k_dft_axis", ("dft", "forward_y"): "k_dft_axis"}
     if args.precision != "fp32" and dom == "row":
         kernel_names[("dft", "row")] = "k_tc_row"
+    if tile_info and tile_info.get("fft_row_warps"):
+        kernel_names[("fft", "row")] = "k_fft_row_w"
     if tile_info and tile_info.get("fft_fused") == 3:
         # the persistent solve: one kernel; its stages are the row and the column phase, each
         # timed up to its grid barrier by global-timer stamps of block 0

@@ -136,7 +136,14 @@ typedef struct rf_phase {
  *             library default, 2^26 polls); >= 0.
  *  stall_test  split-precision modes, for testing the timeout path: when 1, every tensor-core
  *             kernel first waits on a barrier that nothing completes, so the bounded wait runs
- *             out after wait_limit polls and the solve returns RF_ERR_TIMEOUT. 0 otherwise. */
+ *             out after wait_limit polls and the solve returns RF_ERR_TIMEOUT. 0 otherwise.
+ *  fft_row_warps  2D FFT mode with Nx = 1024 and plane strain: the row passes between column
+ *             phases (not the final pass) may run on the warp-FFT row kernel, a warp pair per
+ *             grid row with the 1024-point transforms in registers (four-step 32 x 32). 0 = the
+ *             autotuner compares it with the shared-memory row kernel (only when fft_rows and
+ *             fft_row_blocks are 0); 2 or 4 = always, with that many warps (one or two rows) per
+ *             block; -1 = never. Ignored where it does not apply; the same update either way up
+ *             to FP32 rounding order. */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
@@ -152,7 +159,7 @@ typedef struct rf_options {
   int32_t fft_row_blocks;
   int64_t wait_limit;
   int32_t stall_test;
-  int32_t reserved;
+  int32_t fft_row_warps;
 } rf_options;
 
 /* Run statistics of the last solve on a context. */
@@ -175,6 +182,8 @@ typedef struct rf_info {
   int32_t fft_row_blocks; /* FFT mode: row-kernel blocks (fft_rows is the largest block's row
                            * count; blocks may hold one row fewer to balance the SMs), else 0;
                            * the persistent solve's grid (and fft_row_threads its block size) */
+  int32_t fft_row_warps;  /* warps per block of the warp-FFT row kernel in use, else 0 */
+  int32_t reserved;
 } rf_info;
 
 /* Create a solver context for one microstructure.

@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-DNDEBUG"]
 SOURCES = ["rf_api.cu", "rf_kernels.cu", "rf_pattern.cu", "rf_tc.cu", "rf_fft.cu", "rf_batch.cu",
-           "rf_mlp.cu", "rf_persist.cu"]
+           "rf_mlp.cu", "rf_persist.cu", "rf_fftwarp.cu"]
 
 
 def _nvcc() -> str:

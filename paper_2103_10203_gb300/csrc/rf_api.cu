@@ -44,6 +44,7 @@ void init_attributes(int dev) {
   init_attributes_tc();
   init_attributes_fft();
   init_attributes_persist();
+  init_attributes_fftwarp();
   g_attr_done[dev] = true;
 }
 
@@ -553,6 +554,9 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (opt->fft_rows < 0 || opt->fft_rows > 64 || opt->fft_cols < 0 || opt->fft_cols > 64)
     return invalid("options: fft_rows and fft_cols in [0, 64]");
   if (opt->fft_row_blocks < 0) return invalid("options: fft_row_blocks >= 0");
+  if (opt->fft_row_warps != -1 && opt->fft_row_warps != 0 && opt->fft_row_warps != 2 &&
+      opt->fft_row_warps != 4)
+    return invalid("options: fft_row_warps -1, 0, 2 or 4");
   if (opt->wait_limit < 0 || (opt->stall_test != 0 && opt->stall_test != 1))
     return invalid("options: wait_limit >= 0, stall_test 0 or 1");
   if (opt->stall_test && opt->precision == RF_PREC_FP32)
@@ -1236,6 +1240,8 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
     info->fft_row_threads = c->persist_threads;
     info->fft_rows = (c->rows + c->persist_G - 1) / c->persist_G;
   }
+  info->fft_row_warps = fft && c->fft_colmode != kColPersistent ? c->fft_row_warps : 0;
+  info->reserved = 0;
   return RF_OK;
 }
 

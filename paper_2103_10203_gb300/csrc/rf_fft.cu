@@ -749,6 +749,7 @@ int fft_geometry(rf_ctx* c) {
     return RF_ERR_INVALID;
   }
   c->fft_C = C;
+  c->fft_row_warps = (c->opt.fft_row_warps > 0 && row_warp_ok(c)) ? c->opt.fft_row_warps : 0;
   // fused column phase (2D): kx columns per block within shared memory
   c->fft_colmode = kColSeparate;
   c->fft_M = std::max(1, std::min(c->opt.fft_fuse_kx > 0 ? c->opt.fft_fuse_kx : 1, c->Kx));
@@ -820,6 +821,7 @@ static int fft_row_launch(rf_ctx* c, const FftRowArgs& a) {
 }
 
 int launch_fft_row(rf_ctx* c, const int* done, bool final_pass, int commit) {
+  if (!final_pass && c->fft_row_warps > 0) return launch_fft_row_warp(c, done);
   FftRowArgs a = fft_row_args(c, done);
   if (final_pass) {
     a.eps_out = c->d_eps;
@@ -955,6 +957,8 @@ int fft_autotune(rf_ctx* c) {
                          colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
   const bool fuse_shape = c->fft_colmode == kColFused && c->opt.fft_fuse_kx == 0;
   const bool rows_pinned = c->opt.fft_rows > 0 || c->opt.fft_row_blocks > 0;
+  // the warp-FFT row kernel: compared with the shared-memory row kernel's best tile
+  const bool warp_auto = !rows_pinned && c->opt.fft_row_warps == 0 && row_warp_ok(c);
   // the persistent solve: compared with the other modes (fft_fuse 0, unless the row kernel's
   // tiles are pinned) or only its geometry chosen (fft_fuse 3); needs the barrier words set up
   // with the pattern
@@ -969,6 +973,7 @@ int fft_autotune(rf_ctx* c) {
       if (tu.row_blocks_balanced) set_rows_balanced(c, tu.row_blocks_balanced);
       else set_rows(c, tu.R);
       c->fft_row_threads = tu.row_threads;
+      if (warp_auto) c->fft_row_warps = tu.row_warps;
     }
     if (c->opt.fft_cols <= 0) {
       c->fft_C = tu.C;
@@ -1031,6 +1036,7 @@ int fft_autotune(rf_ctx* c) {
       const int Rmax = c->rows / nb + 1;
       if (row_smem(c->nx, c->nc, c->Kx, Rmax) <= kFftSmemMax) cands.push_back({Rmax, nb});
     }
+    c->fft_row_warps = 0;   // the shared-memory row kernel's tiles first (it runs the final pass)
     float best = 1e30f;
     Cand bestC{c->fft_R, 0};
     int bestT = c->fft_row_threads;
@@ -1053,6 +1059,21 @@ int fft_autotune(rf_ctx* c) {
     if (bestC.nb) set_rows_balanced(c, bestC.nb);
     else set_rows(c, bestC.R);
     c->fft_row_threads = bestT;
+    c->fft_row_warps = (c->opt.fft_row_warps > 0 && row_warp_ok(c)) ? c->opt.fft_row_warps : 0;
+    if (!err && warp_auto) {
+      int bestW = 0;
+      for (int W : {2, 4}) {
+        c->fft_row_warps = W;
+        float ms = 0.f;
+        err = time_it([&] { return launch_fft_row(c, nullptr, false, 0); }, &ms);
+        if (err) break;
+        if (ms < best) {
+          best = ms;
+          bestW = W;
+        }
+      }
+      c->fft_row_warps = bestW;
+    }
   }
   if (!err && c->opt.fft_cols <= 0) {
     const int Lc = std::max(c->ny, c->dim == 3 ? c->nz : 1);
@@ -1209,6 +1230,7 @@ int fft_autotune(rf_ctx* c) {
     tu.colmode = c->fft_colmode;
     tu.persist_per_sm = c->persist_per_sm;
     tu.persist_threads = c->persist_threads;
+    tu.row_warps = c->fft_row_warps;
   }
   return err;
 }

@@ -204,6 +204,7 @@ struct rf_ctx {
   int fft_R = 0, fft_blocks = 0, fft_C = 0;
   int fft_rbase = 0, fft_rextra = 0;    // row partition (see set_rows_balanced)
   int fft_row_threads = 256, fft_col_threads = 256;   // block sizes (autotuned with the tiles)
+  int fft_row_warps = 0;   // > 0: row passes (not the final one) on the warp-FFT row kernel
   size_t fft_smem = 0;
   // 2D column phase: 0 forward y, Green kernel, inverse y; 1 one fused kernel per kx group
   // (kColFused); 2 forward y, then the Green operator inside the inverse y kernel
@@ -228,6 +229,7 @@ struct rf_ctx {
     int row_blocks_balanced = 0;
     int colmode = 0;
     int persist_per_sm = 0, persist_threads = 0;
+    int row_warps = 0;
   } tuned;
 
   // split-precision (tensor-core) transforms along x
@@ -446,6 +448,12 @@ void trace_collect_graph(rf_ctx* c, const rf_ctx::GraphEntry& g, long long base,
 void init_attributes_kernels();
 void init_attributes_tc();
 void init_attributes_fft();
+void init_attributes_fftwarp();
+// warp-FFT row kernel (2D, Nx = 1024, three components): applicability, shared memory of a block
+// of `warps` warps, and one row pass with c->fft_row_warps warps per block
+bool row_warp_ok(const rf_ctx* c);
+size_t row_warp_smem(int Kx, int warps);
+int launch_fft_row_warp(rf_ctx* c, const int* done);
 // pattern.cu
 int pattern_adapted(const rf_grid* g, const uint8_t* pm, int incl, long long k_target,
                     int32_t* out, long long cap, long long* K_out, cudaStream_t s);

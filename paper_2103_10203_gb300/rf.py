@@ -38,7 +38,7 @@ class rf_options(C.Structure):
                 ("transform", C.c_int32), ("fft_rows", C.c_int32), ("fft_cols", C.c_int32),
                 ("fft_fuse", C.c_int32), ("fft_fuse_kx", C.c_int32),
                 ("fft_row_blocks", C.c_int32), ("wait_limit", C.c_int64),
-                ("stall_test", C.c_int32), ("reserved", C.c_int32)]
+                ("stall_test", C.c_int32), ("fft_row_warps", C.c_int32)]
 
 
 class rf_info(C.Structure):
@@ -49,7 +49,8 @@ class rf_info(C.Structure):
                 ("fft_row_threads", C.c_int32), ("fft_cols", C.c_int32),
                 ("fft_col_threads", C.c_int32), ("fft_fused", C.c_int32),
                 ("fft_fuse_kx", C.c_int32), ("fft_fuse_threads", C.c_int32),
-                ("fft_row_blocks", C.c_int32)]
+                ("fft_row_blocks", C.c_int32), ("fft_row_warps", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class rf_mlp_dims(C.Structure):
@@ -205,7 +206,8 @@ def make_phases(table) -> C.Array:
 
 def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
                  check_every=0, transform="dft", fft_rows=0, fft_cols=0, fft_fuse=0,
-                 fft_fuse_kx=0, fft_row_blocks=0, wait_limit=0, stall_test=0) -> rf_options:
+                 fft_fuse_kx=0, fft_row_blocks=0, wait_limit=0, stall_test=0,
+                 fft_row_warps=0) -> rf_options:
     o = rf_options()
     o.tol, o.max_iter = float(tol), int(max_iter)
     o.green, o.ref_medium = GREEN[green], REF[ref]
@@ -215,6 +217,7 @@ def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precisi
     o.fft_fuse, o.fft_fuse_kx = int(fft_fuse), int(fft_fuse_kx)
     o.fft_row_blocks = int(fft_row_blocks)
     o.wait_limit, o.stall_test = int(wait_limit), int(stall_test)
+    o.fft_row_warps = int(fft_row_warps)
     return o
 
 

@@ -593,6 +593,78 @@ def test_fft_balanced_row_blocks(lib, name, blocks):
     assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
 
 
+def _strip_1024(name):
+    """Grids of 1024-voxel rows for the warp-FFT row kernel: a J2 strip cut from a disc
+    composite (24 rows), an elastic random strip with every frequency (kx = 0 and the
+    self-conjugate kx = 512 included; 3 rows: ragged against two rows per block), and an
+    elastic strip with an adapted pattern (12 rows)."""
+    if name == "j2_strip":
+        pm = np.ascontiguousarray(random_discs(1024, (8.0, 24.0), 0.4, seed=21)[300:324])
+        return pm, j2_phases(), np.array([0.02, 0, 0, 0, 0, 0.003]), \
+            O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    if name == "full_strip":
+        pm = (np.random.default_rng(22).random((3, 1024)) < 0.3).astype(np.uint8)
+        return pm, elastic_phases(), random_macro_strain(23, 2), O.full_pattern((1,) + pm.shape)
+    if name == "el_strip":
+        pm = (np.random.default_rng(24).random((12, 1024)) < 0.35).astype(np.uint8)
+        return pm, elastic_phases(), random_macro_strain(25, 2), \
+            O.pattern_adapted(pm, 1, k_target(0.08, pm.size))
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["j2_strip", "full_strip", "el_strip"])
+@pytest.mark.parametrize("warps", [2, 4])
+@pytest.mark.parametrize("fuse", [-1, 1, 2])
+def test_fft_warp_row_kernel_matches_oracle(lib, name, warps, fuse):
+    """Row passes on the warp-FFT row kernel (1024-point four-step transforms in registers, a
+    warp pair per grid row, `warps` warps per block) between each column-phase mode: the
+    oracle's updates at the FP32 parity tolerances, reduced coefficients included."""
+    pm, ph, macro, pat = _strip_1024(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=5, transform="fft", fft_fuse=fuse,
+                   fft_row_warps=warps)
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    coeffs = s.rf_get_reduced_strain()
+    info = s.rf_get_info()
+    s.close()
+    assert info["fft_row_warps"] == warps and out["iters"] == 5
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=5)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    want = np.stack([r.eps_hat[:, i, j] for (i, j) in VOIGT], axis=1)
+    assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
+
+
+def test_fft_warp_row_kernel_option(lib):
+    """fft_row_warps: 2 and 4 force the warp-FFT row kernel where it applies (2D, rows of 1024)
+    and are ignored elsewhere; -1 keeps the shared-memory row kernel; other values are rejected.
+    A J2 load path to the tolerance takes the same decisions with either row kernel."""
+    for bad in (-2, 1, 3, 8):
+        with pytest.raises(lib.RFError):
+            lib.Solver(np.zeros((8, 1024), np.uint8), elastic_phases(), transform="fft",
+                       fft_row_warps=bad)
+    pm, ph, macro, pat = _pow2_case("j2_64")
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=2, transform="fft", fft_row_warps=2)
+    s.rf_solve(macro)
+    assert s.rf_get_info()["fft_row_warps"] == 0
+    s.close()
+    pm, ph, _, pat = _strip_1024("j2_strip")
+    path = uniaxial_path(20, 0.02)[::5]
+    res = {}
+    for w in (-1, 2):
+        s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform="fft",
+                       fft_fuse=-1, fft_row_warps=w)
+        res[w] = (s.rf_solve_path(path), s.rf_get_fields()[0])
+        assert s.rf_get_info()["fft_row_warps"] == max(w, 0)
+        s.close()
+    (a, ea), (b, eb) = res[-1], res[2]
+    assert a["converged"] and b["converged"]
+    assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
+    assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
+    assert rel(eb, ea) <= 2e-5
+
+
 def test_fft_transform_load_path_and_tolerance(lib):
     pm = random_discs(64, (4.0, 9.0), 0.4, seed=2)
     ph = j2_phases()
@@ -625,14 +697,19 @@ def test_fft_and_dft_transforms_agree(lib):
     assert rel(eb, ea) <= 2e-5
 
 
-def test_fft_full_size_c2_first_iterations(lib):
+@pytest.mark.parametrize("warps", [-1, 2, 4])
+def test_fft_full_size_c2_first_iterations(lib, warps):
+    """The 1024^2 J2 composite, three updates, with the shared-memory row kernel (-1) and the
+    warp-FFT row kernel (2 or 4 warps per block)."""
     cfg = make_config("c2")
     pm, ph = cfg["phase_map"], cfg["phases"]
     pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
     macro = np.array([0.02, 0, 0, 0, 0, 0])
-    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft")
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft",
+                   fft_row_warps=warps)
     out = s.rf_solve(macro)
     eps, _, _ = s.rf_get_fields()
+    assert s.rf_get_info()["fft_row_warps"] == max(warps, 0)
     s.close()
     r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=3)
     assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
