@@ -60,11 +60,11 @@ def parse():
                    help="c2 FFT mode: row-kernel blocks with the rows spread evenly (0: autotuned)")
     p.add_argument("--fft-cols", type=int, default=0,
                    help="c2 FFT mode: columns per column-kernel block (0: autotuned)")
-    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2, 3],
+    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4],
                    help="c2 FFT mode column phase: three kernels (-1), one fused kernel (1), "
                         "Green operator inside the inverse y kernel (2), the persistent solve "
-                        "(3), or timed (0)")
-    p.add_argument("--fft-row-warps", type=int, default=0, choices=[-1, 0, 2, 4],
+                        "(3), the warp-FFT column kernel (4), or timed (0)")
+    p.add_argument("--fft-row-warps", type=int, default=0, choices=[-1, 0, 2, 4, 8],
                    help="c2 FFT mode: warps per block of the warp-FFT row kernel (-1: the "
                         "shared-memory row kernel, 0: timed)")
     p.add_argument("--no-e2e", action="store_true")
@@ -814,6 +814,8 @@ def main():
         kernel_names[("dft", "row")] = "k_tc_row"
     if tile_info and tile_info.get("fft_row_warps"):
         kernel_names[("fft", "row")] = "k_fft_row_w"
+    if tile_info and tile_info.get("fft_fused") == 4:
+        kernel_names[("fft", "column_phase")] = "k_fft_colphase_w"
     if tile_info and tile_info.get("fft_fused") == 3:
         # the persistent solve: one kernel; its stages are the row and the column phase, each
         # timed up to its grid barrier by global-timer stamps of block 0

@@ -413,7 +413,8 @@ int run_iterations(rf_ctx* c) {
     // first one needs the line transforms of the start coefficients
     const bool tr = c->tracing;
     c->tracing = false;
-    const int e = fft_inverse_stages(c, nullptr);
+    const int e = c->fft_colmode == kColWarp ? launch_fft_coly_init_warp(c)
+                                             : fft_inverse_stages(c, nullptr);
     c->tracing = tr;
     if (e) return e;
   }
@@ -555,16 +556,22 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
     return invalid("options: fft_rows and fft_cols in [0, 64]");
   if (opt->fft_row_blocks < 0) return invalid("options: fft_row_blocks >= 0");
   if (opt->fft_row_warps != -1 && opt->fft_row_warps != 0 && opt->fft_row_warps != 2 &&
-      opt->fft_row_warps != 4)
-    return invalid("options: fft_row_warps -1, 0, 2 or 4");
+      opt->fft_row_warps != 4 && opt->fft_row_warps != 8)
+    return invalid("options: fft_row_warps -1, 0, 2, 4 or 8");
+  if ((opt->fft_row_warps == 8) != (opt->fft_fuse == 4) && opt->fft_row_warps != 0)
+    return invalid("options: fft_row_warps 8 goes with fft_fuse 4 and only with it");
   if (opt->wait_limit < 0 || (opt->stall_test != 0 && opt->stall_test != 1))
     return invalid("options: wait_limit >= 0, stall_test 0 or 1");
   if (opt->stall_test && opt->precision == RF_PREC_FP32)
     return invalid("options: stall_test applies to the split-precision modes only");
-  if (opt->fft_fuse < -1 || opt->fft_fuse > 3 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
-    return invalid("options: fft_fuse in {-1, 0, 1, 2, 3}, fft_fuse_kx in [0, 16]");
+  if (opt->fft_fuse < -1 || opt->fft_fuse > 4 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
+    return invalid("options: fft_fuse in {-1, 0, 1, 2, 3, 4}, fft_fuse_kx in [0, 16]");
   if (opt->fft_fuse >= 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))
-    return invalid("options: fft_fuse 1, 2 or 3 needs the FFT transform on a 2D grid");
+    return invalid("options: fft_fuse 1 to 4 needs the FFT transform on a 2D grid");
+  if (opt->fft_fuse == 4 && (grid->n[0] != 1024 || grid->n[1] != 1024 || opt->fft_fuse_kx > 2 ||
+                             (opt->fft_row_warps != 0 && opt->fft_row_warps != 8)))
+    return invalid("options: fft_fuse 4 needs a 1024 x 1024 grid, fft_fuse_kx 0, 1 or 2 and "
+                   "the warp-FFT row kernel");
   if (opt->transform == RF_TRANSFORM_FFT) {
     // 2^b or 3 * 2^b (the FFT stages are radix 16, 4, 2 and one radix-3)
     auto pow2 = [](int v) {
@@ -1232,7 +1239,8 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   info->fft_cols = fft ? c->fft_C : 0;
   info->fft_col_threads = fft ? c->fft_col_threads : 0;
   info->fft_fused = c->fft_colmode;
-  info->fft_fuse_kx = c->fft_colmode == kColFused ? c->fft_M : 0;
+  info->fft_fuse_kx = c->fft_colmode == kColFused ? c->fft_M
+                      : c->fft_colmode == kColWarp ? c->fft_colw_M : 0;
   info->fft_fuse_threads = c->fft_colmode == kColFused ? c->fft_M_threads : 0;
   info->fft_row_blocks = fft ? c->fft_blocks : 0;
   if (c->fft_colmode == kColPersistent) {

@@ -766,6 +766,16 @@ int fft_geometry(rf_ctx* c) {
       c->fft_colmode = kColFused;
     } else if (c->opt.fft_fuse == 2) {
       c->fft_colmode = kColGreenInv;
+    } else if (c->opt.fft_fuse == 4) {
+      if (c->nx != 1024 || c->ny != 1024 || c->nc != 3 ||
+          (c->opt.fft_row_warps != 0 && c->opt.fft_row_warps != 8)) {
+        set_error("FFT mode: the warp-FFT column phase needs a 1024 x 1024 grid in 2D and the "
+                  "warp-FFT row kernel");
+        return RF_ERR_INVALID;
+      }
+      c->fft_colmode = kColWarp;
+      c->fft_colw_M = c->opt.fft_fuse_kx > 0 ? c->opt.fft_fuse_kx : 1;
+      c->fft_row_warps = 8;   // the row-group slab row kernel
     }
   }
   return RF_OK;
@@ -956,15 +966,23 @@ int fft_autotune(rf_ctx* c) {
   const bool fuse_auto = c->dim == 2 && c->opt.fft_fuse == 0 && c->d_jptr &&
                          colphase_smem(c->ny, c->nc, 1) <= kFftSmemMax;
   const bool fuse_shape = c->fft_colmode == kColFused && c->opt.fft_fuse_kx == 0;
+  // the warp-FFT column phase: compared with the other modes (fft_fuse 0) or only its kx columns
+  // per block chosen (fft_fuse 4 without fft_fuse_kx)
+  const bool colw_auto = fuse_auto && col_warp_ok(c) && c->opt.fft_row_warps == 0 &&
+                         c->opt.fft_rows <= 0 && c->opt.fft_row_blocks <= 0;
+  const bool colw_shape = c->fft_colmode == kColWarp && c->opt.fft_fuse_kx == 0;
   const bool rows_pinned = c->opt.fft_rows > 0 || c->opt.fft_row_blocks > 0;
-  // the warp-FFT row kernel: compared with the shared-memory row kernel's best tile
-  const bool warp_auto = !rows_pinned && c->opt.fft_row_warps == 0 && row_warp_ok(c);
+  // the warp-FFT row kernel: compared with the shared-memory row kernel's best tile (the
+  // warp-FFT column phase fixes it to its row-group slab form)
+  const bool warp_need = c->fft_colmode == kColWarp;
+  const bool warp_auto = !rows_pinned && c->opt.fft_row_warps == 0 && row_warp_ok(c) && !warp_need;
   // the persistent solve: compared with the other modes (fft_fuse 0, unless the row kernel's
   // tiles are pinned) or only its geometry chosen (fft_fuse 3); needs the barrier words set up
   // with the pattern
   const bool persist_auto = c->dim == 2 && c->d_jptr && c->d_bar &&
                             ((c->opt.fft_fuse == 0 && !rows_pinned) || c->opt.fft_fuse == 3);
-  if (rows_pinned && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape && !persist_auto)
+  if (rows_pinned && c->opt.fft_cols > 0 && !fuse_auto && !fuse_shape && !persist_auto &&
+      !colw_shape)
     return RF_OK;
   rf_ctx::Tuned& tu = c->tuned;
   if (tu.valid && tu.Kx == c->Kx && tu.Ky == c->Ky && tu.Kz == c->Kz) {
@@ -982,8 +1000,12 @@ int fft_autotune(rf_ctx* c) {
     if (fuse_auto || fuse_shape) {
       c->fft_M = tu.M;
       c->fft_M_threads = tu.M_threads;
-      if (fuse_auto) c->fft_colmode = tu.colmode;
+      if (fuse_auto) {
+        c->fft_colmode = tu.colmode == kColPersistent ? kColSeparate : tu.colmode;
+        c->fft_colw_M = tu.colw_M;
+      }
     }
+    if (colw_shape) c->fft_colw_M = tu.colw_M;
     if (persist_auto && tu.persist_per_sm > 0 &&
         persist_geometry(c, tu.persist_threads, tu.persist_per_sm)) {
       if (c->opt.fft_fuse == 0 && tu.colmode == kColPersistent) c->fft_colmode = kColPersistent;
@@ -1019,6 +1041,26 @@ int fft_autotune(rf_ctx* c) {
       *ms = std::min(*ms, t);
     }
     return RF_OK;
+  };
+  // one whole update (row pass and column phase) in the given column mode
+  auto run_update = [&](int mode) -> int {
+    if (mode == kColFused) {
+      if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
+      return launch_fft_colphase(c, nullptr);
+    }
+    if (mode == kColWarp) {
+      if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
+      return launch_fft_colphase_warp(c, nullptr);
+    }
+    if (mode == kColGreenInv) {
+      if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
+      if (int e = fft_forward_stages(c, nullptr)) return e;
+      return launch_fft_green_inv(c, nullptr);
+    }
+    if (int e = fft_inverse_stages(c, nullptr)) return e;
+    if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
+    if (int e = fft_forward_stages(c, nullptr)) return e;
+    return launch_gamma_finalize(c, 1, nullptr);
   };
   if (!err && !rows_pinned) {
     // uniform tiles of R rows, and balanced partitions over k blocks per SM
@@ -1059,7 +1101,8 @@ int fft_autotune(rf_ctx* c) {
     if (bestC.nb) set_rows_balanced(c, bestC.nb);
     else set_rows(c, bestC.R);
     c->fft_row_threads = bestT;
-    c->fft_row_warps = (c->opt.fft_row_warps > 0 && row_warp_ok(c)) ? c->opt.fft_row_warps : 0;
+    c->fft_row_warps = warp_need ? 8
+                       : (c->opt.fft_row_warps > 0 && row_warp_ok(c)) ? c->opt.fft_row_warps : 0;
     if (!err && warp_auto) {
       int bestW = 0;
       for (int W : {2, 4}) {
@@ -1140,7 +1183,48 @@ int fft_autotune(rf_ctx* c) {
       c->fft_colmode = kColSeparate;
       if (!err && gi < sep && gi <= best) c->fft_colmode = kColGreenInv;
       else if (!err && best < sep) c->fft_colmode = kColFused;
+      if (!err && colw_auto) {
+        // whole updates: the mode chosen so far against the warp-FFT column phase with the
+        // warp-FFT row kernel on kx slabs
+        const int keep_mode = c->fft_colmode, keep_w = c->fft_row_warps;
+        float t_keep = 1e30f;
+        err = time_it([&] { return run_update(keep_mode); }, &t_keep);
+        c->fft_colmode = kColWarp;
+        c->fft_row_warps = 8;
+        float bw = 1e30f;
+        int bestMw = 1;
+        for (int Mw : {1, 2}) {
+          if (err) break;
+          c->fft_colw_M = Mw;
+          float ms = 0.f;
+          err = time_it([&] { return run_update(kColWarp); }, &ms);
+          if (!err && ms < bw) {
+            bw = ms;
+            bestMw = Mw;
+          }
+        }
+        c->fft_colw_M = bestMw;
+        if (err || !(bw < t_keep)) {
+          c->fft_colmode = keep_mode;
+          c->fft_row_warps = keep_w;
+        }
+      }
     }
+  }
+  if (!err && colw_shape) {
+    float bw = 1e30f;
+    int bestMw = 1;
+    for (int Mw : {1, 2}) {
+      c->fft_colw_M = Mw;
+      float ms = 0.f;
+      err = time_it([&] { return launch_fft_colphase_warp(c, nullptr); }, &ms);
+      if (err) break;
+      if (ms < bw) {
+        bw = ms;
+        bestMw = Mw;
+      }
+    }
+    c->fft_colw_M = bestMw;
   }
   if (!err && persist_auto) {
     // per-update time of the best separate-kernel mode against the persistent solve (one launch
@@ -1150,21 +1234,7 @@ int fft_autotune(rf_ctx* c) {
     if (c->opt.fft_fuse == 0) {
       const int keep = c->fft_colmode;
       c->fft_colmode = mode_np;
-      err = time_it([&] {
-        if (mode_np == kColFused) {
-          if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
-          return launch_fft_colphase(c, nullptr);
-        }
-        if (mode_np == kColGreenInv) {
-          if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
-          if (int e = fft_forward_stages(c, nullptr)) return e;
-          return launch_fft_green_inv(c, nullptr);
-        }
-        if (int e = fft_inverse_stages(c, nullptr)) return e;
-        if (int e = launch_fft_row(c, nullptr, false, 0)) return e;
-        if (int e = fft_forward_stages(c, nullptr)) return e;
-        return launch_gamma_finalize(c, 1, nullptr);
-      }, &t_np);
+      err = time_it([&] { return run_update(mode_np); }, &t_np);
       t_np /= 3.f;
       c->fft_colmode = keep;
     }
@@ -1231,6 +1301,7 @@ int fft_autotune(rf_ctx* c) {
     tu.persist_per_sm = c->persist_per_sm;
     tu.persist_threads = c->persist_threads;
     tu.row_warps = c->fft_row_warps;
+    tu.colw_M = c->fft_colw_M;
   }
   return err;
 }

@@ -102,9 +102,19 @@ __device__ __forceinline__ void fwd1024(float2* v, float2* T, const float2* __re
   }
 }
 
+// Line-coefficient layouts between the row pass and the column phase: row-major [rows][NC][Kx]
+// (every other column mode), or row-group slabs [rows / 4][Kx][4][NC] (the warp-FFT column
+// phase): the coefficients of four consecutive rows at one kx are 96 contiguous bytes, so the
+// row pass (a block per group of four rows) reads and writes its group as one contiguous block
+// and the column phase (a block per kx) reads and writes whole 32-byte sectors.
+constexpr int kGroup = 4;
+__device__ __forceinline__ long long slab_at(int j, int y, int c, int Kx) {
+  return ((((long long)(y >> 2) * Kx + j) << 2) + (y & 3)) * 3 + c;
+}
+
 struct RowWArgs {
-  const float2* T;      // [rows][NC][Kx] strain line coefficients
-  float2* Tout;         // [rows][NC][Kx] polarization line coefficients
+  const float2* T;      // strain line coefficients (row-major or kx slabs)
+  float2* Tout;         // polarization line coefficients (same layout)
   const uint8_t* phase;
   const float* state;   // [4][N] or null
   const int* kx;        // [Kx]
@@ -116,11 +126,15 @@ struct RowWArgs {
   const int* done;
 };
 
-// Barrier of the two warps of pair p (named barrier 1 + p; 0 is the block's). Both warps of a
-// pair reach each of these once per row.
+// Barrier of the two warps of pair p < 4 (named barrier 1 + p; 0 is the block's). Both warps of
+// a pair reach each of these once per row.
 __device__ __forceinline__ void pair_sync(int p) {
-  if (p == 0) asm volatile("bar.sync 1, 64;" ::: "memory");
-  else asm volatile("bar.sync 2, 64;" ::: "memory");
+  switch (p) {
+    case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+  }
 }
 
 // A warp pair per grid row: warp 0 of the pair carries A = line 11 + i line 22, warp 1 carries
@@ -129,8 +143,9 @@ __device__ __forceinline__ void pair_sync(int p) {
 // the law on half of the row's voxels, the pair meets again, and each warp transforms its part of
 // the polarization back and writes the pattern's kx columns. Shared memory per pair: SA and SB,
 // each holding its sequence's spectrum, its transposes and, between the transforms, the
-// sequence in space.
-template <bool PLASTIC, int R>
+// sequence in space. SLAB (R = 4, a block per row group): the group's line coefficients are
+// staged in shared memory, loaded and stored by the whole block as one contiguous block.
+template <bool PLASTIC, int R, bool SLAB>
 __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
   constexpr int NC = 3, L = kN;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -139,7 +154,7 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
   const int Kx = a.Kx;
   int* kxs = reinterpret_cast<int*>(smem);
   float2* SA = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15)) +
-               (size_t)pair * kPairRegion;
+               (SLAB ? (size_t)Kx * kGroup * NC : 0) + (size_t)pair * kPairRegion;
   float2* SB = SA + kRegion;
   float2* S = role ? SB : SA;   // this warp's region
   for (int i = threadIdx.x; i < Kx; i += blockDim.x) kxs[i] = a.kx[i];
@@ -148,9 +163,28 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
   grid_dep_wait();
   if (a.done && *a.done) return;   // the same flag value for every thread of the grid
   const float lam0 = a.law.lam0, mu0 = a.law.mu0;
+  // kx slabs: the block's row group staged in shared memory, [Kx][4][NC]
+  float2* G = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15));
   for (int row = blockIdx.x * R + pair; row < a.rows; row += gridDim.x * R) {
     const float2* Tr = a.T + (long long)row * NC * Kx;
     float2* To = a.Tout + (long long)row * NC * Kx;
+    const int r4 = row & (kGroup - 1);
+    if (SLAB) {
+      // the group's coefficients: Kx * 96 contiguous bytes, 16-byte loads
+      const float4* src = reinterpret_cast<const float4*>(a.T + slab_at(0, row - r4, 0, Kx));
+      float4* g4 = reinterpret_cast<float4*>(G);
+      const int n4 = Kx * kGroup * NC / 2;
+      for (int q0 = threadIdx.x; q0 < n4; q0 += 4 * blockDim.x) {
+        float4 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (q0 + u * (int)blockDim.x < n4) t[u] = src[q0 + u * blockDim.x];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (q0 + u * (int)blockDim.x < n4) g4[q0 + u * blockDim.x] = t[u];
+      }
+      __syncthreads();
+    }
     // ---- spectrum: A from lines 11 and 22, B from line 12; loads eight per lane in flight
 #pragma unroll
     for (int i = 0; i < 32; ++i) S[lane + 32 * i] = make_float2(0.f, 0.f);
@@ -164,8 +198,14 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
         const int j = j0 + lane + 32 * u;
         c0[u] = c1[u] = make_float2(0.f, 0.f);
         if (j < Kx) {
-          c0[u] = l0[j];
-          if (!role) c1[u] = Tr[Kx + j];
+          if (SLAB) {
+            const float2* p = G + (j * kGroup + r4) * NC + (role ? 2 : 0);
+            c0[u] = p[0];
+            if (!role) c1[u] = p[1];
+          } else {
+            c0[u] = l0[j];
+            if (!role) c1[u] = Tr[Kx + j];
+          }
         }
       }
 #pragma unroll
@@ -185,6 +225,7 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
       }
     }
     __syncwarp();
+    if (SLAB) __syncthreads();   // the staged group is read; it takes the outputs next
     // the law's first phase ids and internal variables (voxels x = 32 n1 + lane for n1 in this
     // warp's half of the row, kU per step) go out before the transform to space; each law step
     // then loads the next step's while it computes
@@ -269,43 +310,345 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
       if (role) {
         float2 z = zk;
         if (k == 0 || 2 * k == L) z.y = 0.f;   // a real line's self-conjugate coefficients
-        To[2 * Kx + j] = z;
+        if (SLAB) G[(j * kGroup + r4) * NC + 2] = z;
+        else To[2 * Kx + j] = z;
       } else {
         const float2 zm = S[k == 0 ? 0 : L - k];
-        To[j] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        To[Kx + j] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        const float2 t0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 t1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        if (SLAB) {
+          float2* p = G + (j * kGroup + r4) * NC;
+          p[0] = t0;
+          p[1] = t1;
+        } else {
+          To[j] = t0;
+          To[Kx + j] = t1;
+        }
       }
     }
     __syncwarp();
+    if (SLAB) {
+      // the group's polarization coefficients out with 16-byte stores
+      __syncthreads();
+      float4* dst = reinterpret_cast<float4*>(a.Tout + slab_at(0, row - r4, 0, Kx));
+      const float4* g4 = reinterpret_cast<const float4*>(G);
+      const int n4 = Kx * kGroup * NC / 2;
+      for (int q = threadIdx.x; q < n4; q += blockDim.x) dst[q] = g4[q];
+      __syncthreads();   // before the next group overwrites the staging
+    }
+  }
+}
+
+struct ColWArgs {
+  const float2* T1p;      // [Kx][1024][NC] polarization line coefficients (row pass output)
+  float2* T1;             // [Kx][1024][NC] strain line coefficients (next row pass input)
+  float2* ER;             // [Ky][NC][Kx] strain coefficients on the (ky, kx) rectangle
+  const int* jptr;        // [Kx + 1] offsets of each kx's entries in the grouped order
+  const int2* jent;       // grouped order: (rectangle row iy, frequency kind)
+  const float4* jn;       // grouped order: unit wave vector and multiplicity
+  const int* kym;         // position (ky mod Ny) of each rectangle row
+  const float2* table;    // exp(+2 pi i t / 1024), t < 1024
+  int Kx;
+  float inv2mu0, cgam;
+  Status* st;
+  unsigned* counter;      // blocks finished (reset to 0 by the last block)
+  double* part;           // [gridDim.x]
+  const int* done;
+  cudaGraphConditionalHandle cond;
+  int use_cond;
+};
+
+constexpr int kColRegion = kRegion + kN;   // a column warp's region: R (1056) and D (1024)
+
+// Column phase of a 2D update on 1024 x 1024 grids (steps b, c, d of Sec. 4 along y, fused), on
+// line coefficients in row-group slabs: a block takes M kx values, a warp each of their NC
+// component columns. The block loads its kx's 96-byte pieces of every row group (16-byte loads,
+// whole sectors) into the warps' regions R; each
+// warp transforms its column forward in registers and leaves the spectrum in R; the block applies
+// the Green operator at its kx's pattern entries (all NC components of an entry come from the
+// regions of the same kx), writes the new coefficients to ER and into the zeroed spectra D, and
+// sums the convergence measure (FP64 partial per block; the last block takes the decision); each
+// warp transforms D back to space along y (R as the transpose buffer), and the block stores its
+// pieces for the next row pass. INIT: only the inverse of the coefficients held in ER (the start
+// of a solve), no decision.
+template <int M, bool INIT>
+__global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd) {
+  constexpr int NC = 3, kB = 4;   // entries per thread in flight
+  constexpr int kSlab4 = kN * NC / 2;   // float4 of one kx: 256 row groups of 6
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[3 * M];
+  __shared__ double sh[32];
+  __shared__ bool last;
+  float2* R0 = reinterpret_cast<float2*>(smem);   // warp w's region at w kColRegion
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j0 = blockIdx.x * M;
+  const int nj = min(M, a.Kx - j0);   // kx values of this block
+  float2* R = R0 + w * kColRegion;
+  float2* D = R + kRegion;
+  const int e0 = a.jptr[j0], e1 = a.jptr[j0 + nj];
+  const int eM = M == 2 ? a.jptr[j0 + 1] : e1;   // first entry of the second kx
+#pragma unroll
+  for (int i = 0; i < 32; ++i) D[lane + 32 * i] = make_float2(0.f, 0.f);
+  grid_dep_wait();
+  if (!INIT && a.done && __ldcg(a.done)) return;   // the same flag value for every thread
+  float2 v[32];
+  double diff = 0.0;
+  if (!INIT) {
+    // the block's kx in every row group: 96 contiguous bytes (six float4) per group; float4 k
+    // of group g holds the entries 2k, 2k + 1 of [4][NC], i.e. (y - 4 g, c) = divmod(., NC)
+    const float4* src = reinterpret_cast<const float4*>(a.T1p);
+    for (int q0 = threadIdx.x; q0 < nj * kSlab4; q0 += 8 * blockDim.x) {
+      float4 t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < nj * kSlab4) {
+          const int jj = q >= kSlab4 ? 1 : 0, r = q - jj * kSlab4, g = r / 6;
+          t[u] = src[((long long)g * a.Kx + j0 + jj) * 6 + (r - 6 * g)];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q >= nj * kSlab4) continue;
+        const int jj = q >= kSlab4 ? 1 : 0, r = q - jj * kSlab4, g = r / 6, e = 2 * (r - 6 * g);
+        const int y0 = 4 * g + e / NC, c0 = e % NC;
+        const int y1 = 4 * g + (e + 1) / NC, c1 = (e + 1) % NC;
+        R0[(jj * NC + c0) * kColRegion + y0] = make_float2(t[u].x, t[u].y);
+        R0[(jj * NC + c1) * kColRegion + y1] = make_float2(t[u].z, t[u].w);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = R[lane + 32 * i];
+    __syncwarp();
+    fwd1024(v, R, a.table, lane);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) R[lane + 32 * i] = v[i];
+    __syncthreads();
+  }
+  // Green operator at the block's pattern entries (INIT: the held coefficients), kB per thread
+  // with their loads issued together (tau^ read only where it is used: regular frequencies, and
+  // the zero frequency under mixed control)
+  for (int eb = e0 + threadIdx.x; eb < e1; eb += kB * blockDim.x) {
+    int2 en[kB];
+    float4 nv[kB];
+    int pos[kB];
+    float2 old[kB][NC];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = eb + u * blockDim.x;
+      if (e < e1) {
+        en[u] = a.jent[e];
+        if (!INIT) nv[u] = a.jn[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = eb + u * blockDim.x;
+      if (e < e1) {
+        const int je = (M == 2 && e >= eM) ? 1 : 0;
+        pos[u] = a.kym[en[u].x];
+        const long long base = ((long long)en[u].x * NC) * a.Kx + j0 + je;
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) old[u][cc] = a.ER[base + (long long)cc * a.Kx];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = eb + u * blockDim.x;
+      if (e >= e1) continue;
+      const int je = (M == 2 && e >= eM) ? 1 : 0;
+      if (INIT) {
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc)
+          R0[(je * NC + cc) * kColRegion + kRegion + pos[u]] = old[u][cc];
+        continue;
+      }
+      const int kind = en[u].y;
+      const long long base = ((long long)en[u].x * NC) * a.Kx + j0 + je;
+      const bool mixed0 = kind == 1 && a.st->mixed;
+      float2 tv[NC];
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc)
+        tv[cc] = (kind == 0 || mixed0) ? R0[(je * NC + cc) * kColRegion + pos[u]]
+                                       : make_float2(0.f, 0.f);
+      float er[NC], ei[NC];
+      const double* ebar = a.st->ebar;
+      double em[6];
+      if (mixed0) {
+        mixed_macro<NC>(tv, Nd, a.st, em);
+        for (int i = 0; i < 6; ++i) a.st->ebar[i] = em[i];
+        ebar = em;
+      }
+      green_update<NC>(kind, nv[u], tv, ebar, Nd, a.inv2mu0, a.cgam, er, ei);
+      float d = 0.f;   // one frequency's squared increment (at most six non-negative terms)
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) {
+        const float dr = er[cc] - old[u][cc].x, di = ei[cc] - old[u][cc].y;
+        const float wc = (comp6<NC>(cc) >= 3) ? 2.f : 1.f;   // Frobenius: shear counted twice
+        d = fmaf(nv[u].w * wc, dr * dr + di * di, d);
+        const float2 z = make_float2(er[cc], ei[cc]);
+        a.ER[base + (long long)cc * a.Kx] = z;
+        R0[(je * NC + cc) * kColRegion + kRegion + pos[u]] = z;   // D of warp (je, cc)
+      }
+      diff += (double)d;
+    }
+  }
+  if (!INIT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+    if (lane == 0) red[w] = diff;
+  }
+  __syncthreads();   // also: every spectrum D is complete
+  if (!INIT) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < 3 * M; ++i) t += red[i];
+      a.part[blockIdx.x] = t;
+      __threadfence();
+      last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      decide(a.part, gridDim.x, a.st, sh);
+      if (threadIdx.x == 0) {
+        *a.counter = 0u;
+        // the only call site of the loop condition in this mode: one thread of one block
+        if (a.use_cond && a.st->done) cudaGraphSetConditional(a.cond, 0u);
+      }
+    }
+  }
+  // inverse along y as the conjugate of the forward transform of the conjugate; the column back
+  // to R, then the block's slabs out with 16-byte stores
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    v[i] = D[lane + 32 * i];
+    v[i].y = -v[i].y;
+  }
+  fwd1024(v, R, a.table, lane);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) R[lane + 32 * i] = make_float2(v[i].x, -v[i].y);
+  __syncthreads();
+  float4* dst = reinterpret_cast<float4*>(a.T1);
+  for (int q = threadIdx.x; q < nj * kSlab4; q += blockDim.x) {
+    const int jj = q >= kSlab4 ? 1 : 0, r = q - jj * kSlab4, g = r / 6, e = 2 * (r - 6 * g);
+    const int y0 = 4 * g + e / NC, c0 = e % NC;
+    const int y1 = 4 * g + (e + 1) / NC, c1 = (e + 1) % NC;
+    const float2 z0 = R0[(jj * NC + c0) * kColRegion + y0];
+    const float2 z1 = R0[(jj * NC + c1) * kColRegion + y1];
+    dst[((long long)g * a.Kx + j0 + jj) * 6 + (r - 6 * g)] = make_float4(z0.x, z0.y, z1.x, z1.y);
   }
 }
 
 }  // namespace wfft
 
+// largest dynamic shared memory of the row kernel (two rows per block) and of the column
+// phase (two kx columns per block), set as the kernels' limits
+constexpr int kRowWSmemMax = 128 * 1024, kColWSmemMax = 112 * 1024;
+
 size_t row_warp_smem(int Kx, int warps) {
+  // warps = 8: the row-group slab kernel, with its group staged
   return (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15) +
+         (warps == 8 ? (size_t)Kx * wfft::kGroup * 3 * sizeof(float2) : 0) +
          (size_t)(warps / 2) * wfft::kPairRegion * sizeof(float2);
 }
 
 bool row_warp_ok(const rf_ctx* c) { return c->dim == 2 && c->nx == wfft::kN && c->nc == 3; }
 
-void init_attributes_fftwarp() {
-  const int s = 64 * 1024;
-  cudaFuncSetAttribute(wfft::k_fft_row_w<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
-  cudaFuncSetAttribute(wfft::k_fft_row_w<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
-  cudaFuncSetAttribute(wfft::k_fft_row_w<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
-  cudaFuncSetAttribute(wfft::k_fft_row_w<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+bool col_warp_ok(const rf_ctx* c) {
+  return c->dim == 2 && c->nx == wfft::kN && c->ny == wfft::kN && c->nc == 3 &&
+         c->d_jptr != nullptr && c->d_jent != nullptr;
+}
+
+static size_t col_warp_smem(int M) { return (size_t)3 * M * wfft::kColRegion * sizeof(float2); }
+
+template <int M, bool INIT>
+static void set_colw_attributes() {
+  cudaFuncSetAttribute(wfft::k_fft_colphase_w<M, INIT>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, kColWSmemMax);
+  cudaFuncSetAttribute(wfft::k_fft_colphase_w<M, INIT>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <bool PL, int R, bool SLAB>
+static void set_roww_attributes() {
+  cudaFuncSetAttribute(wfft::k_fft_row_w<PL, R, SLAB>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, kRowWSmemMax);
   // many small blocks per SM: the largest shared-memory carveout
-  const int pc = cudaSharedmemCarveoutMaxShared;
-  cudaFuncSetAttribute(wfft::k_fft_row_w<true, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-  cudaFuncSetAttribute(wfft::k_fft_row_w<false, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-  cudaFuncSetAttribute(wfft::k_fft_row_w<true, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-  cudaFuncSetAttribute(wfft::k_fft_row_w<false, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+  cudaFuncSetAttribute(wfft::k_fft_row_w<PL, R, SLAB>,
+                       cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
+}
+
+void init_attributes_fftwarp() {
+  set_roww_attributes<true, 1, false>();
+  set_roww_attributes<false, 1, false>();
+  set_roww_attributes<true, 2, false>();
+  set_roww_attributes<false, 2, false>();
+  set_roww_attributes<true, 4, true>();
+  set_roww_attributes<false, 4, true>();
+  set_colw_attributes<1, false>();
+  set_colw_attributes<2, false>();
+  set_colw_attributes<1, true>();
+  set_colw_attributes<2, true>();
   cudaGetLastError();
 }
 
-// One row pass (not the final one) with c->fft_row_warps (2 or 4) warps per block: one or two
-// grid rows per block, a warp pair per row.
+// The warp-FFT column phase with c->fft_colw_M (1 or 2) kx columns per block on kx slabs
+// (T1p -> Green operator and decision -> T1); init: the inverse along y of the coefficients held
+// in ER into T1 (the start of a solve in this mode).
+static int colw_launch(rf_ctx* c, const int* done, bool init) {
+  wfft::ColWArgs a{};
+  a.T1p = c->d_T1p;
+  a.T1 = c->d_T1;
+  a.ER = c->d_ER;
+  a.jptr = c->d_jptr;
+  a.jent = c->d_jent;
+  a.jn = c->d_jn;
+  a.kym = c->d_kym;
+  a.table = c->d_twy;
+  a.Kx = c->Kx;
+  a.inv2mu0 = (float)(0.5 / c->mu0);
+  a.cgam = (float)((c->lam0 + c->mu0) / (c->mu0 * (c->lam0 + 2.0 * c->mu0)));
+  a.st = c->d_status;
+  a.counter = c->d_counter;
+  a.part = c->d_part;
+  a.done = done;
+  a.cond = c->while_cond;
+  a.use_cond = (!init && c->capturing_while) ? 1 : 0;
+  const int M = c->fft_colw_M;
+  if ((M != 1 && M != 2) || col_warp_smem(M) > (size_t)kColWSmemMax) {
+    set_error("fft column phase (warp FFTs): kx columns per block must be 1 or 2");
+    return RF_ERR_INVALID;
+  }
+  if (!init) trace_stage(c, 6);
+  const dim3 grid((unsigned)((c->Kx + M - 1) / M)), block(96 * M);
+  const size_t sm = col_warp_smem(M);
+  const double Nd = (double)c->N;
+  cudaError_t e;
+  if (init)
+    e = M == 1 ? launch_pdl(wfft::k_fft_colphase_w<1, true>, grid, block, sm, c->stream, a, Nd)
+               : launch_pdl(wfft::k_fft_colphase_w<2, true>, grid, block, sm, c->stream, a, Nd);
+  else
+    e = M == 1 ? launch_pdl(wfft::k_fft_colphase_w<1, false>, grid, block, sm, c->stream, a, Nd)
+               : launch_pdl(wfft::k_fft_colphase_w<2, false>, grid, block, sm, c->stream, a, Nd);
+  c->launches += 1;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fft column phase (warp FFTs)");
+  if (!init) trace_end(c);
+  return RF_OK;
+}
+
+int launch_fft_colphase_warp(rf_ctx* c, const int* done) { return colw_launch(c, done, false); }
+
+int launch_fft_coly_init_warp(rf_ctx* c) { return colw_launch(c, nullptr, true); }
+
+// One row pass (not the final one) with c->fft_row_warps warps per block, a warp pair per row:
+// 2 or 4 (one or two rows per block) on row-major line coefficients, 8 (a row group of four
+// rows per block) on row-group slabs when the column phase is the warp-FFT one.
 int launch_fft_row_warp(rf_ctx* c, const int* done) {
   wfft::RowWArgs a{};
   a.T = c->d_T1;
@@ -320,17 +663,22 @@ int launch_fft_row_warp(rf_ctx* c, const int* done) {
   a.invN = (float)(1.0 / (double)c->N);
   a.law = c->law;
   a.done = done;
+  const bool slab = c->fft_colmode == kColWarp;
   const int R = c->fft_row_warps / 2;
   const dim3 grid((unsigned)((c->rows + R - 1) / R)), block(64 * R);
   const size_t smem = row_warp_smem(c->Kx, 2 * R);
+  if ((slab ? (R != 4 || c->rows % 4 != 0) : (R != 1 && R != 2)) ||
+      smem > (size_t)kRowWSmemMax) {
+    set_error("fft row (warp FFTs): one or two rows per block, four on row-group slabs");
+    return RF_ERR_INVALID;
+  }
   const bool pl = c->has_plastic;
   cudaError_t e;
-  if (R == 1)
-    e = pl ? launch_pdl(wfft::k_fft_row_w<true, 1>, grid, block, smem, c->stream, a)
-           : launch_pdl(wfft::k_fft_row_w<false, 1>, grid, block, smem, c->stream, a);
-  else
-    e = pl ? launch_pdl(wfft::k_fft_row_w<true, 2>, grid, block, smem, c->stream, a)
-           : launch_pdl(wfft::k_fft_row_w<false, 2>, grid, block, smem, c->stream, a);
+#define RF_ROWW(P, RR, S) launch_pdl(wfft::k_fft_row_w<P, RR, S>, grid, block, smem, c->stream, a)
+  if (slab) e = pl ? RF_ROWW(true, 4, true) : RF_ROWW(false, 4, true);
+  else if (R == 1) e = pl ? RF_ROWW(true, 1, false) : RF_ROWW(false, 1, false);
+  else e = pl ? RF_ROWW(true, 2, false) : RF_ROWW(false, 2, false);
+#undef RF_ROWW
   c->launches += 1;
   if (e != cudaSuccess) return cuda_fail(e, "fft row (warp FFTs)");
   e = cudaGetLastError();

@@ -205,10 +205,13 @@ struct rf_ctx {
   int fft_rbase = 0, fft_rextra = 0;    // row partition (see set_rows_balanced)
   int fft_row_threads = 256, fft_col_threads = 256;   // block sizes (autotuned with the tiles)
   int fft_row_warps = 0;   // > 0: row passes (not the final one) on the warp-FFT row kernel
+  int fft_colw_M = 1;      // kx columns per block of the warp-FFT column phase (kColWarp)
   size_t fft_smem = 0;
   // 2D column phase: 0 forward y, Green kernel, inverse y; 1 one fused kernel per kx group
   // (kColFused); 2 forward y, then the Green operator inside the inverse y kernel
-  // (kColGreenInv). Modes 1 and 2 start a solve with one inverse y of the start coefficients.
+  // (kColGreenInv); 4 as 1 with a warp per line column, the transforms in registers and the
+  // line coefficients in kx slabs (kColWarp, 1024 x 1024, warp-FFT row kernel). Modes 1, 2 and
+  // 4 start a solve with one inverse y of the start coefficients.
   int fft_colmode = 0;
   int fft_M = 1, fft_M_threads = 256;   // kx columns and threads per fused block
   // persistent 2D solve (column mode kColPersistent): grid, block size, dynamic shared memory,
@@ -229,7 +232,7 @@ struct rf_ctx {
     int row_blocks_balanced = 0;
     int colmode = 0;
     int persist_per_sm = 0, persist_threads = 0;
-    int row_warps = 0;
+    int row_warps = 0, colw_M = 1;
   } tuned;
 
   // split-precision (tensor-core) transforms along x
@@ -431,7 +434,8 @@ int launch_tc_axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits,
                    long long out_bstride, int N, int batch, const int* done);
 int launch_fft_green_inv(rf_ctx* c, const int* done);
 int launch_gather_jentries(rf_ctx* c);
-constexpr int kColSeparate = 0, kColFused = 1, kColGreenInv = 2, kColPersistent = 3;
+constexpr int kColSeparate = 0, kColFused = 1, kColGreenInv = 2, kColPersistent = 3,
+              kColWarp = 4;
 // rf_persist.cu
 bool persist_geometry(rf_ctx* c, int threads, int per_sm);
 int launch_persist_solve(rf_ctx* c, unsigned long long* trace, int trace_cap);
@@ -454,6 +458,12 @@ void init_attributes_fftwarp();
 bool row_warp_ok(const rf_ctx* c);
 size_t row_warp_smem(int Kx, int warps);
 int launch_fft_row_warp(rf_ctx* c, const int* done);
+// warp-FFT column phase (2D, 1024 x 1024, three components; column mode kColWarp; line
+// coefficients in kx slabs between the row pass and the column phase) and the inverse along y
+// of the held coefficients that starts a solve in that mode
+bool col_warp_ok(const rf_ctx* c);
+int launch_fft_colphase_warp(rf_ctx* c, const int* done);
+int launch_fft_coly_init_warp(rf_ctx* c);
 // pattern.cu
 int pattern_adapted(const rf_grid* g, const uint8_t* pm, int incl, long long k_target,
                     int32_t* out, long long cap, long long* K_out, cudaStream_t s);

@@ -812,6 +812,12 @@ int launch_iteration(rf_ctx* c) {
     if (int e = launch_fft_row(c, done, false, 0)) return e;
     return launch_fft_colphase(c, done);
   }
+  if (fftm && c->fft_colmode == kColWarp) {
+    // as kColFused, the column phase on the warp-FFT column kernel
+    trace_stage(c, 2);
+    if (int e = launch_fft_row(c, done, false, 0)) return e;
+    return launch_fft_colphase_warp(c, done);
+  }
   if (fftm && c->fft_colmode == kColGreenInv) {
     // row pass, forward y, then the Green operator + decision inside the inverse y kernel
     trace_stage(c, 2);

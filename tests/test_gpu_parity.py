@@ -636,11 +636,91 @@ def test_fft_warp_row_kernel_matches_oracle(lib, name, warps, fuse):
     assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
 
 
+def _square_1024(name):
+    """1024 x 1024 cases for the warp-FFT column phase: the J2 fibre composite with its adapted
+    pattern (K = 5 %), an elastic disc composite with every frequency (Kx = 513: odd, dense
+    columns of 1024 entries), and the elastic composite with an adapted pattern (K = 2 %)."""
+    cfg = make_config("c2")
+    pm = cfg["phase_map"]
+    if name == "c2_j2":
+        return pm, cfg["phases"], np.array([0.02, 0, 0, 0, 0, 0.003]), \
+            O.pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    if name == "full_elastic":
+        return pm, elastic_phases(), random_macro_strain(31, 2), O.full_pattern((1,) + pm.shape)
+    if name == "adapted_elastic":
+        return pm, elastic_phases(), random_macro_strain(32, 2), \
+            O.pattern_adapted(pm, 1, k_target(0.02, pm.size))
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,kx", [("c2_j2", 1), ("c2_j2", 2), ("full_elastic", 2),
+                                     ("adapted_elastic", 1)])
+def test_fft_warp_column_phase_matches_oracle(lib, name, kx):
+    """fft_fuse 4 on 1024 x 1024 grids: the warp-FFT row kernel and the warp-FFT column phase
+    (a warp per line column, the 1024-point transforms along y in registers, Green operator and
+    decision in the same kernel) exchanging line coefficients in kx slabs, `kx` kx columns per
+    block; three updates against the oracle at the FP32 parity tolerances, reduced coefficients
+    included."""
+    pm, ph, macro, pat = _square_1024(name)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft", fft_fuse=4,
+                   fft_fuse_kx=kx)
+    out = s.rf_solve(macro)
+    eps, sig, _ = s.rf_get_fields()
+    coeffs = s.rf_get_reduced_strain()
+    info = s.rf_get_info()
+    s.close()
+    assert info["fft_fused"] == 4 and info["fft_fuse_kx"] == kx and out["iters"] == 3
+    assert info["fft_row_warps"] == 8                   # the row-group slab row kernel
+    r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=3)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(sig, vec6_field(r.sigma)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    want = np.stack([r.eps_hat[:, i, j] for (i, j) in VOIGT], axis=1)
+    assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
+
+
+def test_fft_warp_column_phase_load_path_mixed_control_and_options(lib):
+    """The 1024^2 J2 composite: a load path to the tolerance and a mixed stress/strain solve in
+    the warp-FFT column mode take the three-kernel mode's decisions (update counts within one:
+    FP64 sums in another order) and reach its answers; options outside the mode's range are
+    rejected (kx columns per block, the shared-memory row kernel, grids other than 1024^2)."""
+    pm, ph, _, pat = _square_1024("c2_j2")
+    path = uniaxial_path(20, 0.02)[[4, 9, 14]]
+    control = np.array([1, 0, 0, 0, 0, 1], np.int32)
+    target = np.array([0.01, 0.0, 0.0, 0.0, 0.0, 0.0])
+    res = {}
+    for fuse in (-1, 4):
+        s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform="fft",
+                       fft_fuse=fuse)
+        p = s.rf_solve_path(path)
+        e = s.rf_get_fields()[0]
+        s.rf_reset_path()
+        m = s.rf_solve_mixed(control, target)
+        res[fuse] = (p, e, m)
+        s.close()
+    (a, ea, ma), (b, eb, mb) = res[-1], res[4]
+    assert a["converged"] and b["converged"]
+    assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
+    assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
+    assert rel(eb, ea) <= 2e-5
+    assert abs(ma["iters"] - mb["iters"]) <= 1
+    assert rel(mb["sigma_bar"], ma["sigma_bar"]) <= 1e-5
+    assert rel(mb["strain_bar"], ma["strain_bar"]) <= 1e-5
+    for bad in (dict(fft_fuse=4, fft_fuse_kx=3), dict(fft_fuse=4, fft_row_warps=-1),
+                dict(fft_fuse=4, fft_row_warps=2), dict(fft_fuse=1, fft_row_warps=8),
+                dict(fft_fuse=5)):
+        with pytest.raises(lib.RFError):
+            lib.Solver(pm, ph, pattern=pat, transform="fft", **bad)
+    with pytest.raises(lib.RFError):
+        lib.Solver(np.zeros((1024, 512), np.uint8), ph, transform="fft", fft_fuse=4)
+
+
 def test_fft_warp_row_kernel_option(lib):
     """fft_row_warps: 2 and 4 force the warp-FFT row kernel where it applies (2D, rows of 1024)
-    and are ignored elsewhere; -1 keeps the shared-memory row kernel; other values are rejected.
+    and are ignored elsewhere; -1 keeps the shared-memory row kernel; 8 (the row-group slab
+    form) goes only with fft_fuse 4; other values are rejected.
     A J2 load path to the tolerance takes the same decisions with either row kernel."""
-    for bad in (-2, 1, 3, 8):
+    for bad in (-2, 1, 3, 8, 16):
         with pytest.raises(lib.RFError):
             lib.Solver(np.zeros((8, 1024), np.uint8), elastic_phases(), transform="fft",
                        fft_row_warps=bad)
