@@ -163,7 +163,8 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
   grid_dep_wait();
   if (a.done && *a.done) return;   // the same flag value for every thread of the grid
   const float lam0 = a.law.lam0, mu0 = a.law.mu0;
-  // kx slabs: the block's row group staged in shared memory, [Kx][4][NC]
+  // row-group slabs: the block's group staged in shared memory as [4][NC][Kx] (lanes on
+  // consecutive kx read and write it without bank conflicts)
   float2* G = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15));
   for (int row = blockIdx.x * R + pair; row < a.rows; row += gridDim.x * R) {
     const float2* Tr = a.T + (long long)row * NC * Kx;
@@ -172,7 +173,6 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
     if (SLAB) {
       // the group's coefficients: Kx * 96 contiguous bytes, 16-byte loads
       const float4* src = reinterpret_cast<const float4*>(a.T + slab_at(0, row - r4, 0, Kx));
-      float4* g4 = reinterpret_cast<float4*>(G);
       const int n4 = Kx * kGroup * NC / 2;
       for (int q0 = threadIdx.x; q0 < n4; q0 += 4 * blockDim.x) {
         float4 t[4];
@@ -180,8 +180,14 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
         for (int u = 0; u < 4; ++u)
           if (q0 + u * (int)blockDim.x < n4) t[u] = src[q0 + u * blockDim.x];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (q0 + u * (int)blockDim.x < n4) g4[q0 + u * blockDim.x] = t[u];
+        for (int u = 0; u < 4; ++u) {
+          const int q = q0 + u * blockDim.x;
+          if (q >= n4) continue;
+          // entries 2q, 2q + 1 of [Kx][4][NC]
+          const int e = 2 * q, j = e / 12, m = e - 12 * j;
+          G[m * Kx + j] = make_float2(t[u].x, t[u].y);
+          G[(m + 1) * Kx + j] = make_float2(t[u].z, t[u].w);   // m even: m + 1 < 12
+        }
       }
       __syncthreads();
     }
@@ -199,9 +205,9 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
         c0[u] = c1[u] = make_float2(0.f, 0.f);
         if (j < Kx) {
           if (SLAB) {
-            const float2* p = G + (j * kGroup + r4) * NC + (role ? 2 : 0);
+            const float2* p = G + (r4 * NC + (role ? 2 : 0)) * Kx + j;
             c0[u] = p[0];
-            if (!role) c1[u] = p[1];
+            if (!role) c1[u] = p[Kx];
           } else {
             c0[u] = l0[j];
             if (!role) c1[u] = Tr[Kx + j];
@@ -310,16 +316,16 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
       if (role) {
         float2 z = zk;
         if (k == 0 || 2 * k == L) z.y = 0.f;   // a real line's self-conjugate coefficients
-        if (SLAB) G[(j * kGroup + r4) * NC + 2] = z;
+        if (SLAB) G[(r4 * NC + 2) * Kx + j] = z;
         else To[2 * Kx + j] = z;
       } else {
         const float2 zm = S[k == 0 ? 0 : L - k];
         const float2 t0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         const float2 t1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
         if (SLAB) {
-          float2* p = G + (j * kGroup + r4) * NC;
+          float2* p = G + r4 * NC * Kx + j;
           p[0] = t0;
-          p[1] = t1;
+          p[Kx] = t1;
         } else {
           To[j] = t0;
           To[Kx + j] = t1;
@@ -331,9 +337,12 @@ __global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
       // the group's polarization coefficients out with 16-byte stores
       __syncthreads();
       float4* dst = reinterpret_cast<float4*>(a.Tout + slab_at(0, row - r4, 0, Kx));
-      const float4* g4 = reinterpret_cast<const float4*>(G);
       const int n4 = Kx * kGroup * NC / 2;
-      for (int q = threadIdx.x; q < n4; q += blockDim.x) dst[q] = g4[q];
+      for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+        const int e = 2 * q, j = e / 12, m = e - 12 * j;
+        const float2 z0 = G[m * Kx + j], z1 = G[(m + 1) * Kx + j];
+        dst[q] = make_float4(z0.x, z0.y, z1.x, z1.y);
+      }
       __syncthreads();   // before the next group overwrites the staging
     }
   }
@@ -389,6 +398,27 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
   const int eM = M == 2 ? a.jptr[j0 + 1] : e1;   // first entry of the second kx
 #pragma unroll
   for (int i = 0; i < 32; ++i) D[lane + 32 * i] = make_float2(0.f, 0.f);
+  // the pattern's entry data (fixed with the pattern): the first kB entries of this thread are
+  // fetched before the dependency wait
+  int2 en[kB];
+  float4 nv[kB];
+  int pos[kB];
+  auto fetch = [&](int eb) {
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = eb + u * blockDim.x;
+      if (e < e1) {
+        en[u] = a.jent[e];
+        if (!INIT) nv[u] = a.jn[e];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = eb + u * blockDim.x;
+      if (e < e1) pos[u] = a.kym[en[u].x];
+    }
+  };
+  fetch(e0 + threadIdx.x);
   grid_dep_wait();
   if (!INIT && a.done && __ldcg(a.done)) return;   // the same flag value for every thread
   float2 v[32];
@@ -397,10 +427,10 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
     // the block's kx in every row group: 96 contiguous bytes (six float4) per group; float4 k
     // of group g holds the entries 2k, 2k + 1 of [4][NC], i.e. (y - 4 g, c) = divmod(., NC)
     const float4* src = reinterpret_cast<const float4*>(a.T1p);
-    for (int q0 = threadIdx.x; q0 < nj * kSlab4; q0 += 8 * blockDim.x) {
-      float4 t[8];
+    for (int q0 = threadIdx.x; q0 < nj * kSlab4; q0 += 16 * blockDim.x) {
+      float4 t[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int q = q0 + u * blockDim.x;
         if (q < nj * kSlab4) {
           const int jj = q >= kSlab4 ? 1 : 0, r = q - jj * kSlab4, g = r / 6;
@@ -408,7 +438,7 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
         }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int q = q0 + u * blockDim.x;
         if (q >= nj * kSlab4) continue;
         const int jj = q >= kSlab4 ? 1 : 0, r = q - jj * kSlab4, g = r / 6, e = 2 * (r - 6 * g);
@@ -431,24 +461,13 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
   // with their loads issued together (tau^ read only where it is used: regular frequencies, and
   // the zero frequency under mixed control)
   for (int eb = e0 + threadIdx.x; eb < e1; eb += kB * blockDim.x) {
-    int2 en[kB];
-    float4 nv[kB];
-    int pos[kB];
     float2 old[kB][NC];
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int e = eb + u * blockDim.x;
-      if (e < e1) {
-        en[u] = a.jent[e];
-        if (!INIT) nv[u] = a.jn[e];
-      }
-    }
+    if (eb != e0 + (int)threadIdx.x) fetch(eb);
 #pragma unroll
     for (int u = 0; u < kB; ++u) {
       const int e = eb + u * blockDim.x;
       if (e < e1) {
         const int je = (M == 2 && e >= eM) ? 1 : 0;
-        pos[u] = a.kym[en[u].x];
         const long long base = ((long long)en[u].x * NC) * a.Kx + j0 + je;
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) old[u][cc] = a.ER[base + (long long)cc * a.Kx];
