@@ -64,6 +64,8 @@ def parse():
                    help="c2 FFT mode column phase: three kernels (-1), one fused kernel (1), "
                         "Green operator inside the inverse y kernel (2), the persistent solve "
                         "(3), the warp-FFT column kernel (4), or timed (0)")
+    p.add_argument("--fft-fuse-kx", type=int, default=0,
+                   help="c2 FFT mode: kx columns per fused column block (0: autotuned)")
     p.add_argument("--fft-row-warps", type=int, default=0, choices=[-1, 0, 2, 4, 8],
                    help="c2 FFT mode: warps per block of the warp-FFT row kernel (-1: the "
                         "shared-memory row kernel, 0: timed)")
@@ -736,7 +738,8 @@ def main():
     tiles = {}
     if args.transform == "fft":
         tiles = dict(fft_rows=args.fft_rows, fft_cols=args.fft_cols, fft_fuse=args.fft_fuse,
-                     fft_row_blocks=args.fft_row_blocks, fft_row_warps=args.fft_row_warps)
+                     fft_row_blocks=args.fft_row_blocks, fft_row_warps=args.fft_row_warps,
+                     fft_fuse_kx=args.fft_fuse_kx)
     if args.profile_updates > 0:
         s = rf.Solver(pm, phases, pattern=pattern, stream=sh, tol=0.0,
                       max_iter=args.profile_updates, transform=args.transform,

@@ -615,6 +615,7 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
     d.plastic = phases[p].plastic ? 1 : 0;
     d.sy = d.plastic ? (float)phases[p].sigma_y0 : 0.f;
     d.H = d.plastic ? (float)phases[p].hardening : 0.f;
+    d.r3muH = d.plastic ? (float)(1.0 / (3.0 * phases[p].mu + phases[p].hardening)) : 0.f;
     any_plastic = any_plastic || d.plastic;
   }
   c->has_plastic = any_plastic;

@@ -30,7 +30,8 @@ constexpr int kGammaBlock = 128;   // threads per Green-operator block (one freq
 struct DevPhase {
   float lam, mu, sy, H;
   int plastic;
-  int pad[3];
+  float r3muH;   // 1 / (3 mu + H) of a plastic phase (the radial return's scaling), else 0
+  int pad[2];
 };
 
 struct LawParams {

@@ -48,10 +48,12 @@ __device__ __forceinline__ void stress6(const float* e, const DevPhase& p, const
   float phi = seq - (p.sy + p.H * alpha);
   float pm = (p.lam + (2.f / 3.f) * p.mu) * tre;
   if (phi > 0.f) {
-    // radial return: dgamma = phi / (3 mu + H), flow direction 3/2 s / sigma_eq
-    float dg = phi / (3.f * p.mu + p.H);
-    float fl = 1.5f * dg / seq;
-    float f = 1.f - 3.f * p.mu * dg / seq;
+    // radial return: dgamma = phi / (3 mu + H), flow direction 3/2 s / sigma_eq (seq > 0 here:
+    // phi > 0 and sigma_y0 > 0); one division per voxel
+    const float rs = 1.f / seq;
+    float dg = phi * p.r3muH;
+    float fl = 1.5f * dg * rs;
+    float f = 1.f - 3.f * p.mu * dg * rs;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       o.ep[i] = ep[i] + fl * s[i];
