@@ -376,10 +376,10 @@ constexpr int kColRegion = kRegion + kN;   // a column warp's region: R (1056) a
 // warp transforms its column forward in registers and leaves the spectrum in R; the block applies
 // the Green operator at its kx's pattern entries (all NC components of an entry come from the
 // regions of the same kx), writes the new coefficients to ER and into the zeroed spectra D, and
-// sums the convergence measure (FP64 partial per block; the last block takes the decision); each
-// warp transforms D back to space along y (R as the transpose buffer), and the block stores its
-// pieces for the next row pass. INIT: only the inverse of the coefficients held in ER (the start
-// of a solve), no decision.
+// sums the convergence measure; each warp transforms D back to space along y (R as the transpose
+// buffer), the block stores its pieces for the next row pass and then writes its FP64 partial of
+// the measure (the last block takes the decision). INIT: only the inverse of the coefficients
+// held in ER (the start of a solve), no decision.
 template <int M, bool INIT>
 __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd) {
   constexpr int NC = 3, kB = 4;   // entries per thread in flight
@@ -514,33 +514,10 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
       diff += (double)d;
     }
   }
-  if (!INIT) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
-    if (lane == 0) red[w] = diff;
-  }
-  __syncthreads();   // also: every spectrum D is complete
-  if (!INIT) {
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < 3 * M; ++i) t += red[i];
-      a.part[blockIdx.x] = t;
-      __threadfence();
-      last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      decide(a.part, gridDim.x, a.st, sh);
-      if (threadIdx.x == 0) {
-        *a.counter = 0u;
-        // the only call site of the loop condition in this mode: one thread of one block
-        if (a.use_cond && a.st->done) cudaGraphSetConditional(a.cond, 0u);
-      }
-    }
-  }
+  __syncthreads();   // every spectrum D is complete
   // inverse along y as the conjugate of the forward transform of the conjugate; the column back
-  // to R, then the block's slabs out with 16-byte stores
+  // to R, then the block's pieces out with 16-byte stores; the convergence decision after them
+  // (it only gates the next update), so the last block's decision is all that trails the stores
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     v[i] = D[lane + 32 * i];
@@ -558,6 +535,28 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
     const float2 z0 = R0[(jj * NC + c0) * kColRegion + y0];
     const float2 z1 = R0[(jj * NC + c1) * kColRegion + y1];
     dst[((long long)g * a.Kx + j0 + jj) * 6 + (r - 6 * g)] = make_float4(z0.x, z0.y, z1.x, z1.y);
+  }
+  if (INIT) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+  if (lane == 0) red[w] = diff;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 3 * M; ++i) t += red[i];
+    a.part[blockIdx.x] = t;
+    __threadfence();
+    last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    decide(a.part, gridDim.x, a.st, sh);
+    if (threadIdx.x == 0) {
+      *a.counter = 0u;
+      // the only call site of the loop condition in this mode: one thread of one block
+      if (a.use_cond && a.st->done) cudaGraphSetConditional(a.cond, 0u);
+    }
   }
 }
 
