@@ -145,207 +145,217 @@ __device__ __forceinline__ void pair_sync(int p) {
 // each holding its sequence's spectrum, its transposes and, between the transforms, the
 // sequence in space. SLAB (R = 4, a block per row group): the group's line coefficients are
 // staged in shared memory, loaded and stored by the whole block as one contiguous block.
-template <bool PLASTIC, int R, bool SLAB>
-__global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
+// One grid row of the row pass for the warp pair of this thread (pair = threadIdx.x / 64 within
+// the block; both warps of the pair call it with the same row). SLAB: the whole block calls it
+// for the four rows of one group (it stages the group through G with block barriers).
+template <bool PLASTIC, bool SLAB>
+__device__ __forceinline__ void row_pass(const RowWArgs& a, int row, const int* kxs,
+                                         const DevPhase* phs, float2* G, float2* SA, float2* SB) {
   constexpr int NC = 3, L = kN;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ DevPhase phs[kMaxPhases];
   const int lane = threadIdx.x & 31, pair = threadIdx.x >> 6, role = (threadIdx.x >> 5) & 1;
   const int Kx = a.Kx;
-  int* kxs = reinterpret_cast<int*>(smem);
-  float2* SA = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15)) +
-               (SLAB ? (size_t)Kx * kGroup * NC : 0) + (size_t)pair * kPairRegion;
-  float2* SB = SA + kRegion;
   float2* S = role ? SB : SA;   // this warp's region
+  const float lam0 = a.law.lam0, mu0 = a.law.mu0;
+  const float2* Tr = a.T + (long long)row * NC * Kx;
+  float2* To = a.Tout + (long long)row * NC * Kx;
+  const int r4 = row & (kGroup - 1);
+  if (SLAB) {
+    // the group's coefficients: Kx * 96 contiguous bytes, 16-byte loads
+    const float4* src = reinterpret_cast<const float4*>(a.T + slab_at(0, row - r4, 0, Kx));
+    const int n4 = Kx * kGroup * NC / 2;
+    for (int q0 = threadIdx.x; q0 < n4; q0 += 4 * blockDim.x) {
+      float4 t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u * (int)blockDim.x < n4) t[u] = src[q0 + u * blockDim.x];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q >= n4) continue;
+        // entries 2q, 2q + 1 of [Kx][4][NC]
+        const int e = 2 * q, j = e / 12, m = e - 12 * j;
+        G[m * Kx + j] = make_float2(t[u].x, t[u].y);
+        G[(m + 1) * Kx + j] = make_float2(t[u].z, t[u].w);   // m even: m + 1 < 12
+      }
+    }
+    __syncthreads();
+  }
+  // ---- spectrum: A from lines 11 and 22, B from line 12; loads eight per lane in flight
+#pragma unroll
+  for (int i = 0; i < 32; ++i) S[lane + 32 * i] = make_float2(0.f, 0.f);
+  __syncwarp();
+  const float2* l0 = Tr + (role ? 2 * Kx : 0);
+#pragma unroll 1
+  for (int j0 = 0; j0 < Kx; j0 += 256) {
+    float2 c0[8], c1[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + lane + 32 * u;
+      c0[u] = c1[u] = make_float2(0.f, 0.f);
+      if (j < Kx) {
+        if (SLAB) {
+          const float2* p = G + (r4 * NC + (role ? 2 : 0)) * Kx + j;
+          c0[u] = p[0];
+          if (!role) c1[u] = p[Kx];
+        } else {
+          c0[u] = l0[j];
+          if (!role) c1[u] = Tr[Kx + j];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + lane + 32 * u;
+      if (j >= Kx) continue;
+      const int k = kxs[j];
+      float2 t0 = c0[u], t1 = c1[u];
+      const bool self = (k == 0) || (2 * k == L);
+      if (self) {
+        t0.y = 0.f;
+        t1.y = 0.f;
+      }
+      // t0 + i t1 at k, conj(t0) + i conj(t1) at L - k (t1 = 0 for B)
+      S[k] = make_float2(t0.x - t1.y, t0.y + t1.x);
+      if (!self) S[L - k] = make_float2(t0.x + t1.y, t1.x - t0.y);
+    }
+  }
+  __syncwarp();
+  if (SLAB) __syncthreads();   // the staged group is read; it takes the outputs next
+  // the law's first phase ids and internal variables (voxels x = 32 n1 + lane for n1 in this
+  // warp's half of the row, kU per step) go out before the transform to space; each law step
+  // then loads the next step's while it computes
+  constexpr int kU = 2;
+  const int nb = 16 * role;
+  const long long g0 = (long long)row * L + lane;
+  uint8_t pid[kU], pidn[kU];
+  float stv[kU][4], stn[kU][4];
+  auto load = [&](int n1b, uint8_t* pd, float (*st)[4]) {
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const long long g = g0 + 32 * (n1b + u);
+      pd[u] = a.phase[g];
+      if (PLASTIC) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) st[u][i] = a.state[i * a.N + g];
+      }
+    }
+  };
+  load(nb, pid, stv);
+  // ---- to space: the conjugate of the forward transform of the conjugate spectrum
+  float2 v[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    v[i] = S[lane + 32 * i];
+    v[i].y = -v[i].y;
+  }
+  __syncwarp();
+  fwd1024(v, S, a.table, lane);
+  // this warp's sequence in space, voxel x at S[x]
+#pragma unroll
+  for (int i = 0; i < 32; ++i) S[lane + 32 * i] = make_float2(v[i].x, -v[i].y);
+  pair_sync(pair);
+  // ---- the law
+  {
+#pragma unroll 1
+    for (int n1b = nb; n1b < nb + 16; n1b += kU) {
+      if (n1b + kU < nb + 16) load(n1b + kU, pidn, stn);
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int x = 32 * (n1b + u) + lane;
+        const float2 qa = SA[x];
+        float e6[6] = {qa.x * a.invN, qa.y * a.invN, 0.f, 0.f, 0.f, SB[x].x * a.invN};
+        float ep[6] = {0, 0, 0, 0, 0, 0};
+        float alpha = 0.f;
+        if (PLASTIC) {
+          ep[0] = stv[u][0];
+          ep[1] = stv[u][1];
+          ep[5] = stv[u][2];
+          ep[2] = -(ep[0] + ep[1]);
+          alpha = stv[u][3];
+        }
+        LawOut o;
+        stress6<PLASTIC>(e6, phs[pid[u]], ep, alpha, o);
+        const float tr = e6[0] + e6[1] + e6[2];
+        SA[x] = make_float2(o.s[0] - (lam0 * tr + 2.f * mu0 * e6[0]),
+                           o.s[1] - (lam0 * tr + 2.f * mu0 * e6[1]));
+        SB[x] = make_float2(o.s[5] - 2.f * mu0 * e6[5], 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        pid[u] = pidn[u];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) stv[u][i] = stn[u][i];
+      }
+    }
+  }
+  pair_sync(pair);
+  // ---- the polarization's coefficients: forward transform, then the pattern's kx columns,
+  // B (role 1) directly, A (role 0) separated into lines 11 and 22
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = S[lane + 32 * i];
+  __syncwarp();
+  fwd1024(v, S, a.table, lane);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) S[lane + 32 * i] = v[i];
+  __syncwarp();
+#pragma unroll 4
+  for (int j = lane; j < Kx; j += 32) {
+    const int k = kxs[j];
+    const float2 zk = S[k];
+    if (role) {
+      float2 z = zk;
+      if (k == 0 || 2 * k == L) z.y = 0.f;   // a real line's self-conjugate coefficients
+      if (SLAB) G[(r4 * NC + 2) * Kx + j] = z;
+      else To[2 * Kx + j] = z;
+    } else {
+      const float2 zm = S[k == 0 ? 0 : L - k];
+      const float2 t0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      const float2 t1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      if (SLAB) {
+        float2* p = G + r4 * NC * Kx + j;
+        p[0] = t0;
+        p[Kx] = t1;
+      } else {
+        To[j] = t0;
+        To[Kx + j] = t1;
+      }
+    }
+  }
+  __syncwarp();
+  if (SLAB) {
+    // the group's polarization coefficients out with 16-byte stores
+    __syncthreads();
+    float4* dst = reinterpret_cast<float4*>(a.Tout + slab_at(0, row - r4, 0, Kx));
+    const int n4 = Kx * kGroup * NC / 2;
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+      const int e = 2 * q, j = e / 12, m = e - 12 * j;
+      const float2 z0 = G[m * Kx + j], z1 = G[(m + 1) * Kx + j];
+      dst[q] = make_float4(z0.x, z0.y, z1.x, z1.y);
+    }
+    __syncthreads();   // before the next group overwrites the staging
+  }
+}
+
+template <bool PLASTIC, int R, bool SLAB>
+__global__ __maxnreg__(128) void k_fft_row_w(RowWArgs a) {
+  constexpr int NC = 3;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ DevPhase phs[kMaxPhases];
+  const int pair = threadIdx.x >> 6;
+  const int Kx = a.Kx;
+  int* kxs = reinterpret_cast<int*>(smem);
+  // row-group slabs: the block's group staged in shared memory as [4][NC][Kx] (lanes on
+  // consecutive kx read and write it without bank conflicts)
+  float2* G = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15));
+  float2* SA = G + (SLAB ? (size_t)Kx * kGroup * NC : 0) + (size_t)pair * kPairRegion;
+  float2* SB = SA + kRegion;
   for (int i = threadIdx.x; i < Kx; i += blockDim.x) kxs[i] = a.kx[i];
   for (int i = threadIdx.x; i < kMaxPhases; i += blockDim.x) phs[i] = a.law.ph[i];
   __syncthreads();
   grid_dep_wait();
   if (a.done && *a.done) return;   // the same flag value for every thread of the grid
-  const float lam0 = a.law.lam0, mu0 = a.law.mu0;
-  // row-group slabs: the block's group staged in shared memory as [4][NC][Kx] (lanes on
-  // consecutive kx read and write it without bank conflicts)
-  float2* G = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15));
-  for (int row = blockIdx.x * R + pair; row < a.rows; row += gridDim.x * R) {
-    const float2* Tr = a.T + (long long)row * NC * Kx;
-    float2* To = a.Tout + (long long)row * NC * Kx;
-    const int r4 = row & (kGroup - 1);
-    if (SLAB) {
-      // the group's coefficients: Kx * 96 contiguous bytes, 16-byte loads
-      const float4* src = reinterpret_cast<const float4*>(a.T + slab_at(0, row - r4, 0, Kx));
-      const int n4 = Kx * kGroup * NC / 2;
-      for (int q0 = threadIdx.x; q0 < n4; q0 += 4 * blockDim.x) {
-        float4 t[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (q0 + u * (int)blockDim.x < n4) t[u] = src[q0 + u * blockDim.x];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int q = q0 + u * blockDim.x;
-          if (q >= n4) continue;
-          // entries 2q, 2q + 1 of [Kx][4][NC]
-          const int e = 2 * q, j = e / 12, m = e - 12 * j;
-          G[m * Kx + j] = make_float2(t[u].x, t[u].y);
-          G[(m + 1) * Kx + j] = make_float2(t[u].z, t[u].w);   // m even: m + 1 < 12
-        }
-      }
-      __syncthreads();
-    }
-    // ---- spectrum: A from lines 11 and 22, B from line 12; loads eight per lane in flight
-#pragma unroll
-    for (int i = 0; i < 32; ++i) S[lane + 32 * i] = make_float2(0.f, 0.f);
-    __syncwarp();
-    const float2* l0 = Tr + (role ? 2 * Kx : 0);
-#pragma unroll 1
-    for (int j0 = 0; j0 < Kx; j0 += 256) {
-      float2 c0[8], c1[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = j0 + lane + 32 * u;
-        c0[u] = c1[u] = make_float2(0.f, 0.f);
-        if (j < Kx) {
-          if (SLAB) {
-            const float2* p = G + (r4 * NC + (role ? 2 : 0)) * Kx + j;
-            c0[u] = p[0];
-            if (!role) c1[u] = p[Kx];
-          } else {
-            c0[u] = l0[j];
-            if (!role) c1[u] = Tr[Kx + j];
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = j0 + lane + 32 * u;
-        if (j >= Kx) continue;
-        const int k = kxs[j];
-        float2 t0 = c0[u], t1 = c1[u];
-        const bool self = (k == 0) || (2 * k == L);
-        if (self) {
-          t0.y = 0.f;
-          t1.y = 0.f;
-        }
-        // t0 + i t1 at k, conj(t0) + i conj(t1) at L - k (t1 = 0 for B)
-        S[k] = make_float2(t0.x - t1.y, t0.y + t1.x);
-        if (!self) S[L - k] = make_float2(t0.x + t1.y, t1.x - t0.y);
-      }
-    }
-    __syncwarp();
-    if (SLAB) __syncthreads();   // the staged group is read; it takes the outputs next
-    // the law's first phase ids and internal variables (voxels x = 32 n1 + lane for n1 in this
-    // warp's half of the row, kU per step) go out before the transform to space; each law step
-    // then loads the next step's while it computes
-    constexpr int kU = 2;
-    const int nb = 16 * role;
-    const long long g0 = (long long)row * L + lane;
-    uint8_t pid[kU], pidn[kU];
-    float stv[kU][4], stn[kU][4];
-    auto load = [&](int n1b, uint8_t* pd, float (*st)[4]) {
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const long long g = g0 + 32 * (n1b + u);
-        pd[u] = a.phase[g];
-        if (PLASTIC) {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) st[u][i] = a.state[i * a.N + g];
-        }
-      }
-    };
-    load(nb, pid, stv);
-    // ---- to space: the conjugate of the forward transform of the conjugate spectrum
-    float2 v[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      v[i] = S[lane + 32 * i];
-      v[i].y = -v[i].y;
-    }
-    __syncwarp();
-    fwd1024(v, S, a.table, lane);
-    // this warp's sequence in space, voxel x at S[x]
-#pragma unroll
-    for (int i = 0; i < 32; ++i) S[lane + 32 * i] = make_float2(v[i].x, -v[i].y);
-    pair_sync(pair);
-    // ---- the law
-    {
-#pragma unroll 1
-      for (int n1b = nb; n1b < nb + 16; n1b += kU) {
-        if (n1b + kU < nb + 16) load(n1b + kU, pidn, stn);
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int x = 32 * (n1b + u) + lane;
-          const float2 qa = SA[x];
-          float e6[6] = {qa.x * a.invN, qa.y * a.invN, 0.f, 0.f, 0.f, SB[x].x * a.invN};
-          float ep[6] = {0, 0, 0, 0, 0, 0};
-          float alpha = 0.f;
-          if (PLASTIC) {
-            ep[0] = stv[u][0];
-            ep[1] = stv[u][1];
-            ep[5] = stv[u][2];
-            ep[2] = -(ep[0] + ep[1]);
-            alpha = stv[u][3];
-          }
-          LawOut o;
-          stress6<PLASTIC>(e6, phs[pid[u]], ep, alpha, o);
-          const float tr = e6[0] + e6[1] + e6[2];
-          SA[x] = make_float2(o.s[0] - (lam0 * tr + 2.f * mu0 * e6[0]),
-                             o.s[1] - (lam0 * tr + 2.f * mu0 * e6[1]));
-          SB[x] = make_float2(o.s[5] - 2.f * mu0 * e6[5], 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          pid[u] = pidn[u];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) stv[u][i] = stn[u][i];
-        }
-      }
-    }
-    pair_sync(pair);
-    // ---- the polarization's coefficients: forward transform, then the pattern's kx columns,
-    // B (role 1) directly, A (role 0) separated into lines 11 and 22
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = S[lane + 32 * i];
-    __syncwarp();
-    fwd1024(v, S, a.table, lane);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) S[lane + 32 * i] = v[i];
-    __syncwarp();
-#pragma unroll 4
-    for (int j = lane; j < Kx; j += 32) {
-      const int k = kxs[j];
-      const float2 zk = S[k];
-      if (role) {
-        float2 z = zk;
-        if (k == 0 || 2 * k == L) z.y = 0.f;   // a real line's self-conjugate coefficients
-        if (SLAB) G[(r4 * NC + 2) * Kx + j] = z;
-        else To[2 * Kx + j] = z;
-      } else {
-        const float2 zm = S[k == 0 ? 0 : L - k];
-        const float2 t0 = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        const float2 t1 = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        if (SLAB) {
-          float2* p = G + r4 * NC * Kx + j;
-          p[0] = t0;
-          p[Kx] = t1;
-        } else {
-          To[j] = t0;
-          To[Kx + j] = t1;
-        }
-      }
-    }
-    __syncwarp();
-    if (SLAB) {
-      // the group's polarization coefficients out with 16-byte stores
-      __syncthreads();
-      float4* dst = reinterpret_cast<float4*>(a.Tout + slab_at(0, row - r4, 0, Kx));
-      const int n4 = Kx * kGroup * NC / 2;
-      for (int q = threadIdx.x; q < n4; q += blockDim.x) {
-        const int e = 2 * q, j = e / 12, m = e - 12 * j;
-        const float2 z0 = G[m * Kx + j], z1 = G[(m + 1) * Kx + j];
-        dst[q] = make_float4(z0.x, z0.y, z1.x, z1.y);
-      }
-      __syncthreads();   // before the next group overwrites the staging
-    }
-  }
+  for (int row = blockIdx.x * R + pair; row < a.rows; row += gridDim.x * R)
+    row_pass<PLASTIC, SLAB>(a, row, kxs, phs, G, SA, SB);
 }
 
 struct ColWArgs {
@@ -380,24 +390,28 @@ constexpr int kColRegion = kRegion + kN;   // a column warp's region: R (1056) a
 // buffer), the block stores its pieces for the next row pass and then writes its FP64 partial of
 // the measure (the last block takes the decision). INIT: only the inverse of the coefficients
 // held in ER (the start of a solve), no decision.
+// The column phase of the kx values j0 .. j0 + M - 1 (those below Kx) for the whole block: warps
+// 0 .. 3M - 1 carry the component columns (warp w: kx j0 + w / 3, component w % 3, region
+// R0 + w kColRegion); further warps of the block take part in the block-wide loops only. With
+// dep_wait the pattern's entry data are fetched before the dependency wait and the pass returns
+// false at once if the solve is done. Each thread's share of the convergence measure is added to
+// diff. The whole block calls it.
 template <int M, bool INIT>
-__global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd) {
+__device__ __forceinline__ bool col_pass(const ColWArgs& a, int j0, float2* R0, double Nd,
+                                         bool dep_wait, double& diff) {
   constexpr int NC = 3, kB = 4;   // entries per thread in flight
   constexpr int kSlab4 = kN * NC / 2;   // float4 of one kx: 256 row groups of 6
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[3 * M];
-  __shared__ double sh[32];
-  __shared__ bool last;
-  float2* R0 = reinterpret_cast<float2*>(smem);   // warp w's region at w kColRegion
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int j0 = blockIdx.x * M;
+  const bool active = w < 3 * M;   // a warp with a component column
   const int nj = min(M, a.Kx - j0);   // kx values of this block
   float2* R = R0 + w * kColRegion;
   float2* D = R + kRegion;
   const int e0 = a.jptr[j0], e1 = a.jptr[j0 + nj];
   const int eM = M == 2 ? a.jptr[j0 + 1] : e1;   // first entry of the second kx
+  if (active) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) D[lane + 32 * i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 32; ++i) D[lane + 32 * i] = make_float2(0.f, 0.f);
+  }
   // the pattern's entry data (fixed with the pattern): the first kB entries of this thread are
   // fetched before the dependency wait
   int2 en[kB];
@@ -419,10 +433,13 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
     }
   };
   fetch(e0 + threadIdx.x);
-  grid_dep_wait();
-  if (!INIT && a.done && __ldcg(a.done)) return;   // the same flag value for every thread
+  if (dep_wait) {
+    grid_dep_wait();
+    if (!INIT && a.done && __ldcg(a.done)) return false;   // the same value for every thread
+  } else {
+    __syncthreads();   // the zeroed spectra D before any thread scatters into them
+  }
   float2 v[32];
-  double diff = 0.0;
   if (!INIT) {
     // the block's kx in every row group: 96 contiguous bytes (six float4) per group; float4 k
     // of group g holds the entries 2k, 2k + 1 of [4][NC], i.e. (y - 4 g, c) = divmod(., NC)
@@ -449,12 +466,14 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
       }
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = R[lane + 32 * i];
-    __syncwarp();
-    fwd1024(v, R, a.table, lane);
+      for (int i = 0; i < 32; ++i) v[i] = R[lane + 32 * i];
+      __syncwarp();
+      fwd1024(v, R, a.table, lane);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) R[lane + 32 * i] = v[i];
+      for (int i = 0; i < 32; ++i) R[lane + 32 * i] = v[i];
+    }
     __syncthreads();
   }
   // Green operator at the block's pattern entries (INIT: the held coefficients), kB per thread
@@ -518,14 +537,16 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
   // inverse along y as the conjugate of the forward transform of the conjugate; the column back
   // to R, then the block's pieces out with 16-byte stores; the convergence decision after them
   // (it only gates the next update), so the last block's decision is all that trails the stores
+  if (active) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    v[i] = D[lane + 32 * i];
-    v[i].y = -v[i].y;
+    for (int i = 0; i < 32; ++i) {
+      v[i] = D[lane + 32 * i];
+      v[i].y = -v[i].y;
+    }
+    fwd1024(v, R, a.table, lane);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) R[lane + 32 * i] = make_float2(v[i].x, -v[i].y);
   }
-  fwd1024(v, R, a.table, lane);
-#pragma unroll
-  for (int i = 0; i < 32; ++i) R[lane + 32 * i] = make_float2(v[i].x, -v[i].y);
   __syncthreads();
   float4* dst = reinterpret_cast<float4*>(a.T1);
   for (int q = threadIdx.x; q < nj * kSlab4; q += blockDim.x) {
@@ -536,26 +557,40 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
     const float2 z1 = R0[(jj * NC + c1) * kColRegion + y1];
     dst[((long long)g * a.Kx + j0 + jj) * 6 + (r - 6 * g)] = make_float4(z0.x, z0.y, z1.x, z1.y);
   }
-  if (INIT) return;
+  return true;
+}
+
+template <int M, bool INIT>
+__global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[3 * M];
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double diff = 0.0;
+  if (!col_pass<M, INIT>(a, blockIdx.x * M, reinterpret_cast<float2*>(smem), Nd, true, diff))
+    return;
+  if constexpr (!INIT) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
-  if (lane == 0) red[w] = diff;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 3 * M; ++i) t += red[i];
-    a.part[blockIdx.x] = t;
-    __threadfence();
-    last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    decide(a.part, gridDim.x, a.st, sh);
+    for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+    if (lane == 0) red[w] = diff;
+    __syncthreads();
     if (threadIdx.x == 0) {
-      *a.counter = 0u;
-      // the only call site of the loop condition in this mode: one thread of one block
-      if (a.use_cond && a.st->done) cudaGraphSetConditional(a.cond, 0u);
+      double t = 0.0;
+      for (int i = 0; i < 3 * M; ++i) t += red[i];
+      a.part[blockIdx.x] = t;
+      __threadfence();
+      last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      decide(a.part, gridDim.x, a.st, sh);
+      if (threadIdx.x == 0) {
+        *a.counter = 0u;
+        // the only call site of the loop condition in this mode: one thread of one block
+        if (a.use_cond && a.st->done) cudaGraphSetConditional(a.cond, 0u);
+      }
     }
   }
 }
