@@ -60,10 +60,11 @@ def parse():
                    help="c2 FFT mode: row-kernel blocks with the rows spread evenly (0: autotuned)")
     p.add_argument("--fft-cols", type=int, default=0,
                    help="c2 FFT mode: columns per column-kernel block (0: autotuned)")
-    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4],
+    p.add_argument("--fft-fuse", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4, 5],
                    help="c2 FFT mode column phase: three kernels (-1), one fused kernel (1), "
                         "Green operator inside the inverse y kernel (2), the persistent solve "
-                        "(3), the warp-FFT column kernel (4), or timed (0)")
+                        "(3), the warp-FFT column kernel (4), the persistent solve on the "
+                        "warp-FFT passes (5), or timed (0)")
     p.add_argument("--fft-fuse-kx", type=int, default=0,
                    help="c2 FFT mode: kx columns per fused column block (0: autotuned)")
     p.add_argument("--fft-row-warps", type=int, default=0, choices=[-1, 0, 2, 4, 8],
@@ -819,6 +820,11 @@ def main():
         kernel_names[("fft", "row")] = "k_fft_row_w"
     if tile_info and tile_info.get("fft_fused") == 4:
         kernel_names[("fft", "column_phase")] = "k_fft_colphase_w"
+    if tile_info and tile_info.get("fft_fused") == 5:
+        # the persistent solve on the warp-FFT passes: its row and column phases, each timed up
+        # to its grid barrier by global-timer stamps of block 0
+        kernel_names[("fft", "row")] = "k_persist_w (row phase)"
+        kernel_names[("fft", "column_phase")] = "k_persist_w (column phase)"
     if tile_info and tile_info.get("fft_fused") == 3:
         # the persistent solve: one kernel; its stages are the row and the column phase, each
         # timed up to its grid barrier by global-timer stamps of block 0

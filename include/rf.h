@@ -124,12 +124,14 @@ typedef struct rf_phase {
  *             grid barrier, column phase per kx, grid barrier, decision) with the grid
  *             co-resident (one or two blocks per SM); 4 (Ny = 1024) as 1 on the warp-FFT
  *             column kernel: a warp per line column, the 1024-point transforms along y in
- *             registers (four-step 32 x 32); 0 = chosen by timing when the pattern is set (the
- *             persistent solve only when fft_rows and fft_row_blocks are 0; mode 4 where
- *             Ny = 1024). Must be 0 or -1 in 3D. All give the same update up to the order of
- *             FP32 and FP64 summation.
+ *             registers (four-step 32 x 32); 5 (1024 x 1024) the persistent solve on the
+ *             passes of mode 4 (one cooperative launch per solve, grid barriers between the
+ *             passes); 0 = chosen by timing when the pattern is set (the persistent solves only
+ *             when fft_rows and fft_row_blocks are 0; modes 4 and 5 on 1024 x 1024 grids). Must
+ *             be 0 or -1 in 3D. All give the same update up to the order of FP32 and FP64
+ *             summation.
  *  fft_fuse_kx  kx columns per block of the fused kernel (0 = chosen by timing; 1..16; 1 or 2
- *             in mode 4).
+ *             in mode 4; mode 5 uses 2).
  *  fft_row_blocks  FFT mode: run the row kernel on this many blocks with the grid rows spread
  *             evenly (blocks differ by at most one row; clamped to the row count), instead of
  *             tiles of fft_rows; 0 = fft_rows or the autotuner (which also times such
@@ -146,7 +148,7 @@ typedef struct rf_phase {
  *             autotuner compares it with the shared-memory row kernel (only when fft_rows and
  *             fft_row_blocks are 0); 2 or 4 = always, with that many warps (one or two rows) per
  *             block; 8 = four rows per block on row-group slabs, the form that goes with
- *             fft_fuse 4 (and only with it; 0 there means 8); -1 = never. Ignored where it does
+ *             fft_fuse 4 and 5 (and only with them; 0 there means 8); -1 = never. Ignored where it does
  *             not apply; the same update either way up to FP32 rounding order. */
 typedef struct rf_options {
   double tol;
@@ -180,7 +182,7 @@ typedef struct rf_info {
   int32_t fft_row_threads;/* FFT mode: threads per row-kernel block, else 0 */
   int32_t fft_cols;       /* FFT mode: columns per column-kernel block, else 0 */
   int32_t fft_col_threads;/* FFT mode: threads per column-kernel block, else 0 */
-  int32_t fft_fused;      /* column-phase mode in use (see fft_fuse): 0 to 4 */
+  int32_t fft_fused;      /* column-phase mode in use (see fft_fuse): 0 to 5 */
   int32_t fft_fuse_kx;    /* kx columns per fused block, else 0 */
   int32_t fft_fuse_threads;/* threads per fused block, else 0 */
   int32_t fft_row_blocks; /* FFT mode: row-kernel blocks (fft_rows is the largest block's row

@@ -380,7 +380,10 @@ int run_persistent(rf_ctx* c) {
   const int cap = c->tracing ? std::min(c->opt.max_iter, 8192) : 0;
   if (cap > 0)
     if (int e = palloc(c, &c->d_ptrace, 3 * (size_t)cap, "trace")) return e;
-  if (int e = launch_persist_solve(c, cap > 0 ? c->d_ptrace : nullptr, cap)) return e;
+  unsigned long long* tr = cap > 0 ? c->d_ptrace : nullptr;
+  if (int e = c->fft_colmode == kColPersistW ? launch_persist_warp(c, tr, cap)
+                                             : launch_persist_solve(c, tr, cap))
+    return e;
   if (int e = ck(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status), cudaMemcpyDeviceToHost,
                                  c->stream), "read status"))
     return e;
@@ -407,7 +410,7 @@ int run_persistent(rf_ctx* c) {
 int run_iterations(rf_ctx* c) {
   const int maxchunk = c->opt.check_every > 0 ? c->opt.check_every : 32;
   int chunk = std::min(4, maxchunk);
-  const bool persistent = c->fft_colmode == kColPersistent;
+  const bool persistent = c->fft_colmode == kColPersistent || c->fft_colmode == kColPersistW;
   if (!persistent && c->fft_colmode != kColSeparate) {
     // these updates end with the inverse transform along y of their new coefficients, so the
     // first one needs the line transforms of the start coefficients
@@ -558,16 +561,20 @@ int rf_create(rf_ctx** out, const rf_grid* grid, int32_t n_phases, const rf_phas
   if (opt->fft_row_warps != -1 && opt->fft_row_warps != 0 && opt->fft_row_warps != 2 &&
       opt->fft_row_warps != 4 && opt->fft_row_warps != 8)
     return invalid("options: fft_row_warps -1, 0, 2, 4 or 8");
-  if ((opt->fft_row_warps == 8) != (opt->fft_fuse == 4) && opt->fft_row_warps != 0)
-    return invalid("options: fft_row_warps 8 goes with fft_fuse 4 and only with it");
+  if ((opt->fft_row_warps == 8) != (opt->fft_fuse == 4 || opt->fft_fuse == 5) &&
+      opt->fft_row_warps != 0)
+    return invalid("options: fft_row_warps 8 goes with fft_fuse 4 or 5 and only with them");
   if (opt->wait_limit < 0 || (opt->stall_test != 0 && opt->stall_test != 1))
     return invalid("options: wait_limit >= 0, stall_test 0 or 1");
   if (opt->stall_test && opt->precision == RF_PREC_FP32)
     return invalid("options: stall_test applies to the split-precision modes only");
-  if (opt->fft_fuse < -1 || opt->fft_fuse > 4 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
-    return invalid("options: fft_fuse in {-1, 0, 1, 2, 3, 4}, fft_fuse_kx in [0, 16]");
+  if (opt->fft_fuse < -1 || opt->fft_fuse > 5 || opt->fft_fuse_kx < 0 || opt->fft_fuse_kx > 16)
+    return invalid("options: fft_fuse in {-1, 0, 1, 2, 3, 4, 5}, fft_fuse_kx in [0, 16]");
   if (opt->fft_fuse >= 1 && (opt->transform != RF_TRANSFORM_FFT || grid->dim != 2))
-    return invalid("options: fft_fuse 1 to 4 needs the FFT transform on a 2D grid");
+    return invalid("options: fft_fuse 1 to 5 needs the FFT transform on a 2D grid");
+  if (opt->fft_fuse == 5 && (grid->n[0] != 1024 || grid->n[1] != 1024 ||
+                             (opt->fft_row_warps != 0 && opt->fft_row_warps != 8)))
+    return invalid("options: fft_fuse 5 needs a 1024 x 1024 grid and the warp-FFT row kernel");
   if (opt->fft_fuse == 4 && (grid->n[0] != 1024 || grid->n[1] != 1024 || opt->fft_fuse_kx > 2 ||
                              (opt->fft_row_warps != 0 && opt->fft_row_warps != 8)))
     return invalid("options: fft_fuse 4 needs a 1024 x 1024 grid, fft_fuse_kx 0, 1 or 2 and "
@@ -1241,7 +1248,8 @@ int rf_get_info(const rf_ctx* c, rf_info* info) {
   info->fft_col_threads = fft ? c->fft_col_threads : 0;
   info->fft_fused = c->fft_colmode;
   info->fft_fuse_kx = c->fft_colmode == kColFused ? c->fft_M
-                      : c->fft_colmode == kColWarp ? c->fft_colw_M : 0;
+                      : (c->fft_colmode == kColWarp || c->fft_colmode == kColPersistW)
+                          ? c->fft_colw_M : 0;
   info->fft_fuse_threads = c->fft_colmode == kColFused ? c->fft_M_threads : 0;
   info->fft_row_blocks = fft ? c->fft_blocks : 0;
   if (c->fft_colmode == kColPersistent) {

@@ -776,6 +776,14 @@ int fft_geometry(rf_ctx* c) {
       c->fft_colmode = kColWarp;
       c->fft_colw_M = c->opt.fft_fuse_kx > 0 ? c->opt.fft_fuse_kx : 1;
       c->fft_row_warps = 8;   // the row-group slab row kernel
+    } else if (c->opt.fft_fuse == 5) {
+      if (c->nx != 1024 || c->ny != 1024 || c->nc != 3) {
+        set_error("FFT mode: the persistent warp-FFT solve needs a 1024 x 1024 grid in 2D");
+        return RF_ERR_INVALID;
+      }
+      c->fft_colmode = kColPersistW;
+      c->fft_colw_M = 2;
+      c->fft_row_warps = 8;
     }
   }
   return RF_OK;
@@ -974,7 +982,7 @@ int fft_autotune(rf_ctx* c) {
   const bool rows_pinned = c->opt.fft_rows > 0 || c->opt.fft_row_blocks > 0;
   // the warp-FFT row kernel: compared with the shared-memory row kernel's best tile (the
   // warp-FFT column phase fixes it to its row-group slab form)
-  const bool warp_need = c->fft_colmode == kColWarp;
+  const bool warp_need = c->fft_colmode == kColWarp || c->fft_colmode == kColPersistW;
   const bool warp_auto = !rows_pinned && c->opt.fft_row_warps == 0 && row_warp_ok(c) && !warp_need;
   // the persistent solve: compared with the other modes (fft_fuse 0, unless the row kernel's
   // tiles are pinned) or only its geometry chosen (fft_fuse 3); needs the barrier words set up
@@ -1281,6 +1289,56 @@ int fft_autotune(rf_ctx* c) {
       err = RF_ERR_CUDA;
     } else {
       c->fft_colmode = mode_np;
+    }
+  }
+  if (!err && colw_auto && persist_warp_ok(c)) {
+    // the persistent solve on the warp-FFT passes against the mode chosen so far, per update
+    auto time_persist = [&](int mode, float* per_update) -> int {
+      constexpr int kUpd = 8;
+      Status& hs = *c->h_status;
+      std::memset(&hs, 0, sizeof(Status));
+      hs.max_iter = kUpd;
+      hs.tol = 0.0;
+      hs.enorm = 1.0;
+      hs.inv_n2 = 1.0 / ((double)c->N * (double)c->N);
+      hs.rmin = HUGE_VAL;
+      hs.lam0 = c->lam0;
+      hs.mu0 = c->mu0;
+      float ms = 1e30f;
+      const int e = time_it([&] {
+        if (int e2 = tck(cudaMemcpyAsync(c->d_status, c->h_status, sizeof(Status),
+                                         cudaMemcpyHostToDevice, c->stream), "tuner"))
+          return e2;
+        return mode == kColPersistW ? launch_persist_warp(c, nullptr, 0)
+                                    : launch_persist_solve(c, nullptr, 0);
+      }, &ms);
+      *per_update = ms / (3.f * kUpd);
+      return e;
+    };
+    const int keep_mode = c->fft_colmode, keep_w = c->fft_row_warps, keep_M = c->fft_colw_M;
+    float t_cur = 1e30f;
+    if (keep_mode == kColPersistent) {
+      err = time_persist(kColPersistent, &t_cur);
+    } else {
+      err = time_it([&] { return run_update(keep_mode); }, &t_cur);
+      t_cur /= 3.f;
+    }
+    float t_pw = 1e30f;
+    if (!err) {
+      c->fft_colmode = kColPersistW;
+      c->fft_row_warps = 8;
+      c->fft_colw_M = 2;
+      const int e = time_persist(kColPersistW, &t_pw);
+      if (e) {   // a launch the device refuses (co-residency) is not a candidate
+        cudaGetLastError();
+        set_error("");
+        t_pw = 1e30f;
+      }
+    }
+    if (err || !(t_pw < t_cur)) {
+      c->fft_colmode = keep_mode;
+      c->fft_row_warps = keep_w;
+      c->fft_colw_M = keep_M;
     }
   }
   cudaEventDestroy(e0);

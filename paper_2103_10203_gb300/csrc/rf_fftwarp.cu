@@ -167,7 +167,7 @@ __device__ __forceinline__ void row_pass(const RowWArgs& a, int row, const int* 
       float4 t[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (q0 + u * (int)blockDim.x < n4) t[u] = src[q0 + u * blockDim.x];
+        if (q0 + u * (int)blockDim.x < n4) t[u] = __ldcg(src + q0 + u * blockDim.x);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = q0 + u * blockDim.x;
@@ -392,14 +392,15 @@ constexpr int kColRegion = kRegion + kN;   // a column warp's region: R (1056) a
 // held in ER (the start of a solve), no decision.
 // The column phase of the kx values j0 .. j0 + M - 1 (those below Kx) for the whole block: warps
 // 0 .. 3M - 1 carry the component columns (warp w: kx j0 + w / 3, component w % 3, region
-// R0 + w kColRegion); further warps of the block take part in the block-wide loops only. With
-// dep_wait the pattern's entry data are fetched before the dependency wait and the pass returns
-// false at once if the solve is done. Each thread's share of the convergence measure is added to
-// diff. The whole block calls it.
-template <int M, bool INIT>
+// R0 + w kColRegion); further warps of the block take part in the block-wide loops only. WAIT:
+// the pattern's entry data are fetched before the dependency wait and the pass returns false at
+// once if the solve is done (else they are fetched just before the Green step). Each thread's
+// share of the convergence measure is added to diff. The whole block calls it.
+template <int M, bool INIT, bool WAIT, int kB = 4, int kL = 16>
 __device__ __forceinline__ bool col_pass(const ColWArgs& a, int j0, float2* R0, double Nd,
-                                         bool dep_wait, double& diff) {
-  constexpr int NC = 3, kB = 4;   // entries per thread in flight
+                                         double& diff) {
+  // kB entries and kL 16-byte slab loads per thread in flight
+  constexpr int NC = 3;
   constexpr int kSlab4 = kN * NC / 2;   // float4 of one kx: 256 row groups of 6
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const bool active = w < 3 * M;   // a warp with a component column
@@ -432,8 +433,8 @@ __device__ __forceinline__ bool col_pass(const ColWArgs& a, int j0, float2* R0, 
       if (e < e1) pos[u] = a.kym[en[u].x];
     }
   };
-  fetch(e0 + threadIdx.x);
-  if (dep_wait) {
+  if constexpr (WAIT) {
+    fetch(e0 + threadIdx.x);
     grid_dep_wait();
     if (!INIT && a.done && __ldcg(a.done)) return false;   // the same value for every thread
   } else {
@@ -444,18 +445,18 @@ __device__ __forceinline__ bool col_pass(const ColWArgs& a, int j0, float2* R0, 
     // the block's kx in every row group: 96 contiguous bytes (six float4) per group; float4 k
     // of group g holds the entries 2k, 2k + 1 of [4][NC], i.e. (y - 4 g, c) = divmod(., NC)
     const float4* src = reinterpret_cast<const float4*>(a.T1p);
-    for (int q0 = threadIdx.x; q0 < nj * kSlab4; q0 += 16 * blockDim.x) {
-      float4 t[16];
+    for (int q0 = threadIdx.x; q0 < nj * kSlab4; q0 += kL * blockDim.x) {
+      float4 t[kL];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
+      for (int u = 0; u < kL; ++u) {
         const int q = q0 + u * blockDim.x;
         if (q < nj * kSlab4) {
           const int jj = q >= kSlab4 ? 1 : 0, r = q - jj * kSlab4, g = r / 6;
-          t[u] = src[((long long)g * a.Kx + j0 + jj) * 6 + (r - 6 * g)];
+          t[u] = __ldcg(src + ((long long)g * a.Kx + j0 + jj) * 6 + (r - 6 * g));
         }
       }
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
+      for (int u = 0; u < kL; ++u) {
         const int q = q0 + u * blockDim.x;
         if (q >= nj * kSlab4) continue;
         const int jj = q >= kSlab4 ? 1 : 0, r = q - jj * kSlab4, g = r / 6, e = 2 * (r - 6 * g);
@@ -481,7 +482,7 @@ __device__ __forceinline__ bool col_pass(const ColWArgs& a, int j0, float2* R0, 
   // the zero frequency under mixed control)
   for (int eb = e0 + threadIdx.x; eb < e1; eb += kB * blockDim.x) {
     float2 old[kB][NC];
-    if (eb != e0 + (int)threadIdx.x) fetch(eb);
+    if (!WAIT || eb != e0 + (int)threadIdx.x) fetch(eb);
 #pragma unroll
     for (int u = 0; u < kB; ++u) {
       const int e = eb + u * blockDim.x;
@@ -489,7 +490,7 @@ __device__ __forceinline__ bool col_pass(const ColWArgs& a, int j0, float2* R0, 
         const int je = (M == 2 && e >= eM) ? 1 : 0;
         const long long base = ((long long)en[u].x * NC) * a.Kx + j0 + je;
 #pragma unroll
-        for (int cc = 0; cc < NC; ++cc) old[u][cc] = a.ER[base + (long long)cc * a.Kx];
+        for (int cc = 0; cc < NC; ++cc) old[u][cc] = __ldcg(a.ER + base + (long long)cc * a.Kx);
       }
     }
 #pragma unroll
@@ -568,7 +569,7 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
   __shared__ bool last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double diff = 0.0;
-  if (!col_pass<M, INIT>(a, blockIdx.x * M, reinterpret_cast<float2*>(smem), Nd, true, diff))
+  if (!col_pass<M, INIT, true>(a, blockIdx.x * M, reinterpret_cast<float2*>(smem), Nd, diff))
     return;
   if constexpr (!INIT) {
 #pragma unroll
@@ -595,11 +596,164 @@ __global__ __launch_bounds__(96 * M) void k_fft_colphase_w(ColWArgs a, double Nd
   }
 }
 
+// ---- persistent solve on the warp-FFT kernels (one cooperative launch per solve)
+
+struct PersistWArgs {
+  RowWArgs row;          // T = T1, Tout = T1p (row-group slabs), no done flag
+  ColWArgs col;          // T1p -> T1, status and partials, no done flag
+  unsigned* bar;         // [2] arrival count, generation
+  long bar_limit;        // polls per barrier wait
+  double Nd;
+  int n_groups;          // row groups of four rows
+  int n_col;             // column items of two kx
+  unsigned long long* trace;   // nullable: [trace_cap][3] global-timer stamps per update
+  int trace_cap;
+};
+
+__device__ __forceinline__ unsigned pw_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long pw_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier over the whole co-resident grid (arrival count and generation word); false if the
+// wait ran out after `limit` polls.
+__device__ bool pw_grid_sync(unsigned* bar, long limit, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = pw_ld_acquire(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long it = 0;
+      while (pw_ld_acquire(bar + 1) == gen) {
+        if (++it > limit) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// Every update of a 2D 1024^2 solve in one cooperative launch of 256-thread blocks: the start's
+// inverse along y of the held coefficients, then per update the row pass over the row groups,
+// a grid barrier, the column pass over pairs of kx (writing one FP64 partial each), a grid
+// barrier, and the decision, which every block takes identically from the partials in a fixed
+// order (block 0 writes the status). The passes are the ones of the launch-per-phase kernels.
+template <bool PLASTIC>
+__global__ __launch_bounds__(256, 2) void k_persist_w(const __grid_constant__ PersistWArgs a) {
+  constexpr int NC = 3;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ DevPhase phs[kMaxPhases];
+  __shared__ double red[8];
+  __shared__ int s_flag, s_done, s_iters;
+  __shared__ double s_rmin;
+  __shared__ unsigned long long s_tupd, s_trow;
+  const int Kx = a.row.Kx, tid = threadIdx.x, pair = tid >> 6;
+  int* kxs = reinterpret_cast<int*>(smem);
+  float2* base = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15));
+  float2* G = base;                                   // row pass: staged group
+  float2* SA = base + (size_t)Kx * kGroup * NC + (size_t)pair * kPairRegion;
+  float2* SB = SA + kRegion;
+  for (int i = tid; i < Kx; i += blockDim.x) kxs[i] = a.row.kx[i];
+  for (int i = tid; i < kMaxPhases; i += blockDim.x) phs[i] = a.row.law.ph[i];
+  if (tid == 0) {
+    s_iters = a.col.st->iters;
+    s_rmin = a.col.st->rmin;
+  }
+  __syncthreads();
+  double d0 = 0.0;
+  for (int p = blockIdx.x; p < a.n_col; p += gridDim.x) {
+    col_pass<2, true, false, 1, 4>(a.col, 2 * p, base, a.Nd, d0);
+    __syncthreads();
+  }
+  if (!pw_grid_sync(a.bar, a.bar_limit, &s_flag)) {
+    if (tid == 0) atomicExch(&a.col.st->timeout, 1);
+    return;
+  }
+  if (a.trace && blockIdx.x == 0 && tid == 0) s_tupd = pw_now();
+  for (int u = 0;; ++u) {
+    for (int g = blockIdx.x; g < a.n_groups; g += gridDim.x)
+      row_pass<PLASTIC, true>(a.row, kGroup * g + pair, kxs, phs, G, SA, SB);
+    if (!pw_grid_sync(a.bar, a.bar_limit, &s_flag)) {
+      if (tid == 0) atomicExch(&a.col.st->timeout, 1);
+      return;
+    }
+    if (a.trace && blockIdx.x == 0 && tid == 0) s_trow = pw_now();
+    for (int p = blockIdx.x; p < a.n_col; p += gridDim.x) {
+      double diff = 0.0;
+      col_pass<2, false, false, 1, 4>(a.col, 2 * p, base, a.Nd, diff);
+      const double t = block_sum_d(diff, red);
+      if (tid == 0) a.col.part[p] = t;
+    }
+    if (!pw_grid_sync(a.bar, a.bar_limit, &s_flag)) {
+      if (tid == 0) atomicExch(&a.col.st->timeout, 1);
+      return;
+    }
+    // decision from the partials in a fixed order, the same in every block
+    double s = 0.0;
+    for (int i = tid; i < a.n_col; i += blockDim.x) s += __ldcg(a.col.part + i);
+    s = block_sum_d(s, red);
+    if (tid == 0) {
+      // tol, enorm, inv_n2 and max_iter are set by the host before the launch
+      Status* st = a.col.st;
+      double r = sqrt(s * st->inv_n2);
+      if (st->enorm > 0.0) r /= st->enorm;
+      const int iters = s_iters + 1;
+      const double rmin = fmin(s_rmin, r);
+      s_iters = iters;
+      s_rmin = rmin;
+      int done = 0, nonfinite = 0, diverged = 0;
+      if (!isfinite(r)) {
+        nonfinite = done = 1;
+      } else if (r > kDivergeRatio * rmin && r > kDivergeFloor) {
+        diverged = done = 1;
+      } else if (r < st->tol || iters >= st->max_iter) {
+        done = 1;
+      }
+      if (blockIdx.x == 0) {
+        st->iters = iters;
+        st->last_r = r;
+        st->rmin = rmin;
+        st->nonfinite = nonfinite;
+        st->diverged = diverged;
+        st->done = done;
+        if (a.trace && u < a.trace_cap) {
+          const unsigned long long t_col = pw_now();
+          a.trace[3 * u] = s_tupd;
+          a.trace[3 * u + 1] = s_trow;
+          a.trace[3 * u + 2] = t_col;
+          s_tupd = t_col;
+        }
+      }
+      s_done = done;
+    }
+    __syncthreads();
+    if (s_done) break;
+  }
+}
+
 }  // namespace wfft
 
 // largest dynamic shared memory of the row kernel (two rows per block) and of the column
 // phase (two kx columns per block), set as the kernels' limits
-constexpr int kRowWSmemMax = 128 * 1024, kColWSmemMax = 112 * 1024;
+constexpr int kRowWSmemMax = 128 * 1024, kColWSmemMax = 112 * 1024, kPersistWSmemMax = 200 * 1024;
 
 size_t row_warp_smem(int Kx, int warps) {
   // warps = 8: the row-group slab kernel, with its group staged
@@ -636,6 +790,18 @@ static void set_roww_attributes() {
                        (int)cudaSharedmemCarveoutMaxShared);
 }
 
+// Shared memory of a persistent warp-FFT block: kx values, then the larger of the row pass's
+// (staged group and four pair regions) and the column pass's (six column regions)
+static size_t persist_w_smem(int Kx) {
+  const size_t row = (size_t)Kx * wfft::kGroup * 3 + 4 * (size_t)wfft::kPairRegion;
+  const size_t col = 6 * (size_t)wfft::kColRegion;
+  return (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15) + std::max(row, col) * sizeof(float2);
+}
+
+static const void* persist_w_kernel(bool pl) {
+  return pl ? (const void*)wfft::k_persist_w<true> : (const void*)wfft::k_persist_w<false>;
+}
+
 void init_attributes_fftwarp() {
   set_roww_attributes<true, 1, false>();
   set_roww_attributes<false, 1, false>();
@@ -647,6 +813,12 @@ void init_attributes_fftwarp() {
   set_colw_attributes<2, false>();
   set_colw_attributes<1, true>();
   set_colw_attributes<2, true>();
+  for (bool pl : {true, false}) {
+    cudaFuncSetAttribute(persist_w_kernel(pl), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kPersistWSmemMax);
+    cudaFuncSetAttribute(persist_w_kernel(pl), cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+  }
   cudaGetLastError();
 }
 
@@ -693,6 +865,79 @@ static int colw_launch(rf_ctx* c, const int* done, bool init) {
   if (e != cudaSuccess) return cuda_fail(e, "fft column phase (warp FFTs)");
   if (!init) trace_end(c);
   return RF_OK;
+}
+
+bool persist_warp_ok(const rf_ctx* c) {
+  if (!col_warp_ok(c) || !c->d_bar || c->rows % wfft::kGroup != 0) return false;
+  const size_t sm = persist_w_smem(c->Kx);
+  if (sm > (size_t)kPersistWSmemMax) return false;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, persist_w_kernel(c->has_plastic), 256,
+                                                    sm) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return occ >= 1;
+}
+
+// One cooperative launch: the start's inverse along y, then updates until the decision ends the
+// solve (the status on the device holds tol, max_iter and the normalisation).
+int launch_persist_warp(rf_ctx* c, unsigned long long* trace, int trace_cap) {
+  const size_t sm = persist_w_smem(c->Kx);
+  int sms = 152, occ = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+  const void* k = persist_w_kernel(c->has_plastic);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 256, sm) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    set_error("persistent warp-FFT solve: no co-resident grid for this pattern");
+    return RF_ERR_INVALID;
+  }
+  wfft::PersistWArgs a{};
+  wfft::RowWArgs& r = a.row;
+  r.T = c->d_T1;
+  r.Tout = c->d_T1p;
+  r.phase = c->d_phase;
+  r.state = c->d_state;
+  r.kx = c->d_kx;
+  r.table = c->d_twx;
+  r.Kx = c->Kx;
+  r.rows = c->rows;
+  r.N = c->N;
+  r.invN = (float)(1.0 / (double)c->N);
+  r.law = c->law;
+  r.done = nullptr;
+  wfft::ColWArgs& q = a.col;
+  q.T1p = c->d_T1p;
+  q.T1 = c->d_T1;
+  q.ER = c->d_ER;
+  q.jptr = c->d_jptr;
+  q.jent = c->d_jent;
+  q.jn = c->d_jn;
+  q.kym = c->d_kym;
+  q.table = c->d_twy;
+  q.Kx = c->Kx;
+  q.inv2mu0 = (float)(0.5 / c->mu0);
+  q.cgam = (float)((c->lam0 + c->mu0) / (c->mu0 * (c->lam0 + 2.0 * c->mu0)));
+  q.st = c->d_status;
+  q.counter = c->d_counter;
+  q.part = c->d_part;
+  q.done = nullptr;
+  q.use_cond = 0;
+  a.bar = c->d_bar;
+  a.bar_limit = 1L << 26;
+  a.Nd = (double)c->N;
+  a.n_groups = c->rows / wfft::kGroup;
+  a.n_col = (c->Kx + 1) / 2;
+  a.trace = trace;
+  a.trace_cap = trace_cap;
+  cudaError_t e = cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) {
+    void* args[] = {&a};
+    e = cudaLaunchCooperativeKernel(k, dim3((unsigned)(std::min(occ, 2) * sms)), dim3(256), args,
+                                    sm, c->stream);
+  }
+  c->launches += 1;
+  return e == cudaSuccess ? RF_OK : cuda_fail(e, "persistent warp-FFT solve");
 }
 
 int launch_fft_colphase_warp(rf_ctx* c, const int* done) { return colw_launch(c, done, false); }

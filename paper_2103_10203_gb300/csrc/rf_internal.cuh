@@ -211,8 +211,9 @@ struct rf_ctx {
   // 2D column phase: 0 forward y, Green kernel, inverse y; 1 one fused kernel per kx group
   // (kColFused); 2 forward y, then the Green operator inside the inverse y kernel
   // (kColGreenInv); 4 as 1 with a warp per line column, the transforms in registers and the
-  // line coefficients in kx slabs (kColWarp, 1024 x 1024, warp-FFT row kernel). Modes 1, 2 and
-  // 4 start a solve with one inverse y of the start coefficients.
+  // line coefficients in kx slabs (kColWarp, 1024 x 1024, warp-FFT row kernel); 5 the
+  // persistent solve on the same passes (kColPersistW). Modes 1, 2 and 4 start a solve with one
+  // inverse y of the start coefficients (3 and 5 inside their launch).
   int fft_colmode = 0;
   int fft_M = 1, fft_M_threads = 256;   // kx columns and threads per fused block
   // persistent 2D solve (column mode kColPersistent): grid, block size, dynamic shared memory,
@@ -436,7 +437,7 @@ int launch_tc_axis(rf_ctx* c, const TcAxis& ax, const float2* in, int in_splits,
 int launch_fft_green_inv(rf_ctx* c, const int* done);
 int launch_gather_jentries(rf_ctx* c);
 constexpr int kColSeparate = 0, kColFused = 1, kColGreenInv = 2, kColPersistent = 3,
-              kColWarp = 4;
+              kColWarp = 4, kColPersistW = 5;
 // rf_persist.cu
 bool persist_geometry(rf_ctx* c, int threads, int per_sm);
 int launch_persist_solve(rf_ctx* c, unsigned long long* trace, int trace_cap);
@@ -465,6 +466,10 @@ int launch_fft_row_warp(rf_ctx* c, const int* done);
 bool col_warp_ok(const rf_ctx* c);
 int launch_fft_colphase_warp(rf_ctx* c, const int* done);
 int launch_fft_coly_init_warp(rf_ctx* c);
+// the persistent solve on the warp-FFT passes (column mode kColPersistW): applicability (1024^2,
+// barrier words, a co-resident grid) and one cooperative launch per solve
+bool persist_warp_ok(const rf_ctx* c);
+int launch_persist_warp(rf_ctx* c, unsigned long long* trace, int trace_cap);
 // pattern.cu
 int pattern_adapted(const rf_grid* g, const uint8_t* pm, int incl, long long k_target,
                     int32_t* out, long long cap, long long* K_out, cudaStream_t s);

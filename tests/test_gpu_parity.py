@@ -653,23 +653,26 @@ def _square_1024(name):
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name,kx", [("c2_j2", 1), ("c2_j2", 2), ("full_elastic", 2),
-                                     ("adapted_elastic", 1)])
-def test_fft_warp_column_phase_matches_oracle(lib, name, kx):
+@pytest.mark.parametrize("name,fuse,kx", [("c2_j2", 4, 1), ("c2_j2", 4, 2), ("full_elastic", 4, 2),
+                                          ("adapted_elastic", 4, 1), ("c2_j2", 5, 0),
+                                          ("full_elastic", 5, 0)])
+def test_fft_warp_column_phase_matches_oracle(lib, name, fuse, kx):
     """fft_fuse 4 on 1024 x 1024 grids: the warp-FFT row kernel and the warp-FFT column phase
     (a warp per line column, the 1024-point transforms along y in registers, Green operator and
-    decision in the same kernel) exchanging line coefficients in kx slabs, `kx` kx columns per
-    block; three updates against the oracle at the FP32 parity tolerances, reduced coefficients
+    decision in the same kernel) exchanging line coefficients in row-group slabs, `kx` kx
+    columns per block; fft_fuse 5: the same passes in one persistent cooperative launch per
+    solve (grid barriers between them, two kx per column item, the decision in every block).
+    Three updates against the oracle at the FP32 parity tolerances, reduced coefficients
     included."""
     pm, ph, macro, pat = _square_1024(name)
-    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft", fft_fuse=4,
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft", fft_fuse=fuse,
                    fft_fuse_kx=kx)
     out = s.rf_solve(macro)
     eps, sig, _ = s.rf_get_fields()
     coeffs = s.rf_get_reduced_strain()
     info = s.rf_get_info()
     s.close()
-    assert info["fft_fused"] == 4 and info["fft_fuse_kx"] == kx and out["iters"] == 3
+    assert info["fft_fused"] == fuse and info["fft_fuse_kx"] == (kx or 2) and out["iters"] == 3
     assert info["fft_row_warps"] == 8                   # the row-group slab row kernel
     r = O.solve(pm, ph, macro, pat, tol=0.0, max_iter=3)
     assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
@@ -681,38 +684,48 @@ def test_fft_warp_column_phase_matches_oracle(lib, name, kx):
 
 def test_fft_warp_column_phase_load_path_mixed_control_and_options(lib):
     """The 1024^2 J2 composite: a load path to the tolerance and a mixed stress/strain solve in
-    the warp-FFT column mode take the three-kernel mode's decisions (update counts within one:
-    FP64 sums in another order) and reach its answers; options outside the mode's range are
-    rejected (kx columns per block, the shared-memory row kernel, grids other than 1024^2)."""
+    the warp-FFT column mode and in its persistent form take the three-kernel mode's decisions
+    (update counts within one: FP64 sums in another order) and reach its answers; the traced
+    persistent solve stamps every update; options outside the modes' range are rejected (kx
+    columns per block, the shared-memory row kernel, grids other than 1024^2)."""
     pm, ph, _, pat = _square_1024("c2_j2")
     path = uniaxial_path(20, 0.02)[[4, 9, 14]]
     control = np.array([1, 0, 0, 0, 0, 1], np.int32)
     target = np.array([0.01, 0.0, 0.0, 0.0, 0.0, 0.0])
     res = {}
-    for fuse in (-1, 4):
+    for fuse in (-1, 4, 5):
         s = lib.Solver(pm, ph, pattern=pat, tol=1e-6, max_iter=3000, transform="fft",
                        fft_fuse=fuse)
+        s.rf_set_tracing(fuse == 5)
         p = s.rf_solve_path(path)
         e = s.rf_get_fields()[0]
+        st = s.rf_get_stage_times()
         s.rf_reset_path()
+        s.rf_set_tracing(False)
         m = s.rf_solve_mixed(control, target)
         res[fuse] = (p, e, m)
         s.close()
-    (a, ea, ma), (b, eb, mb) = res[-1], res[4]
-    assert a["converged"] and b["converged"]
-    assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
-    assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
-    assert rel(eb, ea) <= 2e-5
-    assert abs(ma["iters"] - mb["iters"]) <= 1
-    assert rel(mb["sigma_bar"], ma["sigma_bar"]) <= 1e-5
-    assert rel(mb["strain_bar"], ma["strain_bar"]) <= 1e-5
+        if fuse == 5:   # traced persistent solve: every update's row and column phases stamped
+            n = int(np.sum(p["iters"]))
+            assert st["row"][1] == n and st["column_phase"][1] == n and st["row"][0] > 0
+    a, ea, ma = res[-1]
+    for fuse in (4, 5):
+        b, eb, mb = res[fuse]
+        assert a["converged"] and b["converged"]
+        assert np.all(np.abs(a["iters"] - b["iters"]) <= 1)
+        assert rel(b["sigma_bar"][-1], a["sigma_bar"][-1]) <= 1e-5
+        assert rel(eb, ea) <= 2e-5
+        assert abs(ma["iters"] - mb["iters"]) <= 1
+        assert rel(mb["sigma_bar"], ma["sigma_bar"]) <= 1e-5
+        assert rel(mb["strain_bar"], ma["strain_bar"]) <= 1e-5
     for bad in (dict(fft_fuse=4, fft_fuse_kx=3), dict(fft_fuse=4, fft_row_warps=-1),
                 dict(fft_fuse=4, fft_row_warps=2), dict(fft_fuse=1, fft_row_warps=8),
-                dict(fft_fuse=5)):
+                dict(fft_fuse=5, fft_row_warps=4), dict(fft_fuse=6)):
         with pytest.raises(lib.RFError):
             lib.Solver(pm, ph, pattern=pat, transform="fft", **bad)
-    with pytest.raises(lib.RFError):
-        lib.Solver(np.zeros((1024, 512), np.uint8), ph, transform="fft", fft_fuse=4)
+    for fuse in (4, 5):
+        with pytest.raises(lib.RFError):
+            lib.Solver(np.zeros((1024, 512), np.uint8), ph, transform="fft", fft_fuse=fuse)
 
 
 def test_fft_warp_row_kernel_option(lib):
