@@ -148,8 +148,8 @@ typedef struct rf_phase {
  *             autotuner compares it with the shared-memory row kernel (only when fft_rows and
  *             fft_row_blocks are 0); 2 or 4 = always, with that many warps (one or two rows) per
  *             block; 8 = four rows per block on row-group slabs, the form that goes with
- *             fft_fuse 4 and 5 (and only with them; 0 there means 8); -1 = never. Ignored where it does
- *             not apply; the same update either way up to FP32 rounding order. */
+ *             fft_fuse 4 and 5 (and only with them; 0 there means 8); -1 = never. Ignored
+ *             where it does not apply; the same update either way up to FP32 rounding order. */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
