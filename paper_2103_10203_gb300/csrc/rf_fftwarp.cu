@@ -437,6 +437,9 @@ __device__ __forceinline__ bool col_pass(const ColWArgs& a, int j0, float2* R0, 
     fetch(e0 + threadIdx.x);
     grid_dep_wait();
     if (!INIT && a.done && __ldcg(a.done)) return false;   // the same value for every thread
+    // the zeroed spectra D before any thread scatters into them (the update's path meets the
+    // barrier after its slab loads, the start's has none of its own)
+    if (INIT) __syncthreads();
   } else {
     __syncthreads();   // the zeroed spectra D before any thread scatters into them
   }

@@ -682,6 +682,30 @@ def test_fft_warp_column_phase_matches_oracle(lib, name, fuse, kx):
     assert rel(coeffs[..., 0] + 1j * coeffs[..., 1], want) <= EPS_TOL
 
 
+@pytest.mark.parametrize("kx", [1, 2])
+def test_fft_warp_column_phase_is_deterministic(lib, kx):
+    """The 1024^2 J2 composite over three increments with commits in the warp-FFT column mode:
+    two runs in fresh contexts give bit-identical fields (no atomics touch the data; a missing
+    barrier between zeroing and scattering the start's spectra once made the start of each
+    increment depend on warp timing), and the strain field stays at the oracle's."""
+    cfg = make_config("c2")
+    pm, ph = cfg["phase_map"], cfg["phases"]
+    pat = lib.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size))
+    path = cfg["path"][[4, 9, 14]]
+    runs = []
+    for _ in range(2):
+        s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, transform="fft", fft_fuse=4,
+                       fft_fuse_kx=kx)
+        out = s.rf_solve_path(path)
+        runs.append((out["sigma_bar"], s.rf_get_fields()))
+        s.close()
+    (sa, (ea, ga, aa)), (sb, (eb, gb, ab)) = runs
+    assert np.array_equal(sa, sb) and np.array_equal(ea, eb) and np.array_equal(ga, gb)
+    assert np.array_equal(aa, ab)
+    _, _, r = O.solve_path(pm, ph, path, pat, fixed_iters=[3, 3, 3])
+    assert rel(ea, vec6_field(r.eps)) <= EPS_TOL
+
+
 def test_fft_warp_column_phase_load_path_mixed_control_and_options(lib):
     """The 1024^2 J2 composite: a load path to the tolerance and a mixed stress/strain solve in
     the warp-FFT column mode and in its persistent form take the three-kernel mode's decisions
