@@ -752,6 +752,42 @@ def test_fft_warp_column_phase_load_path_mixed_control_and_options(lib):
             lib.Solver(np.zeros((1024, 512), np.uint8), ph, transform="fft", fft_fuse=fuse)
 
 
+@pytest.mark.parametrize("fuse,rw", [(-1, 2), (4, 0), (5, 0)])
+def test_fft_warp_kernels_degenerate_cases(lib, fuse, rw):
+    """Degenerate cases in the warp-FFT modes: the zero frequency alone (the Voigt bound, one
+    update: Kx = 1 and one rectangle row), a homogeneous medium (converged after one update,
+    the measure zero up to FP32 rounding), and a pattern whose only kx are 0 and the
+    self-conjugate 512 (columns of every ky at both) against the oracle."""
+    shape = (1024, 1024) if fuse in (4, 5) else (4, 1024)
+    ph = elastic_phases()
+    pm = (np.random.default_rng(41).random(shape) < 0.3).astype(np.uint8)
+    macro = np.array([0.01, 0.003, 0, 0, 0, -0.002])
+    opts = dict(transform="fft", fft_fuse=fuse, fft_row_warps=rw)
+    s = lib.Solver(pm, ph, pattern=np.zeros((1, 3), np.int32), tol=1e-8, **opts)
+    out = s.rf_solve(macro)
+    s.close()
+    r = O.solve(pm, ph, macro, np.zeros((1, 3), np.int64), tol=1e-8)
+    assert out["iters"] == 1 and rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+    hom = np.zeros(shape, np.uint8)
+    s = lib.Solver(hom, phase_table([(40.0, 27.0, 0, 0, 0)]), pattern=O.pattern_adapted(hom, 1, 300),
+                   tol=1e-8, **opts)
+    out = s.rf_solve(macro)
+    s.close()
+    assert out["iters"] == 1 and out["residual"] <= 1e-12
+    ny = shape[0]
+    ky = np.arange(ny) - (ny - 1) // 2
+    pat = np.array([(kx, k, 0) for kx in (0, 512) for k in ky], np.int32)
+    s = lib.Solver(pm, ph, pattern=pat, tol=0.0, max_iter=3, **opts)
+    out = s.rf_solve(macro)
+    eps, _, _ = s.rf_get_fields()
+    info = s.rf_get_info()
+    s.close()
+    assert info["Kx"] == 2
+    r = O.solve(pm, ph, macro, pat.astype(np.int64), tol=0.0, max_iter=3)
+    assert rel(eps, vec6_field(r.eps)) <= EPS_TOL
+    assert rel(out["sigma_bar"], r.sigma_bar) <= SBAR_TOL
+
+
 def test_fft_warp_row_kernel_option(lib):
     """fft_row_warps: 2 and 4 force the warp-FFT row kernel where it applies (2D, rows of 1024)
     and are ignored elsewhere; -1 keeps the shared-memory row kernel; 8 (the row-group slab
