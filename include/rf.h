@@ -384,8 +384,10 @@ int rf_pattern_radial(const rf_grid* grid, int64_t k_target, int32_t* freqs_out,
  *  RVE converged, RF_NOT_CONVERGED otherwise, or a hard error (RF_ERR_NONFINITE for a
  *  non-finite macroscopic strain).
  *  rf_batch_info: kernels launched so far (graph replays included), the rows per row item
- *  chosen for each of the five size classes (rows_per_item: int32 [5], nullable), persistent
- *  grid size. */
+ *  chosen for each of the five size classes (rows_per_item: int32 [5], nullable: 1, 2, 4 or 8
+ *  for shared-memory FFT or DFT items; 85, 53, 42, 26 or 21 for the warp-FFT row items of rows
+ *  of 64, 96, 128, 192 or 256 voxels, which transform 32 / P packed line pairs of L = 32 P
+ *  points per warp in registers), persistent grid size. */
 typedef struct rf_batch rf_batch;
 int rf_batch_create(rf_batch** batch, int32_t n_rve, const rf_grid* grids,
                     const uint8_t* const* phase_maps, int32_t n_phases, const rf_phase* phases,

@@ -46,6 +46,8 @@ struct BDesc {
   int tab_x, tab_y;      // offsets into the twiddle buffer
   FastDiv dKx, dnx;      // division by Kx and Nx
   int fft;               // row items use FFTs along x (Nx = 2^b or 3 2^b), else the pruned DFT
+  int warp;              // row items use warp-resident FFTs (Nx in {64, 96, 128, 192, 256})
+  int pad_w;
   int fft_y, cy;         // y transforms by FFT over groups of cy line columns (Ny = 2^b, 3 2^b)
   long long zero_base;   // ER offset (within the RVE) of the zero frequency
   float lam0, mu0, inv2mu0, cgam;
@@ -355,6 +357,299 @@ __device__ void row_item_fft(const BArgs& a, int2 w, const BDesc& d, unsigned ch
     if ((sl & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
     To[(long long)sl * Kx + j] = out;
+  }
+}
+
+// ---- row items with warp-resident FFTs (rows of L = 32 P voxels, P in {2, 3, 4, 6, 8})
+//
+// A warp transforms S = 32 / P packed sequences (two real lines each) of length L at once: lane
+// n2 holds entries 32 n1 + n2 of sequence s in v[s P + n1]; a P-point DFT per sequence in
+// registers, the twiddle exp(sign 2 pi i k1 n2 / L), a transpose through a padded warp region
+// (row s P + k1 to lane s P + k1), and a 32-point DFT per lane: lane s P + k1 then holds entries
+// k1 + P k2 of sequence s's transform in v[k2]. The item's rows are staged in the warps'
+// regions between the transforms, and the law runs on every voxel of the item.
+
+constexpr int kWRegion = 32 * 33;   // a warp's region (entries): transposes and S sequences
+
+// P-point DFT of v[0 .. P) in natural order in and out, kernel exp(sign 2 pi i k n / P)
+template <int P>
+__device__ __forceinline__ void dft_small(float2* v, int sign) {
+  const float sg = sign < 0 ? -1.f : 1.f;
+  if constexpr (P == 2) {
+    const float2 a = v[0], b = v[1];
+    v[0] = make_float2(a.x + b.x, a.y + b.y);
+    v[1] = make_float2(a.x - b.x, a.y - b.y);
+  } else if constexpr (P == 3) {
+    // X1,2 = a - (b + c) / 2 +- i sign sqrt(3)/2 (b - c)
+    const float2 a = v[0], b = v[1], c = v[2];
+    const float2 t1 = make_float2(b.x + c.x, b.y + c.y);
+    const float2 t2 = make_float2(a.x - 0.5f * t1.x, a.y - 0.5f * t1.y);
+    const float h = 0.86602540378443865f * sg;
+    const float2 t3 = make_float2(h * (b.x - c.x), h * (b.y - c.y));
+    v[0] = make_float2(a.x + t1.x, a.y + t1.y);
+    v[1] = make_float2(t2.x - t3.y, t2.y + t3.x);
+    v[2] = make_float2(t2.x + t3.y, t2.y - t3.x);
+  } else if constexpr (P == 4) {
+    fftc::dft4(v[0], v[1], v[2], v[3], sign);
+  } else if constexpr (P == 6) {
+    // n = 3 n1 + n2, k = k1 + 2 k2: 2-point DFTs over n1, twiddles exp(sign 2 pi i n2 k1 / 6),
+    // 3-point DFTs over n2
+    float2 y0[3], y1[3];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) {
+      const float2 a = v[n2], b = v[3 + n2];
+      y0[n2] = make_float2(a.x + b.x, a.y + b.y);
+      y1[n2] = make_float2(a.x - b.x, a.y - b.y);
+    }
+    const float h = 0.86602540378443865f * sg;
+    y1[1] = fftc::cmul(y1[1], make_float2(0.5f, h));    // exp(sign i pi / 3)
+    y1[2] = fftc::cmul(y1[2], make_float2(-0.5f, h));   // exp(sign 2 i pi / 3)
+    dft_small<3>(y0, sign);
+    dft_small<3>(y1, sign);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+      v[2 * k2] = y0[k2];
+      v[2 * k2 + 1] = y1[k2];
+    }
+  } else {
+    static_assert(P == 8, "P");
+    float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    fftc::dft4(e[0], e[1], e[2], e[3], sign);
+    fftc::dft4(o[0], o[1], o[2], o[3], sign);
+    const float r = 0.70710678118654752f;
+    const float2 w[4] = {make_float2(1.f, 0.f), make_float2(r, sg * r), make_float2(0.f, sg),
+                         make_float2(-r, sg * r)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 t = k == 0 ? o[0] : fftc::cmul(o[k], w[k]);
+      v[k] = make_float2(e[k].x + t.x, e[k].y + t.y);
+      v[k + 4] = make_float2(e[k].x - t.x, e[k].y - t.y);
+    }
+  }
+}
+
+// 32-point DFT in registers (natural order in and out): even and odd samples through two
+// 16-point DFTs and a radix-2 step
+__device__ __forceinline__ void dft32_regs(float2* v, int sign) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    e[m] = v[2 * m];
+    o[m] = v[2 * m + 1];
+  }
+  fftc::dft16(e, sign);
+  fftc::dft16(o, sign);
+  const float c[9] = {1.f,
+                      0.98078528040323044912f,
+                      0.92387953251128675613f,
+                      0.83146961230254523708f,
+                      0.70710678118654752440f,
+                      0.55557023301960222474f,
+                      0.38268343236508977173f,
+                      0.19509032201612826785f,
+                      0.f};
+  const float sg = sign < 0 ? -1.f : 1.f;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int i = 4 * (q & 3) + (q >> 2);   // where the 16-point kernel leaves its output q
+    const float cs = q <= 8 ? c[q] : -c[16 - q];
+    const float sn = q <= 8 ? c[8 - q] : c[q - 8];
+    const float2 O = fftc::cmul(o[i], make_float2(cs, sg * sn));
+    v[q] = make_float2(e[i].x + O.x, e[i].y + O.y);
+    v[q + 16] = make_float2(e[i].x - O.x, e[i].y - O.y);
+  }
+}
+
+// Forward transforms (exp(-2 pi i k n / L), L = 32 P) of the S = 32 / P sequences a warp holds
+// (layout above); tab[t] = exp(+2 pi i t / L); T: the warp's region (32 rows of 33).
+template <int P>
+__device__ __forceinline__ void fwd_batch(float2* v, float2* T, const float2* __restrict__ tab,
+                                          int lane) {
+  constexpr int S = 32 / P;
+#pragma unroll
+  for (int s = 0; s < S; ++s) dft_small<P>(v + s * P, -1);
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int k1 = 1; k1 < P; ++k1) {
+      float2 w = __ldg(tab + k1 * lane);
+      w.y = -w.y;
+      v[s * P + k1] = fftc::cmul(v[s * P + k1], w);
+    }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < S * P; ++r) T[r * 33 + lane] = v[r];
+  __syncwarp();
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = lane < S * P ? T[lane * 33 + n2] : make_float2(0.f, 0.f);
+  __syncwarp();
+  dft32_regs(v, -1);
+}
+
+// Row item with warp-resident FFTs (FINAL: homogenised-stress partials after the law). Sequence
+// p = (line 2p) + i (line 2p + 1) of the item's 3 nr lines (line s = r NC + c) lives in warp
+// p / S at p % S; between the transforms the region holds it in space at s L + x.
+template <int P, bool FINAL>
+__device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned char* smem,
+                              double* red) {
+  constexpr int L = 32 * P, S = 32 / P;
+  const int Kx = d.Kx, R = d.R;
+  const int row0 = w.y * R;
+  const int nr = min(R, d.rows - row0);
+  const int nl = nr * NC, nseq = (nl + 1) / 2;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  int* kxs = reinterpret_cast<int*>(smem);
+  float2* W0 = reinterpret_cast<float2*>(smem + (((size_t)Kx * sizeof(int) + 15) & ~(size_t)15));
+  float2* Wr = W0 + (size_t)wp * kWRegion;   // this warp's region
+  const float2* tab = a.tab + d.tab_x;
+  for (int i = tid; i < Kx; i += blockDim.x) kxs[i] = a.kx[d.off_kx + i];
+  for (int i = lane; i < kWRegion; i += 32) Wr[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  // spectra: z_p[k] = ta + i tb, z_p[L - k] = conj(ta) + i conj(tb)
+  const float2* Tg = a.T1 + d.off_t1 + (long long)row0 * NC * Kx;
+  for (int u0 = tid; u0 < nseq * Kx; u0 += 4 * blockDim.x) {
+    float2 ta[4], tb[4];
+    int jj[4], pp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int u = u0 + q * blockDim.x;
+      pp[q] = -1;
+      if (u < nseq * Kx) {
+        const int p = fdiv(u, d.dKx), j = u - p * Kx;
+        const int s0 = 2 * p, s1 = s0 + 1;
+        ta[q] = Tg[(long long)s0 * Kx + j];
+        tb[q] = s1 < nl ? Tg[(long long)s1 * Kx + j] : make_float2(0.f, 0.f);
+        pp[q] = p;
+        jj[q] = j;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (pp[q] < 0) continue;
+      const int k = kxs[jj[q]];
+      const bool self = (k == 0) || (2 * k == L);
+      if (self) {
+        ta[q].y = 0.f;
+        tb[q].y = 0.f;
+      }
+      float2* z = W0 + (size_t)(pp[q] / S) * kWRegion + (pp[q] % S) * L;
+      z[k] = make_float2(ta[q].x - tb[q].y, ta[q].y + tb[q].x);
+      if (!self) z[L - k] = make_float2(ta[q].x + tb[q].y, tb[q].x - ta[q].y);
+    }
+  }
+  __syncthreads();
+  float2 v[32];
+  const bool busy = wp * S < nseq;   // a warp with sequences
+  if (busy) {
+    // to space: the conjugate of the forward transform of the conjugate spectra
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) {
+        const float2 z = Wr[s * L + 32 * n1 + lane];
+        v[s * P + n1] = make_float2(z.x, -z.y);
+      }
+#pragma unroll
+    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    fwd_batch<P>(v, Wr, tab, lane);
+    if (lane < S * P) {
+      const int s = lane / P, k1 = lane - s * P;
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = make_float2(v[k2].x, -v[k2].y);
+    }
+  }
+  __syncthreads();
+  // the law on every voxel of the item
+  const float invN = 1.f / (float)d.N;
+  double sb[6] = {0, 0, 0, 0, 0, 0};
+  for (int vx = tid; vx < nr * L; vx += blockDim.x) {
+    const int r = vx / L, x = vx - r * L;
+    const uint8_t pid = a.phase[d.off_phase + (long long)(row0 + r) * L + x];
+    float e[NC];
+    float* at[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int sl = r * NC + c, p = sl >> 1;
+      at[c] = reinterpret_cast<float*>(W0 + (size_t)(p / S) * kWRegion + (p % S) * L + x) +
+              (sl & 1);
+      e[c] = *at[c] * invN;
+    }
+    float e6[6];
+    comp_to6<NC>(e, e6);
+    const DevPhase ph = a.law.ph[pid];
+    float ep[6] = {0, 0, 0, 0, 0, 0};
+    LawOut o;
+    stress6<false>(e6, ph, ep, 0.f, o);
+    if (FINAL) {
+#pragma unroll
+      for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
+    } else {
+      const float tr = e6[0] + e6[1] + e6[2];
+      float tau6[6];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (d.lam0 * tr + 2.f * d.mu0 * e6[i]);
+#pragma unroll
+      for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * d.mu0 * e6[i];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) *at[c] = tau6[comp6<NC>(c)];
+    }
+  }
+  if (FINAL) {
+    for (int i = 0; i < 6; ++i) {
+      const double t = block_sum_d(sb[i], red);
+      if (tid == 0) a.spart[d.off_spart + (long long)w.y * 6 + i] = t;
+    }
+    return;
+  }
+  // an odd line count leaves the last sequence's imaginary carrier unused: zero it
+  if (nl & 1) {
+    const int p = nseq - 1;
+    float2* z = W0 + (size_t)(p / S) * kWRegion + (p % S) * L;
+    for (int x = tid; x < L; x += blockDim.x) z[x].y = 0.f;
+  }
+  __syncthreads();
+  if (busy) {
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) v[s * P + n1] = Wr[s * L + 32 * n1 + lane];
+#pragma unroll
+    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    fwd_batch<P>(v, Wr, tab, lane);
+    if (lane < S * P) {
+      const int s = lane / P, k1 = lane - s * P;
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = v[k2];
+    }
+  }
+  __syncthreads();
+  float2* To = a.T1p + d.off_t1 + (long long)row0 * NC * Kx;
+  for (int u = tid; u < nl * Kx; u += blockDim.x) {
+    const int sl = fdiv(u, d.dKx), j = u - sl * Kx;
+    const int k = kxs[j], p = sl >> 1;
+    const float2* z = W0 + (size_t)(p / S) * kWRegion + (p % S) * L;
+    const float2 zk = z[k], zm = z[k == 0 ? 0 : L - k];
+    float2 out;
+    if ((sl & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    To[(long long)sl * Kx + j] = out;
+  }
+}
+
+// warp-FFT row items of one row length L = 32 P (their own work list, a kernel per P: each
+// has its own register budget)
+template <int P>
+__global__ __launch_bounds__(256, 2) void kb_row_w(BArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[8];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int2 w = a.items[it];
+    if (!a.final_pass && rve_done(a, w.x)) continue;
+    const BDesc d = a.d[w.x];
+    __syncthreads();   // the previous item's shared-memory reads are done
+    if (a.final_pass) row_item_warp<P, true>(a, w, d, smem, red);
+    else row_item_warp<P, false>(a, w, d, smem, red);
+    __syncthreads();
   }
 }
 
@@ -875,6 +1170,8 @@ struct rf_batch {
   long long warm_total = 0;
   int grid = 0;
   size_t row_smem = 0;
+  size_t row_w_smem = 0;   // warp-FFT row items (work list 4, grouped by row length)
+  int w_off[6] = {0, 0, 0, 0, 0, 0};   // work list 4: items of row length 32 P for P = kWP[i]
   int R_choice[5] = {0, 0, 0, 0, 0};   // rows per row item, per size class (autotuned)
   bool use_fft = true;                 // FFT row and column items where the sides allow
   size_t col_smem = 0;                 // dynamic shared memory of the column kernels
@@ -930,14 +1227,47 @@ BArgs batch_args(rf_batch* b, int stage) {
   return a;
 }
 
+constexpr int kWP[5] = {2, 3, 4, 6, 8};   // P of the warp-FFT row lengths 64, 96, 128, 192, 256
+
+int warp_row_kernels(const rf_batch* b) {
+  int n = 0;
+  for (int i = 0; i < 5; ++i) n += b->w_off[i + 1] > b->w_off[i] ? 1 : 0;
+  return n;
+}
+
+// the warp-FFT row items, one launch per row length present
+void launch_warp_rows(rf_batch* b, bool final_pass) {
+  for (int i = 0; i < 5; ++i) {
+    const int n = b->w_off[i + 1] - b->w_off[i];
+    if (n <= 0) continue;
+    BArgs a = batch_args(b, 4);
+    a.items = b->d_items[4] + b->w_off[i];
+    a.n_items = n;
+    a.final_pass = final_pass ? 1 : 0;
+    switch (kWP[i]) {
+      case 2: kb_row_w<2><<<b->grid, 256, b->row_w_smem, b->stream>>>(a); break;
+      case 3: kb_row_w<3><<<b->grid, 256, b->row_w_smem, b->stream>>>(a); break;
+      case 4: kb_row_w<4><<<b->grid, 256, b->row_w_smem, b->stream>>>(a); break;
+      case 6: kb_row_w<6><<<b->grid, 256, b->row_w_smem, b->stream>>>(a); break;
+      default: kb_row_w<8><<<b->grid, 256, b->row_w_smem, b->stream>>>(a); break;
+    }
+  }
+}
+
+// kernels of one update: y transforms both ways, the row kernels with items, Green, decision
+int update_kernels(const rf_batch* b) {
+  return 4 + (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b);
+}
+
 int launch_update(rf_batch* b) {
   const int G = b->grid;
   kb_inv_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 0));
-  kb_row<<<G, 256, b->row_smem, b->stream>>>(batch_args(b, 1));
+  if (b->n_items[1] > 0) kb_row<<<G, 256, b->row_smem, b->stream>>>(batch_args(b, 1));
+  launch_warp_rows(b, false);
   kb_fwd_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 2));
   kb_gamma<<<G, 256, 0, b->stream>>>(batch_args(b, 3));
   kb_decide<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
-  b->launches += 5;
+  b->launches += update_kernels(b);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? RF_OK : bfail(e, "batch update");
 }
@@ -949,20 +1279,32 @@ int size_class(int side) {
   return 4;
 }
 
-// row items for a given rows-per-item choice per size class; sets desc R / row_items
+// rows per warp-FFT row item for rows of nx voxels (the item's 3 R lines pair into sequences
+// that fill the block's eight warps, 32 / P sequences each), 0 where that path does not apply
+int warp_rows(int nx) {
+  if (nx != 64 && nx != 96 && nx != 128 && nx != 192 && nx != 256) return 0;
+  const int S = 32 / (nx / 32);
+  return (16 * S) / 3;
+}
+
+// row items for a given rows-per-item choice per size class (-1: warp-FFT row items where
+// the row length allows them); sets desc R / row_items
 int build_row_items(rf_batch* b) {
-  std::vector<int2> items;
+  std::vector<int2> items, witems;
   std::vector<int> order(b->n);
   for (int i = 0; i < b->n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return b->desc[x].N > b->desc[y].N; });
-  size_t smem = 0;
+  size_t smem = 0, wsmem = 0;
   long long spart = 0;
   for (int r : order) {
     BDesc& d = b->desc[r];
-    d.R = std::max(1, std::min(b->R_choice[size_class(std::max(d.nx, d.ny))], d.rows));
+    const int choice = b->R_choice[size_class(std::max(d.nx, d.ny))];
+    d.warp = (choice < 0 && b->use_fft && warp_rows(d.nx) > 0) ? 1 : 0;
+    d.R = d.warp ? std::min(warp_rows(d.nx), d.rows)
+                 : std::max(1, std::min(choice < 0 ? 2 : choice, d.rows));
     d.row_items = (d.rows + d.R - 1) / d.R;
-    for (int k = 0; k < d.row_items; ++k) items.push_back(make_int2(r, k));
+    for (int k = 0; k < d.row_items; ++k) (d.warp ? witems : items).push_back(make_int2(r, k));
     const size_t s_dft = (size_t)d.nx * sizeof(float2) + (size_t)d.R * NC * d.Kx * sizeof(float2) +
                          (size_t)d.Kx * 8 + (size_t)d.R * NC * d.nx * sizeof(float) + 64;
     const int P = (d.R * NC + 1) / 2;
@@ -971,24 +1313,47 @@ int build_row_items(rf_batch* b) {
                          (size_t)d.Kx * sizeof(int) + 64;
     const int p2 = d.nx % 3 == 0 ? d.nx / 3 : d.nx;
     d.fft = (b->use_fft && p2 >= 1 && (p2 & (p2 - 1)) == 0 && s_fft <= 160 * 1024) ? 1 : 0;
-    smem = std::max(smem, d.fft ? s_fft : s_dft);
+    const size_t s_warp = (((size_t)d.Kx * sizeof(int) + 15) & ~(size_t)15) +
+                          8 * (size_t)kWRegion * sizeof(float2);
+    if (d.warp) wsmem = std::max(wsmem, s_warp);
+    else smem = std::max(smem, d.fft ? s_fft : s_dft);
   }
   for (int r = 0; r < b->n; ++r) {
     b->desc[r].off_spart = spart;
     spart += (long long)b->desc[r].row_items * 6;
   }
   if (b->d_items[1]) cudaFree(b->d_items[1]);
+  if (b->d_items[4]) cudaFree(b->d_items[4]);
+  b->d_items[1] = b->d_items[4] = nullptr;
   if (b->d_spart) cudaFree(b->d_spart);
-  if (int e = balloc(&b->d_items[1], items.size(), "batch items")) return e;
+  if (int e = balloc(&b->d_items[1], std::max<size_t>(items.size(), 1), "batch items")) return e;
+  if (int e = balloc(&b->d_items[4], std::max<size_t>(witems.size(), 1), "batch items")) return e;
   if (int e = balloc(&b->d_spart, (size_t)spart, "batch partials")) return e;
   b->n_items[1] = (int)items.size();
+  b->n_items[4] = (int)witems.size();
+  b->row_w_smem = wsmem;
+  // group the warp items by row length (stable: largest RVEs first within each)
+  std::stable_sort(witems.begin(), witems.end(), [&](const int2& x, const int2& y) {
+    return b->desc[x.x].nx < b->desc[y.x].nx;
+  });
+  for (int i = 0; i < 6; ++i) b->w_off[i] = 0;
+  for (const int2& it : witems) {
+    const int P = b->desc[it.x].nx / 32;
+    for (int i = 0; i < 5; ++i)
+      if (kWP[i] == P) b->w_off[i + 1] += 1;
+  }
+  for (int i = 0; i < 5; ++i) b->w_off[i + 1] += b->w_off[i];
   if (smem > 200 * 1024) {
     set_error("batch: row tile too large for shared memory");
     return RF_ERR_INVALID;
   }
   b->row_smem = smem;
-  cudaError_t e = cudaMemcpy(b->d_items[1], items.data(), sizeof(int2) * items.size(),
-                             cudaMemcpyHostToDevice);
+  cudaError_t e = items.empty() ? cudaSuccess
+                                : cudaMemcpy(b->d_items[1], items.data(),
+                                             sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !witems.empty())
+    e = cudaMemcpy(b->d_items[4], witems.data(), sizeof(int2) * witems.size(),
+                   cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_desc, b->desc.data(), sizeof(BDesc) * b->n, cudaMemcpyHostToDevice);
   return e == cudaSuccess ? RF_OK : bfail(e, "batch upload");
@@ -1123,7 +1488,7 @@ int iterate(rf_batch* b) {
       e = cudaMemcpyAsync(b->h_ndone, b->d_ndone, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(e, "batch iterate");
-    b->launches += 5LL * chunk;
+    b->launches += (long long)update_kernels(b) * chunk;
     if (*b->h_ndone >= b->n) break;
     chunk = std::min(chunk * 2, maxchunk);
   }
@@ -1146,7 +1511,7 @@ int run_solve(rf_batch* b, const double* macro, bool use_warm, const float2* pwa
 int autotune(rf_batch* b, const double* macro) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
-  const int Rc[4] = {1, 2, 4, 8};
+  const int Rc[5] = {1, 2, 4, 8, -1};   // -1: warp-FFT row items
   const int Gc[3] = {2, 4, 8};
   bool present[5] = {false, false, false, false, false};
   for (const BDesc& d : b->desc) present[size_class(std::max(d.nx, d.ny))] = true;
@@ -1182,6 +1547,7 @@ int autotune(rf_batch* b, const double* macro) {
     float best = 1e30f;
     int bestR = b->R_choice[k];
     for (int R : Rc) {
+      if (R < 0 && !b->use_fft) continue;
       b->R_choice[k] = R;
       float ms = 0.f;
       err = build_row_items(b);
@@ -1224,9 +1590,10 @@ int finish_solve(rf_batch* b, double* hom_stress, int32_t* iters, double* residu
   kb_inv_y<<<b->grid, 256, b->col_smem, b->stream>>>(a0);
   BArgs a1 = batch_args(b, 1);
   a1.final_pass = 1;
-  kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
+  if (b->n_items[1] > 0) kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
+  launch_warp_rows(b, true);
   kb_sbar<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
-  b->launches += 3;
+  b->launches += 2 + (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b);
   cudaError_t e = cudaMemcpyAsync(b->h_stat, b->d_stat, sizeof(BStat) * b->n,
                                   cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1246,8 +1613,9 @@ int finish_solve(rf_batch* b, double* hom_stress, int32_t* iters, double* residu
     if (st != RF_OK && code == RF_OK) code = RF_NOT_CONVERGED;
     b->last_max_iters = std::max(b->last_max_iters, s.iters);
   }
-  if (b->last_while)   // bodies of kBatchBody updates of five kernels each
-    b->launches += 5LL * kBatchBody * ((b->last_max_iters + kBatchBody - 1) / kBatchBody);
+  if (b->last_while)   // bodies of kBatchBody updates
+    b->launches += (long long)update_kernels(b) * kBatchBody *
+                   ((b->last_max_iters + kBatchBody - 1) / kBatchBody);
   return code;
 }
 
@@ -1557,6 +1925,10 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     std::vector<long long> none(n_rve, -1);
     up(b->d_warm_off, none.data(), sizeof(long long) * n_rve);
     cudaFuncSetAttribute(kb_row, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    for (const void* k : {(const void*)kb_row_w<2>, (const void*)kb_row_w<3>,
+                          (const void*)kb_row_w<4>, (const void*)kb_row_w<6>,
+                          (const void*)kb_row_w<8>})
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     cudaFuncSetAttribute(kb_inv_y, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     cudaFuncSetAttribute(kb_fwd_y, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   }
@@ -1706,8 +2078,11 @@ int rf_batch_info(const rf_batch* b, int64_t* kernel_launches, int32_t* rows_per
     return RF_ERR_INVALID;
   }
   if (kernel_launches) *kernel_launches = b->launches;
-  if (rows_per_item)
-    for (int k = 0; k < 5; ++k) rows_per_item[k] = b->R_choice[k];
+  if (rows_per_item) {
+    static const int sides[5] = {64, 96, 128, 192, 256};
+    for (int k = 0; k < 5; ++k)
+      rows_per_item[k] = b->R_choice[k] < 0 ? warp_rows(sides[k]) : b->R_choice[k];
+  }
   if (grid) *grid = b->grid;
   return RF_OK;
 }
