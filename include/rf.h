@@ -375,8 +375,11 @@ int rf_pattern_radial(const rf_grid* grid, int64_t k_target, int32_t* freqs_out,
  *  rf_batch_create: grids[n_rve]; phase_maps[n_rve] HOST uint8 pointers; phases shared by all
  *  RVEs; patterns[n_rve] HOST int32 [K[r]][3] pointers (rules of rf_set_pattern, kz = 0); all
  *  inputs are copied. Chooses the rows per row work item for each size class of RVE (largest
- *  side <= 64, <= 96, <= 128, <= 192, larger) and the persistent grid size by timing updates
- *  of the whole batch (autotuner). stream as in rf_create.
+ *  side <= 64, <= 96, <= 128, <= 192, larger), whether the y transforms run as warp-FFT column
+ *  items, and the persistent grid size by timing updates of the whole batch (autotuner).
+ *  With options.transform = RF_TRANSFORM_FFT, options.fft_row_warps = -1 keeps every row and
+ *  column item on the shared-memory FFTs, > 0 puts every row and column of 64, 96, 128, 192 or
+ *  256 voxels on the warp-FFT items, 0 lets the autotuner choose. stream as in rf_create.
  *  rf_batch_solve: macro [n_rve][6]; warm nullable, else warm[r] nullable HOST float
  *  [K[r]][6][2] start coefficients (projected as in rf_solve); outputs (each nullable):
  *  hom_stress [n_rve][6], iters [n_rve], residuals [n_rve], status [n_rve] (RF_OK,

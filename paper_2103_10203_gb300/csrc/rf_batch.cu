@@ -636,6 +636,87 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
   }
 }
 
+// Column item with warp-resident FFTs along y (column length L = 32 P): 8 S consecutive line
+// columns (of the NC Kx per row) of one RVE, S = 32 / P per warp. Inverse (sign +1): the
+// pattern's ky rows of ER scattered into zeroed columns, transformed, all L rows of T1.
+// Forward: all L rows of T1p, transformed, the pattern's ky rows into OUT.
+template <int P>
+__device__ void col_item_warp(const BArgs& a, int g, const BDesc& d, unsigned char* smem,
+                              int sign) {
+  constexpr int L = 32 * P, S = 32 / P, G = 8 * S;
+  const int NCK = NC * d.Kx;
+  const int c0 = g * G, cc_n = min(G, NCK - c0);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  float2* W0 = reinterpret_cast<float2*>(smem);
+  float2* Wr = W0 + (size_t)wp * kWRegion;
+  const float2* tab = a.tab + d.tab_y;
+  const int* kym = a.kym + d.off_ky;
+  if (sign > 0)
+    for (int i = lane; i < kWRegion; i += 32) Wr[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2* src = sign > 0 ? a.ER + d.off_er : a.T1p + d.off_t1;
+  const int rows_in = sign > 0 ? d.Ky : L;
+  const int tot = rows_in * cc_n;
+  for (int i0 = tid; i0 < tot; i0 += 8 * blockDim.x) {
+    float2 v[8];
+    int dst[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * blockDim.x;
+      dst[u] = -1;
+      if (i < tot) {
+        const int r = i / cc_n, cc = i - r * cc_n;
+        v[u] = src[(long long)r * NCK + c0 + cc];
+        dst[u] = (cc / S) * kWRegion + (cc % S) * L + (sign > 0 ? kym[r] : r);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (dst[u] >= 0) W0[dst[u]] = v[u];
+  }
+  __syncthreads();
+  if (wp * S < cc_n) {
+    float2 v[32];
+    const float cj = sign > 0 ? -1.f : 1.f;   // the inverse as the conjugate of the forward
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) {
+        const float2 z = Wr[s * L + 32 * n1 + lane];
+        v[s * P + n1] = make_float2(z.x, cj * z.y);
+      }
+#pragma unroll
+    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    fwd_batch<P>(v, Wr, tab, lane);
+    if (lane < S * P) {
+      const int s = lane / P, k1 = lane - s * P;
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = make_float2(v[k2].x, cj * v[k2].y);
+    }
+  }
+  __syncthreads();
+  float2* dstg = sign > 0 ? a.T1 + d.off_t1 : a.OUT + d.off_er;
+  const int rows_out = sign > 0 ? L : d.Ky;
+  for (int i = tid; i < rows_out * cc_n; i += blockDim.x) {
+    const int r = i / cc_n, cc = i - r * cc_n;
+    dstg[(long long)r * NCK + c0 + cc] =
+        W0[(cc / S) * kWRegion + (cc % S) * L + (sign > 0 ? r : kym[r])];
+  }
+  __syncthreads();   // the next item reuses the regions
+}
+
+// warp-FFT column items of one column length (a kernel per P and direction)
+template <int P, int SIGN>
+__global__ __launch_bounds__(256, 2) void kb_y_w(BArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const int2 w = a.items[it];
+    if (!a.final_pass && rve_done(a, w.x)) continue;   // the final pass covers every RVE
+    const BDesc d = a.d[w.x];
+    col_item_warp<P>(a, w.y, d, smem, SIGN);
+  }
+}
+
 // warp-FFT row items of one row length L = 32 P (their own work list, a kernel per P: each
 // has its own register budget)
 template <int P>
@@ -1161,8 +1242,11 @@ struct rf_batch {
   double *d_part = nullptr, *d_spart = nullptr;
   int* d_ndone = nullptr;
   int* h_ndone = nullptr;   // pinned
-  int2* d_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  int n_items[5] = {0, 0, 0, 0, 0};
+  // work lists: 0 inverse y, 1 rows, 2 forward y, 3 Green, 4 warp-FFT rows, 5 warp-FFT columns
+  int2* d_items[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int n_items[6] = {0, 0, 0, 0, 0, 0};
+  int col_warp = 0;                    // 1: warp-FFT column items where the column length allows
+  int y_off[6] = {0, 0, 0, 0, 0, 0};   // work list 5: groups of column length 32 P, P = kWP[i]
   float2* d_warm = nullptr;
   long long* d_warm_off = nullptr;
   long long n_slots = 0;    // half entries of all RVEs
@@ -1254,17 +1338,50 @@ void launch_warp_rows(rf_batch* b, bool final_pass) {
   }
 }
 
+int warp_col_kernels(const rf_batch* b) {
+  int n = 0;
+  for (int i = 0; i < 5; ++i) n += b->y_off[i + 1] > b->y_off[i] ? 1 : 0;
+  return n;
+}
+
+// the warp-FFT column items of one direction, one launch per column length present
+void launch_warp_cols(rf_batch* b, int sign, bool final_pass) {
+  for (int i = 0; i < 5; ++i) {
+    const int n = b->y_off[i + 1] - b->y_off[i];
+    if (n <= 0) continue;
+    BArgs a = batch_args(b, 5);
+    a.items = b->d_items[5] + b->y_off[i];
+    a.n_items = n;
+    a.final_pass = final_pass ? 1 : 0;
+    const size_t sm = 8 * (size_t)kWRegion * sizeof(float2);
+#define RF_YW(PP)                                                                          \
+  (sign > 0 ? (kb_y_w<PP, 1><<<b->grid, 256, sm, b->stream>>>(a), 0)                      \
+            : (kb_y_w<PP, -1><<<b->grid, 256, sm, b->stream>>>(a), 0))
+    switch (kWP[i]) {
+      case 2: RF_YW(2); break;
+      case 3: RF_YW(3); break;
+      case 4: RF_YW(4); break;
+      case 6: RF_YW(6); break;
+      default: RF_YW(8); break;
+    }
+#undef RF_YW
+  }
+}
+
 // kernels of one update: y transforms both ways, the row kernels with items, Green, decision
 int update_kernels(const rf_batch* b) {
-  return 4 + (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b);
+  return 2 + (b->n_items[0] > 0 ? 1 : 0) + (b->n_items[2] > 0 ? 1 : 0) +
+         (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b) + 2 * warp_col_kernels(b);
 }
 
 int launch_update(rf_batch* b) {
   const int G = b->grid;
-  kb_inv_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 0));
+  if (b->n_items[0] > 0) kb_inv_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 0));
+  launch_warp_cols(b, +1, false);
   if (b->n_items[1] > 0) kb_row<<<G, 256, b->row_smem, b->stream>>>(batch_args(b, 1));
   launch_warp_rows(b, false);
-  kb_fwd_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 2));
+  if (b->n_items[2] > 0) kb_fwd_y<<<G, 256, b->col_smem, b->stream>>>(batch_args(b, 2));
+  launch_warp_cols(b, -1, false);
   kb_gamma<<<G, 256, 0, b->stream>>>(batch_args(b, 3));
   kb_decide<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
   b->launches += update_kernels(b);
@@ -1272,11 +1389,73 @@ int launch_update(rf_batch* b) {
   return e == cudaSuccess ? RF_OK : bfail(e, "batch update");
 }
 
+constexpr int kSides[5] = {64, 96, 128, 192, 256};   // the size classes' sides
+
 int size_class(int side) {
   static const int sides[5] = {64, 96, 128, 192, 256};
   for (int i = 0; i < 5; ++i)
     if (side <= sides[i]) return i;
   return 4;
+}
+
+// groups of 8 S line columns per warp-FFT column item for columns of ny voxels, 0 where that
+// path does not apply
+int warp_col_group(const BDesc& d) {
+  const int ny = d.ny;
+  if (!d.fft_y || (ny != 64 && ny != 96 && ny != 128 && ny != 192 && ny != 256)) return 0;
+  return 8 * (32 / (ny / 32));
+}
+
+// the y-transform work lists: shared-memory FFT groups or DFT tiles (lists 0 and 2), and with
+// b->col_warp the warp-FFT column groups (list 5, grouped by column length)
+int build_col_items(rf_batch* b) {
+  std::vector<int> order(b->n);
+  for (int i = 0; i < b->n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->desc[x].N > b->desc[y].N; });
+  std::vector<int2> inv, fwd, yw;
+  for (int r : order) {
+    const BDesc& d = b->desc[r];
+    const int G = b->col_warp ? warp_col_group(d) : 0;
+    if (G > 0) {
+      for (int k = 0; k < (NC * d.Kx + G - 1) / G; ++k) yw.push_back(make_int2(r, k));
+    } else if (d.fft_y) {
+      const int groups = (NC * d.Kx + d.cy - 1) / d.cy;
+      for (int k = 0; k < groups; ++k) {
+        inv.push_back(make_int2(r, k | kColFft));
+        fwd.push_back(make_int2(r, k | kColFft));
+      }
+    } else {
+      for (int k = 0; k < d.mt_inv * d.nt; ++k) inv.push_back(make_int2(r, k));
+      for (int k = 0; k < d.mt_fwd * d.nt; ++k) fwd.push_back(make_int2(r, k));
+    }
+  }
+  std::stable_sort(yw.begin(), yw.end(), [&](const int2& x, const int2& y) {
+    return b->desc[x.x].ny < b->desc[y.x].ny;
+  });
+  for (int i = 0; i < 6; ++i) b->y_off[i] = 0;
+  for (const int2& it : yw) {
+    const int P = b->desc[it.x].ny / 32;
+    for (int i = 0; i < 5; ++i)
+      if (kWP[i] == P) b->y_off[i + 1] += 1;
+  }
+  for (int i = 0; i < 5; ++i) b->y_off[i + 1] += b->y_off[i];
+  std::vector<int2>* lists[3] = {&inv, &fwd, &yw};
+  const int slot[3] = {0, 2, 5};
+  for (int q = 0; q < 3; ++q) {
+    const int st = slot[q];
+    if (b->d_items[st]) cudaFree(b->d_items[st]);
+    b->d_items[st] = nullptr;
+    if (int e = balloc(&b->d_items[st], std::max<size_t>(lists[q]->size(), 1), "batch items"))
+      return e;
+    b->n_items[st] = (int)lists[q]->size();
+    if (!lists[q]->empty()) {
+      cudaError_t e = cudaMemcpy(b->d_items[st], lists[q]->data(),
+                                 sizeof(int2) * lists[q]->size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return bfail(e, "batch upload");
+    }
+  }
+  return RF_OK;
 }
 
 // rows per warp-FFT row item for rows of nx voxels (the item's 3 R lines pair into sequences
@@ -1547,7 +1726,10 @@ int autotune(rf_batch* b, const double* macro) {
     float best = 1e30f;
     int bestR = b->R_choice[k];
     for (int R : Rc) {
-      if (R < 0 && !b->use_fft) continue;
+      // options.fft_row_warps: -1 never the warp-FFT items, > 0 only them (where they apply)
+      const int ow = b->opt.fft_row_warps;
+      if (R < 0 && (!b->use_fft || ow < 0)) continue;
+      if (R > 0 && ow > 0 && b->use_fft && warp_rows(kSides[k]) > 0) continue;
       b->R_choice[k] = R;
       float ms = 0.f;
       err = build_row_items(b);
@@ -1561,6 +1743,25 @@ int autotune(rf_batch* b, const double* macro) {
     b->R_choice[k] = bestR;
   }
   if (!err) err = build_row_items(b);
+  if (!err && b->use_fft && b->opt.fft_row_warps != 0) {
+    b->col_warp = b->opt.fft_row_warps > 0 ? 1 : 0;
+    err = build_col_items(b);
+  } else if (!err && b->use_fft) {
+    // warp-FFT column items against the shared-memory ones
+    float t1 = 1e30f, t0 = 1e30f;
+    b->col_warp = 1;
+    err = build_col_items(b);
+    if (!err) err = time_updates(&t1);
+    if (!err) {
+      b->col_warp = 0;
+      err = build_col_items(b);
+      if (!err) err = time_updates(&t0);
+    }
+    if (!err) {
+      b->col_warp = t1 < t0 ? 1 : 0;
+      err = build_col_items(b);
+    }
+  }
   if (!err) {
     float best = 1e30f;
     int bestG = 4;
@@ -1587,13 +1788,15 @@ int finish_solve(rf_batch* b, double* hom_stress, int32_t* iters, double* residu
   // final pass: fields of the converged coefficients -> homogenised stresses
   BArgs a0 = batch_args(b, 0);
   a0.final_pass = 1;
-  kb_inv_y<<<b->grid, 256, b->col_smem, b->stream>>>(a0);
+  if (b->n_items[0] > 0) kb_inv_y<<<b->grid, 256, b->col_smem, b->stream>>>(a0);
+  launch_warp_cols(b, +1, true);
   BArgs a1 = batch_args(b, 1);
   a1.final_pass = 1;
   if (b->n_items[1] > 0) kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
   launch_warp_rows(b, true);
   kb_sbar<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
-  b->launches += 2 + (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b);
+  b->launches += 1 + (b->n_items[0] > 0 ? 1 : 0) + warp_col_kernels(b) +
+                 (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b);
   cudaError_t e = cudaMemcpyAsync(b->h_stat, b->d_stat, sizeof(BStat) * b->n,
                                   cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1901,27 +2104,16 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
     for (int i = 0; i < n_rve; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return b->desc[x].N > b->desc[y].N; });
-    std::vector<int2> inv, fwd, gam;
+    std::vector<int2> gam;
     for (int r : order) {
       const BDesc& d = b->desc[r];
-      if (d.fft_y) {
-        const int groups = (NC * d.Kx + d.cy - 1) / d.cy;
-        for (int k = 0; k < groups; ++k) {
-          inv.push_back(make_int2(r, k | kColFft));
-          fwd.push_back(make_int2(r, k | kColFft));
-        }
-      } else {
-        for (int k = 0; k < d.mt_inv * d.nt; ++k) inv.push_back(make_int2(r, k));
-        for (int k = 0; k < d.mt_fwd * d.nt; ++k) fwd.push_back(make_int2(r, k));
-      }
       for (int k = 0; k < d.chunks; ++k) gam.push_back(make_int2(r, k));
     }
-    std::vector<int2>* lists[5] = {&inv, nullptr, &fwd, &gam, nullptr};
-    for (int s : {0, 2, 3}) {
-      if (!err) err = balloc(&b->d_items[s], lists[s]->size(), "batch items");
-      up(b->d_items[s], lists[s]->data(), sizeof(int2) * lists[s]->size());
-      b->n_items[s] = (int)lists[s]->size();
-    }
+    if (!err) err = balloc(&b->d_items[3], gam.size(), "batch items");
+    up(b->d_items[3], gam.data(), sizeof(int2) * gam.size());
+    b->n_items[3] = (int)gam.size();
+    b->col_warp = (b->use_fft && opt->fft_row_warps >= 0) ? 1 : 0;
+    if (!err) err = build_col_items(b);
     std::vector<long long> none(n_rve, -1);
     up(b->d_warm_off, none.data(), sizeof(long long) * n_rve);
     cudaFuncSetAttribute(kb_row, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1930,6 +2122,12 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
                           (const void*)kb_row_w<8>})
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     cudaFuncSetAttribute(kb_inv_y, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    for (const void* k :
+         {(const void*)kb_y_w<2, 1>, (const void*)kb_y_w<3, 1>, (const void*)kb_y_w<4, 1>,
+          (const void*)kb_y_w<6, 1>, (const void*)kb_y_w<8, 1>, (const void*)kb_y_w<2, -1>,
+          (const void*)kb_y_w<3, -1>, (const void*)kb_y_w<4, -1>, (const void*)kb_y_w<6, -1>,
+          (const void*)kb_y_w<8, -1>})
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     cudaFuncSetAttribute(kb_fwd_y, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
   }
   if (!err) {
@@ -2110,7 +2308,7 @@ int rf_batch_destroy(rf_batch* b) {
   cudaFree(b->d_counter);
   cudaFree(b->d_warm);
   cudaFree(b->d_warm_off);
-  for (int s = 0; s < 5; ++s) cudaFree(b->d_items[s]);
+  for (int s = 0; s < 6; ++s) cudaFree(b->d_items[s]);
   if (b->h_stat) cudaFreeHost(b->h_stat);
   if (b->h_ndone) cudaFreeHost(b->h_ndone);
   if (b->own_stream) cudaStreamDestroy(b->stream);

@@ -106,12 +106,13 @@ def half_order(pat):
     return sorted((int(k[0]), int(k[1])) for k in pat if k[0] >= 0)
 
 
-@pytest.mark.parametrize("transform", ["fft", "dft"])
-def test_batch_reduced_coefficients_match_oracle_at_full_sizes(lib, transform):
+@pytest.mark.parametrize("transform,warps", [("fft", -1), ("fft", 2), ("dft", 0)])
+def test_batch_reduced_coefficients_match_oracle_at_full_sizes(lib, transform, warps):
     """Sides 64, 96, 128, 192 and 256 (the FE-FFT population's sizes: radix-2 and radix-3 FFT
-    items along x and y, or pruned-DFT items), a fixed number of updates, every reduced strain
-    coefficient compared with the oracle's (relative L2 per RVE <= 1e-5), and the homogenised
-    stress (<= 1e-6)."""
+    items along x and y, on shared memory (warps -1) or as warp-FFT row and column items with
+    2, 3, 4, 6 and 8 points per lane (warps 2), or pruned-DFT items), a fixed number of
+    updates, every reduced strain coefficient compared with the oracle's (relative L2 per RVE
+    <= 1e-5), and the homogenised stress (<= 1e-6)."""
     ph = elastic_phases()
     pms, pats, macros = [], [], []
     for i, side in enumerate((64, 96, 128, 192, 256)):
@@ -120,12 +121,18 @@ def test_batch_reduced_coefficients_match_oracle_at_full_sizes(lib, transform):
         pats.append(lib.rf_pattern_adapted(c["phase_map"], 1, c["k_target"]))
         macros.append(c["macro"])
     macros = np.array(macros)
-    b = lib.BatchSolver(pms, ph, pats, tol=0.0, max_iter=4, transform=transform)
+    b = lib.BatchSolver(pms, ph, pats, tol=0.0, max_iter=4, transform=transform,
+                        fft_row_warps=warps)
     out = b.rf_batch_solve(macros)
+    info = b.rf_batch_info()
     coeffs = b.rf_batch_reduced_strain().cpu().numpy()
     _, off = b.rf_batch_slots()
     b.close()
     assert np.all(out["iters"] == 4)
+    if warps > 0:
+        assert list(info["rows_per_item"]) == [85, 53, 42, 26, 21]
+    elif transform == "fft":
+        assert all(r in (1, 2, 4, 8) for r in info["rows_per_item"])
     for i, (pm, pat) in enumerate(zip(pms, pats)):
         r = O.solve(pm, ph, macros[i], pat, tol=0.0, max_iter=4)
         at = {(int(k[0]), int(k[1])): p for p, k in enumerate(pat)}
