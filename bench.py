@@ -378,7 +378,9 @@ def batch_summary(rf, torch, n, steps, warmup, sample_every=8):
             "gpu_launches": int(launches), "autotuned": info,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
-                         "kernel": "whole update (five persistent kernels)",
+                         "kernel": ("kb_resident (a block per RVE runs all its updates)"
+                                    if info.get("resident") else
+                                    "whole update (the sweep kernels over all RVEs)"),
                          "algorithmic_bytes_per_voxel_iteration": bytes_per_vox_it},
             "clocks": clk.summary()}
 

@@ -149,7 +149,14 @@ typedef struct rf_phase {
  *             fft_row_blocks are 0); 2 or 4 = always, with that many warps (one or two rows) per
  *             block; 8 = four rows per block on row-group slabs, the form that goes with
  *             fft_fuse 4 and 5 (and only with them; 0 there means 8); -1 = never. Ignored
- *             where it does not apply; the same update either way up to FP32 rounding order. */
+ *             where it does not apply; the same update either way up to FP32 rounding order.
+ *  batch_resident  rf_batch only, FFT transforms: when every RVE is square with a side of 64,
+ *             96, 128, 192 or 256, a solve may run as one RVE-resident launch (a block holds
+ *             an RVE for all of its updates and its final pass, RVEs taken largest first from a
+ *             queue; no step waits for other RVEs) instead of sweeps of every RVE per update.
+ *             0 = the faster of the two by timing a short solve each way at creation; 1 =
+ *             always where the batch qualifies; -1 = never. The same update and convergence
+ *             rules either way (up to FP32 rounding order). Ignored by rf_create. */
 typedef struct rf_options {
   double tol;
   int32_t max_iter;
@@ -166,6 +173,7 @@ typedef struct rf_options {
   int64_t wait_limit;
   int32_t stall_test;
   int32_t fft_row_warps;
+  int32_t batch_resident;
 } rf_options;
 
 /* Run statistics of the last solve on a context. */
@@ -400,6 +408,9 @@ int rf_batch_solve(rf_batch* batch, const double* macro, const float* const* war
                    double* hom_stress, int32_t* iters, double* residuals, int32_t* status);
 int rf_batch_info(const rf_batch* batch, int64_t* kernel_launches, int32_t* rows_per_item,
                   int32_t* grid);
+/* rf_batch_mode: *resident = 1 when the batch's solves run RVE-resident (options.batch_resident),
+ * else 0. */
+int rf_batch_mode(const rf_batch* batch, int32_t* resident);
 int rf_batch_destroy(rf_batch* batch);
 
 /* Message of the last error on the calling thread ("" if none). */

@@ -734,6 +734,373 @@ __global__ __launch_bounds__(256, 2) void kb_row_w(BArgs a) {
   }
 }
 
+// ---- RVE-resident solve: a block holds one RVE for every update of its solve
+//
+// Each block of kResWarps warps takes RVEs from a queue (largest first) and runs all updates of
+// its RVE back to back: the inverse y transforms of the coefficients (S line columns per warp),
+// the row passes (R_w rows per warp: their 3 R_w lines as packed pairs, inverse x transform,
+// law, forward x transform, the coefficients at the pattern's kx), the forward y transforms,
+// the Green step with the FP64 measure (the chunked reduction of kb_gamma / kb_decide), and the
+// decision; then the final pass (homogenised stress). Block barriers separate the phases; no
+// block waits for another. The line transforms live in the block's scratch slot in global
+// memory, [Ny][NC Kx] (the RVE's working set, L2-resident while the block holds it).
+
+constexpr int kResWarps = 8;
+constexpr int kResThreads = 32 * kResWarps;
+constexpr int kResMaxL = 256;
+
+struct ResShared {
+  int kxs[kResMaxL / 2 + 1];
+  int inv_ky[kResMaxL];   // position of ky (mod Ny) in the pattern's ky list, or -1
+  double red[kResWarps];
+  int next, done;
+};
+
+// inverse y transforms (conjugate of the forward transform of the conjugate) of the NC Kx line
+// columns, S adjacent columns per warp: the pattern's ky rows of ER gathered straight into the
+// transform layout, all L rows written to T
+template <int P>
+__device__ __noinline__ void res_inv_y(const BArgs& a, const BDesc& d, float2* T, float2* Wr,
+                          const ResShared& sh, int lane, int wp) {
+  constexpr int L = 32 * P, S = 32 / P;
+  const int NCK = NC * d.Kx, groups = (NCK + S - 1) / S;
+  const float2* ER = a.ER + d.off_er;
+  const float2* tab = a.tab + d.tab_y;
+  for (int g = wp; g < groups; g += kResWarps) {
+    const int q0 = g * S, ns = min(S, NCK - q0);
+    float2 v[32];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) {
+      const int i = sh.inv_ky[32 * n1 + lane];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        float2 z = make_float2(0.f, 0.f);
+        if (i >= 0 && s < ns) z = ER[(long long)i * NCK + q0 + s];
+        v[s * P + n1] = make_float2(z.x, -z.y);
+      }
+    }
+#pragma unroll
+    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    fwd_batch<P>(v, Wr, tab, lane);
+    if (lane < S * P) {
+      const int s = lane / P, k1 = lane - s * P;
+      if (s < ns) {
+        float2* col = T + q0 + s;
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2)
+          col[(long long)(k1 + P * k2) * NCK] = make_float2(v[k2].x, -v[k2].y);
+      }
+    }
+    __syncwarp();   // the region is the next group's transpose buffer
+  }
+}
+
+// forward y transforms of the line columns of T (all L rows), the pattern's ky rows written
+// back in place: row i of T holds the i-th ky of the list afterwards
+template <int P>
+__device__ __noinline__ void res_fwd_y(const BArgs& a, const BDesc& d, float2* T, float2* Wr,
+                          const ResShared& sh, int lane, int wp) {
+  constexpr int L = 32 * P, S = 32 / P;
+  const int NCK = NC * d.Kx, groups = (NCK + S - 1) / S;
+  const float2* tab = a.tab + d.tab_y;
+  for (int g = wp; g < groups; g += kResWarps) {
+    const int q0 = g * S, ns = min(S, NCK - q0);
+    float2 v[32];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1)
+        v[s * P + n1] = s < ns ? T[(long long)(32 * n1 + lane) * NCK + q0 + s]
+                               : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    fwd_batch<P>(v, Wr, tab, lane);
+    if (lane < S * P) {
+      const int s = lane / P, k1 = lane - s * P;
+      if (s < ns) {
+        float2* col = T + q0 + s;
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) {
+          const int i = sh.inv_ky[k1 + P * k2];
+          if (i >= 0) col[(long long)i * NCK] = v[k2];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// row passes: warp items of R_w = 2 S / 3 rows (3 R_w lines, packed in pairs into at most S
+// sequences), each warp on its own items; FINAL: homogenised-stress sums instead of the
+// forward transform
+template <int P, bool FINAL>
+__device__ __noinline__ void res_rows(const BArgs& a, const BDesc& d, float2* T, float2* Wr,
+                         const ResShared& sh, int lane, int wp, double* sb) {
+  constexpr int L = 32 * P, S = 32 / P, RW = (2 * S) / 3;
+  const int Kx = d.Kx, NCK = NC * Kx;
+  const float2* tab = a.tab + d.tab_x;
+  const uint8_t* phase = a.phase + d.off_phase;
+  const float invN = 1.f / (float)d.N;
+  const int items = (L + RW - 1) / RW;
+  for (int it = wp; it < items; it += kResWarps) {
+    const int y0 = it * RW, nr = min(RW, L - y0), nl = nr * NC, nseq = (nl + 1) / 2;
+    for (int i = lane; i < S * L; i += 32) Wr[i] = make_float2(0.f, 0.f);
+    __syncwarp();
+    // z_p = line 2p + i line 2p+1 (line s = r NC + c of the item): z[k] = ta + i tb,
+    // z[L - k] = conj(ta) + i conj(tb)
+    float2* Tg = T + (long long)y0 * NCK;
+    for (int u0 = lane; u0 < nseq * Kx; u0 += 4 * 32) {
+      float2 ta[4], tb[4];
+      int jj[4], pp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int u = u0 + q * 32;
+        pp[q] = -1;
+        if (u < nseq * Kx) {
+          const int p = fdiv(u, d.dKx), j = u - p * Kx;
+          const int s0 = 2 * p, s1 = s0 + 1;
+          ta[q] = Tg[s0 * Kx + j];
+          tb[q] = s1 < nl ? Tg[s1 * Kx + j] : make_float2(0.f, 0.f);
+          pp[q] = p;
+          jj[q] = j;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (pp[q] < 0) continue;
+        const int k = sh.kxs[jj[q]];
+        const bool self = (k == 0) || (2 * k == L);
+        if (self) {
+          ta[q].y = 0.f;
+          tb[q].y = 0.f;
+        }
+        float2* z = Wr + pp[q] * L;
+        z[k] = make_float2(ta[q].x - tb[q].y, ta[q].y + tb[q].x);
+        if (!self) z[L - k] = make_float2(ta[q].x + tb[q].y, tb[q].x - ta[q].y);
+      }
+    }
+    __syncwarp();
+    float2 v[32];
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) {
+        const float2 z = Wr[s * L + 32 * n1 + lane];
+        v[s * P + n1] = make_float2(z.x, -z.y);
+      }
+#pragma unroll
+    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    fwd_batch<P>(v, Wr, tab, lane);
+    if (lane < S * P) {
+      const int s = lane / P, k1 = lane - s * P;
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = make_float2(v[k2].x, -v[k2].y);
+    }
+    __syncwarp();
+    // the law on the item's voxels, phase ids four at a time
+    for (int v0 = lane; v0 < nr * L; v0 += 4 * 32) {
+      uint8_t pid[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int vx = v0 + q * 32;
+        pid[q] = vx < nr * L ? phase[(long long)y0 * L + vx] : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int vx = v0 + q * 32;
+        if (vx >= nr * L) continue;
+        const int r = vx / L, x = vx - r * L;
+        float e[NC];
+        float* at[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int sl = r * NC + c;
+          at[c] = reinterpret_cast<float*>(Wr + (sl >> 1) * L + x) + (sl & 1);
+          e[c] = *at[c] * invN;
+        }
+        float e6[6];
+        comp_to6<NC>(e, e6);
+        const DevPhase ph = a.law.ph[pid[q]];
+        float ep[6] = {0, 0, 0, 0, 0, 0};
+        LawOut o;
+        stress6<false>(e6, ph, ep, 0.f, o);
+        if (FINAL) {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
+        } else {
+          const float tr = e6[0] + e6[1] + e6[2];
+          float tau6[6];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (d.lam0 * tr + 2.f * d.mu0 * e6[i]);
+#pragma unroll
+          for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * d.mu0 * e6[i];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) *at[c] = tau6[comp6<NC>(c)];
+        }
+      }
+    }
+    if (FINAL) {
+      __syncwarp();   // the next item zeroes the region
+      continue;
+    }
+    // an odd line count leaves the last sequence's imaginary carrier unused: zero it
+    if (nl & 1)
+      for (int x = lane; x < L; x += 32) Wr[(nseq - 1) * L + x].y = 0.f;
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) v[s * P + n1] = Wr[s * L + 32 * n1 + lane];
+#pragma unroll
+    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    fwd_batch<P>(v, Wr, tab, lane);
+    if (lane < S * P) {
+      const int s = lane / P, k1 = lane - s * P;
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = v[k2];
+    }
+    __syncwarp();
+    for (int u = lane; u < nl * Kx; u += 32) {
+      const int sl = fdiv(u, d.dKx), j = u - sl * Kx;
+      const int k = sh.kxs[j];
+      const float2* z = Wr + (sl >> 1) * L;
+      const float2 zk = z[k], zm = z[k == 0 ? 0 : L - k];
+      float2 out;
+      if ((sl & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      Tg[sl * Kx + j] = out;
+    }
+    __syncwarp();
+  }
+}
+
+// Green step at the RVE's half-pattern entries (chunks of 256, one thread per entry), ER
+// updated, squared-increment measure summed as kb_gamma and kb_decide sum it; the sum is
+// valid in thread 0
+__device__ __noinline__ double res_green(const BArgs& a, const BDesc& d, int r, const float2* T,
+                            ResShared& sh) {
+  const int NCK = NC * d.Kx;
+  float2* ER = a.ER + d.off_er;
+  const double* ebar = a.st[r].ebar;
+  double s = 0.0;
+  for (int ch = 0; ch < d.chunks; ++ch) {
+    const int h = ch * kResThreads + threadIdx.x;
+    float diff = 0.f;
+    if (h < d.Kh) {
+      const HIdx hi = a.hidx[d.off_h + h];
+      const float4 n = a.hn[d.off_h + h];
+      const long long base = (long long)hi.iy * NCK + hi.j;
+      float2 tv[NC], old[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        tv[c] = T[base + c * d.Kx];
+        old[c] = ER[base + c * d.Kx];
+      }
+      float er[NC], ei[NC];
+      green_update<NC>(hi.kind, n, tv, ebar, (double)d.N, d.inv2mu0, d.cgam, er, ei);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const float dr = er[c] - old[c].x, di = ei[c] - old[c].y;
+        const float wc = (comp6<NC>(c) >= 3) ? 2.f : 1.f;
+        diff = fmaf(n.w * wc, dr * dr + di * di, diff);
+        ER[base + c * d.Kx] = make_float2(er[c], ei[c]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
+    if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = (double)diff;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < kResWarps; ++k) t += sh.red[k];
+      s += t;
+    }
+    __syncthreads();
+  }
+  return s;
+}
+
+// the decision of kb_decide for one RVE (thread 0)
+__device__ bool res_decide(const BArgs& a, int r, double s) {
+  BStat& st = a.st[r];
+  double rr = sqrt(s * st.inv_n2);
+  if (st.enorm > 0.0) rr /= st.enorm;
+  st.iters += 1;
+  st.last_r = rr;
+  st.rmin = fmin(st.rmin, rr);
+  if (!isfinite(rr)) {
+    st.nonfinite = 1;
+    st.done = 1;
+  } else if (rr > kDivergeRatio * st.rmin && rr > kDivergeFloor) {
+    st.diverged = 1;
+    st.done = 1;
+  } else if (rr < st.tol || st.iters >= st.max_iter) {
+    st.done = 1;
+  }
+  if (st.done) atomicAdd(a.n_done, 1);
+  return st.done != 0;
+}
+
+template <int P>
+__device__ __noinline__ void res_solve(const BArgs& a, int r, const BDesc& d, float2* T, float2* Wr,
+                          ResShared& sh) {
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (;;) {
+    res_inv_y<P>(a, d, T, Wr, sh, lane, wp);
+    __syncthreads();
+    res_rows<P, false>(a, d, T, Wr, sh, lane, wp, nullptr);
+    __syncthreads();
+    res_fwd_y<P>(a, d, T, Wr, sh, lane, wp);
+    __syncthreads();
+    const double s = res_green(a, d, r, T, sh);
+    if (threadIdx.x == 0) sh.done = res_decide(a, r, s) ? 1 : 0;
+    __syncthreads();
+    if (sh.done) break;
+  }
+  // final pass: fields of the converged coefficients, homogenised stress
+  res_inv_y<P>(a, d, T, Wr, sh, lane, wp);
+  __syncthreads();
+  double sb[6] = {0, 0, 0, 0, 0, 0};
+  res_rows<P, true>(a, d, T, Wr, sh, lane, wp, sb);
+  __syncthreads();
+  for (int i = 0; i < 6; ++i) {
+    const double t = block_sum_d(sb[i], sh.red);
+    if (threadIdx.x == 0) a.st[r].sbar[i] = t / (double)d.N;
+  }
+}
+
+// whole solves of the RVEs order[0 .. n_order) (square, sides 64, 96, 128, 192 or 256), a
+// block per RVE at a time from the queue counter; T slots of slot float2 per block
+__global__ __launch_bounds__(kResThreads, 2) void kb_resident(BArgs a, const int* order,
+                                                              int n_order, unsigned* queue,
+                                                              float2* scratch, long long slot) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ResShared sh;
+  float2* Wr = reinterpret_cast<float2*>(smem) + (size_t)(threadIdx.x >> 5) * kWRegion;
+  float2* T = scratch + (long long)blockIdx.x * slot;
+  for (;;) {
+    if (threadIdx.x == 0) sh.next = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int q = sh.next;
+    if (q >= n_order) break;
+    const int r = order[q];
+    const BDesc d = a.d[r];
+    for (int i = threadIdx.x; i < d.Kx; i += kResThreads) sh.kxs[i] = a.kx[d.off_kx + i];
+    for (int i = threadIdx.x; i < d.ny; i += kResThreads) sh.inv_ky[i] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < d.Ky; i += kResThreads) sh.inv_ky[a.kym[d.off_ky + i]] = i;
+    __syncthreads();
+    switch (d.nx) {
+      case 64: res_solve<2>(a, r, d, T, Wr, sh); break;
+      case 96: res_solve<3>(a, r, d, T, Wr, sh); break;
+      case 128: res_solve<4>(a, r, d, T, Wr, sh); break;
+      case 192: res_solve<6>(a, r, d, T, Wr, sh); break;
+      default: res_solve<8>(a, r, d, T, Wr, sh); break;
+    }
+    __syncthreads();   // sh is rewritten for the next RVE
+  }
+}
+
 __global__ __launch_bounds__(256) void kb_row(BArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[8];
@@ -1269,6 +1636,14 @@ struct rf_batch {
   unsigned* d_counter = nullptr;   // finished blocks of the decision kernel
   long long launches = 0;
   int last_max_iters = 0;
+  // RVE-resident solve (kb_resident): every RVE square with a side of 64, 96, 128, 192 or 256
+  bool res_ok = false;             // the batch qualifies
+  int resident = 0;                // 1: solves run as kb_resident
+  int res_grid = 0;
+  long long res_slot = 0;          // float2 per block's line-transform slot
+  int* d_order = nullptr;          // RVEs, largest first
+  unsigned* d_queue = nullptr;
+  float2* d_scratch = nullptr;
 };
 
 using namespace rfk;
@@ -1623,12 +1998,12 @@ int graph_for(rf_batch* b, int chunk, cudaGraphExec_t* out) {
   return RF_OK;
 }
 
-int set_status(rf_batch* b, const double* macro) {
+int set_status(rf_batch* b, const double* macro, int max_iter = 0) {
   for (int r = 0; r < b->n; ++r) {
     BStat& s = b->h_stat[r];
     std::memset(&s, 0, sizeof(s));
-    s.max_iter = b->opt.max_iter;
-    s.tol = b->opt.tol;
+    s.max_iter = max_iter > 0 ? max_iter : b->opt.max_iter;
+    s.tol = max_iter > 0 ? 0.0 : b->opt.tol;
     const double* m = macro + 6 * r;
     for (int i = 0; i < 6; ++i) s.ebar[i] = m[i];
     s.enorm = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] +
@@ -1674,6 +2049,19 @@ int iterate(rf_batch* b) {
   return RF_OK;
 }
 
+constexpr size_t kResSmem = (size_t)kResWarps * kWRegion * sizeof(float2);
+
+// every RVE's whole solve (updates and final pass) in one kb_resident launch
+int launch_resident(rf_batch* b) {
+  cudaError_t e = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream);
+  if (e != cudaSuccess) return bfail(e, "batch resident");
+  kb_resident<<<b->res_grid, kResThreads, kResSmem, b->stream>>>(
+      batch_args(b, -1), b->d_order, b->n, b->d_queue, b->d_scratch, b->res_slot);
+  b->launches += 1;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? RF_OK : bfail(e, "batch resident");
+}
+
 int run_solve(rf_batch* b, const double* macro, bool use_warm, const float2* pwarm = nullptr) {
   if (int e = set_status(b, macro)) return e;
   BArgs a = batch_args(b, -1);
@@ -1681,6 +2069,10 @@ int run_solve(rf_batch* b, const double* macro, bool use_warm, const float2* pwa
                                        pwarm);
   b->launches += 1;
   if (cudaGetLastError() != cudaSuccess) return bfail(cudaGetLastError(), "batch init");
+  if (b->resident) {
+    b->last_while = false;
+    return launch_resident(b);
+  }
   return iterate(b);
 }
 
@@ -1777,6 +2169,38 @@ int autotune(rf_batch* b, const double* macro) {
     }
     b->grid = sms * bestG;
   }
+  // options.batch_resident: -1 never, 1 always (where the batch qualifies), 0 the faster of a
+  // three-update solve each way (the sweeps without their final pass, the resident kernel with)
+  b->resident = 0;
+  if (!err && b->res_ok && b->opt.batch_resident > 0) b->resident = 1;
+  if (!err && b->res_ok && b->opt.batch_resident == 0) {
+    auto time_solve = [&](bool res, float* ms) -> int {
+      *ms = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if (int e = set_status(b, macro, 3)) return e;
+        cudaEventRecord(e0, b->stream);
+        kb_init<<<b->n, 256, 0, b->stream>>>(batch_args(b, -1), b->n, nullptr, b->d_warm_off,
+                                             nullptr);
+        if (res) {
+          if (int e = launch_resident(b)) return e;
+        } else {
+          for (int i = 0; i < 3; ++i)
+            if (int e = launch_update(b)) return e;
+        }
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess)
+          return bfail(cudaGetLastError(), "batch tuner");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        *ms = std::min(*ms, t);
+      }
+      return RF_OK;
+    };
+    float t_sweep = 0.f, t_res = 0.f;
+    err = time_solve(false, &t_sweep);
+    if (!err) err = time_solve(true, &t_res);
+    if (!err) b->resident = t_res < t_sweep ? 1 : 0;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return err;
@@ -1785,18 +2209,21 @@ int autotune(rf_batch* b, const double* macro) {
 // final pass: fields of the converged coefficients -> homogenised stresses; per-RVE outputs
 int finish_solve(rf_batch* b, double* hom_stress, int32_t* iters, double* residuals,
                  int32_t* status) {
-  // final pass: fields of the converged coefficients -> homogenised stresses
-  BArgs a0 = batch_args(b, 0);
-  a0.final_pass = 1;
-  if (b->n_items[0] > 0) kb_inv_y<<<b->grid, 256, b->col_smem, b->stream>>>(a0);
-  launch_warp_cols(b, +1, true);
-  BArgs a1 = batch_args(b, 1);
-  a1.final_pass = 1;
-  if (b->n_items[1] > 0) kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
-  launch_warp_rows(b, true);
-  kb_sbar<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
-  b->launches += 1 + (b->n_items[0] > 0 ? 1 : 0) + warp_col_kernels(b) +
-                 (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b);
+  // final pass: fields of the converged coefficients -> homogenised stresses (kb_resident
+  // ran its own)
+  if (!b->resident) {
+    BArgs a0 = batch_args(b, 0);
+    a0.final_pass = 1;
+    if (b->n_items[0] > 0) kb_inv_y<<<b->grid, 256, b->col_smem, b->stream>>>(a0);
+    launch_warp_cols(b, +1, true);
+    BArgs a1 = batch_args(b, 1);
+    a1.final_pass = 1;
+    if (b->n_items[1] > 0) kb_row<<<b->grid, 256, b->row_smem, b->stream>>>(a1);
+    launch_warp_rows(b, true);
+    kb_sbar<<<(b->n + 255) / 256, 256, 0, b->stream>>>(batch_args(b, -1), b->n);
+    b->launches += 1 + (b->n_items[0] > 0 ? 1 : 0) + warp_col_kernels(b) +
+                   (b->n_items[1] > 0 ? 1 : 0) + warp_row_kernels(b);
+  }
   cudaError_t e = cudaMemcpyAsync(b->h_stat, b->d_stat, sizeof(BStat) * b->n,
                                   cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1854,9 +2281,11 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
   if ((opt->transform != RF_TRANSFORM_DFT && opt->transform != RF_TRANSFORM_FFT) ||
       opt->precision != RF_PREC_FP32 || opt->max_iter < 1 || !(opt->tol >= 0.0) ||
       (opt->green != 0 && opt->green != 1) ||
-      (opt->ref_medium != RF_REF_MINMAX && opt->ref_medium != RF_REF_VOLUME)) {
+      (opt->ref_medium != RF_REF_MINMAX && opt->ref_medium != RF_REF_VOLUME) ||
+      opt->batch_resident < -1 || opt->batch_resident > 1) {
     set_error("rf_batch_create: options must select FP32 precision, the DFT or FFT transform, "
-              "tol >= 0, max_iter >= 1 and a known Green operator and reference medium");
+              "tol >= 0, max_iter >= 1, a known Green operator and reference medium, and "
+              "batch_resident -1, 0 or 1");
     return RF_ERR_INVALID;
   }
   rf_batch* b = new rf_batch();
@@ -2129,6 +2558,26 @@ int rf_batch_create(rf_batch** out, int32_t n_rve, const rf_grid* grids,
           (const void*)kb_y_w<8, -1>})
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     cudaFuncSetAttribute(kb_fwd_y, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    // the RVE-resident solve: square RVEs with sides of the warp-FFT lengths
+    b->res_ok = b->use_fft && opt->batch_resident >= 0;
+    long long slot = 0;
+    for (const BDesc& d : b->desc) {
+      if (d.nx != d.ny || warp_rows(d.nx) == 0) b->res_ok = false;
+      slot = std::max(slot, (long long)d.ny * NC * d.Kx);
+    }
+    if (b->res_ok) {
+      cudaFuncSetAttribute(kb_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kResSmem);
+      int sms = 152, per_sm = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_resident, kResThreads, kResSmem);
+      b->res_grid = sms * std::max(1, per_sm);
+      b->res_slot = (slot + 1) & ~1LL;   // 16-byte aligned slots
+      if (!err) err = balloc(&b->d_order, order.size(), "batch queue");
+      up(b->d_order, order.data(), sizeof(int) * order.size());
+      if (!err) err = balloc(&b->d_queue, 1, "batch queue");
+      if (!err) err = balloc(&b->d_scratch, (size_t)b->res_grid * b->res_slot, "batch scratch");
+    }
   }
   if (!err) {
     std::vector<double> macro0(6 * (size_t)n_rve, 0.0);
@@ -2285,6 +2734,15 @@ int rf_batch_info(const rf_batch* b, int64_t* kernel_launches, int32_t* rows_per
   return RF_OK;
 }
 
+int rf_batch_mode(const rf_batch* b, int32_t* resident) {
+  if (!b || !resident) {
+    set_error("rf_batch_mode: null argument");
+    return RF_ERR_INVALID;
+  }
+  *resident = b->resident;
+  return RF_OK;
+}
+
 int rf_batch_destroy(rf_batch* b) {
   if (!b) return RF_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -2308,6 +2766,9 @@ int rf_batch_destroy(rf_batch* b) {
   cudaFree(b->d_counter);
   cudaFree(b->d_warm);
   cudaFree(b->d_warm_off);
+  cudaFree(b->d_order);
+  cudaFree(b->d_queue);
+  cudaFree(b->d_scratch);
   for (int s = 0; s < 6; ++s) cudaFree(b->d_items[s]);
   if (b->h_stat) cudaFreeHost(b->h_stat);
   if (b->h_ndone) cudaFreeHost(b->h_ndone);

@@ -38,7 +38,8 @@ class rf_options(C.Structure):
                 ("transform", C.c_int32), ("fft_rows", C.c_int32), ("fft_cols", C.c_int32),
                 ("fft_fuse", C.c_int32), ("fft_fuse_kx", C.c_int32),
                 ("fft_row_blocks", C.c_int32), ("wait_limit", C.c_int64),
-                ("stall_test", C.c_int32), ("fft_row_warps", C.c_int32)]
+                ("stall_test", C.c_int32), ("fft_row_warps", C.c_int32),
+                ("batch_resident", C.c_int32)]
 
 
 class rf_info(C.Structure):
@@ -109,6 +110,7 @@ def _load() -> C.CDLL:
         "rf_batch_solve": [P, P, P, P, P, P, P],
         "rf_batch_info": [P, P, P, P],
         "rf_batch_destroy": [P],
+        "rf_batch_mode": [P, P],
         "rf_set_tracing": [P, i32],
         "rf_get_stage_times": [P, P, P],
         "rf_reset_stage_times": [P],
@@ -149,7 +151,7 @@ EXPORTED = ["rf_create", "rf_set_phase_map", "rf_set_phase_map_device", "rf_set_
             "rf_pattern_adapted", "rf_pattern_radial", "rf_last_error", "rf_set_tracing",
             "rf_get_stage_times", "rf_reset_stage_times", "rf_pattern_adapted_noalloc",
             "rf_batch_create", "rf_batch_solve", "rf_batch_info", "rf_batch_destroy",
-            "rf_batch_slots", "rf_batch_descriptors", "rf_batch_reduced_strain",
+            "rf_batch_mode", "rf_batch_slots", "rf_batch_descriptors", "rf_batch_reduced_strain",
             "rf_batch_solve_warm", "rf_compat", "rf_stress_errors", "rf_solve_mixed",
             "rf_law_sweep",
             "rf_solve_path_mixed",
@@ -207,7 +209,7 @@ def make_phases(table) -> C.Array:
 def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precision="fp32",
                  check_every=0, transform="dft", fft_rows=0, fft_cols=0, fft_fuse=0,
                  fft_fuse_kx=0, fft_row_blocks=0, wait_limit=0, stall_test=0,
-                 fft_row_warps=0) -> rf_options:
+                 fft_row_warps=0, batch_resident=0) -> rf_options:
     o = rf_options()
     o.tol, o.max_iter = float(tol), int(max_iter)
     o.green, o.ref_medium = GREEN[green], REF[ref]
@@ -218,6 +220,7 @@ def make_options(tol=1e-6, max_iter=1000, green="rotated", ref="minmax", precisi
     o.fft_row_blocks = int(fft_row_blocks)
     o.wait_limit, o.stall_test = int(wait_limit), int(stall_test)
     o.fft_row_warps = int(fft_row_warps)
+    o.batch_resident = int(batch_resident)
     return o
 
 
@@ -453,7 +456,10 @@ class BatchSolver:
         r = np.zeros(5, np.int32)
         g = C.c_int32(0)
         _check(lib.rf_batch_info(self.b, C.byref(n), _ptr(r), C.byref(g)), allow_nc=False)
-        return dict(kernel_launches=n.value, rows_per_item=[int(x) for x in r], grid=g.value)
+        m = C.c_int32(0)
+        _check(lib.rf_batch_mode(self.b, C.byref(m)), allow_nc=False)
+        return dict(kernel_launches=n.value, rows_per_item=[int(x) for x in r], grid=g.value,
+                    resident=bool(m.value))
 
 
     # --- learned warm start hooks (include/rf_mlp.h); device buffers are torch CUDA tensors

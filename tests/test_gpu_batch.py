@@ -106,13 +106,15 @@ def half_order(pat):
     return sorted((int(k[0]), int(k[1])) for k in pat if k[0] >= 0)
 
 
-@pytest.mark.parametrize("transform,warps", [("fft", -1), ("fft", 2), ("dft", 0)])
-def test_batch_reduced_coefficients_match_oracle_at_full_sizes(lib, transform, warps):
+@pytest.mark.parametrize("transform,warps,resident", [("fft", -1, -1), ("fft", 2, -1),
+                                                      ("dft", 0, -1), ("fft", 0, 1)])
+def test_batch_reduced_coefficients_match_oracle_at_full_sizes(lib, transform, warps, resident):
     """Sides 64, 96, 128, 192 and 256 (the FE-FFT population's sizes: radix-2 and radix-3 FFT
     items along x and y, on shared memory (warps -1) or as warp-FFT row and column items with
-    2, 3, 4, 6 and 8 points per lane (warps 2), or pruned-DFT items), a fixed number of
-    updates, every reduced strain coefficient compared with the oracle's (relative L2 per RVE
-    <= 1e-5), and the homogenised stress (<= 1e-6)."""
+    2, 3, 4, 6 and 8 points per lane (warps 2), or pruned-DFT items, or the RVE-resident solve
+    (resident 1: a block per RVE for all its updates, the same warp-FFT transforms)), a fixed
+    number of updates, every reduced strain coefficient compared with the oracle's (relative
+    L2 per RVE <= 1e-5), and the homogenised stress (<= 1e-6)."""
     ph = elastic_phases()
     pms, pats, macros = [], [], []
     for i, side in enumerate((64, 96, 128, 192, 256)):
@@ -122,13 +124,14 @@ def test_batch_reduced_coefficients_match_oracle_at_full_sizes(lib, transform, w
         macros.append(c["macro"])
     macros = np.array(macros)
     b = lib.BatchSolver(pms, ph, pats, tol=0.0, max_iter=4, transform=transform,
-                        fft_row_warps=warps)
+                        fft_row_warps=warps, batch_resident=resident)
     out = b.rf_batch_solve(macros)
     info = b.rf_batch_info()
     coeffs = b.rf_batch_reduced_strain().cpu().numpy()
     _, off = b.rf_batch_slots()
     b.close()
     assert np.all(out["iters"] == 4)
+    assert info["resident"] == (resident > 0)
     if warps > 0:
         assert list(info["rows_per_item"]) == [85, 53, 42, 26, 21]
     elif transform == "fft":
@@ -175,3 +178,82 @@ def test_batch_reports_divergence_and_non_finite_input(lib):
         s.rf_solve(macro[1])
     assert e.value.code == -4
     s.close()
+
+
+def c4_population(n, seed_index=0):
+    pms, pats, macros = [], [], []
+    for i in range(n):
+        side = (64, 96, 128, 192, 256)[i % 5]
+        c = make_config("c4", n=side, index=seed_index + i)
+        pms.append(c["phase_map"])
+        pats.append(O.pattern_adapted(c["phase_map"], 1, c["k_target"]))
+        macros.append(c["macro"])
+    return pms, pats, np.array(macros)
+
+
+def test_batch_resident_solve_matches_sweeps(lib):
+    """The RVE-resident solve against the sweep kernels on the same 10 RVEs (sides 64 to 256):
+    the same updates and convergence rules, so iteration counts within one and homogenised
+    stresses within 2e-6; a warm start from the converged coefficients (device export mapped
+    to the host warm layout) converges in at most 2 updates; a re-solve repeats the first."""
+    ph = elastic_phases()
+    pms, pats, macros = c4_population(10, seed_index=70)
+    sw = lib.BatchSolver(pms, ph, pats, tol=1e-6, max_iter=500, transform="fft",
+                         batch_resident=-1)
+    ref = sw.rf_batch_solve(macros)
+    assert not sw.rf_batch_info()["resident"]
+    sw.close()
+    b = lib.BatchSolver(pms, ph, pats, tol=1e-6, max_iter=500, transform="fft",
+                        batch_resident=1)
+    assert b.rf_batch_info()["resident"]
+    out = b.rf_batch_solve(macros)
+    assert out["converged"] and np.all(out["status"] == 0)
+    assert np.all(np.abs(out["iters"].astype(int) - ref["iters"].astype(int)) <= 1)
+    for i in range(len(pms)):
+        assert rel(out["sigma_bar"][i], ref["sigma_bar"][i]) <= 2e-6, i
+    coeffs = b.rf_batch_reduced_strain().cpu().numpy()
+    _, off = b.rf_batch_slots()
+    warm = []
+    for i, pat in enumerate(pats):
+        at = {k: p for p, k in enumerate(half_order(pat))}
+        w = np.zeros((len(pat), 6, 2), np.float32)
+        for p, k in enumerate(pat):
+            key = (int(k[0]), int(k[1]))
+            if key in at:
+                c = coeffs[off[i] + at[key]]
+                for a, comp in ((0, 0), (1, 1), (5, 2)):   # Voigt 11, 22, 12
+                    w[p, a] = c[comp]
+        warm.append(w if i % 2 == 0 else None)
+    hot = b.rf_batch_solve(macros, warm=warm)
+    again = b.rf_batch_solve(macros)
+    b.close()
+    for i in range(len(pms)):
+        if warm[i] is not None:
+            assert hot["iters"][i] <= 2 < out["iters"][i], i
+        else:
+            assert hot["iters"][i] == out["iters"][i], i
+        assert rel(hot["sigma_bar"][i], out["sigma_bar"][i]) <= 2e-6, i
+    assert np.array_equal(again["sigma_bar"], out["sigma_bar"])
+    assert np.array_equal(again["iters"], out["iters"])
+
+
+def test_batch_resident_mode_selection(lib):
+    """batch_resident: 1 where every RVE is square with a warp-FFT side, else the sweeps; -1
+    never; values outside -1..1 are rejected; the DFT transform never runs resident."""
+    ph = elastic_phases()
+    pms, pats, macros = c4_population(3, seed_index=90)
+    for opt, want in ((1, True), (-1, False)):
+        b = lib.BatchSolver(pms, ph, pats, tol=1e-6, max_iter=50, transform="fft",
+                            batch_resident=opt)
+        assert b.rf_batch_info()["resident"] == want
+        b.close()
+    b = lib.BatchSolver(pms, ph, pats, tol=1e-6, max_iter=50, transform="dft", batch_resident=1)
+    assert not b.rf_batch_info()["resident"]
+    b.close()
+    small, spats, _ = population(2)                     # sides 16 and 24: not eligible
+    b = lib.BatchSolver(small + pms, ph, spats + pats, tol=1e-6, max_iter=50, transform="fft",
+                        batch_resident=1)
+    assert not b.rf_batch_info()["resident"]
+    b.close()
+    with pytest.raises(lib.RFError):
+        lib.BatchSolver(pms, ph, pats, transform="fft", batch_resident=2)
