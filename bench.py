@@ -79,6 +79,8 @@ def parse():
                         "pattern study on the paper-shaped inputs of Sec. 5 (256^2, 256^3); "
                         "sweep: the unfused constitutive sweep alone (4096^2)")
     p.add_argument("--rves", type=int, default=4096, help="c4 / c5: RVEs in the solved batch")
+    p.add_argument("--batch-resident", type=int, default=0, choices=[-1, 0, 1],
+                   help="c4: RVE-resident solve (1), sweep kernels (-1), or autotuned (0)")
     p.add_argument("--train", type=int, default=50000, help="c5: training RVEs")
     p.add_argument("--epochs", type=int, default=20, help="c5: training epochs")
     p.add_argument("--profile-updates", type=int, default=0,
@@ -313,7 +315,7 @@ def _timed(torch, stream, fn):
     return out, e0.elapsed_time(e1)
 
 
-def batch_summary(rf, torch, n, steps, warmup, sample_every=8):
+def batch_summary(rf, torch, n, steps, warmup, sample_every=8, resident=0):
     """c4: one batched solve of `n` RVEs (sides 64..256, K = 5 %) to 1e-6 vs the same RVEs solved
     one context at a time (every `sample_every`-th RVE, same FP32 FFT transforms)."""
     from synth.configs import elastic_phases, k_target
@@ -324,7 +326,8 @@ def batch_summary(rf, torch, n, steps, warmup, sample_every=8):
     sh = stream.cuda_stream
     pats = [rf.rf_pattern_adapted(pm, 1, k_target(0.05, pm.size), stream=sh) for pm in pms]
     ph = elastic_phases()
-    b = rf.BatchSolver(pms, ph, pats, stream=sh, tol=TOL, max_iter=2000, transform="fft")
+    b = rf.BatchSolver(pms, ph, pats, stream=sh, tol=TOL, max_iter=2000, transform="fft",
+                       batch_resident=resident)
     vox = np.array([pm.size for pm in pms], np.float64)
     for _ in range(warmup):
         b.rf_batch_solve(macros)
@@ -386,7 +389,8 @@ def batch_summary(rf, torch, n, steps, warmup, sample_every=8):
 
 
 def run_batch(args, rf, torch):
-    print(json.dumps(batch_summary(rf, torch, args.rves, args.steps, args.warmup)), flush=True)
+    print(json.dumps(batch_summary(rf, torch, args.rves, args.steps, args.warmup,
+                                   resident=args.batch_resident)), flush=True)
 
 
 def _c5_rves(seeds, side=128):

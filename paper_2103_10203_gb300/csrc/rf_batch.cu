@@ -460,16 +460,18 @@ __device__ __forceinline__ void dft32_regs(float2* v, int sign) {
   }
 }
 
-// Forward transforms (exp(-2 pi i k n / L), L = 32 P) of the S = 32 / P sequences a warp holds
-// (layout above); tab[t] = exp(+2 pi i t / L); T: the warp's region (32 rows of 33).
-template <int P>
-__device__ __forceinline__ void fwd_batch(float2* v, float2* T, const float2* __restrict__ tab,
-                                          int lane) {
-  constexpr int S = 32 / P;
+// Forward transforms (exp(-2 pi i k n / L), L = 32 P) of the first SU of the S = 32 / P
+// sequences a warp holds (layout above; the others are left as zeros); tab[t] = exp(+2 pi i t /
+// L); T: the warp's region (32 rows of 33), free again when after_transpose() runs (before the
+// 32-point DFTs).
+template <int P, int SU = 32 / P, class F>
+__device__ __forceinline__ void fwd_batch_cb(float2* v, float2* T, const float2* __restrict__ tab,
+                                             int lane, F&& after_transpose) {
+  static_assert(SU >= 1 && SU <= 32 / P, "sequences");
 #pragma unroll
-  for (int s = 0; s < S; ++s) dft_small<P>(v + s * P, -1);
+  for (int s = 0; s < SU; ++s) dft_small<P>(v + s * P, -1);
 #pragma unroll
-  for (int s = 0; s < S; ++s)
+  for (int s = 0; s < SU; ++s)
 #pragma unroll
     for (int k1 = 1; k1 < P; ++k1) {
       float2 w = __ldg(tab + k1 * lane);
@@ -478,12 +480,19 @@ __device__ __forceinline__ void fwd_batch(float2* v, float2* T, const float2* __
     }
   __syncwarp();
 #pragma unroll
-  for (int r = 0; r < S * P; ++r) T[r * 33 + lane] = v[r];
+  for (int r = 0; r < SU * P; ++r) T[r * 33 + lane] = v[r];
   __syncwarp();
 #pragma unroll
-  for (int n2 = 0; n2 < 32; ++n2) v[n2] = lane < S * P ? T[lane * 33 + n2] : make_float2(0.f, 0.f);
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = lane < SU * P ? T[lane * 33 + n2] : make_float2(0.f, 0.f);
   __syncwarp();
+  after_transpose();
   dft32_regs(v, -1);
+}
+
+template <int P>
+__device__ __forceinline__ void fwd_batch(float2* v, float2* T, const float2* __restrict__ tab,
+                                          int lane) {
+  fwd_batch_cb<P>(v, T, tab, lane, [] {});
 }
 
 // Row item with warp-resident FFTs (FINAL: homogenised-stress partials after the law). Sequence
@@ -743,112 +752,140 @@ __global__ __launch_bounds__(256, 2) void kb_row_w(BArgs a) {
 // the Green step with the FP64 measure (the chunked reduction of kb_gamma / kb_decide), and the
 // decision; then the final pass (homogenised stress). Block barriers separate the phases; no
 // block waits for another. The line transforms live in the block's scratch slot in global
-// memory, [Ny][NC Kx] (the RVE's working set, L2-resident while the block holds it).
+// memory, [Ny][NC Kx] (the RVE's working set, L2-resident while the block holds it); the RVE's
+// parameters, the phase table and the pattern's index maps sit in shared memory.
 
 constexpr int kResWarps = 8;
 constexpr int kResThreads = 32 * kResWarps;
 constexpr int kResMaxL = 256;
+constexpr int kResPhaseBytes = 640;   // a warp item's phase ids (at most 10 rows of 64, 5 of 128)
 
-struct ResShared {
-  int kxs[kResMaxL / 2 + 1];
-  int inv_ky[kResMaxL];   // position of ky (mod Ny) in the pattern's ky list, or -1
-  double red[kResWarps];
-  int next, done;
+struct ResCtx {
+  float2* T;            // the block's line transforms, [Ny][NC Kx]
+  float2* ER;           // the RVE's coefficients, [Ky][NC Kx]
+  const float2* tab;    // exp(2 pi i t / L)
+  const uint8_t* phase;
+  const HIdx* hidx;
+  const float4* hn;
+  BStat* st;
+  int Kx, Ky, Kh, NCK, chunks, pad;
+  FastDiv dKx;
+  float invN, lam0, mu0, inv2mu0, cgam, pad2;
+  double N;
 };
 
-// inverse y transforms (conjugate of the forward transform of the conjugate) of the NC Kx line
-// columns, S adjacent columns per warp: the pattern's ky rows of ER gathered straight into the
-// transform layout, all L rows written to T
-template <int P>
-__device__ __noinline__ void res_inv_y(const BArgs& a, const BDesc& d, float2* T, float2* Wr,
-                          const ResShared& sh, int lane, int wp) {
-  constexpr int L = 32 * P, S = 32 / P;
-  const int NCK = NC * d.Kx, groups = (NCK + S - 1) / S;
-  const float2* ER = a.ER + d.off_er;
-  const float2* tab = a.tab + d.tab_y;
-  for (int g = wp; g < groups; g += kResWarps) {
-    const int q0 = g * S, ns = min(S, NCK - q0);
-    float2 v[32];
-#pragma unroll
-    for (int n1 = 0; n1 < P; ++n1) {
-      const int i = sh.inv_ky[32 * n1 + lane];
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        float2 z = make_float2(0.f, 0.f);
-        if (i >= 0 && s < ns) z = ER[(long long)i * NCK + q0 + s];
-        v[s * P + n1] = make_float2(z.x, -z.y);
-      }
-    }
-#pragma unroll
-    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
-    fwd_batch<P>(v, Wr, tab, lane);
-    if (lane < S * P) {
-      const int s = lane / P, k1 = lane - s * P;
-      if (s < ns) {
-        float2* col = T + q0 + s;
-#pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2)
-          col[(long long)(k1 + P * k2) * NCK] = make_float2(v[k2].x, -v[k2].y);
-      }
-    }
-    __syncwarp();   // the region is the next group's transpose buffer
-  }
+struct ResShared {
+  ResCtx c;
+  DevPhase ph[kMaxPhases];
+  double sb[kResWarps][6];   // per-warp stress sums of the final pass
+  double red[kResWarps];
+  int kxs[kResMaxL / 2 + 1];
+  int inv_ky[kResMaxL];   // position of ky (mod Ny) in the pattern's ky list, or -1
+  int next, done;
+  __align__(16) uint8_t phs[kResWarps][kResPhaseBytes];
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+// 8 bytes, zero-filled when bytes = 0 (nothing is read then)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// forward y transforms of the line columns of T (all L rows), the pattern's ky rows written
-// back in place: row i of T holds the i-th ky of the list afterwards
+// y transforms of the NC Kx line columns, S adjacent columns per warp. Inverse (conjugate of the
+// forward transform of the conjugate): the pattern's ky rows of ER gathered straight into the
+// transform layout, all L rows written to T. Forward: all L rows of T, the pattern's ky rows
+// written back in place (row i of T holds the i-th ky of the list afterwards).
 template <int P>
-__device__ __noinline__ void res_fwd_y(const BArgs& a, const BDesc& d, float2* T, float2* Wr,
-                          const ResShared& sh, int lane, int wp) {
+__device__ __noinline__ void res_cols(ResShared& sh, float2* Wr, int lane, int wp, bool inverse) {
   constexpr int L = 32 * P, S = 32 / P;
-  const int NCK = NC * d.Kx, groups = (NCK + S - 1) / S;
-  const float2* tab = a.tab + d.tab_y;
+  const ResCtx& c = sh.c;
+  const int NCK = c.NCK, groups = (NCK + S - 1) / S;
+  const float cj = inverse ? -1.f : 1.f;
+  const float2* src = inverse ? c.ER : c.T;
+  float2* T = c.T;
+  const float2* tab = c.tab;
+  // group g's inputs into the region at s L + y by asynchronous copies (zero where the column
+  // or the pattern row is absent); the next group's are issued once the transpose has read the
+  // region, so they arrive while the 32-point DFTs and the stores run
+  auto stage = [&](int g) {
+    const int q0 = g * S, ns = min(S, NCK - q0);
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) {
+      const int y = 32 * n1 + lane;
+      const int row = inverse ? sh.inv_ky[y] : y;
+      const float2* p = src + (long long)max(row, 0) * NCK + q0;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const bool ok = row >= 0 && s < ns;
+        cp_async8(Wr + s * L + y, ok ? p + s : src, ok ? 8 : 0);
+      }
+    }
+  };
+  if (wp < groups) stage(wp);
   for (int g = wp; g < groups; g += kResWarps) {
     const int q0 = g * S, ns = min(S, NCK - q0);
+    cp_async_wait_all();
+    __syncwarp();
     float2 v[32];
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
-      for (int n1 = 0; n1 < P; ++n1)
-        v[s * P + n1] = s < ns ? T[(long long)(32 * n1 + lane) * NCK + q0 + s]
-                               : make_float2(0.f, 0.f);
+      for (int n1 = 0; n1 < P; ++n1) {
+        const float2 z = Wr[s * L + 32 * n1 + lane];
+        v[s * P + n1] = make_float2(z.x, cj * z.y);
+      }
 #pragma unroll
     for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
-    fwd_batch<P>(v, Wr, tab, lane);
+    fwd_batch_cb<P>(v, Wr, tab, lane, [&] {
+      if (g + kResWarps < groups) stage(g + kResWarps);
+    });
     if (lane < S * P) {
       const int s = lane / P, k1 = lane - s * P;
       if (s < ns) {
         float2* col = T + q0 + s;
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
-          const int i = sh.inv_ky[k1 + P * k2];
-          if (i >= 0) col[(long long)i * NCK] = v[k2];
+          const int y = k1 + P * k2;
+          const int row = inverse ? y : sh.inv_ky[y];
+          if (row >= 0) col[(long long)row * NCK] = make_float2(v[k2].x, cj * v[k2].y);
         }
       }
     }
-    __syncwarp();
   }
 }
 
 // row passes: warp items of R_w = 2 S / 3 rows (3 R_w lines, packed in pairs into at most S
-// sequences), each warp on its own items; FINAL: homogenised-stress sums instead of the
-// forward transform
-template <int P, bool FINAL>
-__device__ __noinline__ void res_rows(const BArgs& a, const BDesc& d, float2* T, float2* Wr,
-                         const ResShared& sh, int lane, int wp, double* sb) {
-  constexpr int L = 32 * P, S = 32 / P, RW = (2 * S) / 3;
-  const int Kx = d.Kx, NCK = NC * Kx;
-  const float2* tab = a.tab + d.tab_x;
-  const uint8_t* phase = a.phase + d.off_phase;
-  const float invN = 1.f / (float)d.N;
+// sequences at a stride of L + P entries, which keeps the transform's scattered writes free of
+// bank conflicts), each warp on its own items; one transform body for both directions. Final
+// pass: homogenised-stress sums per warp instead of the forward transform.
+template <int P>
+__device__ __noinline__ void res_rows(ResShared& sh, float2* Wr, int lane, int wp, bool final) {
+  constexpr int L = 32 * P, S = 32 / P, RW = (2 * S) / 3, LS = L + P;
+  constexpr int SU = (3 * RW + 1) / 2;   // sequences in use (3 of 4 at P = 8)
+  static_assert(S * LS <= kWRegion && RW * L <= kResPhaseBytes, "region");
+  const ResCtx& c = sh.c;
+  const int Kx = c.Kx, NCK = c.NCK;
+  const float2* tab = c.tab;
+  uint8_t* phs = sh.phs[wp];
   const int items = (L + RW - 1) / RW;
   for (int it = wp; it < items; it += kResWarps) {
     const int y0 = it * RW, nr = min(RW, L - y0), nl = nr * NC, nseq = (nl + 1) / 2;
-    for (int i = lane; i < S * L; i += 32) Wr[i] = make_float2(0.f, 0.f);
+    // the item's phase ids: asynchronous 16-byte copies, waited for before the law
+    for (int k = lane; k < nr * L / 16; k += 32)
+      cp_async16(phs + 16 * k, c.phase + (long long)y0 * L + 16 * k);
+    for (int i = lane; i < SU * LS; i += 32) Wr[i] = make_float2(0.f, 0.f);
     __syncwarp();
     // z_p = line 2p + i line 2p+1 (line s = r NC + c of the item): z[k] = ta + i tb,
     // z[L - k] = conj(ta) + i conj(tb)
-    float2* Tg = T + (long long)y0 * NCK;
+    float2* Tg = c.T + (long long)y0 * NCK;
     for (int u0 = lane; u0 < nseq * Kx; u0 += 4 * 32) {
       float2 ta[4], tb[4];
       int jj[4], pp[4];
@@ -857,7 +894,7 @@ __device__ __noinline__ void res_rows(const BArgs& a, const BDesc& d, float2* T,
         const int u = u0 + q * 32;
         pp[q] = -1;
         if (u < nseq * Kx) {
-          const int p = fdiv(u, d.dKx), j = u - p * Kx;
+          const int p = fdiv(u, c.dKx), j = u - p * Kx;
           const int s0 = 2 * p, s1 = s0 + 1;
           ta[q] = Tg[s0 * Kx + j];
           tb[q] = s1 < nl ? Tg[s1 * Kx + j] : make_float2(0.f, 0.f);
@@ -874,136 +911,137 @@ __device__ __noinline__ void res_rows(const BArgs& a, const BDesc& d, float2* T,
           ta[q].y = 0.f;
           tb[q].y = 0.f;
         }
-        float2* z = Wr + pp[q] * L;
+        float2* z = Wr + pp[q] * LS;
         z[k] = make_float2(ta[q].x - tb[q].y, ta[q].y + tb[q].x);
         if (!self) z[L - k] = make_float2(ta[q].x + tb[q].y, tb[q].x - ta[q].y);
       }
     }
     __syncwarp();
-    float2 v[32];
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const float cj = pass == 0 ? -1.f : 1.f;   // pass 0: inverse, as the conjugate trick
+      float2 v[32];
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+      for (int s = 0; s < SU; ++s)
 #pragma unroll
-      for (int n1 = 0; n1 < P; ++n1) {
-        const float2 z = Wr[s * L + 32 * n1 + lane];
-        v[s * P + n1] = make_float2(z.x, -z.y);
-      }
-#pragma unroll
-    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
-    fwd_batch<P>(v, Wr, tab, lane);
-    if (lane < S * P) {
-      const int s = lane / P, k1 = lane - s * P;
-#pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = make_float2(v[k2].x, -v[k2].y);
-    }
-    __syncwarp();
-    // the law on the item's voxels, phase ids four at a time
-    for (int v0 = lane; v0 < nr * L; v0 += 4 * 32) {
-      uint8_t pid[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int vx = v0 + q * 32;
-        pid[q] = vx < nr * L ? phase[(long long)y0 * L + vx] : 0;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int vx = v0 + q * 32;
-        if (vx >= nr * L) continue;
-        const int r = vx / L, x = vx - r * L;
-        float e[NC];
-        float* at[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const int sl = r * NC + c;
-          at[c] = reinterpret_cast<float*>(Wr + (sl >> 1) * L + x) + (sl & 1);
-          e[c] = *at[c] * invN;
+        for (int n1 = 0; n1 < P; ++n1) {
+          const float2 z = Wr[s * LS + 32 * n1 + lane];
+          v[s * P + n1] = make_float2(z.x, cj * z.y);
         }
-        float e6[6];
-        comp_to6<NC>(e, e6);
-        const DevPhase ph = a.law.ph[pid[q]];
-        float ep[6] = {0, 0, 0, 0, 0, 0};
-        LawOut o;
-        stress6<false>(e6, ph, ep, 0.f, o);
-        if (FINAL) {
 #pragma unroll
-          for (int i = 0; i < 6; ++i) sb[i] += (double)o.s[i];
-        } else {
-          const float tr = e6[0] + e6[1] + e6[2];
-          float tau6[6];
+      for (int r = SU * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+      fwd_batch_cb<P, SU>(v, Wr, tab, lane, [] {});
+      if (lane < SU * P) {
+        const int s = lane / P, k1 = lane - s * P;
 #pragma unroll
-          for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (d.lam0 * tr + 2.f * d.mu0 * e6[i]);
+        for (int k2 = 0; k2 < 32; ++k2)
+          Wr[s * LS + k1 + P * k2] = make_float2(v[k2].x, cj * v[k2].y);
+      }
+      __syncwarp();
+      if (pass == 1) break;
+      cp_async_wait_all();
+      __syncwarp();
+      // the law on the item's voxels, two rows at a time: rows 2m and 2m + 1 hold lines
+      // 6m .. 6m + 5, i.e. whole sequences 3m, 3m + 1 and 3m + 2 (read and written as float2);
+      // a missing row 2m + 1 leaves zeros in its carriers
+      double s6[6] = {0, 0, 0, 0, 0, 0};
+      for (int vx = lane; vx < (nr + 1) / 2 * L; vx += 32) {
+        const int m = vx / L, x = vx - m * L;
+        const bool two = 2 * m + 1 < nr;
+        float2* zA = Wr + 3 * m * LS + x;
+        const float2 A = zA[0], B = zA[LS];
+        const float2 Cz = two ? zA[2 * LS] : make_float2(0.f, 0.f);
+        const float ev[2][NC] = {{A.x, A.y, B.x}, {B.y, Cz.x, Cz.y}};
+        float tv[2][NC] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
-          for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * d.mu0 * e6[i];
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          float e[NC];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) *at[c] = tau6[comp6<NC>(c)];
+          for (int cc = 0; cc < NC; ++cc) e[cc] = ev[h][cc] * c.invN;
+          float e6[6];
+          comp_to6<NC>(e, e6);
+          const DevPhase ph = sh.ph[phs[(2 * m + h) * L + x]];
+          float ep[6] = {0, 0, 0, 0, 0, 0};
+          LawOut o;
+          stress6<false>(e6, ph, ep, 0.f, o);
+          if (final) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) s6[i] += (double)o.s[i];
+          } else {
+            const float tr = e6[0] + e6[1] + e6[2];
+            float tau6[6];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (c.lam0 * tr + 2.f * c.mu0 * e6[i]);
+#pragma unroll
+            for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * c.mu0 * e6[i];
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) tv[h][cc] = tau6[comp6<NC>(cc)];
+          }
+        }
+        if (!final) {
+          zA[0] = make_float2(tv[0][0], tv[0][1]);
+          zA[LS] = make_float2(tv[0][2], tv[1][0]);
+          if (two) zA[2 * LS] = make_float2(tv[1][1], tv[1][2]);
         }
       }
-    }
-    if (FINAL) {
-      __syncwarp();   // the next item zeroes the region
-      continue;
-    }
-    // an odd line count leaves the last sequence's imaginary carrier unused: zero it
-    if (nl & 1)
-      for (int x = lane; x < L; x += 32) Wr[(nseq - 1) * L + x].y = 0.f;
-    __syncwarp();
+      if (final) {
 #pragma unroll
-    for (int s = 0; s < S; ++s)
+        for (int i = 0; i < 6; ++i) {
+          double t = s6[i];
 #pragma unroll
-      for (int n1 = 0; n1 < P; ++n1) v[s * P + n1] = Wr[s * L + 32 * n1 + lane];
-#pragma unroll
-    for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
-    fwd_batch<P>(v, Wr, tab, lane);
-    if (lane < S * P) {
-      const int s = lane / P, k1 = lane - s * P;
-#pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = v[k2];
+          for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+          if (lane == 0) sh.sb[wp][i] += t;
+        }
+        break;
+      }
+      __syncwarp();
     }
-    __syncwarp();
-    for (int u = lane; u < nl * Kx; u += 32) {
-      const int sl = fdiv(u, d.dKx), j = u - sl * Kx;
-      const int k = sh.kxs[j];
-      const float2* z = Wr + (sl >> 1) * L;
-      const float2 zk = z[k], zm = z[k == 0 ? 0 : L - k];
-      float2 out;
-      if ((sl & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-      else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-      Tg[sl * Kx + j] = out;
+    if (!final) {
+      for (int u = lane; u < nl * Kx; u += 32) {
+        const int sl = fdiv(u, c.dKx), j = u - sl * Kx;
+        const int k = sh.kxs[j];
+        const float2* z = Wr + (sl >> 1) * LS;
+        const float2 zk = z[k], zm = z[k == 0 ? 0 : L - k];
+        float2 out;
+        if ((sl & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        else out = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        Tg[sl * Kx + j] = out;
+      }
     }
-    __syncwarp();
+    __syncwarp();   // the next item rewrites the region and the phase bytes
   }
 }
 
 // Green step at the RVE's half-pattern entries (chunks of 256, one thread per entry), ER
 // updated, squared-increment measure summed as kb_gamma and kb_decide sum it; the sum is
 // valid in thread 0
-__device__ __noinline__ double res_green(const BArgs& a, const BDesc& d, int r, const float2* T,
-                            ResShared& sh) {
-  const int NCK = NC * d.Kx;
-  float2* ER = a.ER + d.off_er;
-  const double* ebar = a.st[r].ebar;
+__device__ __noinline__ double res_green(ResShared& sh) {
+  const ResCtx& c = sh.c;
+  const int NCK = c.NCK, Kx = c.Kx;
+  const double* ebar = c.st->ebar;
   double s = 0.0;
-  for (int ch = 0; ch < d.chunks; ++ch) {
+  for (int ch = 0; ch * kResThreads < c.Kh; ++ch) {
     const int h = ch * kResThreads + threadIdx.x;
     float diff = 0.f;
-    if (h < d.Kh) {
-      const HIdx hi = a.hidx[d.off_h + h];
-      const float4 n = a.hn[d.off_h + h];
+    if (h < c.Kh) {
+      const HIdx hi = c.hidx[h];
+      const float4 n = c.hn[h];
       const long long base = (long long)hi.iy * NCK + hi.j;
       float2 tv[NC], old[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        tv[c] = T[base + c * d.Kx];
-        old[c] = ER[base + c * d.Kx];
+      for (int cc = 0; cc < NC; ++cc) {
+        tv[cc] = c.T[base + cc * Kx];
+        old[cc] = c.ER[base + cc * Kx];
       }
       float er[NC], ei[NC];
-      green_update<NC>(hi.kind, n, tv, ebar, (double)d.N, d.inv2mu0, d.cgam, er, ei);
+      green_update<NC>(hi.kind, n, tv, ebar, c.N, c.inv2mu0, c.cgam, er, ei);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const float dr = er[c] - old[c].x, di = ei[c] - old[c].y;
-        const float wc = (comp6<NC>(c) >= 3) ? 2.f : 1.f;
+      for (int cc = 0; cc < NC; ++cc) {
+        const float dr = er[cc] - old[cc].x, di = ei[cc] - old[cc].y;
+        const float wc = (comp6<NC>(cc) >= 3) ? 2.f : 1.f;
         diff = fmaf(n.w * wc, dr * dr + di * di, diff);
-        ER[base + c * d.Kx] = make_float2(er[c], ei[c]);
+        c.ER[base + cc * Kx] = make_float2(er[cc], ei[cc]);
       }
     }
 #pragma unroll
@@ -1021,8 +1059,7 @@ __device__ __noinline__ double res_green(const BArgs& a, const BDesc& d, int r, 
 }
 
 // the decision of kb_decide for one RVE (thread 0)
-__device__ bool res_decide(const BArgs& a, int r, double s) {
-  BStat& st = a.st[r];
+__device__ bool res_decide(BStat& st, int* n_done, double s) {
   double rr = sqrt(s * st.inv_n2);
   if (st.enorm > 0.0) rr /= st.enorm;
   st.iters += 1;
@@ -1037,35 +1074,34 @@ __device__ bool res_decide(const BArgs& a, int r, double s) {
   } else if (rr < st.tol || st.iters >= st.max_iter) {
     st.done = 1;
   }
-  if (st.done) atomicAdd(a.n_done, 1);
+  if (st.done) atomicAdd(n_done, 1);
   return st.done != 0;
 }
 
 template <int P>
-__device__ __noinline__ void res_solve(const BArgs& a, int r, const BDesc& d, float2* T, float2* Wr,
-                          ResShared& sh) {
+__device__ __noinline__ void res_solve(ResShared& sh, float2* Wr, int* n_done) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   for (;;) {
-    res_inv_y<P>(a, d, T, Wr, sh, lane, wp);
+    res_cols<P>(sh, Wr, lane, wp, true);
     __syncthreads();
-    res_rows<P, false>(a, d, T, Wr, sh, lane, wp, nullptr);
+    res_rows<P>(sh, Wr, lane, wp, false);
     __syncthreads();
-    res_fwd_y<P>(a, d, T, Wr, sh, lane, wp);
+    res_cols<P>(sh, Wr, lane, wp, false);
     __syncthreads();
-    const double s = res_green(a, d, r, T, sh);
-    if (threadIdx.x == 0) sh.done = res_decide(a, r, s) ? 1 : 0;
+    const double s = res_green(sh);
+    if (threadIdx.x == 0) sh.done = res_decide(*sh.c.st, n_done, s) ? 1 : 0;
     __syncthreads();
     if (sh.done) break;
   }
   // final pass: fields of the converged coefficients, homogenised stress
-  res_inv_y<P>(a, d, T, Wr, sh, lane, wp);
+  res_cols<P>(sh, Wr, lane, wp, true);
   __syncthreads();
-  double sb[6] = {0, 0, 0, 0, 0, 0};
-  res_rows<P, true>(a, d, T, Wr, sh, lane, wp, sb);
+  res_rows<P>(sh, Wr, lane, wp, true);
   __syncthreads();
-  for (int i = 0; i < 6; ++i) {
-    const double t = block_sum_d(sb[i], sh.red);
-    if (threadIdx.x == 0) a.st[r].sbar[i] = t / (double)d.N;
+  if (threadIdx.x < 6) {
+    double t = 0.0;
+    for (int w = 0; w < kResWarps; ++w) t += sh.sb[w][threadIdx.x];
+    sh.c.st->sbar[threadIdx.x] = t / sh.c.N;
   }
 }
 
@@ -1077,25 +1113,49 @@ __global__ __launch_bounds__(kResThreads, 2) void kb_resident(BArgs a, const int
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ResShared sh;
   float2* Wr = reinterpret_cast<float2*>(smem) + (size_t)(threadIdx.x >> 5) * kWRegion;
-  float2* T = scratch + (long long)blockIdx.x * slot;
+  if (threadIdx.x < kMaxPhases) sh.ph[threadIdx.x] = a.law.ph[threadIdx.x];
   for (;;) {
     if (threadIdx.x == 0) sh.next = (int)atomicAdd(queue, 1u);
     __syncthreads();
     const int q = sh.next;
     if (q >= n_order) break;
     const int r = order[q];
-    const BDesc d = a.d[r];
+    const BDesc& d = a.d[r];
+    const int nx = d.nx;
+    if (threadIdx.x == 0) {
+      ResCtx& c = sh.c;
+      c.T = scratch + (long long)blockIdx.x * slot;
+      c.ER = a.ER + d.off_er;
+      c.tab = a.tab + d.tab_x;
+      c.phase = a.phase + d.off_phase;
+      c.hidx = a.hidx + d.off_h;
+      c.hn = a.hn + d.off_h;
+      c.st = a.st + r;
+      c.Kx = d.Kx;
+      c.Ky = d.Ky;
+      c.Kh = d.Kh;
+      c.NCK = NC * d.Kx;
+      c.chunks = d.chunks;
+      c.dKx = d.dKx;
+      c.invN = 1.f / (float)d.N;
+      c.lam0 = d.lam0;
+      c.mu0 = d.mu0;
+      c.inv2mu0 = d.inv2mu0;
+      c.cgam = d.cgam;
+      c.N = (double)d.N;
+    }
+    if (threadIdx.x < kResWarps * 6) sh.sb[threadIdx.x / 6][threadIdx.x % 6] = 0.0;
     for (int i = threadIdx.x; i < d.Kx; i += kResThreads) sh.kxs[i] = a.kx[d.off_kx + i];
     for (int i = threadIdx.x; i < d.ny; i += kResThreads) sh.inv_ky[i] = -1;
     __syncthreads();
     for (int i = threadIdx.x; i < d.Ky; i += kResThreads) sh.inv_ky[a.kym[d.off_ky + i]] = i;
     __syncthreads();
-    switch (d.nx) {
-      case 64: res_solve<2>(a, r, d, T, Wr, sh); break;
-      case 96: res_solve<3>(a, r, d, T, Wr, sh); break;
-      case 128: res_solve<4>(a, r, d, T, Wr, sh); break;
-      case 192: res_solve<6>(a, r, d, T, Wr, sh); break;
-      default: res_solve<8>(a, r, d, T, Wr, sh); break;
+    switch (nx) {
+      case 64: res_solve<2>(sh, Wr, a.n_done); break;
+      case 96: res_solve<3>(sh, Wr, a.n_done); break;
+      case 128: res_solve<4>(sh, Wr, a.n_done); break;
+      case 192: res_solve<6>(sh, Wr, a.n_done); break;
+      default: res_solve<8>(sh, Wr, a.n_done); break;
     }
     __syncthreads();   // sh is rewritten for the next RVE
   }
