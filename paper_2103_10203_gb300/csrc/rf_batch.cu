@@ -1013,49 +1013,37 @@ __device__ __noinline__ void res_rows(ResShared& sh, float2* Wr, int lane, int w
   }
 }
 
-// Green step at the RVE's half-pattern entries (chunks of 256, one thread per entry), ER
-// updated, squared-increment measure summed as kb_gamma and kb_decide sum it; the sum is
-// valid in thread 0
+// Green step at the RVE's half-pattern entries (thread t takes entries t, t + kResThreads, ...),
+// ER updated, the squared-increment measure summed in FP64 per thread and over the block in a
+// fixed order; the sum is valid in thread 0
 __device__ __noinline__ double res_green(ResShared& sh) {
   const ResCtx& c = sh.c;
   const int NCK = c.NCK, Kx = c.Kx;
   const double* ebar = c.st->ebar;
   double s = 0.0;
-  for (int ch = 0; ch * kResThreads < c.Kh; ++ch) {
-    const int h = ch * kResThreads + threadIdx.x;
+  for (int h = threadIdx.x; h < c.Kh; h += kResThreads) {
+    const HIdx hi = c.hidx[h];
+    const float4 n = c.hn[h];
+    const long long base = (long long)hi.iy * NCK + hi.j;
+    float2 tv[NC], old[NC];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+      tv[cc] = c.T[base + cc * Kx];
+      old[cc] = c.ER[base + cc * Kx];
+    }
+    float er[NC], ei[NC];
+    green_update<NC>(hi.kind, n, tv, ebar, c.N, c.inv2mu0, c.cgam, er, ei);
     float diff = 0.f;
-    if (h < c.Kh) {
-      const HIdx hi = c.hidx[h];
-      const float4 n = c.hn[h];
-      const long long base = (long long)hi.iy * NCK + hi.j;
-      float2 tv[NC], old[NC];
 #pragma unroll
-      for (int cc = 0; cc < NC; ++cc) {
-        tv[cc] = c.T[base + cc * Kx];
-        old[cc] = c.ER[base + cc * Kx];
-      }
-      float er[NC], ei[NC];
-      green_update<NC>(hi.kind, n, tv, ebar, c.N, c.inv2mu0, c.cgam, er, ei);
-#pragma unroll
-      for (int cc = 0; cc < NC; ++cc) {
-        const float dr = er[cc] - old[cc].x, di = ei[cc] - old[cc].y;
-        const float wc = (comp6<NC>(cc) >= 3) ? 2.f : 1.f;
-        diff = fmaf(n.w * wc, dr * dr + di * di, diff);
-        c.ER[base + cc * Kx] = make_float2(er[cc], ei[cc]);
-      }
+    for (int cc = 0; cc < NC; ++cc) {
+      const float dr = er[cc] - old[cc].x, di = ei[cc] - old[cc].y;
+      const float wc = (comp6<NC>(cc) >= 3) ? 2.f : 1.f;
+      diff = fmaf(n.w * wc, dr * dr + di * di, diff);
+      c.ER[base + cc * Kx] = make_float2(er[cc], ei[cc]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) diff += __shfl_down_sync(0xffffffffu, diff, o);
-    if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = (double)diff;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int k = 0; k < kResWarps; ++k) t += sh.red[k];
-      s += t;
-    }
-    __syncthreads();
+    s += (double)diff;
   }
-  return s;
+  return block_sum_d(s, sh.red);
 }
 
 // the decision of kb_decide for one RVE (thread 0)
