@@ -409,7 +409,7 @@ def learned_summary(rf, torch, n_train, n_test, epochs, steps, single_sample=128
     t0 = time.perf_counter()
     pms, macros = _c5_rves(range(500000, 500000 + n_train))
     pats = W.patterns(pms, 0.05)
-    net = rf.WarmStartNet(512, 1024)
+    net = rf.WarmStartNet(512, 4096)
     net.rf_mlp_set_params(W.init_params(net, 0))
     ds = W.generate(net, pms, macros, pats, ph, chunk=8192)
     del pms, pats

@@ -160,9 +160,11 @@ def slot_keys(slots, pm):
 
 def test_batch_descriptors_slots_and_coefficients_match_oracle(lib):
     import torch
-    pms, macros = population(5)
+    pms, macros = population(6)
     pms[3] = np.ascontiguousarray(pms[3][:15])           # a rectangular cell with an odd side
     pms[4] = random_discs(32, (2.0, 6.0), 0.35, seed=9)
+    # FFT sides on both axes, Ny != Nx (the y transform by FFT with its own twiddles)
+    pms[5] = np.ascontiguousarray(random_discs(48, (2.0, 6.0), 0.3, seed=11)[:24])
     pats = [O.pattern_adapted(pm, 1, k_target(0.08, pm.size)) for pm in pms]
     ph = elastic_phases()
     net = lib.WarmStartNet(16, 8)
