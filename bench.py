@@ -235,16 +235,16 @@ def sources_sha(files):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu capture, or None when a source
-    file the kernel is built from changed since the capture."""
+def ncu_traffic(kernel, key="dram_bytes_per_launch"):
+    """DRAM bytes of `kernel` (per launch, or per `key`) from the committed ncu capture, or None
+    when a source file the kernel is built from changed since the capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as fh:
             k = json.load(fh)["kernels"][kernel]
         if k["sources_sha"] != sources_sha(k["sources"]):
             return None
-        return k["dram_bytes_per_launch"]
+        return k[key]
     except Exception:
         return None
 
@@ -361,6 +361,11 @@ def batch_summary(rf, torch, n, steps, warmup, sample_every=8, resident=0):
     bytes_per_vox_it = 49.0      # phase 1 B + strain in 12 B + tau out 12 B + line I/O 24 B
     achieved = bytes_per_vox_it * value / 1e9
     hbm = _hbm_peak()
+    # DRAM bytes of one solve launch of the resident kernel: the capture's bytes per
+    # voxel-iteration (a smaller batch of the same population) times this solve's
+    # voxel-iterations
+    per_vi = ncu_traffic("kb_resident", "dram_bytes_per_voxel_iteration")
+    traffic = (per_vi * vi / steps) if (per_vi is not None and info.get("resident")) else None
     return {"metric": "RVE voxel-iterations/s to 1e-6 residual, batched (plain start)",
             "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": warmup, "ms_per_step": total_ms / steps,
@@ -380,7 +385,9 @@ def batch_summary(rf, torch, n, steps, warmup, sample_every=8, resident=0):
             "batched_over_per_rve": value / (solo_vi / (solo_ms / 1e3)),
             "gpu_launches": int(launches), "autotuned": info,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "traffic_per_voxel_iteration": (per_vi if traffic is not None
+                                                         else None),
                          "kernel": ("kb_resident (a block per RVE runs all its updates)"
                                     if info.get("resident") else
                                     "whole update (the sweep kernels over all RVEs)"),
