@@ -257,3 +257,23 @@ def test_batch_resident_mode_selection(lib):
     b.close()
     with pytest.raises(lib.RFError):
         lib.BatchSolver(pms, ph, pats, transform="fft", batch_resident=2)
+
+
+def test_batch_resident_reports_divergence(lib):
+    """The RVE-resident solve applies the same divergence rule per RVE: a stiff minority phase
+    (contrast 1000 at about 5 % volume) with a volume-average reference medium ends with
+    RF_ERR_DIVERGED within a few updates, while the homogeneous RVE beside it converges."""
+    from synth import phase_table
+    ph = phase_table([(1.0, 1.0, 0, 0, 0), (1000.0, 1000.0, 0, 0, 0)])
+    good = np.zeros((64, 64), np.uint8)
+    bad = np.zeros((64, 64), np.uint8)
+    bad[20:34, 24:38] = 1                          # 196 of 4096 voxels
+    pats = [O.pattern_adapted(pm, 1, k_target(0.1, pm.size)) for pm in (good, bad)]
+    macro = np.array([[0.01, 0, 0, 0, 0, 0.002]] * 2)
+    b = lib.BatchSolver([good, bad], ph, pats, tol=1e-6, max_iter=500, ref="volume",
+                        transform="fft", batch_resident=1)
+    assert b.rf_batch_info()["resident"]
+    out = b.rf_batch_solve(macro)
+    b.close()
+    assert out["status"][0] == 0 and out["status"][1] == -4 and not out["converged"]
+    assert out["iters"][1] < 20
