@@ -295,3 +295,6 @@ def test_learned_warm_start_cuts_iterations(lib):
     # same fixed point: the stress averages agree to within what tol 1e-6 leaves open
     sp, sl = res["plain"]["sigma_bar"], res["learned"]["sigma_bar"]
     assert np.max(np.abs(sp - sl)) <= 1e-4 * np.max(np.abs(sp))
+    # descriptors computed once for the RVE set: the same warm start, the same solves
+    assert np.array_equal(res["learned_cached"]["iters"], res["learned"]["iters"])
+    assert np.array_equal(res["learned_cached"]["sigma_bar"], sl)
