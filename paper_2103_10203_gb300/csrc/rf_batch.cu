@@ -1,8 +1,12 @@
 // Batched solver: many independent 2D RVEs of uneven size (FE-FFT Gauss points), each with its
 // own phase map, adapted pattern and macroscopic strain, solved together.
 //
-// One update of every unconverged RVE is five persistent kernels, each walking a work list of
-// (RVE, tile) items in a fixed order (largest RVEs first) with a stride of the grid size:
+// Two forms, the faster chosen by timing at creation (options.batch_resident). RVE-resident
+// (kb_resident, square RVEs with sides 64, 96, 128, 192, 256): one launch per solve, a block
+// holds one RVE for all of its updates and its final pass, RVEs taken largest first from a
+// queue. Sweeps: one update of every unconverged RVE is five persistent kernels, each walking
+// a work list of (RVE, tile) items in a fixed order (largest RVEs first) with a stride of the
+// grid size:
 //   inverse y transform tiles, row tiles (x transforms + law), forward y transform tiles,
 //   Green-operator chunks (with squared-increment partials), per-RVE convergence decisions.
 // Items of converged RVEs return at once. A solve is one CUDA graph launch: a conditional while
