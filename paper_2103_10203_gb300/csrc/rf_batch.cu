@@ -781,6 +781,7 @@ struct ResCtx {
 struct ResShared {
   ResCtx c;
   DevPhase ph[kMaxPhases];
+  float2 dph[kMaxPhases];   // per phase (lambda - lambda0, 2 (mu - mu0)) of the RVE's medium
   double sb[kResWarps][6];   // per-warp stress sums of the final pass
   double red[kResWarps];
   int kxs[kResMaxL / 2 + 1];
@@ -963,24 +964,24 @@ __device__ __noinline__ void res_rows(ResShared& sh, float2* Wr, int lane, int w
           float e[NC];
 #pragma unroll
           for (int cc = 0; cc < NC; ++cc) e[cc] = ev[h][cc] * c.invN;
-          float e6[6];
-          comp_to6<NC>(e, e6);
-          const DevPhase ph = sh.ph[phs[(2 * m + h) * L + x]];
-          float ep[6] = {0, 0, 0, 0, 0, 0};
-          LawOut o;
-          stress6<false>(e6, ph, ep, 0.f, o);
+          const int pid = phs[(2 * m + h) * L + x];
           if (final) {
+            float e6[6];
+            comp_to6<NC>(e, e6);
+            const DevPhase ph = sh.ph[pid];
+            float ep[6] = {0, 0, 0, 0, 0, 0};
+            LawOut o;
+            stress6<false>(e6, ph, ep, 0.f, o);
 #pragma unroll
             for (int i = 0; i < 6; ++i) s6[i] += (double)o.s[i];
           } else {
-            const float tr = e6[0] + e6[1] + e6[2];
-            float tau6[6];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) tau6[i] = o.s[i] - (c.lam0 * tr + 2.f * c.mu0 * e6[i]);
-#pragma unroll
-            for (int i = 3; i < 6; ++i) tau6[i] = o.s[i] - 2.f * c.mu0 * e6[i];
-#pragma unroll
-            for (int cc = 0; cc < NC; ++cc) tv[h][cc] = tau6[comp6<NC>(cc)];
+            // elastic phases in plane strain: tau = sigma - C0 : eps
+            //   = (lambda - lambda0) tr(eps) 1 + 2 (mu - mu0) eps, components 11, 22, 12
+            const float2 dm = sh.dph[pid];
+            const float tr = e[0] + e[1];
+            tv[h][0] = fmaf(dm.y, e[0], dm.x * tr);
+            tv[h][1] = fmaf(dm.y, e[1], dm.x * tr);
+            tv[h][2] = dm.y * e[2];
           }
         }
         if (!final) {
@@ -1137,6 +1138,9 @@ __global__ __launch_bounds__(kResThreads, 2) void kb_resident(BArgs a, const int
       c.N = (double)d.N;
     }
     if (threadIdx.x < kResWarps * 6) sh.sb[threadIdx.x / 6][threadIdx.x % 6] = 0.0;
+    if (threadIdx.x < kMaxPhases)
+      sh.dph[threadIdx.x] = make_float2(sh.ph[threadIdx.x].lam - d.lam0,
+                                        2.f * (sh.ph[threadIdx.x].mu - d.mu0));
     for (int i = threadIdx.x; i < d.Kx; i += kResThreads) sh.kxs[i] = a.kx[d.off_kx + i];
     for (int i = threadIdx.x; i < d.ny; i += kResThreads) sh.inv_ky[i] = -1;
     __syncthreads();
