@@ -501,11 +501,12 @@ __device__ __forceinline__ void fwd_batch(float2* v, float2* T, const float2* __
 
 // Row item with warp-resident FFTs (FINAL: homogenised-stress partials after the law). Sequence
 // p = (line 2p) + i (line 2p + 1) of the item's 3 nr lines (line s = r NC + c) lives in warp
-// p / S at p % S; between the transforms the region holds it in space at s L + x.
+// p / S at p % S; between the transforms the region holds it in space at s (L + P) + x (the
+// padded stride keeps the transform's scattered writes free of bank conflicts).
 template <int P, bool FINAL>
 __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned char* smem,
                               double* red) {
-  constexpr int L = 32 * P, S = 32 / P;
+  constexpr int L = 32 * P, S = 32 / P, LS = L + P;   // sequence stride: conflict-free writes
   const int Kx = d.Kx, R = d.R;
   const int row0 = w.y * R;
   const int nr = min(R, d.rows - row0);
@@ -545,7 +546,7 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
         ta[q].y = 0.f;
         tb[q].y = 0.f;
       }
-      float2* z = W0 + (size_t)(pp[q] / S) * kWRegion + (pp[q] % S) * L;
+      float2* z = W0 + (size_t)(pp[q] / S) * kWRegion + (pp[q] % S) * LS;
       z[k] = make_float2(ta[q].x - tb[q].y, ta[q].y + tb[q].x);
       if (!self) z[L - k] = make_float2(ta[q].x + tb[q].y, tb[q].x - ta[q].y);
     }
@@ -559,7 +560,7 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
     for (int s = 0; s < S; ++s)
 #pragma unroll
       for (int n1 = 0; n1 < P; ++n1) {
-        const float2 z = Wr[s * L + 32 * n1 + lane];
+        const float2 z = Wr[s * LS + 32 * n1 + lane];
         v[s * P + n1] = make_float2(z.x, -z.y);
       }
 #pragma unroll
@@ -568,7 +569,7 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
     if (lane < S * P) {
       const int s = lane / P, k1 = lane - s * P;
 #pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = make_float2(v[k2].x, -v[k2].y);
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * LS + k1 + P * k2] = make_float2(v[k2].x, -v[k2].y);
     }
   }
   __syncthreads();
@@ -583,7 +584,7 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int sl = r * NC + c, p = sl >> 1;
-      at[c] = reinterpret_cast<float*>(W0 + (size_t)(p / S) * kWRegion + (p % S) * L + x) +
+      at[c] = reinterpret_cast<float*>(W0 + (size_t)(p / S) * kWRegion + (p % S) * LS + x) +
               (sl & 1);
       e[c] = *at[c] * invN;
     }
@@ -617,7 +618,7 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
   // an odd line count leaves the last sequence's imaginary carrier unused: zero it
   if (nl & 1) {
     const int p = nseq - 1;
-    float2* z = W0 + (size_t)(p / S) * kWRegion + (p % S) * L;
+    float2* z = W0 + (size_t)(p / S) * kWRegion + (p % S) * LS;
     for (int x = tid; x < L; x += blockDim.x) z[x].y = 0.f;
   }
   __syncthreads();
@@ -625,14 +626,14 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
-      for (int n1 = 0; n1 < P; ++n1) v[s * P + n1] = Wr[s * L + 32 * n1 + lane];
+      for (int n1 = 0; n1 < P; ++n1) v[s * P + n1] = Wr[s * LS + 32 * n1 + lane];
 #pragma unroll
     for (int r = S * P; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
     fwd_batch<P>(v, Wr, tab, lane);
     if (lane < S * P) {
       const int s = lane / P, k1 = lane - s * P;
 #pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = v[k2];
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * LS + k1 + P * k2] = v[k2];
     }
   }
   __syncthreads();
@@ -640,7 +641,7 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
   for (int u = tid; u < nl * Kx; u += blockDim.x) {
     const int sl = fdiv(u, d.dKx), j = u - sl * Kx;
     const int k = kxs[j], p = sl >> 1;
-    const float2* z = W0 + (size_t)(p / S) * kWRegion + (p % S) * L;
+    const float2* z = W0 + (size_t)(p / S) * kWRegion + (p % S) * LS;
     const float2 zk = z[k], zm = z[k == 0 ? 0 : L - k];
     float2 out;
     if ((sl & 1) == 0) out = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
@@ -656,7 +657,7 @@ __device__ void row_item_warp(const BArgs& a, int2 w, const BDesc& d, unsigned c
 template <int P>
 __device__ void col_item_warp(const BArgs& a, int g, const BDesc& d, unsigned char* smem,
                               int sign) {
-  constexpr int L = 32 * P, S = 32 / P, G = 8 * S;
+  constexpr int L = 32 * P, S = 32 / P, G = 8 * S, LS = L + P;
   const int NCK = NC * d.Kx;
   const int c0 = g * G, cc_n = min(G, NCK - c0);
   const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
@@ -680,7 +681,7 @@ __device__ void col_item_warp(const BArgs& a, int g, const BDesc& d, unsigned ch
       if (i < tot) {
         const int r = i / cc_n, cc = i - r * cc_n;
         v[u] = src[(long long)r * NCK + c0 + cc];
-        dst[u] = (cc / S) * kWRegion + (cc % S) * L + (sign > 0 ? kym[r] : r);
+        dst[u] = (cc / S) * kWRegion + (cc % S) * LS + (sign > 0 ? kym[r] : r);
       }
     }
 #pragma unroll
@@ -695,7 +696,7 @@ __device__ void col_item_warp(const BArgs& a, int g, const BDesc& d, unsigned ch
     for (int s = 0; s < S; ++s)
 #pragma unroll
       for (int n1 = 0; n1 < P; ++n1) {
-        const float2 z = Wr[s * L + 32 * n1 + lane];
+        const float2 z = Wr[s * LS + 32 * n1 + lane];
         v[s * P + n1] = make_float2(z.x, cj * z.y);
       }
 #pragma unroll
@@ -704,7 +705,7 @@ __device__ void col_item_warp(const BArgs& a, int g, const BDesc& d, unsigned ch
     if (lane < S * P) {
       const int s = lane / P, k1 = lane - s * P;
 #pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) Wr[s * L + k1 + P * k2] = make_float2(v[k2].x, cj * v[k2].y);
+      for (int k2 = 0; k2 < 32; ++k2) Wr[s * LS + k1 + P * k2] = make_float2(v[k2].x, cj * v[k2].y);
     }
   }
   __syncthreads();
@@ -713,7 +714,7 @@ __device__ void col_item_warp(const BArgs& a, int g, const BDesc& d, unsigned ch
   for (int i = tid; i < rows_out * cc_n; i += blockDim.x) {
     const int r = i / cc_n, cc = i - r * cc_n;
     dstg[(long long)r * NCK + c0 + cc] =
-        W0[(cc / S) * kWRegion + (cc % S) * L + (sign > 0 ? r : kym[r])];
+        W0[(cc / S) * kWRegion + (cc % S) * LS + (sign > 0 ? r : kym[r])];
   }
   __syncthreads();   // the next item reuses the regions
 }
