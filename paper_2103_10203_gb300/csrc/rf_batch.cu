@@ -751,7 +751,8 @@ __global__ __launch_bounds__(256, 2) void kb_row_w(BArgs a) {
 // ---- RVE-resident solve: a block holds one RVE for every update of its solve
 //
 // Each block of kResWarps warps takes RVEs from a queue (largest first) and runs all updates of
-// its RVE back to back: the inverse y transforms of the coefficients (S line columns per warp),
+// its RVE back to back (each the update of Sec. 4, steps d, a, b, c in that order, and the
+// convergence test): the inverse y transforms of the coefficients (S line columns per warp),
 // the row passes (R_w rows per warp: their 3 R_w lines as packed pairs, inverse x transform,
 // law, forward x transform, the coefficients at the pattern's kx), the forward y transforms,
 // the Green step with the FP64 measure (the chunked reduction of kb_gamma / kb_decide), and the
