@@ -755,8 +755,8 @@ __global__ __launch_bounds__(256, 2) void kb_row_w(BArgs a) {
 // convergence test): the inverse y transforms of the coefficients (S line columns per warp),
 // the row passes (R_w rows per warp: their 3 R_w lines as packed pairs, inverse x transform,
 // law, forward x transform, the coefficients at the pattern's kx), the forward y transforms,
-// the Green step with the FP64 measure (the chunked reduction of kb_gamma / kb_decide), and the
-// decision; then the final pass (homogenised stress). Block barriers separate the phases; no
+// the Green step with the FP64 measure (a partial per thread, one block sum), and the decision
+// (the rules of kb_decide); then the final pass (homogenised stress). Block barriers separate the phases; no
 // block waits for another. The line transforms live in the block's scratch slot in global
 // memory, [Ny][NC Kx] (the RVE's working set, L2-resident while the block holds it); the RVE's
 // parameters, the phase table and the pattern's index maps sit in shared memory.
@@ -774,7 +774,7 @@ struct ResCtx {
   const HIdx* hidx;
   const float4* hn;
   BStat* st;
-  int Kx, Ky, Kh, NCK, chunks, pad;
+  int Kx, Ky, Kh, NCK, chunks, pad;   // chunks: as in BDesc (kept for the layout)
   FastDiv dKx;
   float invN, lam0, mu0, inv2mu0, cgam, pad2;
   double N;
